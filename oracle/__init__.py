@@ -1,0 +1,281 @@
+"""CPU oracle for the connected-sum hot path of CoS++ (arXiv 2507.12349).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+timed CPU baseline of ``bench.py`` may import this package.  It shares no code
+with the CUDA path; both read the seeded inputs of
+``paper_2507_12349_b300.inputs`` and nothing else in common.
+
+Functions and the passages they follow:
+
+* ``brute``    -- sum over decorated covers, enumerated one by one (the
+  definition of the connected sum, Results A: cycle covers, -1 and a flavor
+  weight per closed loop, connectivity of the vertex graph).  n <= 5.
+* ``closed``   -- determinants of every flavor block plus the subset
+  subtraction c(S) = a(S) - sum c(T) a(S \\ T) of Methods A.  n <= 12.
+* ``dp``       -- the merged clow-sequence DP of Results A / Alg. 2-3 in plain
+  loops (``oracle_impl.h`` states each rule).  n <= 12.
+* ``point_dp`` -- the unmerged point form of Alg. 2 (visited point set R, new
+  heads at the smallest unvisited partner of a visited point), pure Python.
+* ``propagators`` -- G0 tables by the plain momentum sum of Methods A, the
+  linear interpolation in tau and the gather into M.
+* ``torch_brute`` -- the brute-force sum as dense torch ops, for autograd.
+
+Precision: 'd' (double), 'ld' (x87 long double) or 'q' (__float128).
+"""
+from __future__ import annotations
+
+import ctypes
+import itertools
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build_oracle
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build_oracle.build()
+        L = ctypes.CDLL(path)
+        dp_ = ctypes.POINTER(ctypes.c_double)
+        for sfx in ("_d", "_ld", "_q"):
+            f = getattr(L, "brute" + sfx)
+            f.argtypes = [ctypes.c_int, ctypes.c_int, dp_, dp_, ctypes.c_int, dp_, dp_]
+            f.restype = ctypes.c_int
+            f = getattr(L, "closed" + sfx)
+            f.argtypes = [ctypes.c_int, ctypes.c_int, dp_, dp_, dp_, dp_, dp_, dp_]
+            f.restype = ctypes.c_int
+            f = getattr(L, "dp" + sfx)
+            f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp_, dp_, ctypes.c_int, dp_, dp_]
+            f.restype = ctypes.c_int
+            f = getattr(L, "dp_batch" + sfx)
+            f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp_, dp_, ctypes.c_int,
+                          dp_, dp_, ctypes.c_int]
+            f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def tiled(M: np.ndarray) -> np.ndarray:
+    """Point matrices [nf][2n][2n] from vertex matrices [nf][n][n]: the
+    2n x 2n matrix indexed by vertex = point mod n (Alg. 3's A_l indexing)."""
+    M = np.asarray(M, dtype=np.float64)
+    return np.ascontiguousarray(np.tile(M, (1, 2, 2)))
+
+
+def brute(A_points: np.ndarray, sigma: Optional[Sequence[float]] = None, connected: bool = True,
+          prec: str = "d") -> float:
+    """Sum over (connected) decorated covers of 2n points, point matrices
+    [nf][2n][2n]; sigma = per-flavor shift weights or None (no shift points)."""
+    A = _f64(A_points)
+    nf, np2, _ = A.shape
+    n = np2 // 2
+    sig = None if sigma is None else _f64(sigma)
+    hi, lo = ctypes.c_double(), ctypes.c_double()
+    rc = getattr(lib(), "brute_" + prec)(n, nf, _ptr(A), _ptr(sig), int(connected),
+                                          ctypes.byref(hi), ctypes.byref(lo))
+    if rc:
+        raise ValueError("brute: unsupported sizes")
+    return hi.value + lo.value
+
+
+def closed(M: np.ndarray, sigma: Optional[Sequence[float]] = None, prec: str = "d",
+           subsets: bool = False):
+    """Connected sum c(V) from determinants and the subset subtraction; with
+    subsets=True also returns a(S) for every S and c(S) for every S containing
+    vertex 0 (bit i of S = vertex i)."""
+    M = _f64(M)
+    nf, n, _ = M.shape
+    sig = None if sigma is None else _f64(sigma)
+    hi, lo = ctypes.c_double(), ctypes.c_double()
+    a_all = np.zeros(1 << n) if subsets else None
+    c_all = np.zeros(1 << n) if subsets else None
+    rc = getattr(lib(), "closed_" + prec)(n, nf, _ptr(M), _ptr(sig), ctypes.byref(hi), ctypes.byref(lo),
+                                           _ptr(a_all), _ptr(c_all))
+    if rc:
+        raise ValueError("closed: unsupported sizes")
+    if subsets:
+        return hi.value + lo.value, a_all, c_all
+    return hi.value + lo.value
+
+
+def dp(M: np.ndarray, sigma: Optional[Sequence[float]] = None, weight: int = 1, absmode: bool = False,
+       prec: str = "d", pair: bool = False):
+    """Merged DP.  M [nf][n][n]; `weight` multiplies every closed loop (the
+    symmetric SU(N) run passes one matrix and weight N)."""
+    M = _f64(M)
+    nf, n, _ = M.shape
+    sig = None if sigma is None else _f64(sigma)
+    hi, lo = ctypes.c_double(), ctypes.c_double()
+    rc = getattr(lib(), "dp_" + prec)(n, nf, int(weight), _ptr(M), _ptr(sig), int(absmode),
+                                       ctypes.byref(hi), ctypes.byref(lo))
+    if rc:
+        raise ValueError("dp: unsupported sizes")
+    return (hi.value, lo.value) if pair else hi.value + lo.value
+
+
+def dp_batch(Ms: np.ndarray, sigma: Optional[Sequence[float]] = None, weight: int = 1,
+             absmode: bool = False, prec: str = "d", nthreads: int = 0) -> Tuple[np.ndarray, np.ndarray, int]:
+    """Merged DP over a batch [cfg][nf][n][n] of one order (OpenMP over
+    configurations).  Returns (hi, lo, threads used)."""
+    Ms = _f64(Ms)
+    ncfg, nf, n, _ = Ms.shape
+    sig = None if sigma is None else _f64(sigma)
+    hi = np.zeros(ncfg)
+    lo = np.zeros(ncfg)
+    used = getattr(lib(), "dp_batch_" + prec)(ncfg, n, nf, int(weight), _ptr(Ms), _ptr(sig), int(absmode),
+                                               _ptr(hi), _ptr(lo), int(nthreads))
+    if used < 0:
+        raise ValueError("dp_batch: unsupported sizes")
+    return hi, lo, used
+
+
+# ------------------------------------------------------------------ pure Python tiers
+
+def brute_py(A_points: np.ndarray, sigma=None, connected: bool = True) -> float:
+    """Second, independent brute force in pure Python (n <= 3): enumerate
+    decorations, then permutations of the normal points; weight = product over
+    cycles of (-sum_l prod A^l * prod of -sigma_l over shifts whose partner
+    is on the cycle)."""
+    A = np.asarray(A_points, dtype=np.float64)
+    nf, np2, _ = A.shape
+    n = np2 // 2
+    total = 0.0
+    decos = itertools.product(range(3), repeat=n) if sigma is not None else [(0,) * n]
+    for deco in decos:
+        shifts = {i if d == 1 else i + n for i, d in enumerate(deco) if d}
+        pts = [p for p in range(np2) if p not in shifts]
+        for img in itertools.permutations(pts):
+            pi = dict(zip(pts, img))
+            if connected:
+                comp = {i: i for i in range(n)}
+
+                def find(x):
+                    while comp[x] != x:
+                        x = comp[x]
+                    return x
+                for p in pts:
+                    comp[find(p % n)] = find(pi[p] % n)
+                if len({find(i) for i in range(n)}) > 1:
+                    continue
+            seen = set()
+            w = 1.0
+            for p in pts:
+                if p in seen:
+                    continue
+                cyc = []
+                q = p
+                while q not in seen:
+                    seen.add(q)
+                    cyc.append(q)
+                    q = pi[q]
+                loop = 0.0
+                for l in range(nf):
+                    t = 1.0
+                    for q in cyc:
+                        t *= A[l, q, pi[q]]
+                    for q in cyc:
+                        if (q + n) % np2 in shifts:
+                            t *= -sigma[l]
+                    loop += t
+                w *= -loop
+            total += w
+    return total
+
+
+def point_dp(A_points: np.ndarray, weight: int = 1, connected: bool = True) -> float:
+    """Unmerged point form of Alg. 2 (no sublattice labels, no shifts), pure
+    Python.  States (u, v, R): head point u, current point v, visited point
+    set R.  Extend: v -> w for every w not in R, weight A[v][w].  Close:
+    weight -A[v][u] (times `weight`, Alg. 2's N_f); the next head is the
+    smallest unvisited point whose partner is visited (connected=True, Results
+    A / Alg. 2's P set) or simply the smallest unvisited point (connected=False,
+    the Mahajan-Vinay head rule restricted to cycle covers).  With one matrix,
+    weight 1 and connected=False the sum is det(A) (Results A)."""
+    A = np.asarray(A_points, dtype=np.float64)
+    np2 = A.shape[0]
+    n = np2 // 2
+    full = (1 << np2) - 1
+    layer = {(0, 0, 1): 1.0}
+    S = 0.0
+    for _ in range(np2):
+        nxt = {}
+        for (u, v, R), w in layer.items():
+            for x in range(np2):
+                if not R & (1 << x):
+                    key = (u, x, R | (1 << x))
+                    nxt[key] = nxt.get(key, 0.0) + w * A[v, x]
+            cw = -w * A[v, u] * weight
+            if R == full:
+                S += cw
+                continue
+            if connected:
+                cand = [q for q in range(np2) if not R & (1 << q) and R & (1 << ((q + n) % np2))]
+            else:
+                cand = [q for q in range(np2) if not R & (1 << q)]
+            if cand:
+                h = min(cand)
+                key = (h, h, R | (1 << h))
+                nxt[key] = nxt.get(key, 0.0) + cw
+        layer = nxt
+    return S
+
+
+def torch_brute(M, sigma=None):
+    """Connected sum as dense torch ops over the enumerated connected
+    decorated covers of the tiled matrix (n <= 3); differentiable in M
+    [nf][n][n] and sigma [nf] (autograd reference for the adjoint)."""
+    import torch
+    nf, n, _ = M.shape
+    np2 = 2 * n
+    total = M.new_zeros(())
+    decos = itertools.product(range(3), repeat=n) if sigma is not None else [(0,) * n]
+    for deco in decos:
+        shifts = {i if d == 1 else i + n for i, d in enumerate(deco) if d}
+        pts = [p for p in range(np2) if p not in shifts]
+        for img in itertools.permutations(pts):
+            pi = dict(zip(pts, img))
+            comp = {i: i for i in range(n)}
+
+            def find(x):
+                while comp[x] != x:
+                    x = comp[x]
+                return x
+            for p in pts:
+                comp[find(p % n)] = find(pi[p] % n)
+            if len({find(i) for i in range(n)}) > 1:
+                continue
+            seen = set()
+            w = M.new_ones(())
+            for p in pts:
+                if p in seen:
+                    continue
+                cyc = []
+                q = p
+                while q not in seen:
+                    seen.add(q)
+                    cyc.append(q)
+                    q = pi[q]
+                rows = torch.tensor([q % n for q in cyc])
+                cols = torch.tensor([pi[q] % n for q in cyc])
+                per_flavor = M[:, rows, cols].prod(dim=1)
+                nsh = sum(1 for q in cyc if (q + n) % np2 in shifts)
+                if nsh:
+                    per_flavor = per_flavor * (-sigma) ** nsh
+                w = w * (-per_flavor.sum())
+            total = total + w
+    return total
