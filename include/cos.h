@@ -1,0 +1,191 @@
+/*
+ * libcos -- connected-sum hot path of CoS++ (arXiv 2507.12349) on one B300.
+ *
+ * For each Monte Carlo configuration of n interaction vertices X_i = (r_i, tau_i)
+ * the library returns the sum of all connected Feynman diagrams of order n of a
+ * square-lattice SU(N_f) Hubbard model (Methods A: "the coefficients f_n are
+ * the sum of all connected diagrams at order n"), evaluated with the
+ * cycle-aware clow-sequence dynamic program of Results A and Alg. 2-3, in its
+ * merged contact-interaction form (Results A: interaction masks in {0,1,2}
+ * replace the visited point set, cost O(n^3 3^n)).
+ *
+ * Conventions shared by every entry point
+ *   - Result c(V) is the bare combinatorial sum: sum over connected decorated
+ *     covers of the 2n points (point i and i+n belong to vertex i) of
+ *     prod_loops ( -sum_l prod G0^l(edge) prod_{shifts on the loop} (-sigma_l) ),
+ *     with at most one shift point per vertex (counter-term, Methods A shifted
+ *     action) whose weight takes the flavor of its partner's loop (Alg. 3).
+ *     Prefactors (-U)^n / n! are the caller's business.
+ *   - A "symmetric" run (all flavors share one propagator and one shift)
+ *     carries one matrix per configuration and weight N_f per closed loop
+ *     (Alg. 2 multiplies every close by N_f).
+ *   - Device pointers (d_*) are caller-owned CUDA device memory; host
+ *     pointers (h_*) are read before the call returns.  Every call is
+ *     asynchronous on `stream` (a cudaStream_t, 0 = legacy default stream).
+ *     Argument errors are returned synchronously; errors detected on the
+ *     device (order out of range, non-finite result) are recorded in a
+ *     per-stream status word reported by cos_sync_status().
+ *   - No entry point falls back to host arithmetic: without a usable CUDA
+ *     device the calls return COS_ERR_CUDA.
+ *   - Calls enqueued on different streams of one device use different
+ *     internal workspaces and may overlap; calls on one stream serialize.
+ */
+#ifndef COS_H
+#define COS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define COS_NMAX 12      /* largest order n supported (3^12 interaction masks) */
+#define COS_MAX_FLAVORS 8
+
+typedef void *cos_stream_t; /* cudaStream_t */
+
+typedef enum {
+    COS_OK = 0,
+    COS_ERR_ARG = -1,           /* null pointer, negative count, bad enum */
+    COS_ERR_ORDER = -2,         /* an order n < 1 or n > n_max (or > COS_NMAX) */
+    COS_ERR_CUDA = -3,          /* a CUDA call failed (message: cos_last_error) */
+    COS_ERR_TIMEOUT = -4,       /* a bounded device-side wait gave up */
+    COS_ERR_NONFINITE = -5,     /* a result was NaN or infinite */
+    COS_ERR_UNIMPLEMENTED = -6,
+    COS_ERR_NOMEM = -7          /* device workspace could not be allocated */
+} cos_status;
+
+typedef enum {
+    COS_FP64 = 0,   /* every step in FP64 */
+    COS_MIXED = 1   /* clow extension in FP32 with FP32 accumulation; loop-closing
+                       sums, seeds of new loops and the sink in FP64 */
+} cos_precision;
+
+/* Square-lattice model (Methods A): dispersion
+ *   xi_l(k) = -2t [cos k_x + cos k_y] - mu_l + alpha_l,  k = 2 pi m / L,
+ * shift weight sigma_l = alpha_l / U (equal-time shift of SB-CoS, Methods A).
+ * mu and alpha are host arrays of n_flavors values.  The imaginary-time grid
+ * holds n_tau points tau_m = m beta / (n_tau - 1), m = 0 .. n_tau - 1. */
+typedef struct {
+    int L;
+    double t, beta, U;
+    int n_flavors;
+    const double *mu;
+    const double *alpha;
+    int n_tau;
+} cos_model;
+
+typedef struct cos_tables cos_tables; /* opaque; owns device propagator tables */
+
+typedef struct {
+    int L, n_tau, n_flavors;
+    int symmetric;          /* 1: one table and weight n_flavors per loop */
+    int n_mat;              /* matrices per configuration: 1 if symmetric else n_flavors */
+    double beta, U;
+    double sigma[COS_MAX_FLAVORS];
+    const double *d_G;      /* [n_mat][L*L][n_tau]  G0(r, tau_m), r = x + L y */
+    const double *d_dGdmu;  /* same layout, d G0 / d mu; NULL until a gradient call */
+} cos_tables_info;
+
+/* ------------------------------------------------------------------ K-TAB
+ * Tabulates, on the device, for every distinct flavor l
+ *   G0_l(r, tau_m) = -(1/L^2) sum_k cos(k.r) exp(-xi tau_m)(1 - n_F(xi))
+ * (Methods A dispersion; G0 = -<T c c^+>, antiperiodic in tau), stored at
+ * tau_m for m = 0 .. n_tau-1 (G(0^+) first, G(beta^-) last).
+ * model      host struct; copied.  L in [1, 256], n_tau in [2, 65536],
+ *            n_flavors in [1, COS_MAX_FLAVORS], beta > 0, U != 0.
+ * out        receives a new table object owned by the caller (cos_free_tables).
+ * The call returns after the tables are complete (it synchronizes `stream`). */
+cos_status cos_build_propagators(const cos_model *model, cos_stream_t stream, cos_tables **out);
+cos_status cos_free_tables(cos_tables *tables);
+cos_status cos_get_tables_info(const cos_tables *tables, cos_tables_info *info);
+/* Copies a whole table ([n_mat][L*L][n_tau] doubles) into caller device memory d_dst,
+ * asynchronously on `stream`.  which = 0: G0; which = 1: dG0/dmu (built on first request). */
+cos_status cos_copy_table(const cos_tables *tables, int which, double *d_dst, cos_stream_t stream);
+
+/* ------------------------------------------------------------------ K-GATHER
+ * M^l[i][j] = G0_l(r_i - r_j, tau_i - tau_j) for every configuration (Methods A:
+ * the matrix entries g(X_i, X_j) of the diagrammatic expansion), by linear
+ * interpolation in tau; a difference dt <= 0 (equal times and the diagonal
+ * included) is read as -G0(r, dt + beta), i.e. equal times at tau = 0^-.
+ * d_order[c]  n_c in [1, COS_NMAX]
+ * d_offset[c] index of the first vertex of configuration c in d_site / d_tau
+ * d_site[k]   x + L*y in [0, L^2);  d_tau[k] in [0, beta)
+ * d_moff[c]   offset (in doubles) of configuration c's block [n_mat][n_c][n_c]
+ *             in d_M (row-major, row i = first vertex).
+ * Out-of-range orders or sites set the device status (COS_ERR_ORDER / COS_ERR_ARG). */
+cos_status cos_gather(const cos_tables *tables, int n_cfg, const int32_t *d_order,
+                      const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
+                      const int64_t *d_moff, double *d_M, cos_stream_t stream);
+
+/* ------------------------------------------------------------------ K-DP
+ * Connected sum of every configuration from explicit matrices (the DP
+ * proper: seed, clow extension, loop closing, sink).
+ * n_cfg        number of configurations (0 allowed)
+ * n_max        largest order present (sizes the workspace); orders must lie
+ *              in [1, n_max], n_max <= COS_NMAX
+ * d_order[c]   order n_c
+ * d_moff[c]    offset of configuration c's matrices [n_mat][n_c][n_c] in d_M
+ * n_mat        matrices per configuration: 1 (symmetric) or the number of
+ *              flavors (broken), <= COS_MAX_FLAVORS
+ * loop_weight  weight of a closed loop beyond the flavor sum: N_f for a
+ *              symmetric run (n_mat = 1), 1 for a broken run
+ * h_sigma      host array of n_mat shift weights sigma_l, or NULL (no shifts)
+ * d_out[c]     connected sum c(V) of configuration c
+ * d_abs_mass   NULL, or d_abs_mass[c] = the same DP on |M|, |sigma| with every
+ *              sign +, an upper bound of sum |term| (for error statements)
+ * Configurations of different orders share one persistent launch (largest
+ * order first, one CTA per batch of configurations). */
+cos_status cos_connected_sum_matrices(int n_cfg, int n_max, const int32_t *d_order,
+                                      const int64_t *d_moff, int n_mat, int loop_weight,
+                                      const double *h_sigma, const double *d_M,
+                                      cos_precision precision, double *d_out,
+                                      double *d_abs_mass, cos_stream_t stream);
+
+/* Gather + DP from vertex coordinates (arguments as in cos_gather and
+ * cos_connected_sum_matrices; sigma and the loop weight come from the tables). */
+cos_status cos_connected_sum_batch(const cos_tables *tables, int n_cfg, int n_max,
+                                   const int32_t *d_order, const int64_t *d_offset,
+                                   const int32_t *d_site, const double *d_tau,
+                                   cos_precision precision, double *d_out,
+                                   double *d_abs_mass, cos_stream_t stream);
+
+/* ------------------------------------------------------------------ status
+ * Synchronizes `stream`, returns and clears the device status word of the
+ * calls enqueued on it (COS_OK if none failed). */
+cos_status cos_sync_status(cos_stream_t stream);
+const char *cos_status_string(cos_status status);
+/* Message of the last synchronous error in this thread ("" if none). */
+const char *cos_last_error(void);
+
+/* ------------------------------------------------------------------ structure (host only)
+ * Counts of the merged DP for order n (no device needed): interaction masks
+ * (mu_0 >= 1), state slots (head x endpoint per mask), reachable states, and
+ * the FP64 multiply-adds of one flavor array (extension dot products and
+ * loop-closing sums over reachable states) plus the shift products. */
+typedef struct {
+    int n;
+    int64_t masks;
+    int64_t slots;
+    int64_t max_layer_slots;
+    int64_t states;
+    int64_t fma_ext;        /* clow extension multiply-adds */
+    int64_t fma_close;      /* loop-closing multiply-adds */
+    int64_t mul_shift;      /* shift-target products (one per row and untouched vertex) */
+} cos_structure_info;
+
+cos_status cos_structure(int n, cos_structure_info *info);
+
+/* ------------------------------------------------------------------ measurement
+ * Peak-throughput probe (no counterpart in the paper; it supplies the roofline
+ * denominator of the FP64 / FP32 pipes).  kind 0: FP64 FMA, 8 independent chains
+ * per thread; kind 1: FP32 FMA, 16 chains.  Work = 2 * blocks * threads * chains
+ * * iters flops.  d_sink: device buffer of `blocks` elements of the probed type
+ * (written only if a chain hits an impossible value).  Time it with CUDA events. */
+cos_status cos_peak_probe(int kind, int blocks, int threads, int iters, void *d_sink, cos_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COS_H */

@@ -1,0 +1,237 @@
+"""ctypes binding of libcos (include/cos.h): same names, argument marshalling only.
+
+Every step of the connected-sum path runs in the CUDA kernels of libcos.so; this
+module only converts torch tensors to device pointers and the current CUDA
+stream to a handle.  There is no host fallback: if the library or a CUDA device
+is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+COS_NMAX = 12
+COS_MAX_FLAVORS = 8
+COS_FP64 = 0
+COS_MIXED = 1
+PRECISIONS = {"fp64": COS_FP64, "mixed": COS_MIXED}
+
+STATUS = {0: "COS_OK", -1: "COS_ERR_ARG", -2: "COS_ERR_ORDER", -3: "COS_ERR_CUDA", -4: "COS_ERR_TIMEOUT",
+          -5: "COS_ERR_NONFINITE", -6: "COS_ERR_UNIMPLEMENTED", -7: "COS_ERR_NOMEM"}
+
+# Every symbol include/cos.h declares (checked by the CPU tests).
+EXPORTS = [
+    "cos_build_propagators", "cos_free_tables", "cos_get_tables_info", "cos_copy_table", "cos_gather",
+    "cos_connected_sum_matrices", "cos_connected_sum_batch", "cos_sync_status", "cos_status_string",
+    "cos_last_error", "cos_structure", "cos_peak_probe",
+]
+
+
+class CosError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} {message}".strip())
+
+
+class cos_model(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("t", ctypes.c_double), ("beta", ctypes.c_double), ("U", ctypes.c_double),
+                ("n_flavors", ctypes.c_int), ("mu", ctypes.POINTER(ctypes.c_double)),
+                ("alpha", ctypes.POINTER(ctypes.c_double)), ("n_tau", ctypes.c_int)]
+
+
+class cos_tables_info(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("n_tau", ctypes.c_int), ("n_flavors", ctypes.c_int),
+                ("symmetric", ctypes.c_int), ("n_mat", ctypes.c_int), ("beta", ctypes.c_double),
+                ("U", ctypes.c_double), ("sigma", ctypes.c_double * COS_MAX_FLAVORS),
+                ("d_G", ctypes.c_void_p), ("d_dGdmu", ctypes.c_void_p)]
+
+
+class cos_structure_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("masks", ctypes.c_int64), ("slots", ctypes.c_int64),
+                ("max_layer_slots", ctypes.c_int64), ("states", ctypes.c_int64), ("fma_ext", ctypes.c_int64),
+                ("fma_close", ctypes.c_int64), ("mul_shift", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib(build: bool = True):
+    """Load libcos.so (building it from source first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise OSError(f"libcos.so not found at {path}; run paper_2507_12349_b300.build")
+        L = ctypes.CDLL(path)
+        vp, i32, i64, dptr = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+        L.cos_build_propagators.argtypes = [ctypes.POINTER(cos_model), vp, ctypes.POINTER(vp)]
+        L.cos_free_tables.argtypes = [vp]
+        L.cos_get_tables_info.argtypes = [vp, ctypes.POINTER(cos_tables_info)]
+        L.cos_copy_table.argtypes = [vp, i32, vp, vp]
+        L.cos_gather.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.cos_connected_sum_matrices.argtypes = [i32, i32, vp, vp, i32, i32, dptr, vp, i32, vp, vp, vp]
+        L.cos_connected_sum_batch.argtypes = [vp, i32, i32, vp, vp, vp, vp, i32, vp, vp, vp]
+        L.cos_sync_status.argtypes = [vp]
+        L.cos_status_string.argtypes = [i32]
+        L.cos_status_string.restype = ctypes.c_char_p
+        L.cos_last_error.argtypes = []
+        L.cos_last_error.restype = ctypes.c_char_p
+        L.cos_structure.argtypes = [i32, ctypes.POINTER(cos_structure_info)]
+        L.cos_peak_probe.argtypes = [i32, i32, i32, i32, vp, vp]
+        for name in EXPORTS:
+            f = getattr(L, name)
+            if name not in ("cos_status_string", "cos_last_error"):
+                f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise CosError(rc, where, lib().cos_last_error().decode())
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Tables:
+    """Owner of device propagator tables (cos_build_propagators / cos_free_tables)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self.handle = handle
+
+    def info(self) -> cos_tables_info:
+        inf = cos_tables_info()
+        _check(lib().cos_get_tables_info(self.handle, ctypes.byref(inf)), "cos_get_tables_info")
+        return inf
+
+    def table(self, deriv: bool = False, stream=None):
+        """Device copy of the table [n_mat][L^2][n_tau] (G0, or dG0/dmu with deriv=True)."""
+        import torch
+        inf = self.info()
+        buf = torch.empty(inf.n_mat * inf.L * inf.L * inf.n_tau, dtype=torch.float64, device="cuda")
+        _check(lib().cos_copy_table(self.handle, int(deriv), _ptr(buf), _stream(stream)), "cos_copy_table")
+        return buf.view(inf.n_mat, inf.L * inf.L, inf.n_tau)
+
+    def close(self):
+        if self.handle:
+            lib().cos_free_tables(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cos_build_propagators(L: int, t: float, beta: float, U: float, mu: Sequence[float], alpha: Sequence[float],
+                          n_tau: int, stream=None) -> Tables:
+    mu_a = (ctypes.c_double * len(mu))(*mu)
+    al_a = (ctypes.c_double * len(alpha))(*alpha)
+    m = cos_model(int(L), float(t), float(beta), float(U), len(mu), mu_a, al_a, int(n_tau))
+    h = ctypes.c_void_p()
+    _check(lib().cos_build_propagators(ctypes.byref(m), _stream(stream), ctypes.byref(h)), "cos_build_propagators")
+    return Tables(h)
+
+
+def tables_for(model, stream=None) -> Tables:
+    """Tables for an inputs.Model."""
+    return cos_build_propagators(model.L, model.t, model.beta, model.U, model.mu, model.alpha, model.n_tau, stream)
+
+
+def cos_gather(tables: Tables, order, offset, site, tau, moff, M, stream=None):
+    _check(lib().cos_gather(tables.handle, int(order.numel()), _ptr(order), _ptr(offset), _ptr(site), _ptr(tau),
+                            _ptr(moff), _ptr(M), _stream(stream)), "cos_gather")
+
+
+def cos_connected_sum_matrices(n_max: int, order, moff, n_mat: int, loop_weight: int,
+                               sigma: Optional[Sequence[float]], M, precision: str, out, abs_mass=None,
+                               stream=None):
+    sig = None
+    if sigma is not None:
+        sig = (ctypes.c_double * n_mat)(*[float(s) for s in sigma])
+    _check(lib().cos_connected_sum_matrices(int(order.numel()), int(n_max), _ptr(order), _ptr(moff), int(n_mat),
+                                            int(loop_weight), sig, _ptr(M), PRECISIONS[precision], _ptr(out),
+                                            _ptr(abs_mass), _stream(stream)), "cos_connected_sum_matrices")
+
+
+def cos_connected_sum_batch(tables: Tables, n_max: int, order, offset, site, tau, precision: str, out,
+                            abs_mass=None, stream=None):
+    _check(lib().cos_connected_sum_batch(tables.handle, int(order.numel()), int(n_max), _ptr(order), _ptr(offset),
+                                         _ptr(site), _ptr(tau), PRECISIONS[precision], _ptr(out), _ptr(abs_mass),
+                                         _stream(stream)), "cos_connected_sum_batch")
+
+
+def cos_sync_status(stream=None):
+    _check(lib().cos_sync_status(_stream(stream)), "cos_sync_status")
+
+
+def cos_structure(n: int) -> cos_structure_info:
+    inf = cos_structure_info()
+    _check(lib().cos_structure(int(n), ctypes.byref(inf)), "cos_structure")
+    return inf
+
+
+# ------------------------------------------------------------------ torch-facing helpers
+
+def configs_to_device(cfgs, device="cuda"):
+    """Device copies (order int32, offset int64, site int32, tau float64) of inputs.Configs."""
+    import torch
+    return (torch.as_tensor(cfgs.order, dtype=torch.int32, device=device),
+            torch.as_tensor(cfgs.offset, dtype=torch.int64, device=device),
+            torch.as_tensor(cfgs.site, dtype=torch.int32, device=device),
+            torch.as_tensor(cfgs.tau, dtype=torch.float64, device=device))
+
+
+def matrix_offsets(order: np.ndarray, n_mat: int) -> np.ndarray:
+    """Offsets of packed [n_mat][n_c][n_c] blocks for the given orders."""
+    sizes = n_mat * np.asarray(order, dtype=np.int64) ** 2
+    off = np.zeros(len(sizes), dtype=np.int64)
+    if len(sizes):
+        off[1:] = np.cumsum(sizes[:-1])
+    return off
+
+
+def cos_peak_probe(kind: int, blocks: int, threads: int, iters: int, sink, stream=None):
+    _check(lib().cos_peak_probe(int(kind), int(blocks), int(threads), int(iters), _ptr(sink), _stream(stream)),
+           "cos_peak_probe")
+
+
+def measure_peak(kind: int = 0, iters: int = 4096, reps: int = 3) -> float:
+    """Measured FMA throughput (FLOP/s) of the FP64 (kind 0) or FP32 (kind 1) pipe."""
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    blocks, threads = props.multi_processor_count * 8, 256
+    chains = 8 if kind == 0 else 16
+    sink = torch.zeros(blocks, dtype=torch.float64 if kind == 0 else torch.float32, device="cuda")
+    cos_peak_probe(kind, blocks, threads, 64, sink)              # warm-up
+    best = 0.0
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        cos_peak_probe(kind, blocks, threads, iters, sink)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+        best = max(best, 2.0 * blocks * threads * chains * iters / sec)
+    return best

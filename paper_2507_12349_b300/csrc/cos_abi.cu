@@ -1,0 +1,309 @@
+// C ABI of libcos: argument checks, per-(device, stream) workspaces, device status words,
+// launch tuning and the public entry points that chain the kernels.
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+
+#include "cos_internal.h"
+
+namespace cosdp {
+
+namespace {
+thread_local std::string t_err;
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace *> g_ws;
+}  // namespace
+
+void set_error(const std::string &msg) { t_err = msg; }
+
+cos_status cuda_fail(cudaError_t e, const char *what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    cudaGetLastError();  // clear a sticky launch error of this thread
+    return e == cudaErrorMemoryAllocation ? COS_ERR_NOMEM : COS_ERR_CUDA;
+}
+
+cos_status ensure(void **ptr, size_t *cap, size_t need, size_t elem, const char *what) {
+    if (*ptr && *cap >= need) return COS_OK;
+    // Growth: the old buffer may still be in use by work queued on this stream.
+    cudaDeviceSynchronize();
+    cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    const size_t grow = need + need / 4;
+    cudaError_t e = cudaMalloc(ptr, grow * elem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaMalloc(ptr, need * elem);
+        if (e != cudaSuccess) {
+            *ptr = nullptr;
+            return cuda_fail(e, what);
+        }
+        *cap = need;
+        return COS_OK;
+    }
+    *cap = grow;
+    return COS_OK;
+}
+
+Workspace *get_workspace(cudaStream_t stream, std::string *err) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        *err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    auto key = std::make_pair(dev, stream);
+    auto it = g_ws.find(key);
+    if (it != g_ws.end()) return it->second;
+    Workspace *ws = new Workspace();
+    ws->device = dev;
+    ws->stream = stream;
+    e = cudaMalloc(&ws->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ws->plan_counts, 80 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ws->queue, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ws->status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        *err = std::string("workspace: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        delete ws;
+        return nullptr;
+    }
+    g_ws[key] = ws;
+    return ws;
+}
+
+// Launch shape per order: warps per CTA and CTAs per SM of the persistent grid.  Defaults
+// keep four or more warps per SM sub-partition; large orders use one CTA per SM so the layer
+// scratch (two layers of up to 1.26 M slots x 32 lanes at n = 12) stays within HBM.
+// COS_TUNE="n:warps:ctas,..." overrides (written by the autotuner).
+Tuning get_tuning(int n, int precision, int nf_lanes) {
+    (void)precision;
+    (void)nf_lanes;
+    Tuning t;
+    if (n >= 11) {
+        t.warps = 16;
+        t.ctas_per_sm = 1;
+    } else if (n >= 9) {
+        t.warps = 8;
+        t.ctas_per_sm = 2;
+    } else {
+        t.warps = 8;
+        t.ctas_per_sm = 2;
+    }
+    if (const char *s = getenv("COS_TUNE")) {
+        const char *p = s;
+        while (*p) {
+            int tn = 0, tw = 0, tc = 0, used = 0;
+            if (sscanf(p, "%d:%d:%d%n", &tn, &tw, &tc, &used) == 3) {
+                if (tn == n && tw >= 1 && tw <= 16 && tc >= 1 && tc <= 8) {
+                    t.warps = tw;
+                    t.ctas_per_sm = tc;
+                }
+                p += used;
+                while (*p == ',' || *p == ' ') ++p;
+            } else {
+                break;
+            }
+        }
+    }
+    return t;
+}
+
+static cos_status check_common(int n_cfg, int n_max, cos_precision prec, const char *fn) {
+    if (n_cfg < 0) {
+        set_error(std::string(fn) + ": n_cfg < 0");
+        return COS_ERR_ARG;
+    }
+    if (n_max < 1 || n_max > COS_NMAX) {
+        set_error(std::string(fn) + ": n_max outside [1, 12]");
+        return COS_ERR_ORDER;
+    }
+    if (prec != COS_FP64 && prec != COS_MIXED) {
+        set_error(std::string(fn) + ": unknown precision");
+        return COS_ERR_ARG;
+    }
+    return COS_OK;
+}
+
+static cos_status run_dp(Workspace *ws, DpLaunch L, double *d_abs_mass, cudaStream_t stream) {
+    const int cpb = kLanes / L.n_mat;
+    cos_status st = launch_plan_batches(ws, L.n_cfg, L.n_max, L.order, cpb, stream);
+    if (st != COS_OK) return st;
+    st = launch_dp(ws, L, stream);
+    if (st != COS_OK) return st;
+    if (d_abs_mass) {
+        L.out = d_abs_mass;
+        L.absmode = true;
+        st = launch_dp(ws, L, stream);
+    }
+    return st;
+}
+
+}  // namespace cosdp
+
+using namespace cosdp;
+
+extern "C" const char *cos_status_string(cos_status s) {
+    switch (s) {
+        case COS_OK: return "ok";
+        case COS_ERR_ARG: return "invalid argument";
+        case COS_ERR_ORDER: return "order out of range";
+        case COS_ERR_CUDA: return "CUDA error";
+        case COS_ERR_TIMEOUT: return "device wait timed out";
+        case COS_ERR_NONFINITE: return "non-finite result";
+        case COS_ERR_UNIMPLEMENTED: return "not implemented";
+        case COS_ERR_NOMEM: return "device memory exhausted";
+    }
+    return "unknown status";
+}
+
+extern "C" const char *cos_last_error(void) { return t_err.c_str(); }
+
+extern "C" cos_status cos_sync_status(cos_stream_t stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cos_sync_status");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    Workspace *ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        auto it = g_ws.find(std::make_pair(dev, s));
+        if (it != g_ws.end()) ws = it->second;
+    }
+    if (!ws) return COS_OK;
+    int word = 0;
+    e = cudaMemcpy(&word, ws->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ws->status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "cos_sync_status read");
+    if (word & kStatusOrder) {
+        set_error("device: order out of range");
+        return COS_ERR_ORDER;
+    }
+    if (word & kStatusSite) {
+        set_error("device: site out of range");
+        return COS_ERR_ARG;
+    }
+    if (word & kStatusTimeout) {
+        set_error("device: bounded wait gave up");
+        return COS_ERR_TIMEOUT;
+    }
+    if (word & kStatusNonFinite) {
+        set_error("device: non-finite result");
+        return COS_ERR_NONFINITE;
+    }
+    return COS_OK;
+}
+
+extern "C" cos_status cos_connected_sum_matrices(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                                                 int n_mat, int loop_weight, const double *h_sigma,
+                                                 const double *d_M, cos_precision precision, double *d_out,
+                                                 double *d_abs_mass, cos_stream_t stream) {
+    cos_status st = check_common(n_cfg, n_max, precision, "cos_connected_sum_matrices");
+    if (st != COS_OK) return st;
+    if (n_mat < 1 || n_mat > COS_MAX_FLAVORS || loop_weight < 1) {
+        set_error("cos_connected_sum_matrices: n_mat outside [1, 8] or loop_weight < 1");
+        return COS_ERR_ARG;
+    }
+    if (n_cfg == 0) return COS_OK;
+    if (!d_order || !d_moff || !d_M || !d_out) {
+        set_error("cos_connected_sum_matrices: null device pointer");
+        return COS_ERR_ARG;
+    }
+    std::string err;
+    Workspace *ws = get_workspace((cudaStream_t)stream, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    DpLaunch L;
+    L.n_cfg = n_cfg;
+    L.n_max = n_max;
+    L.order = d_order;
+    L.M = d_M;
+    L.moff = d_moff;
+    L.n_mat = n_mat;
+    L.loop_weight = loop_weight;
+    for (int l = 0; l < n_mat; ++l) {
+        L.sigma[l] = h_sigma ? h_sigma[l] : 0.0;
+        if (L.sigma[l] != 0.0) L.shifts = true;
+    }
+    L.precision = precision;
+    L.out = d_out;
+    return run_dp(ws, L, d_abs_mass, (cudaStream_t)stream);
+}
+
+extern "C" cos_status cos_gather(const cos_tables *t, int n_cfg, const int32_t *d_order, const int64_t *d_offset,
+                                 const int32_t *d_site, const double *d_tau, const int64_t *d_moff, double *d_M,
+                                 cos_stream_t stream) {
+    if (!t) {
+        set_error("cos_gather: null tables");
+        return COS_ERR_ARG;
+    }
+    if (n_cfg < 0) {
+        set_error("cos_gather: n_cfg < 0");
+        return COS_ERR_ARG;
+    }
+    if (n_cfg == 0) return COS_OK;
+    if (!d_order || !d_offset || !d_site || !d_tau || !d_moff || !d_M) {
+        set_error("cos_gather: null device pointer");
+        return COS_ERR_ARG;
+    }
+    std::string err;
+    Workspace *ws = get_workspace((cudaStream_t)stream, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    return launch_gather(t, n_cfg, d_order, d_offset, d_site, d_tau, d_moff, 0, d_M, ws->status,
+                         (cudaStream_t)stream);
+}
+
+extern "C" cos_status cos_connected_sum_batch(const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order,
+                                              const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
+                                              cos_precision precision, double *d_out, double *d_abs_mass,
+                                              cos_stream_t stream) {
+    cos_status st = check_common(n_cfg, n_max, precision, "cos_connected_sum_batch");
+    if (st != COS_OK) return st;
+    if (!t) {
+        set_error("cos_connected_sum_batch: null tables");
+        return COS_ERR_ARG;
+    }
+    if (n_cfg == 0) return COS_OK;
+    if (!d_order || !d_offset || !d_site || !d_tau || !d_out) {
+        set_error("cos_connected_sum_batch: null device pointer");
+        return COS_ERR_ARG;
+    }
+    std::string err;
+    Workspace *ws = get_workspace((cudaStream_t)stream, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    const int64_t stride = (int64_t)t->n_mat * n_max * n_max;
+    st = ensure((void **)&ws->M, &ws->M_cap, (size_t)n_cfg * stride, sizeof(double), "matrix workspace");
+    if (st != COS_OK) return st;
+    st = launch_gather(t, n_cfg, d_order, d_offset, d_site, d_tau, nullptr, stride, ws->M, ws->status,
+                       (cudaStream_t)stream);
+    if (st != COS_OK) return st;
+    DpLaunch L;
+    L.n_cfg = n_cfg;
+    L.n_max = n_max;
+    L.order = d_order;
+    L.M = ws->M;
+    L.moff = nullptr;
+    L.mstride = stride;
+    L.n_mat = t->n_mat;
+    L.loop_weight = t->symmetric ? t->model.n_flavors : 1;
+    for (int l = 0; l < t->n_mat; ++l) {
+        L.sigma[l] = t->sigma[l];
+        if (L.sigma[l] != 0.0) L.shifts = true;
+    }
+    L.precision = precision;
+    L.out = d_out;
+    return run_dp(ws, L, d_abs_mass, (cudaStream_t)stream);
+}

@@ -1,0 +1,158 @@
+// Internal declarations of libcos (CUDA side).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "cos.h"
+
+namespace cosdp {
+
+constexpr int kLanes = 32;          // lanes of a warp = (configuration, flavor) pairs of a batch
+constexpr int kMaxLayers = 2 * COS_NMAX + 1;
+
+// Device status bits (OR-ed into the per-stream status word).
+enum : int {
+    kStatusOrder = 1,
+    kStatusSite = 2,
+    kStatusNonFinite = 4,
+    kStatusTimeout = 8,
+};
+
+// One interaction mask mu in {0,1,2}^n with mu_0 >= 1, as stored on the device.
+//   ab   : visited set A = {i : mu_i >= 1} in bits 0..15, full set B = {i : mu_i = 2} in bits 16..31
+//   code : sum_i mu_i 3^i
+//   off  : offset (in state slots) of the mask's block inside its layer; the block holds
+//          |H(mu)| rows (heads) of |A| slots (endpoints), slot (h, v) at off + idxH(h)*|A| + idxA(v)
+struct MaskRec {
+    uint32_t ab;
+    uint32_t code;
+    uint32_t off;
+    uint32_t cost;
+};
+
+// Structure of the merged DP for one order n, device copy.
+struct OrderTab {
+    const MaskRec *masks;     // grouped by layer, cost-sorted (descending) inside a layer
+    const uint32_t *rank3;    // code -> block offset inside its layer
+    uint32_t layer_first[kMaxLayers + 1];
+    uint32_t layer_count[kMaxLayers + 1];
+    uint32_t layer_slots[kMaxLayers + 1];
+    uint32_t max_slots;
+    uint32_t n;
+};
+
+// Endpoints v that a row (mu, h) can hold (reachable slots; the others are never written
+// and never read).  A = visited set, ones = {i : mu_i = 1}.
+//   h = 0, mu_0 = 1 : the first loop has visited only point 0 of vertex 0, so v = 0 only at the
+//                     start mu = e_0; otherwise v ranges over A \ {0}.
+//   h = 0, mu_0 = 2 : every visited vertex.
+//   h != 0          : later loops never return to vertex 0 (it was full before they opened);
+//                     v = h only if h was the smallest half-visited vertex when the loop opened,
+//                     i.e. no vertex below h is half-visited now.
+__host__ __device__ inline uint32_t row_vmask(uint32_t A, uint32_t ones, int h) {
+    if (h == 0) {
+        if (ones & 1u) return (A == 1u) ? 1u : (A & ~1u);
+        return A;
+    }
+    uint32_t v = A & ~1u;
+    if (ones & ((1u << h) - 1u)) v &= ~(1u << h);
+    return v;
+}
+
+// Heads of the open loop: vertex 0 while the first loop is open with mu_0 = 1, else the full set.
+__host__ __device__ inline uint32_t head_set(uint32_t B, uint32_t ones) {
+    return (ones & 1u) ? 1u : B;
+}
+
+// Host-side structure (built once per order).
+struct HostOrder {
+    int n = 0;
+    std::vector<MaskRec> masks;
+    std::vector<uint32_t> rank3;
+    uint32_t layer_first[kMaxLayers + 1] = {};
+    uint32_t layer_count[kMaxLayers + 1] = {};
+    uint32_t layer_slots[kMaxLayers + 1] = {};
+    uint32_t max_slots = 0;
+    cos_structure_info info{};
+};
+
+const HostOrder &host_order(int n);   // thread-safe, cached
+
+// Per-device copy of the tables of orders 1..COS_NMAX; returns a device array of 13 OrderTab.
+const OrderTab *device_orders(int device, std::string *err);
+
+// Thread-local error message.
+void set_error(const std::string &msg);
+cos_status cuda_fail(cudaError_t e, const char *what);
+
+// Per (device, stream) workspace.
+struct Workspace {
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    int *status = nullptr;           // device status word
+    // planner
+    int *plan_counts = nullptr;      // [16] counts per order, [16] cursors, [16] bucket starts, [16] batch starts, [4] misc
+    int *batch_list = nullptr;       // sorted configuration indices
+    int4 *batches = nullptr;         // {n, start, count, 0}
+    size_t batches_cap = 0;          // capacity in batches
+    size_t batch_cap = 0;            // capacity in configurations
+    int *queue = nullptr;            // persistent-kernel work counter
+    // gathered matrices (batch path)
+    double *M = nullptr;
+    size_t M_cap = 0;                // doubles
+    int64_t *moff = nullptr;
+    size_t moff_cap = 0;
+    // DP layer scratch
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+};
+
+Workspace *get_workspace(cudaStream_t stream, std::string *err);
+cos_status ensure(void **ptr, size_t *cap, size_t need, size_t elem, const char *what);
+
+// Launch tuning for one order.
+struct Tuning {
+    int warps = 8;          // warps per CTA
+    int ctas_per_sm = 2;    // resident CTAs per SM targeted by the persistent grid
+};
+Tuning get_tuning(int n, int precision, int nf_lanes);
+
+struct DpLaunch {
+    int n_cfg = 0;
+    int n_max = 0;
+    const int32_t *order = nullptr;
+    const double *M = nullptr;
+    const int64_t *moff = nullptr;
+    int64_t mstride = 0;            // used when moff == nullptr
+    int n_mat = 1;
+    int loop_weight = 1;
+    double sigma[COS_MAX_FLAVORS] = {};
+    bool shifts = false;
+    int precision = COS_FP64;
+    double *out = nullptr;
+    bool absmode = false;
+};
+
+cos_status launch_plan_batches(Workspace *ws, int n_cfg, int n_max, const int32_t *order, int cpb,
+                               cudaStream_t stream);
+cos_status launch_dp(Workspace *ws, const DpLaunch &a, cudaStream_t stream);
+cos_status launch_gather(const cos_tables *t, int n_cfg, const int32_t *order, const int64_t *offset,
+                         const int32_t *site, const double *tau, const int64_t *moff, int64_t mstride,
+                         double *M, int *status, cudaStream_t stream);
+
+}  // namespace cosdp
+
+struct cos_tables {
+    int device;
+    cos_model model;          // mu/alpha point into the vectors below
+    std::vector<double> mu, alpha;
+    int n_mat;
+    int symmetric;
+    double sigma[COS_MAX_FLAVORS];
+    double *d_G;
+    double *d_dG;
+};

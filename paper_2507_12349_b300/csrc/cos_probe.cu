@@ -1,0 +1,38 @@
+// Throughput probes for the roofline denominators: independent FMA chains per thread,
+// enough warps to fill every SM sub-partition.  FLOPs = 2 * blocks * threads * chains * iters.
+#include "cos_internal.h"
+
+namespace cosdp {
+
+template <typename T, int CHAINS>
+__global__ void fma_probe_kernel(int iters, T *sink) {
+    T a[CHAINS];
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) a[c] = (T)(threadIdx.x + c) * (T)1e-3;
+    const T b = (T)0.999999, d = (T)1e-7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < CHAINS; ++c) a[c] = a[c] * b + d;   // contracted to one FMA
+    }
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) s += a[c];
+    if (s == (T)-1.2345) sink[blockIdx.x] = s;   // never true; keeps the chains live
+}
+
+}  // namespace cosdp
+
+extern "C" cos_status cos_peak_probe(int kind, int blocks, int threads, int iters, void *d_sink, cos_stream_t stream) {
+    using namespace cosdp;
+    if (blocks < 1 || threads < 32 || threads > 1024 || iters < 1 || !d_sink || (kind != 0 && kind != 1)) {
+        set_error("cos_peak_probe: bad argument");
+        return COS_ERR_ARG;
+    }
+    if (kind == 0)
+        fma_probe_kernel<double, 8><<<blocks, threads, 0, (cudaStream_t)stream>>>(iters, (double *)d_sink);
+    else
+        fma_probe_kernel<float, 16><<<blocks, threads, 0, (cudaStream_t)stream>>>(iters, (float *)d_sink);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "cos_peak_probe");
+    return COS_OK;
+}

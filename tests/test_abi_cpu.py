@@ -1,0 +1,95 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every
+declared symbol, rejects bad arguments without a device, and its host-built
+DP structure has the counts of the merged recurrence."""
+import itertools
+import os
+import re
+
+import pytest
+
+from paper_2507_12349_b300 import binding as B
+from paper_2507_12349_b300 import build as BLD
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "cos.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(cos_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    lib = B.lib()
+    decl = declared_functions()
+    assert decl, "no declarations parsed"
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(decl) == sorted(B.EXPORTS)
+
+
+def test_build_targets_sm103a():
+    assert "arch=compute_103a,code=sm_103a" in " ".join(BLD.ARCH)
+
+
+def test_argument_errors_are_synchronous():
+    lib = B.lib()
+    import ctypes
+    # order out of range is rejected before any device work
+    rc = lib.cos_connected_sum_matrices(1, 13, None, None, 1, 1, None, None, 0, None, None, None)
+    assert rc == -2
+    rc = lib.cos_connected_sum_matrices(-1, 4, None, None, 1, 1, None, None, 0, None, None, None)
+    assert rc == -1
+    rc = lib.cos_connected_sum_matrices(1, 4, None, None, 9, 1, None, None, 0, None, None, None)
+    assert rc == -1
+    rc = lib.cos_connected_sum_matrices(1, 4, None, None, 1, 1, None, None, 7, None, None, None)
+    assert rc == -1
+    # empty batch is a no-op
+    assert lib.cos_connected_sum_matrices(0, 4, None, None, 1, 1, None, None, 0, None, None, None) == 0
+    assert lib.cos_status_string(-2) == b"order out of range"
+    inf = B.cos_structure_info()
+    assert lib.cos_structure(0, ctypes.byref(inf)) == -2
+
+
+def count_merged(n):
+    """Independent count of masks, slots, reachable states and multiply-adds."""
+    masks = slots = states = ext = close = shift = 0
+    for mu in itertools.product(range(3), repeat=n):
+        if mu[0] == 0:
+            continue
+        masks += 1
+        A = [i for i in range(n) if mu[i] >= 1]
+        ones = [i for i in range(n) if mu[i] == 1]
+        B_ = [i for i in range(n) if mu[i] == 2]
+        H = [0] if mu[0] == 1 else B_
+        J = [j for j in range(n) if mu[j] <= 1]
+        Z = [j for j in range(n) if mu[j] == 0]
+        need = bool(ones) or len(B_) == n
+        slots += len(H) * len(A)
+        for h in H:
+            if h == 0 and mu[0] == 1:
+                V = [0] if len(A) == 1 else [v for v in A if v]
+            elif h == 0:
+                V = A
+            else:
+                V = [v for v in A if v and not (v == h and any(o < h for o in ones))]
+            states += len(V)
+            ext += len(V) * len(J)
+            close += len(V) if need else 0
+            shift += len(Z)
+    return masks, slots, states, ext, close, shift
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 7, 8])
+def test_structure_counts(n):
+    inf = B.cos_structure(n)
+    assert (inf.masks, inf.slots, inf.states, inf.fma_ext, inf.fma_close, inf.mul_shift) == count_merged(n)
+    assert inf.masks == 2 * 3 ** (n - 1)
+
+
+def test_structure_counts_large_orders():
+    # slot counts of the merged state space: 252 at n = 4, 708588 at n = 10, 8581788 at n = 12
+    assert B.cos_structure(4).slots == 252
+    assert B.cos_structure(10).slots == 708588
+    inf = B.cos_structure(12)
+    assert inf.slots == 8581788 and inf.max_layer_slots == 1262547
