@@ -1,0 +1,409 @@
+"""Benchmark of the connected-sum hot path on B300.
+
+Workload (the configuration the metric is quoted on): SU(4) square-lattice
+Hubbard model with flavor-dependent chemical potentials mu = (-0.3, -0.1, 0.1,
+0.3), L = 16, t = 1, beta = 4, U = 1.5, order n = 8, 10^5 configurations with
+sites uniform on the torus and tau uniform in [0, beta) (seed 1), FP64,
+per-flavor tables of 1024 tau points.  One step = propagator gather + the
+whole DP (seed, clow extension, loop closing, sink) for all 10^5
+configurations, inputs resident in HBM.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       [--no-extras]
+Prints ONE JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2507_12349_b300 import inputs as I  # noqa: E402
+
+WORKLOAD = "su4_mu_broken_n8"
+METRIC = "connected-sum configs/s at order n (FP64 vs mixed), roofline fraction, grad overhead"
+UNIT = "configs/s"
+NOMINAL_FP64_TFLOPS = 1.25
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--no-extras", action="store_true", help="only the headline workload (for launch lists)")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
+    p.add_argument("--n-cfg", type=int, default=0, help="smaller configuration count (profiling runs only)")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ CPU oracle (reported baseline)
+
+def cpu_oracle_rate(w, budget_s: float, n_limit: int | None = None):
+    """Oracle (plain C DP, OpenMP over configurations, plus the numpy gather) on a
+    bounded sample of the workload.  Returns (configs/s, threads, sample size)."""
+    import oracle as O
+    from oracle import propagators as P
+    model = w.model
+    tabs = P.model_tables(model)
+    wt, sig = 1, list(model.sigma)
+    if model.symmetric:
+        tabs, wt, sig = tabs[:1], model.n_flavors, sig[:1]
+    sig = sig if any(sig) else None
+    # calibrate on a few configurations
+    probe = I.workload_configs(w, 8)
+    t0 = time.perf_counter()
+    Ms = np.stack(P.gather(tabs, probe, model.L, model.beta))
+    _, _, threads = O.dp_batch(Ms, sig, wt, nthreads=0)
+    t1 = time.perf_counter() - t0
+    per_cfg = t1 / 8.0
+    n = max(8, int(budget_s / max(per_cfg, 1e-6)))
+    if n_limit:
+        n = min(n, n_limit)
+    n = min(n, w.n_cfg)
+    cfgs = I.workload_configs(w, n)
+    t0 = time.perf_counter()
+    Ms = np.stack(P.gather(tabs, cfgs, model.L, model.beta))
+    _, _, threads = O.dp_batch(Ms, sig, wt, nthreads=0)
+    dt = time.perf_counter() - t0
+    return n / dt, threads, n
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = I.WORKLOADS[WORKLOAD]
+    budget = max(1.0, 90.0 / max(1, args.steps + 1))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(w, min(budget, 2.0))
+    rates, sample, threads = [], 0, 1
+    t_start = time.perf_counter()
+    for _ in range(args.steps):
+        r, threads, sample = cpu_oracle_rate(w, budget)
+        rates.append(r)
+    wall = time.perf_counter() - t_start
+    value = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": 8, "n_flavors": 4, "n_cfg_sample": sample, "L": 16, "beta": 4.0,
+                   "n_tau": 1024, "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{sample} configurations of the n=8 SU(4) workload per step "
+                                   f"(numpy gather + C DP in double, OpenMP)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU helpers
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms (read-only)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def algorithmic_flops(B, order: np.ndarray, n_mat: int, shifts: bool) -> float:
+    """FP64-equivalent flops the DP must do: 2 per multiply-add of the extension dot
+    products and loop-closing sums over reachable states, 1 per shift product."""
+    total = 0.0
+    for n in np.unique(order):
+        s = B.cos_structure(int(n))
+        cnt = int((order == n).sum())
+        per = 2.0 * (s.fma_ext + s.fma_close) + (s.mul_shift if shifts else 0)
+        total += cnt * n_mat * per
+    return total
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def time_steps(torch, fn, steps, flush):
+    """Per-step CUDA-event times (flush between steps, untimed)."""
+    stream = torch.cuda.current_stream()
+    times = []
+    for _ in range(steps):
+        flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    return times
+
+
+def native_arm(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2507_12349_b300 import binding as B
+    B.lib()
+
+    w = I.WORKLOADS[WORKLOAD]
+    n_cfg = args.n_cfg if args.n_cfg > 0 else w.n_cfg
+    # weak scaling: every rank takes its own 10^5 configurations of the seeded stream
+    cfgs = I.workload_configs(w, n_cfg, first_cfg=rank * n_cfg)
+    tabs = B.tables_for(w.model)
+    d_order, d_offset, d_site, d_tau = B.configs_to_device(cfgs)
+    n_mat = tabs.info().n_mat
+    stride = n_mat * 64
+    d_moff = torch.arange(n_cfg, dtype=torch.int64, device="cuda") * stride
+    d_M = torch.empty(n_cfg * stride, dtype=torch.float64, device="cuda")
+    out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
+    flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2 (126 MB)
+    stream = torch.cuda.current_stream()
+
+    # a step, with CUDA events between the gather and the DP (same stream)
+    dp_times = []
+
+    def step():
+        B.cos_gather(tabs, d_order, d_offset, d_site, d_tau, d_moff, d_M)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        B.cos_connected_sum_matrices(8, d_order, d_moff, n_mat, 1, None, d_M, "fp64", out)
+        ev1.record(stream)
+        dp_times.append((ev0, ev1))
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    B.cos_sync_status()
+    dp_times.clear()
+
+    # FP64 pipe peak (roofline denominator), measured on this GPU just before the run
+    fp64_peak = B.measure_peak(0)
+
+    sampler = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    t_wall0 = time.perf_counter()
+    times = time_steps(torch, step, args.steps, lambda: flush_l2(flush_buf))
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    B.cos_sync_status()
+    total = sum(times)
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    value = world * n_cfg * args.steps / total
+    dp_avg = statistics.mean(a.elapsed_time(b) * 1e-3 for a, b in dp_times)
+    flops_launch = algorithmic_flops(B, cfgs.order, n_mat, False)
+    achieved = flops_launch / dp_avg
+
+    # end to end through the public call with host buffers (pinned), copies inside the region
+    h_order = torch.tensor(cfgs.order).pin_memory()
+    h_offset = torch.tensor(cfgs.offset).pin_memory()
+    h_site = torch.tensor(cfgs.site).pin_memory()
+    h_tau = torch.tensor(cfgs.tau).pin_memory()
+    h_out = torch.empty(n_cfg, dtype=torch.float64).pin_memory()
+    e_order, e_offset, e_site, e_tau = (torch.empty_like(x, device="cuda") for x in (h_order, h_offset, h_site, h_tau))
+    e_out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
+
+    def e2e_step():
+        for dst, src in ((e_order, h_order), (e_offset, h_offset), (e_site, h_site), (e_tau, h_tau)):
+            dst.copy_(src, non_blocking=True)
+        B.cos_connected_sum_batch(tabs, 8, e_order, e_offset, e_site, e_tau, "fp64", e_out)
+        h_out.copy_(e_out, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_times = time_steps(torch, e2e_step, max(2, min(args.steps, 5)), lambda: flush_l2(flush_buf))
+    B.cos_sync_status()
+    h2d = sum(x.numel() * x.element_size() for x in (h_order, h_offset, h_site, h_tau))
+    d2h = h_out.numel() * h_out.element_size()
+    e2e_value = world * n_cfg / statistics.mean(e2e_times)
+    # parity spot check of the timed output against the CPU oracle (few configurations)
+    parity = None
+    if rank == 0:
+        import oracle as O
+        from oracle import propagators as P
+        otabs = P.model_tables(w.model)
+        idx = [0, n_cfg // 2, n_cfg - 1]
+        got = out.cpu().numpy()
+        errs = []
+        for c, M in zip(idx, P.gather(otabs, cfgs, w.model.L, w.model.beta, idx)):
+            ref = O.dp(M, None, prec="ld")
+            errs.append(abs(got[c] - ref) / abs(ref))
+        parity = {"configs_checked": len(idx), "max_rel_err_vs_oracle": max(errs)}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = measure_forms(torch, B, flush_buf)
+
+    launches_per_step = 1 + 4 + 1   # gather, 4 planner kernels, DP
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": 8, "n_flavors": 4, "n_cfg_per_gpu": n_cfg, "L": 16, "beta": 4.0,
+                   "U": 1.5, "mu": list(w.model.mu), "n_tau": 1024, "precision": "fp64",
+                   "full_size": n_cfg == w.n_cfg,
+                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"configs sharded x{world}"},
+        "roofline": {"bound": "alu", "pipe": "fp64 fma", "achieved": achieved / 1e12,
+                     "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                     "peak_source": "measured: FP64 FMA probe (cos_peak_probe kind 0) on this GPU",
+                     "peak_nominal": NOMINAL_FP64_TFLOPS, "frac_of_nominal": achieved / 1e12 / NOMINAL_FP64_TFLOPS,
+                     "kernel": "dp_forward_kernel<double>", "flops_per_launch": flops_launch,
+                     "launch_ms": dp_avg * 1e3, "traffic": None},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "wall_s_timed_region": t_wall,
+    }
+    if parity:
+        line["parity"] = parity
+    if extras:
+        line["forms"] = extras
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    tabs.close()
+
+
+def cpu_baseline(w, budget):
+    rate, threads, n = cpu_oracle_rate(w, budget)
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} configurations of the n=8 SU(4) workload (numpy gather + C DP in double, OpenMP)"}
+
+
+def measure_forms(torch, B, flush_buf):
+    """The other forms of the path on the same GPU: mixed precision, the uneven-order
+    persistent batch, and the plain FP64 form with one configuration per launch."""
+    res = {}
+
+    def run(name, n_cfg, prec, steps=2):
+        w = I.WORKLOADS[name]
+        cfgs = I.workload_configs(w, n_cfg)
+        tabs = B.tables_for(w.model)
+        d = B.configs_to_device(cfgs)
+        out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
+        nmax = int(cfgs.order.max())
+        B.cos_connected_sum_batch(tabs, nmax, *d, prec, out)
+        B.cos_sync_status()
+        ts = time_steps(torch, lambda: B.cos_connected_sum_batch(tabs, nmax, *d, prec, out), steps,
+                        lambda: flush_l2(flush_buf))
+        B.cos_sync_status()
+        n_mat = tabs.info().n_mat
+        shifts = any(w.model.sigma)
+        fl = algorithmic_flops(B, cfgs.order, n_mat, shifts)
+        t = statistics.mean(ts)
+        tabs.close()
+        return {"configs": n_cfg, "configs_per_s": n_cfg / t, "tflops": fl / t / 1e12, "ms": t * 1e3}
+
+    res["su4_n8_mixed"] = run("su4_mu_broken_n8", 100_000, "mixed")
+    res["su3_shift_n10_mixed"] = run("su3_shift_mixed_n10", 20_000, "mixed")
+    res["su3_shift_n10_fp64"] = run("su3_shift_mixed_n10", 20_000, "fp64")
+    res["su6_uneven_n4_12_fp64"] = run("su6_sym_uneven_n4_12", 20_000, "fp64", steps=1)
+    # plain FP64 per-configuration form: one configuration per call
+    w = I.WORKLOADS[WORKLOAD]
+    cfgs = I.workload_configs(w, 200)
+    tabs = B.tables_for(w.model)
+    d = B.configs_to_device(cfgs)
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    per = []
+    for c in range(200):
+        o = int(cfgs.offset[c])
+        per.append((d[0][c:c + 1], torch.zeros(1, dtype=torch.int64, device="cuda"), d[2][o:o + 8], d[3][o:o + 8]))
+    B.cos_connected_sum_batch(tabs, 8, *per[0], "fp64", out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for args in per:
+        B.cos_connected_sum_batch(tabs, 8, *args, "fp64", out)
+    e1.record()
+    e1.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3
+    res["su4_n8_fp64_one_config_per_launch"] = {"configs": 200, "configs_per_s": 200 / t}
+    B.cos_sync_status()
+    tabs.close()
+    return res
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        native_arm(args)
+
+
+if __name__ == "__main__":
+    main()
