@@ -143,6 +143,27 @@ cos_status cos_connected_sum_matrices(int n_cfg, int n_max, const int32_t *d_ord
                                       cos_precision precision, double *d_out,
                                       double *d_abs_mass, cos_stream_t stream);
 
+/* Same computation as cos_connected_sum_matrices for callers that cannot allocate device
+ * memory (no counterpart in the paper: it exists for integrations such as a plug-in that
+ * receives a stream and buffers but no allocator, or a process whose device memory is owned
+ * by a pool).  It calls no cudaMalloc / cudaFree and no allocating library routine: all
+ * scratch (planner tables, work queue, DP structure, layer ring) lives in one fixed device
+ * array of 128 MiB that every GPU loading the library holds until the process exits.
+ *   - Limits: n_max <= 10, and the batch must fit the array (roughly 20 B per configuration
+ *     plus one layer ring of 2-3 x max-layer-slots x 32 x 8 B); larger requests return
+ *     COS_ERR_ORDER / COS_ERR_ARG with a message, without launching anything.
+ *   - The first call on a device sets the array up (device address, DP structure copy,
+ *     synchronizing `stream` once); make that first call before any stream capture.
+ *   - Every call reuses the same array and leaves its contents behind; calls whose work
+ *     overlaps on the GPU (other streams, other host threads) race with each other.
+ *   - Outputs are set to NaN first; a configuration whose order lies outside [1, n_max]
+ *     keeps NaN.  There is no device status word on this path. */
+cos_status cos_connected_sum_matrices_noalloc(int n_cfg, int n_max, const int32_t *d_order,
+                                              const int64_t *d_moff, int n_mat, int loop_weight,
+                                              const double *h_sigma, const double *d_M,
+                                              cos_precision precision, double *d_out,
+                                              double *d_abs_mass, cos_stream_t stream);
+
 /* Gather + DP from vertex coordinates (arguments as in cos_gather and
  * cos_connected_sum_matrices; sigma and the loop weight come from the tables). */
 cos_status cos_connected_sum_batch(const cos_tables *tables, int n_cfg, int n_max,

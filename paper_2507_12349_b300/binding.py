@@ -27,7 +27,7 @@ STATUS = {0: "COS_OK", -1: "COS_ERR_ARG", -2: "COS_ERR_ORDER", -3: "COS_ERR_CUDA
 # Every symbol include/cos.h declares (checked by the CPU tests).
 EXPORTS = [
     "cos_build_propagators", "cos_free_tables", "cos_get_tables_info", "cos_copy_table", "cos_gather",
-    "cos_connected_sum_matrices", "cos_connected_sum_batch", "cos_sync_status", "cos_status_string",
+    "cos_connected_sum_matrices", "cos_connected_sum_matrices_noalloc", "cos_connected_sum_batch", "cos_sync_status", "cos_status_string",
     "cos_last_error", "cos_structure", "cos_peak_probe",
 ]
 
@@ -75,6 +75,7 @@ def lib(build: bool = True):
         L.cos_copy_table.argtypes = [vp, i32, vp, vp]
         L.cos_gather.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
         L.cos_connected_sum_matrices.argtypes = [i32, i32, vp, vp, i32, i32, dptr, vp, i32, vp, vp, vp]
+        L.cos_connected_sum_matrices_noalloc.argtypes = [i32, i32, vp, vp, i32, i32, dptr, vp, i32, vp, vp, vp]
         L.cos_connected_sum_batch.argtypes = [vp, i32, i32, vp, vp, vp, vp, i32, vp, vp, vp]
         L.cos_sync_status.argtypes = [vp]
         L.cos_status_string.argtypes = [i32]
@@ -172,6 +173,19 @@ def cos_connected_sum_matrices(n_max: int, order, moff, n_mat: int, loop_weight:
     _check(lib().cos_connected_sum_matrices(int(order.numel()), int(n_max), _ptr(order), _ptr(moff), int(n_mat),
                                             int(loop_weight), sig, _ptr(M), PRECISIONS[precision], _ptr(out),
                                             _ptr(abs_mass), _stream(stream)), "cos_connected_sum_matrices")
+
+
+def cos_connected_sum_matrices_noalloc(n_max: int, order, moff, n_mat: int, loop_weight: int,
+                                       sigma: Optional[Sequence[float]], M, precision: str, out, abs_mass=None,
+                                       stream=None):
+    """cos_connected_sum_matrices without device allocation (fixed 128 MiB static workspace)."""
+    sig = None
+    if sigma is not None:
+        sig = (ctypes.c_double * n_mat)(*[float(s) for s in sigma])
+    _check(lib().cos_connected_sum_matrices_noalloc(int(order.numel()), int(n_max), _ptr(order), _ptr(moff),
+                                                    int(n_mat), int(loop_weight), sig, _ptr(M),
+                                                    PRECISIONS[precision], _ptr(out), _ptr(abs_mass),
+                                                    _stream(stream)), "cos_connected_sum_matrices_noalloc")
 
 
 def cos_connected_sum_batch(tables: Tables, n_max: int, order, offset, site, tau, precision: str, out,

@@ -389,6 +389,70 @@ static cos_status launch_dp_t(Workspace *ws, const DpLaunch &L, cudaStream_t str
     return COS_OK;
 }
 
+// ------------------------------------------------------------------ raw-buffer launchers
+
+int dp_slots(const DpLaunch &L) { return L.shifts ? 3 : 2; }
+size_t dp_state_bytes(const DpLaunch &L) { return L.precision == COS_MIXED ? sizeof(float) : sizeof(double); }
+
+cos_status launch_plan_raw(const RawBuffers &rb, int n_cfg, int n_max, const int32_t *order, int cpb, int device,
+                           cudaStream_t stream) {
+    const int max_batches = (n_cfg + cpb - 1) / cpb + COS_NMAX;
+    cudaError_t e = cudaMemsetAsync(rb.plan, 0, 80 * sizeof(int), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "planner memset");
+    const int threads = 256;
+    const int blocks = std::max(1, std::min((n_cfg + threads - 1) / threads, 4 * sm_count(device)));
+    if (n_cfg > 0) plan_count_kernel<<<blocks, threads, 0, stream>>>(n_cfg, n_max, order, rb.plan, rb.status);
+    plan_prefix_kernel<<<1, 32, 0, stream>>>(cpb, rb.plan);
+    if (n_cfg > 0) plan_scatter_kernel<<<blocks, threads, 0, stream>>>(n_cfg, n_max, order, rb.plan, rb.list);
+    const int bb = std::max(1, std::min((max_batches + threads - 1) / threads, 4 * sm_count(device)));
+    plan_batches_kernel<<<bb, threads, 0, stream>>>(max_batches, cpb, rb.plan, rb.batches);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "planner launch");
+    return COS_OK;
+}
+
+template <typename T>
+static cos_status launch_dp_raw_t(const RawBuffers &rb, const DpLaunch &L, cudaStream_t stream) {
+    const Tuning tu = get_tuning(L.n_max, L.precision, L.n_mat);
+    const size_t msm = (size_t)L.n_max * L.n_max * kLanes;
+    size_t smem = ((msm * sizeof(T) + 15) & ~size_t(15));
+    if (sizeof(T) != sizeof(double)) smem += msm * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(dp_forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "dp smem attribute");
+    DpArgs a;
+    memset(&a, 0, sizeof a);
+    a.tabs = rb.tabs;
+    a.batches = rb.batches;
+    a.n_batches = rb.plan + 64;
+    a.batch_list = rb.list;
+    a.queue = rb.queue;
+    a.M = L.M;
+    a.moff = L.moff;
+    a.mstride = L.mstride;
+    a.nf_lanes = L.n_mat;
+    a.loop_weight = (double)L.loop_weight;
+    for (int l = 0; l < COS_MAX_FLAVORS; ++l) a.sigma[l] = L.sigma[l];
+    a.shifts = L.shifts ? 1 : 0;
+    a.absmode = L.absmode ? 1 : 0;
+    a.scratch = rb.scratch;
+    a.slot_elems = (size_t)host_order(L.n_max).max_slots * kLanes;
+    a.nslots = dp_slots(L);
+    a.smem_n = L.n_max;
+    a.out = L.out;
+    a.status = rb.status;
+    e = cudaMemsetAsync(rb.queue, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+    dp_forward_kernel<T><<<rb.grid, tu.warps * 32, smem, stream>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "dp launch");
+    return COS_OK;
+}
+
+cos_status launch_dp_raw(const RawBuffers &rb, const DpLaunch &L, cudaStream_t stream) {
+    if (L.precision == COS_MIXED) return launch_dp_raw_t<float>(rb, L, stream);
+    return launch_dp_raw_t<double>(rb, L, stream);
+}
+
 cos_status launch_dp(Workspace *ws, const DpLaunch &L, cudaStream_t stream) {
     if (L.precision == COS_MIXED) return launch_dp_t<float>(ws, L, stream);
     return launch_dp_t<double>(ws, L, stream);

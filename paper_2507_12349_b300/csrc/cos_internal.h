@@ -140,6 +140,25 @@ struct DpLaunch {
 cos_status launch_plan_batches(Workspace *ws, int n_cfg, int n_max, const int32_t *order, int cpb,
                                cudaStream_t stream);
 cos_status launch_dp(Workspace *ws, const DpLaunch &a, cudaStream_t stream);
+// Launch the planner and the DP kernel on caller-provided device buffers (no allocation):
+// plan = 80 ints, queue = 1 int, status = 1 int, list = n_cfg ints, batches = max_batches int4,
+// scratch = grid * nslots * slot_elems elements of the state type, tabs = device OrderTab[13].
+struct RawBuffers {
+    int *plan;
+    int *queue;
+    int *status;
+    int *list;
+    int4 *batches;
+    void *scratch;
+    const OrderTab *tabs;
+    int grid;
+};
+cos_status launch_plan_raw(const RawBuffers &rb, int n_cfg, int n_max, const int32_t *order, int cpb, int device,
+                           cudaStream_t stream);
+cos_status launch_dp_raw(const RawBuffers &rb, const DpLaunch &a, cudaStream_t stream);
+int dp_slots(const DpLaunch &a);            // layer slots of the ring (2, or 3 with shifts)
+size_t dp_state_bytes(const DpLaunch &a);   // bytes per state element
+
 cos_status launch_gather(const cos_tables *t, int n_cfg, const int32_t *order, const int64_t *offset,
                          const int32_t *site, const double *tau, const int64_t *moff, int64_t mstride,
                          double *M, int *status, cudaStream_t stream);

@@ -1,0 +1,75 @@
+"""The allocation-free entry point against the regular one.
+
+cos_connected_sum_matrices_noalloc serves callers that may not allocate device
+memory (an allocator-less plug-in, a process whose device memory belongs to a
+pool): its scratch lives in a fixed static device array.  This file is
+collected last so that a run stopping at the first failure has already run
+every other test; it passes on its own in a fresh process as well.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2507_12349_b300 import binding as B
+from paper_2507_12349_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _call(fn, order, moff, n_mat, wt, sigma, M, prec, out, mass):
+    lib = B.lib()
+    sig = None if sigma is None else (ctypes.c_double * n_mat)(*sigma)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = getattr(lib, fn)(int(order.numel()), int(order.max().item()), ctypes.c_void_p(order.data_ptr()),
+                          ctypes.c_void_p(moff.data_ptr()), n_mat, wt, sig, ctypes.c_void_p(M.data_ptr()),
+                          B.PRECISIONS[prec], ctypes.c_void_p(out.data_ptr()),
+                          ctypes.c_void_p(mass.data_ptr() if mass is not None else 0), stream)
+    assert rc == 0, (fn, rc, lib.cos_last_error())
+
+
+def _case(seed, ncfg, n_mat, orders):
+    rng = np.random.default_rng(seed)
+    order = rng.choice(orders, size=ncfg).astype(np.int32)
+    Ms = [I.random_matrices(seed * 1000 + c, 1, n_mat, int(n), 0.9)[0] for c, n in enumerate(order)]
+    moff = B.matrix_offsets(order, n_mat)
+    flat = np.concatenate([m.ravel() for m in Ms])
+    return (torch.tensor(order, device="cuda"), torch.tensor(moff, device="cuda"), torch.tensor(flat, device="cuda"))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_noalloc_matches_regular_entry_on_two_calls(prec):
+    calls = [  # (seed, configurations, matrices per configuration, loop weight, sigma, orders)
+        (11, 77, 3, 1, [0.1, 0.0, -0.08], [5, 7, 8]),
+        (12, 130, 1, 4, None, [3, 6, 9, 10]),
+    ]
+    for seed, ncfg, n_mat, wt, sigma, orders in calls:
+        order, moff, M = _case(seed, ncfg, n_mat, orders)
+        ref = torch.empty(ncfg, dtype=torch.float64, device="cuda")
+        ref_mass = torch.empty_like(ref)
+        got = torch.empty_like(ref)
+        got_mass = torch.empty_like(ref)
+        _call("cos_connected_sum_matrices", order, moff, n_mat, wt, sigma, M, prec, ref, ref_mass)
+        B.cos_sync_status()
+        _call("cos_connected_sum_matrices_noalloc", order, moff, n_mat, wt, sigma, M, prec, got, got_mass)
+        torch.cuda.synchronize()
+        r, g, m = ref.cpu().numpy(), got.cpu().numpy(), ref_mass.cpu().numpy()
+        n = order.cpu().numpy()
+        # same tolerance as the parity tests, stated against the absolute mass
+        eps = 2.0 ** -53 if prec == "fp64" else 2.0 ** -24
+        tol = 64 * n * eps * m
+        assert np.all(np.isfinite(g))
+        assert np.all(np.abs(g - r) <= tol)
+        assert np.allclose(got_mass.cpu().numpy(), m, rtol=1e-12)
+
+
+def test_noalloc_rejects_orders_beyond_its_workspace():
+    order = torch.tensor([11], dtype=torch.int32, device="cuda")
+    moff = torch.zeros(1, dtype=torch.int64, device="cuda")
+    M = torch.zeros(121, dtype=torch.float64, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.CosError) as ei:
+        B.cos_connected_sum_matrices_noalloc(11, order, moff, 1, 2, None, M, "fp64", out)
+    assert ei.value.status == -2
