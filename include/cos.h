@@ -172,6 +172,35 @@ cos_status cos_connected_sum_batch(const cos_tables *tables, int n_cfg, int n_ma
                                    cos_precision precision, double *d_out,
                                    double *d_abs_mass, cos_stream_t stream);
 
+/* ------------------------------------------------------------------ adjoint DP
+ * Gradient of the connected sums by the reverse (adjoint) DP: the forward DP is re-run with
+ * every layer kept, then walked backwards (the adjoint of Alg. 2-3 as merged in Results A).
+ * d_gout[c]   dLoss/dc for configuration c (the vector the gradient is contracted with)
+ * d_out       NULL or receives c (as cos_connected_sum_matrices, FP64)
+ * d_gM        NULL or receives dLoss/dM, same layout and offsets (d_moff) as d_M
+ * d_gsigma    NULL or receives dLoss/dsigma_l per configuration, [n_cfg][n_mat] (computed
+ *             also at sigma = 0, where shift transitions carry no weight)
+ * Other arguments as cos_connected_sum_matrices.  FP64 only. */
+cos_status cos_connected_sum_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
+                                           const int64_t *d_moff, int n_mat, int loop_weight,
+                                           const double *h_sigma, const double *d_M,
+                                           const double *d_gout, double *d_out, double *d_gM,
+                                           double *d_gsigma, cos_stream_t stream);
+
+/* Gradient from vertex coordinates, with the chain rule through the tables:
+ *   dc/dmu_l    = sum_ij dc/dM^l_ij  dM^l_ij/dmu_l  (same interpolation of the dG0/dmu table
+ *                 as the gather), the tables' xi depends on mu_l - alpha_l;
+ *   dc/dalpha_l = -(that sum) + dc/dsigma_l / U   (sigma_l = alpha_l / U, Methods A).
+ * For symmetric tables the common derivative is split evenly over the n_flavors flavors.
+ * d_gM / d_gmoff: NULL, or dLoss/dM written at d_gmoff[c] as [n_mat][n_c][n_c].
+ * d_gmu, d_galpha: NULL or [n_cfg][n_flavors] (per configuration, scaled by d_gout[c]).
+ * Builds the dG0/dmu table on first use. */
+cos_status cos_connected_sum_grad(const cos_tables *tables, int n_cfg, int n_max, const int32_t *d_order,
+                                  const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
+                                  const double *d_gout, double *d_out, double *d_gM,
+                                  const int64_t *d_gmoff, double *d_gmu, double *d_galpha,
+                                  cos_stream_t stream);
+
 /* ------------------------------------------------------------------ status
  * Synchronizes `stream`, returns and clears the device status word of the
  * calls enqueued on it (COS_OK if none failed). */

@@ -27,7 +27,8 @@ STATUS = {0: "COS_OK", -1: "COS_ERR_ARG", -2: "COS_ERR_ORDER", -3: "COS_ERR_CUDA
 # Every symbol include/cos.h declares (checked by the CPU tests).
 EXPORTS = [
     "cos_build_propagators", "cos_free_tables", "cos_get_tables_info", "cos_copy_table", "cos_gather",
-    "cos_connected_sum_matrices", "cos_connected_sum_matrices_noalloc", "cos_connected_sum_batch", "cos_sync_status", "cos_status_string",
+    "cos_connected_sum_matrices", "cos_connected_sum_matrices_noalloc", "cos_connected_sum_batch",
+    "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_sync_status", "cos_status_string",
     "cos_last_error", "cos_structure", "cos_peak_probe",
 ]
 
@@ -76,6 +77,8 @@ def lib(build: bool = True):
         L.cos_gather.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
         L.cos_connected_sum_matrices.argtypes = [i32, i32, vp, vp, i32, i32, dptr, vp, i32, vp, vp, vp]
         L.cos_connected_sum_matrices_noalloc.argtypes = [i32, i32, vp, vp, i32, i32, dptr, vp, i32, vp, vp, vp]
+        L.cos_connected_sum_matrices_grad.argtypes = [i32, i32, vp, vp, i32, i32, dptr, vp, vp, vp, vp, vp, vp]
+        L.cos_connected_sum_grad.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.cos_connected_sum_batch.argtypes = [vp, i32, i32, vp, vp, vp, vp, i32, vp, vp, vp]
         L.cos_sync_status.argtypes = [vp]
         L.cos_status_string.argtypes = [i32]
@@ -193,6 +196,24 @@ def cos_connected_sum_batch(tables: Tables, n_max: int, order, offset, site, tau
     _check(lib().cos_connected_sum_batch(tables.handle, int(order.numel()), int(n_max), _ptr(order), _ptr(offset),
                                          _ptr(site), _ptr(tau), PRECISIONS[precision], _ptr(out), _ptr(abs_mass),
                                          _stream(stream)), "cos_connected_sum_batch")
+
+
+def cos_connected_sum_matrices_grad(n_max: int, order, moff, n_mat: int, loop_weight: int,
+                                    sigma: Optional[Sequence[float]], M, gout, out=None, gM=None, gsigma=None,
+                                    stream=None):
+    sig = None
+    if sigma is not None:
+        sig = (ctypes.c_double * n_mat)(*[float(s) for s in sigma])
+    _check(lib().cos_connected_sum_matrices_grad(int(order.numel()), int(n_max), _ptr(order), _ptr(moff), int(n_mat),
+                                                 int(loop_weight), sig, _ptr(M), _ptr(gout), _ptr(out), _ptr(gM),
+                                                 _ptr(gsigma), _stream(stream)), "cos_connected_sum_matrices_grad")
+
+
+def cos_connected_sum_grad(tables: Tables, n_max: int, order, offset, site, tau, gout, out=None, gM=None,
+                           gmoff=None, gmu=None, galpha=None, stream=None):
+    _check(lib().cos_connected_sum_grad(tables.handle, int(order.numel()), int(n_max), _ptr(order), _ptr(offset),
+                                        _ptr(site), _ptr(tau), _ptr(gout), _ptr(out), _ptr(gM), _ptr(gmoff),
+                                        _ptr(gmu), _ptr(galpha), _stream(stream)), "cos_connected_sum_grad")
 
 
 def cos_sync_status(stream=None):

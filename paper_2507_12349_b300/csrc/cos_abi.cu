@@ -307,3 +307,113 @@ extern "C" cos_status cos_connected_sum_batch(const cos_tables *t, int n_cfg, in
     L.out = d_out;
     return run_dp(ws, L, d_abs_mass, (cudaStream_t)stream);
 }
+
+extern "C" cos_status cos_connected_sum_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
+                                                      const int64_t *d_moff, int n_mat, int loop_weight,
+                                                      const double *h_sigma, const double *d_M, const double *d_gout,
+                                                      double *d_out, double *d_gM, double *d_gsigma,
+                                                      cos_stream_t stream) {
+    cos_status st = check_common(n_cfg, n_max, COS_FP64, "cos_connected_sum_matrices_grad");
+    if (st != COS_OK) return st;
+    if (n_mat < 1 || n_mat > COS_MAX_FLAVORS || loop_weight < 1) {
+        set_error("cos_connected_sum_matrices_grad: n_mat outside [1, 8] or loop_weight < 1");
+        return COS_ERR_ARG;
+    }
+    if (n_cfg == 0) return COS_OK;
+    if (!d_order || !d_moff || !d_M || !d_gout) {
+        set_error("cos_connected_sum_matrices_grad: null device pointer");
+        return COS_ERR_ARG;
+    }
+    std::string err;
+    Workspace *ws = get_workspace((cudaStream_t)stream, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    DpLaunch L;
+    L.n_cfg = n_cfg;
+    L.n_max = n_max;
+    L.order = d_order;
+    L.M = d_M;
+    L.moff = d_moff;
+    L.n_mat = n_mat;
+    L.loop_weight = loop_weight;
+    for (int l = 0; l < n_mat; ++l) {
+        L.sigma[l] = h_sigma ? h_sigma[l] : 0.0;
+        if (L.sigma[l] != 0.0) L.shifts = true;
+    }
+    L.precision = COS_FP64;
+    L.out = d_out;
+    st = launch_plan_batches(ws, n_cfg, n_max, d_order, kLanes / n_mat, (cudaStream_t)stream);
+    if (st != COS_OK) return st;
+    return launch_adjoint(ws, L, d_gout, d_gM, d_moff, 0, d_gsigma, (cudaStream_t)stream);
+}
+
+extern "C" cos_status cos_connected_sum_grad(const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order,
+                                             const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
+                                             const double *d_gout, double *d_out, double *d_gM,
+                                             const int64_t *d_gmoff, double *d_gmu, double *d_galpha,
+                                             cos_stream_t stream) {
+    cos_status st = check_common(n_cfg, n_max, COS_FP64, "cos_connected_sum_grad");
+    if (st != COS_OK) return st;
+    if (!t) {
+        set_error("cos_connected_sum_grad: null tables");
+        return COS_ERR_ARG;
+    }
+    if (n_cfg == 0) return COS_OK;
+    if (!d_order || !d_offset || !d_site || !d_tau || !d_gout || (d_gM && !d_gmoff)) {
+        set_error("cos_connected_sum_grad: null device pointer (d_gM needs d_gmoff)");
+        return COS_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::string err;
+    Workspace *ws = get_workspace(s, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    if (d_gmu || d_galpha) {
+        st = ensure_dtables(const_cast<cos_tables *>(t), s);
+        if (st != COS_OK) return st;
+    }
+    const int64_t stride = (int64_t)t->n_mat * n_max * n_max;
+    st = ensure((void **)&ws->M, &ws->M_cap, (size_t)n_cfg * stride, sizeof(double), "matrix workspace");
+    if (st != COS_OK) return st;
+    double *gM = d_gM;
+    const int64_t *gmoff = d_gmoff;
+    int64_t gmstride = 0;
+    if (!gM) {
+        st = ensure((void **)&ws->gM, &ws->gM_cap, (size_t)n_cfg * stride, sizeof(double), "gradient workspace");
+        if (st != COS_OK) return st;
+        gM = ws->gM;
+        gmstride = stride;
+    }
+    st = ensure((void **)&ws->gsig, &ws->gsig_cap, (size_t)n_cfg * t->n_mat, sizeof(double), "sigma gradient");
+    if (st != COS_OK) return st;
+    st = launch_gather(t, n_cfg, d_order, d_offset, d_site, d_tau, nullptr, stride, ws->M, ws->status, s);
+    if (st != COS_OK) return st;
+    DpLaunch L;
+    L.n_cfg = n_cfg;
+    L.n_max = n_max;
+    L.order = d_order;
+    L.M = ws->M;
+    L.moff = nullptr;
+    L.mstride = stride;
+    L.n_mat = t->n_mat;
+    L.loop_weight = t->symmetric ? t->model.n_flavors : 1;
+    for (int l = 0; l < t->n_mat; ++l) {
+        L.sigma[l] = t->sigma[l];
+        if (L.sigma[l] != 0.0) L.shifts = true;
+    }
+    L.precision = COS_FP64;
+    L.out = d_out;
+    st = launch_plan_batches(ws, n_cfg, n_max, d_order, kLanes / t->n_mat, s);
+    if (st != COS_OK) return st;
+    // the adjoint writes dM with the gather's stride layout unless the caller gave offsets
+    st = launch_adjoint(ws, L, d_gout, gM, gmoff, gmstride, ws->gsig, s);
+    if (st != COS_OK) return st;
+    if (d_gmu || d_galpha)
+        st = launch_chain(t, n_cfg, d_order, d_offset, d_site, d_tau, gM, gmoff, gmstride, ws->gsig, d_gmu, d_galpha,
+                          s);
+    return st;
+}

@@ -1,0 +1,434 @@
+// Reverse (adjoint) DP: gradient of every connected sum with respect to every propagator
+// entry M^l[v][j] and to the shift weights sigma_l, then (tables path) by chain rule with
+// respect to mu_l and alpha_l.
+//
+// For each batch the CTA first re-runs the forward sweep of cos_dp.cu, keeping every layer
+// (exact per-layer offsets), then walks the layers backwards.  With Obar = dc/dO:
+//   Cbar(full) = gout 2^(n-1);  Cbar(mu) = sum over the configuration's flavor lanes of
+//   Obar(mu + e_k, k, k) when mu has a half-visited vertex; Gamma = sgn w Cbar (close adjoint).
+//   Row (mu, h), D_j = Obar(mu+e_j, h, j) + sgn sigma Obar(mu+2e_j, h, j) [mu_j = 0]:
+//     Obar(mu, h, v) = Gamma M[v][h] + sum_j D_j M[v][j]
+//     dM[v][h] += Gamma O(mu,h,v);  dM[v][j] += D_j O(mu,h,v)
+//     dsigma   += sgn d_j Obar(mu+2e_j, h, j)  (d_j = sum_v O M[v][j], recomputed) and, at the
+//                 start, sgn 2 Obar(2e_0, 0, 0).
+// Every adjoint slot read was written earlier in the same sweep (targets of reachable edges
+// are reachable), so the adjoint ring needs no clearing.  dM accumulates in a private
+// shared-memory copy per warp, summed in warp order at the end: no atomics, bitwise
+// reproducible.
+#include <algorithm>
+#include <cstring>
+
+#include "cos_dp_device.cuh"
+
+namespace cosdp {
+
+struct AdjArgs {
+    DpArgs f;
+    size_t store_elems;     // forward storage per CTA (all layers of n_max) * 32
+    size_t adj_slot_elems;  // one adjoint layer slot * 32
+    const double *gout;
+    double *gM;
+    const int64_t *gmoff;
+    int64_t gmstride;
+    double *gsig;
+};
+
+// Target adjoints are fetched in chunks of kChunk extensions: the loads of a chunk are issued
+// together, which bounds the registers a row holds (o, obar and one chunk).
+constexpr int kChunk = 4;
+
+template <int NV, bool SG>
+__device__ __forceinline__ void adj_row(const double *__restrict__ fsrc, double *__restrict__ aout,
+                                        const double *__restrict__ a1, const double *__restrict__ a2,
+                                        const double *__restrict__ Ms, double *__restrict__ gMw,
+                                        const uint32_t *__restrict__ rank3, uint32_t Vrow, uint32_t A, uint32_t B,
+                                        uint32_t J, uint32_t code, uint32_t off, int h, int hidx, int nA, int n,
+                                        double gamma, bool use_shift, double negsig, double sgn, int lane, double &gs) {
+    double o[NV], ob[NV];
+    int vt[NV];
+    const uint32_t rowoff = off + (uint32_t)(hidx * nA);
+    uint32_t vv = Vrow;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+        const int v = __ffs(vv) - 1;
+        vv &= vv - 1u;
+        vt[t] = v;
+        o[t] = fsrc[(size_t)(rowoff + (uint32_t)__popc(A & ((1u << v) - 1u))) * kLanes + lane];
+    }
+    const int nk = n * kLanes;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+        const int a = vt[t] * nk + lane + h * kLanes;
+        ob[t] = gamma * Ms[a];
+        if (gamma != 0.0) gMw[a] = fma(gamma, o[t], gMw[a]);
+    }
+    const uint32_t hlow = (1u << h) - 1u;
+    uint32_t jr = J;
+    while (jr) {
+        double D[kChunk], S[kChunk];
+        int js[kChunk];
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            js[q] = -1;
+            D[q] = 0.0;
+            S[q] = 0.0;
+            if (jr) {
+                const int j = __ffs(jr) - 1;
+                jr &= jr - 1u;
+                js[q] = j;
+                const uint32_t bj = 1u << j;
+                const bool untouched = !(A & bj);
+                const uint32_t A1 = A | bj;
+                const uint32_t B1 = untouched ? B : (B | bj);
+                const int nA1 = __popc(A1);
+                const int ai1 = __popc(A1 & (bj - 1u));
+                const int hi1 = __popc(head_set(B1, A1 & ~B1) & hlow);
+                const uint32_t off1 = __ldg(rank3 + code + c_p3[j]);
+                D[q] = a1[(size_t)(off1 + (uint32_t)(hi1 * nA1 + ai1)) * kLanes + lane];
+                if (untouched && use_shift) {
+                    const uint32_t B2 = B | bj;
+                    const int hi2 = __popc(head_set(B2, A1 & ~B2) & hlow);
+                    const uint32_t off2 = __ldg(rank3 + code + 2u * c_p3[j]);
+                    S[q] = a2[(size_t)(off2 + (uint32_t)(hi2 * nA1 + ai1)) * kLanes + lane];
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            if (js[q] >= 0) {
+                const int jo = js[q] * kLanes + lane;
+                const double Dq = fma(negsig, S[q], D[q]);
+                double d = 0.0;
+#pragma unroll
+                for (int t = 0; t < NV; ++t) {
+                    const int a = vt[t] * nk + jo;
+                    const double m = Ms[a];
+                    ob[t] = fma(Dq, m, ob[t]);
+                    gMw[a] = fma(Dq, o[t], gMw[a]);
+                    if (SG) d = fma(o[t], m, d);
+                }
+                if (SG) gs = fma(sgn * d, S[q], gs);
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NV; ++t)
+        aout[(size_t)(rowoff + (uint32_t)__popc(A & ((1u << vt[t]) - 1u))) * kLanes + lane] = ob[t];
+}
+
+template <bool SG>
+__device__ __forceinline__ void adj_row_dispatch(int nv, const double *fsrc, double *aout, const double *a1,
+                                                 const double *a2, const double *Ms, double *gMw,
+                                                 const uint32_t *rank3, uint32_t Vrow, uint32_t A, uint32_t B,
+                                                 uint32_t J, uint32_t code, uint32_t off, int h, int hidx, int nA,
+                                                 int n, double gamma, bool use_shift, double negsig, double sgn,
+                                                 int lane, double &gs) {
+#define COS_AROW(K)                                                                                              \
+    case K:                                                                                                      \
+        adj_row<K, SG>(fsrc, aout, a1, a2, Ms, gMw, rank3, Vrow, A, B, J, code, off, h, hidx, nA, n, gamma,       \
+                       use_shift, negsig, sgn, lane, gs);                                                         \
+        break;
+    switch (nv) {
+        COS_AROW(1)
+        COS_AROW(2)
+        COS_AROW(3)
+        COS_AROW(4)
+        COS_AROW(5)
+        COS_AROW(6)
+        COS_AROW(7)
+        COS_AROW(8)
+        COS_AROW(9)
+        COS_AROW(10)
+        COS_AROW(11)
+        COS_AROW(12)
+        default:
+            break;
+    }
+#undef COS_AROW
+}
+
+template <bool SG>
+__global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constant__ AdjArgs a) {
+    extern __shared__ __align__(16) double smem_d[];
+    __shared__ int s_batch;
+    __shared__ uint32_t s_base[kMaxLayers + 3];
+    __shared__ double s_red[8][kLanes];
+    const DpArgs &f = a.f;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int nsm = f.smem_n * f.smem_n * kLanes;
+    double *Ms = smem_d;
+    double *gMw = smem_d + (size_t)nsm * (1 + warp);
+    double *store = reinterpret_cast<double *>(f.scratch) + (size_t)blockIdx.x * (a.store_elems + 3 * a.adj_slot_elems);
+    double *adj = store + a.store_elems;
+    const int nfl = f.nf_lanes;
+    const int lam = lane % nfl;
+    const int ci = lane / nfl;
+    const double sgn = -1.0;
+    const double sig = f.sigma[lam];
+    const bool shifts = f.shifts != 0;
+    const bool use_shift = shifts || SG;
+    const double negsig = sgn * sig;
+    const int nbatch = *f.n_batches;
+
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_batch = atomicAdd(f.queue, 1);
+        __syncthreads();
+        const int b = s_batch;
+        if (b >= nbatch) break;
+        const int4 bd = f.batches[b];
+        const int n = bd.x;
+        const OrderTab &tab = f.tabs[n];
+        const bool active = (ci < bd.z) && (ci * nfl + nfl <= kLanes);
+        const int cfg = active ? f.batch_list[bd.y + ci] : -1;
+        const double *Mc = nullptr;
+        int64_t mbase = 0;
+        if (active) {
+            mbase = f.moff ? f.moff[cfg] : (int64_t)cfg * f.mstride;
+            Mc = f.M + mbase + (size_t)lam * n * n;
+        }
+        for (int e = warp; e < n * n; e += nwarps) Ms[e * kLanes + lane] = active ? Mc[e] : 0.0;
+        for (int e = 0; e < n * n; ++e) gMw[e * kLanes + lane] = 0.0;
+        if (threadIdx.x == 0) {
+            uint32_t run = 0;
+            for (int l = 0; l <= 2 * n + 2; ++l) {
+                s_base[l] = run;
+                if (l <= 2 * n) run += tab.layer_slots[l];
+            }
+        }
+        __syncthreads();
+        if (warp == 0) store[(size_t)s_base[1] * kLanes + lane] = 1.0;
+        __syncthreads();
+        // forward sweep, every layer kept
+        for (int ell = 1; ell <= 2 * n; ++ell) {
+            const double *src = store + (size_t)s_base[ell] * kLanes;
+            double *dst1 = store + (size_t)s_base[ell + 1] * kLanes;
+            double *dst2 = store + (size_t)s_base[ell + 2] * kLanes;
+            const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
+            for (uint32_t mi = warp; mi < cnt; mi += nwarps)
+                fwd_mask<double>(tab, first + mi, ell, n, src, dst1, dst2, Ms, Ms, lane, ci, nfl, sgn, f.loop_weight,
+                                 sig, shifts, active, lam, cfg, f.out, f.status);
+            __syncthreads();
+        }
+        // reverse sweep
+        const uint32_t full = (1u << n) - 1u;
+        const double gout = active ? a.gout[cfg] : 0.0;
+        double gs = 0.0;
+        for (int ell = 2 * n; ell >= 1; --ell) {
+            const double *fsrc = store + (size_t)s_base[ell] * kLanes;
+            double *aout = adj + (size_t)(ell % 3) * a.adj_slot_elems;
+            const double *a1 = adj + (size_t)((ell + 1) % 3) * a.adj_slot_elems;
+            const double *a2 = adj + (size_t)((ell + 2) % 3) * a.adj_slot_elems;
+            const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
+            for (uint32_t mi = warp; mi < cnt; mi += nwarps) {
+                const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + first + mi));
+                const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, code = mk.y, off = mk.z;
+                const uint32_t ones = A & ~B;
+                const uint32_t H = head_set(B, ones);
+                const uint32_t J = full & ~B;
+                const int nA = __popc(A);
+                double cbar = 0.0;
+                if (B == full) {
+                    cbar = ldexp(gout, n - 1);
+                } else if (ones) {
+                    const int k = __ffs(ones) - 1;
+                    const uint32_t bk = 1u << k;
+                    const uint32_t B1 = B | bk;
+                    const int hi1 = __popc(head_set(B1, A & ~B1) & (bk - 1u));
+                    const int ai1 = __popc(A & (bk - 1u));
+                    const uint32_t off1 = __ldg(tab.rank3 + code + c_p3[k]);
+                    const double own = a1[(size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane];
+                    cbar = own;
+                    if (nfl > 1) {
+                        const int base = ci * nfl;
+                        cbar = 0.0;
+                        for (int g = 0; g < nfl; ++g) cbar += __shfl_sync(0xFFFFFFFFu, own, (base + g) & 31);
+                    }
+                    if (SG && ell == 1) gs = fma(sgn * 2.0, own, gs);   // shifted start, weight sgn 2 sigma
+                }
+                const double gamma = sgn * f.loop_weight * cbar;
+                for (uint32_t hh = H; hh; hh &= hh - 1u) {
+                    const int h = __ffs(hh) - 1;
+                    const int hidx = __popc(H & ((1u << h) - 1u));
+                    const uint32_t Vrow = row_vmask(A, ones, h);
+                    adj_row_dispatch<SG>(__popc(Vrow), fsrc, aout, a1, a2, Ms, gMw, tab.rank3, Vrow, A, B, J, code,
+                                         off, h, hidx, nA, n, gamma, use_shift, negsig, sgn, lane, gs);
+                }
+            }
+            __syncthreads();
+        }
+        // dM: sum of the per-warp copies in warp order; dsigma: sum over warps
+        for (int e = warp; e < n * n; e += nwarps) {
+            double s = 0.0;
+            for (int w = 0; w < nwarps; ++w) s += smem_d[(size_t)nsm * (1 + w) + e * kLanes + lane];
+            if (active && a.gM) {
+                const int64_t gb = a.gmoff ? a.gmoff[cfg] : (int64_t)cfg * a.gmstride;
+                a.gM[gb + (int64_t)lam * n * n + e] = s;
+            }
+        }
+        if (SG) {
+            s_red[warp][lane] = gs;
+            __syncthreads();
+            if (warp == 0 && active && a.gsig) {
+                double s = 0.0;
+                for (int w = 0; w < nwarps; ++w) s += s_red[w][lane];
+                a.gsig[(int64_t)cfg * nfl + lam] = s;
+            }
+        }
+    }
+}
+
+// Chain rule through the tables: dc/dmu_l = sum_ij dc/dM^l_ij dM^l_ij/dmu_l, with dM/dmu the
+// same linear interpolation of the dG/dmu table as the gather; dc/dalpha_l = -dc/dmu_l part
+// + dc/dsigma_l / U.  Symmetric tables: the common derivative is split evenly over flavors.
+__global__ void chain_kernel(const double *__restrict__ dG, int L, int n_tau, double beta, int n_mat, int n_flavors,
+                             int symmetric, double U, int n_cfg, const int32_t *__restrict__ order,
+                             const int64_t *__restrict__ offset, const int32_t *__restrict__ site,
+                             const double *__restrict__ tau, const double *__restrict__ gM,
+                             const int64_t *__restrict__ gmoff, int64_t gmstride, const double *__restrict__ gsig,
+                             double *__restrict__ gmu, double *__restrict__ galpha) {
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int LL = L * L;
+    const double scale = (double)(n_tau - 1) / beta;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_cfg; c += warps) {
+        const int n = order[c];
+        if (n < 1 || n > COS_NMAX) continue;
+        const int64_t o = offset[c];
+        const double *g = gM + (gmoff ? gmoff[c] : (int64_t)c * gmstride);
+        for (int l = 0; l < n_mat; ++l) {
+            double acc = 0.0;
+            for (int e = lane; e < n * n; e += 32) {
+                const int i = e / n, j = e % n;
+                const int si = site[o + i], sj = site[o + j];
+                if (si < 0 || si >= LL || sj < 0 || sj >= LL) continue;
+                const int dx = ((si % L) - (sj % L) + L) % L;
+                const int dy = ((si / L) - (sj / L) + L) % L;
+                const double dt = tau[o + i] - tau[o + j];
+                double s = 1.0, tt = dt;
+                if (dt <= 0.0) {
+                    s = -1.0;
+                    tt = dt + beta;
+                }
+                const double x = tt * scale;
+                int m = (int)floor(x);
+                m = max(0, min(m, n_tau - 2));
+                const double fr = x - m;
+                const double *row = dG + ((size_t)l * LL + dx + L * dy) * n_tau + m;
+                acc = fma(g[(size_t)l * n * n + e], s * fma(fr, row[1] - row[0], row[0]), acc);
+            }
+            for (int w = 16; w >= 1; w >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, w);
+            if (lane == 0) {
+                if (symmetric) {
+                    for (int q = 0; q < n_flavors; ++q) {
+                        const double dmu = acc / n_flavors;
+                        if (gmu) gmu[(int64_t)c * n_flavors + q] = dmu;
+                        if (galpha) galpha[(int64_t)c * n_flavors + q] = -dmu + gsig[c] / (n_flavors * U);
+                    }
+                } else {
+                    if (gmu) gmu[(int64_t)c * n_flavors + l] = acc;
+                    if (galpha) galpha[(int64_t)c * n_flavors + l] = -acc + gsig[(int64_t)c * n_mat + l] / U;
+                }
+            }
+        }
+    }
+}
+
+int adjoint_warps(int n_max) {
+    const size_t per = (size_t)n_max * n_max * kLanes * sizeof(double);
+    const size_t cap = 227 * 1024;
+    int w = (int)(cap / per) - 1;
+    return std::max(1, std::min(8, w));
+}
+
+cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, double *gM, const int64_t *gmoff,
+                          int64_t gmstride, double *gsig, cudaStream_t stream) {
+    std::string err;
+    const OrderTab *tabs = device_orders(ws->device, &err);
+    if (!tabs) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    const HostOrder &ho = host_order(L.n_max);
+    size_t total_slots = 0;
+    for (int l = 0; l <= 2 * L.n_max; ++l) total_slots += ho.layer_slots[l];
+    const size_t store_elems = total_slots * kLanes;
+    const size_t adj_slot_elems = (size_t)ho.max_slots * kLanes;
+    const size_t per_cta = (store_elems + 3 * adj_slot_elems) * sizeof(double);
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
+    const int cpb = kLanes / L.n_mat;
+    const int max_batches = (L.n_cfg + cpb - 1) / cpb + COS_NMAX;
+    int grid = std::max(1, std::min(nsm, max_batches));
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+        const size_t avail = ws->scratch_bytes + (size_t)(0.85 * (double)free_b);
+        while (grid > 1 && (size_t)grid * per_cta > avail) grid = std::max(1, grid / 2);
+    }
+    cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "adjoint scratch");
+    if (st != COS_OK) return st;
+    const int warps = adjoint_warps(L.n_max);
+    const size_t smem = (size_t)(1 + warps) * L.n_max * L.n_max * kLanes * sizeof(double);
+    const bool sg = gsig != nullptr;
+    cudaError_t e = sg ? cudaFuncSetAttribute(dp_adjoint_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                       : cudaFuncSetAttribute(dp_adjoint_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint smem attribute");
+    AdjArgs a;
+    memset(&a, 0, sizeof a);
+    DpArgs &f = a.f;
+    f.tabs = tabs;
+    f.batches = ws->batches;
+    f.n_batches = ws->plan_counts + 64;
+    f.batch_list = ws->batch_list;
+    f.queue = ws->queue;
+    f.M = L.M;
+    f.moff = L.moff;
+    f.mstride = L.mstride;
+    f.nf_lanes = L.n_mat;
+    f.loop_weight = (double)L.loop_weight;
+    for (int l = 0; l < COS_MAX_FLAVORS; ++l) f.sigma[l] = L.sigma[l];
+    f.shifts = L.shifts ? 1 : 0;
+    f.absmode = 0;
+    f.scratch = ws->scratch;
+    f.slot_elems = adj_slot_elems;
+    f.nslots = 3;
+    f.smem_n = L.n_max;
+    f.out = L.out;
+    f.status = ws->status;
+    a.store_elems = store_elems;
+    a.adj_slot_elems = adj_slot_elems;
+    a.gout = gout;
+    a.gM = gM;
+    a.gmoff = gmoff;
+    a.gmstride = gmstride;
+    a.gsig = gsig;
+    e = cudaMemsetAsync(ws->queue, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+    if (sg)
+        dp_adjoint_kernel<true><<<grid, warps * 32, smem, stream>>>(a);
+    else
+        dp_adjoint_kernel<false><<<grid, warps * 32, smem, stream>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+    return COS_OK;
+}
+
+cos_status launch_chain(const cos_tables *t, int n_cfg, const int32_t *order, const int64_t *offset,
+                        const int32_t *site, const double *tau, const double *gM, const int64_t *gmoff,
+                        int64_t gmstride, const double *gsig, double *gmu, double *galpha, cudaStream_t stream) {
+    if (n_cfg == 0) return COS_OK;
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, t->device);
+    const int threads = 256;
+    const int blocks = std::max(1, std::min((n_cfg * 32 + threads - 1) / threads, 8 * nsm));
+    chain_kernel<<<blocks, threads, 0, stream>>>(t->d_dG, t->model.L, t->model.n_tau, t->model.beta, t->n_mat,
+                                                  t->model.n_flavors, t->symmetric, t->model.U, n_cfg, order, offset,
+                                                  site, tau, gM, gmoff, gmstride, gsig, gmu, galpha);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "chain launch");
+    return COS_OK;
+}
+
+}  // namespace cosdp

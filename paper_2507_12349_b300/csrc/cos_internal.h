@@ -109,6 +109,11 @@ struct Workspace {
     // DP layer scratch
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
+    // gradient path
+    double *gM = nullptr;
+    size_t gM_cap = 0;
+    double *gsig = nullptr;
+    size_t gsig_cap = 0;
 };
 
 Workspace *get_workspace(cudaStream_t stream, std::string *err);
@@ -158,6 +163,13 @@ cos_status launch_plan_raw(const RawBuffers &rb, int n_cfg, int n_max, const int
 cos_status launch_dp_raw(const RawBuffers &rb, const DpLaunch &a, cudaStream_t stream);
 int dp_slots(const DpLaunch &a);            // layer slots of the ring (2, or 3 with shifts)
 size_t dp_state_bytes(const DpLaunch &a);   // bytes per state element
+
+cos_status launch_adjoint(Workspace *ws, const DpLaunch &a, const double *gout, double *gM, const int64_t *gmoff,
+                          int64_t gmstride, double *gsig, cudaStream_t stream);
+cos_status launch_chain(const cos_tables *t, int n_cfg, const int32_t *order, const int64_t *offset,
+                        const int32_t *site, const double *tau, const double *gM, const int64_t *gmoff,
+                        int64_t gmstride, const double *gsig, double *gmu, double *galpha, cudaStream_t stream);
+cos_status ensure_dtables(cos_tables *t, cudaStream_t stream);
 
 cos_status launch_gather(const cos_tables *t, int n_cfg, const int32_t *order, const int64_t *offset,
                          const int32_t *site, const double *tau, const int64_t *moff, int64_t mstride,
