@@ -329,8 +329,9 @@ def native_arm(args):
         line["parity"] = parity
     if extras:
         line["forms"] = extras
-    if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    if rank == 0:
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
@@ -342,6 +343,30 @@ def cpu_baseline(w, budget):
     rate, threads, n = cpu_oracle_rate(w, budget)
     return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n} configurations of the n=8 SU(4) workload (numpy gather + C DP in double, OpenMP)"}
+
+
+def measure_adjoint(torch, B, flush_buf, n_cfg):
+    """Gradient overhead on the adjoint workload (SU(4), mu broken, n = 10): the gradient call
+    (forward recomputed with every layer kept + reverse DP + chain rule to mu, alpha) against
+    the forward call on the same configurations."""
+    w = I.WORKLOADS["su4_adjoint_n10"]
+    cfgs = I.workload_configs(w, n_cfg)
+    tabs = B.tables_for(w.model)
+    d = B.configs_to_device(cfgs)
+    out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
+    gout = torch.ones(n_cfg, dtype=torch.float64, device="cuda")
+    gmu = torch.empty(n_cfg, 4, dtype=torch.float64, device="cuda")
+    gal = torch.empty_like(gmu)
+    fwd = lambda: B.cos_connected_sum_batch(tabs, 10, *d, "fp64", out)
+    grad = lambda: B.cos_connected_sum_grad(tabs, 10, *d, gout, gmu=gmu, galpha=gal)
+    fwd(); grad()
+    B.cos_sync_status()
+    tf = statistics.mean(time_steps(torch, fwd, 2, lambda: flush_l2(flush_buf)))
+    tg = statistics.mean(time_steps(torch, grad, 2, lambda: flush_l2(flush_buf)))
+    B.cos_sync_status()
+    tabs.close()
+    return {"configs": n_cfg, "forward_configs_per_s": n_cfg / tf, "grad_configs_per_s": n_cfg / tg,
+            "grad_overhead": tg / tf}
 
 
 def measure_forms(torch, B, flush_buf):
@@ -372,6 +397,7 @@ def measure_forms(torch, B, flush_buf):
     res["su3_shift_n10_mixed"] = run("su3_shift_mixed_n10", 20_000, "mixed")
     res["su3_shift_n10_fp64"] = run("su3_shift_mixed_n10", 20_000, "fp64")
     res["su6_uneven_n4_12_fp64"] = run("su6_sym_uneven_n4_12", 20_000, "fp64", steps=1)
+    res["su4_n10_adjoint"] = measure_adjoint(torch, B, flush_buf, 5_000)
     # plain FP64 per-configuration form: one configuration per call
     w = I.WORKLOADS[WORKLOAD]
     cfgs = I.workload_configs(w, 200)

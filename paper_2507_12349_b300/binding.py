@@ -106,13 +106,18 @@ def _stream(stream=None) -> ctypes.c_void_p:
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _ptr(t) -> ctypes.c_void_p:
+def _ptr(t, dtype=None) -> ctypes.c_void_p:
     if t is None:
         return ctypes.c_void_p(0)
     if not t.is_cuda:
         raise ValueError("expected a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
+    if dtype is not None:
+        import torch
+        want = {"f64": torch.float64, "i32": torch.int32, "i64": torch.int64}[dtype]
+        if t.dtype != want:
+            raise TypeError(f"expected {want}, got {t.dtype}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -163,8 +168,8 @@ def tables_for(model, stream=None) -> Tables:
 
 
 def cos_gather(tables: Tables, order, offset, site, tau, moff, M, stream=None):
-    _check(lib().cos_gather(tables.handle, int(order.numel()), _ptr(order), _ptr(offset), _ptr(site), _ptr(tau),
-                            _ptr(moff), _ptr(M), _stream(stream)), "cos_gather")
+    _check(lib().cos_gather(tables.handle, int(order.numel()), _ptr(order, "i32"), _ptr(offset, "i64"), _ptr(site, "i32"), _ptr(tau, "f64"),
+                            _ptr(moff, "i64"), _ptr(M, "f64"), _stream(stream)), "cos_gather")
 
 
 def cos_connected_sum_matrices(n_max: int, order, moff, n_mat: int, loop_weight: int,
@@ -173,9 +178,9 @@ def cos_connected_sum_matrices(n_max: int, order, moff, n_mat: int, loop_weight:
     sig = None
     if sigma is not None:
         sig = (ctypes.c_double * n_mat)(*[float(s) for s in sigma])
-    _check(lib().cos_connected_sum_matrices(int(order.numel()), int(n_max), _ptr(order), _ptr(moff), int(n_mat),
-                                            int(loop_weight), sig, _ptr(M), PRECISIONS[precision], _ptr(out),
-                                            _ptr(abs_mass), _stream(stream)), "cos_connected_sum_matrices")
+    _check(lib().cos_connected_sum_matrices(int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(moff, "i64"), int(n_mat),
+                                            int(loop_weight), sig, _ptr(M, "f64"), PRECISIONS[precision], _ptr(out, "f64"),
+                                            _ptr(abs_mass, "f64"), _stream(stream)), "cos_connected_sum_matrices")
 
 
 def cos_connected_sum_matrices_noalloc(n_max: int, order, moff, n_mat: int, loop_weight: int,
@@ -185,16 +190,16 @@ def cos_connected_sum_matrices_noalloc(n_max: int, order, moff, n_mat: int, loop
     sig = None
     if sigma is not None:
         sig = (ctypes.c_double * n_mat)(*[float(s) for s in sigma])
-    _check(lib().cos_connected_sum_matrices_noalloc(int(order.numel()), int(n_max), _ptr(order), _ptr(moff),
-                                                    int(n_mat), int(loop_weight), sig, _ptr(M),
-                                                    PRECISIONS[precision], _ptr(out), _ptr(abs_mass),
+    _check(lib().cos_connected_sum_matrices_noalloc(int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(moff, "i64"),
+                                                    int(n_mat), int(loop_weight), sig, _ptr(M, "f64"),
+                                                    PRECISIONS[precision], _ptr(out, "f64"), _ptr(abs_mass, "f64"),
                                                     _stream(stream)), "cos_connected_sum_matrices_noalloc")
 
 
 def cos_connected_sum_batch(tables: Tables, n_max: int, order, offset, site, tau, precision: str, out,
                             abs_mass=None, stream=None):
-    _check(lib().cos_connected_sum_batch(tables.handle, int(order.numel()), int(n_max), _ptr(order), _ptr(offset),
-                                         _ptr(site), _ptr(tau), PRECISIONS[precision], _ptr(out), _ptr(abs_mass),
+    _check(lib().cos_connected_sum_batch(tables.handle, int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(offset, "i64"),
+                                         _ptr(site, "i32"), _ptr(tau, "f64"), PRECISIONS[precision], _ptr(out, "f64"), _ptr(abs_mass, "f64"),
                                          _stream(stream)), "cos_connected_sum_batch")
 
 
@@ -204,16 +209,16 @@ def cos_connected_sum_matrices_grad(n_max: int, order, moff, n_mat: int, loop_we
     sig = None
     if sigma is not None:
         sig = (ctypes.c_double * n_mat)(*[float(s) for s in sigma])
-    _check(lib().cos_connected_sum_matrices_grad(int(order.numel()), int(n_max), _ptr(order), _ptr(moff), int(n_mat),
-                                                 int(loop_weight), sig, _ptr(M), _ptr(gout), _ptr(out), _ptr(gM),
-                                                 _ptr(gsigma), _stream(stream)), "cos_connected_sum_matrices_grad")
+    _check(lib().cos_connected_sum_matrices_grad(int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(moff, "i64"), int(n_mat),
+                                                 int(loop_weight), sig, _ptr(M, "f64"), _ptr(gout, "f64"), _ptr(out, "f64"), _ptr(gM, "f64"),
+                                                 _ptr(gsigma, "f64"), _stream(stream)), "cos_connected_sum_matrices_grad")
 
 
 def cos_connected_sum_grad(tables: Tables, n_max: int, order, offset, site, tau, gout, out=None, gM=None,
                            gmoff=None, gmu=None, galpha=None, stream=None):
-    _check(lib().cos_connected_sum_grad(tables.handle, int(order.numel()), int(n_max), _ptr(order), _ptr(offset),
-                                        _ptr(site), _ptr(tau), _ptr(gout), _ptr(out), _ptr(gM), _ptr(gmoff),
-                                        _ptr(gmu), _ptr(galpha), _stream(stream)), "cos_connected_sum_grad")
+    _check(lib().cos_connected_sum_grad(tables.handle, int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(offset, "i64"),
+                                        _ptr(site, "i32"), _ptr(tau, "f64"), _ptr(gout, "f64"), _ptr(out, "f64"), _ptr(gM, "f64"), _ptr(gmoff, "i64"),
+                                        _ptr(gmu, "f64"), _ptr(galpha, "f64"), _stream(stream)), "cos_connected_sum_grad")
 
 
 def cos_sync_status(stream=None):

@@ -336,9 +336,14 @@ __global__ void chain_kernel(const double *__restrict__ dG, int L, int n_tau, do
     }
 }
 
-int adjoint_warps(int n_max) {
+// Warps per adjoint CTA: the matrices plus one private dM copy per warp must fit the opt-in
+// shared memory, less a margin for the kernel's static shared arrays (about 2.2 KB).
+int adjoint_warps(int n_max, int device) {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (optin <= 0) optin = 227 * 1024;
     const size_t per = (size_t)n_max * n_max * kLanes * sizeof(double);
-    const size_t cap = 227 * 1024;
+    const size_t cap = (size_t)optin - 4096;
     int w = (int)(cap / per) - 1;
     return std::max(1, std::min(8, w));
 }
@@ -369,7 +374,7 @@ cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, 
     }
     cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "adjoint scratch");
     if (st != COS_OK) return st;
-    const int warps = adjoint_warps(L.n_max);
+    const int warps = adjoint_warps(L.n_max, ws->device);
     const size_t smem = (size_t)(1 + warps) * L.n_max * L.n_max * kLanes * sizeof(double);
     const bool sg = gsig != nullptr;
     cudaError_t e = sg ? cudaFuncSetAttribute(dp_adjoint_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)

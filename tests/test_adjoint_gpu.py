@@ -40,7 +40,7 @@ def gpu_grad(Ms, n_mat, wt, sigma, gout):
     gM = torch.full_like(d_M, float("nan"))
     gs = torch.full((n, n_mat), float("nan"), dtype=torch.float64, device="cuda")
     B.cos_connected_sum_matrices_grad(int(order.max()), d_order, d_moff, n_mat, wt, sigma, d_M,
-                                      torch.tensor(gout, device="cuda"), out, gM, gs)
+                                      torch.tensor(gout, dtype=torch.float64, device="cuda"), out, gM, gs)
     B.cos_sync_status()
     g = gM.cpu().numpy()
     return out.cpu().numpy(), [g[moff[c]:moff[c] + Ms[c].size].reshape(Ms[c].shape) for c in range(n)], gs.cpu().numpy()
