@@ -201,6 +201,39 @@ cos_status cos_connected_sum_grad(const cos_tables *tables, int n_cfg, int n_max
                                   const int64_t *d_gmoff, double *d_gmu, double *d_galpha,
                                   cos_stream_t stream);
 
+/* ------------------------------------------------------------------ graphs and tuning
+ * A plan freezes one batch (fixed device addresses of inputs and outputs) into a CUDA graph:
+ * device planner, gather (batch plan), persistent DP kernel(s).  Creation runs the call once
+ * eagerly on `stream` (results valid afterwards), then captures it; the plan owns a private
+ * workspace, so plans never share scratch with each other or with direct calls.
+ * cos_plan_launch replays it with one cudaGraphLaunch on any stream; cos_plan_status
+ * synchronizes that stream and reports (and clears) the plan's device status word. */
+typedef struct cos_plan cos_plan;
+cos_status cos_plan_create_batch(const cos_tables *tables, int n_cfg, int n_max, const int32_t *d_order,
+                                 const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
+                                 cos_precision precision, double *d_out, double *d_abs_mass,
+                                 cos_stream_t stream, cos_plan **out);
+cos_status cos_plan_create_matrices(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                                    int n_mat, int loop_weight, const double *h_sigma, const double *d_M,
+                                    cos_precision precision, double *d_out, double *d_abs_mass,
+                                    cos_stream_t stream, cos_plan **out);
+cos_status cos_plan_launch(cos_plan *plan, cos_stream_t stream);
+cos_status cos_plan_status(cos_plan *plan, cos_stream_t stream);
+cos_status cos_plan_grid(const cos_plan *plan, int *grid);   /* persistent CTAs of the plan */
+cos_status cos_plan_destroy(cos_plan *plan);
+
+/* Launch shape of the DP kernel per (order n_max of the launch, precision, matrices per
+ * configuration): warps per CTA (1..16) and resident CTAs per SM (1..8).  A launch mixing
+ * orders uses the shape of its largest order, which dominates its work (a factor 3-4 per
+ * order).  cos_autotune times every shape the occupancy calculator admits on n_cfg
+ * synthetic configurations of order n (device buffers allocated for the run), installs the
+ * fastest, and appends "n precision n_mat warps ctas ms" to the file named by the
+ * environment variable COS_TUNE_FILE (read back when a process starts). */
+cos_status cos_set_tuning(int n, cos_precision precision, int n_mat, int warps, int ctas_per_sm);
+cos_status cos_get_tuning(int n, cos_precision precision, int n_mat, int *warps, int *ctas_per_sm);
+cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts, cos_precision precision, int n_cfg,
+                        cos_stream_t stream, int *best_warps, int *best_ctas, double *best_ms);
+
 /* ------------------------------------------------------------------ status
  * Synchronizes `stream`, returns and clears the device status word of the
  * calls enqueued on it (COS_OK if none failed). */

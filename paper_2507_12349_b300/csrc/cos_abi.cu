@@ -1,5 +1,6 @@
 // C ABI of libcos: argument checks, per-(device, stream) workspaces, device status words,
 // launch tuning and the public entry points that chain the kernels.
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -76,20 +77,52 @@ Workspace *get_workspace(cudaStream_t stream, std::string *err) {
     return ws;
 }
 
-// Launch shape per order: warps per CTA and CTAs per SM of the persistent grid.  Defaults
-// keep four or more warps per SM sub-partition; large orders use one CTA per SM so the layer
-// scratch (two layers of up to 1.26 M slots x 32 lanes at n = 12) stays within HBM.
-// COS_TUNE="n:warps:ctas,..." overrides (written by the autotuner).
+// Launch shape per (order, precision, lanes per configuration): warps per CTA and CTAs per SM
+// of the persistent grid.  Defaults keep four or more warps per SM sub-partition; large orders
+// use one CTA per SM so the layer scratch (two layers of up to 1.26 M slots x 32 lanes at
+// n = 12) stays within HBM.  Overrides, in order of precedence: the table filled by
+// cos_set_tuning / cos_autotune (and loaded from the file named by COS_TUNE_FILE), then
+// COS_TUNE="n:warps:ctas,...".
+namespace {
+std::mutex g_tune_mu;
+std::map<int, Tuning> g_tune;
+bool g_tune_loaded = false;
+int tune_key(int n, int precision, int nf) { return (n * 4 + precision) * 16 + nf; }
+
+void load_tune_file_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = getenv("COS_TUNE_FILE");
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    int n, prec, nf, w, c;
+    double ms;
+    char line[256];
+    while (fgets(line, sizeof line, f)) {
+        if (sscanf(line, "%d %d %d %d %d %lf", &n, &prec, &nf, &w, &c, &ms) >= 5 && n >= 1 && n <= COS_NMAX &&
+            w >= 1 && w <= 16 && c >= 1 && c <= 8) {
+            Tuning t;
+            t.warps = w;
+            t.ctas_per_sm = c;
+            g_tune[tune_key(n, prec, nf)] = t;
+        }
+    }
+    fclose(f);
+}
+}  // namespace
+
+void set_tuning(int n, int precision, int nf_lanes, Tuning t) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    load_tune_file_locked();
+    g_tune[tune_key(n, precision, nf_lanes)] = t;
+}
+
 Tuning get_tuning(int n, int precision, int nf_lanes) {
-    (void)precision;
-    (void)nf_lanes;
     Tuning t;
     if (n >= 11) {
         t.warps = 16;
         t.ctas_per_sm = 1;
-    } else if (n >= 9) {
-        t.warps = 8;
-        t.ctas_per_sm = 2;
     } else {
         t.warps = 8;
         t.ctas_per_sm = 2;
@@ -110,10 +143,45 @@ Tuning get_tuning(int n, int precision, int nf_lanes) {
             }
         }
     }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    load_tune_file_locked();
+    auto it = g_tune.find(tune_key(n, precision, nf_lanes));
+    if (it != g_tune.end()) t = it->second;
     return t;
 }
 
-static cos_status check_common(int n_cfg, int n_max, cos_precision prec, const char *fn) {
+Workspace *new_private_workspace(int device, std::string *err) {
+    Workspace *ws = new Workspace();
+    ws->device = device;
+    cudaError_t e = cudaMalloc(&ws->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ws->plan_counts, 80 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ws->queue, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ws->status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        *err = std::string("workspace: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        free_workspace(ws);
+        return nullptr;
+    }
+    return ws;
+}
+
+void free_workspace(Workspace *ws) {
+    if (!ws) return;
+    cudaFree(ws->status);
+    cudaFree(ws->plan_counts);
+    cudaFree(ws->queue);
+    cudaFree(ws->batch_list);
+    cudaFree(ws->batches);
+    cudaFree(ws->M);
+    cudaFree(ws->moff);
+    cudaFree(ws->scratch);
+    cudaFree(ws->gM);
+    cudaFree(ws->gsig);
+    delete ws;
+}
+
+cos_status check_common(int n_cfg, int n_max, cos_precision prec, const char *fn) {
     if (n_cfg < 0) {
         set_error(std::string(fn) + ": n_cfg < 0");
         return COS_ERR_ARG;
@@ -129,7 +197,7 @@ static cos_status check_common(int n_cfg, int n_max, cos_precision prec, const c
     return COS_OK;
 }
 
-static cos_status run_dp(Workspace *ws, DpLaunch L, double *d_abs_mass, cudaStream_t stream) {
+cos_status run_dp(Workspace *ws, DpLaunch L, double *d_abs_mass, cudaStream_t stream) {
     const int cpb = kLanes / L.n_mat;
     cos_status st = launch_plan_batches(ws, L.n_cfg, L.n_max, L.order, cpb, stream);
     if (st != COS_OK) return st;
@@ -199,27 +267,10 @@ extern "C" cos_status cos_sync_status(cos_stream_t stream) {
     return COS_OK;
 }
 
-extern "C" cos_status cos_connected_sum_matrices(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
-                                                 int n_mat, int loop_weight, const double *h_sigma,
-                                                 const double *d_M, cos_precision precision, double *d_out,
-                                                 double *d_abs_mass, cos_stream_t stream) {
-    cos_status st = check_common(n_cfg, n_max, precision, "cos_connected_sum_matrices");
-    if (st != COS_OK) return st;
-    if (n_mat < 1 || n_mat > COS_MAX_FLAVORS || loop_weight < 1) {
-        set_error("cos_connected_sum_matrices: n_mat outside [1, 8] or loop_weight < 1");
-        return COS_ERR_ARG;
-    }
-    if (n_cfg == 0) return COS_OK;
-    if (!d_order || !d_moff || !d_M || !d_out) {
-        set_error("cos_connected_sum_matrices: null device pointer");
-        return COS_ERR_ARG;
-    }
-    std::string err;
-    Workspace *ws = get_workspace((cudaStream_t)stream, &err);
-    if (!ws) {
-        set_error(err);
-        return COS_ERR_CUDA;
-    }
+namespace cosdp {
+cos_status matrices_body(Workspace *ws, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                         int n_mat, int loop_weight, const double *h_sigma, const double *d_M,
+                         cos_precision precision, double *d_out, double *d_abs_mass, cudaStream_t stream) {
     DpLaunch L;
     L.n_cfg = n_cfg;
     L.n_max = n_max;
@@ -234,7 +285,41 @@ extern "C" cos_status cos_connected_sum_matrices(int n_cfg, int n_max, const int
     }
     L.precision = precision;
     L.out = d_out;
-    return run_dp(ws, L, d_abs_mass, (cudaStream_t)stream);
+    return run_dp(ws, L, d_abs_mass, stream);
+}
+
+cos_status check_matrices(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff, int n_mat,
+                          int loop_weight, const double *d_M, cos_precision precision, const double *d_out,
+                          const char *fn) {
+    cos_status st = check_common(n_cfg, n_max, precision, fn);
+    if (st != COS_OK) return st;
+    if (n_mat < 1 || n_mat > COS_MAX_FLAVORS || loop_weight < 1) {
+        set_error(std::string(fn) + ": n_mat outside [1, 8] or loop_weight < 1");
+        return COS_ERR_ARG;
+    }
+    if (n_cfg > 0 && (!d_order || !d_moff || !d_M || !d_out)) {
+        set_error(std::string(fn) + ": null device pointer");
+        return COS_ERR_ARG;
+    }
+    return COS_OK;
+}
+}  // namespace cosdp
+
+extern "C" cos_status cos_connected_sum_matrices(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                                                 int n_mat, int loop_weight, const double *h_sigma,
+                                                 const double *d_M, cos_precision precision, double *d_out,
+                                                 double *d_abs_mass, cos_stream_t stream) {
+    cos_status st = check_matrices(n_cfg, n_max, d_order, d_moff, n_mat, loop_weight, d_M, precision, d_out,
+                                   "cos_connected_sum_matrices");
+    if (st != COS_OK || n_cfg == 0) return st;
+    std::string err;
+    Workspace *ws = get_workspace((cudaStream_t)stream, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    return matrices_body(ws, n_cfg, n_max, d_order, d_moff, n_mat, loop_weight, h_sigma, d_M, precision, d_out,
+                         d_abs_mass, (cudaStream_t)stream);
 }
 
 extern "C" cos_status cos_gather(const cos_tables *t, int n_cfg, const int32_t *d_order, const int64_t *d_offset,
@@ -263,32 +348,30 @@ extern "C" cos_status cos_gather(const cos_tables *t, int n_cfg, const int32_t *
                          (cudaStream_t)stream);
 }
 
-extern "C" cos_status cos_connected_sum_batch(const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order,
-                                              const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
-                                              cos_precision precision, double *d_out, double *d_abs_mass,
-                                              cos_stream_t stream) {
-    cos_status st = check_common(n_cfg, n_max, precision, "cos_connected_sum_batch");
+namespace cosdp {
+cos_status check_batch(const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_offset,
+                       const int32_t *d_site, const double *d_tau, cos_precision precision, const double *d_out,
+                       const char *fn) {
+    cos_status st = check_common(n_cfg, n_max, precision, fn);
     if (st != COS_OK) return st;
     if (!t) {
-        set_error("cos_connected_sum_batch: null tables");
+        set_error(std::string(fn) + ": null tables");
         return COS_ERR_ARG;
     }
-    if (n_cfg == 0) return COS_OK;
-    if (!d_order || !d_offset || !d_site || !d_tau || !d_out) {
-        set_error("cos_connected_sum_batch: null device pointer");
+    if (n_cfg > 0 && (!d_order || !d_offset || !d_site || !d_tau || !d_out)) {
+        set_error(std::string(fn) + ": null device pointer");
         return COS_ERR_ARG;
     }
-    std::string err;
-    Workspace *ws = get_workspace((cudaStream_t)stream, &err);
-    if (!ws) {
-        set_error(err);
-        return COS_ERR_CUDA;
-    }
+    return COS_OK;
+}
+
+cos_status batch_body(Workspace *ws, const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order,
+                      const int64_t *d_offset, const int32_t *d_site, const double *d_tau, cos_precision precision,
+                      double *d_out, double *d_abs_mass, cudaStream_t stream) {
     const int64_t stride = (int64_t)t->n_mat * n_max * n_max;
-    st = ensure((void **)&ws->M, &ws->M_cap, (size_t)n_cfg * stride, sizeof(double), "matrix workspace");
+    cos_status st = ensure((void **)&ws->M, &ws->M_cap, (size_t)n_cfg * stride, sizeof(double), "matrix workspace");
     if (st != COS_OK) return st;
-    st = launch_gather(t, n_cfg, d_order, d_offset, d_site, d_tau, nullptr, stride, ws->M, ws->status,
-                       (cudaStream_t)stream);
+    st = launch_gather(t, n_cfg, d_order, d_offset, d_site, d_tau, nullptr, stride, ws->M, ws->status, stream);
     if (st != COS_OK) return st;
     DpLaunch L;
     L.n_cfg = n_cfg;
@@ -305,7 +388,25 @@ extern "C" cos_status cos_connected_sum_batch(const cos_tables *t, int n_cfg, in
     }
     L.precision = precision;
     L.out = d_out;
-    return run_dp(ws, L, d_abs_mass, (cudaStream_t)stream);
+    return run_dp(ws, L, d_abs_mass, stream);
+}
+}  // namespace cosdp
+
+extern "C" cos_status cos_connected_sum_batch(const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order,
+                                              const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
+                                              cos_precision precision, double *d_out, double *d_abs_mass,
+                                              cos_stream_t stream) {
+    cos_status st = check_batch(t, n_cfg, n_max, d_order, d_offset, d_site, d_tau, precision, d_out,
+                                "cos_connected_sum_batch");
+    if (st != COS_OK || n_cfg == 0) return st;
+    std::string err;
+    Workspace *ws = get_workspace((cudaStream_t)stream, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    return batch_body(ws, t, n_cfg, n_max, d_order, d_offset, d_site, d_tau, precision, d_out, d_abs_mass,
+                      (cudaStream_t)stream);
 }
 
 extern "C" cos_status cos_connected_sum_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,

@@ -181,12 +181,17 @@ static cos_status launch_dp_t(Workspace *ws, const DpLaunch &L, cudaStream_t str
     const int cpb = kLanes / nfl;
     const int max_batches = (L.n_cfg + cpb - 1) / cpb + COS_NMAX;
     int grid = std::max(1, std::min(nsm * tu.ctas_per_sm, max_batches));
-    // Keep the layer scratch inside the free device memory (leave headroom for the caller).
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-        const size_t avail = ws->scratch_bytes + (size_t)(0.85 * (double)free_b);
-        while (grid > 1 && (size_t)grid * per_cta > avail) grid = std::max(1, grid / 2);
+    if (ws->fixed_grid > 0) {
+        grid = ws->fixed_grid;
+    } else {
+        // Keep the layer scratch inside the free device memory (leave headroom for the caller).
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            const size_t avail = ws->scratch_bytes + (size_t)(0.85 * (double)free_b);
+            while (grid > 1 && (size_t)grid * per_cta > avail) grid = std::max(1, grid / 2);
+        }
     }
+    ws->last_grid = grid;
     cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "layer scratch");
     if (st != COS_OK) return st;
     const int threads = tu.warps * 32;
@@ -286,6 +291,19 @@ static cos_status launch_dp_raw_t(const RawBuffers &rb, const DpLaunch &L, cudaS
 cos_status launch_dp_raw(const RawBuffers &rb, const DpLaunch &L, cudaStream_t stream) {
     if (L.precision == COS_MIXED) return launch_dp_raw_t<float>(rb, L, stream);
     return launch_dp_raw_t<double>(rb, L, stream);
+}
+
+int dp_max_active_ctas(int precision, int threads, size_t smem) {
+    int nb = 0;
+    cudaError_t e;
+    if (precision == COS_MIXED) {
+        cudaFuncSetAttribute(dp_forward_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dp_forward_kernel<float>, threads, smem);
+    } else {
+        cudaFuncSetAttribute(dp_forward_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dp_forward_kernel<double>, threads, smem);
+    }
+    return e == cudaSuccess ? nb : 0;
 }
 
 cos_status launch_dp(Workspace *ws, const DpLaunch &L, cudaStream_t stream) {

@@ -114,6 +114,10 @@ struct Workspace {
     size_t gM_cap = 0;
     double *gsig = nullptr;
     size_t gsig_cap = 0;
+    // launch shape: fixed_grid > 0 pins the persistent grid (plans captured in a graph);
+    // last_grid records the grid of the latest DP launch.
+    int fixed_grid = 0;
+    int last_grid = 0;
 };
 
 Workspace *get_workspace(cudaStream_t stream, std::string *err);
@@ -125,6 +129,9 @@ struct Tuning {
     int ctas_per_sm = 2;    // resident CTAs per SM targeted by the persistent grid
 };
 Tuning get_tuning(int n, int precision, int nf_lanes);
+void set_tuning(int n, int precision, int nf_lanes, Tuning t);
+Workspace *new_private_workspace(int device, std::string *err);   // not registered per stream
+void free_workspace(Workspace *ws);
 
 struct DpLaunch {
     int n_cfg = 0;
@@ -170,6 +177,22 @@ cos_status launch_chain(const cos_tables *t, int n_cfg, const int32_t *order, co
                         const int32_t *site, const double *tau, const double *gM, const int64_t *gmoff,
                         int64_t gmstride, const double *gsig, double *gmu, double *galpha, cudaStream_t stream);
 cos_status ensure_dtables(cos_tables *t, cudaStream_t stream);
+
+cos_status check_common(int n_cfg, int n_max, cos_precision prec, const char *fn);
+cos_status run_dp(Workspace *ws, DpLaunch L, double *d_abs_mass, cudaStream_t stream);
+cos_status matrices_body(Workspace *ws, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                         int n_mat, int loop_weight, const double *h_sigma, const double *d_M,
+                         cos_precision precision, double *d_out, double *d_abs_mass, cudaStream_t stream);
+cos_status check_matrices(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff, int n_mat,
+                          int loop_weight, const double *d_M, cos_precision precision, const double *d_out,
+                          const char *fn);
+cos_status check_batch(const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_offset,
+                       const int32_t *d_site, const double *d_tau, cos_precision precision, const double *d_out,
+                       const char *fn);
+cos_status batch_body(Workspace *ws, const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order,
+                      const int64_t *d_offset, const int32_t *d_site, const double *d_tau, cos_precision precision,
+                      double *d_out, double *d_abs_mass, cudaStream_t stream);
+int dp_max_active_ctas(int precision, int threads, size_t smem);
 
 cos_status launch_gather(const cos_tables *t, int n_cfg, const int32_t *order, const int64_t *offset,
                          const int32_t *site, const double *tau, const int64_t *moff, int64_t mstride,
