@@ -228,7 +228,9 @@ cos_status cos_plan_destroy(cos_plan *plan);
  * order).  cos_autotune times every shape the occupancy calculator admits on n_cfg
  * synthetic configurations of order n (device buffers allocated for the run), installs the
  * fastest, and appends "n precision n_mat warps ctas ms" to the file named by the
- * environment variable COS_TUNE_FILE (read back when a process starts). */
+ * environment variable COS_TUNE_OUT, if set.  At the first launch a process reads the
+ * tuning file named by COS_TUNE_FILE (the Python binding points it at the package's
+ * tuning_b300.txt unless the caller set it). */
 cos_status cos_set_tuning(int n, cos_precision precision, int n_mat, int warps, int ctas_per_sm);
 cos_status cos_get_tuning(int n, cos_precision precision, int n_mat, int *warps, int *ctas_per_sm);
 cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts, cos_precision precision, int n_cfg,

@@ -1,0 +1,50 @@
+"""Write the launch-shape tuning cache (tuning_b300.txt) for the benchmark workloads.
+
+Usage (on the GPU): python -m paper_2507_12349_b300.autotune [--out FILE]
+Runs cos_autotune for every (order, precision, matrices per configuration) that the
+workloads launch with and writes one line per case: "n precision n_mat warps ctas ms".
+The sample size fills the GPU: 32 lanes x 2 CTAs x SMs worth of configurations (one CTA
+per SM at orders 11-12, where one batch already holds ~0.3-0.6 s of FP64 work).
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# (order, matrices per configuration, loop weight, shifts, precision)
+CASES = [
+    (4, 1, 2, False, "fp64"),
+    (8, 4, 1, False, "fp64"), (8, 4, 1, False, "mixed"),
+    (10, 3, 1, True, "mixed"), (10, 3, 1, True, "fp64"),
+    (10, 4, 1, False, "fp64"),
+] + [(n, 1, 6, False, "fp64") for n in range(4, 13)]
+
+
+def main():
+    import torch
+    from paper_2507_12349_b300 import binding as B
+    p = argparse.ArgumentParser()
+    p.add_argument("--out", default=B.TUNING_FILE)
+    args = p.parse_args()
+    torch.cuda.set_device(0)
+    B.lib()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    lines = []
+    for n, n_mat, wt, shifts, prec in CASES:
+        cpb = 32 // n_mat
+        n_cfg = cpb * sms * (1 if n >= 11 else 2)
+        w, c, ms = B.cos_autotune(n, n_mat, wt, shifts, prec, n_cfg)
+        line = f"{n} {B.PRECISIONS[prec]} {n_mat} {w} {c} {ms:.4f}"
+        print(line, f"# {prec} configs={n_cfg}", flush=True)
+        lines.append(line)
+    with open(args.out, "w") as f:
+        f.write("\n".join(lines) + "\n")
+
+
+if __name__ == "__main__":
+    main()

@@ -63,10 +63,15 @@ class cos_structure_info(ctypes.Structure):
 _lib = None
 
 
+TUNING_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_b300.txt")
+
+
 def lib(build: bool = True):
     """Load libcos.so (building it from source first if it is missing or stale)."""
     global _lib
     if _lib is None:
+        if "COS_TUNE_FILE" not in os.environ and os.path.exists(TUNING_FILE):
+            os.environ["COS_TUNE_FILE"] = TUNING_FILE
         path = _build.build() if build else _build.LIB
         if not os.path.exists(path):
             raise OSError(f"libcos.so not found at {path}; run paper_2507_12349_b300.build")

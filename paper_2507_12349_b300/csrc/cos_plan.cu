@@ -316,7 +316,7 @@ extern "C" cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts
     }
     if (st == COS_OK && best_t < 1e300) {
         set_tuning(n, precision, n_mat, best);
-        if (const char *path = getenv("COS_TUNE_FILE")) {
+        if (const char *path = getenv("COS_TUNE_OUT")) {
             if (FILE *f = fopen(path, "a")) {
                 fprintf(f, "%d %d %d %d %d %.4f\n", n, (int)precision, n_mat, best.warps, best.ctas_per_sm, best_t);
                 fclose(f);

@@ -28,9 +28,9 @@ def test_batch_plan_matches_direct_call_uneven_orders():
     assert torch.equal(out, ref)
     assert plan.grid() >= 1
     # new inputs at the same addresses are picked up by the next replay
-    cfgs2 = I.workload_configs(w, 1500, first_cfg=5000)
-    for dst, src in zip(d, B.configs_to_device(cfgs2)):
-        dst.copy_(src)
+    L2 = w.model.L ** 2
+    d[2].copy_((d[2] + 37) % L2)
+    d[3].copy_(torch.remainder(d[3] + 0.37 * w.model.beta, w.model.beta))
     ref2 = torch.empty_like(ref)
     B.cos_connected_sum_batch(tabs, 12, *d, "fp64", ref2)
     plan.launch()
