@@ -58,9 +58,8 @@ def dist_env():
 
 # ------------------------------------------------------------------ CPU oracle (reported baseline)
 
-def cpu_oracle_rate(w, budget_s: float, n_limit: int | None = None):
-    """Oracle (plain C DP, OpenMP over configurations, plus the numpy gather) on a
-    bounded sample of the workload.  Returns (configs/s, threads, sample size)."""
+def oracle_values(w, cfgs, absmode=False):
+    """Oracle connected sums (numpy gather + C DP in double, OpenMP) of `cfgs` (one order)."""
     import oracle as O
     from oracle import propagators as P
     model = w.model
@@ -69,23 +68,27 @@ def cpu_oracle_rate(w, budget_s: float, n_limit: int | None = None):
     if model.symmetric:
         tabs, wt, sig = tabs[:1], model.n_flavors, sig[:1]
     sig = sig if any(sig) else None
-    # calibrate on a few configurations
+    Ms = np.stack(P.gather(tabs, cfgs, model.L, model.beta))
+    hi, lo, threads = O.dp_batch(Ms, sig, wt, absmode=absmode, nthreads=0)
+    return hi + lo, threads
+
+
+def cpu_oracle_rate(w, budget_s: float, n_limit: int | None = None):
+    """Oracle on a bounded sample of the workload (the first configurations of its seeded
+    stream).  Returns (configs/s, threads, sample size, oracle values)."""
     probe = I.workload_configs(w, 8)
     t0 = time.perf_counter()
-    Ms = np.stack(P.gather(tabs, probe, model.L, model.beta))
-    _, _, threads = O.dp_batch(Ms, sig, wt, nthreads=0)
-    t1 = time.perf_counter() - t0
-    per_cfg = t1 / 8.0
+    oracle_values(w, probe)
+    per_cfg = (time.perf_counter() - t0) / 8.0
     n = max(8, int(budget_s / max(per_cfg, 1e-6)))
     if n_limit:
         n = min(n, n_limit)
     n = min(n, w.n_cfg)
     cfgs = I.workload_configs(w, n)
     t0 = time.perf_counter()
-    Ms = np.stack(P.gather(tabs, cfgs, model.L, model.beta))
-    _, _, threads = O.dp_batch(Ms, sig, wt, nthreads=0)
+    vals, threads = oracle_values(w, cfgs)
     dt = time.perf_counter() - t0
-    return n / dt, threads, n
+    return n / dt, threads, n, vals
 
 
 def reference_arm(args):
@@ -99,7 +102,7 @@ def reference_arm(args):
     rates, sample, threads = [], 0, 1
     t_start = time.perf_counter()
     for _ in range(args.steps):
-        r, threads, sample = cpu_oracle_rate(w, budget)
+        r, threads, sample, _ = cpu_oracle_rate(w, budget)
         rates.append(r)
     wall = time.perf_counter() - t_start
     value = statistics.median(rates)
@@ -287,23 +290,10 @@ def native_arm(args):
     h2d = sum(x.numel() * x.element_size() for x in (h_order, h_offset, h_site, h_tau))
     d2h = h_out.numel() * h_out.element_size()
     e2e_value = world * n_cfg / statistics.mean(e2e_times)
-    # parity spot check of the timed output against the CPU oracle (few configurations)
-    parity = None
-    if rank == 0:
-        import oracle as O
-        from oracle import propagators as P
-        otabs = P.model_tables(w.model)
-        idx = [0, n_cfg // 2, n_cfg - 1]
-        got = out.cpu().numpy()
-        errs = []
-        for c, M in zip(idx, P.gather(otabs, cfgs, w.model.L, w.model.beta, idx)):
-            ref = O.dp(M, None, prec="ld")
-            errs.append(abs(got[c] - ref) / abs(ref))
-        parity = {"configs_checked": len(idx), "max_rel_err_vs_oracle": max(errs)}
-
-    extras = {}
+    head_out = out.cpu().numpy()
+    extras, keep = {}, {}
     if not args.no_extras and rank == 0:
-        extras = measure_forms(torch, B, flush_buf)
+        extras, keep = measure_forms(torch, B, flush_buf)
 
     launches_per_step = 1 + 4 + 1   # gather, 4 planner kernels, DP
     line = {
@@ -325,13 +315,11 @@ def native_arm(args):
         "gpu_launches": launches_per_step * args.steps,
         "wall_s_timed_region": t_wall,
     }
-    if parity:
-        line["parity"] = parity
     if extras:
         line["forms"] = extras
     if rank == 0:
         if not args.no_cpu:
-            line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+            line["cpu_baseline"], line["accuracy"] = oracle_leg(w, args.cpu_seconds, head_out, keep)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
@@ -339,10 +327,33 @@ def native_arm(args):
     tabs.close()
 
 
-def cpu_baseline(w, budget):
-    rate, threads, n = cpu_oracle_rate(w, budget)
-    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+def error_stats(got, ref, mass=None):
+    got, ref = np.asarray(got), np.asarray(ref)
+    rel = np.abs(got - ref) / np.abs(ref)
+    out = {"configs": int(len(ref)), "median_rel_err": float(np.median(rel)), "max_rel_err": float(np.max(rel))}
+    if mass is not None:
+        em = np.abs(got - ref) / mass
+        out.update({"max_err_over_mass": float(np.max(em)), "median_kappa": float(np.median(mass / np.abs(ref))),
+                    "max_kappa": float(np.max(mass / np.abs(ref)))})
+    return out
+
+
+def oracle_leg(w, budget, head_out, keep):
+    """The CPU oracle on the host cores: its throughput on a bounded sample of the headline
+    workload, and the error of the GPU results of the same configurations against it (FP64
+    headline; mixed-precision forms against the FP64 oracle, per configuration)."""
+    rate, threads, n, vals = cpu_oracle_rate(w, budget)
+    base = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n} configurations of the n=8 SU(4) workload (numpy gather + C DP in double, OpenMP)"}
+    acc = {"su4_n8_fp64_vs_oracle": error_stats(head_out[:n], vals)}
+    for name, (wname, got) in keep.items():
+        wk = I.WORKLOADS[wname]
+        k = min(len(got), 160)
+        cfgs = I.workload_configs(wk, k)
+        ref, _ = oracle_values(wk, cfgs)
+        mass, _ = oracle_values(wk, cfgs, absmode=True)
+        acc[name] = error_stats(got[:k], ref, mass)
+    return base, acc
 
 
 def measure_adjoint(torch, B, flush_buf, n_cfg):
@@ -370,35 +381,49 @@ def measure_adjoint(torch, B, flush_buf, n_cfg):
 
 
 def measure_forms(torch, B, flush_buf):
-    """The other forms of the path on the same GPU: mixed precision, the uneven-order
-    persistent batch, and the plain FP64 form with one configuration per launch."""
-    res = {}
+    """The other forms of the path on the same GPU: FP64 vs mixed precision at orders 8 and 10,
+    the uneven-order batch as one persistent launch in a CUDA graph (autotuned shapes), the
+    adjoint, and the plain FP64 form with one configuration per launch.  Returns the
+    measurements and the GPU outputs kept for the oracle leg's error statistics."""
+    res, keep = {}, {}
 
-    def run(name, n_cfg, prec, steps=2):
+    def run(name, n_cfg, prec, steps=2, graph=False):
         w = I.WORKLOADS[name]
         cfgs = I.workload_configs(w, n_cfg)
         tabs = B.tables_for(w.model)
         d = B.configs_to_device(cfgs)
         out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
         nmax = int(cfgs.order.max())
-        B.cos_connected_sum_batch(tabs, nmax, *d, prec, out)
-        B.cos_sync_status()
-        ts = time_steps(torch, lambda: B.cos_connected_sum_batch(tabs, nmax, *d, prec, out), steps,
-                        lambda: flush_l2(flush_buf))
-        B.cos_sync_status()
         n_mat = tabs.info().n_mat
-        shifts = any(w.model.sigma)
-        fl = algorithmic_flops(B, cfgs.order, n_mat, shifts)
+        if graph:
+            plan = B.cos_plan_create_batch(tabs, nmax, *d, prec, out)
+            fn = plan.launch
+        else:
+            fn = lambda: B.cos_connected_sum_batch(tabs, nmax, *d, prec, out)
+            fn()
+        B.cos_sync_status()
+        ts = time_steps(torch, fn, steps, lambda: flush_l2(flush_buf))
+        if graph:
+            plan.status()
+            plan.close()
+        B.cos_sync_status()
+        fl = algorithmic_flops(B, cfgs.order, n_mat, any(w.model.sigma))
         t = statistics.mean(ts)
         tabs.close()
-        return {"configs": n_cfg, "configs_per_s": n_cfg / t, "tflops": fl / t / 1e12, "ms": t * 1e3}
+        r = {"configs": n_cfg, "configs_per_s": n_cfg / t, "tflops": fl / t / 1e12, "ms": t * 1e3,
+             "launch_shape_n_max": list(B.cos_get_tuning(nmax, prec, n_mat))}
+        if graph:
+            r["cuda_graph"] = True
+        return r, out.cpu().numpy()
 
-    res["su4_n8_mixed"] = run("su4_mu_broken_n8", 100_000, "mixed")
-    res["su3_shift_n10_mixed"] = run("su3_shift_mixed_n10", 20_000, "mixed")
-    res["su3_shift_n10_fp64"] = run("su3_shift_mixed_n10", 20_000, "fp64")
-    res["su6_uneven_n4_12_fp64"] = run("su6_sym_uneven_n4_12", 20_000, "fp64", steps=1)
+    res["su4_n8_mixed"], keep_n8 = run("su4_mu_broken_n8", 100_000, "mixed")
+    keep["su4_n8_mixed_vs_fp64_oracle"] = ("su4_mu_broken_n8", keep_n8)
+    res["su3_shift_n10_mixed"], keep_n10 = run("su3_shift_mixed_n10", 100_000, "mixed")
+    keep["su3_shift_n10_mixed_vs_fp64_oracle"] = ("su3_shift_mixed_n10", keep_n10)
+    res["su3_shift_n10_fp64"], _ = run("su3_shift_mixed_n10", 20_000, "fp64")
+    res["su6_uneven_n4_12_fp64_graph"], _ = run("su6_sym_uneven_n4_12", 200_000, "fp64", steps=1, graph=True)
     res["su4_n10_adjoint"] = measure_adjoint(torch, B, flush_buf, 5_000)
-    # plain FP64 per-configuration form: one configuration per call
+    # plain FP64 per-configuration form: one configuration per call, no graph
     w = I.WORKLOADS[WORKLOAD]
     cfgs = I.workload_configs(w, 200)
     tabs = B.tables_for(w.model)
@@ -412,15 +437,15 @@ def measure_forms(torch, B, flush_buf):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for args in per:
-        B.cos_connected_sum_batch(tabs, 8, *args, "fp64", out)
+    for a in per:
+        B.cos_connected_sum_batch(tabs, 8, *a, "fp64", out)
     e1.record()
     e1.synchronize()
     t = e0.elapsed_time(e1) * 1e-3
     res["su4_n8_fp64_one_config_per_launch"] = {"configs": 200, "configs_per_s": 200 / t}
     B.cos_sync_status()
     tabs.close()
-    return res
+    return res, keep
 
 
 def main():
