@@ -34,6 +34,7 @@ WORKLOAD = "su4_mu_broken_n8"
 METRIC = "connected-sum configs/s at order n (FP64 vs mixed), roofline fraction, grad overhead"
 UNIT = "configs/s"
 NOMINAL_FP64_TFLOPS = 1.25
+FP64_FMA_PER_CLK_SM = 2.0
 
 
 def parse():
@@ -240,8 +241,8 @@ def native_arm(args):
     B.cos_sync_status()
     dp_times.clear()
 
-    # FP64 pipe peak (roofline denominator), measured on this GPU just before the run
-    fp64_peak = B.measure_peak(0)
+    # FMA probe on this GPU (reported beside the unit-count peak below)
+    probe = B.measure_peak(0)
 
     sampler = ClockSampler(local)
     if world > 1:
@@ -263,6 +264,14 @@ def native_arm(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total = float(t.item())
     value = world * n_cfg * args.steps / total
+    # FP64 roofline denominator from unit counts and the clock seen in the timed region: the
+    # FP64 pipe retires 2 FMA lanes per clock per SM (ncu: the FMA probe issues 1.68 FP64
+    # lanes per SM-cycle at 84.2 % sm__pipe_fp64_cycles_active), 2 flop per FMA.
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    clk = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2032.0
+    fp64_peak = sms * FP64_FMA_PER_CLK_SM * 2.0 * clk * 1e6
+    peak_source = (f"unit count: {sms} SMs x {FP64_FMA_PER_CLK_SM} FP64 FMA/clk/SM x 2 flop x "
+                   f"{clk:.0f} MHz (median SM clock in the timed region)")
     dp_avg = statistics.mean(a.elapsed_time(b) * 1e-3 for a, b in dp_times)
     flops_launch = algorithmic_flops(B, cfgs.order, n_mat, False)
     achieved = flops_launch / dp_avg
@@ -306,7 +315,7 @@ def native_arm(args):
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"configs sharded x{world}"},
         "roofline": {"bound": "alu", "pipe": "fp64 fma", "achieved": achieved / 1e12,
                      "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                     "peak_source": "measured: FP64 FMA probe (cos_peak_probe kind 0) on this GPU",
+                     "peak_source": peak_source, "probe_tflops": probe / 1e12,
                      "peak_nominal": NOMINAL_FP64_TFLOPS, "frac_of_nominal": achieved / 1e12 / NOMINAL_FP64_TFLOPS,
                      "kernel": "dp_forward_kernel<double>", "flops_per_launch": flops_launch,
                      "launch_ms": dp_avg * 1e3, "traffic": None},

@@ -265,7 +265,7 @@ cos_status cos_structure(int n, cos_structure_info *info);
 /* ------------------------------------------------------------------ measurement
  * Peak-throughput probe (no counterpart in the paper; it supplies the roofline
  * denominator of the FP64 / FP32 pipes).  kind 0: FP64 FMA, 8 independent chains
- * per thread; kind 1: FP32 FMA, 16 chains.  Work = 2 * blocks * threads * chains
+ * per thread; kind 1: FP32 FMA, 16 chains; kinds 2, 3, 4: FP64 with 4, 16, 32 chains.  Work = 2 * blocks * threads * chains
  * * iters flops.  d_sink: device buffer of `blocks` elements of the probed type
  * (written only if a chain hits an impossible value).  Time it with CUDA events. */
 cos_status cos_peak_probe(int kind, int blocks, int threads, int iters, void *d_sink, cos_stream_t stream);

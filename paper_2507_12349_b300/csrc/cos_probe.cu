@@ -24,14 +24,21 @@ __global__ void fma_probe_kernel(int iters, T *sink) {
 
 extern "C" cos_status cos_peak_probe(int kind, int blocks, int threads, int iters, void *d_sink, cos_stream_t stream) {
     using namespace cosdp;
-    if (blocks < 1 || threads < 32 || threads > 1024 || iters < 1 || !d_sink || (kind != 0 && kind != 1)) {
+    if (blocks < 1 || threads < 32 || threads > 1024 || iters < 1 || !d_sink || kind < 0 || kind > 4) {
         set_error("cos_peak_probe: bad argument");
         return COS_ERR_ARG;
     }
-    if (kind == 0)
-        fma_probe_kernel<double, 8><<<blocks, threads, 0, (cudaStream_t)stream>>>(iters, (double *)d_sink);
-    else
-        fma_probe_kernel<float, 16><<<blocks, threads, 0, (cudaStream_t)stream>>>(iters, (float *)d_sink);
+    // kind 0/1: FP64 / FP32 with the default chains; kind 2..4: FP64 with 4, 16, 32 chains
+    // (a sweep over instruction-level parallelism for the peak search).
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (kind) {
+        case 0: fma_probe_kernel<double, 8><<<blocks, threads, 0, s>>>(iters, (double *)d_sink); break;
+        case 1: fma_probe_kernel<float, 16><<<blocks, threads, 0, s>>>(iters, (float *)d_sink); break;
+        case 2: fma_probe_kernel<double, 4><<<blocks, threads, 0, s>>>(iters, (double *)d_sink); break;
+        case 3: fma_probe_kernel<double, 16><<<blocks, threads, 0, s>>>(iters, (double *)d_sink); break;
+        case 4: fma_probe_kernel<double, 32><<<blocks, threads, 0, s>>>(iters, (double *)d_sink); break;
+        default: break;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "cos_peak_probe");
     return COS_OK;
