@@ -47,6 +47,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
     p.add_argument("--n-cfg", type=int, default=0, help="smaller configuration count (profiling runs only)")
+    p.add_argument("--workload", default=WORKLOAD, choices=sorted(I.WORKLOADS),
+                   help="profiling runs only: run this workload's DP instead of the headline")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"], help="profiling runs only")
     return p.parse_args()
 
 
@@ -210,14 +213,19 @@ def native_arm(args):
     from paper_2507_12349_b300 import binding as B
     B.lib()
 
-    w = I.WORKLOADS[WORKLOAD]
+    w = I.WORKLOADS[args.workload]
     n_cfg = args.n_cfg if args.n_cfg > 0 else w.n_cfg
     # weak scaling: every rank takes its own 10^5 configurations of the seeded stream
     cfgs = I.workload_configs(w, n_cfg, first_cfg=rank * n_cfg)
     tabs = B.tables_for(w.model)
     d_order, d_offset, d_site, d_tau = B.configs_to_device(cfgs)
-    n_mat = tabs.info().n_mat
-    stride = n_mat * 64
+    inf = tabs.info()
+    n_mat = inf.n_mat
+    n_max = int(cfgs.order.max())
+    loop_weight = w.model.n_flavors if inf.symmetric else 1
+    sigma = list(inf.sigma)[:n_mat]
+    sigma = sigma if any(sigma) else None
+    stride = n_mat * n_max * n_max
     d_moff = torch.arange(n_cfg, dtype=torch.int64, device="cuda") * stride
     d_M = torch.empty(n_cfg * stride, dtype=torch.float64, device="cuda")
     out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
@@ -232,7 +240,7 @@ def native_arm(args):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        B.cos_connected_sum_matrices(8, d_order, d_moff, n_mat, 1, None, d_M, "fp64", out)
+        B.cos_connected_sum_matrices(n_max, d_order, d_moff, n_mat, loop_weight, sigma, d_M, args.precision, out)
         ev1.record(stream)
         dp_times.append((ev0, ev1))
 
@@ -273,7 +281,7 @@ def native_arm(args):
     peak_source = (f"unit count: {sms} SMs x {FP64_FMA_PER_CLK_SM} FP64 FMA/clk/SM x 2 flop x "
                    f"{clk:.0f} MHz (median SM clock in the timed region)")
     dp_avg = statistics.mean(a.elapsed_time(b) * 1e-3 for a, b in dp_times)
-    flops_launch = algorithmic_flops(B, cfgs.order, n_mat, False)
+    flops_launch = algorithmic_flops(B, cfgs.order, n_mat, sigma is not None)
     achieved = flops_launch / dp_avg
 
     # end to end through the public call with host buffers (pinned), copies inside the region
@@ -288,7 +296,7 @@ def native_arm(args):
     def e2e_step():
         for dst, src in ((e_order, h_order), (e_offset, h_offset), (e_site, h_site), (e_tau, h_tau)):
             dst.copy_(src, non_blocking=True)
-        B.cos_connected_sum_batch(tabs, 8, e_order, e_offset, e_site, e_tau, "fp64", e_out)
+        B.cos_connected_sum_batch(tabs, n_max, e_order, e_offset, e_site, e_tau, args.precision, e_out)
         h_out.copy_(e_out, non_blocking=True)
 
     for _ in range(2):
@@ -308,16 +316,18 @@ def native_arm(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": 8, "n_flavors": 4, "n_cfg_per_gpu": n_cfg, "L": 16, "beta": 4.0,
-                   "U": 1.5, "mu": list(w.model.mu), "n_tau": 1024, "precision": "fp64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32 extension / f64 close", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n_max, "n_flavors": w.model.n_flavors, "n_cfg_per_gpu": n_cfg,
+                   "L": w.model.L, "beta": w.model.beta, "U": w.model.U, "mu": list(w.model.mu),
+                   "alpha": list(w.model.alpha), "n_tau": w.model.n_tau, "precision": args.precision,
                    "full_size": n_cfg == w.n_cfg,
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"configs sharded x{world}"},
         "roofline": {"bound": "alu", "pipe": "fp64 fma", "achieved": achieved / 1e12,
                      "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                      "peak_source": peak_source, "probe_tflops": probe / 1e12,
                      "peak_nominal": NOMINAL_FP64_TFLOPS, "frac_of_nominal": achieved / 1e12 / NOMINAL_FP64_TFLOPS,
-                     "kernel": "dp_forward_kernel<double>", "flops_per_launch": flops_launch,
+                     "kernel": "dp_forward_kernel<%s>" % ("double" if args.precision == "fp64" else "float"),
+                     "flops_per_launch": flops_launch,
                      "launch_ms": dp_avg * 1e3, "traffic": None},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -30,7 +30,7 @@
 namespace cosdp {
 
 template <typename T>
-__global__ void __launch_bounds__(512) dp_forward_kernel(const __grid_constant__ DpArgs a) {
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) dp_forward_kernel(const __grid_constant__ DpArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_batch;
     const int lane = threadIdx.x & 31;
