@@ -41,13 +41,46 @@ struct Prec<float> {
     static __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
 };
 
+// Extension targets of one mask, computed once per mask with one lane per target and read
+// back with shuffles by every row of the mask.  Lane q (q < popc(J)) holds the q-th
+// extension mu -> mu + e_j:
+//   off1 : block offset of mask mu + e_j in the next layer
+//   meta : ai1 (bits 0-3, slot of endpoint j inside a row of that block), nA1 (4-7, row
+//          length), untouched (8, mu_j = 0), j (12-15), H1 (16-27, heads of mu + e_j)
+//   off2, h2 : block offset and heads of mu + 2 e_j (shift targets, mu_j = 0)
+struct TgtInfo {
+    uint32_t off1, meta, off2, h2;
+};
+
+__device__ __forceinline__ TgtInfo mask_targets(uint32_t A, uint32_t B, uint32_t J, uint32_t code,
+                                                const uint32_t *__restrict__ rank3, bool shifts, int lane) {
+    TgtInfo ti = {0u, 0u, 0u, 0u};
+    if (lane < __popc(J)) {
+        const int j = __fns(J, 0, lane + 1);
+        const uint32_t bj = 1u << j;
+        const bool untouched = !(A & bj);
+        const uint32_t A1 = A | bj;
+        const uint32_t B1 = untouched ? B : (B | bj);
+        const uint32_t nA1 = (uint32_t)__popc(A1);
+        const uint32_t ai1 = (uint32_t)__popc(A1 & (bj - 1u));
+        ti.off1 = __ldg(rank3 + code + c_p3[j]);
+        ti.meta = ai1 | (nA1 << 4) | ((untouched ? 1u : 0u) << 8) | ((uint32_t)j << 12) |
+                  (head_set(B1, A1 & ~B1) << 16);
+        if (shifts && untouched) {
+            const uint32_t B2 = B | bj;
+            ti.off2 = __ldg(rank3 + code + 2u * c_p3[j]);
+            ti.h2 = head_set(B2, A1 & ~B2);
+        }
+    }
+    return ti;
+}
+
 // One row (mu, h): load its NV endpoint states, accumulate the close, push every extension.
 template <typename T, int NV>
 __device__ __forceinline__ void do_row(const T *__restrict__ src, T *__restrict__ dst1, T *__restrict__ dst2,
-                                       const T *__restrict__ Ms, const double *__restrict__ Md,
-                                       const uint32_t *__restrict__ rank3, uint32_t Vrow, uint32_t A, uint32_t B,
-                                       uint32_t J, uint32_t code, uint32_t off, int h, int hidx, int nA, int n,
-                                       bool needclose, bool shifts, T negsig, int lane, double &csum) {
+                                       const T *__restrict__ Ms, const double *__restrict__ Md, const TgtInfo &ti,
+                                       int nJ, uint32_t Vrow, uint32_t A, uint32_t off, int h, int hidx, int nA,
+                                       int n, bool needclose, bool shifts, T negsig, int lane, double &csum) {
     T o[NV];
     int vs[NV];
     const T *row = src + (size_t)(off + (uint32_t)(hidx * nA)) * kLanes + lane;
@@ -64,30 +97,26 @@ __device__ __forceinline__ void do_row(const T *__restrict__ src, T *__restrict_
         for (int t = 0; t < NV; ++t) csum = fma((double)o[t], Md[vs[t] + h * kLanes], csum);
     }
     const uint32_t hlow = (1u << h) - 1u;
-    for (uint32_t jj = J; jj; jj &= jj - 1u) {
-        const int j = __ffs(jj) - 1;
+    for (int q = 0; q < nJ; ++q) {
+        const uint32_t off1 = __shfl_sync(0xFFFFFFFFu, ti.off1, q);
+        const uint32_t meta = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
+        const int j = (int)((meta >> 12) & 15u);
         T d = T(0);
 #pragma unroll
         for (int t = 0; t < NV; ++t) d = Prec<T>::fma_(o[t], Ms[vs[t] + j * kLanes], d);
-        const uint32_t bj = 1u << j;
-        const bool untouched = !(A & bj);
-        const uint32_t A1 = A | bj;
-        const uint32_t B1 = untouched ? B : (B | bj);
-        const int nA1 = __popc(A1);
-        const int ai1 = __popc(A1 & (bj - 1u));
-        const int hi1 = __popc(head_set(B1, A1 & ~B1) & hlow);
-        const uint32_t off1 = __ldg(rank3 + code + c_p3[j]);
-        T *tp = dst1 + (size_t)(off1 + (uint32_t)(hi1 * nA1 + ai1)) * kLanes + lane;
-        if (untouched) {
+        const uint32_t ai1 = meta & 15u, nA1 = (meta >> 4) & 15u;
+        const uint32_t hi1 = (uint32_t)__popc((meta >> 16) & hlow);
+        T *tp = dst1 + (size_t)(off1 + hi1 * nA1 + ai1) * kLanes + lane;
+        if (meta & 256u) {
             // mu_j = 0 -> 1: the only writer of this slot.
             *tp = d;
             if (shifts) {
                 // mu_j = 0 -> 2 through a shift point: first (plain) writer of the slot; the
                 // extension from mu+e_j adds to it one layer later.
-                const uint32_t B2 = B | bj;
-                const int hi2 = __popc(head_set(B2, A1 & ~B2) & hlow);
-                const uint32_t off2 = __ldg(rank3 + code + 2u * c_p3[j]);
-                dst2[(size_t)(off2 + (uint32_t)(hi2 * nA1 + ai1)) * kLanes + lane] = negsig * d;
+                const uint32_t off2 = __shfl_sync(0xFFFFFFFFu, ti.off2, q);
+                const uint32_t h2 = __shfl_sync(0xFFFFFFFFu, ti.h2, q);
+                const uint32_t hi2 = (uint32_t)__popc(h2 & hlow);
+                dst2[(size_t)(off2 + hi2 * nA1 + ai1) * kLanes + lane] = negsig * d;
             }
         } else if (shifts && j != 0) {
             *tp += d;
@@ -101,13 +130,13 @@ __device__ __forceinline__ void do_row(const T *__restrict__ src, T *__restrict_
 
 template <typename T>
 __device__ __forceinline__ void row_dispatch(int nv, const T *src, T *dst1, T *dst2, const T *Ms, const double *Md,
-                                             const uint32_t *rank3, uint32_t Vrow, uint32_t A, uint32_t B, uint32_t J,
-                                             uint32_t code, uint32_t off, int h, int hidx, int nA, int n,
-                                             bool needclose, bool shifts, T negsig, int lane, double &csum) {
-#define COS_ROW(K)                                                                                          \
-    case K:                                                                                                 \
-        do_row<T, K>(src, dst1, dst2, Ms, Md, rank3, Vrow, A, B, J, code, off, h, hidx, nA, n, needclose,   \
-                     shifts, negsig, lane, csum);                                                           \
+                                             const TgtInfo &ti, int nJ, uint32_t Vrow, uint32_t A, uint32_t off,
+                                             int h, int hidx, int nA, int n, bool needclose, bool shifts, T negsig,
+                                             int lane, double &csum) {
+#define COS_ROW(K)                                                                                            \
+    case K:                                                                                                   \
+        do_row<T, K>(src, dst1, dst2, Ms, Md, ti, nJ, Vrow, A, off, h, hidx, nA, n, needclose, shifts, negsig, \
+                     lane, csum);                                                                             \
         break;
     switch (nv) {
         COS_ROW(1)
@@ -145,12 +174,14 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
     const int nA = __popc(A);
     const bool needclose = (ones != 0u) || (B == full);
     double csum = 0.0;
+    const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, shifts, lane);
+    const int nJ = __popc(J);
     for (uint32_t hh = H; hh; hh &= hh - 1u) {
         const int h = __ffs(hh) - 1;
         const int hidx = __popc(H & ((1u << h) - 1u));
         const uint32_t Vrow = row_vmask(A, ones, h);
-        row_dispatch<T>(__popc(Vrow), src, dst1, dst2, Ms, Md, tab.rank3, Vrow, A, B, J, code, off, h, hidx, nA, n,
-                        needclose, shifts, negsig, lane, csum);
+        row_dispatch<T>(__popc(Vrow), src, dst1, dst2, Ms, Md, ti, nJ, Vrow, A, off, h, hidx, nA, n, needclose,
+                        shifts, negsig, lane, csum);
     }
     if (!needclose) return;  // no half-visited vertex and not full: disconnected, dropped
     // Flavor sum of the loop-closing weight over the lanes of this configuration.
