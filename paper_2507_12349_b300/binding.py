@@ -304,3 +304,74 @@ def measure_peak(kind: int = 0, iters: int = 4096, reps: int = 3, sweep: bool = 
             if rate > best:
                 best, best_shape = rate, {"chains": chains, "threads": threads, "ctas_per_sm": per_sm}
     return (best, best_shape) if sweep else best
+
+
+class Plan:
+    """A batch frozen into a CUDA graph (cos_plan_*); keep the tensors it references alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def launch(self, stream=None):
+        _check(lib().cos_plan_launch(self.handle, _stream(stream)), "cos_plan_launch")
+
+    def status(self, stream=None):
+        _check(lib().cos_plan_status(self.handle, _stream(stream)), "cos_plan_status")
+
+    def grid(self) -> int:
+        g = ctypes.c_int()
+        _check(lib().cos_plan_grid(self.handle, ctypes.byref(g)), "cos_plan_grid")
+        return g.value
+
+    def close(self):
+        if self.handle:
+            lib().cos_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cos_plan_create_batch(tables: Tables, n_max: int, order, offset, site, tau, precision: str, out, abs_mass=None,
+                          stream=None) -> Plan:
+    h = ctypes.c_void_p()
+    _check(lib().cos_plan_create_batch(tables.handle, int(order.numel()), int(n_max), _ptr(order, "i32"),
+                                       _ptr(offset, "i64"), _ptr(site, "i32"), _ptr(tau, "f64"),
+                                       PRECISIONS[precision], _ptr(out, "f64"), _ptr(abs_mass, "f64"),
+                                       _stream(stream), ctypes.byref(h)), "cos_plan_create_batch")
+    return Plan(h, (tables, order, offset, site, tau, out, abs_mass))
+
+
+def cos_plan_create_matrices(n_max: int, order, moff, n_mat: int, loop_weight: int, sigma, M, precision: str, out,
+                             abs_mass=None, stream=None) -> Plan:
+    sig = None
+    if sigma is not None:
+        sig = (ctypes.c_double * n_mat)(*[float(s) for s in sigma])
+    h = ctypes.c_void_p()
+    _check(lib().cos_plan_create_matrices(int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(moff, "i64"),
+                                          int(n_mat), int(loop_weight), sig, _ptr(M, "f64"), PRECISIONS[precision],
+                                          _ptr(out, "f64"), _ptr(abs_mass, "f64"), _stream(stream), ctypes.byref(h)),
+           "cos_plan_create_matrices")
+    return Plan(h, (order, moff, M, out, abs_mass))
+
+
+def cos_set_tuning(n: int, precision: str, n_mat: int, warps: int, ctas_per_sm: int):
+    _check(lib().cos_set_tuning(n, PRECISIONS[precision], n_mat, warps, ctas_per_sm), "cos_set_tuning")
+
+
+def cos_get_tuning(n: int, precision: str, n_mat: int):
+    w, c = ctypes.c_int(), ctypes.c_int()
+    _check(lib().cos_get_tuning(n, PRECISIONS[precision], n_mat, ctypes.byref(w), ctypes.byref(c)), "cos_get_tuning")
+    return w.value, c.value
+
+
+def cos_autotune(n: int, n_mat: int, loop_weight: int, shifts: bool, precision: str, n_cfg: int, stream=None):
+    """Times the DP launch shapes for order n and installs the fastest; returns (warps, ctas, ms)."""
+    w, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().cos_autotune(n, n_mat, loop_weight, int(shifts), PRECISIONS[precision], n_cfg, _stream(stream),
+                              ctypes.byref(w), ctypes.byref(c), ctypes.byref(ms)), "cos_autotune")
+    return w.value, c.value, ms.value

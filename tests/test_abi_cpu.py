@@ -93,3 +93,19 @@ def test_structure_counts_large_orders():
     assert B.cos_structure(10).slots == 708588
     inf = B.cos_structure(12)
     assert inf.slots == 8581788 and inf.max_layer_slots == 1262547
+
+
+def test_binding_wraps_every_entry_point():
+    """Every exported call has a same-named Python wrapper (or a method of the object
+    it manages: Tables for table calls, Plan for plan calls)."""
+    methods = {"cos_free_tables": (B.Tables, "close"), "cos_get_tables_info": (B.Tables, "info"),
+               "cos_copy_table": (B.Tables, "table"), "cos_plan_launch": (B.Plan, "launch"),
+               "cos_plan_status": (B.Plan, "status"), "cos_plan_grid": (B.Plan, "grid"),
+               "cos_plan_destroy": (B.Plan, "close"), "cos_status_string": (B, "STATUS"),
+               "cos_last_error": (B, "_check")}
+    for name in B.EXPORTS:
+        if name in methods:
+            owner, attr = methods[name]
+            assert hasattr(owner, attr), name
+        else:
+            assert callable(getattr(B, name, None)), name
