@@ -29,8 +29,11 @@
 
 namespace cosdp {
 
-template <typename T>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) dp_forward_kernel(const __grid_constant__ DpArgs a) {
+// Two register budgets: MAXT = 256 (two CTAs of up to 8 warps, <= 128 registers) and
+// MAXT = 512 (up to 16 warps; <= 128 registers in FP64 with one CTA, <= 64 in FP32 with two).
+template <typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
+    dp_forward_kernel(const __grid_constant__ DpArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_batch;
     const int lane = threadIdx.x & 31;
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) dp_forward_kernel
             const uint32_t first = tab.layer_first[ell];
             const uint32_t cnt = tab.layer_count[ell];
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
-                fwd_mask<T>(tab, first + mi, ell, n, src, dst1, dst2, Ms, Md, lane, ci, nfl, sgn, a.loop_weight, sig,
+                fwd_mask<T>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1, dst2, Ms, Md, lane, ci, nfl, sgn, a.loop_weight, sig,
                             shifts, active, lam, cfg, a.out, a.status);
             __syncthreads();
         }
@@ -198,7 +201,8 @@ static cos_status launch_dp_t(Workspace *ws, const DpLaunch &L, cudaStream_t str
     const size_t msm = (size_t)L.n_max * L.n_max * kLanes;
     size_t smem = ((msm * sizeof(T) + 15) & ~size_t(15));
     if (sizeof(T) != sizeof(double)) smem += msm * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(dp_forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = threads <= 256 ? dp_forward_kernel<T, 256> : dp_forward_kernel<T, 512>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "dp smem attribute");
     DpArgs a;
     memset(&a, 0, sizeof a);
@@ -223,7 +227,7 @@ static cos_status launch_dp_t(Workspace *ws, const DpLaunch &L, cudaStream_t str
     a.status = ws->status;
     e = cudaMemsetAsync(ws->queue, 0, sizeof(int), stream);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
-    dp_forward_kernel<T><<<grid, threads, smem, stream>>>(a);
+    kern<<<grid, threads, smem, stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "dp launch");
     return COS_OK;
@@ -257,7 +261,9 @@ static cos_status launch_dp_raw_t(const RawBuffers &rb, const DpLaunch &L, cudaS
     const size_t msm = (size_t)L.n_max * L.n_max * kLanes;
     size_t smem = ((msm * sizeof(T) + 15) & ~size_t(15));
     if (sizeof(T) != sizeof(double)) smem += msm * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(dp_forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int threads = tu.warps * 32;
+    auto kern = threads <= 256 ? dp_forward_kernel<T, 256> : dp_forward_kernel<T, 512>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "dp smem attribute");
     DpArgs a;
     memset(&a, 0, sizeof a);
@@ -282,7 +288,7 @@ static cos_status launch_dp_raw_t(const RawBuffers &rb, const DpLaunch &L, cudaS
     a.status = rb.status;
     e = cudaMemsetAsync(rb.queue, 0, sizeof(int), stream);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
-    dp_forward_kernel<T><<<rb.grid, tu.warps * 32, smem, stream>>>(a);
+    kern<<<rb.grid, threads, smem, stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "dp launch");
     return COS_OK;
@@ -297,11 +303,13 @@ int dp_max_active_ctas(int precision, int threads, size_t smem) {
     int nb = 0;
     cudaError_t e;
     if (precision == COS_MIXED) {
-        cudaFuncSetAttribute(dp_forward_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dp_forward_kernel<float>, threads, smem);
+        auto k = threads <= 256 ? dp_forward_kernel<float, 256> : dp_forward_kernel<float, 512>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem);
     } else {
-        cudaFuncSetAttribute(dp_forward_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dp_forward_kernel<double>, threads, smem);
+        auto k = threads <= 256 ? dp_forward_kernel<double, 256> : dp_forward_kernel<double, 512>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem);
     }
     return e == cudaSuccess ? nb : 0;
 }

@@ -41,6 +41,35 @@ struct Prec<float> {
     static __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
 };
 
+// Exact FP32 -> FP64 widening by bit manipulation (IEEE-754 binary32 / binary64 layouts: the
+// exponent is rebiased by 1023 - 127 = 896 and the 23-bit fraction moves up by 29 bits).  On
+// B300 the FP64 conversion instruction occupies the FP64 pipe; this keeps the widening on the
+// integer pipe.  Zeros are widened inline; subnormals, infinities and NaNs take the
+// conversion instruction (rare, and every result is identical to it).
+__device__ __forceinline__ double widen(double x) { return x; }
+__device__ __forceinline__ double widen(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const uint32_t frac = u & 0x7FFFFFu;
+    if (e - 1u < 0xFEu) {
+        const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | (frac >> 3);
+        return __hiloint2double((int)hi, (int)(frac << 29));
+    }
+    if (e == 0u && frac == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return (double)f;
+}
+
+// Warms L2 with the state block of a mask (its |H| x |A| slots of 32 lanes), one cache line
+// per lane and instruction.
+template <typename T>
+__device__ __forceinline__ void prefetch_block(const T *src, uint32_t off, uint32_t nslots, int lane) {
+    for (uint32_t s = lane; s < nslots; s += kLanes) {
+        const char *p = reinterpret_cast<const char *>(src + (size_t)(off + s) * kLanes);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+        if (sizeof(T) == 8) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + 128));
+    }
+}
+
 // Extension targets of one mask, computed once per mask with one lane per target and read
 // back with shuffles by every row of the mask.  Lane q (q < popc(J)) holds the q-th
 // extension mu -> mu + e_j:
@@ -94,7 +123,7 @@ __device__ __forceinline__ void do_row(const T *__restrict__ src, T *__restrict_
     }
     if (needclose) {
 #pragma unroll
-        for (int t = 0; t < NV; ++t) csum = fma((double)o[t], Md[vs[t] + h * kLanes], csum);
+        for (int t = 0; t < NV; ++t) csum = fma(widen(o[t]), Md[vs[t] + h * kLanes], csum);
     }
     const uint32_t hlow = (1u << h) - 1u;
     for (int q = 0; q < nJ; ++q) {
@@ -160,7 +189,8 @@ __device__ __forceinline__ void row_dispatch(int nv, const T *src, T *dst1, T *d
 // One interaction mask of the forward sweep: every row, the flavor sum of the close, and
 // the seed of the next loop (or the sink).  `out` may be null (adjoint recomputation).
 template <typename T>
-__device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_index, int ell, int n, const T *src,
+__device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
+                                         int n, const T *src,
                                          T *dst1, T *dst2, const T *Ms, const double *Md, int lane, int ci,
                                          int nfl, double sgn, double loop_weight, double sig, bool shifts, bool active,
                                          int lam, int cfg, double *out, int *status) {
@@ -173,6 +203,12 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
     const uint32_t J = full & ~B;
     const int nA = __popc(A);
     const bool needclose = (ones != 0u) || (B == full);
+    if (next_index != 0xFFFFFFFFu) {
+        // the next mask of this warp in the layer: start its loads while this one computes
+        const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + next_index));
+        const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
+        prefetch_block(src, nk.z, (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane);
+    }
     double csum = 0.0;
     const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, shifts, lane);
     const int nJ = __popc(J);
