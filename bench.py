@@ -430,7 +430,7 @@ def measure_forms(torch, B, flush_buf):
         t = statistics.mean(ts)
         tabs.close()
         r = {"configs": n_cfg, "configs_per_s": n_cfg / t, "tflops": fl / t / 1e12, "ms": t * 1e3,
-             "launch_shape_n_max": list(B.cos_get_tuning(nmax, prec, n_mat))}
+             "launch_shape_n_max": dict(zip(("warps", "ctas_per_sm", "prefetch"), B.cos_get_tuning(nmax, prec, n_mat)))}
         if graph:
             r["cuda_graph"] = True
         return r, out.cpu().numpy()

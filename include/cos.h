@@ -223,18 +223,21 @@ cos_status cos_plan_grid(const cos_plan *plan, int *grid);   /* persistent CTAs 
 cos_status cos_plan_destroy(cos_plan *plan);
 
 /* Launch shape of the DP kernel per (order n_max of the launch, precision, matrices per
- * configuration): warps per CTA (1..16) and resident CTAs per SM (1..8).  A launch mixing
+ * configuration): warps per CTA (1..16), resident CTAs per SM (1..8) and whether a warp
+ * warms L2 with the states of its next mask while it computes the current one (prefetch).  A launch mixing
  * orders uses the shape of its largest order, which dominates its work (a factor 3-4 per
  * order).  cos_autotune times every shape the occupancy calculator admits on n_cfg
  * synthetic configurations of order n (device buffers allocated for the run), installs the
- * fastest, and appends "n precision n_mat warps ctas ms" to the file named by the
+ * fastest, and appends "n precision n_mat warps ctas ms prefetch" to the file named by the
  * environment variable COS_TUNE_OUT, if set.  At the first launch a process reads the
  * tuning file named by COS_TUNE_FILE (the Python binding points it at the package's
  * tuning_b300.txt unless the caller set it). */
-cos_status cos_set_tuning(int n, cos_precision precision, int n_mat, int warps, int ctas_per_sm);
-cos_status cos_get_tuning(int n, cos_precision precision, int n_mat, int *warps, int *ctas_per_sm);
+cos_status cos_set_tuning(int n, cos_precision precision, int n_mat, int warps, int ctas_per_sm, int prefetch);
+cos_status cos_get_tuning(int n, cos_precision precision, int n_mat, int *warps, int *ctas_per_sm,
+                          int *prefetch /* nullable */);
 cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts, cos_precision precision, int n_cfg,
-                        cos_stream_t stream, int *best_warps, int *best_ctas, double *best_ms);
+                        cos_stream_t stream, int *best_warps, int *best_ctas, int *best_prefetch,
+                        double *best_ms);
 
 /* ------------------------------------------------------------------ status
  * Synchronizes `stream`, returns and clears the device status word of the

@@ -2,7 +2,7 @@
 
 Usage (on the GPU): python -m paper_2507_12349_b300.autotune [--out FILE]
 Runs cos_autotune for every (order, precision, matrices per configuration) that the
-workloads launch with and writes one line per case: "n precision n_mat warps ctas ms".
+workloads launch with and writes one line per case: "n precision n_mat warps ctas ms prefetch".
 The sample size fills the GPU: 32 lanes x 2 CTAs x SMs worth of configurations (one CTA
 per SM at orders 11-12, where one batch already holds ~0.3-0.6 s of FP64 work).
 """
@@ -38,8 +38,8 @@ def main():
     for n, n_mat, wt, shifts, prec in CASES:
         cpb = 32 // n_mat
         n_cfg = cpb * sms * (1 if n >= 11 else 2)
-        w, c, ms = B.cos_autotune(n, n_mat, wt, shifts, prec, n_cfg)
-        line = f"{n} {B.PRECISIONS[prec]} {n_mat} {w} {c} {ms:.4f}"
+        w, c, pf, ms = B.cos_autotune(n, n_mat, wt, shifts, prec, n_cfg)
+        line = f"{n} {B.PRECISIONS[prec]} {n_mat} {w} {c} {ms:.4f} {int(pf)}"
         print(line, f"# {prec} configs={n_cfg}", flush=True)
         lines.append(line)
     with open(args.out, "w") as f:

@@ -101,10 +101,10 @@ def lib(build: bool = True):
         L.cos_plan_status.argtypes = [vp, vp]
         L.cos_plan_grid.argtypes = [vp, ctypes.POINTER(i32)]
         L.cos_plan_destroy.argtypes = [vp]
-        L.cos_set_tuning.argtypes = [i32, i32, i32, i32, i32]
-        L.cos_get_tuning.argtypes = [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.cos_set_tuning.argtypes = [i32, i32, i32, i32, i32, i32]
+        L.cos_get_tuning.argtypes = [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.cos_autotune.argtypes = [i32, i32, i32, i32, i32, i32, vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
-                                   ctypes.POINTER(ctypes.c_double)]
+                                   ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
         for name in EXPORTS:
             f = getattr(L, name)
             if name not in ("cos_status_string", "cos_last_error"):
@@ -359,19 +359,22 @@ def cos_plan_create_matrices(n_max: int, order, moff, n_mat: int, loop_weight: i
     return Plan(h, (order, moff, M, out, abs_mass))
 
 
-def cos_set_tuning(n: int, precision: str, n_mat: int, warps: int, ctas_per_sm: int):
-    _check(lib().cos_set_tuning(n, PRECISIONS[precision], n_mat, warps, ctas_per_sm), "cos_set_tuning")
+def cos_set_tuning(n: int, precision: str, n_mat: int, warps: int, ctas_per_sm: int, prefetch: bool = True):
+    _check(lib().cos_set_tuning(n, PRECISIONS[precision], n_mat, warps, ctas_per_sm, int(prefetch)),
+           "cos_set_tuning")
 
 
 def cos_get_tuning(n: int, precision: str, n_mat: int):
-    w, c = ctypes.c_int(), ctypes.c_int()
-    _check(lib().cos_get_tuning(n, PRECISIONS[precision], n_mat, ctypes.byref(w), ctypes.byref(c)), "cos_get_tuning")
-    return w.value, c.value
+    """(warps per CTA, CTAs per SM, prefetch) of the DP launch for this case."""
+    w, c, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().cos_get_tuning(n, PRECISIONS[precision], n_mat, ctypes.byref(w), ctypes.byref(c), ctypes.byref(p)),
+           "cos_get_tuning")
+    return w.value, c.value, bool(p.value)
 
 
 def cos_autotune(n: int, n_mat: int, loop_weight: int, shifts: bool, precision: str, n_cfg: int, stream=None):
-    """Times the DP launch shapes for order n and installs the fastest; returns (warps, ctas, ms)."""
-    w, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    """Times the DP launch shapes for order n and installs the fastest; returns (warps, ctas, prefetch, ms)."""
+    w, c, p, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _check(lib().cos_autotune(n, n_mat, loop_weight, int(shifts), PRECISIONS[precision], n_cfg, _stream(stream),
-                              ctypes.byref(w), ctypes.byref(c), ctypes.byref(ms)), "cos_autotune")
-    return w.value, c.value, ms.value
+                              ctypes.byref(w), ctypes.byref(c), ctypes.byref(p), ctypes.byref(ms)), "cos_autotune")
+    return w.value, c.value, bool(p.value), ms.value

@@ -96,15 +96,16 @@ void load_tune_file_locked() {
     if (!path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    int n, prec, nf, w, c;
-    double ms;
     char line[256];
     while (fgets(line, sizeof line, f)) {
-        if (sscanf(line, "%d %d %d %d %d %lf", &n, &prec, &nf, &w, &c, &ms) >= 5 && n >= 1 && n <= COS_NMAX &&
-            w >= 1 && w <= 16 && c >= 1 && c <= 8) {
+        int n = 0, prec = 0, nf = 0, w = 0, c = 0, pf = 1;
+        double ms = 0.0;
+        const int got = sscanf(line, "%d %d %d %d %d %lf %d", &n, &prec, &nf, &w, &c, &ms, &pf);
+        if (got >= 5 && n >= 1 && n <= COS_NMAX && w >= 1 && w <= 16 && c >= 1 && c <= 8) {
             Tuning t;
             t.warps = w;
             t.ctas_per_sm = c;
+            t.prefetch = got >= 7 ? pf != 0 : true;
             g_tune[tune_key(n, prec, nf)] = t;
         }
     }

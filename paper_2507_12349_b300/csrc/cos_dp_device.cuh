@@ -26,6 +26,7 @@ struct DpArgs {
     size_t slot_elems;          // elements per layer slot (max layer slots * 32)
     int nslots;
     int smem_n;                 // order used for the shared-memory layout stride (n_max)
+    int prefetch;               // warm L2 with the next mask's states (tuned per order)
     double *out;
     int *status;
 };
@@ -108,7 +109,7 @@ __device__ __forceinline__ TgtInfo mask_targets(uint32_t A, uint32_t B, uint32_t
 template <typename T, int NV>
 __device__ __forceinline__ void do_row(const T *__restrict__ src, T *__restrict__ dst1, T *__restrict__ dst2,
                                        const T *__restrict__ Ms, const double *__restrict__ Md, const TgtInfo &ti,
-                                       int nJ, uint32_t Vrow, uint32_t A, uint32_t off, int h, int hidx, int nA,
+                                       int nJ, uint32_t J, uint32_t Vrow, uint32_t A, uint32_t off, int h, int hidx, int nA,
                                        int n, bool needclose, bool shifts, T negsig, int lane, double &csum) {
     T o[NV];
     int vs[NV];
@@ -126,10 +127,13 @@ __device__ __forceinline__ void do_row(const T *__restrict__ src, T *__restrict_
         for (int t = 0; t < NV; ++t) csum = fma(widen(o[t]), Md[vs[t] + h * kLanes], csum);
     }
     const uint32_t hlow = (1u << h) - 1u;
+    uint32_t jj = J;
     for (int q = 0; q < nJ; ++q) {
+        // j from the mask bits (no wait on the shuffle before the dot product starts)
+        const int j = __ffs(jj) - 1;
+        jj &= jj - 1u;
         const uint32_t off1 = __shfl_sync(0xFFFFFFFFu, ti.off1, q);
         const uint32_t meta = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
-        const int j = (int)((meta >> 12) & 15u);
         T d = T(0);
 #pragma unroll
         for (int t = 0; t < NV; ++t) d = Prec<T>::fma_(o[t], Ms[vs[t] + j * kLanes], d);
@@ -159,12 +163,13 @@ __device__ __forceinline__ void do_row(const T *__restrict__ src, T *__restrict_
 
 template <typename T>
 __device__ __forceinline__ void row_dispatch(int nv, const T *src, T *dst1, T *dst2, const T *Ms, const double *Md,
-                                             const TgtInfo &ti, int nJ, uint32_t Vrow, uint32_t A, uint32_t off,
+                                             const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow, uint32_t A,
+                                             uint32_t off,
                                              int h, int hidx, int nA, int n, bool needclose, bool shifts, T negsig,
                                              int lane, double &csum) {
 #define COS_ROW(K)                                                                                            \
     case K:                                                                                                   \
-        do_row<T, K>(src, dst1, dst2, Ms, Md, ti, nJ, Vrow, A, off, h, hidx, nA, n, needclose, shifts, negsig, \
+        do_row<T, K>(src, dst1, dst2, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, shifts, negsig, \
                      lane, csum);                                                                             \
         break;
     switch (nv) {
@@ -193,7 +198,7 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
                                          int n, const T *src,
                                          T *dst1, T *dst2, const T *Ms, const double *Md, int lane, int ci,
                                          int nfl, double sgn, double loop_weight, double sig, bool shifts, bool active,
-                                         int lam, int cfg, double *out, int *status) {
+                                         int lam, int cfg, double *out, int *status, bool prefetch) {
     const uint32_t full = (1u << n) - 1u;
     const T negsig = (T)(sgn * sig);
     const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + mask_index));
@@ -203,7 +208,7 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
     const uint32_t J = full & ~B;
     const int nA = __popc(A);
     const bool needclose = (ones != 0u) || (B == full);
-    if (next_index != 0xFFFFFFFFu) {
+    if (prefetch && next_index != 0xFFFFFFFFu) {
         // the next mask of this warp in the layer: start its loads while this one computes
         const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + next_index));
         const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
@@ -216,7 +221,7 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
         const int h = __ffs(hh) - 1;
         const int hidx = __popc(H & ((1u << h) - 1u));
         const uint32_t Vrow = row_vmask(A, ones, h);
-        row_dispatch<T>(__popc(Vrow), src, dst1, dst2, Ms, Md, ti, nJ, Vrow, A, off, h, hidx, nA, n, needclose,
+        row_dispatch<T>(__popc(Vrow), src, dst1, dst2, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose,
                         shifts, negsig, lane, csum);
     }
     if (!needclose) return;  // no half-visited vertex and not full: disconnected, dropped

@@ -216,7 +216,8 @@ extern "C" cos_status cos_plan_destroy(cos_plan *p) {
     return COS_OK;
 }
 
-extern "C" cos_status cos_set_tuning(int n, cos_precision precision, int n_mat, int warps, int ctas_per_sm) {
+extern "C" cos_status cos_set_tuning(int n, cos_precision precision, int n_mat, int warps, int ctas_per_sm,
+                                     int prefetch) {
     if (n < 1 || n > COS_NMAX || n_mat < 1 || n_mat > COS_MAX_FLAVORS || warps < 1 || warps > 16 ||
         ctas_per_sm < 1 || ctas_per_sm > 8 || (precision != COS_FP64 && precision != COS_MIXED)) {
         set_error("cos_set_tuning: out of range");
@@ -225,11 +226,13 @@ extern "C" cos_status cos_set_tuning(int n, cos_precision precision, int n_mat, 
     Tuning t;
     t.warps = warps;
     t.ctas_per_sm = ctas_per_sm;
+    t.prefetch = prefetch != 0;
     set_tuning(n, precision, n_mat, t);
     return COS_OK;
 }
 
-extern "C" cos_status cos_get_tuning(int n, cos_precision precision, int n_mat, int *warps, int *ctas_per_sm) {
+extern "C" cos_status cos_get_tuning(int n, cos_precision precision, int n_mat, int *warps, int *ctas_per_sm,
+                                     int *prefetch) {
     if (n < 1 || n > COS_NMAX || !warps || !ctas_per_sm) {
         set_error("cos_get_tuning: bad argument");
         return COS_ERR_ARG;
@@ -237,12 +240,13 @@ extern "C" cos_status cos_get_tuning(int n, cos_precision precision, int n_mat, 
     const Tuning t = get_tuning(n, precision, n_mat);
     *warps = t.warps;
     *ctas_per_sm = t.ctas_per_sm;
+    if (prefetch) *prefetch = t.prefetch ? 1 : 0;
     return COS_OK;
 }
 
 extern "C" cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts, cos_precision precision,
                                    int n_cfg, cos_stream_t stream, int *best_warps, int *best_ctas,
-                                   double *best_ms) {
+                                   int *best_prefetch, double *best_ms) {
     if (n < 1 || n > COS_NMAX || n_mat < 1 || n_mat > COS_MAX_FLAVORS || loop_weight < 1 || n_cfg < 1 ||
         (precision != COS_FP64 && precision != COS_MIXED)) {
         set_error("cos_autotune: out of range");
@@ -280,50 +284,71 @@ extern "C" cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts
         const size_t msm = (size_t)n * n * kLanes;
         size_t smem = precision == COS_MIXED ? ((msm * sizeof(float) + 15) & ~size_t(15)) + msm * sizeof(double)
                                              : msm * sizeof(double);
+        // candidates: every (warps, ctas) the occupancy calculator admits, with prefetch on;
+        // then the best shape again with prefetch off
+        std::vector<Tuning> cands;
         const int warp_c[] = {2, 4, 8, 12, 16};
         const int cta_c[] = {1, 2, 3, 4};
-        for (int w : warp_c) {
-            for (int c : cta_c) {
-                if (dp_max_active_ctas(precision, w * 32, smem) < c) continue;
-                Tuning cand;
-                cand.warps = w;
-                cand.ctas_per_sm = c;
-                set_tuning(n, precision, n_mat, cand);
-                ws->fixed_grid = 0;
-                st = matrices_body(ws, n_cfg, n, order, moff, n_mat, loop_weight, sig.data(), M, precision, outb,
+        for (int w : warp_c)
+            for (int c : cta_c)
+                if (dp_max_active_ctas(precision, w * 32, smem) >= c) {
+                    Tuning cand;
+                    cand.warps = w;
+                    cand.ctas_per_sm = c;
+                    cand.prefetch = true;
+                    cands.push_back(cand);
+                }
+        auto time_one = [&](const Tuning &cand, double *t_out) -> cos_status {
+            set_tuning(n, precision, n_mat, cand);
+            ws->fixed_grid = 0;
+            cos_status s2 = matrices_body(ws, n_cfg, n, order, moff, n_mat, loop_weight, sig.data(), M, precision,
+                                          outb, nullptr, s);
+            double t = 1e300;
+            for (int rep = 0; rep < 2 && s2 == COS_OK; ++rep) {
+                cudaEventRecord(e0, s);
+                s2 = matrices_body(ws, n_cfg, n, order, moff, n_mat, loop_weight, sig.data(), M, precision, outb,
                                    nullptr, s);
-                if (st != COS_OK) break;
-                double t = 1e300;
-                for (int rep = 0; rep < 2; ++rep) {
-                    cudaEventRecord(e0, s);
-                    st = matrices_body(ws, n_cfg, n, order, moff, n_mat, loop_weight, sig.data(), M, precision,
-                                       outb, nullptr, s);
-                    cudaEventRecord(e1, s);
-                    cudaEventSynchronize(e1);
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    t = std::min(t, (double)ms);
-                    if (st != COS_OK) break;
-                }
-                if (st != COS_OK) break;
-                if (t < best_t) {
-                    best_t = t;
-                    best = cand;
-                }
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                t = std::min(t, (double)ms);
             }
+            *t_out = t;
+            return s2;
+        };
+        for (const Tuning &cand : cands) {
+            double t = 0.0;
+            st = time_one(cand, &t);
             if (st != COS_OK) break;
+            if (t < best_t) {
+                best_t = t;
+                best = cand;
+            }
+        }
+        if (st == COS_OK && best_t < 1e300) {
+            Tuning off = best;
+            off.prefetch = false;
+            double t = 0.0;
+            st = time_one(off, &t);
+            if (st == COS_OK && t < best_t) {
+                best_t = t;
+                best = off;
+            }
         }
     }
     if (st == COS_OK && best_t < 1e300) {
         set_tuning(n, precision, n_mat, best);
         if (const char *path = getenv("COS_TUNE_OUT")) {
             if (FILE *f = fopen(path, "a")) {
-                fprintf(f, "%d %d %d %d %d %.4f\n", n, (int)precision, n_mat, best.warps, best.ctas_per_sm, best_t);
+                fprintf(f, "%d %d %d %d %d %.4f %d\n", n, (int)precision, n_mat, best.warps, best.ctas_per_sm, best_t,
+                        best.prefetch ? 1 : 0);
                 fclose(f);
             }
         }
         if (best_warps) *best_warps = best.warps;
         if (best_ctas) *best_ctas = best.ctas_per_sm;
+        if (best_prefetch) *best_prefetch = best.prefetch ? 1 : 0;
         if (best_ms) *best_ms = best_t;
     } else {
         set_tuning(n, precision, n_mat, before);

@@ -81,11 +81,11 @@ def test_autotune_installs_a_shape_and_keeps_results():
     M = torch.tensor(Ms.ravel(), device="cuda")
     ref = torch.empty(300, dtype=torch.float64, device="cuda")
     B.cos_connected_sum_matrices(n, order, moff, n_mat, 1, None, M, "fp64", ref)
-    w, c, ms = B.cos_autotune(n, n_mat, 1, False, "fp64", 2000)
+    w, c, pf, ms = B.cos_autotune(n, n_mat, 1, False, "fp64", 2000)
     assert 1 <= w <= 16 and 1 <= c <= 8 and ms > 0
-    assert B.cos_get_tuning(n, "fp64", n_mat) == (w, c)
+    assert B.cos_get_tuning(n, "fp64", n_mat) == (w, c, pf)
     out = torch.empty_like(ref)
     B.cos_connected_sum_matrices(n, order, moff, n_mat, 1, None, M, "fp64", out)
     B.cos_sync_status()
     assert torch.equal(out, ref)     # per-lane arithmetic does not depend on the launch shape
-    B.cos_set_tuning(n, "fp64", n_mat, 8, 2)
+    B.cos_set_tuning(n, "fp64", n_mat, 8, 2, True)
