@@ -105,6 +105,35 @@ __device__ __forceinline__ TgtInfo mask_targets(uint32_t A, uint32_t B, uint32_t
     return ti;
 }
 
+// Store of one extension's dot product d into its target slot (and the shift target).
+template <typename T>
+__device__ __forceinline__ void push_target(T *__restrict__ dst1, T *__restrict__ dst2, const TgtInfo &ti, int q,
+                                            int j, T d, uint32_t hlow, bool shifts, T negsig, int lane) {
+    const uint32_t off1 = __shfl_sync(0xFFFFFFFFu, ti.off1, q);
+    const uint32_t meta = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
+    const uint32_t ai1 = meta & 15u, nA1 = (meta >> 4) & 15u;
+    const uint32_t hi1 = (uint32_t)__popc((meta >> 16) & hlow);
+    T *tp = dst1 + (size_t)(off1 + hi1 * nA1 + ai1) * kLanes + lane;
+    if (meta & 256u) {
+        // mu_j = 0 -> 1: the only writer of this slot.
+        *tp = d;
+        if (shifts) {
+            // mu_j = 0 -> 2 through a shift point: first (plain) writer of the slot; the
+            // extension from mu+e_j adds to it one layer later.
+            const uint32_t off2 = __shfl_sync(0xFFFFFFFFu, ti.off2, q);
+            const uint32_t h2 = __shfl_sync(0xFFFFFFFFu, ti.h2, q);
+            const uint32_t hi2 = (uint32_t)__popc(h2 & hlow);
+            dst2[(size_t)(off2 + hi2 * nA1 + ai1) * kLanes + lane] = negsig * d;
+        }
+    } else if (shifts && j != 0) {
+        *tp += d;
+    } else {
+        // mu_j = 1 -> 2 without shift sources (j = 0: the seed of the new head at vertex 0,
+        // issued later by this same thread, adds to it).
+        *tp = d;
+    }
+}
+
 // One row (mu, h): load its NV endpoint states, accumulate the close, push every extension.
 template <typename T, int NV>
 __device__ __forceinline__ void do_row(const T *__restrict__ src, T *__restrict__ dst1, T *__restrict__ dst2,
@@ -128,36 +157,28 @@ __device__ __forceinline__ void do_row(const T *__restrict__ src, T *__restrict_
     }
     const uint32_t hlow = (1u << h) - 1u;
     uint32_t jj = J;
-    for (int q = 0; q < nJ; ++q) {
-        // j from the mask bits (no wait on the shuffle before the dot product starts)
-        const int j = __ffs(jj) - 1;
+    int q = 0;
+    // extensions two at a time: two independent FMA chains in flight per row
+    for (; q + 1 < nJ; q += 2) {
+        const int ja = __ffs(jj) - 1;
         jj &= jj - 1u;
-        const uint32_t off1 = __shfl_sync(0xFFFFFFFFu, ti.off1, q);
-        const uint32_t meta = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
+        const int jb = __ffs(jj) - 1;
+        jj &= jj - 1u;
+        T da = T(0), db = T(0);
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            da = Prec<T>::fma_(o[t], Ms[vs[t] + ja * kLanes], da);
+            db = Prec<T>::fma_(o[t], Ms[vs[t] + jb * kLanes], db);
+        }
+        push_target(dst1, dst2, ti, q, ja, da, hlow, shifts, negsig, lane);
+        push_target(dst1, dst2, ti, q + 1, jb, db, hlow, shifts, negsig, lane);
+    }
+    if (q < nJ) {
+        const int j = __ffs(jj) - 1;
         T d = T(0);
 #pragma unroll
         for (int t = 0; t < NV; ++t) d = Prec<T>::fma_(o[t], Ms[vs[t] + j * kLanes], d);
-        const uint32_t ai1 = meta & 15u, nA1 = (meta >> 4) & 15u;
-        const uint32_t hi1 = (uint32_t)__popc((meta >> 16) & hlow);
-        T *tp = dst1 + (size_t)(off1 + hi1 * nA1 + ai1) * kLanes + lane;
-        if (meta & 256u) {
-            // mu_j = 0 -> 1: the only writer of this slot.
-            *tp = d;
-            if (shifts) {
-                // mu_j = 0 -> 2 through a shift point: first (plain) writer of the slot; the
-                // extension from mu+e_j adds to it one layer later.
-                const uint32_t off2 = __shfl_sync(0xFFFFFFFFu, ti.off2, q);
-                const uint32_t h2 = __shfl_sync(0xFFFFFFFFu, ti.h2, q);
-                const uint32_t hi2 = (uint32_t)__popc(h2 & hlow);
-                dst2[(size_t)(off2 + hi2 * nA1 + ai1) * kLanes + lane] = negsig * d;
-            }
-        } else if (shifts && j != 0) {
-            *tp += d;
-        } else {
-            // mu_j = 1 -> 2 without shift sources (j = 0: the seed of the new head at vertex 0,
-            // issued later by this same thread, adds to it).
-            *tp = d;
-        }
+        push_target(dst1, dst2, ti, q, j, d, hlow, shifts, negsig, lane);
     }
 }
 
