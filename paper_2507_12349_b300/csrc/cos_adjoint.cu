@@ -240,12 +240,7 @@ __global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constan
                     const int ai1 = __popc(A & (bk - 1u));
                     const uint32_t off1 = __ldg(tab.rank3 + code + c_p3[k]);
                     const double own = a1[(size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane];
-                    cbar = own;
-                    if (nfl > 1) {
-                        const int base = ci * nfl;
-                        cbar = 0.0;
-                        for (int g = 0; g < nfl; ++g) cbar += __shfl_sync(0xFFFFFFFFu, own, (base + g) & 31);
-                    }
+                    cbar = flavor_sum(own, nfl, ci);
                     if (SG && ell == 1) gs = fma(sgn * 2.0, own, gs);   // shifted start, weight sgn 2 sigma
                 }
                 const double gamma = sgn * f.loop_weight * cbar;

@@ -60,6 +60,29 @@ __device__ __forceinline__ double widen(float f) {
     return (double)f;
 }
 
+// -x by flipping the sign bit (integer pipe; FP64 instructions are the scarce resource).
+__device__ __forceinline__ double neg(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
+// Sum of v over the nfl lanes of configuration ci (lanes ci*nfl .. ci*nfl+nfl-1), identical
+// bits in every lane of the group: a butterfly for powers of two (log2 nfl additions; each
+// level adds the same two values in every lane), a fixed-order chain otherwise.
+__device__ __forceinline__ double flavor_sum(double v, int nfl, int ci) {
+    if (nfl == 1) return v;
+    if ((nfl & (nfl - 1)) == 0) {
+        for (int o = 1; o < nfl; o <<= 1) {
+            const double w = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+            v = (threadIdx.x & o) ? w + v : v + w;
+        }
+        return v;
+    }
+    const int base = ci * nfl;
+    double t = __shfl_sync(0xFFFFFFFFu, v, base & 31);
+    for (int g = 1; g < nfl; ++g) t += __shfl_sync(0xFFFFFFFFu, v, (base + g) & 31);
+    return t;
+}
+
 // Warms L2 with the state block of a mask (its |H| x |A| slots of 32 lanes), one cache line
 // per lane and instruction.
 template <typename T>
@@ -246,14 +269,10 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
                         shifts, negsig, lane, csum);
     }
     if (!needclose) return;  // no half-visited vertex and not full: disconnected, dropped
-    // Flavor sum of the loop-closing weight over the lanes of this configuration.
-    double tot = csum;
-    if (nfl > 1) {
-        const int base = ci * nfl;
-        tot = 0.0;
-        for (int g = 0; g < nfl; ++g) tot += __shfl_sync(0xFFFFFFFFu, csum, (base + g) & 31);
-    }
-    const double C = sgn * loop_weight * tot;
+    // Flavor sum of the loop-closing weight over the lanes of this configuration, then the
+    // loop factor -w: a sign flip on the integer pipe when w = 1, one multiply otherwise.
+    const double tot = flavor_sum(csum, nfl, ci);
+    const double C = loop_weight == 1.0 ? (sgn < 0.0 ? neg(tot) : tot) : tot * (sgn * loop_weight);
     if (ones) {
         const int k = __ffs(ones) - 1;
         const uint32_t bk = 1u << k;
