@@ -40,11 +40,11 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int nsm = a.smem_n * a.smem_n * kLanes;
+    // Ms: matrices for the extension (state type); Md: FP64 matrices times the loop factor
+    // sgn * w for the close (so the close needs no extra multiply per mask).
     T *Ms = reinterpret_cast<T *>(smem_raw);
-    const double *Md = sizeof(T) == sizeof(double)
-                           ? reinterpret_cast<const double *>(smem_raw)
-                           : reinterpret_cast<const double *>(smem_raw + ((nsm * sizeof(T) + 15) & ~size_t(15)));
-    double *Mdw = const_cast<double *>(Md);
+    double *Mdw = reinterpret_cast<double *>(smem_raw + ((nsm * sizeof(T) + 15) & ~size_t(15)));
+    const double *Md = Mdw;
     T *ring = reinterpret_cast<T *>(a.scratch) + (size_t)blockIdx.x * a.nslots * a.slot_elems;
     const int nfl = a.nf_lanes;
     const int lam = lane % nfl;
@@ -68,11 +68,12 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
         const double *Mc = nullptr;
         if (active) Mc = a.M + (a.moff ? a.moff[cfg] : (int64_t)cfg * a.mstride) + (size_t)lam * n * n;
         // Matrices of the batch -> shared memory [v][j][lane].
+        const double cfac = sgn * a.loop_weight;
         for (int e = warp; e < n * n; e += nwarps) {
             double val = active ? Mc[e] : 0.0;
             if (a.absmode) val = fabs(val);
             Ms[e * kLanes + lane] = (T)val;
-            if (sizeof(T) != sizeof(double)) Mdw[e * kLanes + lane] = val;
+            Mdw[e * kLanes + lane] = cfac * val;
         }
         // Start: the loop through the normal point of vertex 0 (layer 1, mask e_0, slot 0).
         if (warp == 0) ring[(1 % a.nslots) * a.slot_elems + lane] = T(1);
@@ -199,8 +200,7 @@ static cos_status launch_dp_t(Workspace *ws, const DpLaunch &L, cudaStream_t str
     if (st != COS_OK) return st;
     const int threads = tu.warps * 32;
     const size_t msm = (size_t)L.n_max * L.n_max * kLanes;
-    size_t smem = ((msm * sizeof(T) + 15) & ~size_t(15));
-    if (sizeof(T) != sizeof(double)) smem += msm * sizeof(double);
+    const size_t smem = ((msm * sizeof(T) + 15) & ~size_t(15)) + msm * sizeof(double);
     auto kern = threads <= 256 ? dp_forward_kernel<T, 256> : dp_forward_kernel<T, 512>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "dp smem attribute");
@@ -260,8 +260,7 @@ template <typename T>
 static cos_status launch_dp_raw_t(const RawBuffers &rb, const DpLaunch &L, cudaStream_t stream) {
     const Tuning tu = get_tuning(L.n_max, L.precision, L.n_mat);
     const size_t msm = (size_t)L.n_max * L.n_max * kLanes;
-    size_t smem = ((msm * sizeof(T) + 15) & ~size_t(15));
-    if (sizeof(T) != sizeof(double)) smem += msm * sizeof(double);
+    const size_t smem = ((msm * sizeof(T) + 15) & ~size_t(15)) + msm * sizeof(double);
     const int threads = tu.warps * 32;
     auto kern = threads <= 256 ? dp_forward_kernel<T, 256> : dp_forward_kernel<T, 512>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -73,7 +73,9 @@ __device__ __forceinline__ double flavor_sum(double v, int nfl, int ci) {
     if ((nfl & (nfl - 1)) == 0) {
         for (int o = 1; o < nfl; o <<= 1) {
             const double w = __shfl_xor_sync(0xFFFFFFFFu, v, o);
-            v = (threadIdx.x & o) ? w + v : v + w;
+            const bool upper = (threadIdx.x & o) != 0;
+            const double lo = upper ? w : v, hi = upper ? v : w;   // operand selects, one add
+            v = lo + hi;
         }
         return v;
     }
@@ -269,10 +271,9 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
                         shifts, negsig, lane, csum);
     }
     if (!needclose) return;  // no half-visited vertex and not full: disconnected, dropped
-    // Flavor sum of the loop-closing weight over the lanes of this configuration, then the
-    // loop factor -w: a sign flip on the integer pipe when w = 1, one multiply otherwise.
-    const double tot = flavor_sum(csum, nfl, ci);
-    const double C = loop_weight == 1.0 ? (sgn < 0.0 ? neg(tot) : tot) : tot * (sgn * loop_weight);
+    // Flavor sum of the loop-closing weight over the lanes of this configuration; the loop
+    // factor sgn * w is already inside Md (the close's copy of the matrices).
+    const double C = flavor_sum(csum, nfl, ci);
     if (ones) {
         const int k = __ffs(ones) - 1;
         const uint32_t bk = 1u << k;

@@ -282,8 +282,8 @@ extern "C" cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts
         fill_matrices_kernel<<<256, 256, 0, s>>>(M, (size_t)stride * n_cfg, 12345u + n);
         fill_layout_kernel<<<64, 256, 0, s>>>(order, moff, n_cfg, n, stride);
         const size_t msm = (size_t)n * n * kLanes;
-        size_t smem = precision == COS_MIXED ? ((msm * sizeof(float) + 15) & ~size_t(15)) + msm * sizeof(double)
-                                             : msm * sizeof(double);
+        const size_t smem = (precision == COS_MIXED ? ((msm * sizeof(float) + 15) & ~size_t(15))
+                                                    : msm * sizeof(double)) + msm * sizeof(double);
         // candidates: every (warps, ctas) the occupancy calculator admits, with prefetch on;
         // then the best shape again with prefetch off
         std::vector<Tuning> cands;
