@@ -239,7 +239,9 @@ __device__ __forceinline__ void row_dispatch(int nv, const T *src, T *dst1, T *d
 
 // One interaction mask of the forward sweep: every row, the flavor sum of the close, and
 // the seed of the next loop (or the sink).  `out` may be null (adjoint recomputation).
-template <typename T>
+// MD_SCALED: Md already carries the loop factor sgn * w (forward kernel); otherwise the
+// factor is applied to the flavor sum (adjoint recomputation, which shares one matrix copy).
+template <typename T, bool MD_SCALED = true>
 __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
                                          int n, const T *src,
                                          T *dst1, T *dst2, const T *Ms, const double *Md, int lane, int ci,
@@ -273,7 +275,7 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
     if (!needclose) return;  // no half-visited vertex and not full: disconnected, dropped
     // Flavor sum of the loop-closing weight over the lanes of this configuration; the loop
     // factor sgn * w is already inside Md (the close's copy of the matrices).
-    const double C = flavor_sum(csum, nfl, ci);
+    const double C = MD_SCALED ? flavor_sum(csum, nfl, ci) : flavor_sum(csum, nfl, ci) * (sgn * loop_weight);
     if (ones) {
         const int k = __ffs(ones) - 1;
         const uint32_t bk = 1u << k;
