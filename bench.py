@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD, choices=sorted(I.WORKLOADS),
                    help="profiling runs only: run this workload's DP instead of the headline")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"], help="profiling runs only")
+    p.add_argument("--grad", action="store_true",
+                   help="profiling runs only: time the gradient call (adjoint DP) instead of the forward")
     return p.parse_args()
 
 
@@ -229,6 +231,10 @@ def native_arm(args):
     d_moff = torch.arange(n_cfg, dtype=torch.int64, device="cuda") * stride
     d_M = torch.empty(n_cfg * stride, dtype=torch.float64, device="cuda")
     out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
+    if args.grad:
+        d_gout = torch.ones(n_cfg, dtype=torch.float64, device="cuda")
+        d_gM = torch.empty_like(d_M)
+        d_gsig = torch.empty(n_cfg, n_mat, dtype=torch.float64, device="cuda")
     flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2 (126 MB)
     stream = torch.cuda.current_stream()
 
@@ -240,7 +246,12 @@ def native_arm(args):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        B.cos_connected_sum_matrices(n_max, d_order, d_moff, n_mat, loop_weight, sigma, d_M, args.precision, out)
+        if args.grad:
+            B.cos_connected_sum_matrices_grad(n_max, d_order, d_moff, n_mat, loop_weight, sigma, d_M, d_gout, out,
+                                              d_gM, d_gsig)
+        else:
+            B.cos_connected_sum_matrices(n_max, d_order, d_moff, n_mat, loop_weight, sigma, d_M, args.precision,
+                                         out)
         ev1.record(stream)
         dp_times.append((ev0, ev1))
 
@@ -326,7 +337,8 @@ def native_arm(args):
                      "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                      "peak_source": peak_source, "probe_tflops": probe / 1e12,
                      "peak_nominal": NOMINAL_FP64_TFLOPS, "frac_of_nominal": achieved / 1e12 / NOMINAL_FP64_TFLOPS,
-                     "kernel": "dp_forward_kernel<%s>" % ("double" if args.precision == "fp64" else "float"),
+                     "kernel": ("dp_adjoint_kernel<sigma grad>" if args.grad else
+                                "dp_forward_kernel<%s>" % ("double" if args.precision == "fp64" else "float")),
                      "flops_per_launch": flops_launch,
                      "launch_ms": dp_avg * 1e3, "traffic": None},
         "clocks": clocks,
