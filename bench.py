@@ -401,10 +401,11 @@ def measure_adjoint(torch, B, flush_buf, n_cfg):
     gal = torch.empty_like(gmu)
     fwd = lambda: B.cos_connected_sum_batch(tabs, 10, *d, "fp64", out)
     grad = lambda: B.cos_connected_sum_grad(tabs, 10, *d, gout, gmu=gmu, galpha=gal)
-    fwd(); grad()
+    fwd()
+    grad()      # full-size warm-up: sizes every workspace before the timed calls
     B.cos_sync_status()
-    tf = statistics.mean(time_steps(torch, fwd, 2, lambda: flush_l2(flush_buf)))
-    tg = statistics.mean(time_steps(torch, grad, 2, lambda: flush_l2(flush_buf)))
+    tf = statistics.mean(time_steps(torch, fwd, 1, lambda: flush_l2(flush_buf)))
+    tg = statistics.mean(time_steps(torch, grad, 1, lambda: flush_l2(flush_buf)))
     B.cos_sync_status()
     tabs.close()
     return {"configs": n_cfg, "forward_configs_per_s": n_cfg / tf, "grad_configs_per_s": n_cfg / tg,
@@ -451,9 +452,9 @@ def measure_forms(torch, B, flush_buf):
     keep["su4_n8_mixed_vs_fp64_oracle"] = ("su4_mu_broken_n8", keep_n8)
     res["su3_shift_n10_mixed"], keep_n10 = run("su3_shift_mixed_n10", 100_000, "mixed")
     keep["su3_shift_n10_mixed_vs_fp64_oracle"] = ("su3_shift_mixed_n10", keep_n10)
-    res["su3_shift_n10_fp64"], _ = run("su3_shift_mixed_n10", 20_000, "fp64")
+    res["su3_shift_n10_fp64"], _ = run("su3_shift_mixed_n10", 100_000, "fp64", steps=1)
     res["su6_uneven_n4_12_fp64_graph"], _ = run("su6_sym_uneven_n4_12", 200_000, "fp64", steps=1, graph=True)
-    res["su4_n10_adjoint"] = measure_adjoint(torch, B, flush_buf, 5_000)
+    res["su4_n10_adjoint"] = measure_adjoint(torch, B, flush_buf, 50_000)
     # plain FP64 per-configuration form: one configuration per call, no graph
     w = I.WORKLOADS[WORKLOAD]
     cfgs = I.workload_configs(w, 200)
