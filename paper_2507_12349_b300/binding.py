@@ -359,7 +359,7 @@ def cos_plan_create_matrices(n_max: int, order, moff, n_mat: int, loop_weight: i
     return Plan(h, (order, moff, M, out, abs_mass))
 
 
-def cos_set_tuning(n: int, precision: str, n_mat: int, warps: int, ctas_per_sm: int, prefetch: bool = True):
+def cos_set_tuning(n: int, precision: str, n_mat: int, warps: int, ctas_per_sm: int, prefetch: int = 1):
     _check(lib().cos_set_tuning(n, PRECISIONS[precision], n_mat, warps, ctas_per_sm, int(prefetch)),
            "cos_set_tuning")
 
@@ -369,7 +369,7 @@ def cos_get_tuning(n: int, precision: str, n_mat: int):
     w, c, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().cos_get_tuning(n, PRECISIONS[precision], n_mat, ctypes.byref(w), ctypes.byref(c), ctypes.byref(p)),
            "cos_get_tuning")
-    return w.value, c.value, bool(p.value)
+    return w.value, c.value, p.value
 
 
 def cos_autotune(n: int, n_mat: int, loop_weight: int, shifts: bool, precision: str, n_cfg: int, stream=None):
@@ -377,4 +377,4 @@ def cos_autotune(n: int, n_mat: int, loop_weight: int, shifts: bool, precision: 
     w, c, p, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _check(lib().cos_autotune(n, n_mat, loop_weight, int(shifts), PRECISIONS[precision], n_cfg, _stream(stream),
                               ctypes.byref(w), ctypes.byref(c), ctypes.byref(p), ctypes.byref(ms)), "cos_autotune")
-    return w.value, c.value, bool(p.value), ms.value
+    return w.value, c.value, p.value, ms.value

@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constan
             const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
                 fwd_mask<double, false>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1, dst2, Ms, Ms, lane, ci, nfl, sgn, f.loop_weight,
-                                 sig, shifts, active, lam, cfg, f.out, f.status, true);
+                                 sig, shifts, active, lam, cfg, f.out, f.status, 1);
             __syncthreads();
         }
         // reverse sweep

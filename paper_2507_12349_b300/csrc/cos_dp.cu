@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
             const uint32_t cnt = tab.layer_count[ell];
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
                 fwd_mask<T>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1, dst2, Ms, Md, lane, ci, nfl, sgn, a.loop_weight, sig,
-                            shifts, active, lam, cfg, a.out, a.status, a.prefetch != 0);
+                            shifts, active, lam, cfg, a.out, a.status, a.prefetch);
             __syncthreads();
         }
     }
@@ -223,7 +223,7 @@ static cos_status launch_dp_t(Workspace *ws, const DpLaunch &L, cudaStream_t str
     a.slot_elems = slot_elems;
     a.nslots = nslots;
     a.smem_n = L.n_max;
-    a.prefetch = tu.prefetch ? 1 : 0;
+    a.prefetch = tu.prefetch;
     a.out = L.out;
     a.status = ws->status;
     e = cudaMemsetAsync(ws->queue, 0, sizeof(int), stream);
@@ -284,7 +284,7 @@ static cos_status launch_dp_raw_t(const RawBuffers &rb, const DpLaunch &L, cudaS
     a.slot_elems = (size_t)host_order(L.n_max).max_slots * kLanes;
     a.nslots = dp_slots(L);
     a.smem_n = L.n_max;
-    a.prefetch = tu.prefetch ? 1 : 0;
+    a.prefetch = tu.prefetch;
     a.out = L.out;
     a.status = rb.status;
     e = cudaMemsetAsync(rb.queue, 0, sizeof(int), stream);

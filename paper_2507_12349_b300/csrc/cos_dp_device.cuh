@@ -26,7 +26,7 @@ struct DpArgs {
     size_t slot_elems;          // elements per layer slot (max layer slots * 32)
     int nslots;
     int smem_n;                 // order used for the shared-memory layout stride (n_max)
-    int prefetch;               // warm L2 with the next mask's states (tuned per order)
+    int prefetch;               // prefetch the next mask's states: 0 off, 1 into L2, 2 into L1 (tuned)
     double *out;
     int *status;
 };
@@ -85,14 +85,19 @@ __device__ __forceinline__ double flavor_sum(double v, int nfl, int ci) {
     return t;
 }
 
-// Warms L2 with the state block of a mask (its |H| x |A| slots of 32 lanes), one cache line
-// per lane and instruction.
+// Prefetches the state block of a mask (its |H| x |A| slots of 32 lanes), one cache line per
+// lane and instruction: level 1 = into L2, level 2 = into L1 as well.
 template <typename T>
-__device__ __forceinline__ void prefetch_block(const T *src, uint32_t off, uint32_t nslots, int lane) {
+__device__ __forceinline__ void prefetch_block(const T *src, uint32_t off, uint32_t nslots, int lane, int level) {
     for (uint32_t s = lane; s < nslots; s += kLanes) {
         const char *p = reinterpret_cast<const char *>(src + (size_t)(off + s) * kLanes);
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-        if (sizeof(T) == 8) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + 128));
+        if (level >= 2) {
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+            if (sizeof(T) == 8) asm volatile("prefetch.global.L1 [%0];" ::"l"(p + 128));
+        } else {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+            if (sizeof(T) == 8) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + 128));
+        }
     }
 }
 
@@ -246,7 +251,7 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
                                          int n, const T *src,
                                          T *dst1, T *dst2, const T *Ms, const double *Md, int lane, int ci,
                                          int nfl, double sgn, double loop_weight, double sig, bool shifts, bool active,
-                                         int lam, int cfg, double *out, int *status, bool prefetch) {
+                                         int lam, int cfg, double *out, int *status, int prefetch) {
     const uint32_t full = (1u << n) - 1u;
     const T negsig = (T)(sgn * sig);
     const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + mask_index));
@@ -256,11 +261,11 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
     const uint32_t J = full & ~B;
     const int nA = __popc(A);
     const bool needclose = (ones != 0u) || (B == full);
-    if (prefetch && next_index != 0xFFFFFFFFu) {
+    if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
         // the next mask of this warp in the layer: start its loads while this one computes
         const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + next_index));
         const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
-        prefetch_block(src, nk.z, (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane);
+        prefetch_block(src, nk.z, (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane, prefetch);
     }
     double csum = 0.0;
     const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, shifts, lane);

@@ -127,7 +127,7 @@ cos_status ensure(void **ptr, size_t *cap, size_t need, size_t elem, const char 
 struct Tuning {
     int warps = 8;          // warps per CTA
     int ctas_per_sm = 2;    // resident CTAs per SM targeted by the persistent grid
-    bool prefetch = true;   // warm L2 with the next mask's states
+    int prefetch = 1;       // prefetch the next mask's states: 0 off, 1 into L2, 2 into L1
 };
 Tuning get_tuning(int n, int precision, int nf_lanes);
 void set_tuning(int n, int precision, int nf_lanes, Tuning t);

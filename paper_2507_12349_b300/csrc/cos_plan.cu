@@ -226,7 +226,7 @@ extern "C" cos_status cos_set_tuning(int n, cos_precision precision, int n_mat, 
     Tuning t;
     t.warps = warps;
     t.ctas_per_sm = ctas_per_sm;
-    t.prefetch = prefetch != 0;
+    t.prefetch = prefetch < 0 ? 0 : (prefetch > 2 ? 2 : prefetch);
     set_tuning(n, precision, n_mat, t);
     return COS_OK;
 }
@@ -240,7 +240,7 @@ extern "C" cos_status cos_get_tuning(int n, cos_precision precision, int n_mat, 
     const Tuning t = get_tuning(n, precision, n_mat);
     *warps = t.warps;
     *ctas_per_sm = t.ctas_per_sm;
-    if (prefetch) *prefetch = t.prefetch ? 1 : 0;
+    if (prefetch) *prefetch = t.prefetch;
     return COS_OK;
 }
 
@@ -284,8 +284,8 @@ extern "C" cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts
         const size_t msm = (size_t)n * n * kLanes;
         const size_t smem = (precision == COS_MIXED ? ((msm * sizeof(float) + 15) & ~size_t(15))
                                                     : msm * sizeof(double)) + msm * sizeof(double);
-        // candidates: every (warps, ctas) the occupancy calculator admits, with prefetch on;
-        // then the best shape again with prefetch off
+        // candidates: every (warps, ctas) the occupancy calculator admits, with prefetch into L2;
+        // then the best shape again with prefetch off and with prefetch into L1
         std::vector<Tuning> cands;
         const int warp_c[] = {2, 4, 8, 12, 16};
         const int cta_c[] = {1, 2, 3, 4};
@@ -295,7 +295,7 @@ extern "C" cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts
                     Tuning cand;
                     cand.warps = w;
                     cand.ctas_per_sm = c;
-                    cand.prefetch = true;
+                    cand.prefetch = 1;
                     cands.push_back(cand);
                 }
         auto time_one = [&](const Tuning &cand, double *t_out) -> cos_status {
@@ -327,13 +327,17 @@ extern "C" cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts
             }
         }
         if (st == COS_OK && best_t < 1e300) {
-            Tuning off = best;
-            off.prefetch = false;
-            double t = 0.0;
-            st = time_one(off, &t);
-            if (st == COS_OK && t < best_t) {
-                best_t = t;
-                best = off;
+            const Tuning shape = best;
+            for (int pf : {0, 2}) {
+                Tuning alt = shape;
+                alt.prefetch = pf;
+                double t = 0.0;
+                st = time_one(alt, &t);
+                if (st != COS_OK) break;
+                if (t < best_t) {
+                    best_t = t;
+                    best = alt;
+                }
             }
         }
     }
@@ -342,13 +346,13 @@ extern "C" cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts
         if (const char *path = getenv("COS_TUNE_OUT")) {
             if (FILE *f = fopen(path, "a")) {
                 fprintf(f, "%d %d %d %d %d %.4f %d\n", n, (int)precision, n_mat, best.warps, best.ctas_per_sm, best_t,
-                        best.prefetch ? 1 : 0);
+                        best.prefetch);
                 fclose(f);
             }
         }
         if (best_warps) *best_warps = best.warps;
         if (best_ctas) *best_ctas = best.ctas_per_sm;
-        if (best_prefetch) *best_prefetch = best.prefetch ? 1 : 0;
+        if (best_prefetch) *best_prefetch = best.prefetch;
         if (best_ms) *best_ms = best_t;
     } else {
         set_tuning(n, precision, n_mat, before);

@@ -88,4 +88,4 @@ def test_autotune_installs_a_shape_and_keeps_results():
     B.cos_connected_sum_matrices(n, order, moff, n_mat, 1, None, M, "fp64", out)
     B.cos_sync_status()
     assert torch.equal(out, ref)     # per-lane arithmetic does not depend on the launch shape
-    B.cos_set_tuning(n, "fp64", n_mat, 8, 2, True)
+    B.cos_set_tuning(n, "fp64", n_mat, 8, 2, 1)
