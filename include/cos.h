@@ -150,7 +150,7 @@ cos_status cos_connected_sum_matrices(int n_cfg, int n_max, const int32_t *d_ord
  * scratch (planner tables, work queue, DP structure, layer ring) lives in one fixed device
  * array of 128 MiB that every GPU loading the library holds until the process exits.
  *   - Limits: n_max <= 10, and the batch must fit the array (roughly 20 B per configuration
- *     plus one layer ring of 2-3 x max-layer-slots x 32 x 8 B); larger requests return
+ *     plus one layer ring of 2 x max-layer-slots x 32 x 8 B); larger requests return
  *     COS_ERR_ORDER / COS_ERR_ARG with a message, without launching anything.
  *   - The first call on a device sets the array up (device address, DP structure copy,
  *     synchronizing `stream` once); make that first call before any stream capture.

@@ -2,15 +2,16 @@
 // entry M^l[v][j] and to the shift weights sigma_l, then (tables path) by chain rule with
 // respect to mu_l and alpha_l.
 //
-// For each batch the CTA first re-runs the forward sweep of cos_dp.cu, keeping every layer
-// (exact per-layer offsets), then walks the layers backwards.  With Obar = dc/dO:
+// For each batch the CTA first re-runs the forward sweep of cos_dp.cu (extension matrices
+// with the shifted diagonal Ms[j][j] = M[j][j] - sigma, close matrices Mc = sgn w M), keeping
+// every layer at exact per-layer offsets, then walks the layers backwards.  With Obar = dc/dO:
 //   Cbar(full) = gout 2^(n-1);  Cbar(mu) = sum over the configuration's flavor lanes of
-//   Obar(mu + e_k, k, k) when mu has a half-visited vertex; Gamma = sgn w Cbar (close adjoint).
-//   Row (mu, h), D_j = Obar(mu+e_j, h, j) + sgn sigma Obar(mu+2e_j, h, j) [mu_j = 0]:
-//     Obar(mu, h, v) = Gamma M[v][h] + sum_j D_j M[v][j]
-//     dM[v][h] += Gamma O(mu,h,v);  dM[v][j] += D_j O(mu,h,v)
-//     dsigma   += sgn d_j Obar(mu+2e_j, h, j)  (d_j = sum_v O M[v][j], recomputed) and, at the
-//                 start, sgn 2 Obar(2e_0, 0, 0).
+//   Obar(mu + e_k, k, k) when mu has a half-visited vertex (the seed it fed).
+//   Row (mu, h), D_j = Obar(mu + e_j, h, j):
+//     Obar(mu, h, v) = Cbar Mc[v][h] + sum_j D_j Ms[v][j]
+//     dM[v][h] += sgn w Cbar O(mu,h,v);   dM[v][j] += D_j O(mu,h,v)   (dMs/dM = 1)
+//     dsigma   += sgn D_j O(mu,h,j) for every half-visited j >= 1 (the shifted diagonal), and
+//                 sgn 2 Obar(2e_0, 0, 0) for the shifted start.
 // Every adjoint slot read was written earlier in the same sweep (targets of reachable edges
 // are reachable), so the adjoint ring needs no clearing.  dM accumulates in a private
 // shared-memory copy per warp, summed in warp order at the end: no atomics, bitwise
@@ -39,11 +40,11 @@ constexpr int kChunk = 4;
 
 template <int NV, bool SG>
 __device__ __forceinline__ void adj_row(const double *__restrict__ fsrc, double *__restrict__ aout,
-                                        const double *__restrict__ a1, const double *__restrict__ a2,
-                                        const double *__restrict__ Ms, double *__restrict__ gMw,
+                                        const double *__restrict__ a1, const double *__restrict__ Ms,
+                                        const double *__restrict__ Mc, double *__restrict__ gMw,
                                         const uint32_t *__restrict__ rank3, uint32_t Vrow, uint32_t A, uint32_t B,
                                         uint32_t J, uint32_t code, uint32_t off, int h, int hidx, int nA, int n,
-                                        double gamma, bool use_shift, double negsig, double sgn, int lane, double &gs) {
+                                        double cbar, double gamma, double sgn, int lane, double &gs) {
     double o[NV], ob[NV];
     int vt[NV];
     const uint32_t rowoff = off + (uint32_t)(hidx * nA);
@@ -59,19 +60,19 @@ __device__ __forceinline__ void adj_row(const double *__restrict__ fsrc, double 
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
         const int a = vt[t] * nk + lane + h * kLanes;
-        ob[t] = gamma * Ms[a];
+        ob[t] = cbar * Mc[a];
         if (gamma != 0.0) gMw[a] = fma(gamma, o[t], gMw[a]);
     }
     const uint32_t hlow = (1u << h) - 1u;
     uint32_t jr = J;
     while (jr) {
-        double D[kChunk], S[kChunk];
+        double D[kChunk], Oj[kChunk];
         int js[kChunk];
 #pragma unroll
         for (int q = 0; q < kChunk; ++q) {
             js[q] = -1;
             D[q] = 0.0;
-            S[q] = 0.0;
+            Oj[q] = 0.0;
             if (jr) {
                 const int j = __ffs(jr) - 1;
                 jr &= jr - 1u;
@@ -85,29 +86,23 @@ __device__ __forceinline__ void adj_row(const double *__restrict__ fsrc, double 
                 const int hi1 = __popc(head_set(B1, A1 & ~B1) & hlow);
                 const uint32_t off1 = __ldg(rank3 + code + c_p3[j]);
                 D[q] = a1[(size_t)(off1 + (uint32_t)(hi1 * nA1 + ai1)) * kLanes + lane];
-                if (untouched && use_shift) {
-                    const uint32_t B2 = B | bj;
-                    const int hi2 = __popc(head_set(B2, A1 & ~B2) & hlow);
-                    const uint32_t off2 = __ldg(rank3 + code + 2u * c_p3[j]);
-                    S[q] = a2[(size_t)(off2 + (uint32_t)(hi2 * nA1 + ai1)) * kLanes + lane];
-                }
+                // state at endpoint j (half-visited j >= 1 is in Vrow): weight of the shifted diagonal
+                if (SG && !untouched && j != 0)
+                    Oj[q] = fsrc[(size_t)(rowoff + (uint32_t)__popc(A & (bj - 1u))) * kLanes + lane];
             }
         }
 #pragma unroll
         for (int q = 0; q < kChunk; ++q) {
             if (js[q] >= 0) {
                 const int jo = js[q] * kLanes + lane;
-                const double Dq = fma(negsig, S[q], D[q]);
-                double d = 0.0;
+                const double Dq = D[q];
 #pragma unroll
                 for (int t = 0; t < NV; ++t) {
                     const int a = vt[t] * nk + jo;
-                    const double m = Ms[a];
-                    ob[t] = fma(Dq, m, ob[t]);
+                    ob[t] = fma(Dq, Ms[a], ob[t]);
                     gMw[a] = fma(Dq, o[t], gMw[a]);
-                    if (SG) d = fma(o[t], m, d);
                 }
-                if (SG) gs = fma(sgn * d, S[q], gs);
+                if (SG) gs = fma(sgn * Dq, Oj[q], gs);
             }
         }
     }
@@ -118,15 +113,14 @@ __device__ __forceinline__ void adj_row(const double *__restrict__ fsrc, double 
 
 template <bool SG>
 __device__ __forceinline__ void adj_row_dispatch(int nv, const double *fsrc, double *aout, const double *a1,
-                                                 const double *a2, const double *Ms, double *gMw,
+                                                 const double *Ms, const double *Mc, double *gMw,
                                                  const uint32_t *rank3, uint32_t Vrow, uint32_t A, uint32_t B,
                                                  uint32_t J, uint32_t code, uint32_t off, int h, int hidx, int nA,
-                                                 int n, double gamma, bool use_shift, double negsig, double sgn,
-                                                 int lane, double &gs) {
+                                                 int n, double cbar, double gamma, double sgn, int lane, double &gs) {
 #define COS_AROW(K)                                                                                              \
     case K:                                                                                                      \
-        adj_row<K, SG>(fsrc, aout, a1, a2, Ms, gMw, rank3, Vrow, A, B, J, code, off, h, hidx, nA, n, gamma,       \
-                       use_shift, negsig, sgn, lane, gs);                                                         \
+        adj_row<K, SG>(fsrc, aout, a1, Ms, Mc, gMw, rank3, Vrow, A, B, J, code, off, h, hidx, nA, n, cbar, gamma, \
+                       sgn, lane, gs);                                                                            \
         break;
     switch (nv) {
         COS_AROW(1)
@@ -158,9 +152,10 @@ __global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constan
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int nsm = f.smem_n * f.smem_n * kLanes;
-    double *Ms = smem_d;
-    double *gMw = smem_d + (size_t)nsm * (1 + warp);
-    double *store = reinterpret_cast<double *>(f.scratch) + (size_t)blockIdx.x * (a.store_elems + 3 * a.adj_slot_elems);
+    double *Ms = smem_d;                               // extension matrices, shifted diagonal
+    double *Mc = smem_d + nsm;                         // close matrices times sgn w
+    double *gMw = smem_d + (size_t)nsm * (2 + warp);   // this warp's dM accumulators
+    double *store = reinterpret_cast<double *>(f.scratch) + (size_t)blockIdx.x * (a.store_elems + 2 * a.adj_slot_elems);
     double *adj = store + a.store_elems;
     const int nfl = f.nf_lanes;
     const int lam = lane % nfl;
@@ -168,8 +163,7 @@ __global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constan
     const double sgn = -1.0;
     const double sig = f.sigma[lam];
     const bool shifts = f.shifts != 0;
-    const bool use_shift = shifts || SG;
-    const double negsig = sgn * sig;
+    const double cfac = sgn * f.loop_weight;
     const int nbatch = *f.n_batches;
 
     for (;;) {
@@ -183,13 +177,14 @@ __global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constan
         const OrderTab &tab = f.tabs[n];
         const bool active = (ci < bd.z) && (ci * nfl + nfl <= kLanes);
         const int cfg = active ? f.batch_list[bd.y + ci] : -1;
-        const double *Mc = nullptr;
-        int64_t mbase = 0;
-        if (active) {
-            mbase = f.moff ? f.moff[cfg] : (int64_t)cfg * f.mstride;
-            Mc = f.M + mbase + (size_t)lam * n * n;
+        const double *Mg = nullptr;
+        if (active) Mg = f.M + (f.moff ? f.moff[cfg] : (int64_t)cfg * f.mstride) + (size_t)lam * n * n;
+        for (int e = warp; e < n * n; e += nwarps) {
+            const double val = active ? Mg[e] : 0.0;
+            const int v = e / n, j = e % n;
+            Ms[e * kLanes + lane] = (v == j && j != 0 && shifts) ? val + sgn * sig : val;
+            Mc[e * kLanes + lane] = cfac * val;
         }
-        for (int e = warp; e < n * n; e += nwarps) Ms[e * kLanes + lane] = active ? Mc[e] : 0.0;
         for (int e = 0; e < n * n; ++e) gMw[e * kLanes + lane] = 0.0;
         if (threadIdx.x == 0) {
             uint32_t run = 0;
@@ -205,11 +200,10 @@ __global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constan
         for (int ell = 1; ell <= 2 * n; ++ell) {
             const double *src = store + (size_t)s_base[ell] * kLanes;
             double *dst1 = store + (size_t)s_base[ell + 1] * kLanes;
-            double *dst2 = store + (size_t)s_base[ell + 2] * kLanes;
             const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
-                fwd_mask<double, false>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1, dst2, Ms, Ms, lane, ci, nfl, sgn, f.loop_weight,
-                                 sig, shifts, active, lam, cfg, f.out, f.status, 1);
+                fwd_mask<double>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src,
+                                 dst1, Ms, Mc, lane, ci, nfl, sgn, sig, shifts, active, lam, cfg, f.out, f.status, 1);
             __syncthreads();
         }
         // reverse sweep
@@ -218,9 +212,8 @@ __global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constan
         double gs = 0.0;
         for (int ell = 2 * n; ell >= 1; --ell) {
             const double *fsrc = store + (size_t)s_base[ell] * kLanes;
-            double *aout = adj + (size_t)(ell % 3) * a.adj_slot_elems;
-            const double *a1 = adj + (size_t)((ell + 1) % 3) * a.adj_slot_elems;
-            const double *a2 = adj + (size_t)((ell + 2) % 3) * a.adj_slot_elems;
+            double *aout = adj + (size_t)(ell & 1) * a.adj_slot_elems;
+            const double *a1 = adj + (size_t)((ell + 1) & 1) * a.adj_slot_elems;
             const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
             for (uint32_t mi = warp; mi < cnt; mi += nwarps) {
                 const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + first + mi));
@@ -243,13 +236,13 @@ __global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constan
                     cbar = flavor_sum(own, nfl, ci);
                     if (SG && ell == 1) gs = fma(sgn * 2.0, own, gs);   // shifted start, weight sgn 2 sigma
                 }
-                const double gamma = sgn * f.loop_weight * cbar;
+                const double gamma = cfac * cbar;
                 for (uint32_t hh = H; hh; hh &= hh - 1u) {
                     const int h = __ffs(hh) - 1;
                     const int hidx = __popc(H & ((1u << h) - 1u));
                     const uint32_t Vrow = row_vmask(A, ones, h);
-                    adj_row_dispatch<SG>(__popc(Vrow), fsrc, aout, a1, a2, Ms, gMw, tab.rank3, Vrow, A, B, J, code,
-                                         off, h, hidx, nA, n, gamma, use_shift, negsig, sgn, lane, gs);
+                    adj_row_dispatch<SG>(__popc(Vrow), fsrc, aout, a1, Ms, Mc, gMw, tab.rank3, Vrow, A, B, J, code,
+                                         off, h, hidx, nA, n, cbar, gamma, sgn, lane, gs);
                 }
             }
             __syncthreads();
@@ -257,7 +250,7 @@ __global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constan
         // dM: sum of the per-warp copies in warp order; dsigma: sum over warps
         for (int e = warp; e < n * n; e += nwarps) {
             double s = 0.0;
-            for (int w = 0; w < nwarps; ++w) s += smem_d[(size_t)nsm * (1 + w) + e * kLanes + lane];
+            for (int w = 0; w < nwarps; ++w) s += smem_d[(size_t)nsm * (2 + w) + e * kLanes + lane];
             if (active && a.gM) {
                 const int64_t gb = a.gmoff ? a.gmoff[cfg] : (int64_t)cfg * a.gmstride;
                 a.gM[gb + (int64_t)lam * n * n + e] = s;
@@ -331,7 +324,7 @@ __global__ void chain_kernel(const double *__restrict__ dG, int L, int n_tau, do
     }
 }
 
-// Warps per adjoint CTA: the matrices plus one private dM copy per warp must fit the opt-in
+// Warps per adjoint CTA: two matrix copies plus one private dM copy per warp must fit the opt-in
 // shared memory, less a margin for the kernel's static shared arrays (about 2.2 KB).
 int adjoint_warps(int n_max, int device) {
     int optin = 0;
@@ -339,7 +332,7 @@ int adjoint_warps(int n_max, int device) {
     if (optin <= 0) optin = 227 * 1024;
     const size_t per = (size_t)n_max * n_max * kLanes * sizeof(double);
     const size_t cap = (size_t)optin - 4096;
-    int w = (int)(cap / per) - 1;
+    int w = (int)(cap / per) - 2;
     return std::max(1, std::min(8, w));
 }
 
@@ -356,7 +349,7 @@ cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, 
     for (int l = 0; l <= 2 * L.n_max; ++l) total_slots += ho.layer_slots[l];
     const size_t store_elems = total_slots * kLanes;
     const size_t adj_slot_elems = (size_t)ho.max_slots * kLanes;
-    const size_t per_cta = (store_elems + 3 * adj_slot_elems) * sizeof(double);
+    const size_t per_cta = (store_elems + 2 * adj_slot_elems) * sizeof(double);
     int nsm = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
     const int cpb = kLanes / L.n_mat;
@@ -370,7 +363,7 @@ cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, 
     cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "adjoint scratch");
     if (st != COS_OK) return st;
     const int warps = adjoint_warps(L.n_max, ws->device);
-    const size_t smem = (size_t)(1 + warps) * L.n_max * L.n_max * kLanes * sizeof(double);
+    const size_t smem = (size_t)(2 + warps) * L.n_max * L.n_max * kLanes * sizeof(double);
     const bool sg = gsig != nullptr;
     cudaError_t e = sg ? cudaFuncSetAttribute(dp_adjoint_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                        : cudaFuncSetAttribute(dp_adjoint_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -393,7 +386,7 @@ cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, 
     f.absmode = 0;
     f.scratch = ws->scratch;
     f.slot_elems = adj_slot_elems;
-    f.nslots = 3;
+    f.nslots = 2;
     f.smem_n = L.n_max;
     f.out = L.out;
     f.status = ws->status;

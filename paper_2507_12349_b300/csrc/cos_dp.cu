@@ -11,17 +11,24 @@
 //     global ring of 2 (3 with shift parameters) layer slots laid out [slot][lane].
 //
 // Recurrence (push form, per row = mask mu, head h, lane flavor l, endpoints v in Vrow):
-//   close   csum(mu)            += sum_v O(mu,h,v) M[v][h]                      (Alg. 2 Close)
-//   extend  O(mu+e_j, h, j)     (+)= d_j = sum_v O(mu,h,v) M[v][j], mu_j <= 1     (Alg. 2 Extend)
-//   shift   O(mu+2e_j, h, j)     = -sigma_l d_j,  mu_j = 0                     (Alg. 3 shift head)
-//   after all rows of mu:  C(mu) = -w sum_{lanes of the configuration} csum   (flavor sum)
+//   close   csum(mu)            += sum_v O(mu,h,v) Md[v][h]     Md = sgn w M   (Alg. 2 Close)
+//   extend  O(mu+e_j, h, j)      = d_j = sum_v O(mu,h,v) Ms[v][j], mu_j <= 1    (Alg. 2 Extend)
+//   after all rows of mu:  C(mu) = sum over the lanes of the configuration of csum (flavor sum)
 //            mu has a 1 -> O(mu+e_k, k, k) = C(mu) in every flavor, k = min{i: mu_i = 1}
 //            mu full    -> c = 2^(n-1) C(mu)
 // The factor 2 for entering an untouched vertex (either of its two points) is the same on
 // every path -- each vertex other than 0 is entered from mu_j = 0 exactly once -- so it is
 // pulled out as the global 2^(n-1); the start with a shifted vertex 0 keeps its 2 (-2 sigma).
-// Each target slot receives one plain store before any read-modify-write (see the cases in
-// process_mask), so slots never need clearing between batches.
+//
+// Shift points (Alg. 3: a shift takes the color of its partner's loop and closes at once with
+// -sigma).  Entering an untouched vertex j whose other point is a shift gives the state
+// (mu + 2e_j, h, j) the weight -sigma d_j, where d_j is the very value the same extension
+// stores at (mu + e_j, h, j) -- that slot's only writer.  So the shift contribution is
+// -sigma O(mu+e_j, h, j), taken when the row (mu + e_j, h) extends from endpoint j into the
+// other point of j: the extension matrix carries Ms[j][j] = M[j][j] - sigma for j >= 1 (the
+// close keeps the unshifted diagonal, vertex 0 keeps its start seed).  Every target slot has
+// a single writer, the ring needs two layer slots, and slots never need clearing between
+// batches (each one read in a batch is written earlier in that batch).
 #include <algorithm>
 #include <cstring>
 
@@ -69,10 +76,12 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
         if (active) Mc = a.M + (a.moff ? a.moff[cfg] : (int64_t)cfg * a.mstride) + (size_t)lam * n * n;
         // Matrices of the batch -> shared memory [v][j][lane].
         const double cfac = sgn * a.loop_weight;
+        const double dshift = sgn * sig;   // -sigma (|sigma| for the mass)
         for (int e = warp; e < n * n; e += nwarps) {
             double val = active ? Mc[e] : 0.0;
             if (a.absmode) val = fabs(val);
-            Ms[e * kLanes + lane] = (T)val;
+            const int v = e / n, j = e % n;
+            Ms[e * kLanes + lane] = (T)((v == j && j != 0 && shifts) ? val + dshift : val);
             Mdw[e * kLanes + lane] = cfac * val;
         }
         // Start: the loop through the normal point of vertex 0 (layer 1, mask e_0, slot 0).
@@ -82,12 +91,11 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
         for (int ell = 1; ell <= 2 * n; ++ell) {
             const T *src = ring + (size_t)(ell % a.nslots) * a.slot_elems;
             T *dst1 = ring + (size_t)((ell + 1) % a.nslots) * a.slot_elems;
-            T *dst2 = ring + (size_t)((ell + 2) % a.nslots) * a.slot_elems;
             const uint32_t first = tab.layer_first[ell];
             const uint32_t cnt = tab.layer_count[ell];
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
-                fwd_mask<T>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1, dst2, Ms, Md, lane, ci, nfl, sgn, a.loop_weight, sig,
-                            shifts, active, lam, cfg, a.out, a.status, a.prefetch);
+                fwd_mask<T>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1,
+                            Ms, Md, lane, ci, nfl, sgn, sig, shifts, active, lam, cfg, a.out, a.status, a.prefetch);
             __syncthreads();
         }
     }
@@ -179,7 +187,7 @@ static cos_status launch_dp_t(Workspace *ws, const DpLaunch &L, cudaStream_t str
     const int nfl = L.n_mat;
     const Tuning tu = get_tuning(L.n_max, L.precision, nfl);
     const int nsm = sm_count(ws->device);
-    const int nslots = L.shifts ? 3 : 2;
+    const int nslots = dp_slots(L);
     const size_t slot_elems = (size_t)host_order(L.n_max).max_slots * kLanes;
     const size_t per_cta = (size_t)nslots * slot_elems * sizeof(T);
     const int cpb = kLanes / nfl;
@@ -236,7 +244,7 @@ static cos_status launch_dp_t(Workspace *ws, const DpLaunch &L, cudaStream_t str
 
 // ------------------------------------------------------------------ raw-buffer launchers
 
-int dp_slots(const DpLaunch &L) { return L.shifts ? 3 : 2; }
+int dp_slots(const DpLaunch &) { return 2; }
 size_t dp_state_bytes(const DpLaunch &L) { return L.precision == COS_MIXED ? sizeof(float) : sizeof(double); }
 
 cos_status launch_plan_raw(const RawBuffers &rb, int n_cfg, int n_max, const int32_t *order, int cpb, int device,

@@ -107,14 +107,13 @@ __device__ __forceinline__ void prefetch_block(const T *src, uint32_t off, uint3
 //   off1 : block offset of mask mu + e_j in the next layer
 //   meta : ai1 (bits 0-3, slot of endpoint j inside a row of that block), nA1 (4-7, row
 //          length), untouched (8, mu_j = 0), j (12-15), H1 (16-27, heads of mu + e_j)
-//   off2, h2 : block offset and heads of mu + 2 e_j (shift targets, mu_j = 0)
 struct TgtInfo {
-    uint32_t off1, meta, off2, h2;
+    uint32_t off1, meta;
 };
 
 __device__ __forceinline__ TgtInfo mask_targets(uint32_t A, uint32_t B, uint32_t J, uint32_t code,
-                                                const uint32_t *__restrict__ rank3, bool shifts, int lane) {
-    TgtInfo ti = {0u, 0u, 0u, 0u};
+                                                const uint32_t *__restrict__ rank3, int lane) {
+    TgtInfo ti = {0u, 0u};
     if (lane < __popc(J)) {
         const int j = __fns(J, 0, lane + 1);
         const uint32_t bj = 1u << j;
@@ -126,50 +125,30 @@ __device__ __forceinline__ TgtInfo mask_targets(uint32_t A, uint32_t B, uint32_t
         ti.off1 = __ldg(rank3 + code + c_p3[j]);
         ti.meta = ai1 | (nA1 << 4) | ((untouched ? 1u : 0u) << 8) | ((uint32_t)j << 12) |
                   (head_set(B1, A1 & ~B1) << 16);
-        if (shifts && untouched) {
-            const uint32_t B2 = B | bj;
-            ti.off2 = __ldg(rank3 + code + 2u * c_p3[j]);
-            ti.h2 = head_set(B2, A1 & ~B2);
-        }
     }
     return ti;
 }
 
-// Store of one extension's dot product d into its target slot (and the shift target).
+// Store of one extension's dot product into its target slot.  Every target has exactly one
+// writer: shift points enter through the shifted diagonal of the extension matrices (see
+// cos_dp.cu), so no target is read back and accumulated -- except the seed of a new loop at
+// vertex 0, which the same thread adds after the row (fwd_mask).
 template <typename T>
-__device__ __forceinline__ void push_target(T *__restrict__ dst1, T *__restrict__ dst2, const TgtInfo &ti, int q,
-                                            int j, T d, uint32_t hlow, bool shifts, T negsig, int lane) {
+__device__ __forceinline__ void push_target(T *__restrict__ dst1, const TgtInfo &ti, int q, T d, uint32_t hlow,
+                                            int lane) {
     const uint32_t off1 = __shfl_sync(0xFFFFFFFFu, ti.off1, q);
     const uint32_t meta = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
     const uint32_t ai1 = meta & 15u, nA1 = (meta >> 4) & 15u;
     const uint32_t hi1 = (uint32_t)__popc((meta >> 16) & hlow);
-    T *tp = dst1 + (size_t)(off1 + hi1 * nA1 + ai1) * kLanes + lane;
-    if (meta & 256u) {
-        // mu_j = 0 -> 1: the only writer of this slot.
-        *tp = d;
-        if (shifts) {
-            // mu_j = 0 -> 2 through a shift point: first (plain) writer of the slot; the
-            // extension from mu+e_j adds to it one layer later.
-            const uint32_t off2 = __shfl_sync(0xFFFFFFFFu, ti.off2, q);
-            const uint32_t h2 = __shfl_sync(0xFFFFFFFFu, ti.h2, q);
-            const uint32_t hi2 = (uint32_t)__popc(h2 & hlow);
-            dst2[(size_t)(off2 + hi2 * nA1 + ai1) * kLanes + lane] = negsig * d;
-        }
-    } else if (shifts && j != 0) {
-        *tp += d;
-    } else {
-        // mu_j = 1 -> 2 without shift sources (j = 0: the seed of the new head at vertex 0,
-        // issued later by this same thread, adds to it).
-        *tp = d;
-    }
+    dst1[(size_t)(off1 + hi1 * nA1 + ai1) * kLanes + lane] = d;
 }
 
 // One row (mu, h): load its NV endpoint states, accumulate the close, push every extension.
 template <typename T, int NV>
-__device__ __forceinline__ void do_row(const T *__restrict__ src, T *__restrict__ dst1, T *__restrict__ dst2,
-                                       const T *__restrict__ Ms, const double *__restrict__ Md, const TgtInfo &ti,
-                                       int nJ, uint32_t J, uint32_t Vrow, uint32_t A, uint32_t off, int h, int hidx, int nA,
-                                       int n, bool needclose, bool shifts, T negsig, int lane, double &csum) {
+__device__ __forceinline__ void do_row(const T *__restrict__ src, T *__restrict__ dst1, const T *__restrict__ Ms,
+                                       const double *__restrict__ Md, const TgtInfo &ti, int nJ, uint32_t J,
+                                       uint32_t Vrow, uint32_t A, uint32_t off, int h, int hidx, int nA, int n,
+                                       bool needclose, int lane, double &csum) {
     T o[NV];
     int vs[NV];
     const T *row = src + (size_t)(off + (uint32_t)(hidx * nA)) * kLanes + lane;
@@ -200,28 +179,26 @@ __device__ __forceinline__ void do_row(const T *__restrict__ src, T *__restrict_
             da = Prec<T>::fma_(o[t], Ms[vs[t] + ja * kLanes], da);
             db = Prec<T>::fma_(o[t], Ms[vs[t] + jb * kLanes], db);
         }
-        push_target(dst1, dst2, ti, q, ja, da, hlow, shifts, negsig, lane);
-        push_target(dst1, dst2, ti, q + 1, jb, db, hlow, shifts, negsig, lane);
+        push_target(dst1, ti, q, da, hlow, lane);
+        push_target(dst1, ti, q + 1, db, hlow, lane);
     }
     if (q < nJ) {
         const int j = __ffs(jj) - 1;
         T d = T(0);
 #pragma unroll
         for (int t = 0; t < NV; ++t) d = Prec<T>::fma_(o[t], Ms[vs[t] + j * kLanes], d);
-        push_target(dst1, dst2, ti, q, j, d, hlow, shifts, negsig, lane);
+        push_target(dst1, ti, q, d, hlow, lane);
     }
 }
 
 template <typename T>
-__device__ __forceinline__ void row_dispatch(int nv, const T *src, T *dst1, T *dst2, const T *Ms, const double *Md,
+__device__ __forceinline__ void row_dispatch(int nv, const T *src, T *dst1, const T *Ms, const double *Md,
                                              const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow, uint32_t A,
-                                             uint32_t off,
-                                             int h, int hidx, int nA, int n, bool needclose, bool shifts, T negsig,
-                                             int lane, double &csum) {
+                                             uint32_t off, int h, int hidx, int nA, int n, bool needclose, int lane,
+                                             double &csum) {
 #define COS_ROW(K)                                                                                            \
     case K:                                                                                                   \
-        do_row<T, K>(src, dst1, dst2, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, shifts, negsig, \
-                     lane, csum);                                                                             \
+        do_row<T, K>(src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, csum);       \
         break;
     switch (nv) {
         COS_ROW(1)
@@ -244,16 +221,13 @@ __device__ __forceinline__ void row_dispatch(int nv, const T *src, T *dst1, T *d
 
 // One interaction mask of the forward sweep: every row, the flavor sum of the close, and
 // the seed of the next loop (or the sink).  `out` may be null (adjoint recomputation).
-// MD_SCALED: Md already carries the loop factor sgn * w (forward kernel); otherwise the
-// factor is applied to the flavor sum (adjoint recomputation, which shares one matrix copy).
-template <typename T, bool MD_SCALED = true>
+// Ms: extension matrices (shifted diagonal); Md: FP64 close matrices times sgn * w.
+template <typename T>
 __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
-                                         int n, const T *src,
-                                         T *dst1, T *dst2, const T *Ms, const double *Md, int lane, int ci,
-                                         int nfl, double sgn, double loop_weight, double sig, bool shifts, bool active,
-                                         int lam, int cfg, double *out, int *status, int prefetch) {
+                                         int n, const T *src, T *dst1, const T *Ms, const double *Md, int lane,
+                                         int ci, int nfl, double sgn, double sig, bool shifts, bool active, int lam,
+                                         int cfg, double *out, int *status, int prefetch) {
     const uint32_t full = (1u << n) - 1u;
-    const T negsig = (T)(sgn * sig);
     const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + mask_index));
     const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, code = mk.y, off = mk.z;
     const uint32_t ones = A & ~B;
@@ -268,19 +242,19 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
         prefetch_block(src, nk.z, (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane, prefetch);
     }
     double csum = 0.0;
-    const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, shifts, lane);
+    const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, lane);
     const int nJ = __popc(J);
     for (uint32_t hh = H; hh; hh &= hh - 1u) {
         const int h = __ffs(hh) - 1;
         const int hidx = __popc(H & ((1u << h) - 1u));
         const uint32_t Vrow = row_vmask(A, ones, h);
-        row_dispatch<T>(__popc(Vrow), src, dst1, dst2, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose,
-                        shifts, negsig, lane, csum);
+        row_dispatch<T>(__popc(Vrow), src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane,
+                        csum);
     }
     if (!needclose) return;  // no half-visited vertex and not full: disconnected, dropped
     // Flavor sum of the loop-closing weight over the lanes of this configuration; the loop
     // factor sgn * w is already inside Md (the close's copy of the matrices).
-    const double C = MD_SCALED ? flavor_sum(csum, nfl, ci) : flavor_sum(csum, nfl, ci) * (sgn * loop_weight);
+    const double C = flavor_sum(csum, nfl, ci);
     if (ones) {
         const int k = __ffs(ones) - 1;
         const uint32_t bk = 1u << k;
