@@ -252,7 +252,7 @@ const char *cos_last_error(void);
  * Counts of the merged DP for order n (no device needed): interaction masks
  * (mu_0 >= 1), state slots (head x endpoint per mask), reachable states, and
  * the FP64 multiply-adds of one flavor array (extension dot products and
- * loop-closing sums over reachable states) plus the shift products. */
+ * loop-closing sums over reachable states). */
 typedef struct {
     int n;
     int64_t masks;
@@ -261,7 +261,8 @@ typedef struct {
     int64_t states;
     int64_t fma_ext;        /* clow extension multiply-adds */
     int64_t fma_close;      /* loop-closing multiply-adds */
-    int64_t mul_shift;      /* shift-target products (one per row and untouched vertex) */
+    int64_t mul_shift;      /* shift transitions (one per row and untouched vertex); they ride on
+                               the shifted diagonal of the extension matrices, no extra work */
 } cos_structure_info;
 
 cos_status cos_structure(int n, cos_structure_info *info);
