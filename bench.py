@@ -377,7 +377,8 @@ def oracle_leg(w, budget, head_out, keep):
     rate, threads, n, vals = cpu_oracle_rate(w, budget)
     base = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n} configurations of the n=8 SU(4) workload (numpy gather + C DP in double, OpenMP)"}
-    acc = {"su4_n8_fp64_vs_oracle": error_stats(head_out[:n], vals)}
+    mass, _ = oracle_values(w, I.workload_configs(w, n), absmode=True)
+    acc = {"su4_n8_fp64_vs_oracle": error_stats(head_out[:n], vals, mass)}
     for name, (wname, got) in keep.items():
         wk = I.WORKLOADS[wname]
         k = min(len(got), 160)
