@@ -275,6 +275,12 @@ cos_status cos_structure(int n, cos_structure_info *info);
  * (written only if a chain hits an impossible value).  Time it with CUDA events. */
 cos_status cos_peak_probe(int kind, int blocks, int threads, int iters, void *d_sink, cos_stream_t stream);
 
+/* Verification of the integer-pipe FP32 <-> FP64 conversions used by the mixed-precision DP
+ * (no counterpart in the paper): d_narrowed[i] = d_in64[i] rounded to FP32 (nearest even),
+ * d_widened[i] = d_in32[i] widened to FP64, exactly as the kernels compute them. */
+cos_status cos_convert_check(int64_t n, const double *d_in64, const float *d_in32, float *d_narrowed,
+                             double *d_widened, cos_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

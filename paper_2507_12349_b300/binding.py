@@ -31,7 +31,7 @@ EXPORTS = [
     "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_sync_status", "cos_status_string",
     "cos_last_error", "cos_structure", "cos_peak_probe",
     "cos_plan_create_batch", "cos_plan_create_matrices", "cos_plan_launch", "cos_plan_status", "cos_plan_grid",
-    "cos_plan_destroy", "cos_set_tuning", "cos_get_tuning", "cos_autotune",
+    "cos_plan_destroy", "cos_set_tuning", "cos_get_tuning", "cos_autotune", "cos_convert_check",
 ]
 
 
@@ -94,6 +94,7 @@ def lib(build: bool = True):
         L.cos_last_error.restype = ctypes.c_char_p
         L.cos_structure.argtypes = [i32, ctypes.POINTER(cos_structure_info)]
         L.cos_peak_probe.argtypes = [i32, i32, i32, i32, vp, vp]
+        L.cos_convert_check.argtypes = [i64, vp, vp, vp, vp, vp]
         L.cos_plan_create_batch.argtypes = [vp, i32, i32, vp, vp, vp, vp, i32, vp, vp, vp, ctypes.POINTER(vp)]
         L.cos_plan_create_matrices.argtypes = [i32, i32, vp, vp, i32, i32, dptr, vp, i32, vp, vp, vp,
                                                ctypes.POINTER(vp)]
@@ -272,6 +273,11 @@ def matrix_offsets(order: np.ndarray, n_mat: int) -> np.ndarray:
 def cos_peak_probe(kind: int, blocks: int, threads: int, iters: int, sink, stream=None):
     _check(lib().cos_peak_probe(int(kind), int(blocks), int(threads), int(iters), _ptr(sink), _stream(stream)),
            "cos_peak_probe")
+
+
+def cos_convert_check(in64, in32, narrowed, widened, stream=None):
+    _check(lib().cos_convert_check(int(in64.numel()), _ptr(in64, "f64"), _ptr(in32), _ptr(narrowed),
+                                   _ptr(widened, "f64"), _stream(stream)), "cos_convert_check")
 
 
 def measure_peak(kind: int = 0, iters: int = 4096, reps: int = 3, sweep: bool = False):

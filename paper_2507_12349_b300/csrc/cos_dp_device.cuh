@@ -45,20 +45,48 @@ struct Prec<float> {
 // Exact FP32 -> FP64 widening by bit manipulation (IEEE-754 binary32 / binary64 layouts: the
 // exponent is rebiased by 1023 - 127 = 896 and the 23-bit fraction moves up by 29 bits).  On
 // B300 the FP64 conversion instruction occupies the FP64 pipe; this keeps the widening on the
-// integer pipe.  Zeros are widened inline; subnormals, infinities and NaNs take the
-// conversion instruction (rare, and every result is identical to it).
+// integer pipe.  Zeros are handled by integer selects; subnormals, infinities and NaNs go
+// through the conversion instruction in a separate (non-inlined) function, so the compiler
+// cannot turn the rare path into a predicated conversion on every lane.  Results equal the
+// conversion instruction's in every case.
+static __device__ __noinline__ double widen_slow(float f) { return (double)f; }
 __device__ __forceinline__ double widen(double x) { return x; }
 __device__ __forceinline__ double widen(float f) {
     const uint32_t u = __float_as_uint(f);
     const uint32_t e = (u >> 23) & 0xFFu;
     const uint32_t frac = u & 0x7FFFFFu;
-    if (e - 1u < 0xFEu) {
-        const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | (frac >> 3);
-        return __hiloint2double((int)hi, (int)(frac << 29));
+    uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | (frac >> 3);
+    uint32_t lo = frac << 29;
+    if (e == 0u) {
+        hi = u & 0x80000000u;
+        lo = 0u;
     }
-    if (e == 0u && frac == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-    return (double)f;
+    double d = __hiloint2double((int)hi, (int)lo);
+    if (__builtin_expect((e == 0u && frac != 0u) || e == 0xFFu, 0)) d = widen_slow(f);
+    return d;
 }
+
+// FP64 -> FP32 with round-to-nearest-even on the integer pipe for results in the normal
+// float range (the 52-bit fraction keeps its top 23 bits, the 29 dropped bits decide the
+// rounding, a carry moves into the exponent); zeros by integer selects; results that would
+// be subnormal, infinite or NaN take the conversion instruction (non-inlined, rare).
+static __device__ __noinline__ float narrow_slow(double x) { return (float)x; }
+__device__ __forceinline__ float narrow_to(float, double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(b >> 32);
+    const uint32_t sgn = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu) - 896;          // binary32 biased exponent
+    const uint32_t mant = (uint32_t)((b >> 29) & 0x7FFFFFull);
+    const uint32_t rem = (uint32_t)(b & 0x1FFFFFFFull);
+    uint32_t r = sgn | ((uint32_t)e << 23) | mant;
+    r += (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) ? 1u : 0u;
+    const bool zero = (b << 1) == 0ull;
+    if (zero) r = sgn;
+    float f = __uint_as_float(r);
+    if (__builtin_expect(!zero && (e < 1 || e > 254), 0)) f = narrow_slow(x);
+    return f;
+}
+__device__ __forceinline__ double narrow_to(double, double x) { return x; }
 
 // -x by flipping the sign bit (integer pipe; FP64 instructions are the scarce resource).
 __device__ __forceinline__ double neg(double x) {
@@ -265,8 +293,9 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
         T *tp = dst1 + (size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane;
         double val = C;
         if (ell == 1 && shifts) val += sgn * 2.0 * sig;  // vertex 0 carries a shift point
-        if (k == 0) *tp += (T)val;                        // the extension into 0' wrote it
-        else *tp = (T)val;
+        const T tv = narrow_to(T(0), val);
+        if (k == 0) *tp += tv;                            // the extension into 0' wrote it
+        else *tp = tv;
     } else if (active && lam == 0 && out) {
         const double c = ldexp(C, n - 1);
         out[cfg] = c;

@@ -1,5 +1,7 @@
 // Throughput probes for the roofline denominators: independent FMA chains per thread,
 // enough warps to fill every SM sub-partition.  FLOPs = 2 * blocks * threads * chains * iters.
+#include <algorithm>
+
 #include "cos_internal.h"
 
 namespace cosdp {
@@ -41,5 +43,35 @@ extern "C" cos_status cos_peak_probe(int kind, int blocks, int threads, int iter
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "cos_peak_probe");
+    return COS_OK;
+}
+
+// Verification hook for the integer-pipe FP32 <-> FP64 conversions of the mixed-precision DP
+// (widen / narrow_to in cos_dp_device.cuh): applies them elementwise so tests can compare
+// them bit for bit with the conversion instructions.
+#include "cos_dp_device.cuh"
+
+namespace cosdp {
+__global__ void convert_check_kernel(int64_t n, const double *in64, const float *in32, float *narrowed,
+                                     double *widened) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        narrowed[i] = narrow_to(0.0f, in64[i]);
+        widened[i] = widen(in32[i]);
+    }
+}
+}  // namespace cosdp
+
+extern "C" cos_status cos_convert_check(int64_t n, const double *d_in64, const float *d_in32, float *d_narrowed,
+                                        double *d_widened, cos_stream_t stream) {
+    using namespace cosdp;
+    if (n < 0 || (n > 0 && (!d_in64 || !d_in32 || !d_narrowed || !d_widened))) {
+        set_error("cos_convert_check: bad argument");
+        return COS_ERR_ARG;
+    }
+    if (n == 0) return COS_OK;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    convert_check_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(n, d_in64, d_in32, d_narrowed, d_widened);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "cos_convert_check");
     return COS_OK;
 }
