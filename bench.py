@@ -34,6 +34,11 @@ WORKLOAD = "su4_mu_broken_n8"
 METRIC = "connected-sum configs/s at order n (FP64 vs mixed), roofline fraction, grad overhead"
 UNIT = "configs/s"
 NOMINAL_FP64_TFLOPS = 1.25
+# DRAM bytes (read + write) of dp_forward_kernel<double> per configuration of the headline
+# workload: ncu dram__bytes_read.sum + dram__bytes_write.sum on a 5 000-configuration launch
+# (8.630 GB + 7.111 GB, profiles/dp_forward_fp64_su4_n8.md); traffic grows in proportion
+# to the configurations of a launch.
+HEADLINE_DRAM_BYTES_PER_CFG = (8.629577e9 + 7.111385e9) / 5000
 FP64_FMA_PER_CLK_SM = 2.0
 
 
@@ -341,7 +346,10 @@ def native_arm(args):
                      "kernel": ("dp_adjoint_kernel<sigma grad>" if args.grad else
                                 "dp_forward_kernel<%s>" % ("double" if args.precision == "fp64" else "float")),
                      "flops_per_launch": flops_launch,
-                     "launch_ms": dp_avg * 1e3, "traffic": None},
+                     "launch_ms": dp_avg * 1e3,
+                     "traffic": (HEADLINE_DRAM_BYTES_PER_CFG * n_cfg
+                                 if args.workload == WORKLOAD and args.precision == "fp64" and not args.grad else None),
+                     "traffic_source": "ncu DRAM bytes of a 5000-configuration launch, scaled by configurations"},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
