@@ -422,6 +422,35 @@ def measure_adjoint(torch, B, flush_buf, n_cfg):
             "grad_overhead": tg / tf}
 
 
+def measure_subsets(torch, B, flush_buf, n_cfg):
+    """All-subsets mode on the headline workload (SU(4), mu broken, n = 8): c(S) of all 255
+    vertex subsets and a(S) by the GPU subset exponential, against the plain call (c(V) only)
+    on the same gathered matrices.  Also the root-0 by-product (c(S) for S containing vertex 0)."""
+    w = I.WORKLOADS[WORKLOAD]
+    cfgs = I.workload_configs(w, n_cfg)
+    tabs = B.tables_for(w.model)
+    n_mat = tabs.info().n_mat
+    d = B.configs_to_device(cfgs)
+    moff = torch.as_tensor(B.matrix_offsets(cfgs.order, n_mat), device="cuda")
+    M = torch.empty(int(n_cfg * n_mat * 64), dtype=torch.float64, device="cuda")
+    B.cos_gather(tabs, d[0], d[1], d[2], d[3], moff, M)
+    out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
+    c = torch.empty(n_cfg * 256, dtype=torch.float64, device="cuda")
+    a = torch.empty_like(c)
+    plain = lambda: B.cos_connected_sum_matrices(8, d[0], moff, n_mat, 1, None, M, "fp64", out)
+    root0 = lambda: B.cos_connected_sum_subsets(8, d[0], moff, n_mat, 1, None, M, "fp64", c, None, False)
+    full = lambda: B.cos_connected_sum_subsets(8, d[0], moff, n_mat, 1, None, M, "fp64", c, a, True)
+    for f in (plain, root0, full):
+        f()
+    B.cos_sync_status()
+    tp, t0, tf = (statistics.mean(time_steps(torch, f, 2, lambda: flush_l2(flush_buf))) for f in (plain, root0, full))
+    B.cos_sync_status()
+    tabs.close()
+    return {"configs": n_cfg, "plain_configs_per_s": n_cfg / tp, "root0_configs_per_s": n_cfg / t0,
+            "all_subsets_configs_per_s": n_cfg / tf, "all_subsets_cost_vs_plain": tf / tp,
+            "root0_cost_vs_plain": t0 / tp}
+
+
 def measure_forms(torch, B, flush_buf):
     """The other forms of the path on the same GPU: FP64 vs mixed precision at orders 8 and 10,
     the uneven-order batch as one persistent launch in a CUDA graph (autotuned shapes), the
@@ -465,6 +494,7 @@ def measure_forms(torch, B, flush_buf):
     res["su3_shift_n10_fp64"], _ = run("su3_shift_mixed_n10", 100_000, "fp64", steps=1)
     res["su6_uneven_n4_12_fp64_graph"], _ = run("su6_sym_uneven_n4_12", 200_000, "fp64", steps=1, graph=True)
     res["su4_n10_adjoint"] = measure_adjoint(torch, B, flush_buf, 50_000)
+    res["su4_n8_all_subsets_fp64"] = measure_subsets(torch, B, flush_buf, 100_000)
     # plain FP64 per-configuration form: one configuration per call, no graph
     w = I.WORKLOADS[WORKLOAD]
     cfgs = I.workload_configs(w, 200)

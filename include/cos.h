@@ -172,6 +172,31 @@ cos_status cos_connected_sum_batch(const cos_tables *tables, int n_cfg, int n_ma
                                    cos_precision precision, double *d_out,
                                    double *d_abs_mass, cos_stream_t stream);
 
+/* ------------------------------------------------------------------ all subsets
+ * Connected sums of every vertex subset (Methods A: the subset recursion between the sum over
+ * all decorated covers a(S) and the sum over connected ones c(S)).  One configuration of n
+ * vertices then yields every lower order, as a CDet evaluation does.
+ *   d_c  [n_cfg][2^n_max]  c(S) at index c * 2^n_max + S, bit i of S = vertex i.
+ *        c(empty) = 0, and sets holding a vertex >= the configuration's order are 0.
+ *        all_roots = 1: every nonempty S.  The merged DP of Results A rooted at vertex m on the
+ *          trailing principal submatrices M^l[m.., m..] gives c(S) for every S whose smallest
+ *          vertex is m (from the closes of the masks with no half-visited vertex); all roots of
+ *          all configurations run as one batch of derived problems, about 1.5 times the work
+ *          of the order-n DP at n = 10.
+ *        all_roots = 0: only the sets containing vertex 0, a by-product of the order-n DP
+ *          (which then also closes the masks it otherwise drops); the other entries are NaN.
+ *   d_a  NULL, or [n_cfg][2^n_max] receiving a(S) = sum_{T subset of S, min S in T}
+ *        c(T) a(S \ T), a(empty) = 1, evaluated in FP64 on the GPU; needs all_roots = 1.
+ * Other arguments as cos_connected_sum_matrices (precision applies to the DP; the recursion
+ * for a is FP64).  Workspace: besides the DP's, all_roots = 1 holds n_cfg * n_max derived
+ * problems and their submatrices (n_mat * n_max (n_max + 1) (2 n_max + 1) / 6 doubles per
+ * configuration).  A device-detected order error is reported as for the other entry points;
+ * the outputs of that call are then undefined. */
+cos_status cos_connected_sum_subsets(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                                     int n_mat, int loop_weight, const double *h_sigma, const double *d_M,
+                                     cos_precision precision, int all_roots, double *d_c, double *d_a,
+                                     cos_stream_t stream);
+
 /* ------------------------------------------------------------------ adjoint DP
  * Gradient of the connected sums by the reverse (adjoint) DP: the forward DP is re-run with
  * every layer kept, then walked backwards (the adjoint of Alg. 2-3 as merged in Results A).

@@ -28,6 +28,7 @@ STATUS = {0: "COS_OK", -1: "COS_ERR_ARG", -2: "COS_ERR_ORDER", -3: "COS_ERR_CUDA
 EXPORTS = [
     "cos_build_propagators", "cos_free_tables", "cos_get_tables_info", "cos_copy_table", "cos_gather",
     "cos_connected_sum_matrices", "cos_connected_sum_matrices_noalloc", "cos_connected_sum_batch",
+    "cos_connected_sum_subsets",
     "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_sync_status", "cos_status_string",
     "cos_last_error", "cos_structure", "cos_peak_probe",
     "cos_plan_create_batch", "cos_plan_create_matrices", "cos_plan_launch", "cos_plan_status", "cos_plan_grid",
@@ -213,6 +214,20 @@ def cos_connected_sum_matrices_noalloc(n_max: int, order, moff, n_mat: int, loop
                                                     int(n_mat), int(loop_weight), sig, _ptr(M, "f64"),
                                                     PRECISIONS[precision], _ptr(out, "f64"), _ptr(abs_mass, "f64"),
                                                     _stream(stream)), "cos_connected_sum_matrices_noalloc")
+
+
+def cos_connected_sum_subsets(n_max: int, order, moff, n_mat: int, loop_weight: int,
+                              sigma: Optional[Sequence[float]], M, precision: str, c_out, a_out=None,
+                              all_roots: bool = True, stream=None):
+    """c(S) (and a(S) when a_out is given) of every vertex subset S: c_out / a_out are
+    [n_cfg * 2^n_max] float64, entry c * 2^n_max + S (bit i of S = vertex i)."""
+    sig = None
+    if sigma is not None:
+        sig = (ctypes.c_double * n_mat)(*[float(s) for s in sigma])
+    _check(lib().cos_connected_sum_subsets(int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(moff, "i64"),
+                                           int(n_mat), int(loop_weight), sig, _ptr(M, "f64"), PRECISIONS[precision],
+                                           int(bool(all_roots)), _ptr(c_out, "f64"), _ptr(a_out, "f64"),
+                                           _stream(stream)), "cos_connected_sum_subsets")
 
 
 def cos_connected_sum_batch(tables: Tables, n_max: int, order, offset, site, tau, precision: str, out,

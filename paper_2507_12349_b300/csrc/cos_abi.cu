@@ -179,6 +179,10 @@ void free_workspace(Workspace *ws) {
     cudaFree(ws->scratch);
     cudaFree(ws->gM);
     cudaFree(ws->gsig);
+    cudaFree(ws->sub_order);
+    cudaFree(ws->sub_moff);
+    cudaFree(ws->sub_key);
+    cudaFree(ws->sub_M);
     delete ws;
 }
 
@@ -200,7 +204,7 @@ cos_status check_common(int n_cfg, int n_max, cos_precision prec, const char *fn
 
 cos_status run_dp(Workspace *ws, DpLaunch L, double *d_abs_mass, cudaStream_t stream) {
     const int cpb = kLanes / L.n_mat;
-    cos_status st = launch_plan_batches(ws, L.n_cfg, L.n_max, L.order, cpb, stream);
+    cos_status st = launch_plan_batches(ws, L.n_cfg, L.n_max, L.order, cpb, stream, L.allow_empty);
     if (st != COS_OK) return st;
     st = launch_dp(ws, L, stream);
     if (st != COS_OK) return st;

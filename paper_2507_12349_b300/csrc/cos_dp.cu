@@ -74,6 +74,13 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
         const int cfg = active ? a.batch_list[bd.y + ci] : -1;
         const double *Mc = nullptr;
         if (active) Mc = a.M + (a.moff ? a.moff[cfg] : (int64_t)cfg * a.mstride) + (size_t)lam * n * n;
+        double *cs = nullptr;
+        int csh = 0;
+        if (a.csub && active) {
+            const int64_t key = a.csub_key[cfg];
+            cs = a.csub + (key >> 4);
+            csh = (int)(key & 15);
+        }
         // Matrices of the batch -> shared memory [v][j][lane].
         const double cfac = sgn * a.loop_weight;
         const double dshift = sgn * sig;   // -sigma (|sigma| for the mass)
@@ -95,7 +102,8 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
             const uint32_t cnt = tab.layer_count[ell];
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
                 fwd_mask<T>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1,
-                            Ms, Md, lane, ci, nfl, sgn, sig, shifts, active, lam, cfg, a.out, a.status, a.prefetch);
+                            Ms, Md, lane, ci, nfl, sgn, sig, shifts, active, lam, cfg, a.out, a.status, a.prefetch,
+                            a.csub != nullptr, cs, csh);
             __syncthreads();
         }
     }
@@ -105,9 +113,13 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
 // Sorts configurations by order (largest first) into batches of `cpb` configurations.
 // plan layout: [0,16) counts, [16,32) cursors, [32,48) bucket starts, [48,64) batch starts, [64] n_batches
 
-__global__ void plan_count_kernel(int n_cfg, int n_max, const int32_t *order, int *plan, int *status) {
+// allow_empty: order 0 marks a configuration slot with nothing to compute (derived problems of
+// the all-subsets mode); it is skipped instead of flagged.
+__global__ void plan_count_kernel(int n_cfg, int n_max, const int32_t *order, int *plan, int *status,
+                                  int allow_empty) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cfg; c += gridDim.x * blockDim.x) {
         const int n = order[c];
+        if (n == 0 && allow_empty) continue;
         if (n < 1 || n > n_max) {
             atomicOr(status, kStatusOrder);
         } else {
@@ -156,7 +168,7 @@ static int sm_count(int device) {
 }
 
 cos_status launch_plan_batches(Workspace *ws, int n_cfg, int n_max, const int32_t *order, int cpb,
-                               cudaStream_t stream) {
+                               cudaStream_t stream, bool allow_empty) {
     const int max_batches = (n_cfg + cpb - 1) / cpb + COS_NMAX;
     cos_status st = ensure((void **)&ws->batch_list, &ws->batch_cap, (size_t)n_cfg + 1, sizeof(int), "batch list");
     if (st != COS_OK) return st;
@@ -166,7 +178,9 @@ cos_status launch_plan_batches(Workspace *ws, int n_cfg, int n_max, const int32_
     if (e != cudaSuccess) return cuda_fail(e, "planner memset");
     const int threads = 256;
     const int blocks = std::max(1, std::min((n_cfg + threads - 1) / threads, 4 * sm_count(ws->device)));
-    if (n_cfg > 0) plan_count_kernel<<<blocks, threads, 0, stream>>>(n_cfg, n_max, order, ws->plan_counts, ws->status);
+    if (n_cfg > 0)
+        plan_count_kernel<<<blocks, threads, 0, stream>>>(n_cfg, n_max, order, ws->plan_counts, ws->status,
+                                                          allow_empty ? 1 : 0);
     plan_prefix_kernel<<<1, 32, 0, stream>>>(cpb, ws->plan_counts);
     if (n_cfg > 0) plan_scatter_kernel<<<blocks, threads, 0, stream>>>(n_cfg, n_max, order, ws->plan_counts, ws->batch_list);
     const int bb = std::max(1, std::min((max_batches + threads - 1) / threads, 4 * sm_count(ws->device)));
@@ -232,6 +246,8 @@ static cos_status launch_dp_t(Workspace *ws, const DpLaunch &L, cudaStream_t str
     a.nslots = nslots;
     a.smem_n = L.n_max;
     a.prefetch = tu.prefetch;
+    a.csub = L.csub;
+    a.csub_key = L.csub_key;
     a.out = L.out;
     a.status = ws->status;
     e = cudaMemsetAsync(ws->queue, 0, sizeof(int), stream);
@@ -254,7 +270,7 @@ cos_status launch_plan_raw(const RawBuffers &rb, int n_cfg, int n_max, const int
     if (e != cudaSuccess) return cuda_fail(e, "planner memset");
     const int threads = 256;
     const int blocks = std::max(1, std::min((n_cfg + threads - 1) / threads, 4 * sm_count(device)));
-    if (n_cfg > 0) plan_count_kernel<<<blocks, threads, 0, stream>>>(n_cfg, n_max, order, rb.plan, rb.status);
+    if (n_cfg > 0) plan_count_kernel<<<blocks, threads, 0, stream>>>(n_cfg, n_max, order, rb.plan, rb.status, 0);
     plan_prefix_kernel<<<1, 32, 0, stream>>>(cpb, rb.plan);
     if (n_cfg > 0) plan_scatter_kernel<<<blocks, threads, 0, stream>>>(n_cfg, n_max, order, rb.plan, rb.list);
     const int bb = std::max(1, std::min((max_batches + threads - 1) / threads, 4 * sm_count(device)));
@@ -293,6 +309,8 @@ static cos_status launch_dp_raw_t(const RawBuffers &rb, const DpLaunch &L, cudaS
     a.nslots = dp_slots(L);
     a.smem_n = L.n_max;
     a.prefetch = tu.prefetch;
+    a.csub = L.csub;
+    a.csub_key = L.csub_key;
     a.out = L.out;
     a.status = rb.status;
     e = cudaMemsetAsync(rb.queue, 0, sizeof(int), stream);

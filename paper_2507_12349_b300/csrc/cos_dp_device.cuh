@@ -27,6 +27,9 @@ struct DpArgs {
     int nslots;
     int smem_n;                 // order used for the shared-memory layout stride (n_max)
     int prefetch;               // prefetch the next mask's states: 0 off, 1 into L2, 2 into L1 (tuned)
+    double *csub;               // nullable (all-subsets mode): connected sums c(S), see csub_key
+    const int64_t *csub_key;    // per configuration: (base << 4) | shift; c(S) of its vertex set S
+                                // (bit i = vertex i) goes to csub[base + (S << shift)]
     double *out;
     int *status;
 };
@@ -254,7 +257,8 @@ template <typename T>
 __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
                                          int n, const T *src, T *dst1, const T *Ms, const double *Md, int lane,
                                          int ci, int nfl, double sgn, double sig, bool shifts, bool active, int lam,
-                                         int cfg, double *out, int *status, int prefetch) {
+                                         int cfg, double *out, int *status, int prefetch, bool subsets = false,
+                                         double *csub = nullptr, int cshift = 0) {
     const uint32_t full = (1u << n) - 1u;
     const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + mask_index));
     const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, code = mk.y, off = mk.z;
@@ -262,7 +266,12 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
     const uint32_t H = head_set(B, ones);
     const uint32_t J = full & ~B;
     const int nA = __popc(A);
-    const bool needclose = (ones != 0u) || (B == full);
+    // Closes feed a new loop (a half-visited vertex remains) or the sink (all full).  With no
+    // half-visited vertex and untouched ones left, the cover of S = {mu_i = 2} is complete and
+    // connected: its close is c(S) (times 2^(1-|S|)), kept only in the all-subsets mode
+    // (`subsets` is warp-uniform; `csub` is this lane's output base, valid on active lanes).
+    const bool dead = (ones == 0u) && (B != full);
+    const bool needclose = !dead || subsets;
     if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
         // the next mask of this warp in the layer: start its loads while this one computes
         const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + next_index));
@@ -279,10 +288,14 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
         row_dispatch<T>(__popc(Vrow), src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane,
                         csum);
     }
-    if (!needclose) return;  // no half-visited vertex and not full: disconnected, dropped
+    if (!needclose) return;  // disconnected continuation: dropped
     // Flavor sum of the loop-closing weight over the lanes of this configuration; the loop
     // factor sgn * w is already inside Md (the close's copy of the matrices).
     const double C = flavor_sum(csum, nfl, ci);
+    if (subsets && ones == 0u) {
+        if (active && lam == 0) csub[(int64_t)B << cshift] = ldexp(C, __popc(B) - 1);
+        if (dead) return;
+    }
     if (ones) {
         const int k = __ffs(ones) - 1;
         const uint32_t bk = 1u << k;

@@ -109,6 +109,15 @@ struct Workspace {
     // DP layer scratch
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
+    // all-subsets mode: derived suffix problems (order, matrix offset, output key) and matrices
+    int32_t *sub_order = nullptr;
+    int64_t *sub_moff = nullptr;
+    int64_t *sub_key = nullptr;
+    size_t sub_cap = 0;              // derived problems (each of the three arrays)
+    size_t sub_moff_cap = 0;
+    size_t sub_key_cap = 0;
+    double *sub_M = nullptr;
+    size_t sub_M_cap = 0;            // doubles
     // gradient path
     double *gM = nullptr;
     size_t gM_cap = 0;
@@ -148,10 +157,13 @@ struct DpLaunch {
     int precision = COS_FP64;
     double *out = nullptr;
     bool absmode = false;
+    double *csub = nullptr;         // all-subsets mode: c(S) written at csub[base + (S << shift)]
+    const int64_t *csub_key = nullptr;  // per configuration: (base << 4) | shift
+    bool allow_empty = false;       // order 0 = empty configuration slot (skipped by the planner)
 };
 
 cos_status launch_plan_batches(Workspace *ws, int n_cfg, int n_max, const int32_t *order, int cpb,
-                               cudaStream_t stream);
+                               cudaStream_t stream, bool allow_empty = false);
 cos_status launch_dp(Workspace *ws, const DpLaunch &a, cudaStream_t stream);
 // Launch the planner and the DP kernel on caller-provided device buffers (no allocation):
 // plan = 80 ints, queue = 1 int, status = 1 int, list = n_cfg ints, batches = max_batches int4,

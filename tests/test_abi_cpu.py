@@ -46,6 +46,15 @@ def test_argument_errors_are_synchronous():
     assert rc == -1
     # empty batch is a no-op
     assert lib.cos_connected_sum_matrices(0, 4, None, None, 1, 1, None, None, 0, None, None, None) == 0
+    # all-subsets mode: a(S) needs every root; all_roots is a flag
+    rc = lib.cos_connected_sum_subsets(1, 4, None, None, 1, 1, None, None, 0, 1, None, None, None)
+    assert rc == -1                                     # null pointers
+    fake = ctypes.c_void_p(256)                         # never dereferenced: rejected before any launch
+    rc = lib.cos_connected_sum_subsets(1, 4, fake, fake, 1, 1, None, fake, 0, 0, fake, fake, None)
+    assert rc == -1
+    rc = lib.cos_connected_sum_subsets(1, 4, fake, fake, 1, 1, None, fake, 0, 2, fake, None, None)
+    assert rc == -1
+    assert lib.cos_connected_sum_subsets(0, 4, None, None, 1, 1, None, None, 0, 1, None, None, None) == 0
     assert lib.cos_status_string(-2) == b"order out of range"
     inf = B.cos_structure_info()
     assert lib.cos_structure(0, ctypes.byref(inf)) == -2
