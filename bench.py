@@ -298,7 +298,9 @@ def native_arm(args):
     peak_source = (f"unit count: {sms} SMs x {FP64_FMA_PER_CLK_SM} FP64 FMA/clk/SM x 2 flop x "
                    f"{clk:.0f} MHz (median SM clock in the timed region)")
     dp_avg = statistics.mean(a.elapsed_time(b) * 1e-3 for a, b in dp_times)
-    flops_launch = algorithmic_flops(B, cfgs.order, n_mat, sigma is not None)
+    # The gradient call runs the forward sweep and its reverse: two multiply-adds (Obar and dM)
+    # per forward multiply-add, so three times the forward's algorithmic flops.
+    flops_launch = algorithmic_flops(B, cfgs.order, n_mat, sigma is not None) * (3 if args.grad else 1)
     achieved = flops_launch / dp_avg
 
     # end to end through the public call with host buffers (pinned), copies inside the region
@@ -418,8 +420,9 @@ def measure_adjoint(torch, B, flush_buf, n_cfg):
     tg = statistics.mean(time_steps(torch, grad, 1, lambda: flush_l2(flush_buf)))
     B.cos_sync_status()
     tabs.close()
+    fl = 3 * algorithmic_flops(B, cfgs.order, 4, False)   # forward sweep + reverse (2 multiply-adds per edge)
     return {"configs": n_cfg, "forward_configs_per_s": n_cfg / tf, "grad_configs_per_s": n_cfg / tg,
-            "grad_overhead": tg / tf}
+            "grad_overhead": tg / tf, "grad_tflops": fl / tg / 1e12}
 
 
 def measure_subsets(torch, B, flush_buf, n_cfg):

@@ -34,127 +34,121 @@ struct AdjArgs {
     double *gsig;
 };
 
-// Target adjoints are fetched in chunks of kChunk extensions: the loads of a chunk are issued
-// together, which bounds the registers a row holds (o, obar and one chunk).
-constexpr int kChunk = 4;
-
-template <int NV, bool SG>
-__device__ __forceinline__ void adj_row(const double *__restrict__ fsrc, double *__restrict__ aout,
-                                        const double *__restrict__ a1, const double *__restrict__ Ms,
-                                        const double *__restrict__ Mc, double *__restrict__ gMw,
-                                        const uint32_t *__restrict__ rank3, uint32_t Vrow, uint32_t A, uint32_t B,
-                                        uint32_t J, uint32_t code, uint32_t off, int h, int hidx, int nA, int n,
-                                        double cbar, double gamma, double sgn, int lane, double &gs) {
-    double o[NV], ob[NV];
-    int vt[NV];
-    const uint32_t rowoff = off + (uint32_t)(hidx * nA);
-    uint32_t vv = Vrow;
+// Reverse step of one endpoint v of row (mu, h), done by the warp that owns v, for a mask with
+// NJ = |J| extensions (templated: every load is issued up front and no FP64 instruction is
+// predicated off -- on B300 an FP64 instruction costs 16 SM cycles whether or not its lanes
+// are enabled):
+//   Obar(mu,h,v) = sum_j D_j Ms[v][j] + Cbar Mc[v][h],  dM[v][j] += D_j O,  dM[v][h] += gamma O,
+//   and for half-visited v >= 1 the shifted diagonal: dsigma += sgn D_v O (qv = index of v in J).
+// D_j = Obar(mu + e_j, h, j) is addressed through the mask's lane-parallel target table
+// (mask_targets, shared with the forward push).  Cbar enters last, so its load and flavor sum
+// overlap the row's target loads.
+// Extensions q in [Q0, Q1) of one endpoint: loads first, then the multiply-adds.
+template <int Q0, int Q1>
+__device__ __forceinline__ void adj_chunk(const double *__restrict__ a1, const double *__restrict__ Ms,
+                                          double *__restrict__ dM, const TgtInfo &ti, uint32_t &jr, uint32_t hlow,
+                                          int vrow, double o, int lane, double &ob, int qv, double &dv) {
+    constexpr int K = Q1 - Q0;
+    double D[K], Mv[K], G[K];
+    int js[K];
 #pragma unroll
-    for (int t = 0; t < NV; ++t) {
-        const int v = __ffs(vv) - 1;
-        vv &= vv - 1u;
-        vt[t] = v;
-        o[t] = fsrc[(size_t)(rowoff + (uint32_t)__popc(A & ((1u << v) - 1u))) * kLanes + lane];
-    }
-    const int nk = n * kLanes;
-#pragma unroll
-    for (int t = 0; t < NV; ++t) {
-        const int a = vt[t] * nk + lane + h * kLanes;
-        ob[t] = cbar * Mc[a];
-        if (gamma != 0.0) gMw[a] = fma(gamma, o[t], gMw[a]);
-    }
-    const uint32_t hlow = (1u << h) - 1u;
-    uint32_t jr = J;
-    while (jr) {
-        double D[kChunk], Oj[kChunk];
-        int js[kChunk];
-#pragma unroll
-        for (int q = 0; q < kChunk; ++q) {
-            js[q] = -1;
-            D[q] = 0.0;
-            Oj[q] = 0.0;
-            if (jr) {
-                const int j = __ffs(jr) - 1;
-                jr &= jr - 1u;
-                js[q] = j;
-                const uint32_t bj = 1u << j;
-                const bool untouched = !(A & bj);
-                const uint32_t A1 = A | bj;
-                const uint32_t B1 = untouched ? B : (B | bj);
-                const int nA1 = __popc(A1);
-                const int ai1 = __popc(A1 & (bj - 1u));
-                const int hi1 = __popc(head_set(B1, A1 & ~B1) & hlow);
-                const uint32_t off1 = __ldg(rank3 + code + c_p3[j]);
-                D[q] = a1[(size_t)(off1 + (uint32_t)(hi1 * nA1 + ai1)) * kLanes + lane];
-                // state at endpoint j (half-visited j >= 1 is in Vrow): weight of the shifted diagonal
-                if (SG && !untouched && j != 0)
-                    Oj[q] = fsrc[(size_t)(rowoff + (uint32_t)__popc(A & (bj - 1u))) * kLanes + lane];
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < kChunk; ++q) {
-            if (js[q] >= 0) {
-                const int jo = js[q] * kLanes + lane;
-                const double Dq = D[q];
-#pragma unroll
-                for (int t = 0; t < NV; ++t) {
-                    const int a = vt[t] * nk + jo;
-                    ob[t] = fma(Dq, Ms[a], ob[t]);
-                    gMw[a] = fma(Dq, o[t], gMw[a]);
-                }
-                if (SG) gs = fma(sgn * Dq, Oj[q], gs);
-            }
-        }
+    for (int u = 0; u < K; ++u) {
+        const uint32_t off1 = __shfl_sync(0xFFFFFFFFu, ti.off1, Q0 + u);
+        const uint32_t meta = __shfl_sync(0xFFFFFFFFu, ti.meta, Q0 + u);
+        const int j = __ffs(jr) - 1;
+        jr &= jr - 1u;
+        js[u] = j;
+        const uint32_t ai1 = meta & 15u, nA1 = (meta >> 4) & 15u;
+        const uint32_t hi1 = (uint32_t)__popc((meta >> 16) & hlow);
+        D[u] = a1[(size_t)(off1 + hi1 * nA1 + ai1) * kLanes + lane];
+        Mv[u] = Ms[vrow + j * kLanes];
+        G[u] = dM[vrow + j * kLanes];
     }
 #pragma unroll
-    for (int t = 0; t < NV; ++t)
-        aout[(size_t)(rowoff + (uint32_t)__popc(A & ((1u << vt[t]) - 1u))) * kLanes + lane] = ob[t];
+    for (int u = 0; u < K; ++u) {
+        ob = fma(D[u], Mv[u], ob);
+        dM[vrow + js[u] * kLanes] = fma(D[u], o, G[u]);
+        dv = (Q0 + u == qv) ? D[u] : dv;   // register select, no FP64 op
+    }
 }
 
-template <bool SG>
-__device__ __forceinline__ void adj_row_dispatch(int nv, const double *fsrc, double *aout, const double *a1,
-                                                 const double *Ms, const double *Mc, double *gMw,
-                                                 const uint32_t *rank3, uint32_t Vrow, uint32_t A, uint32_t B,
-                                                 uint32_t J, uint32_t code, uint32_t off, int h, int hidx, int nA,
-                                                 int n, double cbar, double gamma, double sgn, int lane, double &gs) {
-#define COS_AROW(K)                                                                                              \
-    case K:                                                                                                      \
-        adj_row<K, SG>(fsrc, aout, a1, Ms, Mc, gMw, rank3, Vrow, A, B, J, code, off, h, hidx, nA, n, cbar, gamma, \
-                       sgn, lane, gs);                                                                            \
+template <bool SG, int NJ>
+__device__ __forceinline__ void adj_endpoint(const double *__restrict__ fsrc, double *__restrict__ aout,
+                                             const double *__restrict__ a1, const double *__restrict__ Ms,
+                                             const double *__restrict__ Mc, double *__restrict__ dM,
+                                             const TgtInfo &ti, uint32_t J, int v, uint32_t slot, int qv, int h, int n,
+                                             double cbar, double gamma, int lane, double &gs) {
+    constexpr int kSplit = 6;   // at most 6 extensions' operands in registers at a time
+    const double o = fsrc[(size_t)slot * kLanes + lane];
+    const int vrow = v * n * kLanes + lane;
+    const uint32_t hlow = (1u << h) - 1u;
+    uint32_t jr = J;
+    double ob = 0.0, dv = 0.0;
+    if constexpr (NJ == 0) {
+        // full mask: the close into the sink only
+    } else if constexpr (NJ <= kSplit) {
+        adj_chunk<0, NJ>(a1, Ms, dM, ti, jr, hlow, vrow, o, lane, ob, qv, dv);
+    } else {
+        adj_chunk<0, kSplit>(a1, Ms, dM, ti, jr, hlow, vrow, o, lane, ob, qv, dv);
+        adj_chunk<kSplit, NJ>(a1, Ms, dM, ti, jr, hlow, vrow, o, lane, ob, qv, dv);
+    }
+    if (SG && qv >= 0) gs = fma(neg(dv), o, gs);   // sgn = -1
+    const int vh = vrow + h * kLanes;
+    ob = fma(cbar, Mc[vh], ob);
+    if ((__double_as_longlong(cbar) << 1) != 0) dM[vh] = fma(gamma, o, dM[vh]);
+    aout[(size_t)slot * kLanes + lane] = ob;
+}
+
+// MAXNJ: the largest order the kernel instance runs (larger counts are never dispatched).
+template <bool SG, int MAXNJ>
+__device__ __forceinline__ void adj_endpoint_dispatch(int nJ, const double *fsrc, double *aout, const double *a1,
+                                                      const double *Ms, const double *Mc, double *dM,
+                                                      const TgtInfo &ti, uint32_t J, int v, uint32_t slot, int qv,
+                                                      int h, int n, double cbar, double gamma, int lane, double &gs) {
+#define COS_AEP(K)                                                                                             \
+    case K:                                                                                                    \
+        if constexpr (K <= MAXNJ)                                                                              \
+            adj_endpoint<SG, K>(fsrc, aout, a1, Ms, Mc, dM, ti, J, v, slot, qv, h, n, cbar, gamma, lane, gs);   \
         break;
-    switch (nv) {
-        COS_AROW(1)
-        COS_AROW(2)
-        COS_AROW(3)
-        COS_AROW(4)
-        COS_AROW(5)
-        COS_AROW(6)
-        COS_AROW(7)
-        COS_AROW(8)
-        COS_AROW(9)
-        COS_AROW(10)
-        COS_AROW(11)
-        COS_AROW(12)
+    switch (nJ) {
+        COS_AEP(0)
+        COS_AEP(1)
+        COS_AEP(2)
+        COS_AEP(3)
+        COS_AEP(4)
+        COS_AEP(5)
+        COS_AEP(6)
+        COS_AEP(7)
+        COS_AEP(8)
+        COS_AEP(9)
+        COS_AEP(10)
+        COS_AEP(11)
+        COS_AEP(12)
         default:
             break;
     }
-#undef COS_AROW
+#undef COS_AEP
 }
 
-template <bool SG>
-__global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constant__ AdjArgs a) {
+// Warps own endpoint vertices (v % warps == warp) in the reverse sweep, so the dM accumulators
+// [v][j][lane] of the CTA have one writer per row v: one shared-memory copy, no atomics, each
+// entry summed in a fixed order (bitwise reproducible).  Every warp walks every mask of a layer
+// and takes the rows' endpoints it owns.  The forward recompute splits masks across warps as
+// in the forward kernel.  MAXT = 320 (orders <= 10, two CTAs per SM) or 384 (one CTA).
+template <bool SG, int MAXT>
+__global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(const __grid_constant__ AdjArgs a) {
     extern __shared__ __align__(16) double smem_d[];
     __shared__ int s_batch;
     __shared__ uint32_t s_base[kMaxLayers + 3];
-    __shared__ double s_red[8][kLanes];
+    __shared__ double s_red[MAXT / 32][kLanes];
     const DpArgs &f = a.f;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int nsm = f.smem_n * f.smem_n * kLanes;
-    double *Ms = smem_d;                               // extension matrices, shifted diagonal
-    double *Mc = smem_d + nsm;                         // close matrices times sgn w
-    double *gMw = smem_d + (size_t)nsm * (2 + warp);   // this warp's dM accumulators
+    double *Ms = smem_d;              // extension matrices, shifted diagonal
+    double *Mc = smem_d + nsm;        // close matrices times sgn w
+    double *dM = smem_d + 2 * nsm;    // dc/dM accumulators [v][j][lane]
     double *store = reinterpret_cast<double *>(f.scratch) + (size_t)blockIdx.x * (a.store_elems + 2 * a.adj_slot_elems);
     double *adj = store + a.store_elems;
     const int nfl = f.nf_lanes;
@@ -164,6 +158,7 @@ __global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constan
     const double sig = f.sigma[lam];
     const bool shifts = f.shifts != 0;
     const double cfac = sgn * f.loop_weight;
+    const bool unit_weight = f.loop_weight == 1.0;
     const int nbatch = *f.n_batches;
 
     for (;;) {
@@ -184,8 +179,8 @@ __global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constan
             const int v = e / n, j = e % n;
             Ms[e * kLanes + lane] = (v == j && j != 0 && shifts) ? val + sgn * sig : val;
             Mc[e * kLanes + lane] = cfac * val;
+            dM[e * kLanes + lane] = 0.0;
         }
-        for (int e = 0; e < n * n; ++e) gMw[e * kLanes + lane] = 0.0;
         if (threadIdx.x == 0) {
             uint32_t run = 0;
             for (int l = 0; l <= 2 * n + 2; ++l) {
@@ -206,7 +201,9 @@ __global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constan
                                  dst1, Ms, Mc, lane, ci, nfl, sgn, sig, shifts, active, lam, cfg, f.out, f.status, 1);
             __syncthreads();
         }
-        // reverse sweep
+        // reverse sweep: this warp's endpoints
+        uint32_t own = 0u;
+        for (int v = warp; v < n; v += nwarps) own |= 1u << v;
         const uint32_t full = (1u << n) - 1u;
         const double gout = active ? a.gout[cfg] : 0.0;
         double gs = 0.0;
@@ -215,13 +212,17 @@ __global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constan
             double *aout = adj + (size_t)(ell & 1) * a.adj_slot_elems;
             const double *a1 = adj + (size_t)((ell + 1) & 1) * a.adj_slot_elems;
             const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
-            for (uint32_t mi = warp; mi < cnt; mi += nwarps) {
+            for (uint32_t mi = 0; mi < cnt && own; ++mi) {
                 const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + first + mi));
-                const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, code = mk.y, off = mk.z;
+                const uint32_t A = mk.x & 0xFFFFu;
+                if (!(A & own)) continue;   // endpoints are visited vertices
+                const uint32_t B = mk.x >> 16, code = mk.y, off = mk.z;
                 const uint32_t ones = A & ~B;
                 const uint32_t H = head_set(B, ones);
                 const uint32_t J = full & ~B;
                 const int nA = __popc(A);
+                const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, lane);
+                const int nJ = __popc(J);
                 double cbar = 0.0;
                 if (B == full) {
                     cbar = ldexp(gout, n - 1);
@@ -232,29 +233,33 @@ __global__ void __launch_bounds__(256, 1) dp_adjoint_kernel(const __grid_constan
                     const int hi1 = __popc(head_set(B1, A & ~B1) & (bk - 1u));
                     const int ai1 = __popc(A & (bk - 1u));
                     const uint32_t off1 = __ldg(tab.rank3 + code + c_p3[k]);
-                    const double own = a1[(size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane];
-                    cbar = flavor_sum(own, nfl, ci);
-                    if (SG && ell == 1) gs = fma(sgn * 2.0, own, gs);   // shifted start, weight sgn 2 sigma
+                    const double seed = a1[(size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane];
+                    cbar = flavor_sum(seed, nfl, ci);
+                    // shifted start (mask e_0, owned by the warp of vertex 0), weight sgn 2 sigma
+                    if (SG && ell == 1) gs = fma(sgn * 2.0, seed, gs);
                 }
-                const double gamma = cfac * cbar;
+                // loop weight 1: sgn w Cbar is a sign flip (integer pipe), else one multiply
+                const double gamma = unit_weight ? neg(cbar) : cfac * cbar;
                 for (uint32_t hh = H; hh; hh &= hh - 1u) {
                     const int h = __ffs(hh) - 1;
                     const int hidx = __popc(H & ((1u << h) - 1u));
-                    const uint32_t Vrow = row_vmask(A, ones, h);
-                    adj_row_dispatch<SG>(__popc(Vrow), fsrc, aout, a1, Ms, Mc, gMw, tab.rank3, Vrow, A, B, J, code,
-                                         off, h, hidx, nA, n, cbar, gamma, sgn, lane, gs);
+                    const uint32_t rowoff = off + (uint32_t)(hidx * nA);
+                    for (uint32_t vv = row_vmask(A, ones, h) & own; vv; vv &= vv - 1u) {
+                        const int v = __ffs(vv) - 1;
+                        const uint32_t slot = rowoff + (uint32_t)__popc(A & ((1u << v) - 1u));
+                        // half-visited v >= 1: its index among the extensions (v is in J)
+                        const int qv = (SG && v != 0 && (ones & (1u << v))) ? __popc(J & ((1u << v) - 1u)) : -1;
+                        adj_endpoint_dispatch<SG, (MAXT <= 320 ? 10 : 12)>(nJ, fsrc, aout, a1, Ms, Mc, dM, ti, J, v, slot, qv, h, n, cbar,
+                                                                      gamma, lane, gs);
+                    }
                 }
             }
             __syncthreads();
         }
-        // dM: sum of the per-warp copies in warp order; dsigma: sum over warps
-        for (int e = warp; e < n * n; e += nwarps) {
-            double s = 0.0;
-            for (int w = 0; w < nwarps; ++w) s += smem_d[(size_t)nsm * (2 + w) + e * kLanes + lane];
-            if (active && a.gM) {
-                const int64_t gb = a.gmoff ? a.gmoff[cfg] : (int64_t)cfg * a.gmstride;
-                a.gM[gb + (int64_t)lam * n * n + e] = s;
-            }
+        // dM rows are final (every warp passed the last barrier); dsigma: sum over warps in order
+        if (active && a.gM) {
+            const int64_t gb = (a.gmoff ? a.gmoff[cfg] : (int64_t)cfg * a.gmstride) + (int64_t)lam * n * n;
+            for (int e = warp; e < n * n; e += nwarps) a.gM[gb + e] = dM[e * kLanes + lane];
         }
         if (SG) {
             s_red[warp][lane] = gs;
@@ -324,17 +329,9 @@ __global__ void chain_kernel(const double *__restrict__ dG, int L, int n_tau, do
     }
 }
 
-// Warps per adjoint CTA: two matrix copies plus one private dM copy per warp must fit the opt-in
-// shared memory, less a margin for the kernel's static shared arrays (about 2.2 KB).
-int adjoint_warps(int n_max, int device) {
-    int optin = 0;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    if (optin <= 0) optin = 227 * 1024;
-    const size_t per = (size_t)n_max * n_max * kLanes * sizeof(double);
-    const size_t cap = (size_t)optin - 4096;
-    int w = (int)(cap / per) - 2;
-    return std::max(1, std::min(8, w));
-}
+// Warps per adjoint CTA: one per vertex of the largest order (at least 4), so each warp owns one
+// endpoint in the reverse sweep.
+int adjoint_warps(int n_max) { return std::max(4, std::min(12, n_max)); }
 
 cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, double *gM, const int64_t *gmoff,
                           int64_t gmstride, double *gsig, cudaStream_t stream) {
@@ -350,11 +347,25 @@ cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, 
     const size_t store_elems = total_slots * kLanes;
     const size_t adj_slot_elems = (size_t)ho.max_slots * kLanes;
     const size_t per_cta = (store_elems + 2 * adj_slot_elems) * sizeof(double);
+    const int warps = adjoint_warps(L.n_max);
+    const int threads = warps * 32;
+    const size_t smem = (size_t)3 * L.n_max * L.n_max * kLanes * sizeof(double);
+    const bool sg = gsig != nullptr;
+    const bool big = threads > 320;
+    auto kern = sg ? (big ? dp_adjoint_kernel<true, 384> : dp_adjoint_kernel<true, 320>)
+                   : (big ? dp_adjoint_kernel<false, 384> : dp_adjoint_kernel<false, 320>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint smem attribute");
     int nsm = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
     const int cpb = kLanes / L.n_mat;
     const int max_batches = (L.n_cfg + cpb - 1) / cpb + COS_NMAX;
-    int grid = std::max(1, std::min(nsm, max_batches));
+    int grid = std::max(1, std::min(nsm * std::min(per_sm, 2), max_batches));
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
         const size_t avail = ws->scratch_bytes + (size_t)(0.85 * (double)free_b);
@@ -362,12 +373,6 @@ cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, 
     }
     cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "adjoint scratch");
     if (st != COS_OK) return st;
-    const int warps = adjoint_warps(L.n_max, ws->device);
-    const size_t smem = (size_t)(2 + warps) * L.n_max * L.n_max * kLanes * sizeof(double);
-    const bool sg = gsig != nullptr;
-    cudaError_t e = sg ? cudaFuncSetAttribute(dp_adjoint_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                       : cudaFuncSetAttribute(dp_adjoint_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "adjoint smem attribute");
     AdjArgs a;
     memset(&a, 0, sizeof a);
     DpArgs &f = a.f;
@@ -399,10 +404,7 @@ cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, 
     a.gsig = gsig;
     e = cudaMemsetAsync(ws->queue, 0, sizeof(int), stream);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
-    if (sg)
-        dp_adjoint_kernel<true><<<grid, warps * 32, smem, stream>>>(a);
-    else
-        dp_adjoint_kernel<false><<<grid, warps * 32, smem, stream>>>(a);
+    kern<<<grid, warps * 32, smem, stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
     return COS_OK;

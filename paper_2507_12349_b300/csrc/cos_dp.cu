@@ -36,9 +36,11 @@
 
 namespace cosdp {
 
-// Two register budgets: MAXT = 256 (two CTAs of up to 8 warps, <= 128 registers) and
-// MAXT = 512 (up to 16 warps; <= 128 registers in FP64 with one CTA, <= 64 in FP32 with two).
-template <typename T, int MAXT>
+// Register budgets: MAXT = 256 (two CTAs of up to 8 warps, <= 128 registers), MAXT = 384 (up to
+// 12 warps; FP32 two CTAs, <= 85 registers) and MAXT = 512 (up to 16 warps; <= 128 registers in
+// FP64 with one CTA, <= 64 in FP32 with two).
+// SUB: all-subsets mode (closes of masks with no half-visited vertex stored through csub_key).
+template <typename T, int MAXT, bool SUB>
 __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
     dp_forward_kernel(const __grid_constant__ DpArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
         if (active) Mc = a.M + (a.moff ? a.moff[cfg] : (int64_t)cfg * a.mstride) + (size_t)lam * n * n;
         double *cs = nullptr;
         int csh = 0;
-        if (a.csub && active) {
+        if (SUB && active) {
             const int64_t key = a.csub_key[cfg];
             cs = a.csub + (key >> 4);
             csh = (int)(key & 15);
@@ -101,9 +103,9 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
             const uint32_t first = tab.layer_first[ell];
             const uint32_t cnt = tab.layer_count[ell];
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
-                fwd_mask<T>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1,
+                fwd_mask<T, SUB>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1,
                             Ms, Md, lane, ci, nfl, sgn, sig, shifts, active, lam, cfg, a.out, a.status, a.prefetch,
-                            a.csub != nullptr, cs, csh);
+                            cs, csh);
             __syncthreads();
         }
     }
@@ -190,6 +192,12 @@ cos_status launch_plan_batches(Workspace *ws, int n_cfg, int n_max, const int32_
     return COS_OK;
 }
 
+template <typename T, bool SUB>
+static auto forward_kernel_for(int threads) {
+    return threads <= 256 ? dp_forward_kernel<T, 256, SUB>
+                          : (threads <= 384 ? dp_forward_kernel<T, 384, SUB> : dp_forward_kernel<T, 512, SUB>);
+}
+
 template <typename T>
 static cos_status launch_dp_t(Workspace *ws, const DpLaunch &L, cudaStream_t stream) {
     std::string err;
@@ -223,7 +231,7 @@ static cos_status launch_dp_t(Workspace *ws, const DpLaunch &L, cudaStream_t str
     const int threads = tu.warps * 32;
     const size_t msm = (size_t)L.n_max * L.n_max * kLanes;
     const size_t smem = ((msm * sizeof(T) + 15) & ~size_t(15)) + msm * sizeof(double);
-    auto kern = threads <= 256 ? dp_forward_kernel<T, 256> : dp_forward_kernel<T, 512>;
+    auto kern = L.csub ? forward_kernel_for<T, true>(threads) : forward_kernel_for<T, false>(threads);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "dp smem attribute");
     DpArgs a;
@@ -286,7 +294,7 @@ static cos_status launch_dp_raw_t(const RawBuffers &rb, const DpLaunch &L, cudaS
     const size_t msm = (size_t)L.n_max * L.n_max * kLanes;
     const size_t smem = ((msm * sizeof(T) + 15) & ~size_t(15)) + msm * sizeof(double);
     const int threads = tu.warps * 32;
-    auto kern = threads <= 256 ? dp_forward_kernel<T, 256> : dp_forward_kernel<T, 512>;
+    auto kern = L.csub ? forward_kernel_for<T, true>(threads) : forward_kernel_for<T, false>(threads);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "dp smem attribute");
     DpArgs a;
@@ -330,11 +338,11 @@ int dp_max_active_ctas(int precision, int threads, size_t smem) {
     int nb = 0;
     cudaError_t e;
     if (precision == COS_MIXED) {
-        auto k = threads <= 256 ? dp_forward_kernel<float, 256> : dp_forward_kernel<float, 512>;
+        auto k = forward_kernel_for<float, false>(threads);
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem);
     } else {
-        auto k = threads <= 256 ? dp_forward_kernel<double, 256> : dp_forward_kernel<double, 512>;
+        auto k = forward_kernel_for<double, false>(threads);
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem);
     }

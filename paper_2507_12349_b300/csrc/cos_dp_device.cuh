@@ -253,12 +253,14 @@ __device__ __forceinline__ void row_dispatch(int nv, const T *src, T *dst1, cons
 // One interaction mask of the forward sweep: every row, the flavor sum of the close, and
 // the seed of the next loop (or the sink).  `out` may be null (adjoint recomputation).
 // Ms: extension matrices (shifted diagonal); Md: FP64 close matrices times sgn * w.
-template <typename T>
+// SUBSETS: also close the masks with no half-visited vertex and store c(S) (all-subsets mode);
+// `csub` is this lane's output base (valid on active lanes), `cshift` the root's bit offset.
+template <typename T, bool SUBSETS = false>
 __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
                                          int n, const T *src, T *dst1, const T *Ms, const double *Md, int lane,
                                          int ci, int nfl, double sgn, double sig, bool shifts, bool active, int lam,
-                                         int cfg, double *out, int *status, int prefetch, bool subsets = false,
-                                         double *csub = nullptr, int cshift = 0) {
+                                         int cfg, double *out, int *status, int prefetch, double *csub = nullptr,
+                                         int cshift = 0) {
     const uint32_t full = (1u << n) - 1u;
     const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + mask_index));
     const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, code = mk.y, off = mk.z;
@@ -268,10 +270,9 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
     const int nA = __popc(A);
     // Closes feed a new loop (a half-visited vertex remains) or the sink (all full).  With no
     // half-visited vertex and untouched ones left, the cover of S = {mu_i = 2} is complete and
-    // connected: its close is c(S) (times 2^(1-|S|)), kept only in the all-subsets mode
-    // (`subsets` is warp-uniform; `csub` is this lane's output base, valid on active lanes).
+    // connected: its close is c(S) (times 2^(1-|S|)), kept only in the all-subsets mode.
     const bool dead = (ones == 0u) && (B != full);
-    const bool needclose = !dead || subsets;
+    const bool needclose = !dead || SUBSETS;
     if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
         // the next mask of this warp in the layer: start its loads while this one computes
         const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + next_index));
@@ -292,7 +293,7 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
     // Flavor sum of the loop-closing weight over the lanes of this configuration; the loop
     // factor sgn * w is already inside Md (the close's copy of the matrices).
     const double C = flavor_sum(csum, nfl, ci);
-    if (subsets && ones == 0u) {
+    if (SUBSETS && ones == 0u) {
         if (active && lam == 0) csub[(int64_t)B << cshift] = ldexp(C, __popc(B) - 1);
         if (dead) return;
     }
