@@ -54,7 +54,7 @@ def parse():
     p.add_argument("--n-cfg", type=int, default=0, help="smaller configuration count (profiling runs only)")
     p.add_argument("--workload", default=WORKLOAD, choices=sorted(I.WORKLOADS),
                    help="profiling runs only: run this workload's DP instead of the headline")
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"], help="profiling runs only")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "df64"], help="profiling runs only")
     p.add_argument("--grad", action="store_true",
                    help="profiling runs only: time the gradient call (adjoint DP) instead of the forward")
     return p.parse_args()
@@ -335,7 +335,8 @@ def native_arm(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32 extension / f64 close", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32 extension / f64 close",
+                                                       "df64": "f32 pairs (df64)"}[args.precision], "data": "synthetic",
         "config": {"workload": args.workload, "n": n_max, "n_flavors": w.model.n_flavors, "n_cfg_per_gpu": n_cfg,
                    "L": w.model.L, "beta": w.model.beta, "U": w.model.U, "mu": list(w.model.mu),
                    "alpha": list(w.model.alpha), "n_tau": w.model.n_tau, "precision": args.precision,
@@ -346,7 +347,8 @@ def native_arm(args):
                      "peak_source": peak_source, "probe_tflops": probe / 1e12,
                      "peak_nominal": NOMINAL_FP64_TFLOPS, "frac_of_nominal": achieved / 1e12 / NOMINAL_FP64_TFLOPS,
                      "kernel": ("dp_adjoint_kernel<sigma grad>" if args.grad else
-                                "dp_forward_kernel<%s>" % ("double" if args.precision == "fp64" else "float")),
+                                "dp_forward_kernel<%s>" % {"fp64": "double", "mixed": "float",
+                                                           "df64": "df64"}[args.precision]),
                      "flops_per_launch": flops_launch,
                      "launch_ms": dp_avg * 1e3,
                      "traffic": (HEADLINE_DRAM_BYTES_PER_CFG * n_cfg
@@ -455,7 +457,8 @@ def measure_subsets(torch, B, flush_buf, n_cfg):
 
 
 def measure_forms(torch, B, flush_buf):
-    """The other forms of the path on the same GPU: FP64 vs mixed precision at orders 8 and 10,
+    """The other forms of the path on the same GPU: FP64 vs mixed vs double-float (df64)
+    precision at orders 8 and 10,
     the uneven-order batch as one persistent launch in a CUDA graph (autotuned shapes), the
     adjoint, and the plain FP64 form with one configuration per launch.  Returns the
     measurements and the GPU outputs kept for the oracle leg's error statistics."""
@@ -495,6 +498,10 @@ def measure_forms(torch, B, flush_buf):
     res["su3_shift_n10_mixed"], keep_n10 = run("su3_shift_mixed_n10", 100_000, "mixed")
     keep["su3_shift_n10_mixed_vs_fp64_oracle"] = ("su3_shift_mixed_n10", keep_n10)
     res["su3_shift_n10_fp64"], _ = run("su3_shift_mixed_n10", 100_000, "fp64", steps=1)
+    res["su4_n8_df64"], keep_df8 = run("su4_mu_broken_n8", 100_000, "df64")
+    keep["su4_n8_df64_vs_fp64_oracle"] = ("su4_mu_broken_n8", keep_df8)
+    res["su3_shift_n10_df64"], keep_df10 = run("su3_shift_mixed_n10", 100_000, "df64", steps=1)
+    keep["su3_shift_n10_df64_vs_fp64_oracle"] = ("su3_shift_mixed_n10", keep_df10)
     res["su6_uneven_n4_12_fp64_graph"], _ = run("su6_sym_uneven_n4_12", 200_000, "fp64", steps=1, graph=True)
     res["su4_n10_adjoint"] = measure_adjoint(torch, B, flush_buf, 50_000)
     res["su4_n8_all_subsets_fp64"] = measure_subsets(torch, B, flush_buf, 100_000)

@@ -58,8 +58,17 @@ typedef enum {
 
 typedef enum {
     COS_FP64 = 0,   /* every step in FP64 */
-    COS_MIXED = 1   /* clow extension in FP32 with FP32 accumulation; loop-closing
+    COS_MIXED = 1,  /* clow extension in FP32 with FP32 accumulation; loop-closing
                        sums, seeds of new loops and the sink in FP64 */
+    COS_DF64 = 2    /* double-float: states, matrices, extension and loop-closing sums as
+                       unevaluated pairs hi + lo of FP32 numbers (about 48 bits), each dot
+                       product a compensated (TwoSum / FMA TwoProduct) accumulation on the
+                       FP32 pipe; only the output is formed in FP64.  The paper answers
+                       cancellation with software extended precision (double-double, at 3-5x
+                       the cost: Methods, fast generation of 3^n minors; Discussion); this is
+                       that remedy mapped onto B300's FP32 units, which retire 64 lane
+                       operations for each FP64 one.  Forward entry points only (the
+                       gradient is FP64). */
 } cos_precision;
 
 /* Square-lattice model (Methods A): dispersion

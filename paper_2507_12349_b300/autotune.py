@@ -22,6 +22,7 @@ CASES = [
     (8, 4, 1, False, "fp64"), (8, 4, 1, False, "mixed"),
     (10, 3, 1, True, "mixed"), (10, 3, 1, True, "fp64"),
     (10, 4, 1, False, "fp64"),
+    (8, 4, 1, False, "df64"), (10, 3, 1, True, "df64"),
 ] + [(n, 1, 6, False, "fp64") for n in range(4, 13)]
 
 

@@ -19,7 +19,8 @@ COS_NMAX = 12
 COS_MAX_FLAVORS = 8
 COS_FP64 = 0
 COS_MIXED = 1
-PRECISIONS = {"fp64": COS_FP64, "mixed": COS_MIXED}
+COS_DF64 = 2
+PRECISIONS = {"fp64": COS_FP64, "mixed": COS_MIXED, "df64": COS_DF64}
 
 STATUS = {0: "COS_OK", -1: "COS_ERR_ARG", -2: "COS_ERR_ORDER", -3: "COS_ERR_CUDA", -4: "COS_ERR_TIMEOUT",
           -5: "COS_ERR_NONFINITE", -6: "COS_ERR_UNIMPLEMENTED", -7: "COS_ERR_NOMEM"}

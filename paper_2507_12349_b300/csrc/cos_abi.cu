@@ -195,7 +195,7 @@ cos_status check_common(int n_cfg, int n_max, cos_precision prec, const char *fn
         set_error(std::string(fn) + ": n_max outside [1, 12]");
         return COS_ERR_ORDER;
     }
-    if (prec != COS_FP64 && prec != COS_MIXED) {
+    if (prec != COS_FP64 && prec != COS_MIXED && prec != COS_DF64) {
         set_error(std::string(fn) + ": unknown precision");
         return COS_ERR_ARG;
     }

@@ -31,10 +31,24 @@
 // batches (each one read in a batch is written earlier in that batch).
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "cos_dp_device.cuh"
 
 namespace cosdp {
+
+// State type -> close-matrix type and conversions from the FP64 inputs (once per batch).
+template <typename T>
+struct CloseOf {
+    using type = double;
+};
+template <>
+struct CloseOf<df64> {
+    using type = df64;
+};
+__device__ __forceinline__ void to_elem(double x, double &r) { r = x; }
+__device__ __forceinline__ void to_elem(double x, float &r) { r = (float)x; }
+__device__ __forceinline__ void to_elem(double x, df64 &r) { r = df64_from(x); }
 
 // Register budgets: MAXT = 256 (two CTAs of up to 8 warps, <= 128 registers), MAXT = 384 (up to
 // 12 warps; FP32 two CTAs, <= 85 registers) and MAXT = 512 (up to 16 warps; <= 128 registers in
@@ -51,9 +65,11 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
     const int nsm = a.smem_n * a.smem_n * kLanes;
     // Ms: matrices for the extension (state type); Md: FP64 matrices times the loop factor
     // sgn * w for the close (so the close needs no extra multiply per mask).
+    using CT = typename CloseOf<T>::type;
+    constexpr bool kDf = std::is_same<T, df64>::value;
     T *Ms = reinterpret_cast<T *>(smem_raw);
-    double *Mdw = reinterpret_cast<double *>(smem_raw + ((nsm * sizeof(T) + 15) & ~size_t(15)));
-    const double *Md = Mdw;
+    CT *Mdw = reinterpret_cast<CT *>(smem_raw + ((nsm * sizeof(T) + 15) & ~size_t(15)));
+    const CT *Md = Mdw;
     T *ring = reinterpret_cast<T *>(a.scratch) + (size_t)blockIdx.x * a.nslots * a.slot_elems;
     const int nfl = a.nf_lanes;
     const int lam = lane % nfl;
@@ -62,6 +78,8 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
     const double sig = a.absmode ? fabs(a.sigma[lam]) : a.sigma[lam];
     const bool shifts = a.shifts != 0;
     const int nbatch = *a.n_batches;
+    df64 seed0 = {0.0f, 0.0f};
+    if (kDf) seed0 = df64_from(sgn * 2.0 * sig);
 
     for (;;) {
         __syncthreads();  // previous batch fully done before s_batch / smem are reused
@@ -90,11 +108,11 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
             double val = active ? Mc[e] : 0.0;
             if (a.absmode) val = fabs(val);
             const int v = e / n, j = e % n;
-            Ms[e * kLanes + lane] = (T)((v == j && j != 0 && shifts) ? val + dshift : val);
-            Mdw[e * kLanes + lane] = cfac * val;
+            to_elem((v == j && j != 0 && shifts) ? val + dshift : val, Ms[e * kLanes + lane]);
+            to_elem(cfac * val, Mdw[e * kLanes + lane]);
         }
         // Start: the loop through the normal point of vertex 0 (layer 1, mask e_0, slot 0).
-        if (warp == 0) ring[(1 % a.nslots) * a.slot_elems + lane] = T(1);
+        if (warp == 0) to_elem(1.0, ring[(1 % a.nslots) * a.slot_elems + lane]);
         __syncthreads();
 
         for (int ell = 1; ell <= 2 * n; ++ell) {
@@ -102,10 +120,15 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
             T *dst1 = ring + (size_t)((ell + 1) % a.nslots) * a.slot_elems;
             const uint32_t first = tab.layer_first[ell];
             const uint32_t cnt = tab.layer_count[ell];
-            for (uint32_t mi = warp; mi < cnt; mi += nwarps)
-                fwd_mask<T, SUB>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1,
-                            Ms, Md, lane, ci, nfl, sgn, sig, shifts, active, lam, cfg, a.out, a.status, a.prefetch,
-                            cs, csh);
+            for (uint32_t mi = warp; mi < cnt; mi += nwarps) {
+                const uint32_t next = mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu;
+                if constexpr (kDf)
+                    fwd_mask_df<SUB>(tab, first + mi, next, ell, n, src, dst1, Ms, Md, lane, ci, nfl, seed0, shifts,
+                                     active, lam, cfg, a.out, a.status, a.prefetch, cs, csh);
+                else
+                    fwd_mask<T, SUB>(tab, first + mi, next, ell, n, src, dst1, Ms, Md, lane, ci, nfl, sgn, sig, shifts,
+                                     active, lam, cfg, a.out, a.status, a.prefetch, cs, csh);
+            }
             __syncthreads();
         }
     }
@@ -230,7 +253,7 @@ static cos_status launch_dp_t(Workspace *ws, const DpLaunch &L, cudaStream_t str
     if (st != COS_OK) return st;
     const int threads = tu.warps * 32;
     const size_t msm = (size_t)L.n_max * L.n_max * kLanes;
-    const size_t smem = ((msm * sizeof(T) + 15) & ~size_t(15)) + msm * sizeof(double);
+    const size_t smem = ((msm * sizeof(T) + 15) & ~size_t(15)) + msm * sizeof(typename CloseOf<T>::type);
     auto kern = L.csub ? forward_kernel_for<T, true>(threads) : forward_kernel_for<T, false>(threads);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "dp smem attribute");
@@ -292,7 +315,7 @@ template <typename T>
 static cos_status launch_dp_raw_t(const RawBuffers &rb, const DpLaunch &L, cudaStream_t stream) {
     const Tuning tu = get_tuning(L.n_max, L.precision, L.n_mat);
     const size_t msm = (size_t)L.n_max * L.n_max * kLanes;
-    const size_t smem = ((msm * sizeof(T) + 15) & ~size_t(15)) + msm * sizeof(double);
+    const size_t smem = ((msm * sizeof(T) + 15) & ~size_t(15)) + msm * sizeof(typename CloseOf<T>::type);
     const int threads = tu.warps * 32;
     auto kern = L.csub ? forward_kernel_for<T, true>(threads) : forward_kernel_for<T, false>(threads);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -331,6 +354,7 @@ static cos_status launch_dp_raw_t(const RawBuffers &rb, const DpLaunch &L, cudaS
 
 cos_status launch_dp_raw(const RawBuffers &rb, const DpLaunch &L, cudaStream_t stream) {
     if (L.precision == COS_MIXED) return launch_dp_raw_t<float>(rb, L, stream);
+    if (L.precision == COS_DF64) return launch_dp_raw_t<df64>(rb, L, stream);
     return launch_dp_raw_t<double>(rb, L, stream);
 }
 
@@ -339,6 +363,10 @@ int dp_max_active_ctas(int precision, int threads, size_t smem) {
     cudaError_t e;
     if (precision == COS_MIXED) {
         auto k = forward_kernel_for<float, false>(threads);
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem);
+    } else if (precision == COS_DF64) {
+        auto k = forward_kernel_for<df64, false>(threads);
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem);
     } else {
@@ -351,6 +379,7 @@ int dp_max_active_ctas(int precision, int threads, size_t smem) {
 
 cos_status launch_dp(Workspace *ws, const DpLaunch &L, cudaStream_t stream) {
     if (L.precision == COS_MIXED) return launch_dp_t<float>(ws, L, stream);
+    if (L.precision == COS_DF64) return launch_dp_t<df64>(ws, L, stream);
     return launch_dp_t<double>(ws, L, stream);
 }
 

@@ -1,6 +1,7 @@
 // Device code shared by the forward and adjoint DP kernels (see cos_dp.cu for the scheme).
 #pragma once
 
+#include "cos_df64.cuh"
 #include "cos_internal.h"
 
 namespace cosdp {
@@ -312,6 +313,164 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
         else *tp = tv;
     } else if (active && lam == 0 && out) {
         const double c = ldexp(C, n - 1);
+        out[cfg] = c;
+        if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
+    }
+}
+
+// ------------------------------------------------------------------ double-float (df64) sweep
+// The same row and mask steps with df64 states and matrices: every extension dot product and
+// the loop-closing sum are Dot2 accumulations on the FP32 pipe (cos_df64.cuh); the flavor sum,
+// the seeds and the sink stay in df64; only the sink's output is formed in FP64.
+
+// Target slot of extension q for the row with head h, computed lane-parallel once per row
+// (lane q holds the slot of the q-th extension; read back with one shuffle per push).
+__device__ __forceinline__ uint32_t row_target_slot(const TgtInfo &ti, uint32_t hlow) {
+    const uint32_t ai1 = ti.meta & 15u, nA1 = (ti.meta >> 4) & 15u;
+    const uint32_t hi1 = (uint32_t)__popc((ti.meta >> 16) & hlow);
+    return ti.off1 + hi1 * nA1 + ai1;
+}
+
+// The accumulator is stored as it stands (s, c): s + c is the value exactly, and an
+// unnormalized pair only makes the next layer's dropped lo*lo term relative to the mass
+// rather than to the state, which is the error model of this mode anyway.
+__device__ __forceinline__ void push_target_df(df64 *__restrict__ dst1, uint32_t tslot, int q, const DotAcc &d,
+                                               int lane) {
+    const uint32_t slot = __shfl_sync(0xFFFFFFFFu, tslot, q);
+    df64 v;
+    v.hi = d.s;
+    v.lo = d.c;
+    dst1[(size_t)slot * kLanes + lane] = v;
+}
+
+template <int NV>
+__device__ __forceinline__ void do_row_df(const df64 *__restrict__ src, df64 *__restrict__ dst1,
+                                          const df64 *__restrict__ Ms, const df64 *__restrict__ Md,
+                                          const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow, uint32_t A,
+                                          uint32_t off, int h, int hidx, int nA, int n, bool needclose, int lane,
+                                          DotAcc &csum) {
+    df64 o[NV];
+    int vs[NV];
+    const df64 *row = src + (size_t)(off + (uint32_t)(hidx * nA)) * kLanes + lane;
+    uint32_t vv = Vrow;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+        const int v = __ffs(vv) - 1;
+        vv &= vv - 1u;
+        o[t] = row[__popc(A & ((1u << v) - 1u)) * kLanes];
+        vs[t] = v * n * kLanes + lane;
+    }
+    if (needclose) {
+#pragma unroll
+        for (int t = 0; t < NV; ++t) dot_add(csum, o[t], Md[vs[t] + h * kLanes]);
+    }
+    const uint32_t tslot = row_target_slot(ti, (1u << h) - 1u);
+    uint32_t jj = J;
+    int q = 0;
+    for (; q + 1 < nJ; q += 2) {
+        const int ja = __ffs(jj) - 1;
+        jj &= jj - 1u;
+        const int jb = __ffs(jj) - 1;
+        jj &= jj - 1u;
+        DotAcc da = dot_first(o[0], Ms[vs[0] + ja * kLanes]);
+        DotAcc db = dot_first(o[0], Ms[vs[0] + jb * kLanes]);
+#pragma unroll
+        for (int t = 1; t < NV; ++t) {
+            dot_add(da, o[t], Ms[vs[t] + ja * kLanes]);
+            dot_add(db, o[t], Ms[vs[t] + jb * kLanes]);
+        }
+        push_target_df(dst1, tslot, q, da, lane);
+        push_target_df(dst1, tslot, q + 1, db, lane);
+    }
+    if (q < nJ) {
+        const int j = __ffs(jj) - 1;
+        DotAcc d = dot_first(o[0], Ms[vs[0] + j * kLanes]);
+#pragma unroll
+        for (int t = 1; t < NV; ++t) dot_add(d, o[t], Ms[vs[t] + j * kLanes]);
+        push_target_df(dst1, tslot, q, d, lane);
+    }
+}
+
+__device__ __forceinline__ void row_dispatch_df(int nv, const df64 *src, df64 *dst1, const df64 *Ms, const df64 *Md,
+                                                const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow, uint32_t A,
+                                                uint32_t off, int h, int hidx, int nA, int n, bool needclose,
+                                                int lane, DotAcc &csum) {
+#define COS_ROW_DF(K)                                                                                          \
+    case K:                                                                                                    \
+        do_row_df<K>(src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, csum);       \
+        break;
+    switch (nv) {
+        COS_ROW_DF(1)
+        COS_ROW_DF(2)
+        COS_ROW_DF(3)
+        COS_ROW_DF(4)
+        COS_ROW_DF(5)
+        COS_ROW_DF(6)
+        COS_ROW_DF(7)
+        COS_ROW_DF(8)
+        COS_ROW_DF(9)
+        COS_ROW_DF(10)
+        COS_ROW_DF(11)
+        COS_ROW_DF(12)
+        default:
+            break;
+    }
+#undef COS_ROW_DF
+}
+
+// One interaction mask of the df64 forward sweep (twin of fwd_mask).  seed0 = sgn 2 sigma as
+// df64 (the shifted start at vertex 0, added at layer 1 when shifts are on).
+template <bool SUBSETS = false>
+__device__ __forceinline__ void fwd_mask_df(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
+                                            int n, const df64 *src, df64 *dst1, const df64 *Ms, const df64 *Md,
+                                            int lane, int ci, int nfl, df64 seed0, bool shifts, bool active, int lam,
+                                            int cfg, double *out, int *status, int prefetch, double *csub = nullptr,
+                                            int cshift = 0) {
+    const uint32_t full = (1u << n) - 1u;
+    const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + mask_index));
+    const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, code = mk.y, off = mk.z;
+    const uint32_t ones = A & ~B;
+    const uint32_t H = head_set(B, ones);
+    const uint32_t J = full & ~B;
+    const int nA = __popc(A);
+    const bool dead = (ones == 0u) && (B != full);
+    const bool needclose = !dead || SUBSETS;
+    if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
+        const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + next_index));
+        const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
+        prefetch_block(reinterpret_cast<const double *>(src), nk.z,
+                       (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane, prefetch);
+    }
+    DotAcc csum = {0.0f, 0.0f};
+    const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, lane);
+    const int nJ = __popc(J);
+    for (uint32_t hh = H; hh; hh &= hh - 1u) {
+        const int h = __ffs(hh) - 1;
+        const int hidx = __popc(H & ((1u << h) - 1u));
+        const uint32_t Vrow = row_vmask(A, ones, h);
+        row_dispatch_df(__popc(Vrow), src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane,
+                        csum);
+    }
+    if (!needclose) return;
+    const df64 C = df64_flavor_sum(dot_value(csum), nfl, ci);
+    if (SUBSETS && ones == 0u) {
+        if (active && lam == 0) csub[(int64_t)B << cshift] = ldexp(df64_to_double(C), __popc(B) - 1);
+        if (dead) return;
+    }
+    if (ones) {
+        const int k = __ffs(ones) - 1;
+        const uint32_t bk = 1u << k;
+        const uint32_t B1 = B | bk;
+        const int hi1 = __popc(head_set(B1, A & ~B1) & (bk - 1u));
+        const int ai1 = __popc(A & (bk - 1u));
+        const uint32_t off1 = __ldg(tab.rank3 + code + c_p3[k]);
+        df64 *tp = dst1 + (size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane;
+        df64 val = C;
+        if (ell == 1 && shifts) val = df64_add(val, seed0);   // vertex 0 carries a shift point
+        if (k == 0) *tp = df64_add(*tp, val);                // the extension into 0' wrote it
+        else *tp = val;
+    } else if (active && lam == 0 && out) {
+        const double c = ldexp(df64_to_double(C), n - 1);
         out[cfg] = c;
         if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
     }

@@ -97,7 +97,7 @@ extern "C" cos_status cos_connected_sum_matrices_noalloc(int n_cfg, int n_max, c
                                                          double *d_abs_mass, cos_stream_t stream) {
     const char *fn = "cos_connected_sum_matrices_noalloc";
     if (n_cfg < 0 || n_mat < 1 || n_mat > COS_MAX_FLAVORS || loop_weight < 1 ||
-        (precision != COS_FP64 && precision != COS_MIXED)) {
+        (precision != COS_FP64 && precision != COS_MIXED && precision != COS_DF64)) {
         set_error(std::string(fn) + ": invalid argument");
         return COS_ERR_ARG;
     }

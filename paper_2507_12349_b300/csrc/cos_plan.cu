@@ -219,7 +219,7 @@ extern "C" cos_status cos_plan_destroy(cos_plan *p) {
 extern "C" cos_status cos_set_tuning(int n, cos_precision precision, int n_mat, int warps, int ctas_per_sm,
                                      int prefetch) {
     if (n < 1 || n > COS_NMAX || n_mat < 1 || n_mat > COS_MAX_FLAVORS || warps < 1 || warps > 16 ||
-        ctas_per_sm < 1 || ctas_per_sm > 8 || (precision != COS_FP64 && precision != COS_MIXED)) {
+        ctas_per_sm < 1 || ctas_per_sm > 8 || (precision != COS_FP64 && precision != COS_MIXED && precision != COS_DF64)) {
         set_error("cos_set_tuning: out of range");
         return COS_ERR_ARG;
     }
@@ -248,7 +248,7 @@ extern "C" cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts
                                    int n_cfg, cos_stream_t stream, int *best_warps, int *best_ctas,
                                    int *best_prefetch, double *best_ms) {
     if (n < 1 || n > COS_NMAX || n_mat < 1 || n_mat > COS_MAX_FLAVORS || loop_weight < 1 || n_cfg < 1 ||
-        (precision != COS_FP64 && precision != COS_MIXED)) {
+        (precision != COS_FP64 && precision != COS_MIXED && precision != COS_DF64)) {
         set_error("cos_autotune: out of range");
         return COS_ERR_ARG;
     }

@@ -7,6 +7,13 @@ Tolerances
     bound, the same DP on |M|): |err| <= 2^-53 * 64 n * mass, a few ulps per
     visited point of every term.
   * DP, mixed: |err| <= (2n + log2(32 n)) * 2^-24 * mass (FP32 extension, FP64 close).
+  * DP, df64 (FP32 pairs, compensated dot products): |err| <= (16 n^2 + 64 n) * 2^-48 * mass.
+    Per dot product of K <= n terms: the matrices' df64 split (2^-48 relative), the FP32
+    error accumulator c (of size <= 3K 2^-24 sum|terms|) rounded K times (3K 2^-48), and the
+    dropped lo*lo cross terms, whose state part is c of the previous layer (3K 2^-48
+    relative to the mass): together <= (7K + 2) 2^-48 sum|terms|.  The 2n layers add these
+    relative to the mass; the flavor sums and seeds (df64 additions, <= 2^-45 of their
+    operands' magnitudes) add at most 32 n 2^-48.
 """
 import math
 
@@ -32,6 +39,10 @@ def fp64_bound(n, mass):
 
 def mixed_bound(n, mass):
     return (2 * n + math.log2(32 * n)) * EPS32 * mass
+
+
+def df64_bound(n, mass):
+    return (16 * n * n + 64 * n) * 2.0 ** -48 * mass
 
 
 def run_matrices(Ms_list, n_mat, loop_weight, sigma, precision="fp64", abs_mass=False):
@@ -148,6 +159,34 @@ def test_dp_mixed_within_bound(n, n_mat, wt, shifts, ncfg):
         assert abs(got[c] - ref) <= mixed_bound(n, rmass), (c, got[c], ref, rmass)
 
 
+@pytest.mark.parametrize("n,n_mat,wt,shifts,ncfg", CASES)
+def test_dp_df64_matches_oracle(n, n_mat, wt, shifts, ncfg):
+    Ms = rand_mats(700 + n * 7 + n_mat, ncfg, n_mat, n)
+    sig = list(np.linspace(-0.2, 0.15, n_mat)) if shifts else None
+    got, mass = run_matrices(Ms, n_mat, wt, sig, precision="df64", abs_mass=True)
+    for c in range(ncfg):
+        ref = O.dp(Ms[c], sig, weight=wt, prec="ld")
+        rmass = O.dp(Ms[c], sig, weight=wt, absmode=True)
+        assert abs(got[c] - ref) <= df64_bound(n, rmass), (c, got[c], ref, rmass)
+        assert abs(mass[c] - rmass) <= df64_bound(n, rmass), (c, mass[c], rmass)
+
+
+def test_dp_df64_uneven_orders_and_max_order():
+    """Orders 1..12 in one launch (order 12 at the structure's largest layers); the order-12
+    configurations are checked against the oracle in double, whose own error is far below
+    the df64 bound at this mass."""
+    rng = np.random.default_rng(8)
+    orders = rng.integers(1, 10, size=80)
+    orders[:3] = [12, 11, 10]
+    Ms = [I.random_matrices(int(2000 + c), 1, 3, int(n), 0.9)[0] for c, n in enumerate(orders)]
+    sig = [0.07, 0.0, -0.11]
+    got, _ = run_matrices(Ms, 3, 1, sig, precision="df64")
+    for c in list(range(3)) + list(range(3, 80, 9)):
+        ref = O.dp(Ms[c], sig, prec="ld" if orders[c] <= 10 else "d")
+        rmass = O.dp(Ms[c], sig, absmode=True)
+        assert abs(got[c] - ref) <= df64_bound(int(orders[c]), rmass), (c, orders[c], got[c], ref)
+
+
 def test_dp_uneven_orders_one_launch():
     rng = np.random.default_rng(5)
     orders = rng.integers(1, 10, size=150)
@@ -219,11 +258,13 @@ def workload_check(name, n_cfg, sample, prec="fp64", rel=1e-10):
         n = int(cfgs.order[c])
         ref = O.dp(M, sig, weight=wt, prec="ld")
         rmass = O.dp(M, sig, weight=wt, absmode=True)
-        assert gmass[c] == pytest.approx(rmass, rel=1e-10)
+        assert gmass[c] == pytest.approx(rmass, rel=1e-10 if prec != "mixed" else 1e-5)
         e = abs(got[c] - ref)
         errs.append(e / abs(ref))
         if prec == "fp64":
             assert e <= max(rel * abs(ref), fp64_bound(n, rmass)), (c, n, got[c], ref, rmass)
+        elif prec == "df64":
+            assert e <= df64_bound(n, rmass), (c, n, got[c], ref, rmass)
         else:
             assert e <= mixed_bound(n, rmass), (c, n, got[c], ref, rmass)
     tabs.close()
@@ -250,3 +291,11 @@ def test_workload_su3_fp64_order10_sampled():
 
 def test_workload_su6_uneven_sampled():
     workload_check("su6_sym_uneven_n4_12", 3_000, 12)
+
+
+def test_workload_su4_df64_order8_sampled():
+    workload_check("su4_mu_broken_n8", 20_000, 40, prec="df64")
+
+
+def test_workload_su3_df64_order10_sampled():
+    workload_check("su3_shift_mixed_n10", 1_000, 4, prec="df64")

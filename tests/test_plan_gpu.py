@@ -40,7 +40,8 @@ def test_batch_plan_matches_direct_call_uneven_orders():
     tabs.close()
 
 
-def test_matrices_plan_with_shifts_and_mass():
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_matrices_plan_with_shifts_and_mass(prec):
     n, n_mat, ncfg = 7, 3, 100
     Ms = I.random_matrices(3, ncfg, n_mat, n, 0.9)
     order = torch.full((ncfg,), n, dtype=torch.int32, device="cuda")
@@ -48,9 +49,9 @@ def test_matrices_plan_with_shifts_and_mass():
     M = torch.tensor(Ms.ravel(), device="cuda")
     sig = [0.1, -0.2, 0.05]
     ref, refm = (torch.empty(ncfg, dtype=torch.float64, device="cuda") for _ in range(2))
-    B.cos_connected_sum_matrices(n, order, moff, n_mat, 1, sig, M, "fp64", ref, refm)
+    B.cos_connected_sum_matrices(n, order, moff, n_mat, 1, sig, M, prec, ref, refm)
     out, mass = (torch.empty_like(ref) for _ in range(2))
-    plan = B.cos_plan_create_matrices(n, order, moff, n_mat, 1, sig, M, "fp64", out, mass)
+    plan = B.cos_plan_create_matrices(n, order, moff, n_mat, 1, sig, M, prec, out, mass)
     out.zero_(); mass.zero_()
     plan.launch()
     plan.status()

@@ -39,7 +39,7 @@ def _case(seed, ncfg, n_mat, orders):
     return (torch.tensor(order, device="cuda"), torch.tensor(moff, device="cuda"), torch.tensor(flat, device="cuda"))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "df64"])
 def test_noalloc_matches_regular_entry_on_two_calls(prec):
     calls = [  # (seed, configurations, matrices per configuration, loop weight, sigma, orders)
         (11, 77, 3, 1, [0.1, 0.0, -0.08], [5, 7, 8]),
@@ -58,8 +58,10 @@ def test_noalloc_matches_regular_entry_on_two_calls(prec):
         r, g, m = ref.cpu().numpy(), got.cpu().numpy(), ref_mass.cpu().numpy()
         n = order.cpu().numpy()
         # same tolerance as the parity tests, stated against the absolute mass
-        eps = 2.0 ** -53 if prec == "fp64" else 2.0 ** -24
-        tol = 64 * n * eps * m
+        if prec == "df64":
+            tol = (16 * n * n + 64 * n) * 2.0 ** -48 * m
+        else:
+            tol = 64 * n * (2.0 ** -53 if prec == "fp64" else 2.0 ** -24) * m
         assert np.all(np.isfinite(g))
         assert np.all(np.abs(g - r) <= tol)
         assert np.allclose(got_mass.cpu().numpy(), m, rtol=1e-12)
