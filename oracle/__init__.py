@@ -19,6 +19,11 @@ Functions and the passages they follow:
 * ``propagators`` -- G0 tables by the plain momentum sum of Methods A, the
   linear interpolation in tau and the gather into M.
 * ``torch_brute`` -- the brute-force sum as dense torch ops, for autograd.
+* ``bip``      -- bipartite (two-sublattice) connected sums: the sum over every
+  sublattice assignment of a single-assignment route (Methods A, strategy (i)),
+  or the sublattice-resolved merged DP of Alg. 1-2 (``method="dp4"``).
+* ``dp``, ``closed``, ``brute`` also take per-(flavor, vertex) shift weights
+  (``sigma`` of shape [nf][n]).
 
 Precision: 'd' (double), 'ld' (x87 long double) or 'q' (__float128).
 """
@@ -52,6 +57,22 @@ def lib():
             f = getattr(L, "dp" + sfx)
             f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp_, dp_, ctypes.c_int, dp_, dp_]
             f.restype = ctypes.c_int
+            for name in ("brute_v",):
+                f = getattr(L, name + sfx)
+                f.argtypes = [ctypes.c_int, ctypes.c_int, dp_, dp_, ctypes.c_int, dp_, dp_]
+                f.restype = ctypes.c_int
+            f = getattr(L, "closed_v" + sfx)
+            f.argtypes = [ctypes.c_int, ctypes.c_int, dp_, dp_, dp_, dp_, dp_, dp_]
+            f.restype = ctypes.c_int
+            f = getattr(L, "dp_v" + sfx)
+            f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp_, dp_, ctypes.c_int, dp_, dp_]
+            f.restype = ctypes.c_int
+            f = getattr(L, "bip_sum" + sfx)
+            f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp_, dp_, ctypes.c_int, ctypes.c_int, dp_, dp_]
+            f.restype = ctypes.c_int
+            f = getattr(L, "bip_dp4" + sfx)
+            f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp_, dp_, ctypes.c_int, dp_, dp_]
+            f.restype = ctypes.c_int
             f = getattr(L, "dp_batch" + sfx)
             f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp_, dp_, ctypes.c_int,
                           dp_, dp_, ctypes.c_int]
@@ -70,6 +91,19 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
 
 
+def _sigma(sigma, nf: int, n: int):
+    """Shift weights as a contiguous array and whether they are per (flavor, vertex):
+    None, nf values (per flavor) or an [nf][n] array (per flavor and vertex)."""
+    if sigma is None:
+        return None, False
+    sig = _f64(sigma)
+    if sig.ndim == 2:
+        if sig.shape != (nf, n):
+            raise ValueError("per-vertex sigma must have shape [nf][n]")
+        return np.ascontiguousarray(sig.ravel()), True
+    return sig, False
+
+
 def tiled(M: np.ndarray) -> np.ndarray:
     """Point matrices [nf][2n][2n] from vertex matrices [nf][n][n]: the
     2n x 2n matrix indexed by vertex = point mod n (Alg. 3's A_l indexing)."""
@@ -84,9 +118,9 @@ def brute(A_points: np.ndarray, sigma: Optional[Sequence[float]] = None, connect
     A = _f64(A_points)
     nf, np2, _ = A.shape
     n = np2 // 2
-    sig = None if sigma is None else _f64(sigma)
+    sig, v = _sigma(sigma, nf, n)
     hi, lo = ctypes.c_double(), ctypes.c_double()
-    rc = getattr(lib(), "brute_" + prec)(n, nf, _ptr(A), _ptr(sig), int(connected),
+    rc = getattr(lib(), ("brute_v_" if v else "brute_") + prec)(n, nf, _ptr(A), _ptr(sig), int(connected),
                                           ctypes.byref(hi), ctypes.byref(lo))
     if rc:
         raise ValueError("brute: unsupported sizes")
@@ -100,11 +134,11 @@ def closed(M: np.ndarray, sigma: Optional[Sequence[float]] = None, prec: str = "
     vertex 0 (bit i of S = vertex i)."""
     M = _f64(M)
     nf, n, _ = M.shape
-    sig = None if sigma is None else _f64(sigma)
+    sig, v = _sigma(sigma, nf, n)
     hi, lo = ctypes.c_double(), ctypes.c_double()
     a_all = np.zeros(1 << n) if subsets else None
     c_all = np.zeros(1 << n) if subsets else None
-    rc = getattr(lib(), "closed_" + prec)(n, nf, _ptr(M), _ptr(sig), ctypes.byref(hi), ctypes.byref(lo),
+    rc = getattr(lib(), ("closed_v_" if v else "closed_") + prec)(n, nf, _ptr(M), _ptr(sig), ctypes.byref(hi), ctypes.byref(lo),
                                            _ptr(a_all), _ptr(c_all))
     if rc:
         raise ValueError("closed: unsupported sizes")
@@ -119,9 +153,9 @@ def dp(M: np.ndarray, sigma: Optional[Sequence[float]] = None, weight: int = 1, 
     symmetric SU(N) run passes one matrix and weight N)."""
     M = _f64(M)
     nf, n, _ = M.shape
-    sig = None if sigma is None else _f64(sigma)
+    sig, v = _sigma(sigma, nf, n)
     hi, lo = ctypes.c_double(), ctypes.c_double()
-    rc = getattr(lib(), "dp_" + prec)(n, nf, int(weight), _ptr(M), _ptr(sig), int(absmode),
+    rc = getattr(lib(), ("dp_v_" if v else "dp_") + prec)(n, nf, int(weight), _ptr(M), _ptr(sig), int(absmode),
                                        ctypes.byref(hi), ctypes.byref(lo))
     if rc:
         raise ValueError("dp: unsupported sizes")
@@ -279,3 +313,41 @@ def torch_brute(M, sigma=None):
                 w = w * (-per_flavor.sum())
             total = total + w
     return total
+
+
+def bip(M4: np.ndarray, sigma2: Optional[np.ndarray] = None, weight: int = 1, absmode: bool = False,
+        method: str = "sum_dp", prec: str = "d") -> float:
+    """Bipartite connected sum.  M4 [nf][n][2][n][2] (flavor, vertex, sublattice, vertex,
+    sublattice; sublattice 0 = A, 1 = B), sigma2 [nf][2] shift weights per flavor and
+    sublattice, or None.  method: "sum_dp" / "sum_closed" / "sum_brute" = the sum over all
+    2^n sublattice assignments of the merged DP / the closed form / brute force (the
+    definition, Methods A strategy (i)); "dp4" = the sublattice-resolved merged DP of
+    Alg. 1-2 (n <= 8)."""
+    M4 = _f64(M4)
+    nf, n = M4.shape[0], M4.shape[1]
+    if M4.shape != (nf, n, 2, n, 2):
+        raise ValueError("M4 must have shape [nf][n][2][n][2]")
+    sig = None if sigma2 is None else _f64(sigma2).reshape(nf, 2)
+    hi, lo = ctypes.c_double(), ctypes.c_double()
+    if method == "dp4":
+        rc = getattr(lib(), "bip_dp4_" + prec)(n, nf, int(weight), _ptr(M4), _ptr(sig), int(absmode),
+                                               ctypes.byref(hi), ctypes.byref(lo))
+    else:
+        code = {"sum_dp": 0, "sum_closed": 1, "sum_brute": 2}[method]
+        rc = getattr(lib(), "bip_sum_" + prec)(n, nf, int(weight), _ptr(M4), _ptr(sig), int(absmode), code,
+                                               ctypes.byref(hi), ctypes.byref(lo))
+    if rc:
+        raise ValueError("bip: unsupported sizes or method")
+    return hi.value + lo.value
+
+
+def bip_assignment(M4: np.ndarray, sigma2: Optional[np.ndarray], s: Sequence[int]):
+    """Vertex matrices [nf][n][n] and per-vertex shift weights [nf][n] of one sublattice
+    assignment s (s_i in {0, 1})."""
+    M4 = _f64(M4)
+    s = np.asarray(s, dtype=np.int64)
+    n = M4.shape[1]
+    idx = np.arange(n)
+    M = M4[:, idx[:, None], s[:, None], idx[None, :], s[None, :]]
+    sig = None if sigma2 is None else _f64(sigma2)[:, s]
+    return np.ascontiguousarray(M), sig

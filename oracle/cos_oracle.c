@@ -9,7 +9,9 @@
  *   brute   decorated covers enumerated one by one (n <= 5 in practice)
  *   closed  determinants + the subset subtraction of Methods A
  *   dp      the merged clow-sequence DP of Results A / Alg. 2-3, plain loops
- * Every function states the passage it follows in oracle_impl.h.
+ * and the bipartite (two-sublattice) sums of oracle_bip.h: the definition (sum over
+ * sublattice assignments) and the sublattice-resolved merged DP of Alg. 1-2.
+ * Every function states the passage it follows in oracle_impl.h / oracle_bip.h.
  */
 #include <stdlib.h>
 #include <string.h>
@@ -23,6 +25,7 @@
 #define FN(x) x##_d
 #define RABS(x) fabs(x)
 #include "oracle_impl.h"
+#include "oracle_bip.h"
 #undef REAL
 #undef FN
 #undef RABS
@@ -31,6 +34,7 @@
 #define FN(x) x##_ld
 #define RABS(x) fabsl(x)
 #include "oracle_impl.h"
+#include "oracle_bip.h"
 #undef REAL
 #undef FN
 #undef RABS
@@ -39,6 +43,7 @@
 #define FN(x) x##_q
 #define RABS(x) fabsq(x)
 #include "oracle_impl.h"
+#include "oracle_bip.h"
 #undef REAL
 #undef FN
 #undef RABS

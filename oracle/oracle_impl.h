@@ -38,7 +38,7 @@
 typedef struct {
     int n, nf, np;        /* vertices, flavors, points = 2n */
     const REAL *A;        /* nf * np * np */
-    const REAL *sig;      /* nf or NULL */
+    const REAL *sig;      /* nf * n (flavor, vertex) or NULL */
     int connected;
     int is_shift[24];     /* point -> 1 if shift point */
     int normal[24];       /* list of normal points */
@@ -82,7 +82,7 @@ static void FN(brute_leaf)(FN(brute_ctx) *c) {
             if (c->sig) {
                 for (int e = 0; e < len; e++) {
                     int partner = (cyc[e] + n) % np;
-                    if (c->is_shift[partner]) t *= -c->sig[l];
+                    if (c->is_shift[partner]) t *= -c->sig[l * n + partner % n];
                 }
             }
             loop += t;
@@ -102,15 +102,18 @@ static void FN(brute_perm)(FN(brute_ctx) *c, int a, unsigned used) {
     }
 }
 
-/* Sum over decorated covers.  Returns 0 on success, -1 on bad sizes. */
-int FN(brute)(int n, int nf, const double *A_in, const double *sig_in, int connected,
-              double *out_hi, double *out_lo) {
+/* Sum over decorated covers, shift weights per (flavor, vertex): sig_in[l * n + i] is the
+ * weight of a shift point at vertex i inside a loop of flavor l (a vertex-dependent shift,
+ * e.g. the sublattice-dependent equal-time shift (alpha +- Delta) / U of Methods A).
+ * Returns 0 on success, -1 on bad sizes. */
+int FN(brute_v)(int n, int nf, const double *A_in, const double *sig_in, int connected,
+                double *out_hi, double *out_lo) {
     if (n < 1 || n > 6 || nf < 1 || nf > 8) return -1;
     int np = 2 * n;
     REAL *A = (REAL *)malloc(sizeof(REAL) * nf * np * np);
-    REAL sig[8];
+    REAL sig[8 * 12];
     for (int k = 0; k < nf * np * np; k++) A[k] = (REAL)A_in[k];
-    if (sig_in) for (int l = 0; l < nf; l++) sig[l] = (REAL)sig_in[l];
+    if (sig_in) for (int k = 0; k < nf * n; k++) sig[k] = (REAL)sig_in[k];
     REAL total = 0;
     int ndec = 1;
     for (int i = 0; i < n; i++) ndec *= sig_in ? 3 : 1;
@@ -137,6 +140,17 @@ int FN(brute)(int n, int nf, const double *A_in, const double *sig_in, int conne
     *out_lo = (double)(total - (REAL)(*out_hi));
     free(A);
     return 0;
+}
+
+/* Per-flavor shift weights (the same at every vertex). */
+int FN(brute)(int n, int nf, const double *A_in, const double *sig_in, int connected,
+              double *out_hi, double *out_lo) {
+    if (n < 1 || n > 6 || nf < 1 || nf > 8) return -1;
+    double sv[8 * 12];
+    if (sig_in)
+        for (int l = 0; l < nf; l++)
+            for (int i = 0; i < n; i++) sv[l * n + i] = sig_in[l];
+    return FN(brute_v)(n, nf, A_in, sig_in ? sv : NULL, connected, out_hi, out_lo);
 }
 
 /* ---------------------------------------------------------------- tier 1
@@ -188,8 +202,8 @@ static REAL FN(det_sub)(int n, const REAL *M, unsigned J) {
 
 /* a_out: 2^n values a(S) (may be NULL); c_out: 2^n values c(S) for S
  * containing vertex 0 (others 0; may be NULL).  Returns c(V). */
-int FN(closed)(int n, int nf, const double *M_in, const double *sig_in,
-               double *out_hi, double *out_lo, double *a_out, double *c_out) {
+int FN(closed_v)(int n, int nf, const double *M_in, const double *sig_in,
+                 double *out_hi, double *out_lo, double *a_out, double *c_out) {
     if (n < 1 || n > 12 || nf < 1 || nf > 8) return -1;
     int nsub = 1 << n;
     int p3[13];
@@ -197,8 +211,15 @@ int FN(closed)(int n, int nf, const double *M_in, const double *sig_in,
     for (int i = 1; i <= n; i++) p3[i] = 3 * p3[i - 1];
     REAL *M = (REAL *)malloc(sizeof(REAL) * nf * n * n);
     for (int k = 0; k < nf * n * n; k++) M[k] = (REAL)M_in[k];
-    REAL sig[8];
-    for (int l = 0; l < nf; l++) sig[l] = sig_in ? (REAL)sig_in[l] : 0;
+    REAL sig[8 * 12];              /* [l][vertex] */
+    int sig_any[8];
+    for (int l = 0; l < nf; l++) {
+        sig_any[l] = 0;
+        for (int i = 0; i < n; i++) {
+            sig[l * n + i] = sig_in ? (REAL)sig_in[l * n + i] : 0;
+            if (sig[l * n + i] != 0) sig_any[l] = 1;
+        }
+    }
     REAL *det = (REAL *)malloc(sizeof(REAL) * nf * nsub);
     for (int l = 0; l < nf; l++)
         for (unsigned J = 0; J < (unsigned)nsub; J++) det[l * nsub + J] = FN(det_sub)(n, M + l * n * n, J);
@@ -231,12 +252,12 @@ int FN(closed)(int n, int nf, const double *M_in, const double *sig_in,
                     G[c2] += F[code] * w;
                     /* shifted vertices among the untouched ones of J */
                     unsigned Z = J & zeros;
-                    if (sig_in && sig[l] != 0 && Z) {
+                    if (sig_in && sig_any[l] && Z) {
                         unsigned Sh = Z;
                         while (Sh) {
                             REAL ws = w;
                             int c3 = c2;
-                            for (int v = 0; v < n; v++) if (Sh & (1u << v)) { ws *= 2 * sig[l]; c3 += p3[v]; }
+                            for (int v = 0; v < n; v++) if (Sh & (1u << v)) { ws *= 2 * sig[l * n + v]; c3 += p3[v]; }
                             G[c3] += F[code] * ws;
                             Sh = (Sh - 1) & Z;
                         }
@@ -276,6 +297,16 @@ int FN(closed)(int n, int nf, const double *M_in, const double *sig_in,
     return 0;
 }
 
+int FN(closed)(int n, int nf, const double *M_in, const double *sig_in,
+               double *out_hi, double *out_lo, double *a_out, double *c_out) {
+    if (n < 1 || n > 12 || nf < 1 || nf > 8) return -1;
+    double sv[8 * 12];
+    if (sig_in)
+        for (int l = 0; l < nf; l++)
+            for (int i = 0; i < n; i++) sv[l * n + i] = sig_in[l];
+    return FN(closed_v)(n, nf, M_in, sig_in ? sv : NULL, out_hi, out_lo, a_out, c_out);
+}
+
 /* ---------------------------------------------------------------- tier 2
  * The merged (contact-interaction) form of the cycle-aware DP of Results A
  * and Alg. 2-3, written as plain push loops in the paper's order.
@@ -302,8 +333,8 @@ int FN(closed)(int n, int nf, const double *M_in, const double *sig_in,
  * absmode = 1 runs the same recursion on |M|, |sigma| with every sign +,
  * which bounds the sum of |term| (the "mass").
  */
-int FN(dp)(int n, int nf, int wt, const double *M_in, const double *sig_in, int absmode,
-           double *out_hi, double *out_lo) {
+int FN(dp_v)(int n, int nf, int wt, const double *M_in, const double *sig_in, int absmode,
+             double *out_hi, double *out_lo) {
     if (n < 1 || n > 12 || nf < 1 || nf > 8 || wt < 1) return -1;
     int p3[14];
     p3[0] = 1;
@@ -311,12 +342,12 @@ int FN(dp)(int n, int nf, int wt, const double *M_in, const double *sig_in, int 
     int ncode = p3[n];
     REAL *M = (REAL *)malloc(sizeof(REAL) * nf * n * n);
     for (int k = 0; k < nf * n * n; k++) M[k] = absmode ? RABS((REAL)M_in[k]) : (REAL)M_in[k];
-    REAL sig[8];
+    REAL sig[8 * 12];              /* [l][vertex]: shift weight of vertex i in a loop of flavor l */
     int shifts = 0;
-    for (int l = 0; l < nf; l++) {
-        sig[l] = sig_in ? (REAL)sig_in[l] : 0;
-        if (absmode) sig[l] = RABS(sig[l]);
-        if (sig[l] != 0) shifts = 1;
+    for (int k = 0; k < nf * n; k++) {
+        sig[k] = sig_in ? (REAL)sig_in[k] : 0;
+        if (absmode) sig[k] = RABS(sig[k]);
+        if (sig[k] != 0) shifts = 1;
     }
     REAL sgn = absmode ? 1 : -1;
     /* per-code layer and rank within the layer (layer = number of visited points) */
@@ -338,7 +369,7 @@ int FN(dp)(int n, int nf, int wt, const double *M_in, const double *sig_in, int 
 #define ST(code, h, v, l) ring[layer[code] % 3][(size_t)rank[code] * blk + ((size_t)(h) * n + (v)) * nf + (l)]
     for (int l = 0; l < nf; l++) {
         ST(1, 0, 0, l) += 1;                                   /* mu = e_0 */
-        if (shifts) ST(2, 0, 0, l) += sgn * 2 * sig[l];        /* mu = 2 e_0 */
+        if (shifts) ST(2, 0, 0, l) += sgn * 2 * sig[l * n];    /* mu = 2 e_0 */
     }
     REAL S = 0;
     for (int ell = 1; ell <= 2 * n; ell++) {
@@ -358,7 +389,7 @@ int FN(dp)(int n, int nf, int wt, const double *M_in, const double *sig_in, int 
                             if (mu[j] == 2) continue;
                             ST(code + p3[j], h, j, l) += w * (mu[j] == 0 ? 2 : 1) * Ml[v * n + j];
                             if (mu[j] == 0 && shifts)
-                                ST(code + 2 * p3[j], h, j, l) += w * 2 * Ml[v * n + j] * (sgn * sig[l]);
+                                ST(code + 2 * p3[j], h, j, l) += w * 2 * Ml[v * n + j] * (sgn * sig[l * n + j]);
                         }
                     }
             C[rank[code]] = Cmu;
@@ -386,6 +417,17 @@ int FN(dp)(int n, int nf, int wt, const double *M_in, const double *sig_in, int 
     for (int r = 0; r < 3; r++) free(ring[r]);
     free(C); free(layer); free(rank); free(M);
     return 0;
+}
+
+/* Per-flavor shift weights (the same at every vertex). */
+int FN(dp)(int n, int nf, int wt, const double *M_in, const double *sig_in, int absmode,
+           double *out_hi, double *out_lo) {
+    if (n < 1 || n > 12 || nf < 1 || nf > 8 || wt < 1) return -1;
+    double sv[8 * 12];
+    if (sig_in)
+        for (int l = 0; l < nf; l++)
+            for (int i = 0; i < n; i++) sv[l * n + i] = sig_in[l];
+    return FN(dp_v)(n, nf, wt, M_in, sig_in ? sv : NULL, absmode, out_hi, out_lo);
 }
 
 /* Batch of configurations of one order (matrices packed [cfg][l][n][n]);

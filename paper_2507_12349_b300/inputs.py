@@ -87,6 +87,38 @@ class Model:
 
 
 @dataclass(frozen=True)
+class HoneycombModel:
+    """Honeycomb-lattice SU(N_f) Hubbard model (Methods A, bipartite lattices): L x L unit
+    cells of two sites (sublattices A, B), hopping t, inverse temperature beta, interaction U,
+    per-flavor chemical potential mu, uniform shift alpha and staggered shift delta (+delta
+    on A, -delta on B), n_tau imaginary-time grid points.  A vertex sits in a unit cell
+    (site = r_1 + L r_2 in cell coordinates along the two lattice vectors); its sublattice is
+    summed over."""
+    L: int
+    t: float
+    beta: float
+    U: float
+    mu: tuple
+    alpha: tuple
+    delta: tuple
+    n_tau: int
+
+    @property
+    def n_flavors(self) -> int:
+        return len(self.mu)
+
+    @property
+    def symmetric(self) -> bool:
+        return len(set(self.mu)) == 1 and len(set(self.alpha)) == 1 and len(set(self.delta)) == 1
+
+    @property
+    def sigma2(self) -> tuple:
+        """Shift weights per (flavor, sublattice): (alpha + delta) / U on A, (alpha - delta) / U
+        on B (the sublattice-dependent equal-time shift of Methods A)."""
+        return tuple(((a + d) / self.U, (a - d) / self.U) for a, d in zip(self.alpha, self.delta))
+
+
+@dataclass(frozen=True)
 class Workload:
     name: str
     model: Model
@@ -113,6 +145,12 @@ WORKLOADS = {
     "su4_adjoint_n10": Workload("su4_adjoint_n10",
                                 Model(16, 1.0, 4.0, 1.5, (-0.2, 0.0, 0.0, 0.2), (0.0,) * 4, 1024),
                                 10, 10, 50_000, 4, "fp64", grad=True),
+    # Honeycomb (two sublattices, summed per vertex): SU(2) with an antiferromagnetic
+    # staggered shift (delta of opposite sign for the two spins), half filling, the paper's
+    # honeycomb physics orders (up to 8).
+    "hc_su2_af_n8": Workload("hc_su2_af_n8",
+                             HoneycombModel(16, 1.0, 6.0, 3.0, (0.0, 0.0), (0.0, 0.0), (0.25, -0.25), 1024),
+                             8, 8, 20_000, 5, "fp64"),
 }
 
 
@@ -145,7 +183,7 @@ class Configs:
         return Configs(order, offset, self.site[pos].astype(np.int32), self.tau[pos].astype(np.float64))
 
 
-def make_configs(model: Model, n_lo: int, n_hi: int, n_cfg: int, seed: int,
+def make_configs(model, n_lo: int, n_hi: int, n_cfg: int, seed: int,
                  first_cfg: int = 0) -> Configs:
     """Configurations first_cfg .. first_cfg+n_cfg-1 of the seeded stream."""
     cfg = np.arange(first_cfg, first_cfg + n_cfg, dtype=np.uint64)
