@@ -85,6 +85,26 @@ typedef struct {
     int n_tau;
 } cos_model;
 
+/* Honeycomb-lattice model (Methods A, bipartite lattices): L x L unit cells of two sites
+ * (sublattices A, B), Bloch Hamiltonian per flavor l
+ *   H_l(k) = [[delta_l - (mu_l - alpha_l), eps(k)], [conj(eps(k)), -delta_l - (mu_l - alpha_l)]],
+ *   eps(k) = -t (1 + exp(i k.b1) + exp(i k.b2)),  k.b1 = 2 pi m_1 / L, k.b2 = 2 pi m_2 / L.
+ * Shift weights per (flavor, sublattice): sigma_{l,A} = (alpha_l + delta_l) / U,
+ * sigma_{l,B} = (alpha_l - delta_l) / U (the sublattice-dependent equal-time shift).
+ * mu, alpha and delta are host arrays of n_flavors values; the tau grid is the square
+ * lattice's. */
+typedef struct {
+    int L;
+    double t, beta, U;
+    int n_flavors;
+    const double *mu;
+    const double *alpha;
+    const double *delta;
+    int n_tau;
+} cos_honeycomb_model;
+
+#define COS_BIP_NMAX 9    /* largest order of the bipartite DP (4^n interaction masks) */
+
 typedef struct cos_tables cos_tables; /* opaque; owns device propagator tables */
 
 typedef struct {
@@ -95,6 +115,8 @@ typedef struct {
     double sigma[COS_MAX_FLAVORS];
     const double *d_G;      /* [n_mat][L*L][n_tau]  G0(r, tau_m), r = x + L y */
     const double *d_dGdmu;  /* same layout, d G0 / d mu; NULL until a gradient call */
+    int bipartite;          /* 1: honeycomb tables, d_G = [n_mat][2][2][L*L][n_tau] (s, t, R, tau) */
+    double sigma2[COS_MAX_FLAVORS][2];   /* bipartite: shift weight per (flavor, sublattice) */
 } cos_tables_info;
 
 /* ------------------------------------------------------------------ K-TAB
@@ -109,8 +131,9 @@ typedef struct {
 cos_status cos_build_propagators(const cos_model *model, cos_stream_t stream, cos_tables **out);
 cos_status cos_free_tables(cos_tables *tables);
 cos_status cos_get_tables_info(const cos_tables *tables, cos_tables_info *info);
-/* Copies a whole table ([n_mat][L*L][n_tau] doubles) into caller device memory d_dst,
- * asynchronously on `stream`.  which = 0: G0; which = 1: dG0/dmu (built on first request). */
+/* Copies a whole table ([n_mat][L*L][n_tau] doubles; honeycomb: [n_mat][2][2][L*L][n_tau])
+ * into caller device memory d_dst, asynchronously on `stream`.  which = 0: G0; which = 1:
+ * dG0/dmu (built on first request; square tables only). */
 cos_status cos_copy_table(const cos_tables *tables, int which, double *d_dst, cos_stream_t stream);
 
 /* ------------------------------------------------------------------ K-GATHER
@@ -206,6 +229,47 @@ cos_status cos_connected_sum_subsets(int n_cfg, int n_max, const int32_t *d_orde
                                      cos_precision precision, int all_roots, double *d_c, double *d_a,
                                      cos_stream_t stream);
 
+/* ------------------------------------------------------------------ bipartite lattices
+ * Connected sums summed over every sublattice assignment of the vertices (Methods A,
+ * bipartite lattices, strategy (i)) by the sublattice-resolved merged DP (Results A; Alg. 1-2):
+ * the interaction mask keeps the sublattice of each half-visited vertex, so the 2^n
+ * assignments share one sweep.
+ *
+ * Two-band tables for the honeycomb model: for every distinct flavor l the real 2 x 2 matrix
+ *   G_l(R, tau_m) = -(1/L^2) sum_k exp(i k.R) exp(-H_l(k) tau_m)(1 - n_F(H_l(k))),
+ * R = r_1 + L r_2 in unit-cell coordinates, tau_m as in cos_build_propagators.  Same
+ * ownership and synchronization as cos_build_propagators; the tables serve the bipartite
+ * entry points only. */
+cos_status cos_build_propagators_honeycomb(const cos_honeycomb_model *model, cos_stream_t stream,
+                                           cos_tables **out);
+
+/* M4^l[(i,s)][(j,t)] = G_l^{st}(R_i - R_j, tau_i - tau_j) (same interpolation and dt <= 0 reading
+ * as cos_gather).  Per configuration c the block [n_mat][2 n_c][2 n_c] (row index i*2 + s,
+ * column j*2 + t, s, t = 0 for A, 1 for B) starts at d_moff[c] in d_M4.  d_site[k] is the unit
+ * cell r_1 + L r_2 in [0, L^2).  Orders in [1, COS_BIP_NMAX]. */
+cos_status cos_gather_bipartite(const cos_tables *tables, int n_cfg, const int32_t *d_order,
+                                const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
+                                const int64_t *d_moff, double *d_M4, cos_stream_t stream);
+
+/* Bipartite connected sums of explicit matrices: d_M4 as written by cos_gather_bipartite
+ * (blocks [n_mat][2 n_c][2 n_c] at d_moff[c]); h_sigma2 = NULL or host [n_mat][2] shift weights
+ * per (flavor, sublattice).  n_max <= COS_BIP_NMAX; precision COS_FP64 only
+ * (COS_ERR_UNIMPLEMENTED otherwise).  Other arguments, outputs and errors as
+ * cos_connected_sum_matrices (d_abs_mass: the same DP on |M4|, |sigma| with all signs +). */
+cos_status cos_connected_sum_bipartite_matrices(int n_cfg, int n_max, const int32_t *d_order,
+                                                const int64_t *d_moff, int n_mat, int loop_weight,
+                                                const double *h_sigma2, const double *d_M4,
+                                                cos_precision precision, double *d_out,
+                                                double *d_abs_mass, cos_stream_t stream);
+
+/* Gather + bipartite DP from vertex coordinates (honeycomb tables; the loop weight is
+ * n_flavors for symmetric tables, else 1). */
+cos_status cos_connected_sum_bipartite_batch(const cos_tables *tables, int n_cfg, int n_max,
+                                             const int32_t *d_order, const int64_t *d_offset,
+                                             const int32_t *d_site, const double *d_tau,
+                                             cos_precision precision, double *d_out,
+                                             double *d_abs_mass, cos_stream_t stream);
+
 /* ------------------------------------------------------------------ adjoint DP
  * Gradient of the connected sums by the reverse (adjoint) DP: the forward DP is re-run with
  * every layer kept, then walked backwards (the adjoint of Alg. 2-3 as merged in Results A).
@@ -300,6 +364,10 @@ typedef struct {
 } cos_structure_info;
 
 cos_status cos_structure(int n, cos_structure_info *info);
+
+/* Counts of the bipartite structure at order n (host only): masks, slots (4 |H| |A| per
+ * mask), max_layer_slots, reachable states and multiply-adds per flavor array. */
+cos_status cos_bipartite_structure(int n, cos_structure_info *info);
 
 /* ------------------------------------------------------------------ measurement
  * Peak-throughput probe (no counterpart in the paper; it supplies the roofline

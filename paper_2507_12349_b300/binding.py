@@ -30,6 +30,8 @@ EXPORTS = [
     "cos_build_propagators", "cos_free_tables", "cos_get_tables_info", "cos_copy_table", "cos_gather",
     "cos_connected_sum_matrices", "cos_connected_sum_matrices_noalloc", "cos_connected_sum_batch",
     "cos_connected_sum_subsets",
+    "cos_build_propagators_honeycomb", "cos_gather_bipartite", "cos_connected_sum_bipartite_matrices",
+    "cos_connected_sum_bipartite_batch", "cos_bipartite_structure",
     "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_sync_status", "cos_status_string",
     "cos_last_error", "cos_structure", "cos_peak_probe",
     "cos_plan_create_batch", "cos_plan_create_matrices", "cos_plan_launch", "cos_plan_status", "cos_plan_grid",
@@ -53,7 +55,15 @@ class cos_tables_info(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("n_tau", ctypes.c_int), ("n_flavors", ctypes.c_int),
                 ("symmetric", ctypes.c_int), ("n_mat", ctypes.c_int), ("beta", ctypes.c_double),
                 ("U", ctypes.c_double), ("sigma", ctypes.c_double * COS_MAX_FLAVORS),
-                ("d_G", ctypes.c_void_p), ("d_dGdmu", ctypes.c_void_p)]
+                ("d_G", ctypes.c_void_p), ("d_dGdmu", ctypes.c_void_p), ("bipartite", ctypes.c_int),
+                ("sigma2", (ctypes.c_double * 2) * COS_MAX_FLAVORS)]
+
+
+class cos_honeycomb_model(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("t", ctypes.c_double), ("beta", ctypes.c_double), ("U", ctypes.c_double),
+                ("n_flavors", ctypes.c_int), ("mu", ctypes.POINTER(ctypes.c_double)),
+                ("alpha", ctypes.POINTER(ctypes.c_double)), ("delta", ctypes.POINTER(ctypes.c_double)),
+                ("n_tau", ctypes.c_int)]
 
 
 class cos_structure_info(ctypes.Structure):
@@ -154,11 +164,15 @@ class Tables:
         return inf
 
     def table(self, deriv: bool = False, stream=None):
-        """Device copy of the table [n_mat][L^2][n_tau] (G0, or dG0/dmu with deriv=True)."""
+        """Device copy of the table [n_mat][L^2][n_tau] (G0, or dG0/dmu with deriv=True);
+        honeycomb tables: [n_mat][2][2][L^2][n_tau]."""
         import torch
         inf = self.info()
-        buf = torch.empty(inf.n_mat * inf.L * inf.L * inf.n_tau, dtype=torch.float64, device="cuda")
+        blocks = 4 if inf.bipartite else 1
+        buf = torch.empty(inf.n_mat * blocks * inf.L * inf.L * inf.n_tau, dtype=torch.float64, device="cuda")
         _check(lib().cos_copy_table(self.handle, int(deriv), _ptr(buf), _stream(stream)), "cos_copy_table")
+        if inf.bipartite:
+            return buf.view(inf.n_mat, 2, 2, inf.L * inf.L, inf.n_tau)
         return buf.view(inf.n_mat, inf.L * inf.L, inf.n_tau)
 
     def close(self):
@@ -186,6 +200,63 @@ def cos_build_propagators(L: int, t: float, beta: float, U: float, mu: Sequence[
 def tables_for(model, stream=None) -> Tables:
     """Tables for an inputs.Model."""
     return cos_build_propagators(model.L, model.t, model.beta, model.U, model.mu, model.alpha, model.n_tau, stream)
+
+
+def cos_build_propagators_honeycomb(L: int, t: float, beta: float, U: float, mu: Sequence[float],
+                                    alpha: Sequence[float], delta: Sequence[float], n_tau: int,
+                                    stream=None) -> Tables:
+    nf = len(mu)
+    arr = lambda v: (ctypes.c_double * nf)(*[float(x) for x in v])
+    m = cos_honeycomb_model(int(L), float(t), float(beta), float(U), nf, arr(mu), arr(alpha), arr(delta), int(n_tau))
+    h = ctypes.c_void_p()
+    _check(lib().cos_build_propagators_honeycomb(ctypes.byref(m), _stream(stream), ctypes.byref(h)),
+           "cos_build_propagators_honeycomb")
+    return Tables(h)
+
+
+def honeycomb_tables_for(model, stream=None) -> Tables:
+    """Tables for an inputs.HoneycombModel."""
+    return cos_build_propagators_honeycomb(model.L, model.t, model.beta, model.U, model.mu, model.alpha, model.delta,
+                                           model.n_tau, stream)
+
+
+def cos_gather_bipartite(tables: Tables, order, offset, site, tau, moff, M4, stream=None):
+    _check(lib().cos_gather_bipartite(tables.handle, int(order.numel()), _ptr(order, "i32"), _ptr(offset, "i64"),
+                                      _ptr(site, "i32"), _ptr(tau, "f64"), _ptr(moff, "i64"), _ptr(M4, "f64"),
+                                      _stream(stream)), "cos_gather_bipartite")
+
+
+def cos_connected_sum_bipartite_matrices(n_max: int, order, moff, n_mat: int, loop_weight: int, sigma2, M4,
+                                         precision: str, out, abs_mass=None, stream=None):
+    """sigma2: None or n_mat x 2 shift weights (flavor, sublattice)."""
+    sig = None
+    if sigma2 is not None:
+        flat = [float(x) for row in sigma2 for x in row]
+        sig = (ctypes.c_double * len(flat))(*flat)
+    _check(lib().cos_connected_sum_bipartite_matrices(int(order.numel()), int(n_max), _ptr(order, "i32"),
+                                                      _ptr(moff, "i64"), int(n_mat), int(loop_weight), sig,
+                                                      _ptr(M4, "f64"), PRECISIONS[precision], _ptr(out, "f64"),
+                                                      _ptr(abs_mass, "f64"), _stream(stream)),
+           "cos_connected_sum_bipartite_matrices")
+
+
+def cos_connected_sum_bipartite_batch(tables: Tables, n_max: int, order, offset, site, tau, precision: str, out,
+                                      abs_mass=None, stream=None):
+    _check(lib().cos_connected_sum_bipartite_batch(tables.handle, int(order.numel()), int(n_max), _ptr(order, "i32"),
+                                                   _ptr(offset, "i64"), _ptr(site, "i32"), _ptr(tau, "f64"),
+                                                   PRECISIONS[precision], _ptr(out, "f64"), _ptr(abs_mass, "f64"),
+                                                   _stream(stream)), "cos_connected_sum_bipartite_batch")
+
+
+def cos_bipartite_structure(n: int) -> cos_structure_info:
+    inf = cos_structure_info()
+    _check(lib().cos_bipartite_structure(int(n), ctypes.byref(inf)), "cos_bipartite_structure")
+    return inf
+
+
+def bipartite_matrix_offsets(order: np.ndarray, n_mat: int) -> np.ndarray:
+    """Offsets of packed [n_mat][2 n_c][2 n_c] blocks for the given orders."""
+    return matrix_offsets(2 * np.asarray(order, dtype=np.int64), n_mat)
 
 
 def cos_gather(tables: Tables, order, offset, site, tau, moff, M, stream=None):

@@ -330,8 +330,8 @@ extern "C" cos_status cos_connected_sum_matrices(int n_cfg, int n_max, const int
 extern "C" cos_status cos_gather(const cos_tables *t, int n_cfg, const int32_t *d_order, const int64_t *d_offset,
                                  const int32_t *d_site, const double *d_tau, const int64_t *d_moff, double *d_M,
                                  cos_stream_t stream) {
-    if (!t) {
-        set_error("cos_gather: null tables");
+    if (!t || t->bipartite) {
+        set_error("cos_gather: null tables, or honeycomb tables (use cos_gather_bipartite)");
         return COS_ERR_ARG;
     }
     if (n_cfg < 0) {
@@ -359,8 +359,8 @@ cos_status check_batch(const cos_tables *t, int n_cfg, int n_max, const int32_t 
                        const char *fn) {
     cos_status st = check_common(n_cfg, n_max, precision, fn);
     if (st != COS_OK) return st;
-    if (!t) {
-        set_error(std::string(fn) + ": null tables");
+    if (!t || t->bipartite) {
+        set_error(std::string(fn) + ": null tables, or honeycomb tables (use the bipartite entry points)");
         return COS_ERR_ARG;
     }
     if (n_cfg > 0 && (!d_order || !d_offset || !d_site || !d_tau || !d_out)) {
@@ -462,8 +462,8 @@ extern "C" cos_status cos_connected_sum_grad(const cos_tables *t, int n_cfg, int
                                              cos_stream_t stream) {
     cos_status st = check_common(n_cfg, n_max, COS_FP64, "cos_connected_sum_grad");
     if (st != COS_OK) return st;
-    if (!t) {
-        set_error("cos_connected_sum_grad: null tables");
+    if (!t || t->bipartite) {
+        set_error("cos_connected_sum_grad: null tables, or honeycomb tables (no bipartite gradient)");
         return COS_ERR_ARG;
     }
     if (n_cfg == 0) return COS_OK;

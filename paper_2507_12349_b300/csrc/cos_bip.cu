@@ -1,0 +1,636 @@
+// Bipartite (two-sublattice) connected sums: the sublattice-resolved merged DP on sm_103a.
+//
+// Every vertex sits in a unit cell and carries a sublattice index s in {A, B} that its two
+// points share; the propagator between points depends on both indices, and the connected sum
+// is summed over all sublattice assignments (Methods A, strategy (i)).  Following Results A
+// and Alg. 1-2, the interaction mask records the sublattice of a half-visited vertex, so the
+// sum over assignments is folded into the DP:
+//   mask digits  0 untouched, (1, A), (1, B), 2 full  (a full vertex forgets its sublattice)
+//   state        (mu, h, s_h, v, s_v) per lane (configuration, flavor): the open loop's head
+//                with its sublattice, the current endpoint with its sublattice.
+// Rules (push form; the untouched-vertex factor 2 is the global 2^(n-1) as in cos_dp.cu):
+//   extend  to an untouched j, for both s_j:  O(mu + (1,s_j) e_j, h, s_h, j, s_j) = sum O a(v s_v, j s_j)
+//           to a half-visited j (s_j fixed):   O(mu with j full, h, s_h, j, s_j)  = sum O a(v s_v, j s_j)
+//   close   C(mu) += O(mu,h,s_h,v,s_v) * sgn w a(v s_v, h s_h)
+//   seed    k = min half-visited: O(mu with k full, k, s_k, k, s_k) = C(mu) in every flavor
+//   sink    mu full: c = 2^(n-1) C(mu)
+// Shift points ride on the shifted diagonal a(j s, j s) - sigma_{l,s} of the extension
+// matrices, exactly as in the square-lattice kernel; vertex 0's shifted start seeds
+// -2 sigma_{l, s_0}.
+//
+// Layout: a mask's block holds |H| x 2 rows (h, s_h) of |A| x 2 slots (v, s_v) in the
+// vertex-ordered visited set; only reachable slots are written or read (a half-visited
+// endpoint has its recorded sublattice, the endpoint v = h has s_h, the first loop's head has
+// the recorded sublattice of vertex 0).  Lanes, persistent CTAs, the planner and the two-slot
+// layer ring are those of cos_dp.cu; matrices sit in shared memory as [(v,s)][(j,t)][lane].
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "cos_dp_device.cuh"
+
+namespace cosdp {
+
+static __constant__ uint32_t c_p4[COS_BIP_NMAX + 2] = {1u, 4u, 16u, 64u, 256u, 1024u, 4096u, 16384u, 65536u,
+                                                        262144u, 1048576u};
+
+// ------------------------------------------------------------------ structure (host-built)
+
+namespace {
+
+struct BipHostOrder {
+    int n = 0;
+    std::vector<uint4> masks;       // {A | B << 16, S, code, off}
+    std::vector<uint32_t> rank4;    // code -> block offset inside its layer
+    uint32_t layer_first[kMaxLayers + 1] = {};
+    uint32_t layer_count[kMaxLayers + 1] = {};
+    uint32_t layer_slots[kMaxLayers + 1] = {};
+    uint32_t max_slots = 0;
+    cos_structure_info info{};
+};
+
+int popc_h(uint32_t x) { return __builtin_popcount(x); }
+
+void build_bip_order(int n, BipHostOrder &o) {
+    o.n = n;
+    uint32_t p4[COS_BIP_NMAX + 2];
+    p4[0] = 1;
+    for (int i = 1; i <= n + 1; i++) p4[i] = 4 * p4[i - 1];
+    const uint32_t full = (1u << n) - 1u;
+    o.rank4.assign(p4[n], 0xFFFFFFFFu);
+    struct Rec {
+        uint4 m;
+        uint64_t cost;
+    };
+    std::vector<std::vector<Rec>> per_layer(2 * n + 1);
+    cos_structure_info &info = o.info;
+    info = cos_structure_info{};
+    info.n = n;
+    for (uint32_t code = 0; code < p4[n]; code++) {
+        uint32_t x = code, A = 0, B = 0, S = 0;
+        int layer = 0;
+        for (int i = 0; i < n; i++) {
+            const uint32_t d = x % 4;
+            x /= 4;
+            if (d >= 1) A |= 1u << i;
+            if (d == 3) B |= 1u << i;
+            if (d == 2) S |= 1u << i;
+            layer += d == 3 ? 2 : (d ? 1 : 0);
+        }
+        if (!(A & 1u)) continue;
+        const uint32_t ones = A & ~B;
+        const uint32_t H = head_set(B, ones);
+        const uint32_t J = full & ~B;
+        const int T = popc_h(J) + popc_h(J & ~A);
+        const bool needclose = ones != 0 || B == full;
+        uint64_t cost = 0;
+        for (uint32_t hh = H; hh; hh &= hh - 1) {
+            const int h = __builtin_ctz(hh);
+            const uint32_t V = row_vmask(A, ones, h);
+            const int nv = popc_h(V) + popc_h(V & B & ~(1u << h));
+            const int nrows = (h == 0 && (ones & 1u)) ? 1 : 2;
+            info.states += (int64_t)nrows * nv;
+            info.fma_ext += (int64_t)nrows * nv * T;
+            if (needclose) info.fma_close += (int64_t)nrows * nv;
+            cost += (uint64_t)nrows * ((uint64_t)nv * (T + (needclose ? 1 : 0)) + 4);
+        }
+        Rec r;
+        r.m = make_uint4(A | (B << 16), S, code, 0u);
+        r.cost = cost;
+        per_layer[layer].push_back(r);
+        info.masks++;
+        info.slots += 4 * (int64_t)popc_h(H) * popc_h(A);
+    }
+    uint32_t first = 0;
+    for (int l = 0; l <= 2 * n; l++) {
+        auto &v = per_layer[l];
+        std::stable_sort(v.begin(), v.end(), [](const Rec &a, const Rec &b) { return a.cost > b.cost; });
+        uint32_t off = 0;
+        for (auto &r : v) {
+            r.m.w = off;
+            o.rank4[r.m.z] = off;
+            const uint32_t A = r.m.x & 0xFFFFu, B = r.m.x >> 16;
+            off += 4u * (uint32_t)(popc_h(head_set(B, A & ~B)) * popc_h(A));
+            o.masks.push_back(r.m);
+        }
+        o.layer_first[l] = first;
+        o.layer_count[l] = (uint32_t)v.size();
+        o.layer_slots[l] = off;
+        o.max_slots = std::max(o.max_slots, off);
+        first += (uint32_t)v.size();
+    }
+    info.max_layer_slots = o.max_slots;
+}
+
+std::mutex g_bip_mu;
+BipHostOrder g_bip[COS_BIP_NMAX + 1];
+bool g_bip_built[COS_BIP_NMAX + 1];
+
+}  // namespace
+
+struct BipOrderTab {
+    const uint4 *masks;
+    const uint32_t *rank4;
+    uint32_t layer_first[kMaxLayers + 1];
+    uint32_t layer_count[kMaxLayers + 1];
+    uint32_t layer_slots[kMaxLayers + 1];
+    uint32_t max_slots;
+    uint32_t n;
+};
+
+namespace {
+
+const BipHostOrder &bip_host_order(int n) {
+    std::lock_guard<std::mutex> lk(g_bip_mu);
+    if (!g_bip_built[n]) {
+        build_bip_order(n, g_bip[n]);
+        g_bip_built[n] = true;
+    }
+    return g_bip[n];
+}
+
+BipOrderTab *g_bip_dev[64];
+
+const BipOrderTab *bip_device_orders(int device, std::string *err) {
+    if (device < 0 || device >= 64) {
+        *err = "device index out of range";
+        return nullptr;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_bip_mu);
+        if (g_bip_dev[device]) return g_bip_dev[device];
+    }
+    BipOrderTab tabs[COS_BIP_NMAX + 1];
+    memset(tabs, 0, sizeof tabs);
+    for (int n = 1; n <= COS_BIP_NMAX; n++) {
+        const BipHostOrder &o = bip_host_order(n);
+        uint4 *dm = nullptr;
+        uint32_t *dr = nullptr;
+        cudaError_t e = cudaMalloc(&dm, o.masks.size() * sizeof(uint4));
+        if (e == cudaSuccess) e = cudaMalloc(&dr, o.rank4.size() * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMemcpy(dm, o.masks.data(), o.masks.size() * sizeof(uint4), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(dr, o.rank4.data(), o.rank4.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            *err = std::string("bipartite structure upload: ") + cudaGetErrorString(e);
+            return nullptr;
+        }
+        BipOrderTab &t = tabs[n];
+        t.masks = dm;
+        t.rank4 = dr;
+        memcpy(t.layer_first, o.layer_first, sizeof t.layer_first);
+        memcpy(t.layer_count, o.layer_count, sizeof t.layer_count);
+        memcpy(t.layer_slots, o.layer_slots, sizeof t.layer_slots);
+        t.max_slots = o.max_slots;
+        t.n = n;
+    }
+    BipOrderTab *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof tabs);
+    if (e == cudaSuccess) e = cudaMemcpy(d, tabs, sizeof tabs, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        *err = std::string("bipartite structure upload: ") + cudaGetErrorString(e);
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_bip_mu);
+    if (!g_bip_dev[device]) g_bip_dev[device] = d;
+    return g_bip_dev[device];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ device code
+
+struct BipArgs {
+    const BipOrderTab *tabs;
+    const int4 *batches;
+    const int *n_batches;
+    const int *batch_list;
+    int *queue;
+    const double *M;            // per configuration [n_mat][2n][2n], index (i*2 + s)*2n + (j*2 + t)
+    const int64_t *moff;
+    int nf_lanes;
+    double loop_weight;
+    double sigma2[COS_MAX_FLAVORS][2];
+    int shifts;
+    int absmode;
+    double *scratch;
+    size_t slot_elems;
+    int smem_n;                 // n_max (shared-memory stride 2 n_max)
+    int prefetch;
+    double *out;
+    int *status;
+};
+
+// Extension targets of one mask, one lane per target (q < T = |J| + |J \ A|, at most 2n):
+// the q-th target in (j ascending, s_j ascending) order.
+//   off1 : block offset of the target mask;  meta: ai1 (bits 0-3), nA1 (4-7), s_j (8),
+//   j (12-15), heads of the target mask (16-27).
+__device__ __forceinline__ TgtInfo bip_targets(uint32_t A, uint32_t B, uint32_t S, uint32_t J, uint32_t code,
+                                               const uint32_t *__restrict__ rank4, int lane) {
+    TgtInfo ti = {0u, 0u};
+    const int T = __popc(J) + __popc(J & ~A);
+    if (lane < T) {
+        int cnt = 0, j = 0, sj = 0;
+        bool untouched = false;
+        for (uint32_t jj = J; jj; jj &= jj - 1u) {
+            const int jc = __ffs(jj) - 1;
+            const bool u = !(A & (1u << jc));
+            const int c = u ? 2 : 1;
+            if (lane < cnt + c) {
+                j = jc;
+                untouched = u;
+                sj = u ? lane - cnt : (int)((S >> jc) & 1u);
+                break;
+            }
+            cnt += c;
+        }
+        const uint32_t bj = 1u << j;
+        const uint32_t A1 = A | bj;
+        const uint32_t B1 = untouched ? B : (B | bj);
+        const uint32_t code1 = untouched ? code + (uint32_t)(1 + sj) * c_p4[j] : code + (uint32_t)(2 - sj) * c_p4[j];
+        ti.off1 = __ldg(rank4 + code1);
+        ti.meta = (uint32_t)__popc(A1 & (bj - 1u)) | ((uint32_t)__popc(A1) << 4) | ((uint32_t)sj << 8) |
+                  ((uint32_t)j << 12) | (head_set(B1, A1 & ~B1) << 16);
+    }
+    return ti;
+}
+
+// One row (mu, h, s_h): NV reachable endpoint states, the close, every extension.
+template <int NV>
+__device__ __forceinline__ void bip_row(const double *__restrict__ src, double *__restrict__ dst1,
+                                        const double *__restrict__ Ms, const double *__restrict__ Md,
+                                        const TgtInfo &ti, int T, uint32_t Vrow, uint32_t A, uint32_t B, uint32_t S,
+                                        uint32_t rowbase, int h, int sh, int n2, bool needclose, int lane,
+                                        double &csum) {
+    double o[NV];
+    int rs[NV];
+    const uint32_t ones = A & ~B;
+    uint32_t vv = Vrow;
+    int phase = 0;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+        const int v = __ffs(vv) - 1;
+        const uint32_t bv = 1u << v;
+        const bool half = (ones & bv) != 0;
+        const int sv = half ? (int)((S >> v) & 1u) : (v == h ? sh : phase);
+        o[t] = src[(size_t)(rowbase + (uint32_t)(__popc(A & (bv - 1u)) * 2 + sv)) * kLanes + lane];
+        rs[t] = (v * 2 + sv) * n2 * kLanes + lane;
+        if (!half && v != h && phase == 0) {
+            phase = 1;
+        } else {
+            vv &= vv - 1u;
+            phase = 0;
+        }
+    }
+    if (needclose) {
+        const int hc = (h * 2 + sh) * kLanes;
+#pragma unroll
+        for (int t = 0; t < NV; ++t) csum = fma(o[t], Md[rs[t] + hc], csum);
+    }
+    // this row's target slots, lane-parallel: off1 + ((hidx1 * 2 + s_h) * nA1 + ai1) * 2 + s_j
+    const uint32_t hlow = (1u << h) - 1u;
+    const uint32_t ai1 = ti.meta & 15u, nA1 = (ti.meta >> 4) & 15u, sj1 = (ti.meta >> 8) & 1u;
+    const uint32_t hi1 = (uint32_t)__popc((ti.meta >> 16) & hlow);
+    const uint32_t tslot = ti.off1 + ((hi1 * 2u + (uint32_t)sh) * nA1 + ai1) * 2u + sj1;
+    int q = 0;
+    for (; q + 1 < T; q += 2) {
+        const uint32_t ma = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
+        const uint32_t mb = __shfl_sync(0xFFFFFFFFu, ti.meta, q + 1);
+        const int ca = (int)(((ma >> 12) & 15u) * 2u + ((ma >> 8) & 1u)) * kLanes;
+        const int cb = (int)(((mb >> 12) & 15u) * 2u + ((mb >> 8) & 1u)) * kLanes;
+        double da = 0.0, db = 0.0;
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            da = fma(o[t], Ms[rs[t] + ca], da);
+            db = fma(o[t], Ms[rs[t] + cb], db);
+        }
+        const uint32_t sa = __shfl_sync(0xFFFFFFFFu, tslot, q);
+        const uint32_t sb = __shfl_sync(0xFFFFFFFFu, tslot, q + 1);
+        dst1[(size_t)sa * kLanes + lane] = da;
+        dst1[(size_t)sb * kLanes + lane] = db;
+    }
+    if (q < T) {
+        const uint32_t ma = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
+        const int ca = (int)(((ma >> 12) & 15u) * 2u + ((ma >> 8) & 1u)) * kLanes;
+        double da = 0.0;
+#pragma unroll
+        for (int t = 0; t < NV; ++t) da = fma(o[t], Ms[rs[t] + ca], da);
+        const uint32_t sa = __shfl_sync(0xFFFFFFFFu, tslot, q);
+        dst1[(size_t)sa * kLanes + lane] = da;
+    }
+}
+
+__device__ __forceinline__ void bip_row_dispatch(int nv, const double *src, double *dst1, const double *Ms,
+                                                 const double *Md, const TgtInfo &ti, int T, uint32_t Vrow,
+                                                 uint32_t A, uint32_t B, uint32_t S, uint32_t rowbase, int h, int sh,
+                                                 int n2, bool needclose, int lane, double &csum) {
+#define COS_BROW(K)                                                                                            \
+    case K:                                                                                                    \
+        bip_row<K>(src, dst1, Ms, Md, ti, T, Vrow, A, B, S, rowbase, h, sh, n2, needclose, lane, csum);        \
+        break;
+    switch (nv) {
+        COS_BROW(1)
+        COS_BROW(2)
+        COS_BROW(3)
+        COS_BROW(4)
+        COS_BROW(5)
+        COS_BROW(6)
+        COS_BROW(7)
+        COS_BROW(8)
+        COS_BROW(9)
+        COS_BROW(10)
+        COS_BROW(11)
+        COS_BROW(12)
+        COS_BROW(13)
+        COS_BROW(14)
+        COS_BROW(15)
+        COS_BROW(16)
+        COS_BROW(17)
+        default:
+            break;
+    }
+#undef COS_BROW
+}
+
+// One interaction mask: its rows, the flavor sum of the close, the seed of the next loop or
+// the sink.  seedsh = sgn 2 sigma_{l, s_0} of this lane for vertex 0's shifted start.
+__device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
+                                         int n, const double *src, double *dst1, const double *Ms,
+                                         const double *Md, int lane, int ci, int nfl, const double seedsh[2],
+                                         bool shifts, bool active, int lam, int cfg, double *out, int *status,
+                                         int prefetch) {
+    const uint32_t full = (1u << n) - 1u;
+    const uint4 mk = __ldg(tab.masks + mask_index);
+    const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, S = mk.y, code = mk.z, off = mk.w;
+    const uint32_t ones = A & ~B;
+    const uint32_t H = head_set(B, ones);
+    const uint32_t J = full & ~B;
+    const int nA = __popc(A);
+    const bool needclose = (ones != 0u) || (B == full);
+    if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
+        const uint4 nk = __ldg(tab.masks + next_index);
+        const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
+        prefetch_block(src, nk.w, 4u * (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane, prefetch);
+    }
+    const TgtInfo ti = bip_targets(A, B, S, J, code, tab.rank4, lane);
+    const int T = __popc(J) + __popc(J & ~A);
+    const int n2 = 2 * n;
+    double csum = 0.0;
+    for (uint32_t hh = H; hh; hh &= hh - 1u) {
+        const int h = __ffs(hh) - 1;
+        const int hidx = __popc(H & ((1u << h) - 1u));
+        const uint32_t Vrow = row_vmask(A, ones, h);
+        const int nv = __popc(Vrow) + __popc(Vrow & B & ~(1u << h));
+        const bool first_loop = (h == 0) && (ones & 1u);
+        const int sh0 = first_loop ? (int)(S & 1u) : 0;
+        const int sh1 = first_loop ? sh0 : 1;
+        for (int sh = sh0; sh <= sh1; ++sh) {
+            const uint32_t rowbase = off + (uint32_t)((hidx * 2 + sh) * nA * 2);
+            bip_row_dispatch(nv, src, dst1, Ms, Md, ti, T, Vrow, A, B, S, rowbase, h, sh, n2, needclose, lane, csum);
+        }
+    }
+    if (!needclose) return;   // no half-visited vertex and not full: disconnected, dropped
+    const double C = flavor_sum(csum, nfl, ci);
+    if (ones) {
+        const int k = __ffs(ones) - 1;
+        const uint32_t bk = 1u << k;
+        const int sk = (int)((S >> k) & 1u);
+        const uint32_t B1 = B | bk;
+        const uint32_t code1 = code + (uint32_t)(2 - sk) * c_p4[k];
+        const int hi1 = __popc(head_set(B1, A & ~B1) & (bk - 1u));
+        const uint32_t off1 = __ldg(tab.rank4 + code1);
+        double *tp = dst1 + (size_t)(off1 + (uint32_t)(((hi1 * 2 + sk) * nA + __popc(A & (bk - 1u))) * 2 + sk)) *
+                                kLanes + lane;
+        double val = C;
+        if (ell == 1 && shifts) val += seedsh[S & 1u];   // vertex 0 carries a shift point
+        if (k == 0) *tp += val;                           // the extension into 0' wrote it
+        else *tp = val;
+    } else if (active && (lam == 0) && out) {
+        const double c = ldexp(C, n - 1);
+        out[cfg] = c;
+        if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
+    }
+}
+
+__global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ BipArgs a) {
+    extern __shared__ __align__(16) double smem_b[];
+    __shared__ int s_batch;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int nsm = 4 * a.smem_n * a.smem_n * kLanes;
+    double *Ms = smem_b;          // extension matrices, shifted diagonal
+    double *Md = smem_b + nsm;    // close matrices times sgn w
+    double *ring = a.scratch + (size_t)blockIdx.x * 2 * a.slot_elems;
+    const int nfl = a.nf_lanes;
+    const int lam = lane % nfl;
+    const int ci = lane / nfl;
+    const double sgn = a.absmode ? 1.0 : -1.0;
+    double sig[2], seedsh[2];
+    for (int s = 0; s < 2; ++s) {
+        sig[s] = a.absmode ? fabs(a.sigma2[lam][s]) : a.sigma2[lam][s];
+        seedsh[s] = sgn * 2.0 * sig[s];
+    }
+    const bool shifts = a.shifts != 0;
+    const int nbatch = *a.n_batches;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_batch = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int b = s_batch;
+        if (b >= nbatch) break;
+        const int4 bd = a.batches[b];
+        const int n = bd.x;
+        const BipOrderTab &tab = a.tabs[n];
+        const bool active = (ci < bd.z) && (ci * nfl + nfl <= kLanes);
+        const int cfg = active ? a.batch_list[bd.y + ci] : -1;
+        const int n2 = 2 * n;
+        const double *Mc = nullptr;
+        if (active) Mc = a.M + a.moff[cfg] + (size_t)lam * n2 * n2;
+        const double cfac = sgn * a.loop_weight;
+        for (int e = warp; e < n2 * n2; e += nwarps) {
+            double val = active ? Mc[e] : 0.0;
+            if (a.absmode) val = fabs(val);
+            const int r = e / n2, c = e % n2;
+            const bool shifted = (r == c) && (r >= 2) && shifts;   // (j, s) -> (j, s), j >= 1
+            Ms[e * kLanes + lane] = shifted ? val + sgn * sig[r & 1] : val;
+            Md[e * kLanes + lane] = cfac * val;
+        }
+        // Start: the loop through the normal point of vertex 0 on sublattice s_0 (layer 1,
+        // masks mu_0 = (1, A) and (1, B); row (0, s_0), endpoint (0, s_0)).
+        if (warp == 0) {
+            for (int s0 = 0; s0 < 2; ++s0) {
+                const uint32_t off = __ldg(tab.rank4 + 1 + s0);
+                ring[(size_t)(1 & 1) * a.slot_elems + (size_t)(off + 3u * (uint32_t)s0) * kLanes + lane] = 1.0;
+            }
+        }
+        __syncthreads();
+        for (int ell = 1; ell <= 2 * n; ++ell) {
+            const double *src = ring + (size_t)(ell & 1) * a.slot_elems;
+            double *dst1 = ring + (size_t)((ell + 1) & 1) * a.slot_elems;
+            const uint32_t first = tab.layer_first[ell];
+            const uint32_t cnt = tab.layer_count[ell];
+            for (uint32_t mi = warp; mi < cnt; mi += nwarps)
+                bip_mask(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1, Ms,
+                         Md, lane, ci, nfl, seedsh, shifts, active, lam, cfg, a.out, a.status, a.prefetch);
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launch
+
+struct BipLaunch {
+    int n_cfg = 0;
+    int n_max = 0;
+    const int32_t *order = nullptr;
+    const double *M = nullptr;
+    const int64_t *moff = nullptr;
+    int n_mat = 1;
+    int loop_weight = 1;
+    double sigma2[COS_MAX_FLAVORS][2] = {};
+    bool shifts = false;
+    double *out = nullptr;
+    bool absmode = false;
+};
+
+static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t stream) {
+    std::string err;
+    const BipOrderTab *tabs = bip_device_orders(ws->device, &err);
+    if (!tabs) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
+    const size_t slot_elems = (size_t)bip_host_order(L.n_max).max_slots * kLanes;
+    const size_t per_cta = 2 * slot_elems * sizeof(double);
+    const int cpb = kLanes / L.n_mat;
+    const int max_batches = (L.n_cfg + cpb - 1) / cpb + COS_NMAX;
+    int grid = std::max(1, std::min(nsm, max_batches));
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+        const size_t avail = ws->scratch_bytes + (size_t)(0.85 * (double)free_b);
+        while (grid > 1 && (size_t)grid * per_cta > avail) grid = std::max(1, grid / 2);
+    }
+    ws->last_grid = grid;
+    cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "bipartite layer scratch");
+    if (st != COS_OK) return st;
+    const size_t smem = 2 * (size_t)4 * L.n_max * L.n_max * kLanes * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(dp_bip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "bipartite smem attribute");
+    BipArgs a;
+    memset(&a, 0, sizeof a);
+    a.tabs = tabs;
+    a.batches = ws->batches;
+    a.n_batches = ws->plan_counts + 64;
+    a.batch_list = ws->batch_list;
+    a.queue = ws->queue;
+    a.M = L.M;
+    a.moff = L.moff;
+    a.nf_lanes = L.n_mat;
+    a.loop_weight = (double)L.loop_weight;
+    memcpy(a.sigma2, L.sigma2, sizeof a.sigma2);
+    a.shifts = L.shifts ? 1 : 0;
+    a.absmode = L.absmode ? 1 : 0;
+    a.scratch = reinterpret_cast<double *>(ws->scratch);
+    a.slot_elems = slot_elems;
+    a.smem_n = L.n_max;
+    a.prefetch = 1;
+    a.out = L.out;
+    a.status = ws->status;
+    e = cudaMemsetAsync(ws->queue, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+    dp_bip_kernel<<<grid, 512, smem, stream>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "bipartite dp launch");
+    return COS_OK;
+}
+
+static cos_status run_bip(Workspace *ws, BipLaunch L, double *d_abs_mass, cudaStream_t stream) {
+    cos_status st = launch_plan_batches(ws, L.n_cfg, L.n_max, L.order, kLanes / L.n_mat, stream);
+    if (st != COS_OK) return st;
+    st = launch_bip(ws, L, stream);
+    if (st != COS_OK || !d_abs_mass) return st;
+    L.out = d_abs_mass;
+    L.absmode = true;
+    return launch_bip(ws, L, stream);
+}
+
+static cos_status check_bip(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff, int n_mat,
+                            int loop_weight, const double *d_M4, cos_precision precision, const double *d_out,
+                            const char *fn) {
+    if (n_cfg < 0 || n_mat < 1 || n_mat > COS_MAX_FLAVORS || loop_weight < 1) {
+        set_error(std::string(fn) + ": n_cfg < 0, n_mat outside [1, 8] or loop_weight < 1");
+        return COS_ERR_ARG;
+    }
+    if (n_max < 1 || n_max > COS_BIP_NMAX) {
+        set_error(std::string(fn) + ": n_max outside [1, 9]");
+        return COS_ERR_ORDER;
+    }
+    if (precision != COS_FP64) {
+        set_error(std::string(fn) + ": only COS_FP64 is implemented for bipartite sums");
+        return COS_ERR_UNIMPLEMENTED;
+    }
+    if (n_cfg > 0 && (!d_order || !d_moff || !d_M4 || !d_out)) {
+        set_error(std::string(fn) + ": null device pointer");
+        return COS_ERR_ARG;
+    }
+    return COS_OK;
+}
+
+cos_status bip_matrices_body(Workspace *ws, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                             int n_mat, int loop_weight, const double *h_sigma2, const double *d_M4, double *d_out,
+                             double *d_abs_mass, cudaStream_t stream) {
+    BipLaunch L;
+    L.n_cfg = n_cfg;
+    L.n_max = n_max;
+    L.order = d_order;
+    L.M = d_M4;
+    L.moff = d_moff;
+    L.n_mat = n_mat;
+    L.loop_weight = loop_weight;
+    for (int l = 0; l < n_mat; ++l)
+        for (int s = 0; s < 2; ++s) {
+            L.sigma2[l][s] = h_sigma2 ? h_sigma2[l * 2 + s] : 0.0;
+            if (L.sigma2[l][s] != 0.0) L.shifts = true;
+        }
+    L.out = d_out;
+    return run_bip(ws, L, d_abs_mass, stream);
+}
+
+}  // namespace cosdp
+
+using namespace cosdp;
+
+extern "C" cos_status cos_connected_sum_bipartite_matrices(int n_cfg, int n_max, const int32_t *d_order,
+                                                           const int64_t *d_moff, int n_mat, int loop_weight,
+                                                           const double *h_sigma2, const double *d_M4,
+                                                           cos_precision precision, double *d_out,
+                                                           double *d_abs_mass, cos_stream_t stream) {
+    cos_status st = check_bip(n_cfg, n_max, d_order, d_moff, n_mat, loop_weight, d_M4, precision, d_out,
+                              "cos_connected_sum_bipartite_matrices");
+    if (st != COS_OK || n_cfg == 0) return st;
+    std::string err;
+    Workspace *ws = get_workspace((cudaStream_t)stream, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    return bip_matrices_body(ws, n_cfg, n_max, d_order, d_moff, n_mat, loop_weight, h_sigma2, d_M4, d_out,
+                             d_abs_mass, (cudaStream_t)stream);
+}
+
+extern "C" cos_status cos_bipartite_structure(int n, cos_structure_info *info) {
+    if (n < 1 || n > COS_BIP_NMAX) {
+        set_error("cos_bipartite_structure: order out of range");
+        return COS_ERR_ORDER;
+    }
+    if (!info) {
+        set_error("cos_bipartite_structure: null info");
+        return COS_ERR_ARG;
+    }
+    *info = bip_host_order(n).info;
+    return COS_OK;
+}

@@ -207,6 +207,10 @@ cos_status batch_body(Workspace *ws, const cos_tables *t, int n_cfg, int n_max, 
                       double *d_out, double *d_abs_mass, cudaStream_t stream);
 int dp_max_active_ctas(int precision, int threads, size_t smem);
 
+cos_status bip_matrices_body(Workspace *ws, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                             int n_mat, int loop_weight, const double *h_sigma2, const double *d_M4, double *d_out,
+                             double *d_abs_mass, cudaStream_t stream);
+
 cos_status launch_gather(const cos_tables *t, int n_cfg, const int32_t *order, const int64_t *offset,
                          const int32_t *site, const double *tau, const int64_t *moff, int64_t mstride,
                          double *M, int *status, cudaStream_t stream);
@@ -220,6 +224,9 @@ struct cos_tables {
     int n_mat;
     int symmetric;
     double sigma[COS_MAX_FLAVORS];
-    double *d_G;
+    double *d_G;              // square: [n_mat][L^2][n_tau]; honeycomb: [n_mat][2][2][L^2][n_tau]
     double *d_dG;
+    int bipartite = 0;        // honeycomb (two-band) tables
+    std::vector<double> delta;
+    double sigma2[COS_MAX_FLAVORS][2] = {};   // honeycomb: shift weight per (flavor, sublattice)
 };

@@ -241,6 +241,9 @@ extern "C" cos_status cos_get_tables_info(const cos_tables *t, cos_tables_info *
     for (int l = 0; l < COS_MAX_FLAVORS; ++l) info->sigma[l] = t->sigma[l];
     info->d_G = t->d_G;
     info->d_dGdmu = t->d_dG;
+    info->bipartite = t->bipartite;
+    for (int l = 0; l < COS_MAX_FLAVORS; ++l)
+        for (int s = 0; s < 2; ++s) info->sigma2[l][s] = t->sigma2[l][s];
     return COS_OK;
 }
 
@@ -250,11 +253,15 @@ extern "C" cos_status cos_copy_table(const cos_tables *t, int which, double *d_d
         set_error("cos_copy_table: bad argument");
         return COS_ERR_ARG;
     }
+    if (which == 1 && t->bipartite) {
+        set_error("cos_copy_table: honeycomb tables have no dG/dmu table");
+        return COS_ERR_ARG;
+    }
     if (which == 1) {
         cos_status st = ensure_dtables(const_cast<cos_tables *>(t), (cudaStream_t)stream);
         if (st != COS_OK) return st;
     }
-    const size_t n = (size_t)t->n_mat * t->model.L * t->model.L * t->model.n_tau;
+    const size_t n = (size_t)t->n_mat * (t->bipartite ? 4 : 1) * t->model.L * t->model.L * t->model.n_tau;
     cudaError_t e = cudaMemcpyAsync(d_dst, which ? t->d_dG : t->d_G, n * sizeof(double), cudaMemcpyDeviceToDevice,
                                     (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cos_copy_table");

@@ -118,3 +118,56 @@ def test_binding_wraps_every_entry_point():
             assert hasattr(owner, attr), name
         else:
             assert callable(getattr(B, name, None)), name
+
+
+def count_bipartite(n):
+    """Independent count of the bipartite structure: masks in {0, 1A, 1B, 2}^n with vertex 0
+    visited, rows (h, s_h) -- one for the first loop's head, else two -- and reachable
+    endpoint states (one for a half-visited endpoint or v = h, else two sublattices)."""
+    full = (1 << n) - 1
+    masks = slots = states = ext = close = 0
+    for d in itertools.product(range(4), repeat=n):
+        if d[0] == 0:
+            continue
+        masks += 1
+        A = sum(1 << i for i in range(n) if d[i] > 0)
+        B = sum(1 << i for i in range(n) if d[i] == 3)
+        ones = A & ~B
+        H = [0] if ones & 1 else [i for i in range(n) if B >> i & 1]
+        slots += 4 * len(H) * bin(A).count("1")
+        T = sum(2 if d[j] == 0 else 1 for j in range(n) if d[j] != 3)
+        need = ones != 0 or B == full
+        for h in H:
+            rows = 1 if (h == 0 and ones & 1) else 2
+            if h == 0 and ones & 1:
+                V = [0] if A == 1 else [v for v in range(1, n) if A >> v & 1]
+            elif h == 0:
+                V = [v for v in range(n) if A >> v & 1]
+            else:
+                V = [v for v in range(1, n) if A >> v & 1
+                     and not (v == h and any(ones >> o & 1 for o in range(h)))]
+            nv = sum(1 if (ones >> v & 1 or v == h) else 2 for v in V)
+            states += rows * nv
+            ext += rows * nv * T
+            close += rows * nv if need else 0
+    return masks, slots, states, ext, close
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6])
+def test_bipartite_structure_counts(n):
+    inf = B.cos_bipartite_structure(n)
+    masks, slots, states, ext, close = count_bipartite(n)
+    assert (inf.masks, inf.slots, inf.states, inf.fma_ext, inf.fma_close) == (masks, slots, states, ext, close)
+
+
+def test_bipartite_argument_errors():
+    lib = B.lib()
+    import ctypes
+    fake = ctypes.c_void_p(256)     # never dereferenced: rejected before any launch
+    assert lib.cos_connected_sum_bipartite_matrices(1, 10, fake, fake, 1, 1, None, fake, 0, fake, None, None) == -2
+    assert lib.cos_connected_sum_bipartite_matrices(1, 4, fake, fake, 1, 1, None, fake, 1, fake, None, None) == -6
+    assert lib.cos_connected_sum_bipartite_matrices(1, 4, None, fake, 1, 1, None, fake, 0, fake, None, None) == -1
+    assert lib.cos_connected_sum_bipartite_matrices(0, 4, None, None, 1, 1, None, None, 0, None, None, None) == 0
+    assert lib.cos_connected_sum_bipartite_batch(None, 1, 4, fake, fake, fake, fake, 0, fake, None, None) == -1
+    inf = B.cos_structure_info()
+    assert lib.cos_bipartite_structure(10, ctypes.byref(inf)) == -2

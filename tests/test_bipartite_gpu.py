@@ -1,0 +1,174 @@
+"""GPU parity of the bipartite (two-sublattice) path against the oracle.
+
+The oracle value is the definition: the sum over every sublattice assignment of the merged DP
+(`oracle.bip(..., method="sum_dp")`, long double), itself pinned against the closed form,
+brute force and the sublattice-resolved DP of Alg. 1-2 in test_oracle_bip_pins.
+Tolerance: |err| <= 64 n 2^-53 mass, the FP64 bound of the square-lattice tests; the mass
+(the same DP on |M4|, |sigma| with all signs +) sums the assignments' masses.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from oracle import honeycomb as HC
+from paper_2507_12349_b300 import binding as B
+from paper_2507_12349_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+EPS64 = 2.0 ** -53
+
+
+def bound(n, mass):
+    return 64 * n * EPS64 * mass
+
+
+def rand_m4(seed, ncfg, nf, n, scale=0.9):
+    M = I.random_matrices(seed, ncfg, nf, 2 * n, scale)         # [cfg][nf][2n][2n], index i*2 + s
+    return [np.ascontiguousarray(m.reshape(nf, n, 2, n, 2)) for m in M]
+
+
+def run(M4s, n_mat, wt, sigma2, abs_mass=False, n_max=None):
+    order = np.array([m.shape[1] for m in M4s], dtype=np.int32)
+    moff = B.bipartite_matrix_offsets(order, n_mat)
+    flat = np.concatenate([m.ravel() for m in M4s])
+    d_order = torch.tensor(order, device="cuda")
+    d_moff = torch.tensor(moff, device="cuda")
+    d_M = torch.tensor(flat, device="cuda")
+    out = torch.full((len(M4s),), float("nan"), dtype=torch.float64, device="cuda")
+    mass = torch.full_like(out, float("nan")) if abs_mass else None
+    n_max = int(order.max()) if n_max is None else n_max
+    B.cos_connected_sum_bipartite_matrices(n_max, d_order, d_moff, n_mat, wt, sigma2, d_M, "fp64", out, mass)
+    B.cos_sync_status()
+    return out.cpu().numpy(), (mass.cpu().numpy() if abs_mass else None)
+
+
+CASES = [  # n, n_mat, loop weight, shifts, configurations
+    (1, 2, 1, True, 5), (2, 1, 2, False, 9), (3, 2, 1, True, 17), (4, 1, 3, True, 33), (4, 3, 1, False, 7),
+    (5, 2, 1, True, 12), (6, 1, 2, True, 6), (7, 2, 1, False, 3),
+]
+
+
+@pytest.mark.parametrize("n,n_mat,wt,shifts,ncfg", CASES)
+def test_bipartite_matches_oracle(n, n_mat, wt, shifts, ncfg):
+    M4s = rand_m4(500 + 10 * n + n_mat, ncfg, n_mat, n)
+    s2 = np.array([[0.11 - 0.05 * l, -0.07 + 0.04 * l] for l in range(n_mat)]) if shifts else None
+    got, mass = run(M4s, n_mat, wt, None if s2 is None else s2.tolist(), abs_mass=True)
+    for c in sorted({0, ncfg // 2, ncfg - 1}):
+        ref = O.bip(M4s[c], s2, weight=wt, method="sum_dp", prec="ld")
+        rmass = O.bip(M4s[c], s2, weight=wt, method="sum_dp", absmode=True)
+        assert abs(got[c] - ref) <= bound(n, rmass), (c, got[c], ref, rmass)
+        assert mass[c] == pytest.approx(rmass, rel=1e-12)
+
+
+def test_bipartite_uneven_orders_and_order9():
+    """Orders 1..9 in one launch.  At n = 9 (512 assignments) the equal-block identity gives
+    the reference: every assignment sees the same matrices, so c_bip = 2^9 c."""
+    orders = [9, 3, 8, 1, 6, 2, 7, 5, 4, 9]
+    M4s = []
+    for c, n in enumerate(orders):
+        if n == 9:
+            M = I.random_matrices(900 + c, 1, 2, n, 0.9)[0]
+            M4s.append(np.ascontiguousarray(np.broadcast_to(M[:, :, None, :, None], (2, n, 2, n, 2))))
+        else:
+            M4s.append(rand_m4(700 + c, 1, 2, n)[0])
+    sig = [0.06, -0.09]
+    s2 = [[sig[0], sig[0]], [sig[1], sig[1]]]
+    got, mass = run(M4s, 2, 1, s2, abs_mass=True)
+    for c, n in enumerate(orders):
+        if n == 9:
+            M = M4s[c][:, :, 0, :, 0]
+            ref = 2 ** 9 * O.dp(M, sig, prec="ld")
+            rmass = 2 ** 9 * O.dp(M, sig, absmode=True)
+        else:
+            ref = O.bip(M4s[c], np.array(s2), method="sum_dp", prec="ld")
+            rmass = O.bip(M4s[c], np.array(s2), method="sum_dp", absmode=True)
+        assert abs(got[c] - ref) <= bound(n, rmass), (c, n, got[c], ref)
+
+
+def test_bipartite_deterministic():
+    M4s = rand_m4(33, 40, 2, 5)
+    a, _ = run(M4s, 2, 1, [[0.1, -0.1], [0.05, 0.02]])
+    b, _ = run(M4s, 2, 1, [[0.1, -0.1], [0.05, 0.02]])
+    assert np.array_equal(a, b)
+
+
+def small_hc_model():
+    m = I.WORKLOADS["hc_su2_af_n8"].model
+    return I.HoneycombModel(6, m.t, m.beta, m.U, (0.1, -0.05), (0.02, 0.0), m.delta, 257)
+
+
+def test_honeycomb_tables_match_oracle():
+    for model in (small_hc_model(), I.WORKLOADS["hc_su2_af_n8"].model):
+        tabs = B.honeycomb_tables_for(model)
+        got = tabs.table().cpu().numpy()
+        ref = HC.hc_model_tables(model)
+        assert got.shape == ref.shape
+        assert np.max(np.abs(got - ref)) < 1e-13
+        inf = tabs.info()
+        assert inf.bipartite == 1
+        for l in range(model.n_flavors):
+            assert list(inf.sigma2[l]) == pytest.approx(list(model.sigma2[l]), rel=1e-15)
+        tabs.close()
+
+
+def test_honeycomb_symmetric_tables_collapse():
+    m = I.HoneycombModel(4, 1.0, 3.0, 2.0, (0.1, 0.1), (0.0, 0.0), (0.2, 0.2), 65)
+    tabs = B.honeycomb_tables_for(m)
+    inf = tabs.info()
+    assert inf.symmetric == 1 and inf.n_mat == 1
+    tabs.close()
+
+
+def test_bipartite_gather_and_batch_vs_oracle():
+    model = small_hc_model()
+    cfgs = I.make_configs(model, 3, 6, 60, 11)
+    tabs = B.honeycomb_tables_for(model)
+    d = B.configs_to_device(cfgs)
+    moff = B.bipartite_matrix_offsets(cfgs.order, 2)
+    total = int(moff[-1] + 2 * (2 * int(cfgs.order[-1])) ** 2)
+    M4 = torch.full((total,), float("nan"), dtype=torch.float64, device="cuda")
+    B.cos_gather_bipartite(tabs, *d, torch.tensor(moff, device="cuda"), M4)
+    out = torch.full((60,), float("nan"), dtype=torch.float64, device="cuda")
+    mass = torch.full_like(out, float("nan"))
+    B.cos_connected_sum_bipartite_batch(tabs, 6, *d, "fp64", out, mass)
+    B.cos_sync_status()
+    g = M4.cpu().numpy()
+    otabs = HC.hc_model_tables(model)
+    s2 = np.array(model.sigma2)
+    got, gmass = out.cpu().numpy(), mass.cpu().numpy()
+    for c in (0, 17, 59):
+        n = int(cfgs.order[c])
+        o = int(cfgs.offset[c])
+        ref_M4 = HC.hc_gather_one(otabs, cfgs.site[o:o + n], cfgs.tau[o:o + n], model.L, model.beta)
+        blk = g[moff[c]:moff[c] + 2 * 4 * n * n].reshape(2, n, 2, n, 2)
+        assert np.max(np.abs(blk - ref_M4)) < 1e-13
+        ref = O.bip(ref_M4, s2, method="sum_dp", prec="ld")
+        rmass = O.bip(ref_M4, s2, method="sum_dp", absmode=True)
+        assert abs(got[c] - ref) <= bound(n, rmass) + 1e-13 * rmass, (c, got[c], ref)
+        assert gmass[c] == pytest.approx(rmass, rel=1e-10)
+    tabs.close()
+
+
+def test_workload_honeycomb_order8_sampled():
+    """SU(2) honeycomb with an antiferromagnetic staggered shift, n = 8: sampled configurations
+    against the oracle's sum over the 256 sublattice assignments."""
+    w = I.WORKLOADS["hc_su2_af_n8"]
+    cfgs = I.workload_configs(w, 256)
+    tabs = B.honeycomb_tables_for(w.model)
+    d = B.configs_to_device(cfgs)
+    out = torch.full((256,), float("nan"), dtype=torch.float64, device="cuda")
+    B.cos_connected_sum_bipartite_batch(tabs, 8, *d, "fp64", out)
+    B.cos_sync_status()
+    got = out.cpu().numpy()
+    otabs = HC.hc_model_tables(w.model)
+    s2 = np.array(w.model.sigma2)
+    for c in (0, 255):
+        o = int(cfgs.offset[c])
+        M4 = HC.hc_gather_one(otabs, cfgs.site[o:o + 8], cfgs.tau[o:o + 8], w.model.L, w.model.beta)
+        ref = O.bip(M4, s2, method="sum_dp", prec="ld")
+        rmass = O.bip(M4, s2, method="sum_dp", absmode=True)
+        assert abs(got[c] - ref) <= max(1e-10 * abs(ref), bound(8, rmass)), (c, got[c], ref, rmass)
+    tabs.close()
