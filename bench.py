@@ -52,11 +52,15 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
     p.add_argument("--n-cfg", type=int, default=0, help="smaller configuration count (profiling runs only)")
-    p.add_argument("--workload", default=WORKLOAD, choices=sorted(I.WORKLOADS),
+    p.add_argument("--workload", default=WORKLOAD,
+                   choices=sorted(k for k, v in I.WORKLOADS.items() if isinstance(v.model, I.Model)),
                    help="profiling runs only: run this workload's DP instead of the headline")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "df64"], help="profiling runs only")
     p.add_argument("--grad", action="store_true",
                    help="profiling runs only: time the gradient call (adjoint DP) instead of the forward")
+    p.add_argument("--bipartite", action="store_true",
+                   help="profiling runs only: time the honeycomb workload's bipartite step (gather + DP)")
+    p.add_argument("--order", type=int, default=0, help="with --bipartite: order of the configurations")
     return p.parse_args()
 
 
@@ -456,6 +460,27 @@ def measure_subsets(torch, B, flush_buf, n_cfg):
             "root0_cost_vs_plain": t0 / tp}
 
 
+def measure_bipartite(torch, B, flush_buf, n_cfg):
+    """Honeycomb workload (SU(2), antiferromagnetic staggered shift, n = 8; sublattices summed
+    per vertex by the sublattice-resolved DP): gather + bipartite DP from vertex coordinates."""
+    w = I.WORKLOADS["hc_su2_af_n8"]
+    cfgs = I.workload_configs(w, n_cfg)
+    tabs = B.honeycomb_tables_for(w.model)
+    n_mat = tabs.info().n_mat
+    d = B.configs_to_device(cfgs)
+    out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
+    fn = lambda: B.cos_connected_sum_bipartite_batch(tabs, 8, *d, "fp64", out)
+    fn()
+    B.cos_sync_status()
+    t = statistics.mean(time_steps(torch, fn, 2, lambda: flush_l2(flush_buf)))
+    B.cos_sync_status()
+    s = B.cos_bipartite_structure(8)
+    fl = n_cfg * n_mat * 2.0 * (s.fma_ext + s.fma_close)
+    tabs.close()
+    return {"configs": n_cfg, "configs_per_s": n_cfg / t, "tflops": fl / t / 1e12, "ms": t * 1e3,
+            "assignments_per_config": 256}
+
+
 def measure_forms(torch, B, flush_buf):
     """The other forms of the path on the same GPU: FP64 vs mixed vs double-float (df64)
     precision at orders 8 and 10,
@@ -505,6 +530,7 @@ def measure_forms(torch, B, flush_buf):
     res["su6_uneven_n4_12_fp64_graph"], _ = run("su6_sym_uneven_n4_12", 200_000, "fp64", steps=1, graph=True)
     res["su4_n10_adjoint"] = measure_adjoint(torch, B, flush_buf, 50_000)
     res["su4_n8_all_subsets_fp64"] = measure_subsets(torch, B, flush_buf, 100_000)
+    res["hc_su2_af_n8_bipartite_fp64"] = measure_bipartite(torch, B, flush_buf, I.WORKLOADS["hc_su2_af_n8"].n_cfg)
     # plain FP64 per-configuration form: one configuration per call, no graph
     w = I.WORKLOADS[WORKLOAD]
     cfgs = I.workload_configs(w, 200)
@@ -530,10 +556,43 @@ def measure_forms(torch, B, flush_buf):
     return res, keep
 
 
+def bipartite_arm(args):
+    """Profiling runs of the bipartite path alone: the honeycomb workload's gather + DP from
+    vertex coordinates, at its order or --order, --n-cfg configurations, CUDA-event timing."""
+    import torch
+    from paper_2507_12349_b300 import binding as B
+    B.lib()
+    w = I.WORKLOADS["hc_su2_af_n8"]
+    n = args.order if args.order > 0 else w.n_lo
+    n_cfg = args.n_cfg if args.n_cfg > 0 else w.n_cfg
+    cfgs = I.make_configs(w.model, n, n, n_cfg, w.seed)
+    tabs = B.honeycomb_tables_for(w.model)
+    n_mat = tabs.info().n_mat
+    d = B.configs_to_device(cfgs)
+    out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
+    flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    fn = lambda: B.cos_connected_sum_bipartite_batch(tabs, n, *d, "fp64", out)
+    for _ in range(max(1, args.warmup)):
+        fn()
+    B.cos_sync_status()
+    ts = time_steps(torch, fn, args.steps, lambda: flush_l2(flush_buf))
+    B.cos_sync_status()
+    s = B.cos_bipartite_structure(n)
+    t = statistics.mean(ts)
+    fl = n_cfg * n_mat * 2.0 * (s.fma_ext + s.fma_close)
+    print(json.dumps({"metric": "bipartite connected-sum configs/s (honeycomb, sublattices summed)",
+                      "value": n_cfg / t, "unit": "configs/s", "order": n, "configs": n_cfg,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+                      "tflops": fl / t / 1e12, "dtype": "f64"}), flush=True)
+    tabs.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.bipartite:
+        bipartite_arm(args)
     else:
         native_arm(args)
 
