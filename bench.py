@@ -460,7 +460,7 @@ def measure_subsets(torch, B, flush_buf, n_cfg):
             "root0_cost_vs_plain": t0 / tp}
 
 
-def measure_bipartite(torch, B, flush_buf, n_cfg):
+def measure_bipartite(torch, B, flush_buf, n_cfg, precision="fp64"):
     """Honeycomb workload (SU(2), antiferromagnetic staggered shift, n = 8; sublattices summed
     per vertex by the sublattice-resolved DP): gather + bipartite DP from vertex coordinates."""
     w = I.WORKLOADS["hc_su2_af_n8"]
@@ -469,7 +469,7 @@ def measure_bipartite(torch, B, flush_buf, n_cfg):
     n_mat = tabs.info().n_mat
     d = B.configs_to_device(cfgs)
     out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
-    fn = lambda: B.cos_connected_sum_bipartite_batch(tabs, 8, *d, "fp64", out)
+    fn = lambda: B.cos_connected_sum_bipartite_batch(tabs, 8, *d, precision, out)
     fn()
     B.cos_sync_status()
     t = statistics.mean(time_steps(torch, fn, 2, lambda: flush_l2(flush_buf)))
@@ -531,6 +531,8 @@ def measure_forms(torch, B, flush_buf):
     res["su4_n10_adjoint"] = measure_adjoint(torch, B, flush_buf, 50_000)
     res["su4_n8_all_subsets_fp64"] = measure_subsets(torch, B, flush_buf, 100_000)
     res["hc_su2_af_n8_bipartite_fp64"] = measure_bipartite(torch, B, flush_buf, I.WORKLOADS["hc_su2_af_n8"].n_cfg)
+    res["hc_su2_af_n8_bipartite_df64"] = measure_bipartite(torch, B, flush_buf, I.WORKLOADS["hc_su2_af_n8"].n_cfg,
+                                                           "df64")
     # plain FP64 per-configuration form: one configuration per call, no graph
     w = I.WORKLOADS[WORKLOAD]
     cfgs = I.workload_configs(w, 200)
@@ -571,7 +573,7 @@ def bipartite_arm(args):
     d = B.configs_to_device(cfgs)
     out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
     flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    fn = lambda: B.cos_connected_sum_bipartite_batch(tabs, n, *d, "fp64", out)
+    fn = lambda: B.cos_connected_sum_bipartite_batch(tabs, n, *d, args.precision, out)
     for _ in range(max(1, args.warmup)):
         fn()
     B.cos_sync_status()
@@ -583,7 +585,8 @@ def bipartite_arm(args):
     print(json.dumps({"metric": "bipartite connected-sum configs/s (honeycomb, sublattices summed)",
                       "value": n_cfg / t, "unit": "configs/s", "order": n, "configs": n_cfg,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
-                      "tflops": fl / t / 1e12, "dtype": "f64"}), flush=True)
+                      "tflops": fl / t / 1e12, "dtype": {"fp64": "f64", "df64": "f32 pairs (df64)"}.get(
+                          args.precision, args.precision)}), flush=True)
     tabs.close()
 
 

@@ -253,8 +253,8 @@ cos_status cos_gather_bipartite(const cos_tables *tables, int n_cfg, const int32
 
 /* Bipartite connected sums of explicit matrices: d_M4 as written by cos_gather_bipartite
  * (blocks [n_mat][2 n_c][2 n_c] at d_moff[c]); h_sigma2 = NULL or host [n_mat][2] shift weights
- * per (flavor, sublattice).  n_max <= COS_BIP_NMAX; precision COS_FP64 only
- * (COS_ERR_UNIMPLEMENTED otherwise).  Other arguments, outputs and errors as
+ * per (flavor, sublattice).  n_max <= COS_BIP_NMAX; precision COS_FP64 or COS_DF64
+ * (COS_ERR_UNIMPLEMENTED for COS_MIXED).  Other arguments, outputs and errors as
  * cos_connected_sum_matrices (d_abs_mass: the same DP on |M4|, |sigma| with all signs +). */
 cos_status cos_connected_sum_bipartite_matrices(int n_cfg, int n_max, const int32_t *d_order,
                                                 const int64_t *d_moff, int n_mat, int loop_weight,

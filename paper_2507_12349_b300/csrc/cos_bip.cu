@@ -214,7 +214,7 @@ struct BipArgs {
     double sigma2[COS_MAX_FLAVORS][2];
     int shifts;
     int absmode;
-    double *scratch;
+    void *scratch;              // layer ring, 8-byte elements (double or df64)
     size_t slot_elems;
     int smem_n;                 // n_max (shared-memory stride 2 n_max)
     int prefetch;
@@ -256,14 +256,43 @@ __device__ __forceinline__ TgtInfo bip_targets(uint32_t A, uint32_t B, uint32_t 
     return ti;
 }
 
+// Arithmetic of the bipartite sweep for a state type: FP64 multiply-adds, or the double-float
+// compensated accumulation of cos_df64.cuh (states stored as the accumulator leaves them).
+template <typename T>
+struct BipArith;
+template <>
+struct BipArith<double> {
+    using Acc = double;
+    static __device__ __forceinline__ Acc zero() { return 0.0; }
+    static __device__ __forceinline__ Acc first(double x, double y) { return x * y; }
+    static __device__ __forceinline__ void mad(Acc &a, double x, double y) { a = fma(x, y, a); }
+    static __device__ __forceinline__ double store(Acc a) { return a; }
+    static __device__ __forceinline__ double close_sum(Acc a, int nfl, int ci) { return flavor_sum(a, nfl, ci); }
+    static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+    static __device__ __forceinline__ double to_double(double a) { return a; }
+};
+template <>
+struct BipArith<df64> {
+    using Acc = DotAcc;
+    static __device__ __forceinline__ Acc zero() { return DotAcc{0.0f, 0.0f}; }
+    static __device__ __forceinline__ Acc first(df64 x, df64 y) { return dot_first(x, y); }
+    static __device__ __forceinline__ void mad(Acc &a, df64 x, df64 y) { dot_add(a, x, y); }
+    static __device__ __forceinline__ df64 store(Acc a) { return df64{a.s, a.c}; }
+    static __device__ __forceinline__ df64 close_sum(Acc a, int nfl, int ci) {
+        return df64_flavor_sum(dot_value(a), nfl, ci);
+    }
+    static __device__ __forceinline__ df64 add(df64 a, df64 b) { return df64_add(a, b); }
+    static __device__ __forceinline__ double to_double(df64 a) { return df64_to_double(a); }
+};
+
 // One row (mu, h, s_h): NV reachable endpoint states, the close, every extension.
-template <int NV>
-__device__ __forceinline__ void bip_row(const double *__restrict__ src, double *__restrict__ dst1,
-                                        const double *__restrict__ Ms, const double *__restrict__ Md,
-                                        const TgtInfo &ti, int T, uint32_t Vrow, uint32_t A, uint32_t B, uint32_t S,
-                                        uint32_t rowbase, int h, int sh, int n2, bool needclose, int lane,
-                                        double &csum) {
-    double o[NV];
+template <typename T, int NV>
+__device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict__ dst1, const T *__restrict__ Ms,
+                                        const T *__restrict__ Md, const TgtInfo &ti, int nT, uint32_t Vrow,
+                                        uint32_t A, uint32_t B, uint32_t S, uint32_t rowbase, int h, int sh, int n2,
+                                        bool needclose, int lane, typename BipArith<T>::Acc &csum) {
+    using Ar = BipArith<T>;
+    T o[NV];
     int rs[NV];
     const uint32_t ones = A & ~B;
     uint32_t vv = Vrow;
@@ -286,7 +315,7 @@ __device__ __forceinline__ void bip_row(const double *__restrict__ src, double *
     if (needclose) {
         const int hc = (h * 2 + sh) * kLanes;
 #pragma unroll
-        for (int t = 0; t < NV; ++t) csum = fma(o[t], Md[rs[t] + hc], csum);
+        for (int t = 0; t < NV; ++t) Ar::mad(csum, o[t], Md[rs[t] + hc]);
     }
     // this row's target slots, lane-parallel: off1 + ((hidx1 * 2 + s_h) * nA1 + ai1) * 2 + s_j
     const uint32_t hlow = (1u << h) - 1u;
@@ -294,40 +323,42 @@ __device__ __forceinline__ void bip_row(const double *__restrict__ src, double *
     const uint32_t hi1 = (uint32_t)__popc((ti.meta >> 16) & hlow);
     const uint32_t tslot = ti.off1 + ((hi1 * 2u + (uint32_t)sh) * nA1 + ai1) * 2u + sj1;
     int q = 0;
-    for (; q + 1 < T; q += 2) {
+    for (; q + 1 < nT; q += 2) {
         const uint32_t ma = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
         const uint32_t mb = __shfl_sync(0xFFFFFFFFu, ti.meta, q + 1);
         const int ca = (int)(((ma >> 12) & 15u) * 2u + ((ma >> 8) & 1u)) * kLanes;
         const int cb = (int)(((mb >> 12) & 15u) * 2u + ((mb >> 8) & 1u)) * kLanes;
-        double da = 0.0, db = 0.0;
+        typename Ar::Acc da = Ar::first(o[0], Ms[rs[0] + ca]);
+        typename Ar::Acc db = Ar::first(o[0], Ms[rs[0] + cb]);
 #pragma unroll
-        for (int t = 0; t < NV; ++t) {
-            da = fma(o[t], Ms[rs[t] + ca], da);
-            db = fma(o[t], Ms[rs[t] + cb], db);
+        for (int t = 1; t < NV; ++t) {
+            Ar::mad(da, o[t], Ms[rs[t] + ca]);
+            Ar::mad(db, o[t], Ms[rs[t] + cb]);
         }
         const uint32_t sa = __shfl_sync(0xFFFFFFFFu, tslot, q);
         const uint32_t sb = __shfl_sync(0xFFFFFFFFu, tslot, q + 1);
-        dst1[(size_t)sa * kLanes + lane] = da;
-        dst1[(size_t)sb * kLanes + lane] = db;
+        dst1[(size_t)sa * kLanes + lane] = Ar::store(da);
+        dst1[(size_t)sb * kLanes + lane] = Ar::store(db);
     }
-    if (q < T) {
+    if (q < nT) {
         const uint32_t ma = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
         const int ca = (int)(((ma >> 12) & 15u) * 2u + ((ma >> 8) & 1u)) * kLanes;
-        double da = 0.0;
+        typename Ar::Acc da = Ar::first(o[0], Ms[rs[0] + ca]);
 #pragma unroll
-        for (int t = 0; t < NV; ++t) da = fma(o[t], Ms[rs[t] + ca], da);
+        for (int t = 1; t < NV; ++t) Ar::mad(da, o[t], Ms[rs[t] + ca]);
         const uint32_t sa = __shfl_sync(0xFFFFFFFFu, tslot, q);
-        dst1[(size_t)sa * kLanes + lane] = da;
+        dst1[(size_t)sa * kLanes + lane] = Ar::store(da);
     }
 }
 
-__device__ __forceinline__ void bip_row_dispatch(int nv, const double *src, double *dst1, const double *Ms,
-                                                 const double *Md, const TgtInfo &ti, int T, uint32_t Vrow,
-                                                 uint32_t A, uint32_t B, uint32_t S, uint32_t rowbase, int h, int sh,
-                                                 int n2, bool needclose, int lane, double &csum) {
+template <typename T>
+__device__ __forceinline__ void bip_row_dispatch(int nv, const T *src, T *dst1, const T *Ms, const T *Md,
+                                                 const TgtInfo &ti, int nT, uint32_t Vrow, uint32_t A, uint32_t B,
+                                                 uint32_t S, uint32_t rowbase, int h, int sh, int n2, bool needclose,
+                                                 int lane, typename BipArith<T>::Acc &csum) {
 #define COS_BROW(K)                                                                                            \
     case K:                                                                                                    \
-        bip_row<K>(src, dst1, Ms, Md, ti, T, Vrow, A, B, S, rowbase, h, sh, n2, needclose, lane, csum);        \
+        bip_row<T, K>(src, dst1, Ms, Md, ti, nT, Vrow, A, B, S, rowbase, h, sh, n2, needclose, lane, csum);    \
         break;
     switch (nv) {
         COS_BROW(1)
@@ -354,12 +385,13 @@ __device__ __forceinline__ void bip_row_dispatch(int nv, const double *src, doub
 }
 
 // One interaction mask: its rows, the flavor sum of the close, the seed of the next loop or
-// the sink.  seedsh = sgn 2 sigma_{l, s_0} of this lane for vertex 0's shifted start.
+// the sink.  seedsh = sgn 2 sigma_{l, s} of this lane for vertex 0's shifted start on s.
+template <typename T>
 __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
-                                         int n, const double *src, double *dst1, const double *Ms,
-                                         const double *Md, int lane, int ci, int nfl, const double seedsh[2],
-                                         bool shifts, bool active, int lam, int cfg, double *out, int *status,
-                                         int prefetch) {
+                                         int n, const T *src, T *dst1, const T *Ms, const T *Md, int lane, int ci,
+                                         int nfl, const T seedsh[2], bool shifts, bool active, int lam, int cfg,
+                                         double *out, int *status, int prefetch) {
+    using Ar = BipArith<T>;
     const uint32_t full = (1u << n) - 1u;
     const uint4 mk = __ldg(tab.masks + mask_index);
     const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, S = mk.y, code = mk.z, off = mk.w;
@@ -371,12 +403,13 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
     if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
         const uint4 nk = __ldg(tab.masks + next_index);
         const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
-        prefetch_block(src, nk.w, 4u * (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane, prefetch);
+        prefetch_block(reinterpret_cast<const double *>(src), nk.w,
+                       4u * (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane, prefetch);
     }
     const TgtInfo ti = bip_targets(A, B, S, J, code, tab.rank4, lane);
-    const int T = __popc(J) + __popc(J & ~A);
+    const int nT = __popc(J) + __popc(J & ~A);
     const int n2 = 2 * n;
-    double csum = 0.0;
+    typename Ar::Acc csum = Ar::zero();
     for (uint32_t hh = H; hh; hh &= hh - 1u) {
         const int h = __ffs(hh) - 1;
         const int hidx = __popc(H & ((1u << h) - 1u));
@@ -387,11 +420,12 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
         const int sh1 = first_loop ? sh0 : 1;
         for (int sh = sh0; sh <= sh1; ++sh) {
             const uint32_t rowbase = off + (uint32_t)((hidx * 2 + sh) * nA * 2);
-            bip_row_dispatch(nv, src, dst1, Ms, Md, ti, T, Vrow, A, B, S, rowbase, h, sh, n2, needclose, lane, csum);
+            bip_row_dispatch<T>(nv, src, dst1, Ms, Md, ti, nT, Vrow, A, B, S, rowbase, h, sh, n2, needclose, lane,
+                                csum);
         }
     }
     if (!needclose) return;   // no half-visited vertex and not full: disconnected, dropped
-    const double C = flavor_sum(csum, nfl, ci);
+    const T C = Ar::close_sum(csum, nfl, ci);
     if (ones) {
         const int k = __ffs(ones) - 1;
         const uint32_t bk = 1u << k;
@@ -400,37 +434,39 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
         const uint32_t code1 = code + (uint32_t)(2 - sk) * c_p4[k];
         const int hi1 = __popc(head_set(B1, A & ~B1) & (bk - 1u));
         const uint32_t off1 = __ldg(tab.rank4 + code1);
-        double *tp = dst1 + (size_t)(off1 + (uint32_t)(((hi1 * 2 + sk) * nA + __popc(A & (bk - 1u))) * 2 + sk)) *
-                                kLanes + lane;
-        double val = C;
-        if (ell == 1 && shifts) val += seedsh[S & 1u];   // vertex 0 carries a shift point
-        if (k == 0) *tp += val;                           // the extension into 0' wrote it
+        T *tp = dst1 + (size_t)(off1 + (uint32_t)(((hi1 * 2 + sk) * nA + __popc(A & (bk - 1u))) * 2 + sk)) * kLanes +
+                lane;
+        T val = C;
+        if (ell == 1 && shifts) val = Ar::add(val, seedsh[S & 1u]);   // vertex 0 carries a shift point
+        if (k == 0) *tp = Ar::add(*tp, val);                           // the extension into 0' wrote it
         else *tp = val;
     } else if (active && (lam == 0) && out) {
-        const double c = ldexp(C, n - 1);
+        const double c = ldexp(Ar::to_double(C), n - 1);
         out[cfg] = c;
         if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
     }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ BipArgs a) {
-    extern __shared__ __align__(16) double smem_b[];
+    extern __shared__ __align__(16) unsigned char smem_bip[];
     __shared__ int s_batch;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int nsm = 4 * a.smem_n * a.smem_n * kLanes;
-    double *Ms = smem_b;          // extension matrices, shifted diagonal
-    double *Md = smem_b + nsm;    // close matrices times sgn w
-    double *ring = a.scratch + (size_t)blockIdx.x * 2 * a.slot_elems;
+    T *Ms = reinterpret_cast<T *>(smem_bip);   // extension matrices, shifted diagonal
+    T *Md = Ms + nsm;                           // close matrices times sgn w
+    T *ring = reinterpret_cast<T *>(a.scratch) + (size_t)blockIdx.x * 2 * a.slot_elems;
     const int nfl = a.nf_lanes;
     const int lam = lane % nfl;
     const int ci = lane / nfl;
     const double sgn = a.absmode ? 1.0 : -1.0;
-    double sig[2], seedsh[2];
+    double sig[2];
+    T seedsh[2];
     for (int s = 0; s < 2; ++s) {
         sig[s] = a.absmode ? fabs(a.sigma2[lam][s]) : a.sigma2[lam][s];
-        seedsh[s] = sgn * 2.0 * sig[s];
+        to_elem(sgn * 2.0 * sig[s], seedsh[s]);
     }
     const bool shifts = a.shifts != 0;
     const int nbatch = *a.n_batches;
@@ -454,26 +490,26 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
             if (a.absmode) val = fabs(val);
             const int r = e / n2, c = e % n2;
             const bool shifted = (r == c) && (r >= 2) && shifts;   // (j, s) -> (j, s), j >= 1
-            Ms[e * kLanes + lane] = shifted ? val + sgn * sig[r & 1] : val;
-            Md[e * kLanes + lane] = cfac * val;
+            to_elem(shifted ? val + sgn * sig[r & 1] : val, Ms[e * kLanes + lane]);
+            to_elem(cfac * val, Md[e * kLanes + lane]);
         }
         // Start: the loop through the normal point of vertex 0 on sublattice s_0 (layer 1,
         // masks mu_0 = (1, A) and (1, B); row (0, s_0), endpoint (0, s_0)).
         if (warp == 0) {
             for (int s0 = 0; s0 < 2; ++s0) {
                 const uint32_t off = __ldg(tab.rank4 + 1 + s0);
-                ring[(size_t)(1 & 1) * a.slot_elems + (size_t)(off + 3u * (uint32_t)s0) * kLanes + lane] = 1.0;
+                to_elem(1.0, ring[(size_t)(1 & 1) * a.slot_elems + (size_t)(off + 3u * (uint32_t)s0) * kLanes + lane]);
             }
         }
         __syncthreads();
         for (int ell = 1; ell <= 2 * n; ++ell) {
-            const double *src = ring + (size_t)(ell & 1) * a.slot_elems;
-            double *dst1 = ring + (size_t)((ell + 1) & 1) * a.slot_elems;
+            const T *src = ring + (size_t)(ell & 1) * a.slot_elems;
+            T *dst1 = ring + (size_t)((ell + 1) & 1) * a.slot_elems;
             const uint32_t first = tab.layer_first[ell];
             const uint32_t cnt = tab.layer_count[ell];
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
-                bip_mask(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1, Ms,
-                         Md, lane, ci, nfl, seedsh, shifts, active, lam, cfg, a.out, a.status, a.prefetch);
+                bip_mask<T>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1,
+                            Ms, Md, lane, ci, nfl, seedsh, shifts, active, lam, cfg, a.out, a.status, a.prefetch);
             __syncthreads();
         }
     }
@@ -493,6 +529,7 @@ struct BipLaunch {
     bool shifts = false;
     double *out = nullptr;
     bool absmode = false;
+    int precision = COS_FP64;
 };
 
 static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t stream) {
@@ -517,8 +554,9 @@ static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t str
     ws->last_grid = grid;
     cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "bipartite layer scratch");
     if (st != COS_OK) return st;
-    const size_t smem = 2 * (size_t)4 * L.n_max * L.n_max * kLanes * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(dp_bip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = 2 * (size_t)4 * L.n_max * L.n_max * kLanes * sizeof(double);   // 8-byte elements
+    auto kern = L.precision == COS_DF64 ? dp_bip_kernel<df64> : dp_bip_kernel<double>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "bipartite smem attribute");
     BipArgs a;
     memset(&a, 0, sizeof a);
@@ -534,7 +572,7 @@ static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t str
     memcpy(a.sigma2, L.sigma2, sizeof a.sigma2);
     a.shifts = L.shifts ? 1 : 0;
     a.absmode = L.absmode ? 1 : 0;
-    a.scratch = reinterpret_cast<double *>(ws->scratch);
+    a.scratch = ws->scratch;
     a.slot_elems = slot_elems;
     a.smem_n = L.n_max;
     a.prefetch = 1;
@@ -542,7 +580,7 @@ static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t str
     a.status = ws->status;
     e = cudaMemsetAsync(ws->queue, 0, sizeof(int), stream);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
-    dp_bip_kernel<<<grid, 512, smem, stream>>>(a);
+    kern<<<grid, 512, smem, stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "bipartite dp launch");
     return COS_OK;
@@ -569,8 +607,8 @@ static cos_status check_bip(int n_cfg, int n_max, const int32_t *d_order, const 
         set_error(std::string(fn) + ": n_max outside [1, 9]");
         return COS_ERR_ORDER;
     }
-    if (precision != COS_FP64) {
-        set_error(std::string(fn) + ": only COS_FP64 is implemented for bipartite sums");
+    if (precision != COS_FP64 && precision != COS_DF64) {
+        set_error(std::string(fn) + ": bipartite sums run in COS_FP64 or COS_DF64");
         return COS_ERR_UNIMPLEMENTED;
     }
     if (n_cfg > 0 && (!d_order || !d_moff || !d_M4 || !d_out)) {
@@ -581,9 +619,10 @@ static cos_status check_bip(int n_cfg, int n_max, const int32_t *d_order, const 
 }
 
 cos_status bip_matrices_body(Workspace *ws, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
-                             int n_mat, int loop_weight, const double *h_sigma2, const double *d_M4, double *d_out,
-                             double *d_abs_mass, cudaStream_t stream) {
+                             int n_mat, int loop_weight, const double *h_sigma2, const double *d_M4,
+                             cos_precision precision, double *d_out, double *d_abs_mass, cudaStream_t stream) {
     BipLaunch L;
+    L.precision = precision;
     L.n_cfg = n_cfg;
     L.n_max = n_max;
     L.order = d_order;
@@ -618,8 +657,8 @@ extern "C" cos_status cos_connected_sum_bipartite_matrices(int n_cfg, int n_max,
         set_error(err);
         return COS_ERR_CUDA;
     }
-    return bip_matrices_body(ws, n_cfg, n_max, d_order, d_moff, n_mat, loop_weight, h_sigma2, d_M4, d_out,
-                             d_abs_mass, (cudaStream_t)stream);
+    return bip_matrices_body(ws, n_cfg, n_max, d_order, d_moff, n_mat, loop_weight, h_sigma2, d_M4, precision,
+                             d_out, d_abs_mass, (cudaStream_t)stream);
 }
 
 extern "C" cos_status cos_bipartite_structure(int n, cos_structure_info *info) {

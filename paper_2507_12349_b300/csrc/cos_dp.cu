@@ -46,9 +46,6 @@ template <>
 struct CloseOf<df64> {
     using type = df64;
 };
-__device__ __forceinline__ void to_elem(double x, double &r) { r = x; }
-__device__ __forceinline__ void to_elem(double x, float &r) { r = (float)x; }
-__device__ __forceinline__ void to_elem(double x, df64 &r) { r = df64_from(x); }
 
 // Register budgets: MAXT = 256 (two CTAs of up to 8 warps, <= 128 registers), MAXT = 384 (up to
 // 12 warps; FP32 two CTAs, <= 85 registers) and MAXT = 512 (up to 16 warps; <= 128 registers in

@@ -46,6 +46,11 @@ struct Prec<float> {
     static __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
 };
 
+// Conversions of the FP64 inputs to a state or matrix element type (once per batch).
+__device__ __forceinline__ void to_elem(double x, double &r) { r = x; }
+__device__ __forceinline__ void to_elem(double x, float &r) { r = (float)x; }
+__device__ __forceinline__ void to_elem(double x, df64 &r) { r = df64_from(x); }
+
 // Exact FP32 -> FP64 widening by bit manipulation (IEEE-754 binary32 / binary64 layouts: the
 // exponent is rebiased by 1023 - 127 = 896 and the 23-bit fraction moves up by 29 bits).  On
 // B300 the FP64 conversion instruction occupies the FP64 pipe; this keeps the widening on the

@@ -293,8 +293,8 @@ extern "C" cos_status cos_connected_sum_bipartite_batch(const cos_tables *t, int
         set_error(std::string(fn) + ": n_max outside [1, 9]");
         return COS_ERR_ORDER;
     }
-    if (precision != COS_FP64) {
-        set_error(std::string(fn) + ": only COS_FP64 is implemented for bipartite sums");
+    if (precision != COS_FP64 && precision != COS_DF64) {
+        set_error(std::string(fn) + ": bipartite sums run in COS_FP64 or COS_DF64");
         return COS_ERR_UNIMPLEMENTED;
     }
     if (n_cfg == 0) return COS_OK;
@@ -328,6 +328,6 @@ extern "C" cos_status cos_connected_sum_bipartite_batch(const cos_tables *t, int
         sig2[2 * l + 1] = t->sigma2[l][1];
     }
     const int loop_weight = t->symmetric ? t->model.n_flavors : 1;
-    return bip_matrices_body(ws, n_cfg, n_max, d_order, ws->moff, n_mat, loop_weight, sig2, ws->M, d_out, d_abs_mass,
-                             s);
+    return bip_matrices_body(ws, n_cfg, n_max, d_order, ws->moff, n_mat, loop_weight, sig2, ws->M, precision, d_out,
+                             d_abs_mass, s);
 }

@@ -208,8 +208,8 @@ cos_status batch_body(Workspace *ws, const cos_tables *t, int n_cfg, int n_max, 
 int dp_max_active_ctas(int precision, int threads, size_t smem);
 
 cos_status bip_matrices_body(Workspace *ws, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
-                             int n_mat, int loop_weight, const double *h_sigma2, const double *d_M4, double *d_out,
-                             double *d_abs_mass, cudaStream_t stream);
+                             int n_mat, int loop_weight, const double *h_sigma2, const double *d_M4,
+                             cos_precision precision, double *d_out, double *d_abs_mass, cudaStream_t stream);
 
 cos_status launch_gather(const cos_tables *t, int n_cfg, const int32_t *order, const int64_t *offset,
                          const int32_t *site, const double *tau, const int64_t *moff, int64_t mstride,

@@ -30,7 +30,11 @@ def rand_m4(seed, ncfg, nf, n, scale=0.9):
     return [np.ascontiguousarray(m.reshape(nf, n, 2, n, 2)) for m in M]
 
 
-def run(M4s, n_mat, wt, sigma2, abs_mass=False, n_max=None):
+def df64_bound(n, mass):
+    return (16 * n * n + 64 * n) * 2.0 ** -48 * mass
+
+
+def run(M4s, n_mat, wt, sigma2, abs_mass=False, n_max=None, precision="fp64"):
     order = np.array([m.shape[1] for m in M4s], dtype=np.int32)
     moff = B.bipartite_matrix_offsets(order, n_mat)
     flat = np.concatenate([m.ravel() for m in M4s])
@@ -40,7 +44,7 @@ def run(M4s, n_mat, wt, sigma2, abs_mass=False, n_max=None):
     out = torch.full((len(M4s),), float("nan"), dtype=torch.float64, device="cuda")
     mass = torch.full_like(out, float("nan")) if abs_mass else None
     n_max = int(order.max()) if n_max is None else n_max
-    B.cos_connected_sum_bipartite_matrices(n_max, d_order, d_moff, n_mat, wt, sigma2, d_M, "fp64", out, mass)
+    B.cos_connected_sum_bipartite_matrices(n_max, d_order, d_moff, n_mat, wt, sigma2, d_M, precision, out, mass)
     B.cos_sync_status()
     return out.cpu().numpy(), (mass.cpu().numpy() if abs_mass else None)
 
@@ -61,6 +65,18 @@ def test_bipartite_matches_oracle(n, n_mat, wt, shifts, ncfg):
         rmass = O.bip(M4s[c], s2, weight=wt, method="sum_dp", absmode=True)
         assert abs(got[c] - ref) <= bound(n, rmass), (c, got[c], ref, rmass)
         assert mass[c] == pytest.approx(rmass, rel=1e-12)
+
+
+@pytest.mark.parametrize("n,n_mat,wt,shifts,ncfg", CASES[1::2])
+def test_bipartite_df64_matches_oracle(n, n_mat, wt, shifts, ncfg):
+    M4s = rand_m4(800 + 10 * n + n_mat, ncfg, n_mat, n)
+    s2 = np.array([[0.09 - 0.04 * l, -0.06 + 0.05 * l] for l in range(n_mat)]) if shifts else None
+    got, mass = run(M4s, n_mat, wt, None if s2 is None else s2.tolist(), abs_mass=True, precision="df64")
+    for c in sorted({0, ncfg // 2, ncfg - 1}):
+        ref = O.bip(M4s[c], s2, weight=wt, method="sum_dp", prec="ld")
+        rmass = O.bip(M4s[c], s2, weight=wt, method="sum_dp", absmode=True)
+        assert abs(got[c] - ref) <= df64_bound(n, rmass), (c, got[c], ref, rmass)
+        assert abs(mass[c] - rmass) <= df64_bound(n, rmass)
 
 
 def test_bipartite_uneven_orders_and_order9():
