@@ -203,7 +203,7 @@ cos_status check_common(int n_cfg, int n_max, cos_precision prec, const char *fn
 }
 
 cos_status run_dp(Workspace *ws, DpLaunch L, double *d_abs_mass, cudaStream_t stream) {
-    const int cpb = kLanes / L.n_mat;
+    const int cpb = dp_configs_per_batch(L);
     cos_status st = launch_plan_batches(ws, L.n_cfg, L.n_max, L.order, cpb, stream, L.allow_empty);
     if (st != COS_OK) return st;
     st = launch_dp(ws, L, stream);

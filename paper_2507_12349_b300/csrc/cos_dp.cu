@@ -359,9 +359,7 @@ int dp_max_active_ctas(int precision, int threads, size_t smem) {
     int nb = 0;
     cudaError_t e;
     if (precision == COS_MIXED) {
-        auto k = forward_kernel_for<float, false>(threads);
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem);
+        return pair_max_active_ctas(threads, smem);   // the launches of this precision use the pair kernel
     } else if (precision == COS_DF64) {
         auto k = forward_kernel_for<df64, false>(threads);
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -374,7 +372,20 @@ int dp_max_active_ctas(int precision, int threads, size_t smem) {
     return e == cudaSuccess ? nb : 0;
 }
 
+bool dp_uses_pair(const DpLaunch &L) { return L.precision == COS_MIXED && L.csub == nullptr; }
+
+int dp_configs_per_batch(const DpLaunch &L) {
+    return dp_uses_pair(L) ? 2 * (kLanes / L.n_mat) : kLanes / L.n_mat;
+}
+
+size_t dp_smem_bytes(int precision, int n_max) {
+    const size_t msm = (size_t)n_max * n_max * kLanes;
+    if (precision == COS_MIXED) return pair_smem_bytes(n_max);
+    return msm * 8 + msm * 8;   // double or df64 extension and close matrices
+}
+
 cos_status launch_dp(Workspace *ws, const DpLaunch &L, cudaStream_t stream) {
+    if (dp_uses_pair(L)) return launch_dp_pair(ws, L, stream);
     if (L.precision == COS_MIXED) return launch_dp_t<float>(ws, L, stream);
     if (L.precision == COS_DF64) return launch_dp_t<df64>(ws, L, stream);
     return launch_dp_t<double>(ws, L, stream);

@@ -1,0 +1,337 @@
+// Mixed-precision DP with two configurations per lane.
+//
+// In the mixed mode (FP32 extension, FP64 close) the FP32 multiply-adds are cheap and the
+// warp-uniform index work of a mask -- target offsets, endpoint slots, shuffles, stores --
+// dominates the issue slots.  Here every lane carries the same flavor of two configurations
+// (the .x and .y components of a float2 state), so each index computation, shared-memory
+// address and branch serves two configurations: a batch holds 2 x floor(32 / n_flavors)
+// configurations.  The arithmetic per configuration is that of dp_forward_kernel<float>:
+// FP32 extension states and accumulation, the FP64 close on exactly widened states, seeds
+// rounded to FP32, flavor sums in FP64 (one butterfly per component, identical bits in every
+// lane of a configuration), and the sink in FP64.  Layout: states [slot][lane] as float2 (8
+// bytes, as FP64), extension matrices [v][j][lane] as float2, close matrices (times sgn w)
+// as double2.
+#include <algorithm>
+#include <cstring>
+
+#include "cos_dp_device.cuh"
+
+namespace cosdp {
+
+namespace {
+
+__device__ __forceinline__ void push_target_pair(float2 *__restrict__ dst1, const TgtInfo &ti, int q, float2 d,
+                                                 uint32_t hlow, int lane) {
+    const uint32_t off1 = __shfl_sync(0xFFFFFFFFu, ti.off1, q);
+    const uint32_t meta = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
+    const uint32_t ai1 = meta & 15u, nA1 = (meta >> 4) & 15u;
+    const uint32_t hi1 = (uint32_t)__popc((meta >> 16) & hlow);
+    dst1[(size_t)(off1 + hi1 * nA1 + ai1) * kLanes + lane] = d;
+}
+
+template <int NV>
+__device__ __forceinline__ void do_row_pair(const float2 *__restrict__ src, float2 *__restrict__ dst1,
+                                            const float2 *__restrict__ Ms, const double2 *__restrict__ Md,
+                                            const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow, uint32_t A,
+                                            uint32_t off, int h, int hidx, int nA, int n, bool needclose, int lane,
+                                            double2 &csum) {
+    float2 o[NV];
+    int vs[NV];
+    const float2 *row = src + (size_t)(off + (uint32_t)(hidx * nA)) * kLanes + lane;
+    uint32_t vv = Vrow;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+        const int v = __ffs(vv) - 1;
+        vv &= vv - 1u;
+        o[t] = row[__popc(A & ((1u << v) - 1u)) * kLanes];
+        vs[t] = v * n * kLanes + lane;
+    }
+    if (needclose) {
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            const double2 m = Md[vs[t] + h * kLanes];
+            csum.x = fma(widen(o[t].x), m.x, csum.x);
+            csum.y = fma(widen(o[t].y), m.y, csum.y);
+        }
+    }
+    const uint32_t hlow = (1u << h) - 1u;
+    uint32_t jj = J;
+    int q = 0;
+    for (; q + 1 < nJ; q += 2) {
+        const int ja = __ffs(jj) - 1;
+        jj &= jj - 1u;
+        const int jb = __ffs(jj) - 1;
+        jj &= jj - 1u;
+        float2 da = make_float2(0.0f, 0.0f), db = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            const float2 ma = Ms[vs[t] + ja * kLanes];
+            const float2 mb = Ms[vs[t] + jb * kLanes];
+            da.x = fmaf(o[t].x, ma.x, da.x);
+            da.y = fmaf(o[t].y, ma.y, da.y);
+            db.x = fmaf(o[t].x, mb.x, db.x);
+            db.y = fmaf(o[t].y, mb.y, db.y);
+        }
+        push_target_pair(dst1, ti, q, da, hlow, lane);
+        push_target_pair(dst1, ti, q + 1, db, hlow, lane);
+    }
+    if (q < nJ) {
+        const int j = __ffs(jj) - 1;
+        float2 d = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            const float2 m = Ms[vs[t] + j * kLanes];
+            d.x = fmaf(o[t].x, m.x, d.x);
+            d.y = fmaf(o[t].y, m.y, d.y);
+        }
+        push_target_pair(dst1, ti, q, d, hlow, lane);
+    }
+}
+
+__device__ __forceinline__ void row_dispatch_pair(int nv, const float2 *src, float2 *dst1, const float2 *Ms,
+                                                  const double2 *Md, const TgtInfo &ti, int nJ, uint32_t J,
+                                                  uint32_t Vrow, uint32_t A, uint32_t off, int h, int hidx, int nA,
+                                                  int n, bool needclose, int lane, double2 &csum) {
+#define COS_ROW_P(K)                                                                                           \
+    case K:                                                                                                    \
+        do_row_pair<K>(src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, csum);     \
+        break;
+    switch (nv) {
+        COS_ROW_P(1)
+        COS_ROW_P(2)
+        COS_ROW_P(3)
+        COS_ROW_P(4)
+        COS_ROW_P(5)
+        COS_ROW_P(6)
+        COS_ROW_P(7)
+        COS_ROW_P(8)
+        COS_ROW_P(9)
+        COS_ROW_P(10)
+        COS_ROW_P(11)
+        COS_ROW_P(12)
+        default:
+            break;
+    }
+#undef COS_ROW_P
+}
+
+// One interaction mask for both configurations of every lane (twin of fwd_mask<float>).
+__device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
+                                              int n, const float2 *src, float2 *dst1, const float2 *Ms,
+                                              const double2 *Md, int lane, int ci, int nfl, double sgn, double sig,
+                                              bool shifts, bool act_x, bool act_y, int lam, int cfg_x, int cfg_y,
+                                              double *out, int *status, int prefetch) {
+    const uint32_t full = (1u << n) - 1u;
+    const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + mask_index));
+    const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, code = mk.y, off = mk.z;
+    const uint32_t ones = A & ~B;
+    const uint32_t H = head_set(B, ones);
+    const uint32_t J = full & ~B;
+    const int nA = __popc(A);
+    const bool needclose = (ones != 0u) || (B == full);
+    if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
+        const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + next_index));
+        const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
+        prefetch_block(reinterpret_cast<const double *>(src), nk.z,
+                       (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane, prefetch);
+    }
+    double2 csum = make_double2(0.0, 0.0);
+    const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, lane);
+    const int nJ = __popc(J);
+    for (uint32_t hh = H; hh; hh &= hh - 1u) {
+        const int h = __ffs(hh) - 1;
+        const int hidx = __popc(H & ((1u << h) - 1u));
+        const uint32_t Vrow = row_vmask(A, ones, h);
+        row_dispatch_pair(__popc(Vrow), src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane,
+                          csum);
+    }
+    if (!needclose) return;   // no half-visited vertex and not full: disconnected, dropped
+    const double Cx = flavor_sum(csum.x, nfl, ci);
+    const double Cy = flavor_sum(csum.y, nfl, ci);
+    if (ones) {
+        const int k = __ffs(ones) - 1;
+        const uint32_t bk = 1u << k;
+        const uint32_t B1 = B | bk;
+        const int hi1 = __popc(head_set(B1, A & ~B1) & (bk - 1u));
+        const int ai1 = __popc(A & (bk - 1u));
+        const uint32_t off1 = __ldg(tab.rank3 + code + c_p3[k]);
+        float2 *tp = dst1 + (size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane;
+        double vx = Cx, vy = Cy;
+        if (ell == 1 && shifts) {   // vertex 0 carries a shift point
+            vx += sgn * 2.0 * sig;
+            vy += sgn * 2.0 * sig;
+        }
+        const float2 tv = make_float2(narrow_to(0.0f, vx), narrow_to(0.0f, vy));
+        if (k == 0) {               // the extension into 0' wrote it
+            float2 cur = *tp;
+            cur.x += tv.x;
+            cur.y += tv.y;
+            *tp = cur;
+        } else {
+            *tp = tv;
+        }
+    } else if (lam == 0 && out) {
+        if (act_x) {
+            const double c = ldexp(Cx, n - 1);
+            out[cfg_x] = c;
+            if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
+        }
+        if (act_y) {
+            const double c = ldexp(Cy, n - 1);
+            out[cfg_y] = c;
+            if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
+        }
+    }
+}
+
+}  // namespace
+
+// MAXT = 256 (two CTAs of up to 8 warps, <= 128 registers), 384 (two CTAs of up to 12 warps,
+// <= 85) or 512 (one CTA of up to 16 warps, <= 128).
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_kernel(const __grid_constant__ DpArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_p[];
+    __shared__ int s_batch;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int nsm = a.smem_n * a.smem_n * kLanes;
+    float2 *Ms = reinterpret_cast<float2 *>(smem_p);
+    double2 *Md = reinterpret_cast<double2 *>(smem_p + (size_t)nsm * sizeof(float2));
+    float2 *ring = reinterpret_cast<float2 *>(a.scratch) + (size_t)blockIdx.x * a.nslots * a.slot_elems;
+    const int nfl = a.nf_lanes;
+    const int lam = lane % nfl;
+    const int ci = lane / nfl;
+    const int cpl = kLanes / nfl;   // configurations per component
+    const double sgn = a.absmode ? 1.0 : -1.0;
+    const double sig = a.absmode ? fabs(a.sigma[lam]) : a.sigma[lam];
+    const bool shifts = a.shifts != 0;
+    const int nbatch = *a.n_batches;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_batch = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int b = s_batch;
+        if (b >= nbatch) break;
+        const int4 bd = a.batches[b];
+        const int n = bd.x;
+        const OrderTab &tab = a.tabs[n];
+        const bool lane_ok = ci * nfl + nfl <= kLanes;
+        const bool act_x = lane_ok && (ci < bd.z);
+        const bool act_y = lane_ok && (ci + cpl < bd.z);
+        const int cfg_x = act_x ? a.batch_list[bd.y + ci] : -1;
+        const int cfg_y = act_y ? a.batch_list[bd.y + cpl + ci] : -1;
+        const double *Mx = act_x ? a.M + (a.moff ? a.moff[cfg_x] : (int64_t)cfg_x * a.mstride) + (size_t)lam * n * n
+                                 : nullptr;
+        const double *My = act_y ? a.M + (a.moff ? a.moff[cfg_y] : (int64_t)cfg_y * a.mstride) + (size_t)lam * n * n
+                                 : nullptr;
+        const double cfac = sgn * a.loop_weight;
+        const double dshift = sgn * sig;
+        for (int e = warp; e < n * n; e += nwarps) {
+            double vx = act_x ? Mx[e] : 0.0, vy = act_y ? My[e] : 0.0;
+            if (a.absmode) {
+                vx = fabs(vx);
+                vy = fabs(vy);
+            }
+            const int v = e / n, j = e % n;
+            const bool sh = v == j && j != 0 && shifts;
+            Ms[e * kLanes + lane] = make_float2((float)(sh ? vx + dshift : vx), (float)(sh ? vy + dshift : vy));
+            Md[e * kLanes + lane] = make_double2(cfac * vx, cfac * vy);
+        }
+        if (warp == 0) ring[(1 % a.nslots) * a.slot_elems + lane] = make_float2(1.0f, 1.0f);
+        __syncthreads();
+        for (int ell = 1; ell <= 2 * n; ++ell) {
+            const float2 *src = ring + (size_t)(ell % a.nslots) * a.slot_elems;
+            float2 *dst1 = ring + (size_t)((ell + 1) % a.nslots) * a.slot_elems;
+            const uint32_t first = tab.layer_first[ell];
+            const uint32_t cnt = tab.layer_count[ell];
+            for (uint32_t mi = warp; mi < cnt; mi += nwarps)
+                fwd_mask_pair(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src,
+                              dst1, Ms, Md, lane, ci, nfl, sgn, sig, shifts, act_x, act_y, lam, cfg_x, cfg_y, a.out,
+                              a.status, a.prefetch);
+            __syncthreads();
+        }
+    }
+}
+
+static auto pair_kernel_for(int threads) {
+    return threads <= 256 ? dp_pair_kernel<256> : (threads <= 384 ? dp_pair_kernel<384> : dp_pair_kernel<512>);
+}
+
+size_t pair_smem_bytes(int n_max) {
+    const size_t msm = (size_t)n_max * n_max * kLanes;
+    return msm * sizeof(float2) + msm * sizeof(double2);
+}
+
+int pair_max_active_ctas(int threads, size_t smem) {
+    int nb = 0;
+    auto k = pair_kernel_for(threads);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem) == cudaSuccess ? nb : 0;
+}
+
+cos_status launch_dp_pair(Workspace *ws, const DpLaunch &L, cudaStream_t stream) {
+    std::string err;
+    const OrderTab *tabs = device_orders(ws->device, &err);
+    if (!tabs) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    const int nfl = L.n_mat;
+    const Tuning tu = get_tuning(L.n_max, L.precision, nfl);
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
+    const int nslots = 2;
+    const size_t slot_elems = (size_t)host_order(L.n_max).max_slots * kLanes;
+    const size_t per_cta = (size_t)nslots * slot_elems * sizeof(float2);
+    const int cpb = 2 * (kLanes / nfl);
+    const int max_batches = (L.n_cfg + cpb - 1) / cpb + COS_NMAX;
+    int grid = std::max(1, std::min(nsm * tu.ctas_per_sm, max_batches));
+    if (ws->fixed_grid > 0) {
+        grid = ws->fixed_grid;
+    } else {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            const size_t avail = ws->scratch_bytes + (size_t)(0.85 * (double)free_b);
+            while (grid > 1 && (size_t)grid * per_cta > avail) grid = std::max(1, grid / 2);
+        }
+    }
+    ws->last_grid = grid;
+    cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "layer scratch");
+    if (st != COS_OK) return st;
+    const int threads = tu.warps * 32;
+    const size_t smem = pair_smem_bytes(L.n_max);
+    auto kern = pair_kernel_for(threads);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "dp smem attribute");
+    DpArgs a;
+    memset(&a, 0, sizeof a);
+    a.tabs = tabs;
+    a.batches = ws->batches;
+    a.n_batches = ws->plan_counts + 64;
+    a.batch_list = ws->batch_list;
+    a.queue = ws->queue;
+    a.M = L.M;
+    a.moff = L.moff;
+    a.mstride = L.mstride;
+    a.nf_lanes = nfl;
+    a.loop_weight = (double)L.loop_weight;
+    for (int l = 0; l < COS_MAX_FLAVORS; ++l) a.sigma[l] = L.sigma[l];
+    a.shifts = L.shifts ? 1 : 0;
+    a.absmode = L.absmode ? 1 : 0;
+    a.scratch = ws->scratch;
+    a.slot_elems = slot_elems;
+    a.nslots = nslots;
+    a.smem_n = L.n_max;
+    a.prefetch = tu.prefetch;
+    a.out = L.out;
+    a.status = ws->status;
+    e = cudaMemsetAsync(ws->queue, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+    kern<<<grid, threads, smem, stream>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "dp launch");
+    return COS_OK;
+}
+
+}  // namespace cosdp

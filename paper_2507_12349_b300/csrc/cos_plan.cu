@@ -281,9 +281,7 @@ extern "C" cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts
     if (st == COS_OK) {
         fill_matrices_kernel<<<256, 256, 0, s>>>(M, (size_t)stride * n_cfg, 12345u + n);
         fill_layout_kernel<<<64, 256, 0, s>>>(order, moff, n_cfg, n, stride);
-        const size_t msm = (size_t)n * n * kLanes;
-        const size_t smem = (precision == COS_MIXED ? ((msm * sizeof(float) + 15) & ~size_t(15))
-                                                    : msm * sizeof(double)) + msm * sizeof(double);
+        const size_t smem = dp_smem_bytes(precision, n);
         // candidates: every (warps, ctas) the occupancy calculator admits, with prefetch into L2;
         // then the best shape again with prefetch off and with prefetch into L1
         std::vector<Tuning> cands;
