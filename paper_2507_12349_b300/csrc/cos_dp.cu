@@ -358,12 +358,8 @@ cos_status launch_dp_raw(const RawBuffers &rb, const DpLaunch &L, cudaStream_t s
 int dp_max_active_ctas(int precision, int threads, size_t smem) {
     int nb = 0;
     cudaError_t e;
-    if (precision == COS_MIXED) {
-        return pair_max_active_ctas(threads, smem);   // the launches of this precision use the pair kernel
-    } else if (precision == COS_DF64) {
-        auto k = forward_kernel_for<df64, false>(threads);
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem);
+    if (precision == COS_MIXED || precision == COS_DF64) {
+        return pair_max_active_ctas(precision, threads, smem);   // these precisions launch the pair kernels
     } else {
         auto k = forward_kernel_for<double, false>(threads);
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -372,7 +368,9 @@ int dp_max_active_ctas(int precision, int threads, size_t smem) {
     return e == cudaSuccess ? nb : 0;
 }
 
-bool dp_uses_pair(const DpLaunch &L) { return L.precision == COS_MIXED && L.csub == nullptr; }
+bool dp_uses_pair(const DpLaunch &L) {
+    return (L.precision == COS_MIXED || L.precision == COS_DF64) && L.csub == nullptr;
+}
 
 int dp_configs_per_batch(const DpLaunch &L) {
     return dp_uses_pair(L) ? 2 * (kLanes / L.n_mat) : kLanes / L.n_mat;
@@ -380,7 +378,7 @@ int dp_configs_per_batch(const DpLaunch &L) {
 
 size_t dp_smem_bytes(int precision, int n_max) {
     const size_t msm = (size_t)n_max * n_max * kLanes;
-    if (precision == COS_MIXED) return pair_smem_bytes(n_max);
+    if (precision == COS_MIXED || precision == COS_DF64) return pair_smem_bytes(precision, n_max);
     return msm * 8 + msm * 8;   // double or df64 extension and close matrices
 }
 

@@ -11,6 +11,10 @@
 // lane of a configuration), and the sink in FP64.  Layout: states [slot][lane] as float2 (8
 // bytes, as FP64), extension matrices [v][j][lane] as float2, close matrices (times sgn w)
 // as double2.
+//
+// The double-float mode (FP32 pairs) is issue-bound for the same reason and gets the same
+// treatment: df64x2 states (two df64 values, 16 bytes per lane), compensated accumulation
+// per component, df64 flavor sums and seeds, the sink in FP64.
 #include <algorithm>
 #include <cstring>
 
@@ -184,10 +188,188 @@ __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask
     }
 }
 
+// ---------------------------------------------------------------- double-float, two per lane
+
+struct __align__(16) df64x2 {
+    df64 x, y;
+};
+
+__device__ __forceinline__ void push_target_dfp(df64x2 *__restrict__ dst1, uint32_t tslot, int q, const DotAcc &dx,
+                                                const DotAcc &dy, int lane) {
+    const uint32_t slot = __shfl_sync(0xFFFFFFFFu, tslot, q);
+    df64x2 v;
+    v.x = df64{dx.s, dx.c};
+    v.y = df64{dy.s, dy.c};
+    dst1[(size_t)slot * kLanes + lane] = v;
+}
+
+template <int NV>
+__device__ __forceinline__ void do_row_dfp(const df64x2 *__restrict__ src, df64x2 *__restrict__ dst1,
+                                           const df64x2 *__restrict__ Ms, const df64x2 *__restrict__ Md,
+                                           const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow, uint32_t A,
+                                           uint32_t off, int h, int hidx, int nA, int n, bool needclose, int lane,
+                                           DotAcc &cx, DotAcc &cy) {
+    df64x2 o[NV];
+    int vs[NV];
+    const df64x2 *row = src + (size_t)(off + (uint32_t)(hidx * nA)) * kLanes + lane;
+    uint32_t vv = Vrow;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+        const int v = __ffs(vv) - 1;
+        vv &= vv - 1u;
+        o[t] = row[__popc(A & ((1u << v) - 1u)) * kLanes];
+        vs[t] = v * n * kLanes + lane;
+    }
+    if (needclose) {
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            const df64x2 m = Md[vs[t] + h * kLanes];
+            dot_add(cx, o[t].x, m.x);
+            dot_add(cy, o[t].y, m.y);
+        }
+    }
+    const uint32_t tslot = row_target_slot(ti, (1u << h) - 1u);
+    uint32_t jj = J;
+    int q = 0;
+    for (; q + 1 < nJ; q += 2) {
+        const int ja = __ffs(jj) - 1;
+        jj &= jj - 1u;
+        const int jb = __ffs(jj) - 1;
+        jj &= jj - 1u;
+        const df64x2 ma0 = Ms[vs[0] + ja * kLanes];
+        const df64x2 mb0 = Ms[vs[0] + jb * kLanes];
+        DotAcc ax = dot_first(o[0].x, ma0.x), ay = dot_first(o[0].y, ma0.y);
+        DotAcc bx = dot_first(o[0].x, mb0.x), by = dot_first(o[0].y, mb0.y);
+#pragma unroll
+        for (int t = 1; t < NV; ++t) {
+            const df64x2 ma = Ms[vs[t] + ja * kLanes];
+            const df64x2 mb = Ms[vs[t] + jb * kLanes];
+            dot_add(ax, o[t].x, ma.x);
+            dot_add(ay, o[t].y, ma.y);
+            dot_add(bx, o[t].x, mb.x);
+            dot_add(by, o[t].y, mb.y);
+        }
+        push_target_dfp(dst1, tslot, q, ax, ay, lane);
+        push_target_dfp(dst1, tslot, q + 1, bx, by, lane);
+    }
+    if (q < nJ) {
+        const int j = __ffs(jj) - 1;
+        const df64x2 m0 = Ms[vs[0] + j * kLanes];
+        DotAcc ax = dot_first(o[0].x, m0.x), ay = dot_first(o[0].y, m0.y);
+#pragma unroll
+        for (int t = 1; t < NV; ++t) {
+            const df64x2 m = Ms[vs[t] + j * kLanes];
+            dot_add(ax, o[t].x, m.x);
+            dot_add(ay, o[t].y, m.y);
+        }
+        push_target_dfp(dst1, tslot, q, ax, ay, lane);
+    }
+}
+
+__device__ __forceinline__ void row_dispatch_dfp(int nv, const df64x2 *src, df64x2 *dst1, const df64x2 *Ms,
+                                                 const df64x2 *Md, const TgtInfo &ti, int nJ, uint32_t J,
+                                                 uint32_t Vrow, uint32_t A, uint32_t off, int h, int hidx, int nA,
+                                                 int n, bool needclose, int lane, DotAcc &cx, DotAcc &cy) {
+#define COS_ROW_DP(K)                                                                                          \
+    case K:                                                                                                    \
+        do_row_dfp<K>(src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, cx, cy);    \
+        break;
+    switch (nv) {
+        COS_ROW_DP(1)
+        COS_ROW_DP(2)
+        COS_ROW_DP(3)
+        COS_ROW_DP(4)
+        COS_ROW_DP(5)
+        COS_ROW_DP(6)
+        COS_ROW_DP(7)
+        COS_ROW_DP(8)
+        COS_ROW_DP(9)
+        COS_ROW_DP(10)
+        COS_ROW_DP(11)
+        COS_ROW_DP(12)
+        default:
+            break;
+    }
+#undef COS_ROW_DP
+}
+
+__device__ __forceinline__ void fwd_mask_dfp(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
+                                             int n, const df64x2 *src, df64x2 *dst1, const df64x2 *Ms,
+                                             const df64x2 *Md, int lane, int ci, int nfl, df64 seed0, bool shifts,
+                                             bool act_x, bool act_y, int lam, int cfg_x, int cfg_y, double *out,
+                                             int *status, int prefetch) {
+    const uint32_t full = (1u << n) - 1u;
+    const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + mask_index));
+    const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, code = mk.y, off = mk.z;
+    const uint32_t ones = A & ~B;
+    const uint32_t H = head_set(B, ones);
+    const uint32_t J = full & ~B;
+    const int nA = __popc(A);
+    const bool needclose = (ones != 0u) || (B == full);
+    if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
+        // 16-byte states: two 256-byte lines per warp row, fetched as two double-sized rows
+        const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + next_index));
+        const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
+        const uint32_t ns = (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_));
+        prefetch_block(reinterpret_cast<const double *>(src), 2 * nk.z, 2 * ns, lane, prefetch);
+    }
+    DotAcc cx = {0.0f, 0.0f}, cy = {0.0f, 0.0f};
+    const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, lane);
+    const int nJ = __popc(J);
+    for (uint32_t hh = H; hh; hh &= hh - 1u) {
+        const int h = __ffs(hh) - 1;
+        const int hidx = __popc(H & ((1u << h) - 1u));
+        const uint32_t Vrow = row_vmask(A, ones, h);
+        row_dispatch_dfp(__popc(Vrow), src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, cx,
+                         cy);
+    }
+    if (!needclose) return;
+    const df64 Cx = df64_flavor_sum(dot_value(cx), nfl, ci);
+    const df64 Cy = df64_flavor_sum(dot_value(cy), nfl, ci);
+    if (ones) {
+        const int k = __ffs(ones) - 1;
+        const uint32_t bk = 1u << k;
+        const uint32_t B1 = B | bk;
+        const int hi1 = __popc(head_set(B1, A & ~B1) & (bk - 1u));
+        const int ai1 = __popc(A & (bk - 1u));
+        const uint32_t off1 = __ldg(tab.rank3 + code + c_p3[k]);
+        df64x2 *tp = dst1 + (size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane;
+        df64x2 val;
+        val.x = Cx;
+        val.y = Cy;
+        if (ell == 1 && shifts) {   // vertex 0 carries a shift point
+            val.x = df64_add(val.x, seed0);
+            val.y = df64_add(val.y, seed0);
+        }
+        if (k == 0) {               // the extension into 0' wrote it
+            df64x2 cur = *tp;
+            cur.x = df64_add(cur.x, val.x);
+            cur.y = df64_add(cur.y, val.y);
+            *tp = cur;
+        } else {
+            *tp = val;
+        }
+    } else if (lam == 0 && out) {
+        if (act_x) {
+            const double c = ldexp(df64_to_double(Cx), n - 1);
+            out[cfg_x] = c;
+            if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
+        }
+        if (act_y) {
+            const double c = ldexp(df64_to_double(Cy), n - 1);
+            out[cfg_y] = c;
+            if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
+        }
+    }
+}
+
 }  // namespace
 
 // MAXT = 256 (two CTAs of up to 8 warps, <= 128 registers), 384 (two CTAs of up to 12 warps,
 // <= 85) or 512 (one CTA of up to 16 warps, <= 128).
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_dfp_kernel(const __grid_constant__ DpArgs a);
+
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_kernel(const __grid_constant__ DpArgs a) {
     extern __shared__ __align__(16) unsigned char smem_p[];
@@ -254,18 +436,101 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_kernel(cons
     }
 }
 
-static auto pair_kernel_for(int threads) {
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_dfp_kernel(const __grid_constant__ DpArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_q[];
+    __shared__ int s_batch;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int nsm = a.smem_n * a.smem_n * kLanes;
+    df64x2 *Ms = reinterpret_cast<df64x2 *>(smem_q);
+    df64x2 *Md = Ms + nsm;
+    df64x2 *ring = reinterpret_cast<df64x2 *>(a.scratch) + (size_t)blockIdx.x * a.nslots * a.slot_elems;
+    const int nfl = a.nf_lanes;
+    const int lam = lane % nfl;
+    const int ci = lane / nfl;
+    const int cpl = kLanes / nfl;
+    const double sgn = a.absmode ? 1.0 : -1.0;
+    const double sig = a.absmode ? fabs(a.sigma[lam]) : a.sigma[lam];
+    const bool shifts = a.shifts != 0;
+    const df64 seed0 = df64_from(sgn * 2.0 * sig);
+    const int nbatch = *a.n_batches;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_batch = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int b = s_batch;
+        if (b >= nbatch) break;
+        const int4 bd = a.batches[b];
+        const int n = bd.x;
+        const OrderTab &tab = a.tabs[n];
+        const bool lane_ok = ci * nfl + nfl <= kLanes;
+        const bool act_x = lane_ok && (ci < bd.z);
+        const bool act_y = lane_ok && (ci + cpl < bd.z);
+        const int cfg_x = act_x ? a.batch_list[bd.y + ci] : -1;
+        const int cfg_y = act_y ? a.batch_list[bd.y + cpl + ci] : -1;
+        const double *Mx = act_x ? a.M + (a.moff ? a.moff[cfg_x] : (int64_t)cfg_x * a.mstride) + (size_t)lam * n * n
+                                 : nullptr;
+        const double *My = act_y ? a.M + (a.moff ? a.moff[cfg_y] : (int64_t)cfg_y * a.mstride) + (size_t)lam * n * n
+                                 : nullptr;
+        const double cfac = sgn * a.loop_weight;
+        const double dshift = sgn * sig;
+        for (int e = warp; e < n * n; e += nwarps) {
+            double vx = act_x ? Mx[e] : 0.0, vy = act_y ? My[e] : 0.0;
+            if (a.absmode) {
+                vx = fabs(vx);
+                vy = fabs(vy);
+            }
+            const int v = e / n, j = e % n;
+            const bool sh = v == j && j != 0 && shifts;
+            df64x2 m, c;
+            m.x = df64_from(sh ? vx + dshift : vx);
+            m.y = df64_from(sh ? vy + dshift : vy);
+            c.x = df64_from(cfac * vx);
+            c.y = df64_from(cfac * vy);
+            Ms[e * kLanes + lane] = m;
+            Md[e * kLanes + lane] = c;
+        }
+        if (warp == 0) {
+            df64x2 one;
+            one.x = df64{1.0f, 0.0f};
+            one.y = df64{1.0f, 0.0f};
+            ring[(1 % a.nslots) * a.slot_elems + lane] = one;
+        }
+        __syncthreads();
+        for (int ell = 1; ell <= 2 * n; ++ell) {
+            const df64x2 *src = ring + (size_t)(ell % a.nslots) * a.slot_elems;
+            df64x2 *dst1 = ring + (size_t)((ell + 1) % a.nslots) * a.slot_elems;
+            const uint32_t first = tab.layer_first[ell];
+            const uint32_t cnt = tab.layer_count[ell];
+            for (uint32_t mi = warp; mi < cnt; mi += nwarps)
+                fwd_mask_dfp(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1,
+                             Ms, Md, lane, ci, nfl, seed0, shifts, act_x, act_y, lam, cfg_x, cfg_y, a.out, a.status,
+                             a.prefetch);
+            __syncthreads();
+        }
+    }
+}
+
+static auto pair_kernel_for(int precision, int threads) {
+    if (precision == COS_DF64)
+        return threads <= 256 ? dp_pair_dfp_kernel<256>
+                              : (threads <= 384 ? dp_pair_dfp_kernel<384> : dp_pair_dfp_kernel<512>);
     return threads <= 256 ? dp_pair_kernel<256> : (threads <= 384 ? dp_pair_kernel<384> : dp_pair_kernel<512>);
 }
 
-size_t pair_smem_bytes(int n_max) {
+size_t pair_smem_bytes(int precision, int n_max) {
     const size_t msm = (size_t)n_max * n_max * kLanes;
+    if (precision == COS_DF64) return 2 * msm * sizeof(df64x2);
     return msm * sizeof(float2) + msm * sizeof(double2);
 }
 
-int pair_max_active_ctas(int threads, size_t smem) {
+size_t pair_state_bytes(int precision) { return precision == COS_DF64 ? sizeof(df64x2) : sizeof(float2); }
+
+int pair_max_active_ctas(int precision, int threads, size_t smem) {
     int nb = 0;
-    auto k = pair_kernel_for(threads);
+    auto k = pair_kernel_for(precision, threads);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem) == cudaSuccess ? nb : 0;
 }
@@ -283,7 +548,7 @@ cos_status launch_dp_pair(Workspace *ws, const DpLaunch &L, cudaStream_t stream)
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
     const int nslots = 2;
     const size_t slot_elems = (size_t)host_order(L.n_max).max_slots * kLanes;
-    const size_t per_cta = (size_t)nslots * slot_elems * sizeof(float2);
+    const size_t per_cta = (size_t)nslots * slot_elems * pair_state_bytes(L.precision);
     const int cpb = 2 * (kLanes / nfl);
     const int max_batches = (L.n_cfg + cpb - 1) / cpb + COS_NMAX;
     int grid = std::max(1, std::min(nsm * tu.ctas_per_sm, max_batches));
@@ -300,8 +565,8 @@ cos_status launch_dp_pair(Workspace *ws, const DpLaunch &L, cudaStream_t stream)
     cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "layer scratch");
     if (st != COS_OK) return st;
     const int threads = tu.warps * 32;
-    const size_t smem = pair_smem_bytes(L.n_max);
-    auto kern = pair_kernel_for(threads);
+    const size_t smem = pair_smem_bytes(L.precision, L.n_max);
+    auto kern = pair_kernel_for(L.precision, threads);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "dp smem attribute");
     DpArgs a;

@@ -182,13 +182,13 @@ cos_status launch_plan_raw(const RawBuffers &rb, int n_cfg, int n_max, const int
                            cudaStream_t stream);
 cos_status launch_dp_raw(const RawBuffers &rb, const DpLaunch &a, cudaStream_t stream);
 int dp_slots(const DpLaunch &a);            // layer slots of the ring (2, or 3 with shifts)
-// Mixed precision runs two configurations per lane (cos_dp_pair.cu) except in the all-subsets
-// mode; configurations per batch follow the kernel the launch selects.
+// Mixed and double-float precision run two configurations per lane (cos_dp_pair.cu) except
+// in the all-subsets mode; configurations per batch follow the kernel the launch selects.
 bool dp_uses_pair(const DpLaunch &a);
 int dp_configs_per_batch(const DpLaunch &a);
 cos_status launch_dp_pair(Workspace *ws, const DpLaunch &a, cudaStream_t stream);
-size_t pair_smem_bytes(int n_max);
-int pair_max_active_ctas(int threads, size_t smem);
+size_t pair_smem_bytes(int precision, int n_max);
+int pair_max_active_ctas(int precision, int threads, size_t smem);
 size_t dp_smem_bytes(int precision, int n_max);   // forward kernel shared memory of a precision
 size_t dp_state_bytes(const DpLaunch &a);   // bytes per state element
 
