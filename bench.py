@@ -333,7 +333,7 @@ def native_arm(args):
     head_out = out.cpu().numpy()
     extras, keep = {}, {}
     if not args.no_extras and rank == 0:
-        extras, keep = measure_forms(torch, B, flush_buf)
+        extras, keep = measure_forms(torch, B, flush_buf, fp64_peak, sms * 128 * clk * 1e6)
 
     launches_per_step = 1 + 4 + 1   # gather, 4 planner kernels, DP
     line = {
@@ -481,7 +481,21 @@ def measure_bipartite(torch, B, flush_buf, n_cfg, precision="fp64"):
             "assignments_per_config": 256}
 
 
-def measure_forms(torch, B, flush_buf):
+# FP32 instructions a double-float term needs at least (the Dot2 step: 1 multiply, 3 FMA,
+# 8 additions; the first term of a dot product fewer): the FP32-pipe floor of that mode.
+DF64_FP32_PER_TERM = 11.5
+
+
+def close_flops(B, order: np.ndarray, n_mat: int) -> float:
+    """FP64 flops of the loop-closing sums alone (2 per close multiply-add)."""
+    total = 0.0
+    for n in np.unique(order):
+        s = B.cos_structure(int(n))
+        total += int((order == n).sum()) * n_mat * 2.0 * s.fma_close
+    return total
+
+
+def measure_forms(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
     """The other forms of the path on the same GPU: FP64 vs mixed vs double-float (df64)
     precision at orders 8 and 10,
     the uneven-order batch as one persistent launch in a CUDA graph (autotuned shapes), the
@@ -514,6 +528,17 @@ def measure_forms(torch, B, flush_buf):
         tabs.close()
         r = {"configs": n_cfg, "configs_per_s": n_cfg / t, "tflops": fl / t / 1e12, "ms": t * 1e3,
              "launch_shape_n_max": dict(zip(("warps", "ctas_per_sm", "prefetch"), B.cos_get_tuning(nmax, prec, n_mat)))}
+        # roofline of the form: FP64 pipe (FP64), FP64 pipe for the close (mixed), FP32 floor
+        # of the compensated terms (double-float); peaks from the headline's clock sample
+        if prec == "fp64":
+            r["frac_fp64_peak"] = fl / t / fp64_peak
+        elif prec == "mixed":
+            cf = close_flops(B, cfgs.order, n_mat)
+            r["fp64_close_tflops"] = cf / t / 1e12
+            r["frac_fp64_peak_close"] = cf / t / fp64_peak
+        else:
+            terms = fl / 2.0
+            r["frac_fp32_floor"] = terms * DF64_FP32_PER_TERM / t / fp32_lane_ops
         if graph:
             r["cuda_graph"] = True
         return r, out.cpu().numpy()
@@ -528,11 +553,16 @@ def measure_forms(torch, B, flush_buf):
     res["su3_shift_n10_df64"], keep_df10 = run("su3_shift_mixed_n10", 100_000, "df64", steps=1)
     keep["su3_shift_n10_df64_vs_fp64_oracle"] = ("su3_shift_mixed_n10", keep_df10)
     res["su6_uneven_n4_12_fp64_graph"], _ = run("su6_sym_uneven_n4_12", 200_000, "fp64", steps=1, graph=True)
-    res["su4_n10_adjoint"] = measure_adjoint(torch, B, flush_buf, 50_000)
+    adj = measure_adjoint(torch, B, flush_buf, 50_000)
+    adj["frac_fp64_peak"] = adj["grad_tflops"] * 1e12 / fp64_peak
+    res["su4_n10_adjoint"] = adj
     res["su4_n8_all_subsets_fp64"] = measure_subsets(torch, B, flush_buf, 100_000)
-    res["hc_su2_af_n8_bipartite_fp64"] = measure_bipartite(torch, B, flush_buf, I.WORKLOADS["hc_su2_af_n8"].n_cfg)
-    res["hc_su2_af_n8_bipartite_df64"] = measure_bipartite(torch, B, flush_buf, I.WORKLOADS["hc_su2_af_n8"].n_cfg,
-                                                           "df64")
+    hb = measure_bipartite(torch, B, flush_buf, I.WORKLOADS["hc_su2_af_n8"].n_cfg)
+    hb["frac_fp64_peak"] = hb["tflops"] * 1e12 / fp64_peak
+    res["hc_su2_af_n8_bipartite_fp64"] = hb
+    hd = measure_bipartite(torch, B, flush_buf, I.WORKLOADS["hc_su2_af_n8"].n_cfg, "df64")
+    hd["frac_fp32_floor"] = hd["tflops"] * 1e12 / 2.0 * DF64_FP32_PER_TERM / fp32_lane_ops
+    res["hc_su2_af_n8_bipartite_df64"] = hd
     # plain FP64 per-configuration form: one configuration per call, no graph
     w = I.WORKLOADS[WORKLOAD]
     cfgs = I.workload_configs(w, 200)
