@@ -543,6 +543,10 @@ def measure_forms(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
             r["cuda_graph"] = True
         return r, out.cpu().numpy()
 
+    # SU(2) symmetric, order 4, 10^4 configurations: latency- and launch-bound (about 15 us of
+    # FP64 work), one plain call and one CUDA-graph plan launch
+    res["su2_n4_fp64"], _ = run("su2_sym_n4", 10_000, "fp64", steps=5)
+    res["su2_n4_fp64_graph"], _ = run("su2_sym_n4", 10_000, "fp64", steps=5, graph=True)
     res["su4_n8_mixed"], keep_n8 = run("su4_mu_broken_n8", 100_000, "mixed")
     keep["su4_n8_mixed_vs_fp64_oracle"] = ("su4_mu_broken_n8", keep_n8)
     res["su3_shift_n10_mixed"], keep_n10 = run("su3_shift_mixed_n10", 100_000, "mixed")
