@@ -3,8 +3,8 @@
 Usage (on the GPU): python -m paper_2507_12349_b300.autotune [--out FILE]
 Runs cos_autotune for every (order, precision, matrices per configuration) that the
 workloads launch with and writes one line per case: "n precision n_mat warps ctas ms prefetch".
-The sample size fills the GPU: 32 lanes x 2 CTAs x SMs worth of configurations (one CTA
-per SM at orders 11-12, where one batch already holds ~0.3-0.6 s of FP64 work).
+The sample size fills the GPU: a batch per CTA for 2 CTAs per SM (one CTA per SM at orders
+11-12, where one batch already holds ~0.3-0.6 s of FP64 work).
 """
 from __future__ import annotations
 
@@ -36,8 +36,11 @@ def main():
     B.lib()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     lines = []
+    # configurations per lane of each precision's forward kernel (mixed: four, double-float:
+    # two, FP64: one), so that the sample fills every SM with batches
+    per_lane = {"fp64": 1, "mixed": 4, "df64": 2}
     for n, n_mat, wt, shifts, prec in CASES:
-        cpb = 32 // n_mat
+        cpb = (32 // n_mat) * per_lane[prec]
         n_cfg = cpb * sms * (1 if n >= 11 else 2)
         w, c, pf, ms = B.cos_autotune(n, n_mat, wt, shifts, prec, n_cfg)
         line = f"{n} {B.PRECISIONS[prec]} {n_mat} {w} {c} {ms:.4f} {int(pf)}"

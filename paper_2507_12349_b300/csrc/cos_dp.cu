@@ -373,7 +373,7 @@ bool dp_uses_pair(const DpLaunch &L) {
 }
 
 int dp_configs_per_batch(const DpLaunch &L) {
-    return dp_uses_pair(L) ? 2 * (kLanes / L.n_mat) : kLanes / L.n_mat;
+    return dp_uses_pair(L) ? pair_width(L.precision) * (kLanes / L.n_mat) : kLanes / L.n_mat;
 }
 
 size_t dp_smem_bytes(int precision, int n_max) {

@@ -24,7 +24,21 @@ namespace cosdp {
 
 namespace {
 
-__device__ __forceinline__ void push_target_pair(float2 *__restrict__ dst1, const TgtInfo &ti, int q, float2 d,
+// P floats / doubles of one lane (one per configuration), aligned for single vector accesses.
+template <int P>
+struct __align__(4 * P) FV {
+    float v[P];
+};
+template <int P>
+struct __align__(16) DV {
+    double v[P];
+};
+
+// Configurations per lane of the mixed kernel.
+constexpr int kMixedWidth = 4;
+
+template <int P>
+__device__ __forceinline__ void push_target_pair(FV<P> *__restrict__ dst1, const TgtInfo &ti, int q, const FV<P> &d,
                                                  uint32_t hlow, int lane) {
     const uint32_t off1 = __shfl_sync(0xFFFFFFFFu, ti.off1, q);
     const uint32_t meta = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
@@ -33,15 +47,15 @@ __device__ __forceinline__ void push_target_pair(float2 *__restrict__ dst1, cons
     dst1[(size_t)(off1 + hi1 * nA1 + ai1) * kLanes + lane] = d;
 }
 
-template <int NV>
-__device__ __forceinline__ void do_row_pair(const float2 *__restrict__ src, float2 *__restrict__ dst1,
-                                            const float2 *__restrict__ Ms, const double2 *__restrict__ Md,
+template <int P, int NV>
+__device__ __forceinline__ void do_row_pair(const FV<P> *__restrict__ src, FV<P> *__restrict__ dst1,
+                                            const FV<P> *__restrict__ Ms, const DV<P> *__restrict__ Md,
                                             const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow, uint32_t A,
                                             uint32_t off, int h, int hidx, int nA, int n, bool needclose, int lane,
-                                            double2 &csum) {
-    float2 o[NV];
+                                            DV<P> &csum) {
+    FV<P> o[NV];
     int vs[NV];
-    const float2 *row = src + (size_t)(off + (uint32_t)(hidx * nA)) * kLanes + lane;
+    const FV<P> *row = src + (size_t)(off + (uint32_t)(hidx * nA)) * kLanes + lane;
     uint32_t vv = Vrow;
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
@@ -53,9 +67,9 @@ __device__ __forceinline__ void do_row_pair(const float2 *__restrict__ src, floa
     if (needclose) {
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
-            const double2 m = Md[vs[t] + h * kLanes];
-            csum.x = fma(widen(o[t].x), m.x, csum.x);
-            csum.y = fma(widen(o[t].y), m.y, csum.y);
+            const DV<P> m = Md[vs[t] + h * kLanes];
+#pragma unroll
+            for (int c = 0; c < P; ++c) csum.v[c] = fma(widen(o[t].v[c]), m.v[c], csum.v[c]);
         }
     }
     const uint32_t hlow = (1u << h) - 1u;
@@ -66,39 +80,45 @@ __device__ __forceinline__ void do_row_pair(const float2 *__restrict__ src, floa
         jj &= jj - 1u;
         const int jb = __ffs(jj) - 1;
         jj &= jj - 1u;
-        float2 da = make_float2(0.0f, 0.0f), db = make_float2(0.0f, 0.0f);
+        FV<P> da, db;
+#pragma unroll
+        for (int c = 0; c < P; ++c) da.v[c] = db.v[c] = 0.0f;
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
-            const float2 ma = Ms[vs[t] + ja * kLanes];
-            const float2 mb = Ms[vs[t] + jb * kLanes];
-            da.x = fmaf(o[t].x, ma.x, da.x);
-            da.y = fmaf(o[t].y, ma.y, da.y);
-            db.x = fmaf(o[t].x, mb.x, db.x);
-            db.y = fmaf(o[t].y, mb.y, db.y);
+            const FV<P> ma = Ms[vs[t] + ja * kLanes];
+            const FV<P> mb = Ms[vs[t] + jb * kLanes];
+#pragma unroll
+            for (int c = 0; c < P; ++c) {
+                da.v[c] = fmaf(o[t].v[c], ma.v[c], da.v[c]);
+                db.v[c] = fmaf(o[t].v[c], mb.v[c], db.v[c]);
+            }
         }
-        push_target_pair(dst1, ti, q, da, hlow, lane);
-        push_target_pair(dst1, ti, q + 1, db, hlow, lane);
+        push_target_pair<P>(dst1, ti, q, da, hlow, lane);
+        push_target_pair<P>(dst1, ti, q + 1, db, hlow, lane);
     }
     if (q < nJ) {
         const int j = __ffs(jj) - 1;
-        float2 d = make_float2(0.0f, 0.0f);
+        FV<P> d;
+#pragma unroll
+        for (int c = 0; c < P; ++c) d.v[c] = 0.0f;
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
-            const float2 m = Ms[vs[t] + j * kLanes];
-            d.x = fmaf(o[t].x, m.x, d.x);
-            d.y = fmaf(o[t].y, m.y, d.y);
+            const FV<P> m = Ms[vs[t] + j * kLanes];
+#pragma unroll
+            for (int c = 0; c < P; ++c) d.v[c] = fmaf(o[t].v[c], m.v[c], d.v[c]);
         }
-        push_target_pair(dst1, ti, q, d, hlow, lane);
+        push_target_pair<P>(dst1, ti, q, d, hlow, lane);
     }
 }
 
-__device__ __forceinline__ void row_dispatch_pair(int nv, const float2 *src, float2 *dst1, const float2 *Ms,
-                                                  const double2 *Md, const TgtInfo &ti, int nJ, uint32_t J,
+template <int P>
+__device__ __forceinline__ void row_dispatch_pair(int nv, const FV<P> *src, FV<P> *dst1, const FV<P> *Ms,
+                                                  const DV<P> *Md, const TgtInfo &ti, int nJ, uint32_t J,
                                                   uint32_t Vrow, uint32_t A, uint32_t off, int h, int hidx, int nA,
-                                                  int n, bool needclose, int lane, double2 &csum) {
+                                                  int n, bool needclose, int lane, DV<P> &csum) {
 #define COS_ROW_P(K)                                                                                           \
     case K:                                                                                                    \
-        do_row_pair<K>(src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, csum);     \
+        do_row_pair<P, K>(src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, csum);  \
         break;
     switch (nv) {
         COS_ROW_P(1)
@@ -119,12 +139,13 @@ __device__ __forceinline__ void row_dispatch_pair(int nv, const float2 *src, flo
 #undef COS_ROW_P
 }
 
-// One interaction mask for both configurations of every lane (twin of fwd_mask<float>).
+// One interaction mask for the P configurations of every lane (twin of fwd_mask<float>).
+template <int P>
 __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
-                                              int n, const float2 *src, float2 *dst1, const float2 *Ms,
-                                              const double2 *Md, int lane, int ci, int nfl, double sgn, double sig,
-                                              bool shifts, bool act_x, bool act_y, int lam, int cfg_x, int cfg_y,
-                                              double *out, int *status, int prefetch) {
+                                              int n, const FV<P> *src, FV<P> *dst1, const FV<P> *Ms,
+                                              const DV<P> *Md, int lane, int ci, int nfl, double sgn, double sig,
+                                              bool shifts, const bool act[P], const int cfg[P], int lam, double *out,
+                                              int *status, int prefetch) {
     const uint32_t full = (1u << n) - 1u;
     const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + mask_index));
     const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, code = mk.y, off = mk.z;
@@ -134,24 +155,29 @@ __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask
     const int nA = __popc(A);
     const bool needclose = (ones != 0u) || (B == full);
     if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
+        // P * 4-byte states: P / 2 rows of 256 bytes per state slot
         const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + next_index));
         const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
-        prefetch_block(reinterpret_cast<const double *>(src), nk.z,
-                       (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane, prefetch);
+        const uint32_t ns = (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_));
+        prefetch_block(reinterpret_cast<const double *>(src), (uint32_t)(P / 2) * nk.z, (uint32_t)(P / 2) * ns, lane,
+                       prefetch);
     }
-    double2 csum = make_double2(0.0, 0.0);
+    DV<P> csum;
+#pragma unroll
+    for (int c = 0; c < P; ++c) csum.v[c] = 0.0;
     const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, lane);
     const int nJ = __popc(J);
     for (uint32_t hh = H; hh; hh &= hh - 1u) {
         const int h = __ffs(hh) - 1;
         const int hidx = __popc(H & ((1u << h) - 1u));
         const uint32_t Vrow = row_vmask(A, ones, h);
-        row_dispatch_pair(__popc(Vrow), src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane,
-                          csum);
+        row_dispatch_pair<P>(__popc(Vrow), src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose,
+                             lane, csum);
     }
     if (!needclose) return;   // no half-visited vertex and not full: disconnected, dropped
-    const double Cx = flavor_sum(csum.x, nfl, ci);
-    const double Cy = flavor_sum(csum.y, nfl, ci);
+    double C[P];
+#pragma unroll
+    for (int c = 0; c < P; ++c) C[c] = flavor_sum(csum.v[c], nfl, ci);
     if (ones) {
         const int k = __ffs(ones) - 1;
         const uint32_t bk = 1u << k;
@@ -159,32 +185,30 @@ __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask
         const int hi1 = __popc(head_set(B1, A & ~B1) & (bk - 1u));
         const int ai1 = __popc(A & (bk - 1u));
         const uint32_t off1 = __ldg(tab.rank3 + code + c_p3[k]);
-        float2 *tp = dst1 + (size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane;
-        double vx = Cx, vy = Cy;
-        if (ell == 1 && shifts) {   // vertex 0 carries a shift point
-            vx += sgn * 2.0 * sig;
-            vy += sgn * 2.0 * sig;
+        FV<P> *tp = dst1 + (size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane;
+        FV<P> tv;
+#pragma unroll
+        for (int c = 0; c < P; ++c) {
+            double v = C[c];
+            if (ell == 1 && shifts) v += sgn * 2.0 * sig;   // vertex 0 carries a shift point
+            tv.v[c] = narrow_to(0.0f, v);
         }
-        const float2 tv = make_float2(narrow_to(0.0f, vx), narrow_to(0.0f, vy));
-        if (k == 0) {               // the extension into 0' wrote it
-            float2 cur = *tp;
-            cur.x += tv.x;
-            cur.y += tv.y;
+        if (k == 0) {                                       // the extension into 0' wrote it
+            FV<P> cur = *tp;
+#pragma unroll
+            for (int c = 0; c < P; ++c) cur.v[c] += tv.v[c];
             *tp = cur;
         } else {
             *tp = tv;
         }
     } else if (lam == 0 && out) {
-        if (act_x) {
-            const double c = ldexp(Cx, n - 1);
-            out[cfg_x] = c;
-            if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
-        }
-        if (act_y) {
-            const double c = ldexp(Cy, n - 1);
-            out[cfg_y] = c;
-            if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
-        }
+#pragma unroll
+        for (int c = 0; c < P; ++c)
+            if (act[c]) {
+                const double r = ldexp(C[c], n - 1);
+                out[cfg[c]] = r;
+                if (!isfinite(r)) atomicOr(status, kStatusNonFinite);
+            }
     }
 }
 
@@ -370,7 +394,7 @@ __device__ __forceinline__ void fwd_mask_dfp(const OrderTab &tab, uint32_t mask_
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_dfp_kernel(const __grid_constant__ DpArgs a);
 
-template <int MAXT>
+template <int P, int MAXT>
 __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_kernel(const __grid_constant__ DpArgs a) {
     extern __shared__ __align__(16) unsigned char smem_p[];
     __shared__ int s_batch;
@@ -378,9 +402,9 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_kernel(cons
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int nsm = a.smem_n * a.smem_n * kLanes;
-    float2 *Ms = reinterpret_cast<float2 *>(smem_p);
-    double2 *Md = reinterpret_cast<double2 *>(smem_p + (size_t)nsm * sizeof(float2));
-    float2 *ring = reinterpret_cast<float2 *>(a.scratch) + (size_t)blockIdx.x * a.nslots * a.slot_elems;
+    FV<P> *Ms = reinterpret_cast<FV<P> *>(smem_p);
+    DV<P> *Md = reinterpret_cast<DV<P> *>(smem_p + (((size_t)nsm * sizeof(FV<P>) + 15) & ~size_t(15)));
+    FV<P> *ring = reinterpret_cast<FV<P> *>(a.scratch) + (size_t)blockIdx.x * a.nslots * a.slot_elems;
     const int nfl = a.nf_lanes;
     const int lam = lane % nfl;
     const int ci = lane / nfl;
@@ -399,38 +423,49 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_kernel(cons
         const int n = bd.x;
         const OrderTab &tab = a.tabs[n];
         const bool lane_ok = ci * nfl + nfl <= kLanes;
-        const bool act_x = lane_ok && (ci < bd.z);
-        const bool act_y = lane_ok && (ci + cpl < bd.z);
-        const int cfg_x = act_x ? a.batch_list[bd.y + ci] : -1;
-        const int cfg_y = act_y ? a.batch_list[bd.y + cpl + ci] : -1;
-        const double *Mx = act_x ? a.M + (a.moff ? a.moff[cfg_x] : (int64_t)cfg_x * a.mstride) + (size_t)lam * n * n
-                                 : nullptr;
-        const double *My = act_y ? a.M + (a.moff ? a.moff[cfg_y] : (int64_t)cfg_y * a.mstride) + (size_t)lam * n * n
-                                 : nullptr;
+        bool act[P];
+        int cfg[P];
+        const double *Mp[P];
+#pragma unroll
+        for (int c = 0; c < P; ++c) {
+            act[c] = lane_ok && (ci + c * cpl < bd.z);
+            cfg[c] = act[c] ? a.batch_list[bd.y + c * cpl + ci] : -1;
+            Mp[c] = act[c] ? a.M + (a.moff ? a.moff[cfg[c]] : (int64_t)cfg[c] * a.mstride) + (size_t)lam * n * n
+                           : nullptr;
+        }
         const double cfac = sgn * a.loop_weight;
         const double dshift = sgn * sig;
         for (int e = warp; e < n * n; e += nwarps) {
-            double vx = act_x ? Mx[e] : 0.0, vy = act_y ? My[e] : 0.0;
-            if (a.absmode) {
-                vx = fabs(vx);
-                vy = fabs(vy);
-            }
             const int v = e / n, j = e % n;
             const bool sh = v == j && j != 0 && shifts;
-            Ms[e * kLanes + lane] = make_float2((float)(sh ? vx + dshift : vx), (float)(sh ? vy + dshift : vy));
-            Md[e * kLanes + lane] = make_double2(cfac * vx, cfac * vy);
+            FV<P> m;
+            DV<P> d;
+#pragma unroll
+            for (int c = 0; c < P; ++c) {
+                double val = act[c] ? Mp[c][e] : 0.0;
+                if (a.absmode) val = fabs(val);
+                m.v[c] = (float)(sh ? val + dshift : val);
+                d.v[c] = cfac * val;
+            }
+            Ms[e * kLanes + lane] = m;
+            Md[e * kLanes + lane] = d;
         }
-        if (warp == 0) ring[(1 % a.nslots) * a.slot_elems + lane] = make_float2(1.0f, 1.0f);
+        if (warp == 0) {
+            FV<P> one;
+#pragma unroll
+            for (int c = 0; c < P; ++c) one.v[c] = 1.0f;
+            ring[(1 % a.nslots) * a.slot_elems + lane] = one;
+        }
         __syncthreads();
         for (int ell = 1; ell <= 2 * n; ++ell) {
-            const float2 *src = ring + (size_t)(ell % a.nslots) * a.slot_elems;
-            float2 *dst1 = ring + (size_t)((ell + 1) % a.nslots) * a.slot_elems;
+            const FV<P> *src = ring + (size_t)(ell % a.nslots) * a.slot_elems;
+            FV<P> *dst1 = ring + (size_t)((ell + 1) % a.nslots) * a.slot_elems;
             const uint32_t first = tab.layer_first[ell];
             const uint32_t cnt = tab.layer_count[ell];
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
-                fwd_mask_pair(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src,
-                              dst1, Ms, Md, lane, ci, nfl, sgn, sig, shifts, act_x, act_y, lam, cfg_x, cfg_y, a.out,
-                              a.status, a.prefetch);
+                fwd_mask_pair<P>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src,
+                                 dst1, Ms, Md, lane, ci, nfl, sgn, sig, shifts, act, cfg, lam, a.out, a.status,
+                                 a.prefetch);
             __syncthreads();
         }
     }
@@ -517,16 +552,19 @@ static auto pair_kernel_for(int precision, int threads) {
     if (precision == COS_DF64)
         return threads <= 256 ? dp_pair_dfp_kernel<256>
                               : (threads <= 384 ? dp_pair_dfp_kernel<384> : dp_pair_dfp_kernel<512>);
-    return threads <= 256 ? dp_pair_kernel<256> : (threads <= 384 ? dp_pair_kernel<384> : dp_pair_kernel<512>);
+    return threads <= 256 ? dp_pair_kernel<kMixedWidth, 256>
+                          : (threads <= 384 ? dp_pair_kernel<kMixedWidth, 384> : dp_pair_kernel<kMixedWidth, 512>);
 }
 
 size_t pair_smem_bytes(int precision, int n_max) {
     const size_t msm = (size_t)n_max * n_max * kLanes;
     if (precision == COS_DF64) return 2 * msm * sizeof(df64x2);
-    return msm * sizeof(float2) + msm * sizeof(double2);
+    return ((msm * sizeof(FV<kMixedWidth>) + 15) & ~size_t(15)) + msm * sizeof(DV<kMixedWidth>);
 }
 
-size_t pair_state_bytes(int precision) { return precision == COS_DF64 ? sizeof(df64x2) : sizeof(float2); }
+size_t pair_state_bytes(int precision) { return precision == COS_DF64 ? sizeof(df64x2) : sizeof(FV<kMixedWidth>); }
+
+int pair_width(int precision) { return precision == COS_DF64 ? 2 : kMixedWidth; }
 
 int pair_max_active_ctas(int precision, int threads, size_t smem) {
     int nb = 0;
@@ -549,7 +587,7 @@ cos_status launch_dp_pair(Workspace *ws, const DpLaunch &L, cudaStream_t stream)
     const int nslots = 2;
     const size_t slot_elems = (size_t)host_order(L.n_max).max_slots * kLanes;
     const size_t per_cta = (size_t)nslots * slot_elems * pair_state_bytes(L.precision);
-    const int cpb = 2 * (kLanes / nfl);
+    const int cpb = pair_width(L.precision) * (kLanes / nfl);
     const int max_batches = (L.n_cfg + cpb - 1) / cpb + COS_NMAX;
     int grid = std::max(1, std::min(nsm * tu.ctas_per_sm, max_batches));
     if (ws->fixed_grid > 0) {

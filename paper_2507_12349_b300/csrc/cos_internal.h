@@ -188,6 +188,7 @@ bool dp_uses_pair(const DpLaunch &a);
 int dp_configs_per_batch(const DpLaunch &a);
 cos_status launch_dp_pair(Workspace *ws, const DpLaunch &a, cudaStream_t stream);
 size_t pair_smem_bytes(int precision, int n_max);
+int pair_width(int precision);   // configurations per lane of the pair kernel of a precision
 int pair_max_active_ctas(int precision, int threads, size_t smem);
 size_t dp_smem_bytes(int precision, int n_max);   // forward kernel shared memory of a precision
 size_t dp_state_bytes(const DpLaunch &a);   // bytes per state element
