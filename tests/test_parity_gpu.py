@@ -233,6 +233,23 @@ def test_dp_order12_relabel_invariance():
     assert abs(got[0] - ref) <= fp64_bound(12, mass[0])
 
 
+@pytest.mark.parametrize("precision", ["mixed", "df64"])
+def test_order11_invariances_reduced_precision(precision):
+    """Relabeling and transpose at order 11 with three broken flavors and shifts, for the
+    reduced-precision kernels (two and four configurations per lane): each result stays
+    within its mode's bound of the FP64 one."""
+    n, nf = 11, 3
+    M = I.random_matrices(88, 1, nf, n, 0.9)[0]
+    perm = np.random.default_rng(2).permutation(n)
+    Ms = [M, M[:, perm][:, :, perm], M.transpose(0, 2, 1)] * 3   # several per batch
+    sig = [0.08, -0.05, 0.0]
+    ref, mass = run_matrices(Ms, nf, 1, sig, abs_mass=True)
+    got, _ = run_matrices(Ms, nf, 1, sig, precision=precision)
+    bound = mixed_bound(n, mass[0]) if precision == "mixed" else df64_bound(n, mass[0])
+    assert np.all(np.abs(ref - ref[0]) <= fp64_bound(n, mass[0]))
+    assert np.all(np.abs(got - ref[0]) <= bound + fp64_bound(n, mass[0]))
+
+
 # ------------------------------------------------------------------ workloads through the coordinates path
 
 def workload_check(name, n_cfg, sample, prec="fp64", rel=1e-10):
@@ -299,3 +316,11 @@ def test_workload_su4_df64_order8_sampled():
 
 def test_workload_su3_df64_order10_sampled():
     workload_check("su3_shift_mixed_n10", 1_000, 4, prec="df64")
+
+
+def test_workload_su6_uneven_df64_sampled():
+    workload_check("su6_sym_uneven_n4_12", 2_000, 10, prec="df64")
+
+
+def test_workload_su4_mixed_order8_sampled():
+    workload_check("su4_mu_broken_n8", 5_000, 12, prec="mixed")

@@ -131,7 +131,7 @@ def test_uneven_orders_and_padding():
             assert abs(a[k][S] - ar[S]) <= 2 * bounds(n, am[S], "fp64", n), (k, S)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "df64"])
 def test_root_zero_mode_is_the_dp_by_product(precision):
     """all_roots = 0: sets holding vertex 0 equal the all-roots values bit for bit (same per-lane
     arithmetic), the other sets are NaN, and c(V) equals cos_connected_sum_matrices."""
