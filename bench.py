@@ -36,9 +36,9 @@ UNIT = "configs/s"
 NOMINAL_FP64_TFLOPS = 1.25
 # DRAM bytes (read + write) of dp_forward_kernel<double> per configuration of the headline
 # workload: ncu dram__bytes_read.sum + dram__bytes_write.sum on a 5 000-configuration launch
-# (8.630 GB + 7.111 GB, profiles/dp_forward_fp64_su4_n8.md); traffic grows in proportion
+# (8.617 GB + 7.107 GB, profiles/dp_forward_fp64_su4_n8.md); traffic grows in proportion
 # to the configurations of a launch.
-HEADLINE_DRAM_BYTES_PER_CFG = (8.629577e9 + 7.111385e9) / 5000
+HEADLINE_DRAM_BYTES_PER_CFG = (8.616600e9 + 7.107427e9) / 5000
 FP64_FMA_PER_CLK_SM = 2.0
 
 
