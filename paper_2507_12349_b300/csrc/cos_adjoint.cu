@@ -214,6 +214,12 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
             const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
             for (uint32_t mi = 0; mi < cnt && own; ++mi) {
                 const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + first + mi));
+                // the warps take turns to pull a later mask's forward states into L2 ahead of use
+                if (mi + 2 < cnt && (int)((mi + 2) % nwarps) == warp) {
+                    const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + first + mi + 2));
+                    const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
+                    prefetch_block(fsrc, nk.z, (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane, 1);
+                }
                 const uint32_t A = mk.x & 0xFFFFu;
                 if (!(A & own)) continue;   // endpoints are visited vertices
                 const uint32_t B = mk.x >> 16, code = mk.y, off = mk.z;
