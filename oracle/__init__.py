@@ -24,6 +24,12 @@ Functions and the passages they follow:
   or the sublattice-resolved merged DP of Alg. 1-2 (``method="dp4"``).
 * ``dp``, ``closed``, ``brute`` also take per-(flavor, vertex) shift weights
   (``sigma`` of shape [nf][n]).
+* ``det_clow`` -- SU(2) connected sums with determinant weights by the DP without
+  cycle factors of Alg. 1 (point-resolved states, interaction masks only, nonphysical
+  clow sequences kept), on one or two sublattices (``oracle_det.h``).
+* ``det_closed`` / ``det_brute`` -- the same sum from its definition: determinants of
+  both spin blocks plus the subset subtraction of Methods A, or the block permutations
+  enumerated one by one with a connectivity check.
 
 Precision: 'd' (double), 'ld' (x87 long double) or 'q' (__float128).
 """
@@ -72,6 +78,9 @@ def lib():
             f.restype = ctypes.c_int
             f = getattr(L, "bip_dp4" + sfx)
             f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp_, dp_, ctypes.c_int, dp_, dp_]
+            f.restype = ctypes.c_int
+            f = getattr(L, "det_clow" + sfx)
+            f.argtypes = [ctypes.c_int, ctypes.c_int, dp_, dp_, ctypes.c_int, dp_, dp_]
             f.restype = ctypes.c_int
             f = getattr(L, "dp_batch" + sfx)
             f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp_, dp_, ctypes.c_int,
@@ -351,3 +360,121 @@ def bip_assignment(M4: np.ndarray, sigma2: Optional[np.ndarray], s: Sequence[int
     M = M4[:, idx[:, None], s[:, None], idx[None, :], s[None, :]]
     sig = None if sigma2 is None else _f64(sigma2)[:, s]
     return np.ascontiguousarray(M), sig
+
+
+# ------------------------------------------------------------------ SU(2) determinant weights
+
+def _det_blocks(G, alpha):
+    """Spin blocks as [2][n][nsub][n][nsub] and diagonal shifts as [2][nsub]: G is [2][n][n]
+    (one sublattice) or [2][n][2][n][2] (two)."""
+    G = _f64(G)
+    if G.ndim == 3 and G.shape[0] == 2 and G.shape[1] == G.shape[2]:
+        n, nsub = G.shape[1], 1
+        G = G.reshape(2, n, 1, n, 1)
+    elif G.ndim == 5 and G.shape[0] == 2 and G.shape[2] == 2 and G.shape[4] == 2 and G.shape[1] == G.shape[3]:
+        n, nsub = G.shape[1], 2
+    else:
+        raise ValueError("G must have shape [2][n][n] or [2][n][2][n][2]")
+    al = None if alpha is None else _f64(alpha).reshape(2, nsub)
+    return np.ascontiguousarray(G), al, n, nsub
+
+
+def det_clow(G, alpha=None, absmode: bool = False, prec: str = "d") -> float:
+    """Connected sum of an SU(2) model with determinant weights by the DP of Alg. 1.
+    G [2][n][n] (spin up, spin down) or [2][n][2][n][2] (spin, vertex, sublattice, vertex,
+    sublattice); alpha [2] or [2][2] diagonal shifts (a(p s, p s) - alpha_{spin, s}) or None."""
+    Gb, al, n, nsub = _det_blocks(G, alpha)
+    hi, lo = ctypes.c_double(), ctypes.c_double()
+    rc = getattr(lib(), "det_clow_" + prec)(n, nsub, _ptr(Gb), _ptr(al), int(absmode), ctypes.byref(hi),
+                                             ctypes.byref(lo))
+    if rc:
+        raise ValueError("det_clow: unsupported sizes")
+    return hi.value + lo.value
+
+
+def _det_assignment(Gb, al, n, nsub, S, s):
+    """Shifted spin-block matrices restricted to the vertex list S with sublattices s."""
+    mats = []
+    for b in range(2):
+        A = np.array([[Gb[b, i, s[x], j, s[y]] for y, j in enumerate(S)] for x, i in enumerate(S)])
+        if al is not None:
+            A = A - np.diag([al[b, s[x]] for x in range(len(S))])
+        mats.append(A)
+    return mats
+
+
+def det_closed(G, alpha=None) -> float:
+    """The connected sum from its definition (Methods A): a(S) = sum over sublattice
+    assignments of det(A_up[S]) det(A_dn[S]) by LU, a(empty) = 1, and the subset subtraction
+    c(S) = a(S) - sum_{T proper, T contains min S} c(T) a(S minus T).  n <= 10 (one
+    sublattice) or n <= 7 (two)."""
+    Gb, al, n, nsub = _det_blocks(G, alpha)
+    if (nsub == 1 and n > 10) or (nsub == 2 and n > 7):
+        raise ValueError("det_closed: n too large")
+    a = np.zeros(1 << n)
+    a[0] = 1.0
+    for m in range(1, 1 << n):
+        S = [i for i in range(n) if m >> i & 1]
+        tot = 0.0
+        for s in itertools.product(range(nsub), repeat=len(S)):
+            up, dn = _det_assignment(Gb, al, n, nsub, S, s)
+            tot += np.linalg.det(up) * np.linalg.det(dn)
+        a[m] = tot
+    c = np.zeros(1 << n)
+    for m in range(1, 1 << n):
+        low = m & -m
+        rest = m ^ low
+        val = a[m]
+        t = rest
+        while True:
+            sub = t | low
+            if sub != m:
+                val -= c[sub] * a[m ^ sub]
+            if t == 0:
+                break
+            t = (t - 1) & rest
+        c[m] = val
+    return float(c[(1 << n) - 1])
+
+
+def det_brute(G, alpha=None) -> float:
+    """The connected sum diagram by diagram (n <= 4): every pair of permutations (one per
+    spin block) and sublattice assignment, signed by sgn(pi_up) sgn(pi_dn), kept when the
+    vertices joined by i - pi_b(i) form one component."""
+    Gb, al, n, nsub = _det_blocks(G, alpha)
+    if n > 4:
+        raise ValueError("det_brute: n <= 4")
+
+    def sign(p):
+        sg, seen = 1, [False] * n
+        for i in range(n):
+            if seen[i]:
+                continue
+            j, ln = i, 0
+            while not seen[j]:
+                seen[j] = True
+                j = p[j]
+                ln += 1
+            sg *= -1 if ln % 2 == 0 else 1
+        return sg
+
+    perms = list(itertools.permutations(range(n)))
+    total = 0.0
+    for s in itertools.product(range(nsub), repeat=n):
+        up, dn = _det_assignment(Gb, al, n, nsub, list(range(n)), s)
+        for pu in perms:
+            wu = sign(pu) * np.prod([up[i, pu[i]] for i in range(n)])
+            for pd in perms:
+                comp = list(range(n))
+
+                def find(x):
+                    while comp[x] != x:
+                        x = comp[x]
+                    return x
+                for i in range(n):
+                    comp[find(i)] = find(pu[i])
+                    comp[find(i)] = find(pd[i])
+                if len({find(i) for i in range(n)}) > 1:
+                    continue
+                total += wu * sign(pd) * np.prod([dn[i, pd[i]] for i in range(n)])
+    return total

@@ -5,7 +5,8 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "cos_oracle.c")
-DEPS = [SRC, os.path.join(HERE, "oracle_impl.h"), os.path.join(HERE, "oracle_bip.h")]
+DEPS = [SRC, os.path.join(HERE, "oracle_impl.h"), os.path.join(HERE, "oracle_bip.h"),
+        os.path.join(HERE, "oracle_det.h")]
 LIB = os.path.join(HERE, "libcos_oracle.so")
 
 

@@ -9,9 +9,11 @@
  *   brute   decorated covers enumerated one by one (n <= 5 in practice)
  *   closed  determinants + the subset subtraction of Methods A
  *   dp      the merged clow-sequence DP of Results A / Alg. 2-3, plain loops
- * and the bipartite (two-sublattice) sums of oracle_bip.h: the definition (sum over
- * sublattice assignments) and the sublattice-resolved merged DP of Alg. 1-2.
- * Every function states the passage it follows in oracle_impl.h / oracle_bip.h.
+ * the bipartite (two-sublattice) sums of oracle_bip.h: the definition (sum over
+ * sublattice assignments) and the sublattice-resolved merged DP of Alg. 1-2; and the SU(2)
+ * determinant-weight DP without cycle factors of oracle_det.h (Alg. 1).
+ * Every function states the passage it follows in oracle_impl.h / oracle_bip.h /
+ * oracle_det.h.
  */
 #include <stdlib.h>
 #include <string.h>
@@ -26,6 +28,7 @@
 #define RABS(x) fabs(x)
 #include "oracle_impl.h"
 #include "oracle_bip.h"
+#include "oracle_det.h"
 #undef REAL
 #undef FN
 #undef RABS
@@ -35,6 +38,7 @@
 #define RABS(x) fabsl(x)
 #include "oracle_impl.h"
 #include "oracle_bip.h"
+#include "oracle_det.h"
 #undef REAL
 #undef FN
 #undef RABS
@@ -44,6 +48,7 @@
 #define RABS(x) fabsq(x)
 #include "oracle_impl.h"
 #include "oracle_bip.h"
+#include "oracle_det.h"
 #undef REAL
 #undef FN
 #undef RABS
