@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
     p.add_argument("--n-cfg", type=int, default=0, help="smaller configuration count (profiling runs only)")
     p.add_argument("--workload", default=WORKLOAD,
-                   choices=sorted(k for k, v in I.WORKLOADS.items() if isinstance(v.model, I.Model)),
+                   choices=sorted(k for k, v in I.WORKLOADS.items() if isinstance(v.model, I.Model) and not v.det),
                    help="profiling runs only: run this workload's DP instead of the headline")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "df64"], help="profiling runs only")
     p.add_argument("--grad", action="store_true",

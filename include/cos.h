@@ -270,6 +270,35 @@ cos_status cos_connected_sum_bipartite_batch(const cos_tables *tables, int n_cfg
                                              cos_precision precision, double *d_out,
                                              double *d_abs_mass, cos_stream_t stream);
 
+/* ------------------------------------------------------------------ SU(2) determinant weights
+ * Connected sums of an SU(2) model whose diagrams are weighted by determinants (the
+ * interaction (n_up - alpha_up)(n_dn - alpha_dn), Methods A): the sum of all diagrams of a
+ * vertex set S is a(S) = det(A_up[S]) det(A_dn[S]) (summed over sublattice assignments on a
+ * bipartite lattice), A_b = M_b - diag(alpha_b), and the output is its connected part c(V)
+ * (the subset subtraction of Methods A).  Computed by the DP without cycle factors of Results
+ * A and Alg. 1: only the interaction mask is tracked, nonphysical clow sequences are kept and
+ * cancel, and every vertex has a spin-up point (block 0) and a spin-down point (block 1).
+ * For alpha = 0 the CoS sum of the same matrices with n_mat = 2, loop_weight = 1 is 2^n c(V).
+ *
+ * Square lattice: d_M holds per configuration the two blocks [2][n_c][n_c] (spin up, spin
+ * down) at d_moff[c], as written by cos_gather for two-flavor tables; h_alpha = NULL or
+ * host [2] diagonal shifts.  Precision COS_FP64, COS_MIXED (FP32 extension, FP64 close) or
+ * COS_DF64.  d_abs_mass: NULL, or the same DP on |M| with |alpha| added to the diagonal and
+ * every sign + (an upper bound on the sum of |terms| of the DP, nonphysical clows included).
+ * Other arguments and errors as cos_connected_sum_matrices. */
+cos_status cos_connected_det_matrices(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                                      const double *h_alpha, const double *d_M, cos_precision precision,
+                                      double *d_out, double *d_abs_mass, cos_stream_t stream);
+
+/* Bipartite lattice (Alg. 1 as stated): d_M4 per configuration [2][2 n_c][2 n_c] (spin block,
+ * then the layout of cos_gather_bipartite), h_alpha2 = NULL or host [2][2] diagonal shifts per
+ * (spin, sublattice); n_max <= COS_BIP_NMAX; precision COS_FP64 or COS_DF64.  Outputs and
+ * errors as cos_connected_sum_bipartite_matrices. */
+cos_status cos_connected_det_bipartite_matrices(int n_cfg, int n_max, const int32_t *d_order,
+                                                const int64_t *d_moff, const double *h_alpha2,
+                                                const double *d_M4, cos_precision precision,
+                                                double *d_out, double *d_abs_mass, cos_stream_t stream);
+
 /* ------------------------------------------------------------------ adjoint DP
  * Gradient of the connected sums by the reverse (adjoint) DP: the forward DP is re-run with
  * every layer kept, then walked backwards (the adjoint of Alg. 2-3 as merged in Results A).

@@ -32,6 +32,7 @@ EXPORTS = [
     "cos_connected_sum_subsets",
     "cos_build_propagators_honeycomb", "cos_gather_bipartite", "cos_connected_sum_bipartite_matrices",
     "cos_connected_sum_bipartite_batch", "cos_bipartite_structure",
+    "cos_connected_det_matrices", "cos_connected_det_bipartite_matrices",
     "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_sync_status", "cos_status_string",
     "cos_last_error", "cos_structure", "cos_peak_probe",
     "cos_plan_create_batch", "cos_plan_create_matrices", "cos_plan_launch", "cos_plan_status", "cos_plan_grid",
@@ -238,6 +239,30 @@ def cos_connected_sum_bipartite_matrices(n_max: int, order, moff, n_mat: int, lo
                                                       _ptr(M4, "f64"), PRECISIONS[precision], _ptr(out, "f64"),
                                                       _ptr(abs_mass, "f64"), _stream(stream)),
            "cos_connected_sum_bipartite_matrices")
+
+
+def cos_connected_det_matrices(n_max: int, order, moff, alpha: Optional[Sequence[float]], M, precision: str, out,
+                               abs_mass=None, stream=None):
+    """SU(2) determinant weights (Alg. 1): M holds [2][n_c][n_c] (spin up, spin down) per
+    configuration at moff; alpha None or the two diagonal shifts."""
+    al = None if alpha is None else (ctypes.c_double * 2)(*[float(x) for x in alpha])
+    _check(lib().cos_connected_det_matrices(int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(moff, "i64"), al,
+                                            _ptr(M, "f64"), PRECISIONS[precision], _ptr(out, "f64"),
+                                            _ptr(abs_mass, "f64"), _stream(stream)), "cos_connected_det_matrices")
+
+
+def cos_connected_det_bipartite_matrices(n_max: int, order, moff, alpha2, M4, precision: str, out, abs_mass=None,
+                                         stream=None):
+    """SU(2) determinant weights on a bipartite lattice (Alg. 1): M4 holds [2][2 n_c][2 n_c]
+    per configuration at moff; alpha2 None or 2 x 2 diagonal shifts (spin, sublattice)."""
+    al = None
+    if alpha2 is not None:
+        flat = [float(x) for row in alpha2 for x in row]
+        al = (ctypes.c_double * 4)(*flat)
+    _check(lib().cos_connected_det_bipartite_matrices(int(order.numel()), int(n_max), _ptr(order, "i32"),
+                                                      _ptr(moff, "i64"), al, _ptr(M4, "f64"), PRECISIONS[precision],
+                                                      _ptr(out, "f64"), _ptr(abs_mass, "f64"), _stream(stream)),
+           "cos_connected_det_bipartite_matrices")
 
 
 def cos_connected_sum_bipartite_batch(tables: Tables, n_max: int, order, offset, site, tau, precision: str, out,

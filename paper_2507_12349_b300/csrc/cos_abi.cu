@@ -327,6 +327,33 @@ extern "C" cos_status cos_connected_sum_matrices(int n_cfg, int n_max, const int
                          d_abs_mass, (cudaStream_t)stream);
 }
 
+extern "C" cos_status cos_connected_det_matrices(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                                                 const double *h_alpha, const double *d_M, cos_precision precision,
+                                                 double *d_out, double *d_abs_mass, cos_stream_t stream) {
+    cos_status st = check_matrices(n_cfg, n_max, d_order, d_moff, 2, 1, d_M, precision, d_out,
+                                   "cos_connected_det_matrices");
+    if (st != COS_OK || n_cfg == 0) return st;
+    std::string err;
+    Workspace *ws = get_workspace((cudaStream_t)stream, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    DpLaunch L;
+    L.n_cfg = n_cfg;
+    L.n_max = n_max;
+    L.order = d_order;
+    L.M = d_M;
+    L.moff = d_moff;
+    L.n_mat = 2;
+    L.loop_weight = 1;
+    for (int b = 0; b < 2; ++b) L.sigma[b] = h_alpha ? h_alpha[b] : 0.0;   // the diagonal shifts
+    L.clow = true;
+    L.precision = precision;
+    L.out = d_out;
+    return run_dp(ws, L, d_abs_mass, (cudaStream_t)stream);
+}
+
 extern "C" cos_status cos_gather(const cos_tables *t, int n_cfg, const int32_t *d_order, const int64_t *d_offset,
                                  const int32_t *d_site, const double *d_tau, const int64_t *d_moff, double *d_M,
                                  cos_stream_t stream) {

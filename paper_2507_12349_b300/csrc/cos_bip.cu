@@ -18,6 +18,12 @@
 // matrices, exactly as in the square-lattice kernel; vertex 0's shifted start seeds
 // -2 sigma_{l, s_0}.
 //
+// Determinant weights without cycle factors (CLOW instantiations, Alg. 1 as stated for the
+// SU(2) bipartite model): lanes are the two spin blocks, entering an untouched vertex has
+// weight 1, the first loop (head point 0 in block 0) never steps onto vertex 0 and its close
+// opens the next loop in block 1 only, every diagonal a(j s, j s) carries - alpha_{b,s} in
+// both matrix copies, and the sink takes no 2^(n-1) (see cos_dp.cu for the mapping).
+//
 // Layout: a mask's block holds |H| x 2 rows (h, s_h) of |A| x 2 slots (v, s_v) in the
 // vertex-ordered visited set; only reachable slots are written or read (a half-visited
 // endpoint has its recorded sublattice, the endpoint v = h has s_h, the first loop's head has
@@ -386,7 +392,7 @@ __device__ __forceinline__ void bip_row_dispatch(int nv, const T *src, T *dst1, 
 
 // One interaction mask: its rows, the flavor sum of the close, the seed of the next loop or
 // the sink.  seedsh = sgn 2 sigma_{l, s} of this lane for vertex 0's shifted start on s.
-template <typename T>
+template <typename T, bool CLOW>
 __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
                                          int n, const T *src, T *dst1, const T *Ms, const T *Md, int lane, int ci,
                                          int nfl, const T seedsh[2], bool shifts, bool active, int lam, int cfg,
@@ -397,7 +403,7 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
     const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, S = mk.y, code = mk.z, off = mk.w;
     const uint32_t ones = A & ~B;
     const uint32_t H = head_set(B, ones);
-    const uint32_t J = full & ~B;
+    const uint32_t J = full & ~B & (CLOW ? ~(ones & 1u) : 0xFFFFFFFFu);   // CLOW: not onto the head point
     const int nA = __popc(A);
     const bool needclose = (ones != 0u) || (B == full);
     if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
@@ -437,17 +443,18 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
         T *tp = dst1 + (size_t)(off1 + (uint32_t)(((hi1 * 2 + sk) * nA + __popc(A & (bk - 1u))) * 2 + sk)) * kLanes +
                 lane;
         T val = C;
-        if (ell == 1 && shifts) val = Ar::add(val, seedsh[S & 1u]);   // vertex 0 carries a shift point
-        if (k == 0) *tp = Ar::add(*tp, val);                           // the extension into 0' wrote it
+        if (!CLOW && ell == 1 && shifts) val = Ar::add(val, seedsh[S & 1u]);   // vertex 0 carries a shift point
+        if (CLOW) *tp = (k == 0 && lam == 0) ? Ar::store(Ar::zero()) : val;    // k = 0: block 1 only
+        else if (k == 0) *tp = Ar::add(*tp, val);                               // the extension into 0' wrote it
         else *tp = val;
     } else if (active && (lam == 0) && out) {
-        const double c = ldexp(Ar::to_double(C), n - 1);
+        const double c = CLOW ? Ar::to_double(C) : ldexp(Ar::to_double(C), n - 1);
         out[cfg] = c;
         if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
     }
 }
 
-template <typename T>
+template <typename T, bool CLOW>
 __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ BipArgs a) {
     extern __shared__ __align__(16) unsigned char smem_bip[];
     __shared__ int s_batch;
@@ -489,16 +496,23 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
             double val = active ? Mc[e] : 0.0;
             if (a.absmode) val = fabs(val);
             const int r = e / n2, c = e % n2;
-            const bool shifted = (r == c) && (r >= 2) && shifts;   // (j, s) -> (j, s), j >= 1
-            to_elem(shifted ? val + sgn * sig[r & 1] : val, Ms[e * kLanes + lane]);
-            to_elem(cfac * val, Md[e * kLanes + lane]);
+            if (CLOW) {
+                const double m = (r == c) ? val + sgn * sig[r & 1] : val;   // a(j s, j s) - alpha_{b,s}
+                to_elem(m, Ms[e * kLanes + lane]);
+                to_elem(cfac * m, Md[e * kLanes + lane]);
+            } else {
+                const bool shifted = (r == c) && (r >= 2) && shifts;   // (j, s) -> (j, s), j >= 1
+                to_elem(shifted ? val + sgn * sig[r & 1] : val, Ms[e * kLanes + lane]);
+                to_elem(cfac * val, Md[e * kLanes + lane]);
+            }
         }
         // Start: the loop through the normal point of vertex 0 on sublattice s_0 (layer 1,
         // masks mu_0 = (1, A) and (1, B); row (0, s_0), endpoint (0, s_0)).
         if (warp == 0) {
             for (int s0 = 0; s0 < 2; ++s0) {
                 const uint32_t off = __ldg(tab.rank4 + 1 + s0);
-                to_elem(1.0, ring[(size_t)(1 & 1) * a.slot_elems + (size_t)(off + 3u * (uint32_t)s0) * kLanes + lane]);
+                to_elem((CLOW && lam != 0) ? 0.0 : 1.0,
+                        ring[(size_t)(1 & 1) * a.slot_elems + (size_t)(off + 3u * (uint32_t)s0) * kLanes + lane]);
             }
         }
         __syncthreads();
@@ -508,7 +522,7 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
             const uint32_t first = tab.layer_first[ell];
             const uint32_t cnt = tab.layer_count[ell];
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
-                bip_mask<T>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1,
+                bip_mask<T, CLOW>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1,
                             Ms, Md, lane, ci, nfl, seedsh, shifts, active, lam, cfg, a.out, a.status, a.prefetch);
             __syncthreads();
         }
@@ -530,6 +544,7 @@ struct BipLaunch {
     double *out = nullptr;
     bool absmode = false;
     int precision = COS_FP64;
+    bool clow = false;   // determinant weights without cycle factors (n_mat = 2 spin blocks)
 };
 
 static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t stream) {
@@ -555,7 +570,8 @@ static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t str
     cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "bipartite layer scratch");
     if (st != COS_OK) return st;
     const size_t smem = 2 * (size_t)4 * L.n_max * L.n_max * kLanes * sizeof(double);   // 8-byte elements
-    auto kern = L.precision == COS_DF64 ? dp_bip_kernel<df64> : dp_bip_kernel<double>;
+    auto kern = L.precision == COS_DF64 ? (L.clow ? dp_bip_kernel<df64, true> : dp_bip_kernel<df64, false>)
+                                        : (L.clow ? dp_bip_kernel<double, true> : dp_bip_kernel<double, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "bipartite smem attribute");
     BipArgs a;
@@ -620,8 +636,10 @@ static cos_status check_bip(int n_cfg, int n_max, const int32_t *d_order, const 
 
 cos_status bip_matrices_body(Workspace *ws, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
                              int n_mat, int loop_weight, const double *h_sigma2, const double *d_M4,
-                             cos_precision precision, double *d_out, double *d_abs_mass, cudaStream_t stream) {
+                             cos_precision precision, double *d_out, double *d_abs_mass, cudaStream_t stream,
+                             bool clow) {
     BipLaunch L;
+    L.clow = clow;
     L.precision = precision;
     L.n_cfg = n_cfg;
     L.n_max = n_max;
@@ -658,7 +676,24 @@ extern "C" cos_status cos_connected_sum_bipartite_matrices(int n_cfg, int n_max,
         return COS_ERR_CUDA;
     }
     return bip_matrices_body(ws, n_cfg, n_max, d_order, d_moff, n_mat, loop_weight, h_sigma2, d_M4, precision,
-                             d_out, d_abs_mass, (cudaStream_t)stream);
+                             d_out, d_abs_mass, (cudaStream_t)stream, false);
+}
+
+extern "C" cos_status cos_connected_det_bipartite_matrices(int n_cfg, int n_max, const int32_t *d_order,
+                                                           const int64_t *d_moff, const double *h_alpha2,
+                                                           const double *d_M4, cos_precision precision,
+                                                           double *d_out, double *d_abs_mass, cos_stream_t stream) {
+    cos_status st = check_bip(n_cfg, n_max, d_order, d_moff, 2, 1, d_M4, precision, d_out,
+                              "cos_connected_det_bipartite_matrices");
+    if (st != COS_OK || n_cfg == 0) return st;
+    std::string err;
+    Workspace *ws = get_workspace((cudaStream_t)stream, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    return bip_matrices_body(ws, n_cfg, n_max, d_order, d_moff, 2, 1, h_alpha2, d_M4, precision, d_out, d_abs_mass,
+                             (cudaStream_t)stream, true);
 }
 
 extern "C" cos_status cos_bipartite_structure(int n, cos_structure_info *info) {

@@ -29,6 +29,18 @@
 // close keeps the unshifted diagonal, vertex 0 keeps its start seed).  Every target slot has
 // a single writer, the ring needs two layer slots, and slots never need clearing between
 // batches (each one read in a batch is written earlier in that batch).
+//
+// Determinant weights without cycle factors (Results A, Alg. 1; CLOW instantiations).  For an
+// SU(2) model with the interaction n_up n_dn every vertex has a spin-up point (block 0) and a
+// spin-down point (block 1), and the matrix is block diagonal in spin.  Alg. 1 keeps only the
+// interaction mask, so a clow may visit one point twice; those nonphysical sequences cancel.
+// A point is (vertex, block), so the state ((u), (v), mu) of Alg. 1 is the merged state
+// (mu, h, v) in the lane of block b, and the sweep above applies with four changes: entering
+// an untouched vertex has weight 1 (no 2^(n-1)); the start is in block 0 only; the first loop
+// (head point 0 of block 0) never steps onto vertex 0; and its close opens the next loop at
+// the other point of vertex 0, i.e. in block 1 only.  Every other close opens at both points
+// of vertex k, one per block, which is the flavor-sum seed.  Diagonal shifts alpha_b of the
+// density (n_b - alpha_b) enter both matrix copies, the close's included.
 #include <algorithm>
 #include <cstring>
 #include <type_traits>
@@ -51,7 +63,8 @@ struct CloseOf<df64> {
 // 12 warps; FP32 two CTAs, <= 85 registers) and MAXT = 512 (up to 16 warps; <= 128 registers in
 // FP64 with one CTA, <= 64 in FP32 with two).
 // SUB: all-subsets mode (closes of masks with no half-visited vertex stored through csub_key).
-template <typename T, int MAXT, bool SUB>
+// CLOW: determinant weights without cycle factors (two spin-block lanes per configuration).
+template <typename T, int MAXT, bool SUB, bool CLOW = false>
 __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
     dp_forward_kernel(const __grid_constant__ DpArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -105,11 +118,18 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
             double val = active ? Mc[e] : 0.0;
             if (a.absmode) val = fabs(val);
             const int v = e / n, j = e % n;
-            to_elem((v == j && j != 0 && shifts) ? val + dshift : val, Ms[e * kLanes + lane]);
-            to_elem(cfac * val, Mdw[e * kLanes + lane]);
+            if (CLOW) {
+                const double m = (v == j) ? val + dshift : val;   // a(p, p) - alpha_b everywhere
+                to_elem(m, Ms[e * kLanes + lane]);
+                to_elem(cfac * m, Mdw[e * kLanes + lane]);
+            } else {
+                to_elem((v == j && j != 0 && shifts) ? val + dshift : val, Ms[e * kLanes + lane]);
+                to_elem(cfac * val, Mdw[e * kLanes + lane]);
+            }
         }
-        // Start: the loop through the normal point of vertex 0 (layer 1, mask e_0, slot 0).
-        if (warp == 0) to_elem(1.0, ring[(1 % a.nslots) * a.slot_elems + lane]);
+        // Start: the loop through the normal point of vertex 0 (layer 1, mask e_0, slot 0);
+        // determinant weights start at the spin-up point only.
+        if (warp == 0) to_elem((CLOW && lam != 0) ? 0.0 : 1.0, ring[(1 % a.nslots) * a.slot_elems + lane]);
         __syncthreads();
 
         for (int ell = 1; ell <= 2 * n; ++ell) {
@@ -120,11 +140,11 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
             for (uint32_t mi = warp; mi < cnt; mi += nwarps) {
                 const uint32_t next = mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu;
                 if constexpr (kDf)
-                    fwd_mask_df<SUB>(tab, first + mi, next, ell, n, src, dst1, Ms, Md, lane, ci, nfl, seed0, shifts,
-                                     active, lam, cfg, a.out, a.status, a.prefetch, cs, csh);
+                    fwd_mask_df<SUB, CLOW>(tab, first + mi, next, ell, n, src, dst1, Ms, Md, lane, ci, nfl, seed0,
+                                           shifts, active, lam, cfg, a.out, a.status, a.prefetch, cs, csh);
                 else
-                    fwd_mask<T, SUB>(tab, first + mi, next, ell, n, src, dst1, Ms, Md, lane, ci, nfl, sgn, sig, shifts,
-                                     active, lam, cfg, a.out, a.status, a.prefetch, cs, csh);
+                    fwd_mask<T, SUB, CLOW>(tab, first + mi, next, ell, n, src, dst1, Ms, Md, lane, ci, nfl, sgn, sig,
+                                           shifts, active, lam, cfg, a.out, a.status, a.prefetch, cs, csh);
             }
             __syncthreads();
         }
@@ -212,10 +232,17 @@ cos_status launch_plan_batches(Workspace *ws, int n_cfg, int n_max, const int32_
     return COS_OK;
 }
 
-template <typename T, bool SUB>
+template <typename T, bool SUB, bool CLOW = false>
 static auto forward_kernel_for(int threads) {
-    return threads <= 256 ? dp_forward_kernel<T, 256, SUB>
-                          : (threads <= 384 ? dp_forward_kernel<T, 384, SUB> : dp_forward_kernel<T, 512, SUB>);
+    return threads <= 256 ? dp_forward_kernel<T, 256, SUB, CLOW>
+                          : (threads <= 384 ? dp_forward_kernel<T, 384, SUB, CLOW>
+                                            : dp_forward_kernel<T, 512, SUB, CLOW>);
+}
+
+template <typename T>
+static auto kernel_for_launch(const DpLaunch &L, int threads) {
+    if (L.clow) return forward_kernel_for<T, false, true>(threads);
+    return L.csub ? forward_kernel_for<T, true>(threads) : forward_kernel_for<T, false>(threads);
 }
 
 template <typename T>
@@ -251,7 +278,7 @@ static cos_status launch_dp_t(Workspace *ws, const DpLaunch &L, cudaStream_t str
     const int threads = tu.warps * 32;
     const size_t msm = (size_t)L.n_max * L.n_max * kLanes;
     const size_t smem = ((msm * sizeof(T) + 15) & ~size_t(15)) + msm * sizeof(typename CloseOf<T>::type);
-    auto kern = L.csub ? forward_kernel_for<T, true>(threads) : forward_kernel_for<T, false>(threads);
+    auto kern = kernel_for_launch<T>(L, threads);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "dp smem attribute");
     DpArgs a;
@@ -314,7 +341,7 @@ static cos_status launch_dp_raw_t(const RawBuffers &rb, const DpLaunch &L, cudaS
     const size_t msm = (size_t)L.n_max * L.n_max * kLanes;
     const size_t smem = ((msm * sizeof(T) + 15) & ~size_t(15)) + msm * sizeof(typename CloseOf<T>::type);
     const int threads = tu.warps * 32;
-    auto kern = L.csub ? forward_kernel_for<T, true>(threads) : forward_kernel_for<T, false>(threads);
+    auto kern = kernel_for_launch<T>(L, threads);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "dp smem attribute");
     DpArgs a;
@@ -369,7 +396,7 @@ int dp_max_active_ctas(int precision, int threads, size_t smem) {
 }
 
 bool dp_uses_pair(const DpLaunch &L) {
-    return (L.precision == COS_MIXED || L.precision == COS_DF64) && L.csub == nullptr;
+    return (L.precision == COS_MIXED || L.precision == COS_DF64) && L.csub == nullptr && !L.clow;
 }
 
 int dp_configs_per_batch(const DpLaunch &L) {

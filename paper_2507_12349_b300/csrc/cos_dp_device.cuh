@@ -261,7 +261,10 @@ __device__ __forceinline__ void row_dispatch(int nv, const T *src, T *dst1, cons
 // Ms: extension matrices (shifted diagonal); Md: FP64 close matrices times sgn * w.
 // SUBSETS: also close the masks with no half-visited vertex and store c(S) (all-subsets mode);
 // `csub` is this lane's output base (valid on active lanes), `cshift` the root's bit offset.
-template <typename T, bool SUBSETS = false>
+// CLOW: determinant weights without cycle factors (Alg. 1, see cos_dp.cu): lanes are the two
+// spin blocks, the first loop never steps onto vertex 0, its close opens the next loop in the
+// spin-down block only, and the sink takes no 2^(n-1).
+template <typename T, bool SUBSETS = false, bool CLOW = false>
 __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
                                          int n, const T *src, T *dst1, const T *Ms, const double *Md, int lane,
                                          int ci, int nfl, double sgn, double sig, bool shifts, bool active, int lam,
@@ -272,7 +275,8 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
     const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, code = mk.y, off = mk.z;
     const uint32_t ones = A & ~B;
     const uint32_t H = head_set(B, ones);
-    const uint32_t J = full & ~B;
+    // (CLOW: while the first loop is open, vertex 0 holds its head point and is no target)
+    const uint32_t J = full & ~B & (CLOW ? ~(ones & 1u) : 0xFFFFFFFFu);
     const int nA = __popc(A);
     // Closes feed a new loop (a half-visited vertex remains) or the sink (all full).  With no
     // half-visited vertex and untouched ones left, the cover of S = {mu_i = 2} is complete and
@@ -312,12 +316,13 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
         const uint32_t off1 = __ldg(tab.rank3 + code + c_p3[k]);
         T *tp = dst1 + (size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane;
         double val = C;
-        if (ell == 1 && shifts) val += sgn * 2.0 * sig;  // vertex 0 carries a shift point
+        if (!CLOW && ell == 1 && shifts) val += sgn * 2.0 * sig;  // vertex 0 carries a shift point
         const T tv = narrow_to(T(0), val);
-        if (k == 0) *tp += tv;                            // the extension into 0' wrote it
+        if (CLOW) *tp = (k == 0 && lam == 0) ? T(0) : tv;        // k = 0: the head point is taken
+        else if (k == 0) *tp += tv;                                // the extension into 0' wrote it
         else *tp = tv;
     } else if (active && lam == 0 && out) {
-        const double c = ldexp(C, n - 1);
+        const double c = CLOW ? C : ldexp(C, n - 1);
         out[cfg] = c;
         if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
     }
@@ -425,7 +430,7 @@ __device__ __forceinline__ void row_dispatch_df(int nv, const df64 *src, df64 *d
 
 // One interaction mask of the df64 forward sweep (twin of fwd_mask).  seed0 = sgn 2 sigma as
 // df64 (the shifted start at vertex 0, added at layer 1 when shifts are on).
-template <bool SUBSETS = false>
+template <bool SUBSETS = false, bool CLOW = false>
 __device__ __forceinline__ void fwd_mask_df(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
                                             int n, const df64 *src, df64 *dst1, const df64 *Ms, const df64 *Md,
                                             int lane, int ci, int nfl, df64 seed0, bool shifts, bool active, int lam,
@@ -436,7 +441,7 @@ __device__ __forceinline__ void fwd_mask_df(const OrderTab &tab, uint32_t mask_i
     const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, code = mk.y, off = mk.z;
     const uint32_t ones = A & ~B;
     const uint32_t H = head_set(B, ones);
-    const uint32_t J = full & ~B;
+    const uint32_t J = full & ~B & (CLOW ? ~(ones & 1u) : 0xFFFFFFFFu);
     const int nA = __popc(A);
     const bool dead = (ones == 0u) && (B != full);
     const bool needclose = !dead || SUBSETS;
@@ -471,11 +476,12 @@ __device__ __forceinline__ void fwd_mask_df(const OrderTab &tab, uint32_t mask_i
         const uint32_t off1 = __ldg(tab.rank3 + code + c_p3[k]);
         df64 *tp = dst1 + (size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane;
         df64 val = C;
-        if (ell == 1 && shifts) val = df64_add(val, seed0);   // vertex 0 carries a shift point
-        if (k == 0) *tp = df64_add(*tp, val);                // the extension into 0' wrote it
+        if (!CLOW && ell == 1 && shifts) val = df64_add(val, seed0);   // vertex 0 carries a shift point
+        if (CLOW) *tp = (k == 0 && lam == 0) ? df64{0.0f, 0.0f} : val;
+        else if (k == 0) *tp = df64_add(*tp, val);                    // the extension into 0' wrote it
         else *tp = val;
     } else if (active && lam == 0 && out) {
-        const double c = ldexp(df64_to_double(C), n - 1);
+        const double c = CLOW ? df64_to_double(C) : ldexp(df64_to_double(C), n - 1);
         out[cfg] = c;
         if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
     }

@@ -160,6 +160,7 @@ struct DpLaunch {
     double *csub = nullptr;         // all-subsets mode: c(S) written at csub[base + (S << shift)]
     const int64_t *csub_key = nullptr;  // per configuration: (base << 4) | shift
     bool allow_empty = false;       // order 0 = empty configuration slot (skipped by the planner)
+    bool clow = false;              // determinant weights without cycle factors (two spin blocks)
 };
 
 cos_status launch_plan_batches(Workspace *ws, int n_cfg, int n_max, const int32_t *order, int cpb,
@@ -218,7 +219,8 @@ int dp_max_active_ctas(int precision, int threads, size_t smem);
 
 cos_status bip_matrices_body(Workspace *ws, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
                              int n_mat, int loop_weight, const double *h_sigma2, const double *d_M4,
-                             cos_precision precision, double *d_out, double *d_abs_mass, cudaStream_t stream);
+                             cos_precision precision, double *d_out, double *d_abs_mass, cudaStream_t stream,
+                             bool clow = false);
 
 cos_status launch_gather(const cos_tables *t, int n_cfg, const int32_t *order, const int64_t *offset,
                          const int32_t *site, const double *tau, const int64_t *moff, int64_t mstride,

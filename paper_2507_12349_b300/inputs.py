@@ -128,6 +128,7 @@ class Workload:
     seed: int
     precision: str  # "fp64" or "mixed"
     grad: bool = False
+    det: bool = False   # SU(2) determinant weights (spin blocks up, down; no cycle factors)
 
 
 WORKLOADS = {
@@ -151,6 +152,11 @@ WORKLOADS = {
     "hc_su2_af_n8": Workload("hc_su2_af_n8",
                              HoneycombModel(16, 1.0, 6.0, 3.0, (0.0, 0.0), (0.0, 0.0), (0.25, -0.25), 1024),
                              8, 8, 20_000, 5, "fp64"),
+    # SU(2) on the square lattice with determinant weights n_up n_dn and a Zeeman split of the
+    # chemical potential (spin-dependent mu, so the two spin blocks differ), order 10.
+    "su2_zeeman_det_n10": Workload("su2_zeeman_det_n10",
+                                   Model(16, 1.0, 4.0, 2.0, (-0.2, 0.2), (0.0, 0.0), 1024),
+                                   10, 10, 20_000, 6, "fp64", det=True),
 }
 
 

@@ -55,6 +55,14 @@ def test_argument_errors_are_synchronous():
     rc = lib.cos_connected_sum_subsets(1, 4, fake, fake, 1, 1, None, fake, 0, 2, fake, None, None)
     assert rc == -1
     assert lib.cos_connected_sum_subsets(0, 4, None, None, 1, 1, None, None, 0, 1, None, None, None) == 0
+    # SU(2) determinant weights: square orders up to 12, bipartite up to 9 and FP64 / df64 only
+    assert lib.cos_connected_det_matrices(1, 13, None, None, None, None, 0, None, None, None) == -2
+    assert lib.cos_connected_det_matrices(1, 4, None, None, None, None, 0, None, None, None) == -1
+    assert lib.cos_connected_det_matrices(1, 4, fake, fake, None, fake, 9, fake, None, None) == -1
+    assert lib.cos_connected_det_matrices(0, 4, None, None, None, None, 0, None, None, None) == 0
+    assert lib.cos_connected_det_bipartite_matrices(1, 10, fake, fake, None, fake, 0, fake, None, None) == -2
+    assert lib.cos_connected_det_bipartite_matrices(1, 4, fake, fake, None, fake, 1, fake, None, None) == -6
+    assert lib.cos_connected_det_bipartite_matrices(1, 4, None, None, None, None, 0, None, None, None) == -1
     assert lib.cos_status_string(-2) == b"order out of range"
     inf = B.cos_structure_info()
     assert lib.cos_structure(0, ctypes.byref(inf)) == -2

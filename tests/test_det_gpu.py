@@ -1,0 +1,239 @@
+"""GPU parity of the SU(2) determinant-weight path (the DP without cycle factors, Alg. 1)
+against the oracle.
+
+The oracle value is `oracle.det_clow` (Alg. 1 as stated, point-resolved, long double),
+itself pinned against LU determinants with the subset subtraction, brute force and the CoS
+relation in test_oracle_det_pins.  Tolerances are the square-lattice ones of
+test_parity_gpu, stated against the DP's mass (the same DP on |M| with |alpha| added to the
+diagonal and every sign +): FP64 64 n 2^-53 mass, mixed (2n + log2(32 n)) 2^-24 mass,
+double-float (16 n^2 + 64 n) 2^-48 mass.  Orders the oracle cannot reach in seconds (11, 12
+on the square lattice, 9 on the bipartite one) use the CoS relation on the GPU: with two
+flavors, loop weight 1 and no shifts the CoS sum of the same matrices is 2^n times this one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from oracle import honeycomb as HC
+from oracle import propagators as P
+from paper_2507_12349_b300 import binding as B
+from paper_2507_12349_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+EPS64 = 2.0 ** -53
+EPS32 = 2.0 ** -24
+
+
+def bound(prec, n, mass):
+    if prec == "fp64":
+        return 64 * n * EPS64 * mass
+    if prec == "mixed":
+        return (2 * n + math.log2(32 * n)) * EPS32 * mass
+    return (16 * n * n + 64 * n) * 2.0 ** -48 * mass
+
+
+def run_square(Ms, alpha=None, precision="fp64", abs_mass=True):
+    order = np.array([m.shape[-1] for m in Ms], dtype=np.int32)
+    moff = B.matrix_offsets(order, 2)
+    flat = np.concatenate([np.asarray(m, dtype=np.float64).ravel() for m in Ms])
+    d_order = torch.tensor(order, device="cuda")
+    d_moff = torch.tensor(moff, device="cuda")
+    d_M = torch.tensor(flat, device="cuda")
+    out = torch.full((len(Ms),), float("nan"), dtype=torch.float64, device="cuda")
+    mass = torch.full_like(out, float("nan")) if abs_mass else None
+    B.cos_connected_det_matrices(int(order.max()), d_order, d_moff, alpha, d_M, precision, out, mass)
+    B.cos_sync_status()
+    return out.cpu().numpy(), (mass.cpu().numpy() if abs_mass else None)
+
+
+def run_cos_square(Ms):
+    """The CoS sum of the same two matrices (two flavors, loop weight 1, no shifts)."""
+    order = np.array([m.shape[-1] for m in Ms], dtype=np.int32)
+    d_order = torch.tensor(order, device="cuda")
+    d_moff = torch.tensor(B.matrix_offsets(order, 2), device="cuda")
+    d_M = torch.tensor(np.concatenate([m.ravel() for m in Ms]), device="cuda")
+    out = torch.full((len(Ms),), float("nan"), dtype=torch.float64, device="cuda")
+    mass = torch.full_like(out, float("nan"))
+    B.cos_connected_sum_matrices(int(order.max()), d_order, d_moff, 2, 1, None, d_M, "fp64", out, mass)
+    B.cos_sync_status()
+    return out.cpu().numpy(), mass.cpu().numpy()
+
+
+def run_bip(M4s, alpha2=None, precision="fp64", abs_mass=True, cos=False):
+    order = np.array([m.shape[1] for m in M4s], dtype=np.int32)
+    moff = B.bipartite_matrix_offsets(order, 2)
+    d_order = torch.tensor(order, device="cuda")
+    d_moff = torch.tensor(moff, device="cuda")
+    d_M = torch.tensor(np.concatenate([m.ravel() for m in M4s]), device="cuda")
+    out = torch.full((len(M4s),), float("nan"), dtype=torch.float64, device="cuda")
+    mass = torch.full_like(out, float("nan")) if abs_mass else None
+    if cos:
+        B.cos_connected_sum_bipartite_matrices(int(order.max()), d_order, d_moff, 2, 1, None, d_M, precision, out,
+                                               mass)
+    else:
+        B.cos_connected_det_bipartite_matrices(int(order.max()), d_order, d_moff, alpha2, d_M, precision, out, mass)
+    B.cos_sync_status()
+    return out.cpu().numpy(), (mass.cpu().numpy() if abs_mass else None)
+
+
+def rand_sq(seed, ncfg, n, scale=0.9):
+    return list(I.random_matrices(seed, ncfg, 2, n, scale))
+
+
+def rand_m4(seed, ncfg, n, scale=0.9):
+    M = I.random_matrices(seed, ncfg, 2, 2 * n, scale)
+    return [np.ascontiguousarray(m.reshape(2, n, 2, n, 2)) for m in M]
+
+
+SQUARE = [  # n, configurations, shifts
+    (1, 5, True), (2, 9, False), (3, 17, True), (4, 33, False), (5, 12, True), (6, 7, True), (7, 20, False),
+    (8, 6, True), (9, 3, False), (10, 3, True),
+]
+
+
+@pytest.mark.parametrize("n,ncfg,shifts", SQUARE)
+@pytest.mark.parametrize("prec", ["fp64", "df64", "mixed"])
+def test_square_matches_oracle(n, ncfg, shifts, prec):
+    if prec != "fp64" and n > 8:
+        pytest.skip("reduced precisions are checked up to n = 8 here and at n = 10 on the workload")
+    Ms = rand_sq(2000 + 10 * n, ncfg, n)
+    al = [0.13, -0.08] if shifts else None
+    got, mass = run_square(Ms, al, prec)
+    for c in sorted({0, ncfg // 2, ncfg - 1}):
+        ref = O.det_clow(Ms[c], al, prec="ld")
+        rmass = O.det_clow(Ms[c], al, absmode=True)
+        assert abs(got[c] - ref) <= bound(prec, n, rmass), (c, got[c], ref, rmass)
+        assert mass[c] == pytest.approx(rmass, rel=1e-12 if prec == "fp64" else 1e-6)
+
+
+def test_square_uneven_orders_and_cos_relation():
+    """Orders 1..12 in one launch; up to 10 against the oracle, 11 and 12 against the CoS
+    kernel on the same matrices (c_CoS = 2^n c)."""
+    orders = [12, 3, 11, 1, 7, 10, 2, 12, 5, 9, 4, 6, 8, 11]
+    Ms = [rand_sq(3000 + c, 1, n)[0] for c, n in enumerate(orders)]
+    got, mass = run_square(Ms)
+    cos, cmass = run_cos_square(Ms)
+    for c, n in enumerate(orders):
+        if n <= 8:
+            ref = O.det_clow(Ms[c], prec="ld")
+            rmass = O.det_clow(Ms[c], absmode=True)
+            assert abs(got[c] - ref) <= bound("fp64", n, rmass), (c, n, got[c], ref)
+        # the two GPU paths agree through the CoS relation at every order
+        tol = bound("fp64", n, mass[c]) + bound("fp64", n, cmass[c]) / 2.0 ** n
+        assert abs(got[c] - cos[c] / 2.0 ** n) <= tol, (c, n, got[c], cos[c] / 2.0 ** n)
+
+
+def test_square_deterministic():
+    Ms = rand_sq(44, 50, 7)
+    a, _ = run_square(Ms, [0.1, 0.2], abs_mass=False)
+    b, _ = run_square(Ms, [0.1, 0.2], abs_mass=False)
+    assert np.array_equal(a, b)
+
+
+BIP = [  # n, configurations, shifts
+    (1, 5, True), (2, 9, False), (3, 17, True), (4, 12, False), (5, 7, True), (6, 5, False), (7, 3, True),
+    (8, 2, True),
+]
+
+
+@pytest.mark.parametrize("n,ncfg,shifts", BIP)
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_bipartite_matches_oracle(n, ncfg, shifts, prec):
+    M4s = rand_m4(5000 + 10 * n, ncfg, n)
+    al = [[0.11, -0.05], [-0.07, 0.09]] if shifts else None
+    got, mass = run_bip(M4s, al, prec)
+    for c in sorted({0, ncfg // 2, ncfg - 1}):
+        ref = O.det_clow(M4s[c], al, prec="ld")
+        rmass = O.det_clow(M4s[c], al, absmode=True)
+        assert abs(got[c] - ref) <= bound(prec, n, rmass), (c, got[c], ref, rmass)
+        assert mass[c] == pytest.approx(rmass, rel=1e-12 if prec == "fp64" else 1e-9)
+
+
+def test_bipartite_uneven_and_order9_cos_relation():
+    orders = [9, 2, 6, 1, 9, 4, 8, 3, 5, 7]
+    M4s = [rand_m4(6000 + c, 1, n)[0] for c, n in enumerate(orders)]
+    got, mass = run_bip(M4s)
+    cos, cmass = run_bip(M4s, cos=True)
+    for c, n in enumerate(orders):
+        if n <= 6:
+            ref = O.det_clow(M4s[c], prec="ld")
+            rmass = O.det_clow(M4s[c], absmode=True)
+            assert abs(got[c] - ref) <= bound("fp64", n, rmass), (c, n, got[c], ref)
+        tol = bound("fp64", n, mass[c]) + bound("fp64", n, cmass[c]) / 2.0 ** n
+        assert abs(got[c] - cos[c] / 2.0 ** n) <= tol, (c, n, got[c], cos[c] / 2.0 ** n)
+
+
+def test_bipartite_deterministic():
+    M4s = rand_m4(55, 40, 5)
+    a, _ = run_bip(M4s, [[0.1, 0.0], [0.0, -0.1]], abs_mass=False)
+    b, _ = run_bip(M4s, [[0.1, 0.0], [0.0, -0.1]], abs_mass=False)
+    assert np.array_equal(a, b)
+
+
+def test_bipartite_rejects_mixed():
+    M4s = rand_m4(1, 1, 2)
+    with pytest.raises(B.CosError) as e:
+        run_bip(M4s, None, "mixed")
+    assert e.value.status == -6
+
+
+@pytest.mark.parametrize("prec,sample", [("fp64", 6), ("df64", 4), ("mixed", 4)])
+def test_workload_su2_zeeman_order10_sampled(prec, sample):
+    """The order-10 SU(2) workload at full size (20 000 configurations, the launch the
+    benchmark times): gather with the two-flavor tables, DP on the GPU, sampled
+    configurations against the oracle's gather and Alg. 1."""
+    w = I.WORKLOADS["su2_zeeman_det_n10"]
+    cfgs = I.workload_configs(w)
+    n_cfg = cfgs.n_cfg
+    tabs = B.tables_for(w.model)
+    d = B.configs_to_device(cfgs)
+    moff = B.matrix_offsets(cfgs.order, 2)
+    d_moff = torch.tensor(moff, device="cuda")
+    M = torch.empty(int(moff[-1]) + 2 * 100, dtype=torch.float64, device="cuda")
+    B.cos_gather(tabs, *d, d_moff, M)
+    out = torch.full((n_cfg,), float("nan"), dtype=torch.float64, device="cuda")
+    mass = torch.full_like(out, float("nan"))
+    B.cos_connected_det_matrices(10, d[0], d_moff, None, M, prec, out, mass)
+    B.cos_sync_status()
+    got, gmass = out.cpu().numpy(), mass.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    otabs = P.model_tables(w.model)
+    idx = sorted(set(np.linspace(0, n_cfg - 1, sample).astype(int)))
+    for c, Mc in zip(idx, P.gather(otabs, cfgs, w.model.L, w.model.beta, idx)):
+        ref = O.det_clow(Mc, prec="ld")
+        rmass = O.det_clow(Mc, absmode=True)
+        assert abs(got[c] - ref) <= bound(prec, 10, rmass), (c, got[c], ref, rmass)
+        if prec == "fp64":
+            assert gmass[c] == pytest.approx(rmass, rel=1e-10)
+    tabs.close()
+
+
+def test_honeycomb_det_sampled():
+    """Honeycomb SU(2) tables (the order-8 workload's model), gathered on the GPU, with the
+    staggered shifts as diagonal shifts of the determinant weights."""
+    w = I.WORKLOADS["hc_su2_af_n8"]
+    cfgs = I.workload_configs(w, 64)
+    tabs = B.honeycomb_tables_for(w.model)
+    d = B.configs_to_device(cfgs)
+    moff = B.bipartite_matrix_offsets(cfgs.order, 2)
+    d_moff = torch.tensor(moff, device="cuda")
+    M4 = torch.empty(int(moff[-1]) + 2 * 16 * 16, dtype=torch.float64, device="cuda")
+    B.cos_gather_bipartite(tabs, *d, d_moff, M4)
+    al = [list(r) for r in w.model.sigma2]
+    out = torch.full((64,), float("nan"), dtype=torch.float64, device="cuda")
+    B.cos_connected_det_bipartite_matrices(8, d[0], d_moff, al, M4, "fp64", out)
+    B.cos_sync_status()
+    got = out.cpu().numpy()
+    otabs = HC.hc_model_tables(w.model)
+    for c in (0, 63):
+        o = int(cfgs.offset[c])
+        M4c = HC.hc_gather_one(otabs, cfgs.site[o:o + 8], cfgs.tau[o:o + 8], w.model.L, w.model.beta)
+        ref = O.det_clow(M4c, al, prec="ld")
+        rmass = O.det_clow(M4c, al, absmode=True)
+        assert abs(got[c] - ref) <= bound("fp64", 8, rmass), (c, got[c], ref, rmass)
+    tabs.close()
