@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -60,7 +61,10 @@ def parse():
                    help="profiling runs only: time the gradient call (adjoint DP) instead of the forward")
     p.add_argument("--bipartite", action="store_true",
                    help="profiling runs only: time the honeycomb workload's bipartite step (gather + DP)")
-    p.add_argument("--order", type=int, default=0, help="with --bipartite: order of the configurations")
+    p.add_argument("--det", action="store_true",
+                   help="profiling runs only: time the SU(2) determinant-weight step (gather + DP, Alg. 1) "
+                        "of the order-10 Zeeman workload")
+    p.add_argument("--order", type=int, default=0, help="with --bipartite or --det: order of the configurations")
     return p.parse_args()
 
 
@@ -86,6 +90,15 @@ def oracle_values(w, cfgs, absmode=False):
     Ms = np.stack(P.gather(tabs, cfgs, model.L, model.beta))
     hi, lo, threads = O.dp_batch(Ms, sig, wt, absmode=absmode, nthreads=0)
     return hi + lo, threads
+
+
+def det_oracle_values(w, cfgs, absmode=False):
+    """Oracle SU(2) determinant-weight sums (numpy gather + the C DP of Alg. 1 in double) of
+    `cfgs`, one configuration at a time."""
+    import oracle as O
+    from oracle import propagators as P
+    tabs = P.model_tables(w.model)
+    return np.array([O.det_clow(M, absmode=absmode) for M in P.gather(tabs, cfgs, w.model.L, w.model.beta)])
 
 
 def cpu_oracle_rate(w, budget_s: float, n_limit: int | None = None):
@@ -397,6 +410,11 @@ def oracle_leg(w, budget, head_out, keep):
     acc = {"su4_n8_fp64_vs_oracle": error_stats(head_out[:n], vals, mass)}
     for name, (wname, got) in keep.items():
         wk = I.WORKLOADS[wname]
+        if wk.det:
+            k = min(len(got), 8)
+            cfgs = I.workload_configs(wk, k)
+            acc[name] = error_stats(got[:k], det_oracle_values(wk, cfgs), det_oracle_values(wk, cfgs, True))
+            continue
         k = min(len(got), 160)
         cfgs = I.workload_configs(wk, k)
         ref, _ = oracle_values(wk, cfgs)
@@ -479,6 +497,82 @@ def measure_bipartite(torch, B, flush_buf, n_cfg, precision="fp64"):
     tabs.close()
     return {"configs": n_cfg, "configs_per_s": n_cfg / t, "tflops": fl / t / 1e12, "ms": t * 1e3,
             "assignments_per_config": 256}
+
+
+def det_fma(B, n: int) -> int:
+    """Multiply-adds of one spin block of the determinant-weight DP at order n: those of the
+    merged structure minus the first loop's step onto vertex 0, which Alg. 1 does not take
+    (one per endpoint state of every mask with vertex 0 half-visited: k other visited
+    vertices give max(k, 1) endpoints, and C(n-1, k) 2^k masks have k)."""
+    s = B.cos_structure(n)
+    saved = sum(math.comb(n - 1, k) * 2 ** k * max(k, 1) for k in range(n))
+    return s.fma_ext - saved + s.fma_close
+
+
+def measure_det(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
+    """SU(2) determinant weights by the DP without cycle factors (Alg. 1): the order-10 square
+    workload with a Zeeman-split chemical potential (gather + DP on the same matrices in
+    FP64, double-float and mixed precision, against the CoS DP of the same two matrices, which
+    returns 2^n times the same sum), and the honeycomb order-8 workload's matrices (bipartite,
+    against the CoS bipartite DP).  Returns the forms and the FP64 output for the accuracy."""
+    res = {}
+    w = I.WORKLOADS["su2_zeeman_det_n10"]
+    n_cfg, n = w.n_cfg, 10
+    cfgs = I.workload_configs(w)
+    tabs = B.tables_for(w.model)
+    d = B.configs_to_device(cfgs)
+    moff = torch.as_tensor(B.matrix_offsets(cfgs.order, 2), device="cuda")
+    M = torch.empty(n_cfg * 2 * n * n, dtype=torch.float64, device="cuda")
+    B.cos_gather(tabs, *d, moff, M)
+    outs = {p: torch.empty(n_cfg, dtype=torch.float64, device="cuda") for p in ("fp64", "df64", "mixed", "cos")}
+    fns = {p: (lambda p=p: B.cos_connected_det_matrices(n, d[0], moff, None, M, p, outs[p]))
+           for p in ("fp64", "df64", "mixed")}
+    fns["cos"] = lambda: B.cos_connected_sum_matrices(n, d[0], moff, 2, 1, None, M, "fp64", outs["cos"])
+    for f in fns.values():
+        f()
+    B.cos_sync_status()
+    ts = {p: statistics.mean(time_steps(torch, f, 2, lambda: flush_l2(flush_buf))) for p, f in fns.items()}
+    B.cos_sync_status()
+    fl = n_cfg * 2 * 2.0 * det_fma(B, n)
+    for p in ("fp64", "df64", "mixed"):
+        r = {"configs": n_cfg, "configs_per_s": n_cfg / ts[p], "ms": ts[p] * 1e3,
+             "cost_vs_cos_fp64": ts[p] / ts["cos"]}
+        if p == "fp64":
+            r["tflops"] = fl / ts[p] / 1e12
+            r["frac_fp64_peak"] = fl / ts[p] / fp64_peak
+        elif p == "df64":
+            r["frac_fp32_floor"] = fl / 2.0 * DF64_FP32_PER_TERM / ts[p] / fp32_lane_ops
+        else:
+            s = B.cos_structure(n)
+            r["frac_fp64_peak_close"] = n_cfg * 2 * 2.0 * s.fma_close / ts[p] / fp64_peak
+        res[f"su2_zeeman_n10_det_{p}"] = r
+    got = outs["fp64"].cpu().numpy()
+    cos = outs["cos"].cpu().numpy()
+    res["su2_zeeman_n10_det_fp64"]["max_rel_diff_vs_cos_over_2n"] = float(np.max(np.abs(got - cos / 2.0 ** n) / np.abs(got)))
+    tabs.close()
+    # bipartite: the honeycomb workload's gathered matrices, det vs CoS bipartite sweep
+    hw = I.WORKLOADS["hc_su2_af_n8"]
+    hc = I.workload_configs(hw)
+    htabs = B.honeycomb_tables_for(hw.model)
+    hd = B.configs_to_device(hc)
+    hmoff = torch.as_tensor(B.bipartite_matrix_offsets(hc.order, 2), device="cuda")
+    M4 = torch.empty(hc.n_cfg * 2 * 16 * 16, dtype=torch.float64, device="cuda")
+    B.cos_gather_bipartite(htabs, *hd, hmoff, M4)
+    hout = torch.empty(hc.n_cfg, dtype=torch.float64, device="cuda")
+    al = [list(r) for r in hw.model.sigma2]
+    hfns = {"det_fp64": lambda: B.cos_connected_det_bipartite_matrices(8, hd[0], hmoff, al, M4, "fp64", hout),
+            "det_df64": lambda: B.cos_connected_det_bipartite_matrices(8, hd[0], hmoff, al, M4, "df64", hout),
+            "cos_fp64": lambda: B.cos_connected_sum_bipartite_matrices(8, hd[0], hmoff, 2, 1, None, M4, "fp64", hout)}
+    for f in hfns.values():
+        f()
+    B.cos_sync_status()
+    ht = {k: statistics.mean(time_steps(torch, f, 2, lambda: flush_l2(flush_buf))) for k, f in hfns.items()}
+    B.cos_sync_status()
+    htabs.close()
+    for k in ("det_fp64", "det_df64"):
+        res[f"hc_su2_af_n8_{k}"] = {"configs": hc.n_cfg, "configs_per_s": hc.n_cfg / ht[k], "ms": ht[k] * 1e3,
+                                    "cost_vs_cos_fp64": ht[k] / ht["cos_fp64"]}
+    return res, got
 
 
 # FP32 instructions a double-float term needs at least (the Dot2 step: 1 multiply, 3 FMA,
@@ -567,6 +661,9 @@ def measure_forms(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
     hd = measure_bipartite(torch, B, flush_buf, I.WORKLOADS["hc_su2_af_n8"].n_cfg, "df64")
     hd["frac_fp32_floor"] = hd["tflops"] * 1e12 / 2.0 * DF64_FP32_PER_TERM / fp32_lane_ops
     res["hc_su2_af_n8_bipartite_df64"] = hd
+    det, det_out = measure_det(torch, B, flush_buf, fp64_peak, fp32_lane_ops)
+    res.update(det)
+    keep["su2_zeeman_n10_det_fp64_vs_oracle"] = ("su2_zeeman_det_n10", det_out)
     # plain FP64 per-configuration form: one configuration per call, no graph
     w = I.WORKLOADS[WORKLOAD]
     cfgs = I.workload_configs(w, 200)
@@ -624,12 +721,49 @@ def bipartite_arm(args):
     tabs.close()
 
 
+def det_arm(args):
+    """Profiling runs of the determinant-weight path alone: the SU(2) Zeeman workload's gather
+    + DP without cycle factors, at its order or --order, --n-cfg configurations."""
+    import torch
+    from paper_2507_12349_b300 import binding as B
+    B.lib()
+    w = I.WORKLOADS["su2_zeeman_det_n10"]
+    n = args.order if args.order > 0 else w.n_lo
+    n_cfg = args.n_cfg if args.n_cfg > 0 else w.n_cfg
+    cfgs = I.make_configs(w.model, n, n, n_cfg, w.seed)
+    tabs = B.tables_for(w.model)
+    d = B.configs_to_device(cfgs)
+    moff = torch.as_tensor(B.matrix_offsets(cfgs.order, 2), device="cuda")
+    M = torch.empty(n_cfg * 2 * n * n, dtype=torch.float64, device="cuda")
+    out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
+    flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def fn():
+        B.cos_gather(tabs, *d, moff, M)
+        B.cos_connected_det_matrices(n, d[0], moff, None, M, args.precision, out)
+    for _ in range(max(1, args.warmup)):
+        fn()
+    B.cos_sync_status()
+    ts = time_steps(torch, fn, args.steps, lambda: flush_l2(flush_buf))
+    B.cos_sync_status()
+    t = statistics.mean(ts)
+    fl = n_cfg * 2 * 2.0 * det_fma(B, n)
+    print(json.dumps({"metric": "SU(2) determinant-weight connected-sum configs/s (Alg. 1)",
+                      "value": n_cfg / t, "unit": "configs/s", "order": n, "configs": n_cfg,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+                      "tflops": fl / t / 1e12, "dtype": {"fp64": "f64", "df64": "f32 pairs (df64)"}.get(
+                          args.precision, args.precision)}), flush=True)
+    tabs.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
     elif args.bipartite:
         bipartite_arm(args)
+    elif args.det:
+        det_arm(args)
     else:
         native_arm(args)
 

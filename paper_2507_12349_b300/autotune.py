@@ -1,8 +1,10 @@
 """Write the launch-shape tuning cache (tuning_b300.txt) for the benchmark workloads.
 
-Usage (on the GPU): python -m paper_2507_12349_b300.autotune [--out FILE]
+Usage (on the GPU): python -m paper_2507_12349_b300.autotune [--out FILE] [--n-mat K]
 Runs cos_autotune for every (order, precision, matrices per configuration) that the
 workloads launch with and writes one line per case: "n precision n_mat warps ctas ms prefetch".
+With --n-mat K only the cases with K matrices per configuration are re-tuned and merged into
+the existing file (other lines kept).
 The sample size fills the GPU: a batch per CTA for 2 CTAs per SM (one CTA per SM at orders
 11-12, where one batch already holds ~0.3-0.6 s of FP64 work).
 """
@@ -23,6 +25,8 @@ CASES = [
     (10, 3, 1, True, "mixed"), (10, 3, 1, True, "fp64"),
     (10, 4, 1, False, "fp64"),
     (8, 4, 1, False, "df64"), (10, 3, 1, True, "df64"),
+    # SU(2) with two spin blocks (determinant weights, or CoS with two flavors)
+    (10, 2, 1, False, "fp64"), (10, 2, 1, False, "mixed"), (10, 2, 1, False, "df64"),
 ] + [(n, 1, 6, False, "fp64") for n in range(4, 13)]
 
 
@@ -31,6 +35,7 @@ def main():
     from paper_2507_12349_b300 import binding as B
     p = argparse.ArgumentParser()
     p.add_argument("--out", default=B.TUNING_FILE)
+    p.add_argument("--n-mat", type=int, default=0, help="re-tune only these cases and merge")
     args = p.parse_args()
     torch.cuda.set_device(0)
     B.lib()
@@ -40,12 +45,18 @@ def main():
     # two, FP64: one), so that the sample fills every SM with batches
     per_lane = {"fp64": 1, "mixed": 4, "df64": 2}
     for n, n_mat, wt, shifts, prec in CASES:
+        if args.n_mat and n_mat != args.n_mat:
+            continue
         cpb = (32 // n_mat) * per_lane[prec]
         n_cfg = cpb * sms * (1 if n >= 11 else 2)
         w, c, pf, ms = B.cos_autotune(n, n_mat, wt, shifts, prec, n_cfg)
         line = f"{n} {B.PRECISIONS[prec]} {n_mat} {w} {c} {ms:.4f} {int(pf)}"
         print(line, f"# {prec} configs={n_cfg}", flush=True)
         lines.append(line)
+    if args.n_mat and os.path.exists(args.out):
+        fresh = {tuple(ln.split()[:3]) for ln in lines}
+        kept = [ln.strip() for ln in open(args.out) if ln.strip() and tuple(ln.split()[:3]) not in fresh]
+        lines = kept + lines
     with open(args.out, "w") as f:
         f.write("\n".join(lines) + "\n")
 

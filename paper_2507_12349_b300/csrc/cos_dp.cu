@@ -140,8 +140,8 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
             for (uint32_t mi = warp; mi < cnt; mi += nwarps) {
                 const uint32_t next = mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu;
                 if constexpr (kDf)
-                    fwd_mask_df<SUB, CLOW>(tab, first + mi, next, ell, n, src, dst1, Ms, Md, lane, ci, nfl, seed0,
-                                           shifts, active, lam, cfg, a.out, a.status, a.prefetch, cs, csh);
+                    fwd_mask_df<SUB>(tab, first + mi, next, ell, n, src, dst1, Ms, Md, lane, ci, nfl, seed0, shifts,
+                                     active, lam, cfg, a.out, a.status, a.prefetch, cs, csh);
                 else
                     fwd_mask<T, SUB, CLOW>(tab, first + mi, next, ell, n, src, dst1, Ms, Md, lane, ci, nfl, sgn, sig,
                                            shifts, active, lam, cfg, a.out, a.status, a.prefetch, cs, csh);
@@ -239,9 +239,13 @@ static auto forward_kernel_for(int threads) {
                                             : dp_forward_kernel<T, 512, SUB, CLOW>);
 }
 
+// Determinant weights (L.clow) reach this launcher in FP64 only: the reduced precisions run
+// the pair kernels (cos_dp_pair.cu).
 template <typename T>
 static auto kernel_for_launch(const DpLaunch &L, int threads) {
-    if (L.clow) return forward_kernel_for<T, false, true>(threads);
+    if constexpr (std::is_same<T, double>::value) {
+        if (L.clow) return forward_kernel_for<T, false, true>(threads);
+    }
     return L.csub ? forward_kernel_for<T, true>(threads) : forward_kernel_for<T, false>(threads);
 }
 
@@ -396,7 +400,7 @@ int dp_max_active_ctas(int precision, int threads, size_t smem) {
 }
 
 bool dp_uses_pair(const DpLaunch &L) {
-    return (L.precision == COS_MIXED || L.precision == COS_DF64) && L.csub == nullptr && !L.clow;
+    return (L.precision == COS_MIXED || L.precision == COS_DF64) && L.csub == nullptr;
 }
 
 int dp_configs_per_batch(const DpLaunch &L) {

@@ -430,7 +430,7 @@ __device__ __forceinline__ void row_dispatch_df(int nv, const df64 *src, df64 *d
 
 // One interaction mask of the df64 forward sweep (twin of fwd_mask).  seed0 = sgn 2 sigma as
 // df64 (the shifted start at vertex 0, added at layer 1 when shifts are on).
-template <bool SUBSETS = false, bool CLOW = false>
+template <bool SUBSETS = false>
 __device__ __forceinline__ void fwd_mask_df(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
                                             int n, const df64 *src, df64 *dst1, const df64 *Ms, const df64 *Md,
                                             int lane, int ci, int nfl, df64 seed0, bool shifts, bool active, int lam,
@@ -441,7 +441,7 @@ __device__ __forceinline__ void fwd_mask_df(const OrderTab &tab, uint32_t mask_i
     const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, code = mk.y, off = mk.z;
     const uint32_t ones = A & ~B;
     const uint32_t H = head_set(B, ones);
-    const uint32_t J = full & ~B & (CLOW ? ~(ones & 1u) : 0xFFFFFFFFu);
+    const uint32_t J = full & ~B;
     const int nA = __popc(A);
     const bool dead = (ones == 0u) && (B != full);
     const bool needclose = !dead || SUBSETS;
@@ -476,12 +476,11 @@ __device__ __forceinline__ void fwd_mask_df(const OrderTab &tab, uint32_t mask_i
         const uint32_t off1 = __ldg(tab.rank3 + code + c_p3[k]);
         df64 *tp = dst1 + (size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane;
         df64 val = C;
-        if (!CLOW && ell == 1 && shifts) val = df64_add(val, seed0);   // vertex 0 carries a shift point
-        if (CLOW) *tp = (k == 0 && lam == 0) ? df64{0.0f, 0.0f} : val;
-        else if (k == 0) *tp = df64_add(*tp, val);                    // the extension into 0' wrote it
+        if (ell == 1 && shifts) val = df64_add(val, seed0);   // vertex 0 carries a shift point
+        if (k == 0) *tp = df64_add(*tp, val);                // the extension into 0' wrote it
         else *tp = val;
     } else if (active && lam == 0 && out) {
-        const double c = CLOW ? df64_to_double(C) : ldexp(df64_to_double(C), n - 1);
+        const double c = ldexp(df64_to_double(C), n - 1);
         out[cfg] = c;
         if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
     }

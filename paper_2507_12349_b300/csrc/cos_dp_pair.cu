@@ -139,8 +139,9 @@ __device__ __forceinline__ void row_dispatch_pair(int nv, const FV<P> *src, FV<P
 #undef COS_ROW_P
 }
 
-// One interaction mask for the P configurations of every lane (twin of fwd_mask<float>).
-template <int P>
+// One interaction mask for the P configurations of every lane (twin of fwd_mask<float>;
+// CLOW: determinant weights without cycle factors, as there).
+template <int P, bool CLOW>
 __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
                                               int n, const FV<P> *src, FV<P> *dst1, const FV<P> *Ms,
                                               const DV<P> *Md, int lane, int ci, int nfl, double sgn, double sig,
@@ -151,7 +152,7 @@ __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask
     const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, code = mk.y, off = mk.z;
     const uint32_t ones = A & ~B;
     const uint32_t H = head_set(B, ones);
-    const uint32_t J = full & ~B;
+    const uint32_t J = full & ~B & (CLOW ? ~(ones & 1u) : 0xFFFFFFFFu);
     const int nA = __popc(A);
     const bool needclose = (ones != 0u) || (B == full);
     if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
@@ -190,10 +191,10 @@ __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask
 #pragma unroll
         for (int c = 0; c < P; ++c) {
             double v = C[c];
-            if (ell == 1 && shifts) v += sgn * 2.0 * sig;   // vertex 0 carries a shift point
-            tv.v[c] = narrow_to(0.0f, v);
+            if (!CLOW && ell == 1 && shifts) v += sgn * 2.0 * sig;   // vertex 0 carries a shift point
+            tv.v[c] = (CLOW && k == 0 && lam == 0) ? 0.0f : narrow_to(0.0f, v);
         }
-        if (k == 0) {                                       // the extension into 0' wrote it
+        if (!CLOW && k == 0) {                              // the extension into 0' wrote it
             FV<P> cur = *tp;
 #pragma unroll
             for (int c = 0; c < P; ++c) cur.v[c] += tv.v[c];
@@ -205,7 +206,7 @@ __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask
 #pragma unroll
         for (int c = 0; c < P; ++c)
             if (act[c]) {
-                const double r = ldexp(C[c], n - 1);
+                const double r = CLOW ? C[c] : ldexp(C[c], n - 1);
                 out[cfg[c]] = r;
                 if (!isfinite(r)) atomicOr(status, kStatusNonFinite);
             }
@@ -317,6 +318,7 @@ __device__ __forceinline__ void row_dispatch_dfp(int nv, const df64x2 *src, df64
 #undef COS_ROW_DP
 }
 
+template <bool CLOW>
 __device__ __forceinline__ void fwd_mask_dfp(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
                                              int n, const df64x2 *src, df64x2 *dst1, const df64x2 *Ms,
                                              const df64x2 *Md, int lane, int ci, int nfl, df64 seed0, bool shifts,
@@ -327,7 +329,7 @@ __device__ __forceinline__ void fwd_mask_dfp(const OrderTab &tab, uint32_t mask_
     const uint32_t A = mk.x & 0xFFFFu, B = mk.x >> 16, code = mk.y, off = mk.z;
     const uint32_t ones = A & ~B;
     const uint32_t H = head_set(B, ones);
-    const uint32_t J = full & ~B;
+    const uint32_t J = full & ~B & (CLOW ? ~(ones & 1u) : 0xFFFFFFFFu);
     const int nA = __popc(A);
     const bool needclose = (ones != 0u) || (B == full);
     if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
@@ -361,11 +363,12 @@ __device__ __forceinline__ void fwd_mask_dfp(const OrderTab &tab, uint32_t mask_
         df64x2 val;
         val.x = Cx;
         val.y = Cy;
-        if (ell == 1 && shifts) {   // vertex 0 carries a shift point
+        if (!CLOW && ell == 1 && shifts) {   // vertex 0 carries a shift point
             val.x = df64_add(val.x, seed0);
             val.y = df64_add(val.y, seed0);
         }
-        if (k == 0) {               // the extension into 0' wrote it
+        if (CLOW && k == 0 && lam == 0) val.x = val.y = df64{0.0f, 0.0f};   // block 1 only
+        if (!CLOW && k == 0) {               // the extension into 0' wrote it
             df64x2 cur = *tp;
             cur.x = df64_add(cur.x, val.x);
             cur.y = df64_add(cur.y, val.y);
@@ -375,12 +378,12 @@ __device__ __forceinline__ void fwd_mask_dfp(const OrderTab &tab, uint32_t mask_
         }
     } else if (lam == 0 && out) {
         if (act_x) {
-            const double c = ldexp(df64_to_double(Cx), n - 1);
+            const double c = CLOW ? df64_to_double(Cx) : ldexp(df64_to_double(Cx), n - 1);
             out[cfg_x] = c;
             if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
         }
         if (act_y) {
-            const double c = ldexp(df64_to_double(Cy), n - 1);
+            const double c = CLOW ? df64_to_double(Cy) : ldexp(df64_to_double(Cy), n - 1);
             out[cfg_y] = c;
             if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
         }
@@ -391,10 +394,10 @@ __device__ __forceinline__ void fwd_mask_dfp(const OrderTab &tab, uint32_t mask_
 
 // MAXT = 256 (two CTAs of up to 8 warps, <= 128 registers), 384 (two CTAs of up to 12 warps,
 // <= 85) or 512 (one CTA of up to 16 warps, <= 128).
-template <int MAXT>
+template <int MAXT, bool CLOW>
 __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_dfp_kernel(const __grid_constant__ DpArgs a);
 
-template <int P, int MAXT>
+template <int P, int MAXT, bool CLOW>
 __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_kernel(const __grid_constant__ DpArgs a) {
     extern __shared__ __align__(16) unsigned char smem_p[];
     __shared__ int s_batch;
@@ -437,7 +440,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_kernel(cons
         const double dshift = sgn * sig;
         for (int e = warp; e < n * n; e += nwarps) {
             const int v = e / n, j = e % n;
-            const bool sh = v == j && j != 0 && shifts;
+            const bool sh = v == j && (CLOW || (j != 0 && shifts));
             FV<P> m;
             DV<P> d;
 #pragma unroll
@@ -445,7 +448,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_kernel(cons
                 double val = act[c] ? Mp[c][e] : 0.0;
                 if (a.absmode) val = fabs(val);
                 m.v[c] = (float)(sh ? val + dshift : val);
-                d.v[c] = cfac * val;
+                d.v[c] = cfac * ((CLOW && sh) ? val + dshift : val);   // CLOW: shifted diagonal in the close too
             }
             Ms[e * kLanes + lane] = m;
             Md[e * kLanes + lane] = d;
@@ -453,7 +456,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_kernel(cons
         if (warp == 0) {
             FV<P> one;
 #pragma unroll
-            for (int c = 0; c < P; ++c) one.v[c] = 1.0f;
+            for (int c = 0; c < P; ++c) one.v[c] = (CLOW && lam != 0) ? 0.0f : 1.0f;
             ring[(1 % a.nslots) * a.slot_elems + lane] = one;
         }
         __syncthreads();
@@ -463,7 +466,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_kernel(cons
             const uint32_t first = tab.layer_first[ell];
             const uint32_t cnt = tab.layer_count[ell];
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
-                fwd_mask_pair<P>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src,
+                fwd_mask_pair<P, CLOW>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src,
                                  dst1, Ms, Md, lane, ci, nfl, sgn, sig, shifts, act, cfg, lam, a.out, a.status,
                                  a.prefetch);
             __syncthreads();
@@ -471,7 +474,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_kernel(cons
     }
 }
 
-template <int MAXT>
+template <int MAXT, bool CLOW>
 __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_dfp_kernel(const __grid_constant__ DpArgs a) {
     extern __shared__ __align__(16) unsigned char smem_q[];
     __shared__ int s_batch;
@@ -518,19 +521,20 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_dfp_kernel(
                 vy = fabs(vy);
             }
             const int v = e / n, j = e % n;
-            const bool sh = v == j && j != 0 && shifts;
+            const bool sh = v == j && (CLOW || (j != 0 && shifts));
             df64x2 m, c;
             m.x = df64_from(sh ? vx + dshift : vx);
             m.y = df64_from(sh ? vy + dshift : vy);
-            c.x = df64_from(cfac * vx);
-            c.y = df64_from(cfac * vy);
+            c.x = df64_from(cfac * ((CLOW && sh) ? vx + dshift : vx));   // CLOW: shifted diagonal in the close too
+            c.y = df64_from(cfac * ((CLOW && sh) ? vy + dshift : vy));
             Ms[e * kLanes + lane] = m;
             Md[e * kLanes + lane] = c;
         }
         if (warp == 0) {
             df64x2 one;
-            one.x = df64{1.0f, 0.0f};
-            one.y = df64{1.0f, 0.0f};
+            const float s0 = (CLOW && lam != 0) ? 0.0f : 1.0f;
+            one.x = df64{s0, 0.0f};
+            one.y = df64{s0, 0.0f};
             ring[(1 % a.nslots) * a.slot_elems + lane] = one;
         }
         __syncthreads();
@@ -540,7 +544,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_dfp_kernel(
             const uint32_t first = tab.layer_first[ell];
             const uint32_t cnt = tab.layer_count[ell];
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
-                fwd_mask_dfp(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1,
+                fwd_mask_dfp<CLOW>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1,
                              Ms, Md, lane, ci, nfl, seed0, shifts, act_x, act_y, lam, cfg_x, cfg_y, a.out, a.status,
                              a.prefetch);
             __syncthreads();
@@ -548,12 +552,18 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_dfp_kernel(
     }
 }
 
-static auto pair_kernel_for(int precision, int threads) {
+template <bool CLOW>
+static auto pair_kernel_mode(int precision, int threads) {
     if (precision == COS_DF64)
-        return threads <= 256 ? dp_pair_dfp_kernel<256>
-                              : (threads <= 384 ? dp_pair_dfp_kernel<384> : dp_pair_dfp_kernel<512>);
-    return threads <= 256 ? dp_pair_kernel<kMixedWidth, 256>
-                          : (threads <= 384 ? dp_pair_kernel<kMixedWidth, 384> : dp_pair_kernel<kMixedWidth, 512>);
+        return threads <= 256 ? dp_pair_dfp_kernel<256, CLOW>
+                              : (threads <= 384 ? dp_pair_dfp_kernel<384, CLOW> : dp_pair_dfp_kernel<512, CLOW>);
+    return threads <= 256 ? dp_pair_kernel<kMixedWidth, 256, CLOW>
+                          : (threads <= 384 ? dp_pair_kernel<kMixedWidth, 384, CLOW>
+                                            : dp_pair_kernel<kMixedWidth, 512, CLOW>);
+}
+
+static auto pair_kernel_for(int precision, int threads, bool clow = false) {
+    return clow ? pair_kernel_mode<true>(precision, threads) : pair_kernel_mode<false>(precision, threads);
 }
 
 size_t pair_smem_bytes(int precision, int n_max) {
@@ -604,7 +614,7 @@ cos_status launch_dp_pair(Workspace *ws, const DpLaunch &L, cudaStream_t stream)
     if (st != COS_OK) return st;
     const int threads = tu.warps * 32;
     const size_t smem = pair_smem_bytes(L.precision, L.n_max);
-    auto kern = pair_kernel_for(L.precision, threads);
+    auto kern = pair_kernel_for(L.precision, threads, L.clow);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "dp smem attribute");
     DpArgs a;
