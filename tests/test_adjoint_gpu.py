@@ -139,21 +139,27 @@ def test_grad_forward_value_and_determinism():
 
 
 def test_grad_order10_sampled_entries():
-    """Adjoint workload shape (SU(4), mu broken, n = 10): sampled entries of dc/dM."""
+    """The adjoint workload at the benchmark's size (SU(4), mu broken, n = 10, 5 x 10^4
+    configurations, one gradient call): sampled entries of dc/dM against central
+    differences of the oracle."""
     w = I.WORKLOADS["su4_adjoint_n10"]
-    cfgs = I.workload_configs(w, 64)
+    nc = w.n_cfg
+    cfgs = I.workload_configs(w)
     tabs = B.tables_for(w.model)
     d = B.configs_to_device(cfgs)
     n_mat = 4
-    gmoff = torch.arange(64, dtype=torch.int64, device="cuda") * n_mat * 100
-    gM = torch.empty(64 * n_mat * 100, dtype=torch.float64, device="cuda")
-    out = torch.empty(64, dtype=torch.float64, device="cuda")
-    B.cos_connected_sum_grad(tabs, 10, *d, torch.ones(64, dtype=torch.float64, device="cuda"), out, gM, gmoff)
+    gmoff = torch.arange(nc, dtype=torch.int64, device="cuda") * n_mat * 100
+    gM = torch.empty(nc * n_mat * 100, dtype=torch.float64, device="cuda")
+    out = torch.empty(nc, dtype=torch.float64, device="cuda")
+    gmu = torch.empty(nc, 4, dtype=torch.float64, device="cuda")
+    B.cos_connected_sum_grad(tabs, 10, *d, torch.ones(nc, dtype=torch.float64, device="cuda"), out, gM, gmoff,
+                             gmu=gmu)
     B.cos_sync_status()
-    g = gM.cpu().numpy().reshape(64, n_mat, 10, 10)
+    g = gM.cpu().numpy().reshape(nc, n_mat, 10, 10)
+    assert np.all(np.isfinite(gmu.cpu().numpy()))
     otabs = P.model_tables(w.model)
     rng = np.random.default_rng(0)
-    for c in (0, 63):
+    for c in (0, nc // 2, nc - 1):
         M = P.gather_one(otabs, cfgs.site[cfgs.offset[c]:cfgs.offset[c] + 10],
                          cfgs.tau[cfgs.offset[c]:cfgs.offset[c] + 10], w.model.L, w.model.beta)
         mass = O.dp(M, None, absmode=True)

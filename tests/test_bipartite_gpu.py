@@ -169,19 +169,22 @@ def test_bipartite_gather_and_batch_vs_oracle():
 
 
 def test_workload_honeycomb_order8_sampled():
-    """SU(2) honeycomb with an antiferromagnetic staggered shift, n = 8: sampled configurations
-    against the oracle's sum over the 256 sublattice assignments."""
+    """SU(2) honeycomb with an antiferromagnetic staggered shift, n = 8, at the benchmark's size
+    (2 x 10^4 configurations): sampled configurations against the oracle's sum over the 256
+    sublattice assignments."""
     w = I.WORKLOADS["hc_su2_af_n8"]
-    cfgs = I.workload_configs(w, 256)
+    nc = w.n_cfg
+    cfgs = I.workload_configs(w)
     tabs = B.honeycomb_tables_for(w.model)
     d = B.configs_to_device(cfgs)
-    out = torch.full((256,), float("nan"), dtype=torch.float64, device="cuda")
+    out = torch.full((nc,), float("nan"), dtype=torch.float64, device="cuda")
     B.cos_connected_sum_bipartite_batch(tabs, 8, *d, "fp64", out)
     B.cos_sync_status()
     got = out.cpu().numpy()
+    assert np.all(np.isfinite(got))
     otabs = HC.hc_model_tables(w.model)
     s2 = np.array(w.model.sigma2)
-    for c in (0, 255):
+    for c in (0, nc // 2, nc - 1):
         o = int(cfgs.offset[c])
         M4 = HC.hc_gather_one(otabs, cfgs.site[o:o + 8], cfgs.tau[o:o + 8], w.model.L, w.model.beta)
         ref = O.bip(M4, s2, method="sum_dp", prec="ld")

@@ -252,14 +252,26 @@ def test_order11_invariances_reduced_precision(precision):
 
 # ------------------------------------------------------------------ workloads through the coordinates path
 
-def workload_check(name, n_cfg, sample, prec="fp64", rel=1e-10):
+def workload_check(name, n_cfg, sample, prec="fp64", rel=1e-10, graph=False):
+    """The workload at the benchmark's size and launch form (graph=True: the CUDA-graph plan
+    the benchmark replays), sampled configurations against the oracle."""
     w = I.WORKLOADS[name]
+    n_cfg = w.n_cfg if n_cfg is None else n_cfg
     cfgs = I.workload_configs(w, n_cfg)
     tabs = B.tables_for(w.model)
     d = B.configs_to_device(cfgs)
     out = torch.full((n_cfg,), float("nan"), dtype=torch.float64, device="cuda")
     mass = torch.full_like(out, float("nan"))
-    B.cos_connected_sum_batch(tabs, int(cfgs.order.max()), *d, prec, out, mass)
+    nmax = int(cfgs.order.max())
+    B.cos_connected_sum_batch(tabs, nmax, *d, prec, mass.new_empty(n_cfg), mass)   # the mass (plain call)
+    if graph:
+        plan = B.cos_plan_create_batch(tabs, nmax, *d, prec, out)
+        out.fill_(float("nan"))
+        plan.launch()
+        plan.status()
+        plan.close()
+    else:
+        B.cos_connected_sum_batch(tabs, nmax, *d, prec, out)
     B.cos_sync_status()
     got, gmass = out.cpu().numpy(), mass.cpu().numpy()
     otabs = P.model_tables(w.model)
@@ -289,38 +301,38 @@ def workload_check(name, n_cfg, sample, prec="fp64", rel=1e-10):
 
 
 def test_workload_su2_order4_all_configs():
-    errs = workload_check("su2_sym_n4", 10_000, 200)
+    errs = workload_check("su2_sym_n4", None, 200)
     assert max(errs) < 1e-10
 
 
 def test_workload_su4_order8_sampled():
-    errs = workload_check("su4_mu_broken_n8", 20_000, 40)
+    errs = workload_check("su4_mu_broken_n8", None, 40)
     assert max(errs) < 1e-10
 
 
 def test_workload_su3_mixed_order10_sampled():
-    workload_check("su3_shift_mixed_n10", 2_000, 6, prec="mixed")
+    workload_check("su3_shift_mixed_n10", None, 6, prec="mixed")
 
 
 def test_workload_su3_fp64_order10_sampled():
-    workload_check("su3_shift_mixed_n10", 500, 4, prec="fp64")
+    workload_check("su3_shift_mixed_n10", None, 4, prec="fp64")
 
 
 def test_workload_su6_uneven_sampled():
-    workload_check("su6_sym_uneven_n4_12", 3_000, 12)
+    workload_check("su6_sym_uneven_n4_12", None, 12, graph=True)
 
 
 def test_workload_su4_df64_order8_sampled():
-    workload_check("su4_mu_broken_n8", 20_000, 40, prec="df64")
+    workload_check("su4_mu_broken_n8", None, 40, prec="df64")
 
 
 def test_workload_su3_df64_order10_sampled():
-    workload_check("su3_shift_mixed_n10", 1_000, 4, prec="df64")
+    workload_check("su3_shift_mixed_n10", None, 4, prec="df64")
 
 
 def test_workload_su6_uneven_df64_sampled():
-    workload_check("su6_sym_uneven_n4_12", 2_000, 10, prec="df64")
+    workload_check("su6_sym_uneven_n4_12", None, 10, prec="df64")
 
 
 def test_workload_su4_mixed_order8_sampled():
-    workload_check("su4_mu_broken_n8", 5_000, 12, prec="mixed")
+    workload_check("su4_mu_broken_n8", None, 12, prec="mixed")
