@@ -44,9 +44,13 @@ def main():
     # configurations per lane of each precision's forward kernel (mixed: four, double-float:
     # two, FP64: one), so that the sample fills every SM with batches
     per_lane = {"fp64": 1, "mixed": 4, "df64": 2}
+    seen = set()
     for n, n_mat, wt, shifts, prec in CASES:
         if args.n_mat and n_mat != args.n_mat:
             continue
+        if (n, n_mat, prec) in seen:     # the shape does not depend on the loop weight
+            continue
+        seen.add((n, n_mat, prec))
         cpb = (32 // n_mat) * per_lane[prec]
         n_cfg = cpb * sms * (1 if n >= 11 else 2)
         w, c, pf, ms = B.cos_autotune(n, n_mat, wt, shifts, prec, n_cfg)
