@@ -138,6 +138,33 @@ def test_grad_forward_value_and_determinism():
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(gms[0], gms[1])
 
 
+def test_grad_orders_11_12_euler_and_transpose():
+    """Orders 11 and 12 (the 12-warp adjoint, every layer of order 12 kept: 2.2 GB per CTA),
+    checked by properties that hold at any size: c is homogeneous of degree 2n in (M, sigma),
+    so sum M dc/dM + sum sigma dc/dsigma = 2n c (Euler); transposing every matrix leaves c
+    unchanged and transposes dc/dM; the forward value equals the forward kernel's bit for bit."""
+    orders = [12, 11, 11, 12]
+    n_mat = 2
+    sigma = [0.07, -0.05]
+    Ms = [I.random_matrices(1200 + c, 1, n_mat, n, 0.9)[0] for c, n in enumerate(orders)]
+    gout = np.ones(len(Ms))
+    out, gM, gs = gpu_grad(Ms, n_mat, 1, sigma, gout)
+    outT, gMT, gsT = gpu_grad([np.ascontiguousarray(np.swapaxes(M, 1, 2)) for M in Ms], n_mat, 1, sigma, gout)
+    d_order, d_moff, d_M, order, _ = pack(Ms, n_mat)
+    ref = torch.empty(len(Ms), dtype=torch.float64, device="cuda")
+    B.cos_connected_sum_matrices(12, d_order, d_moff, n_mat, 1, sigma, d_M, "fp64", ref)
+    B.cos_sync_status()
+    assert np.array_equal(out, ref.cpu().numpy())
+    for c, n in enumerate(orders):
+        terms = Ms[c] * gM[c]
+        lhs = terms.sum() + float(np.dot(sigma, gs[c]))
+        scale = np.abs(terms).sum() + float(np.abs(np.multiply(sigma, gs[c])).sum()) + 2 * n * abs(out[c])
+        assert abs(lhs - 2 * n * out[c]) <= 1e-9 * scale, (c, n, lhs, 2 * n * out[c])
+        assert abs(outT[c] - out[c]) <= 1e-9 * scale / (2 * n)
+        assert np.max(np.abs(gMT[c] - np.swapaxes(gM[c], 1, 2))) <= 1e-9 * np.max(np.abs(gM[c]))
+        assert np.max(np.abs(gsT[c] - gs[c])) <= 1e-9 * np.max(np.abs(gs[c]))
+
+
 def test_grad_order10_sampled_entries():
     """The adjoint workload at the benchmark's size (SU(4), mu broken, n = 10, 5 x 10^4
     configurations, one gradient call): sampled entries of dc/dM against central

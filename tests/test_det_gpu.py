@@ -111,20 +111,21 @@ def test_square_matches_oracle(n, ncfg, shifts, prec):
         assert mass[c] == pytest.approx(rmass, rel=1e-12 if prec == "fp64" else 1e-6)
 
 
-def test_square_uneven_orders_and_cos_relation():
-    """Orders 1..12 in one launch; up to 10 against the oracle, 11 and 12 against the CoS
-    kernel on the same matrices (c_CoS = 2^n c)."""
+@pytest.mark.parametrize("prec", ["fp64", "df64", "mixed"])
+def test_square_uneven_orders_and_cos_relation(prec):
+    """Orders 1..12 in one launch; up to 8 against the oracle, every order against the FP64
+    CoS kernel on the same matrices (c_CoS = 2^n c)."""
     orders = [12, 3, 11, 1, 7, 10, 2, 12, 5, 9, 4, 6, 8, 11]
     Ms = [rand_sq(3000 + c, 1, n)[0] for c, n in enumerate(orders)]
-    got, mass = run_square(Ms)
+    got, mass = run_square(Ms, None, prec)
     cos, cmass = run_cos_square(Ms)
     for c, n in enumerate(orders):
         if n <= 8:
             ref = O.det_clow(Ms[c], prec="ld")
             rmass = O.det_clow(Ms[c], absmode=True)
-            assert abs(got[c] - ref) <= bound("fp64", n, rmass), (c, n, got[c], ref)
+            assert abs(got[c] - ref) <= bound(prec, n, rmass), (c, n, got[c], ref)
         # the two GPU paths agree through the CoS relation at every order
-        tol = bound("fp64", n, mass[c]) + bound("fp64", n, cmass[c]) / 2.0 ** n
+        tol = bound(prec, n, mass[c]) + bound("fp64", n, cmass[c]) / 2.0 ** n
         assert abs(got[c] - cos[c] / 2.0 ** n) <= tol, (c, n, got[c], cos[c] / 2.0 ** n)
 
 
@@ -154,17 +155,18 @@ def test_bipartite_matches_oracle(n, ncfg, shifts, prec):
         assert mass[c] == pytest.approx(rmass, rel=1e-12 if prec == "fp64" else 1e-9)
 
 
-def test_bipartite_uneven_and_order9_cos_relation():
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_bipartite_uneven_and_order9_cos_relation(prec):
     orders = [9, 2, 6, 1, 9, 4, 8, 3, 5, 7]
     M4s = [rand_m4(6000 + c, 1, n)[0] for c, n in enumerate(orders)]
-    got, mass = run_bip(M4s)
+    got, mass = run_bip(M4s, None, prec)
     cos, cmass = run_bip(M4s, cos=True)
     for c, n in enumerate(orders):
         if n <= 6:
             ref = O.det_clow(M4s[c], prec="ld")
             rmass = O.det_clow(M4s[c], absmode=True)
-            assert abs(got[c] - ref) <= bound("fp64", n, rmass), (c, n, got[c], ref)
-        tol = bound("fp64", n, mass[c]) + bound("fp64", n, cmass[c]) / 2.0 ** n
+            assert abs(got[c] - ref) <= bound(prec, n, rmass), (c, n, got[c], ref)
+        tol = bound(prec, n, mass[c]) + bound("fp64", n, cmass[c]) / 2.0 ** n
         assert abs(got[c] - cos[c] / 2.0 ** n) <= tol, (c, n, got[c], cos[c] / 2.0 ** n)
 
 
