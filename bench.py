@@ -64,6 +64,9 @@ def parse():
     p.add_argument("--det", action="store_true",
                    help="profiling runs only: time the SU(2) determinant-weight step (gather + DP, Alg. 1) "
                         "of the order-10 Zeeman workload")
+    p.add_argument("--subsets", action="store_true",
+                   help="profiling runs only: time the all-subsets call (c(S) and a(S) of every vertex subset) "
+                        "on the headline workload's gathered matrices")
     p.add_argument("--order", type=int, default=0, help="with --bipartite or --det: order of the configurations")
     return p.parse_args()
 
@@ -721,6 +724,41 @@ def bipartite_arm(args):
     tabs.close()
 
 
+def subsets_arm(args):
+    """Profiling runs of the all-subsets mode alone: gather + cos_connected_sum_subsets with
+    all roots and a(S) on --n-cfg configurations of the headline workload (SU(4), n = 8)."""
+    import torch
+    from paper_2507_12349_b300 import binding as B
+    B.lib()
+    w = I.WORKLOADS[WORKLOAD]
+    n = w.n_lo
+    n_cfg = args.n_cfg if args.n_cfg > 0 else w.n_cfg
+    cfgs = I.workload_configs(w, n_cfg)
+    tabs = B.tables_for(w.model)
+    n_mat = tabs.info().n_mat
+    d = B.configs_to_device(cfgs)
+    moff = torch.as_tensor(B.matrix_offsets(cfgs.order, n_mat), device="cuda")
+    M = torch.empty(n_cfg * n_mat * n * n, dtype=torch.float64, device="cuda")
+    c = torch.empty(n_cfg << n, dtype=torch.float64, device="cuda")
+    a = torch.empty_like(c)
+    flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def fn():
+        B.cos_gather(tabs, *d, moff, M)
+        B.cos_connected_sum_subsets(n, d[0], moff, n_mat, 1, None, M, "fp64", c, a, True)
+    for _ in range(max(1, args.warmup)):
+        fn()
+    B.cos_sync_status()
+    ts = time_steps(torch, fn, args.steps, lambda: flush_l2(flush_buf))
+    B.cos_sync_status()
+    t = statistics.mean(ts)
+    print(json.dumps({"metric": "all-subsets connected sums configs/s (c(S), a(S) of every subset)",
+                      "value": n_cfg / t, "unit": "configs/s", "order": n, "configs": n_cfg,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "dtype": "f64"}),
+          flush=True)
+    tabs.close()
+
+
 def det_arm(args):
     """Profiling runs of the determinant-weight path alone: the SU(2) Zeeman workload's gather
     + DP without cycle factors, at its order or --order, --n-cfg configurations."""
@@ -764,6 +802,8 @@ def main():
         bipartite_arm(args)
     elif args.det:
         det_arm(args)
+    elif args.subsets:
+        subsets_arm(args)
     else:
         native_arm(args)
 
