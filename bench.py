@@ -549,6 +549,18 @@ def measure_det(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
             s = B.cos_structure(n)
             r["frac_fp64_peak_close"] = n_cfg * 2 * 2.0 * s.fma_close / ts[p] / fp64_peak
         res[f"su2_zeeman_n10_det_{p}"] = r
+    # gradient (reverse sweep of the determinant weights): dc/dM and dc/dalpha of every configuration
+    gout = torch.ones(n_cfg, dtype=torch.float64, device="cuda")
+    gM = torch.empty_like(M)
+    ga = torch.empty(n_cfg, 2, dtype=torch.float64, device="cuda")
+    gfn = lambda: B.cos_connected_det_matrices_grad(n, d[0], moff, None, M, gout, None, gM, ga)
+    gfn()
+    B.cos_sync_status()
+    tg = statistics.mean(time_steps(torch, gfn, 1, lambda: flush_l2(flush_buf)))
+    B.cos_sync_status()
+    res["su2_zeeman_n10_det_grad_fp64"] = {"configs": n_cfg, "grad_configs_per_s": n_cfg / tg, "ms": tg * 1e3,
+                                           "grad_overhead": tg / ts["fp64"],
+                                           "frac_fp64_peak": 3 * fl / tg / fp64_peak}
     got = outs["fp64"].cpu().numpy()
     cos = outs["cos"].cpu().numpy()
     res["su2_zeeman_n10_det_fp64"]["max_rel_diff_vs_cos_over_2n"] = float(np.max(np.abs(got - cos / 2.0 ** n) / np.abs(got)))

@@ -290,6 +290,15 @@ cos_status cos_connected_det_matrices(int n_cfg, int n_max, const int32_t *d_ord
                                       const double *h_alpha, const double *d_M, cos_precision precision,
                                       double *d_out, double *d_abs_mass, cos_stream_t stream);
 
+/* Gradient of the square-lattice determinant-weight sums by the reverse sweep (the adjoint of
+ * Alg. 1 as merged above; the forward sweep is re-run with every layer kept):
+ * d_gout[c]  dLoss/dc;  d_out NULL or receives c;  d_gM NULL or dLoss/dM at d_moff[c] as
+ * [2][n_c][n_c];  d_galpha NULL or [n_cfg][2] dLoss/dalpha_b (= -trace of dLoss/dM_b).
+ * Other arguments as cos_connected_det_matrices; FP64 only. */
+cos_status cos_connected_det_matrices_grad(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                                           const double *h_alpha, const double *d_M, const double *d_gout,
+                                           double *d_out, double *d_gM, double *d_galpha, cos_stream_t stream);
+
 /* Bipartite lattice (Alg. 1 as stated): d_M4 per configuration [2][2 n_c][2 n_c] (spin block,
  * then the layout of cos_gather_bipartite), h_alpha2 = NULL or host [2][2] diagonal shifts per
  * (spin, sublattice); n_max <= COS_BIP_NMAX; precision COS_FP64 or COS_DF64.  Outputs and

@@ -32,7 +32,7 @@ EXPORTS = [
     "cos_connected_sum_subsets",
     "cos_build_propagators_honeycomb", "cos_gather_bipartite", "cos_connected_sum_bipartite_matrices",
     "cos_connected_sum_bipartite_batch", "cos_bipartite_structure",
-    "cos_connected_det_matrices", "cos_connected_det_bipartite_matrices",
+    "cos_connected_det_matrices", "cos_connected_det_bipartite_matrices", "cos_connected_det_matrices_grad",
     "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_sync_status", "cos_status_string",
     "cos_last_error", "cos_structure", "cos_peak_probe",
     "cos_plan_create_batch", "cos_plan_create_matrices", "cos_plan_launch", "cos_plan_status", "cos_plan_grid",
@@ -249,6 +249,17 @@ def cos_connected_det_matrices(n_max: int, order, moff, alpha: Optional[Sequence
     _check(lib().cos_connected_det_matrices(int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(moff, "i64"), al,
                                             _ptr(M, "f64"), PRECISIONS[precision], _ptr(out, "f64"),
                                             _ptr(abs_mass, "f64"), _stream(stream)), "cos_connected_det_matrices")
+
+
+def cos_connected_det_matrices_grad(n_max: int, order, moff, alpha: Optional[Sequence[float]], M, gout, out=None,
+                                    gM=None, galpha=None, stream=None):
+    """Gradient of the SU(2) determinant-weight sums: dLoss/dM (layout of M) and dLoss/dalpha
+    ([n_cfg][2]) for dLoss/dc = gout."""
+    al = None if alpha is None else (ctypes.c_double * 2)(*[float(x) for x in alpha])
+    _check(lib().cos_connected_det_matrices_grad(int(order.numel()), int(n_max), _ptr(order, "i32"),
+                                                 _ptr(moff, "i64"), al, _ptr(M, "f64"), _ptr(gout, "f64"),
+                                                 _ptr(out, "f64"), _ptr(gM, "f64"), _ptr(galpha, "f64"),
+                                                 _stream(stream)), "cos_connected_det_matrices_grad")
 
 
 def cos_connected_det_bipartite_matrices(n_max: int, order, moff, alpha2, M4, precision: str, out, abs_mass=None,

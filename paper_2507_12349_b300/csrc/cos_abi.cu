@@ -482,6 +482,39 @@ extern "C" cos_status cos_connected_sum_matrices_grad(int n_cfg, int n_max, cons
     return launch_adjoint(ws, L, d_gout, d_gM, d_moff, 0, d_gsigma, (cudaStream_t)stream);
 }
 
+extern "C" cos_status cos_connected_det_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
+                                                      const int64_t *d_moff, const double *h_alpha, const double *d_M,
+                                                      const double *d_gout, double *d_out, double *d_gM,
+                                                      double *d_galpha, cos_stream_t stream) {
+    cos_status st = check_common(n_cfg, n_max, COS_FP64, "cos_connected_det_matrices_grad");
+    if (st != COS_OK || n_cfg == 0) return st;
+    if (!d_order || !d_moff || !d_M || !d_gout) {
+        set_error("cos_connected_det_matrices_grad: null device pointer");
+        return COS_ERR_ARG;
+    }
+    std::string err;
+    Workspace *ws = get_workspace((cudaStream_t)stream, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    DpLaunch L;
+    L.n_cfg = n_cfg;
+    L.n_max = n_max;
+    L.order = d_order;
+    L.M = d_M;
+    L.moff = d_moff;
+    L.n_mat = 2;
+    L.loop_weight = 1;
+    for (int b = 0; b < 2; ++b) L.sigma[b] = h_alpha ? h_alpha[b] : 0.0;   // the diagonal shifts
+    L.clow = true;
+    L.precision = COS_FP64;
+    L.out = d_out;
+    st = launch_plan_batches(ws, n_cfg, n_max, d_order, kLanes / 2, (cudaStream_t)stream);
+    if (st != COS_OK) return st;
+    return launch_adjoint(ws, L, d_gout, d_gM, d_moff, 0, d_galpha, (cudaStream_t)stream);
+}
+
 extern "C" cos_status cos_connected_sum_grad(const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order,
                                              const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
                                              const double *d_gout, double *d_out, double *d_gM,

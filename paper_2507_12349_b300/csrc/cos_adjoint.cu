@@ -13,7 +13,11 @@
 //     dsigma   += sgn D_j O(mu,h,j) for every half-visited j >= 1 (the shifted diagonal), and
 //                 sgn 2 Obar(2e_0, 0, 0) for the shifted start.
 // Every adjoint slot read was written earlier in the same sweep (targets of reachable edges
-// are reachable), so the adjoint ring needs no clearing.  dM accumulates in a private
+// are reachable), so the adjoint ring needs no clearing.
+// Determinant weights (CLOW instantiations, the sweep of Alg. 1 in cos_dp.cu): the forward
+// recompute runs that mode, the reverse sweep skips the first loop's step onto vertex 0, a
+// close at k = 0 fed block 1 only (Cbar = Obar of that lane), the sink's Cbar is gout, and the
+// diagonal shifts sit in both matrix copies, so dc/dalpha_b = -sum_j dc/dM_b[j][j].  dM accumulates in a private
 // shared-memory copy per warp, summed in warp order at the end: no atomics, bitwise
 // reproducible.
 #include <algorithm>
@@ -135,7 +139,7 @@ __device__ __forceinline__ void adj_endpoint_dispatch(int nJ, const double *fsrc
 // entry summed in a fixed order (bitwise reproducible).  Every warp walks every mask of a layer
 // and takes the rows' endpoints it owns.  The forward recompute splits masks across warps as
 // in the forward kernel.  MAXT = 320 (orders <= 10, two CTAs per SM) or 384 (one CTA).
-template <bool SG, int MAXT>
+template <bool SG, int MAXT, bool CLOW = false>
 __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(const __grid_constant__ AdjArgs a) {
     extern __shared__ __align__(16) double smem_d[];
     __shared__ int s_batch;
@@ -177,8 +181,14 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
         for (int e = warp; e < n * n; e += nwarps) {
             const double val = active ? Mg[e] : 0.0;
             const int v = e / n, j = e % n;
-            Ms[e * kLanes + lane] = (v == j && j != 0 && shifts) ? val + sgn * sig : val;
-            Mc[e * kLanes + lane] = cfac * val;
+            if (CLOW) {
+                const double m = (v == j) ? val + sgn * sig : val;   // a(p, p) - alpha_b in both copies
+                Ms[e * kLanes + lane] = m;
+                Mc[e * kLanes + lane] = cfac * m;
+            } else {
+                Ms[e * kLanes + lane] = (v == j && j != 0 && shifts) ? val + sgn * sig : val;
+                Mc[e * kLanes + lane] = cfac * val;
+            }
             dM[e * kLanes + lane] = 0.0;
         }
         if (threadIdx.x == 0) {
@@ -189,7 +199,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
             }
         }
         __syncthreads();
-        if (warp == 0) store[(size_t)s_base[1] * kLanes + lane] = 1.0;
+        if (warp == 0) store[(size_t)s_base[1] * kLanes + lane] = (CLOW && lam != 0) ? 0.0 : 1.0;
         __syncthreads();
         // forward sweep, every layer kept
         for (int ell = 1; ell <= 2 * n; ++ell) {
@@ -197,8 +207,9 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
             double *dst1 = store + (size_t)s_base[ell + 1] * kLanes;
             const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
-                fwd_mask<double>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src,
-                                 dst1, Ms, Mc, lane, ci, nfl, sgn, sig, shifts, active, lam, cfg, f.out, f.status, 1);
+                fwd_mask<double, false, CLOW>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu,
+                                              ell, n, src, dst1, Ms, Mc, lane, ci, nfl, sgn, sig, shifts, active, lam,
+                                              cfg, f.out, f.status, 1);
             __syncthreads();
         }
         // reverse sweep: this warp's endpoints
@@ -225,13 +236,13 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
                 const uint32_t B = mk.x >> 16, code = mk.y, off = mk.z;
                 const uint32_t ones = A & ~B;
                 const uint32_t H = head_set(B, ones);
-                const uint32_t J = full & ~B;
+                const uint32_t J = full & ~B & (CLOW ? ~(ones & 1u) : 0xFFFFFFFFu);
                 const int nA = __popc(A);
                 const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, lane);
                 const int nJ = __popc(J);
                 double cbar = 0.0;
                 if (B == full) {
-                    cbar = ldexp(gout, n - 1);
+                    cbar = CLOW ? gout : ldexp(gout, n - 1);
                 } else if (ones) {
                     const int k = __ffs(ones) - 1;
                     const uint32_t bk = 1u << k;
@@ -240,9 +251,10 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
                     const int ai1 = __popc(A & (bk - 1u));
                     const uint32_t off1 = __ldg(tab.rank3 + code + c_p3[k]);
                     const double seed = a1[(size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane];
-                    cbar = flavor_sum(seed, nfl, ci);
+                    // (CLOW: the close at k = 0 seeded block 1 only)
+                    cbar = flavor_sum((CLOW && k == 0 && lam == 0) ? 0.0 : seed, nfl, ci);
                     // shifted start (mask e_0, owned by the warp of vertex 0), weight sgn 2 sigma
-                    if (SG && ell == 1) gs = fma(sgn * 2.0, seed, gs);
+                    if (SG && !CLOW && ell == 1) gs = fma(sgn * 2.0, seed, gs);
                 }
                 // loop weight 1: sgn w Cbar is a sign flip (integer pipe), else one multiply
                 const double gamma = unit_weight ? neg(cbar) : cfac * cbar;
@@ -254,7 +266,8 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
                         const int v = __ffs(vv) - 1;
                         const uint32_t slot = rowoff + (uint32_t)__popc(A & ((1u << v) - 1u));
                         // half-visited v >= 1: its index among the extensions (v is in J)
-                        const int qv = (SG && v != 0 && (ones & (1u << v))) ? __popc(J & ((1u << v) - 1u)) : -1;
+                        const int qv =
+                            (SG && !CLOW && v != 0 && (ones & (1u << v))) ? __popc(J & ((1u << v) - 1u)) : -1;
                         adj_endpoint_dispatch<SG, (MAXT <= 320 ? 10 : 12)>(nJ, fsrc, aout, a1, Ms, Mc, dM, ti, J, v, slot, qv, h, n, cbar,
                                                                       gamma, lane, gs);
                     }
@@ -267,7 +280,13 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
             const int64_t gb = (a.gmoff ? a.gmoff[cfg] : (int64_t)cfg * a.gmstride) + (int64_t)lam * n * n;
             for (int e = warp; e < n * n; e += nwarps) a.gM[gb + e] = dM[e * kLanes + lane];
         }
-        if (SG) {
+        if (CLOW && a.gsig) {   // dc/dalpha_b = -trace(dc/dM_b)
+            if (warp == 0 && active) {
+                double t = 0.0;
+                for (int j = 0; j < n; ++j) t += dM[(j * n + j) * kLanes + lane];
+                a.gsig[(int64_t)cfg * nfl + lam] = -t;
+            }
+        } else if (SG) {
             s_red[warp][lane] = gs;
             __syncthreads();
             if (warp == 0 && active && a.gsig) {
@@ -358,8 +377,9 @@ cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, 
     const size_t smem = (size_t)3 * L.n_max * L.n_max * kLanes * sizeof(double);
     const bool sg = gsig != nullptr;
     const bool big = threads > 320;
-    auto kern = sg ? (big ? dp_adjoint_kernel<true, 384> : dp_adjoint_kernel<true, 320>)
-                   : (big ? dp_adjoint_kernel<false, 384> : dp_adjoint_kernel<false, 320>);
+    auto kern = L.clow ? (big ? dp_adjoint_kernel<false, 384, true> : dp_adjoint_kernel<false, 320, true>)
+                       : sg ? (big ? dp_adjoint_kernel<true, 384> : dp_adjoint_kernel<true, 320>)
+                            : (big ? dp_adjoint_kernel<false, 384> : dp_adjoint_kernel<false, 320>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint smem attribute");
     int nsm = 1;

@@ -1,6 +1,13 @@
 """GPU parity of the SU(2) determinant-weight path (the DP without cycle factors, Alg. 1)
 against the oracle.
 
+The gradient: with determinant weights c is linear in every single matrix entry (an entry
+occurs at most once in a determinant term, and in one factor of each product of the subset
+subtraction; pinned by vanishing second differences in test_oracle_det_pins), so a central
+difference of the
+__float128 oracle is exact up to rounding.  dc/dalpha_b (a whole diagonal shifted) is checked
+by an exact polynomial fit in alpha and by the identity dc/dalpha_b = -sum_j dc/dM_b[j][j].
+
 The oracle value is `oracle.det_clow` (Alg. 1 as stated, point-resolved, long double),
 itself pinned against LU determinants with the subset subtraction, brute force and the CoS
 relation in test_oracle_det_pins.  Tolerances are the square-lattice ones of
@@ -239,3 +246,81 @@ def test_honeycomb_det_sampled():
         rmass = O.det_clow(M4c, al, absmode=True)
         assert abs(got[c] - ref) <= bound("fp64", 8, rmass), (c, got[c], ref, rmass)
     tabs.close()
+
+
+# ------------------------------------------------------------------ gradient
+
+def run_grad(Ms, alpha, gout):
+    order = np.array([m.shape[-1] for m in Ms], dtype=np.int32)
+    moff = B.matrix_offsets(order, 2)
+    d_order = torch.tensor(order, device="cuda")
+    d_moff = torch.tensor(moff, device="cuda")
+    d_M = torch.tensor(np.concatenate([m.ravel() for m in Ms]), device="cuda")
+    nc = len(Ms)
+    out = torch.full((nc,), float("nan"), dtype=torch.float64, device="cuda")
+    gM = torch.full_like(d_M, float("nan"))
+    ga = torch.full((nc, 2), float("nan"), dtype=torch.float64, device="cuda")
+    B.cos_connected_det_matrices_grad(int(order.max()), d_order, d_moff, alpha, d_M,
+                                      torch.tensor(gout, dtype=torch.float64, device="cuda"), out, gM, ga)
+    B.cos_sync_status()
+    g = gM.cpu().numpy()
+    return out.cpu().numpy(), [g[moff[c]:moff[c] + Ms[c].size].reshape(Ms[c].shape) for c in range(nc)], ga.cpu().numpy()
+
+
+def exact_det_dM(G, alpha, h=0.5):
+    g = np.zeros_like(G)
+    for idx in np.ndindex(*G.shape):
+        Gp = G.copy(); Gp[idx] += h
+        Gm = G.copy(); Gm[idx] -= h
+        g[idx] = (O.det_clow(Gp, alpha, prec="q") - O.det_clow(Gm, alpha, prec="q")) / (2 * h)
+    return g
+
+
+def exact_det_dalpha(G, alpha):
+    n = G.shape[-1]
+    a0 = np.zeros(2) if alpha is None else np.array(alpha, dtype=np.float64)
+    out = []
+    for b in range(2):
+        hs = [0.05 * k for k in range(-n - 1, n + 2)]
+        vals = []
+        for h in hs:
+            a2 = a0.copy(); a2[b] += h
+            vals.append(O.det_clow(G, a2, prec="q"))
+        out.append(np.polyfit(hs, vals, n + 1)[-2])
+    return np.array(out)
+
+
+def close_to(a, b, rel=1e-9):
+    scale = max(np.max(np.abs(b)), 1e-300)
+    return np.all(np.abs(a - b) <= rel * (np.abs(b) + scale))
+
+
+@pytest.mark.parametrize("n,ncfg,shifts", [(1, 3, True), (2, 5, False), (3, 7, True), (4, 9, True), (5, 4, False)])
+def test_det_grad_vs_exact_differences(n, ncfg, shifts):
+    Ms = rand_sq(7000 + n, ncfg, n)
+    al = [0.11, -0.06] if shifts else None
+    gout = np.linspace(0.5, 1.5, ncfg)
+    out, gM, ga = run_grad(Ms, al, gout)
+    for c in sorted({0, ncfg // 2, ncfg - 1}):
+        ref = O.det_clow(Ms[c], al, prec="ld")
+        assert abs(out[c] - ref) <= bound("fp64", n, O.det_clow(Ms[c], al, absmode=True))
+        dM = gout[c] * exact_det_dM(Ms[c], al)
+        assert close_to(gM[c], dM), c
+        assert close_to(ga[c], gout[c] * exact_det_dalpha(Ms[c], al), rel=1e-7), c
+        assert close_to(ga[c], -np.array([np.trace(dM[0]), np.trace(dM[1])])), c
+
+
+def test_det_grad_orders_11_12_euler():
+    """Orders 11 and 12: c(t M, t alpha) = t^(2n) c gives sum M dc/dM + sum alpha dc/dalpha = 2n c;
+    the forward value equals the determinant sweep's bit for bit."""
+    orders = [12, 11, 12, 11, 7]
+    al = [0.09, -0.04]
+    Ms = [rand_sq(7100 + c, 1, n)[0] for c, n in enumerate(orders)]
+    out, gM, ga = run_grad(Ms, al, np.ones(len(Ms)))
+    ref, _ = run_square(Ms, al, abs_mass=False)
+    assert np.array_equal(out, ref)
+    for c, n in enumerate(orders):
+        terms = Ms[c] * gM[c]
+        lhs = terms.sum() + float(np.dot(al, ga[c]))
+        scale = np.abs(terms).sum() + float(np.abs(np.multiply(al, ga[c])).sum()) + 2 * n * abs(out[c])
+        assert abs(lhs - 2 * n * out[c]) <= 1e-9 * scale, (c, n, lhs, 2 * n * out[c])

@@ -11,7 +11,10 @@ Each check compares `det_clow` with something other than itself:
     force and LU) equals 2^n times the determinant-weight sum, also per sublattice sum;
   * n = 1 closed form; a vertex with no propagator to the others makes the sum vanish;
   * invariances: transposition, vertex relabeling (the head rule), spin swap, sublattice
-    swap, homogeneity c(t G, t alpha) = t^(2n) c(G, alpha); the mass bounds |c|.
+    swap, homogeneity c(t G, t alpha) = t^(2n) c(G, alpha); the mass bounds |c|;
+  * c is linear in every single matrix entry (an entry occurs at most once in a determinant
+    term and in one factor of each subtraction product): second differences vanish, while
+    a diagonal shift alpha (a whole diagonal at once) is not linear.
 """
 import itertools
 
@@ -161,3 +164,24 @@ def test_invariances(nsub, n):
     t = 1.3
     assert O.det_clow(t * G, t * al, prec="ld") == pytest.approx(t ** (2 * n) * ref, abs=t ** (2 * n) * tol)
     assert abs(ref) <= mass(G, al) * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("nsub", [1, 2])
+def test_linear_in_every_entry(nsub):
+    n = 4 if nsub == 1 else 3
+    G = rand_g(71 + nsub, n, nsub)
+    al = rand_alpha(8, nsub)
+    scale = mass(G, al)
+    rng = np.random.default_rng(nsub)
+    for _ in range(6):
+        idx = tuple(int(rng.integers(s)) for s in G.shape)
+        v = []
+        for h in (-1.0, 0.0, 1.0):
+            Gp = G.copy(); Gp[idx] += h
+            v.append(O.det_clow(Gp, al, prec="q"))
+        assert abs(v[0] - 2 * v[1] + v[2]) <= 1e-14 * scale, idx
+    v = []
+    for h in (-1.0, 0.0, 1.0):
+        a2 = al.copy(); a2[0, 0] += h
+        v.append(O.det_clow(G, a2, prec="q"))
+    assert abs(v[0] - 2 * v[1] + v[2]) > 1e-6 * abs(v[1])
