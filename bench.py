@@ -558,6 +558,17 @@ def measure_det(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
     B.cos_sync_status()
     tg = statistics.mean(time_steps(torch, gfn, 1, lambda: flush_l2(flush_buf)))
     B.cos_sync_status()
+    # every vertex subset: c(S) and a(S) = det(A_up[S]) det(A_dn[S]) (CDet's set of minors)
+    cs = torch.empty(n_cfg << n, dtype=torch.float64, device="cuda")
+    as_ = torch.empty_like(cs)
+    sfn = lambda: B.cos_connected_det_subsets(n, d[0], moff, None, M, cs, as_, True)
+    sfn()
+    B.cos_sync_status()
+    tsub = statistics.mean(time_steps(torch, sfn, 1, lambda: flush_l2(flush_buf)))
+    B.cos_sync_status()
+    res["su2_zeeman_n10_det_all_subsets_fp64"] = {"configs": n_cfg, "configs_per_s": n_cfg / tsub,
+                                                  "ms": tsub * 1e3, "cost_vs_plain": tsub / ts["fp64"]}
+    del cs, as_
     res["su2_zeeman_n10_det_grad_fp64"] = {"configs": n_cfg, "grad_configs_per_s": n_cfg / tg, "ms": tg * 1e3,
                                            "grad_overhead": tg / ts["fp64"],
                                            "frac_fp64_peak": 3 * fl / tg / fp64_peak}

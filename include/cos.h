@@ -299,6 +299,15 @@ cos_status cos_connected_det_matrices_grad(int n_cfg, int n_max, const int32_t *
                                            const double *h_alpha, const double *d_M, const double *d_gout,
                                            double *d_out, double *d_gM, double *d_galpha, cos_stream_t stream);
 
+/* Every vertex subset (the all-subsets mode of cos_connected_sum_subsets for determinant
+ * weights): d_c[c * 2^n_max + S] = c(S), the connected part of det(A_up[S]) det(A_dn[S]) (the
+ * close of the Alg. 1 sweep at the mask 2 1_S, rooted at min S); with d_a, a(S) =
+ * det(A_up[S]) det(A_dn[S]) by the subset exponential.  Layout, all_roots, workspace and
+ * errors as cos_connected_sum_subsets; h_alpha as cos_connected_det_matrices; COS_FP64 only. */
+cos_status cos_connected_det_subsets(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                                     const double *h_alpha, const double *d_M, cos_precision precision,
+                                     int all_roots, double *d_c, double *d_a, cos_stream_t stream);
+
 /* Bipartite lattice (Alg. 1 as stated): d_M4 per configuration [2][2 n_c][2 n_c] (spin block,
  * then the layout of cos_gather_bipartite), h_alpha2 = NULL or host [2][2] diagonal shifts per
  * (spin, sublattice); n_max <= COS_BIP_NMAX; precision COS_FP64 or COS_DF64.  Outputs and

@@ -33,6 +33,7 @@ EXPORTS = [
     "cos_build_propagators_honeycomb", "cos_gather_bipartite", "cos_connected_sum_bipartite_matrices",
     "cos_connected_sum_bipartite_batch", "cos_bipartite_structure",
     "cos_connected_det_matrices", "cos_connected_det_bipartite_matrices", "cos_connected_det_matrices_grad",
+    "cos_connected_det_subsets",
     "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_sync_status", "cos_status_string",
     "cos_last_error", "cos_structure", "cos_peak_probe",
     "cos_plan_create_batch", "cos_plan_create_matrices", "cos_plan_launch", "cos_plan_status", "cos_plan_grid",
@@ -260,6 +261,17 @@ def cos_connected_det_matrices_grad(n_max: int, order, moff, alpha: Optional[Seq
                                                  _ptr(moff, "i64"), al, _ptr(M, "f64"), _ptr(gout, "f64"),
                                                  _ptr(out, "f64"), _ptr(gM, "f64"), _ptr(galpha, "f64"),
                                                  _stream(stream)), "cos_connected_det_matrices_grad")
+
+
+def cos_connected_det_subsets(n_max: int, order, moff, alpha: Optional[Sequence[float]], M, c_out, a_out=None,
+                              all_roots: bool = True, stream=None):
+    """c(S) (and a(S) = det(A_up[S]) det(A_dn[S]) when a_out is given) of every vertex subset S for
+    determinant weights: c_out / a_out are [n_cfg * 2^n_max] float64, entry c * 2^n_max + S."""
+    al = None if alpha is None else (ctypes.c_double * 2)(*[float(x) for x in alpha])
+    _check(lib().cos_connected_det_subsets(int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(moff, "i64"), al,
+                                           _ptr(M, "f64"), PRECISIONS["fp64"], int(bool(all_roots)),
+                                           _ptr(c_out, "f64"), _ptr(a_out, "f64"), _stream(stream)),
+           "cos_connected_det_subsets")
 
 
 def cos_connected_det_bipartite_matrices(n_max: int, order, moff, alpha2, M4, precision: str, out, abs_mass=None,

@@ -240,11 +240,11 @@ static auto forward_kernel_for(int threads) {
 }
 
 // Determinant weights (L.clow) reach this launcher in FP64 only: the reduced precisions run
-// the pair kernels (cos_dp_pair.cu).
+// the pair kernels (cos_dp_pair.cu), and their all-subsets mode is FP64.
 template <typename T>
 static auto kernel_for_launch(const DpLaunch &L, int threads) {
     if constexpr (std::is_same<T, double>::value) {
-        if (L.clow) return forward_kernel_for<T, false, true>(threads);
+        if (L.clow) return L.csub ? forward_kernel_for<T, true, true>(threads) : forward_kernel_for<T, false, true>(threads);
     }
     return L.csub ? forward_kernel_for<T, true>(threads) : forward_kernel_for<T, false>(threads);
 }

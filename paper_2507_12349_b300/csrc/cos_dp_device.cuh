@@ -304,7 +304,7 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
     // factor sgn * w is already inside Md (the close's copy of the matrices).
     const double C = flavor_sum(csum, nfl, ci);
     if (SUBSETS && ones == 0u) {
-        if (active && lam == 0) csub[(int64_t)B << cshift] = ldexp(C, __popc(B) - 1);
+        if (active && lam == 0) csub[(int64_t)B << cshift] = CLOW ? C : ldexp(C, __popc(B) - 1);
         if (dead) return;
     }
     if (ones) {

@@ -132,17 +132,18 @@ __global__ void subset_exp_kernel(int n_cfg, int n_max, const int32_t *order, co
 
 }  // namespace
 
-}  // namespace cosdp
-
-using namespace cosdp;
-
-extern "C" cos_status cos_connected_sum_subsets(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
-                                                int n_mat, int loop_weight, const double *h_sigma,
-                                                const double *d_M, cos_precision precision, int all_roots,
-                                                double *d_c, double *d_a, cos_stream_t stream) {
-    const char *fn = "cos_connected_sum_subsets";
+// clow: determinant weights (two spin blocks, loop weight 1, h_sigma = the diagonal shifts);
+// the closes of the Alg. 1 sweep are the connected sums themselves (no 2^(|S|-1)).
+static cos_status subsets_body(const char *fn, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                        int n_mat, int loop_weight, const double *h_sigma, const double *d_M,
+                        cos_precision precision, int all_roots, double *d_c, double *d_a, bool clow,
+                        cudaStream_t s) {
     cos_status st = check_matrices(n_cfg, n_max, d_order, d_moff, n_mat, loop_weight, d_M, precision, d_c, fn);
     if (st != COS_OK) return st;
+    if (clow && precision != COS_FP64) {
+        set_error(std::string(fn) + ": determinant-weight subsets run in COS_FP64");
+        return COS_ERR_UNIMPLEMENTED;
+    }
     if (all_roots != 0 && all_roots != 1) {
         set_error(std::string(fn) + ": all_roots must be 0 or 1");
         return COS_ERR_ARG;
@@ -156,7 +157,6 @@ extern "C" cos_status cos_connected_sum_subsets(int n_cfg, int n_max, const int3
         set_error(std::string(fn) + ": n_cfg * n_max exceeds the derived-problem limit 2^31 - 1");
         return COS_ERR_ARG;
     }
-    cudaStream_t s = (cudaStream_t)stream;
     std::string err;
     Workspace *ws = get_workspace(s, &err);
     if (!ws) {
@@ -175,8 +175,9 @@ extern "C" cos_status cos_connected_sum_subsets(int n_cfg, int n_max, const int3
     L.loop_weight = loop_weight;
     for (int l = 0; l < n_mat; ++l) {
         L.sigma[l] = h_sigma ? h_sigma[l] : 0.0;
-        if (L.sigma[l] != 0.0) L.shifts = true;
+        if (L.sigma[l] != 0.0 && !clow) L.shifts = true;
     }
+    L.clow = clow;
     L.precision = precision;
     L.csub = d_c;
     if (all_roots) {
@@ -219,4 +220,23 @@ extern "C" cos_status cos_connected_sum_subsets(int n_cfg, int n_max, const int3
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "subset exponential launch");
     return COS_OK;
+}
+
+}  // namespace cosdp
+
+using namespace cosdp;
+
+extern "C" cos_status cos_connected_sum_subsets(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                                                int n_mat, int loop_weight, const double *h_sigma,
+                                                const double *d_M, cos_precision precision, int all_roots,
+                                                double *d_c, double *d_a, cos_stream_t stream) {
+    return subsets_body("cos_connected_sum_subsets", n_cfg, n_max, d_order, d_moff, n_mat, loop_weight, h_sigma, d_M,
+                        precision, all_roots, d_c, d_a, false, (cudaStream_t)stream);
+}
+
+extern "C" cos_status cos_connected_det_subsets(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                                                const double *h_alpha, const double *d_M, cos_precision precision,
+                                                int all_roots, double *d_c, double *d_a, cos_stream_t stream) {
+    return subsets_body("cos_connected_det_subsets", n_cfg, n_max, d_order, d_moff, 2, 1, h_alpha, d_M, precision,
+                        all_roots, d_c, d_a, true, (cudaStream_t)stream);
 }

@@ -324,3 +324,59 @@ def test_det_grad_orders_11_12_euler():
         lhs = terms.sum() + float(np.dot(al, ga[c]))
         scale = np.abs(terms).sum() + float(np.abs(np.multiply(al, ga[c])).sum()) + 2 * n * abs(out[c])
         assert abs(lhs - 2 * n * out[c]) <= 1e-9 * scale, (c, n, lhs, 2 * n * out[c])
+
+
+# ------------------------------------------------------------------ every vertex subset
+
+def run_det_subsets(Ms, alpha, n_max=None, want_a=True, all_roots=True):
+    order = np.array([m.shape[-1] for m in Ms], dtype=np.int32)
+    moff = B.matrix_offsets(order, 2)
+    n_max = int(order.max()) if n_max is None else n_max
+    d_order = torch.tensor(order, device="cuda")
+    d_moff = torch.tensor(moff, device="cuda")
+    d_M = torch.tensor(np.concatenate([m.ravel() for m in Ms]), device="cuda")
+    per = 1 << n_max
+    c = torch.full((len(Ms) * per,), 12345.0, dtype=torch.float64, device="cuda")
+    a = torch.full_like(c, 12345.0) if want_a else None
+    B.cos_connected_det_subsets(n_max, d_order, d_moff, alpha, d_M, c, a, all_roots)
+    B.cos_sync_status()
+    return c.cpu().numpy().reshape(len(Ms), per), (a.cpu().numpy().reshape(len(Ms), per) if want_a else None)
+
+
+@pytest.mark.parametrize("orders,shifts", [([5, 5, 5], True), ([6, 3, 1, 4], False), ([7, 2], True)])
+def test_det_subsets_every_subset(orders, shifts):
+    """c(S) of every subset against Alg. 1 of the oracle on the principal sub-matrices, a(S)
+    against LU determinants (a route that never forms c)."""
+    al = [0.12, -0.07] if shifts else None
+    Ms = [rand_sq(8000 + 10 * c + n, 1, n)[0] for c, n in enumerate(orders)]
+    n_max = max(orders)
+    c_got, a_got = run_det_subsets(Ms, al, n_max)
+    for ci, M in enumerate(Ms):
+        n = M.shape[-1]
+        for S in range(1, 1 << n):
+            idx = [i for i in range(n) if S >> i & 1]
+            sub = np.ascontiguousarray(M[:, idx][:, :, idx])
+            ref = O.det_clow(sub, al, prec="q")
+            rmass = O.det_clow(sub, al, absmode=True)
+            assert abs(c_got[ci, S] - ref) <= bound("fp64", len(idx), rmass), (ci, S, c_got[ci, S], ref)
+            A = [sub[b] - (0.0 if al is None else al[b]) * np.eye(len(idx)) for b in range(2)]
+            aref = np.linalg.det(A[0]) * np.linalg.det(A[1])
+            assert abs(a_got[ci, S] - aref) <= 1e-11 * (abs(aref) + rmass), (ci, S, a_got[ci, S], aref)
+        assert a_got[ci, 0] == 1.0 and c_got[ci, 0] == 0.0
+        assert np.all(c_got[ci, 1 << n:] == 0.0) and np.all(a_got[ci, 1 << n:] == 0.0)
+
+
+def test_det_subsets_root0_only_and_full_value():
+    """all_roots = 0: the subsets containing vertex 0, from one sweep; c(V) equals the plain
+    determinant sweep bit for bit."""
+    Ms = rand_sq(8100, 6, 6)
+    al = [0.05, 0.02]
+    c_got, _ = run_det_subsets(Ms, al, want_a=False, all_roots=False)
+    plain, _ = run_square(Ms, al, abs_mass=False)
+    for ci, M in enumerate(Ms):
+        assert c_got[ci, 63] == plain[ci]
+        for S in (1, 3, 5, 33, 47):
+            idx = [i for i in range(6) if S >> i & 1]
+            sub = np.ascontiguousarray(M[:, idx][:, :, idx])
+            ref = O.det_clow(sub, al, prec="q")
+            assert abs(c_got[ci, S] - ref) <= bound("fp64", len(idx), O.det_clow(sub, al, absmode=True))
