@@ -80,8 +80,9 @@ def dist_env():
 
 # ------------------------------------------------------------------ CPU oracle (reported baseline)
 
-def oracle_values(w, cfgs, absmode=False):
-    """Oracle connected sums (numpy gather + C DP in double, OpenMP) of `cfgs` (one order)."""
+def oracle_values(w, cfgs, absmode=False, prec="d"):
+    """Oracle connected sums (numpy gather + C DP in double, or `prec`, OpenMP) of `cfgs` (one
+    order)."""
     import oracle as O
     from oracle import propagators as P
     model = w.model
@@ -91,7 +92,7 @@ def oracle_values(w, cfgs, absmode=False):
         tabs, wt, sig = tabs[:1], model.n_flavors, sig[:1]
     sig = sig if any(sig) else None
     Ms = np.stack(P.gather(tabs, cfgs, model.L, model.beta))
-    hi, lo, threads = O.dp_batch(Ms, sig, wt, absmode=absmode, nthreads=0)
+    hi, lo, threads = O.dp_batch(Ms, sig, wt, absmode=absmode, prec=prec, nthreads=0)
     return hi + lo, threads
 
 
@@ -413,6 +414,16 @@ def oracle_leg(w, budget, head_out, keep):
     acc = {"su4_n8_fp64_vs_oracle": error_stats(head_out[:n], vals, mass)}
     for name, (wname, got) in keep.items():
         wk = I.WORKLOADS[wname]
+        if name.endswith("_by_order"):
+            acc[name] = accuracy_by_order(wk, got[0], got[1])
+            continue
+        if name.endswith("_vs_oracle_ld"):
+            k = min(len(got), 64)
+            cfgs = I.workload_configs(wk, k)
+            ref, _ = oracle_values(wk, cfgs, prec="ld")
+            mass, _ = oracle_values(wk, cfgs, absmode=True)
+            acc[name] = error_stats(got[:k], ref, mass)
+            continue
         if wk.det:
             k = min(len(got), 8)
             cfgs = I.workload_configs(wk, k)
@@ -424,6 +435,47 @@ def oracle_leg(w, budget, head_out, keep):
         mass, _ = oracle_values(wk, cfgs, absmode=True)
         acc[name] = error_stats(got[:k], ref, mass)
     return base, acc
+
+
+def sample_by_order(w, n_total, per_order=8, span=4000):
+    """The first `per_order` configurations of each order within the first `span` of the
+    seeded stream: {n: indices}."""
+    cfgs = I.workload_configs(w, min(n_total, span))
+    return {n: [c for c in range(cfgs.n_cfg) if int(cfgs.order[c]) == n][:per_order]
+            for n in range(w.n_lo, w.n_hi + 1)}
+
+
+def gathered_matrices(torch, B, w, idx):
+    """The GPU gather's matrices [k][n_mat][n][n] of configurations idx (one order), so that
+    the oracle's DP runs on the very inputs of the GPU DP."""
+    cfgs = I.workload_configs(w, max(idx) + 1).subset(idx)
+    tabs = B.tables_for(w.model)
+    n_mat = tabs.info().n_mat
+    n = int(cfgs.order[0])
+    d = B.configs_to_device(cfgs)
+    moff = torch.as_tensor(B.matrix_offsets(cfgs.order, n_mat), device="cuda")
+    M = torch.empty(len(idx) * n_mat * n * n, dtype=torch.float64, device="cuda")
+    B.cos_gather(tabs, *d, moff, M)
+    B.cos_sync_status()
+    tabs.close()
+    return M.cpu().numpy().reshape(len(idx), n_mat, n, n)
+
+
+def accuracy_by_order(w, got, mats):
+    """FP64 error of an uneven-order batch per order n against the long-double oracle DP on
+    the same gathered matrices: the growth of the DP's cancellation error with the order."""
+    import oracle as O
+    sig = list(w.model.sigma)
+    wt = 1
+    if w.model.symmetric:
+        wt, sig = w.model.n_flavors, sig[:1]
+    sig = sig if any(sig) else None
+    out = {}
+    for n, (idx, Ms) in sorted(mats.items()):
+        hi, lo, _ = O.dp_batch(Ms, sig, wt, prec="ld", nthreads=0)
+        mass = O.dp_batch(Ms, sig, wt, absmode=True, nthreads=0)[0]
+        out[str(n)] = error_stats(np.asarray(got)[idx], hi + lo, mass)
+    return out
 
 
 def measure_adjoint(torch, B, flush_buf, n_cfg):
@@ -671,12 +723,16 @@ def measure_forms(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
     keep["su4_n8_mixed_vs_fp64_oracle"] = ("su4_mu_broken_n8", keep_n8)
     res["su3_shift_n10_mixed"], keep_n10 = run("su3_shift_mixed_n10", 100_000, "mixed")
     keep["su3_shift_n10_mixed_vs_fp64_oracle"] = ("su3_shift_mixed_n10", keep_n10)
-    res["su3_shift_n10_fp64"], _ = run("su3_shift_mixed_n10", 100_000, "fp64", steps=1)
+    res["su3_shift_n10_fp64"], keep_f10 = run("su3_shift_mixed_n10", 100_000, "fp64", steps=1)
+    keep["su3_shift_n10_fp64_vs_oracle_ld"] = ("su3_shift_mixed_n10", keep_f10)
     res["su4_n8_df64"], keep_df8 = run("su4_mu_broken_n8", 100_000, "df64")
     keep["su4_n8_df64_vs_fp64_oracle"] = ("su4_mu_broken_n8", keep_df8)
     res["su3_shift_n10_df64"], keep_df10 = run("su3_shift_mixed_n10", 100_000, "df64", steps=1)
     keep["su3_shift_n10_df64_vs_fp64_oracle"] = ("su3_shift_mixed_n10", keep_df10)
-    res["su6_uneven_n4_12_fp64_graph"], _ = run("su6_sym_uneven_n4_12", 200_000, "fp64", steps=1, graph=True)
+    res["su6_uneven_n4_12_fp64_graph"], keep_un = run("su6_sym_uneven_n4_12", 200_000, "fp64", steps=1, graph=True)
+    wu = I.WORKLOADS["su6_sym_uneven_n4_12"]
+    mats = {n: (idx, gathered_matrices(torch, B, wu, idx)) for n, idx in sample_by_order(wu, 200_000).items() if idx}
+    keep["su6_uneven_fp64_by_order"] = ("su6_sym_uneven_n4_12", (keep_un, mats))
     adj = measure_adjoint(torch, B, flush_buf, 50_000)
     adj["frac_fp64_peak"] = adj["grad_tflops"] * 1e12 / fp64_peak
     res["su4_n10_adjoint"] = adj
