@@ -650,6 +650,21 @@ def measure_det(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
     for k in ("det_fp64", "det_df64"):
         res[f"hc_su2_af_n8_{k}"] = {"configs": hc.n_cfg, "configs_per_s": hc.n_cfg / ht[k], "ms": ht[k] * 1e3,
                                     "cost_vs_cos_fp64": ht[k] / ht["cos_fp64"]}
+    # gradients of both bipartite sweeps (reverse sweep over every kept layer)
+    hg = torch.ones(hc.n_cfg, dtype=torch.float64, device="cuda")
+    gM4 = torch.empty_like(M4)
+    gs2 = torch.empty(hc.n_cfg, 2, 2, dtype=torch.float64, device="cuda")
+    gfns = {"cos_fp64": lambda: B.cos_connected_sum_bipartite_matrices_grad(8, hd[0], hmoff, 2, 1, None, M4, hg,
+                                                                            None, gM4, gs2),
+            "det_fp64": lambda: B.cos_connected_det_bipartite_matrices_grad(8, hd[0], hmoff, al, M4, hg, None,
+                                                                            gM4, gs2)}
+    for k, f in gfns.items():
+        f()
+        B.cos_sync_status()
+        tgk = statistics.mean(time_steps(torch, f, 1, lambda: flush_l2(flush_buf)))
+        B.cos_sync_status()
+        res[f"hc_su2_af_n8_{k.split('_')[0]}_grad_fp64"] = {"configs": hc.n_cfg, "grad_configs_per_s": hc.n_cfg / tgk,
+                                                           "ms": tgk * 1e3, "grad_overhead": tgk / ht[k]}
     return res, got
 
 

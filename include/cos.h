@@ -262,6 +262,18 @@ cos_status cos_connected_sum_bipartite_matrices(int n_cfg, int n_max, const int3
                                                 cos_precision precision, double *d_out,
                                                 double *d_abs_mass, cos_stream_t stream);
 
+/* Gradient of the bipartite sums by the reverse sweep (the forward sweep re-run with every
+ * layer kept, then walked backwards): d_gout[c] = dLoss/dc; d_out NULL or receives c;
+ * d_gM4 NULL or dLoss/dM4 (layout and offsets of d_M4); d_gsigma2 NULL or [n_cfg][n_mat][2]
+ * dLoss/dsigma_{l,s} (also at sigma = 0).  n_max <= 8 (three 2n x 2n matrices per lane in shared
+ * memory; COS_ERR_ORDER above); FP64.  Other arguments as
+ * cos_connected_sum_bipartite_matrices. */
+cos_status cos_connected_sum_bipartite_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
+                                                     const int64_t *d_moff, int n_mat, int loop_weight,
+                                                     const double *h_sigma2, const double *d_M4, const double *d_gout,
+                                                     double *d_out, double *d_gM4, double *d_gsigma2,
+                                                     cos_stream_t stream);
+
 /* Gather + bipartite DP from vertex coordinates (honeycomb tables; the loop weight is
  * n_flavors for symmetric tables, else 1). */
 cos_status cos_connected_sum_bipartite_batch(const cos_tables *tables, int n_cfg, int n_max,
@@ -316,6 +328,14 @@ cos_status cos_connected_det_bipartite_matrices(int n_cfg, int n_max, const int3
                                                 const int64_t *d_moff, const double *h_alpha2,
                                                 const double *d_M4, cos_precision precision,
                                                 double *d_out, double *d_abs_mass, cos_stream_t stream);
+
+/* Gradient of the bipartite determinant-weight sums (the adjoint of the Alg. 1 sweep):
+ * d_galpha2 NULL or [n_cfg][2][2] dLoss/dalpha_{b,s} (= minus the sublattice-s trace of
+ * dLoss/dM4_b); other outputs as cos_connected_sum_bipartite_matrices_grad; n_max <= 8, FP64. */
+cos_status cos_connected_det_bipartite_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
+                                                     const int64_t *d_moff, const double *h_alpha2,
+                                                     const double *d_M4, const double *d_gout, double *d_out,
+                                                     double *d_gM4, double *d_galpha2, cos_stream_t stream);
 
 /* ------------------------------------------------------------------ adjoint DP
  * Gradient of the connected sums by the reverse (adjoint) DP: the forward DP is re-run with

@@ -33,7 +33,8 @@ EXPORTS = [
     "cos_build_propagators_honeycomb", "cos_gather_bipartite", "cos_connected_sum_bipartite_matrices",
     "cos_connected_sum_bipartite_batch", "cos_bipartite_structure",
     "cos_connected_det_matrices", "cos_connected_det_bipartite_matrices", "cos_connected_det_matrices_grad",
-    "cos_connected_det_subsets",
+    "cos_connected_det_subsets", "cos_connected_sum_bipartite_matrices_grad",
+    "cos_connected_det_bipartite_matrices_grad",
     "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_sync_status", "cos_status_string",
     "cos_last_error", "cos_structure", "cos_peak_probe",
     "cos_plan_create_batch", "cos_plan_create_matrices", "cos_plan_launch", "cos_plan_status", "cos_plan_grid",
@@ -286,6 +287,35 @@ def cos_connected_det_bipartite_matrices(n_max: int, order, moff, alpha2, M4, pr
                                                       _ptr(moff, "i64"), al, _ptr(M4, "f64"), PRECISIONS[precision],
                                                       _ptr(out, "f64"), _ptr(abs_mass, "f64"), _stream(stream)),
            "cos_connected_det_bipartite_matrices")
+
+
+def _sig2(sigma2, n_mat):
+    if sigma2 is None:
+        return None
+    flat = [float(x) for row in sigma2 for x in row]
+    if len(flat) != 2 * n_mat:
+        raise ValueError("sigma2 / alpha2 must hold n_mat x 2 values")
+    return (ctypes.c_double * len(flat))(*flat)
+
+
+def cos_connected_sum_bipartite_matrices_grad(n_max: int, order, moff, n_mat: int, loop_weight: int, sigma2, M4,
+                                              gout, out=None, gM4=None, gsigma2=None, stream=None):
+    """Gradient of the bipartite sums: dLoss/dM4 (layout of M4) and dLoss/dsigma2 ([n_cfg][n_mat][2])."""
+    _check(lib().cos_connected_sum_bipartite_matrices_grad(int(order.numel()), int(n_max), _ptr(order, "i32"),
+                                                           _ptr(moff, "i64"), int(n_mat), int(loop_weight),
+                                                           _sig2(sigma2, n_mat), _ptr(M4, "f64"), _ptr(gout, "f64"),
+                                                           _ptr(out, "f64"), _ptr(gM4, "f64"), _ptr(gsigma2, "f64"),
+                                                           _stream(stream)), "cos_connected_sum_bipartite_matrices_grad")
+
+
+def cos_connected_det_bipartite_matrices_grad(n_max: int, order, moff, alpha2, M4, gout, out=None, gM4=None,
+                                              galpha2=None, stream=None):
+    """Gradient of the bipartite determinant-weight sums: dLoss/dM4 and dLoss/dalpha2 ([n_cfg][2][2])."""
+    _check(lib().cos_connected_det_bipartite_matrices_grad(int(order.numel()), int(n_max), _ptr(order, "i32"),
+                                                           _ptr(moff, "i64"), _sig2(alpha2, 2), _ptr(M4, "f64"),
+                                                           _ptr(gout, "f64"), _ptr(out, "f64"), _ptr(gM4, "f64"),
+                                                           _ptr(galpha2, "f64"), _stream(stream)),
+           "cos_connected_det_bipartite_matrices_grad")
 
 
 def cos_connected_sum_bipartite_batch(tables: Tables, n_max: int, order, offset, site, tau, precision: str, out,

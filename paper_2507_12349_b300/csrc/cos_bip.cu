@@ -657,6 +657,410 @@ cos_status bip_matrices_body(Workspace *ws, int n_cfg, int n_max, const int32_t 
     return run_bip(ws, L, d_abs_mass, stream);
 }
 
+// ------------------------------------------------------------------ reverse (adjoint) sweep
+// Gradient of the bipartite sums, the adjoint of the sweep above (as cos_adjoint.cu is of the
+// square one).  Per batch the CTA re-runs the forward sweep keeping every layer, then walks the
+// layers backwards with Obar = dc/dO:
+//   Obar(mu,h,s_h,v,s_v) = sum_q D_q Ms[(v,s_v)][(j_q,s_q)] + Cbar Md[(v,s_v)][(h,s_h)],
+//   dM[(v,s_v)][(j_q,s_q)] += D_q O,  dM[(v,s_v)][(h,s_h)] += sgn w Cbar O,
+// D_q = Obar of extension target q (the forward's target table), Cbar = the flavor sum of the
+// seed slot's Obar (or gout 2^(n-1) at the full mask).  Shift weights: the shifted diagonal
+// (v,s) -> (v,s) for half-visited v >= 1 gives dsigma_{l,s} -= D O, the shifted start
+// sgn 2 Obar(seed) at layer 1.  Determinant weights (CLOW): the Alg. 1 sweep, the k = 0 close
+// seeded block 1 only, Cbar(full) = gout, and dalpha_{b,s} = -sum_j dM_b[(j,s)][(j,s)].
+// Warps own endpoint vertices v (both sublattices): one writer per dM row, no atomics.
+// Shared memory holds Ms, Md and dM, 3 x 4 n^2 doubles per lane: orders <= 8.
+struct BipAdjArgs {
+    BipArgs f;
+    size_t store_elems;     // forward storage per CTA (every layer of n_max) * 32
+    size_t adj_slot_elems;  // one adjoint layer slot * 32
+    const double *gout;
+    double *gM;             // NULL or dLoss/dM4, layout of M4
+    double *gsig;           // NULL or [n_cfg][n_mat][2]
+};
+
+// Targets q in [Q0, Q1) of one endpoint (v, s_v): loads first, then the multiply-adds.
+template <int Q0, int Q1>
+__device__ __forceinline__ void bip_adj_chunk(const double *__restrict__ a1, const double *__restrict__ Ms,
+                                              double *__restrict__ dM, const TgtInfo &ti, uint32_t tslot, int vrow,
+                                              double o, int lane, double &ob, int qv, double &dv) {
+    constexpr int K = Q1 - Q0;
+    double D[K], Mv[K], G[K];
+    int cs[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        const uint32_t sl = __shfl_sync(0xFFFFFFFFu, tslot, Q0 + u);
+        const uint32_t meta = __shfl_sync(0xFFFFFFFFu, ti.meta, Q0 + u);
+        cs[u] = (int)(((meta >> 12) & 15u) * 2u + ((meta >> 8) & 1u)) * kLanes;
+        D[u] = a1[(size_t)sl * kLanes + lane];
+        Mv[u] = Ms[vrow + cs[u]];
+        G[u] = dM[vrow + cs[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        ob = fma(D[u], Mv[u], ob);
+        dM[vrow + cs[u]] = fma(D[u], o, G[u]);
+        dv = (Q0 + u == qv) ? D[u] : dv;   // register select
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void bip_adj_endpoint(const double *__restrict__ fsrc, double *__restrict__ aout,
+                                                 const double *__restrict__ a1, const double *__restrict__ Ms,
+                                                 const double *__restrict__ Md, double *__restrict__ dM,
+                                                 const TgtInfo &ti, uint32_t tslot, uint32_t slot, int vrow, int hc,
+                                                 int qv, double cbar, double gamma, int lane, double &dvout) {
+    constexpr int kSplit = 6;
+    const double o = fsrc[(size_t)slot * kLanes + lane];
+    double ob = 0.0, dv = 0.0;
+    if constexpr (NT == 0) {
+    } else if constexpr (NT <= kSplit) {
+        bip_adj_chunk<0, NT>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob, qv, dv);
+    } else if constexpr (NT <= 2 * kSplit) {
+        bip_adj_chunk<0, kSplit>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob, qv, dv);
+        bip_adj_chunk<kSplit, NT>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob, qv, dv);
+    } else {
+        bip_adj_chunk<0, kSplit>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob, qv, dv);
+        bip_adj_chunk<kSplit, 2 * kSplit>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob, qv, dv);
+        bip_adj_chunk<2 * kSplit, NT>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob, qv, dv);
+    }
+    dvout = qv >= 0 ? dv * o : 0.0;   // D O of the shifted-diagonal step (v,s) -> (v,s)
+    ob = fma(cbar, Md[vrow + hc], ob);
+    if ((__double_as_longlong(cbar) << 1) != 0) dM[vrow + hc] = fma(gamma, o, dM[vrow + hc]);
+    aout[(size_t)slot * kLanes + lane] = ob;
+}
+
+__device__ __forceinline__ void bip_adj_dispatch(int nT, const double *fsrc, double *aout, const double *a1,
+                                                 const double *Ms, const double *Md, double *dM, const TgtInfo &ti,
+                                                 uint32_t tslot, uint32_t slot, int vrow, int hc, int qv, double cbar,
+                                                 double gamma, int lane, double &dvout) {
+#define COS_BADJ(K)                                                                                            \
+    case K:                                                                                                    \
+        bip_adj_endpoint<K>(fsrc, aout, a1, Ms, Md, dM, ti, tslot, slot, vrow, hc, qv, cbar, gamma, lane, dvout); \
+        break;
+    switch (nT) {
+        COS_BADJ(0)
+        COS_BADJ(1)
+        COS_BADJ(2)
+        COS_BADJ(3)
+        COS_BADJ(4)
+        COS_BADJ(5)
+        COS_BADJ(6)
+        COS_BADJ(7)
+        COS_BADJ(8)
+        COS_BADJ(9)
+        COS_BADJ(10)
+        COS_BADJ(11)
+        COS_BADJ(12)
+        COS_BADJ(13)
+        COS_BADJ(14)
+        COS_BADJ(15)
+        COS_BADJ(16)
+        default:
+            break;
+    }
+#undef COS_BADJ
+}
+
+constexpr int kBipAdjMaxN = 8;
+
+template <bool CLOW>
+__global__ void __launch_bounds__(256, 1) dp_bip_adjoint_kernel(const __grid_constant__ BipAdjArgs a) {
+    extern __shared__ __align__(16) double smem_ba[];
+    __shared__ int s_batch;
+    __shared__ uint32_t s_base[2 * kBipAdjMaxN + 3];
+    __shared__ double s_red[8][2][kLanes];
+    const BipArgs &f = a.f;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int nsm = 4 * f.smem_n * f.smem_n * kLanes;
+    double *Ms = smem_ba;             // extension matrices (shifted diagonal)
+    double *Md = smem_ba + nsm;       // close matrices times sgn w
+    double *dM = smem_ba + 2 * nsm;   // dc/dM accumulators [(v,s)][(j,t)][lane]
+    double *store = reinterpret_cast<double *>(f.scratch) + (size_t)blockIdx.x * (a.store_elems + 2 * a.adj_slot_elems);
+    double *adj = store + a.store_elems;
+    const int nfl = f.nf_lanes;
+    const int lam = lane % nfl;
+    const int ci = lane / nfl;
+    const double sgn = -1.0;
+    double sig[2], seedsh[2];
+    for (int s2 = 0; s2 < 2; ++s2) {
+        sig[s2] = f.sigma2[lam][s2];
+        seedsh[s2] = sgn * 2.0 * sig[s2];
+    }
+    const bool shifts = f.shifts != 0 && !CLOW;
+    const bool sgrad = a.gsig != nullptr && !CLOW;   // dc/dsigma, also at sigma = 0
+    const double cfac = sgn * f.loop_weight;
+    const bool unit_weight = f.loop_weight == 1.0;
+    const int nbatch = *f.n_batches;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_batch = atomicAdd(f.queue, 1);
+        __syncthreads();
+        const int b = s_batch;
+        if (b >= nbatch) break;
+        const int4 bd = f.batches[b];
+        const int n = bd.x;
+        const int n2 = 2 * n;
+        const BipOrderTab &tab = f.tabs[n];
+        const bool active = (ci < bd.z) && (ci * nfl + nfl <= kLanes);
+        const int cfg = active ? f.batch_list[bd.y + ci] : -1;
+        const double *Mc = nullptr;
+        if (active) Mc = f.M + f.moff[cfg] + (size_t)lam * n2 * n2;
+        for (int e = warp; e < n2 * n2; e += nwarps) {
+            const double val = active ? Mc[e] : 0.0;
+            const int r = e / n2, c = e % n2;
+            if (CLOW) {
+                const double m = (r == c) ? val + sgn * sig[r & 1] : val;
+                Ms[e * kLanes + lane] = m;
+                Md[e * kLanes + lane] = cfac * m;
+            } else {
+                Ms[e * kLanes + lane] = ((r == c) && (r >= 2) && shifts) ? val + sgn * sig[r & 1] : val;
+                Md[e * kLanes + lane] = cfac * val;
+            }
+            dM[e * kLanes + lane] = 0.0;
+        }
+        if (threadIdx.x == 0) {
+            uint32_t run = 0;
+            for (int l = 0; l <= 2 * n + 2; ++l) {
+                s_base[l] = run;
+                if (l <= 2 * n) run += tab.layer_slots[l];
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (int s0 = 0; s0 < 2; ++s0) {
+                const uint32_t off = __ldg(tab.rank4 + 1 + s0);
+                store[(size_t)(s_base[1] + off + 3u * (uint32_t)s0) * kLanes + lane] = (CLOW && lam != 0) ? 0.0 : 1.0;
+            }
+        }
+        __syncthreads();
+        // forward sweep, every layer kept
+        for (int ell = 1; ell <= 2 * n; ++ell) {
+            const double *src = store + (size_t)s_base[ell] * kLanes;
+            double *dst1 = store + (size_t)s_base[ell + 1] * kLanes;
+            const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
+            for (uint32_t mi = warp; mi < cnt; mi += nwarps)
+                bip_mask<double, CLOW>(tab, first + mi, 0xFFFFFFFFu, ell, n, src, dst1, Ms, Md, lane, ci, nfl, seedsh,
+                                       shifts, active, lam, cfg, f.out, f.status, 0);
+            __syncthreads();
+        }
+        // reverse sweep: this warp's endpoint vertices, both sublattices
+        uint32_t own = 0u;
+        for (int v = warp; v < n; v += nwarps) own |= 1u << v;
+        const uint32_t full = (1u << n) - 1u;
+        const double gout = active ? a.gout[cfg] : 0.0;
+        double gs0 = 0.0, gs1 = 0.0;
+        for (int ell = 2 * n; ell >= 1; --ell) {
+            const double *fsrc = store + (size_t)s_base[ell] * kLanes;
+            double *aout = adj + (size_t)(ell & 1) * a.adj_slot_elems;
+            const double *a1 = adj + (size_t)((ell + 1) & 1) * a.adj_slot_elems;
+            const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
+            for (uint32_t mi = 0; mi < cnt && own; ++mi) {
+                const uint4 mk = __ldg(tab.masks + first + mi);
+                const uint32_t A = mk.x & 0xFFFFu;
+                if (!(A & own)) continue;
+                const uint32_t B = mk.x >> 16, S = mk.y, code = mk.z, off = mk.w;
+                const uint32_t ones = A & ~B;
+                const uint32_t H = head_set(B, ones);
+                const uint32_t J = full & ~B & (CLOW ? ~(ones & 1u) : 0xFFFFFFFFu);
+                const int nA = __popc(A);
+                const TgtInfo ti = bip_targets(A, B, S, J, code, tab.rank4, lane);
+                const int nT = __popc(J) + __popc(J & ~A);
+                double cbar = 0.0;
+                if (B == full) {
+                    cbar = CLOW ? gout : ldexp(gout, n - 1);
+                } else if (ones) {
+                    const int k = __ffs(ones) - 1;
+                    const uint32_t bk = 1u << k;
+                    const int sk = (int)((S >> k) & 1u);
+                    const uint32_t B1 = B | bk;
+                    const uint32_t code1 = code + (uint32_t)(2 - sk) * c_p4[k];
+                    const int hi1 = __popc(head_set(B1, A & ~B1) & (bk - 1u));
+                    const uint32_t off1 = __ldg(tab.rank4 + code1);
+                    const uint32_t ss = off1 + (uint32_t)(((hi1 * 2 + sk) * nA + __popc(A & (bk - 1u))) * 2 + sk);
+                    const double seed = a1[(size_t)ss * kLanes + lane];
+                    cbar = flavor_sum((CLOW && k == 0 && lam == 0) ? 0.0 : seed, nfl, ci);
+                    if (sgrad && ell == 1) {   // vertex 0's shifted start on sublattice S & 1
+                        if (S & 1u) gs1 = fma(sgn * 2.0, seed, gs1);
+                        else gs0 = fma(sgn * 2.0, seed, gs0);
+                    }
+                }
+                const double gamma = unit_weight ? neg(cbar) : cfac * cbar;
+                for (uint32_t hh = H; hh; hh &= hh - 1u) {
+                    const int h = __ffs(hh) - 1;
+                    const int hidx = __popc(H & ((1u << h) - 1u));
+                    const uint32_t Vrow = row_vmask(A, ones, h) & own;
+                    if (!Vrow) continue;
+                    const bool first_loop = (h == 0) && (ones & 1u);
+                    const int sh0 = first_loop ? (int)(S & 1u) : 0;
+                    const int sh1 = first_loop ? sh0 : 1;
+                    const uint32_t hlow = (1u << h) - 1u;
+                    const uint32_t ai1 = ti.meta & 15u, nA1 = (ti.meta >> 4) & 15u, sj1 = (ti.meta >> 8) & 1u;
+                    const uint32_t hi1 = (uint32_t)__popc((ti.meta >> 16) & hlow);
+                    for (int sh = sh0; sh <= sh1; ++sh) {
+                        const uint32_t rowbase = off + (uint32_t)((hidx * 2 + sh) * nA * 2);
+                        const uint32_t tslot = ti.off1 + ((hi1 * 2u + (uint32_t)sh) * nA1 + ai1) * 2u + sj1;
+                        const int hc = (h * 2 + sh) * kLanes;
+                        for (uint32_t vv = Vrow; vv; vv &= vv - 1u) {
+                            const int v = __ffs(vv) - 1;
+                            const uint32_t bv = 1u << v;
+                            const bool half = (ones & bv) != 0;
+                            const int sv0 = half ? (int)((S >> v) & 1u) : (v == h ? sh : 0);
+                            const int sv1 = (half || v == h) ? sv0 : 1;
+                            // a half-visited v >= 1 is its own extension target (index qv)
+                            const uint32_t below = bv - 1u;
+                            const int qv = (sgrad && half && v != 0) ? __popc(J & below) + __popc(J & ~A & below) : -1;
+                            for (int sv = sv0; sv <= sv1; ++sv) {
+                                const uint32_t slot = rowbase + (uint32_t)(__popc(A & below) * 2 + sv);
+                                const int vrow = (v * 2 + sv) * n2 * kLanes + lane;
+                                double dvo = 0.0;
+                                bip_adj_dispatch(nT, fsrc, aout, a1, Ms, Md, dM, ti, tslot, slot, vrow, hc, qv, cbar,
+                                                 gamma, lane, dvo);
+                                if (sv) gs1 -= dvo;
+                                else gs0 -= dvo;
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (active && a.gM) {
+            const int64_t gb = f.moff[cfg] + (int64_t)lam * n2 * n2;
+            for (int e = warp; e < n2 * n2; e += nwarps) a.gM[gb + e] = dM[e * kLanes + lane];
+        }
+        if (CLOW) {
+            if (a.gsig && warp == 0 && active) {   // dc/dalpha_{b,s} = -sum_j dc/dM_b[(j,s)][(j,s)]
+                double t0 = 0.0, t1 = 0.0;
+                for (int j = 0; j < n; ++j) {
+                    t0 += dM[((2 * j) * n2 + 2 * j) * kLanes + lane];
+                    t1 += dM[((2 * j + 1) * n2 + 2 * j + 1) * kLanes + lane];
+                }
+                a.gsig[((int64_t)cfg * nfl + lam) * 2] = -t0;
+                a.gsig[((int64_t)cfg * nfl + lam) * 2 + 1] = -t1;
+            }
+        } else if (a.gsig) {
+            s_red[warp][0][lane] = gs0;
+            s_red[warp][1][lane] = gs1;
+            __syncthreads();
+            if (warp == 0 && active) {
+                double t0 = 0.0, t1 = 0.0;
+                for (int w = 0; w < nwarps; ++w) {
+                    t0 += s_red[w][0][lane];
+                    t1 += s_red[w][1][lane];
+                }
+                a.gsig[((int64_t)cfg * nfl + lam) * 2] = t0;
+                a.gsig[((int64_t)cfg * nfl + lam) * 2 + 1] = t1;
+            }
+        }
+    }
+}
+
+static cos_status launch_bip_adjoint(Workspace *ws, const BipLaunch &L, const double *gout, double *gM,
+                                     double *gsig, cudaStream_t stream) {
+    std::string err;
+    const BipOrderTab *tabs = bip_device_orders(ws->device, &err);
+    if (!tabs) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    const BipHostOrder &ho = bip_host_order(L.n_max);
+    size_t total_slots = 0;
+    for (int l = 0; l <= 2 * L.n_max; ++l) total_slots += ho.layer_slots[l];
+    const size_t store_elems = total_slots * kLanes;
+    const size_t adj_slot_elems = (size_t)ho.max_slots * kLanes;
+    const size_t per_cta = (store_elems + 2 * adj_slot_elems) * sizeof(double);
+    const int warps = std::max(4, L.n_max);
+    const size_t smem = (size_t)3 * 4 * L.n_max * L.n_max * kLanes * sizeof(double);
+    auto kern = L.clow ? dp_bip_adjoint_kernel<true> : dp_bip_adjoint_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "bipartite adjoint smem attribute");
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
+    const int cpb = kLanes / L.n_mat;
+    const int max_batches = (L.n_cfg + cpb - 1) / cpb + COS_NMAX;
+    int grid = std::max(1, std::min(nsm, max_batches));
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+        const size_t avail = ws->scratch_bytes + (size_t)(0.85 * (double)free_b);
+        while (grid > 1 && (size_t)grid * per_cta > avail) grid = std::max(1, grid / 2);
+    }
+    ws->last_grid = grid;
+    cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "bipartite adjoint scratch");
+    if (st != COS_OK) return st;
+    BipAdjArgs a;
+    memset(&a, 0, sizeof a);
+    BipArgs &f = a.f;
+    f.tabs = tabs;
+    f.batches = ws->batches;
+    f.n_batches = ws->plan_counts + 64;
+    f.batch_list = ws->batch_list;
+    f.queue = ws->queue;
+    f.M = L.M;
+    f.moff = L.moff;
+    f.nf_lanes = L.n_mat;
+    f.loop_weight = (double)L.loop_weight;
+    memcpy(f.sigma2, L.sigma2, sizeof f.sigma2);
+    f.shifts = L.shifts ? 1 : 0;
+    f.scratch = ws->scratch;
+    f.slot_elems = adj_slot_elems;
+    f.smem_n = L.n_max;
+    f.out = L.out;
+    f.status = ws->status;
+    a.store_elems = store_elems;
+    a.adj_slot_elems = adj_slot_elems;
+    a.gout = gout;
+    a.gM = gM;
+    a.gsig = gsig;
+    e = cudaMemsetAsync(ws->queue, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+    kern<<<grid, warps * 32, smem, stream>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "bipartite adjoint launch");
+    return COS_OK;
+}
+
+static cos_status bip_grad_body(const char *fn, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                                int n_mat, int loop_weight, const double *h_sigma2, const double *d_M4,
+                                const double *d_gout, double *d_out, double *d_gM4, double *d_gsigma2, bool clow,
+                                cudaStream_t stream) {
+    cos_status st = check_bip(n_cfg, n_max, d_order, d_moff, n_mat, loop_weight, d_M4, COS_FP64, d_gout, fn);
+    if (st != COS_OK) return st;
+    if (n_max > kBipAdjMaxN) {
+        set_error(std::string(fn) + ": the bipartite gradient keeps three 2n x 2n matrices per lane in shared "
+                                    "memory: n_max <= 8");
+        return COS_ERR_ORDER;
+    }
+    if (n_cfg == 0) return COS_OK;
+    std::string err;
+    Workspace *ws = get_workspace(stream, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    BipLaunch L;
+    L.precision = COS_FP64;
+    L.clow = clow;
+    L.n_cfg = n_cfg;
+    L.n_max = n_max;
+    L.order = d_order;
+    L.M = d_M4;
+    L.moff = d_moff;
+    L.n_mat = n_mat;
+    L.loop_weight = loop_weight;
+    for (int l = 0; l < n_mat; ++l)
+        for (int s2 = 0; s2 < 2; ++s2) {
+            L.sigma2[l][s2] = h_sigma2 ? h_sigma2[l * 2 + s2] : 0.0;
+            if (L.sigma2[l][s2] != 0.0) L.shifts = true;
+        }
+    L.out = d_out;
+    st = launch_plan_batches(ws, n_cfg, n_max, d_order, kLanes / n_mat, stream);
+    if (st != COS_OK) return st;
+    return launch_bip_adjoint(ws, L, d_gout, d_gM4, d_gsigma2, stream);
+}
+
 }  // namespace cosdp
 
 using namespace cosdp;
@@ -707,4 +1111,22 @@ extern "C" cos_status cos_bipartite_structure(int n, cos_structure_info *info) {
     }
     *info = bip_host_order(n).info;
     return COS_OK;
+}
+
+extern "C" cos_status cos_connected_sum_bipartite_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
+                                                                const int64_t *d_moff, int n_mat, int loop_weight,
+                                                                const double *h_sigma2, const double *d_M4,
+                                                                const double *d_gout, double *d_out, double *d_gM4,
+                                                                double *d_gsigma2, cos_stream_t stream) {
+    return bip_grad_body("cos_connected_sum_bipartite_matrices_grad", n_cfg, n_max, d_order, d_moff, n_mat,
+                         loop_weight, h_sigma2, d_M4, d_gout, d_out, d_gM4, d_gsigma2, false, (cudaStream_t)stream);
+}
+
+extern "C" cos_status cos_connected_det_bipartite_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
+                                                                const int64_t *d_moff, const double *h_alpha2,
+                                                                const double *d_M4, const double *d_gout,
+                                                                double *d_out, double *d_gM4, double *d_galpha2,
+                                                                cos_stream_t stream) {
+    return bip_grad_body("cos_connected_det_bipartite_matrices_grad", n_cfg, n_max, d_order, d_moff, 2, 1, h_alpha2,
+                         d_M4, d_gout, d_out, d_gM4, d_galpha2, true, (cudaStream_t)stream);
 }

@@ -191,3 +191,122 @@ def test_workload_honeycomb_order8_sampled():
         rmass = O.bip(M4, s2, method="sum_dp", absmode=True)
         assert abs(got[c] - ref) <= max(1e-10 * abs(ref), bound(8, rmass)), (c, got[c], ref, rmass)
     tabs.close()
+
+
+# ------------------------------------------------------------------ gradient (reverse sweep)
+# c_bip is quadratic in every single M4 entry (per assignment a vertex-matrix entry is used at
+# most twice per cover; the determinant-weight sum is even linear), so central differences of
+# the __float128 oracle are exact up to rounding; dc/dsigma2 (dc/dalpha2) from an exact
+# polynomial fit; tolerance |err| <= 1e-9 (|ref| + largest reference entry).
+
+def run_bip_grad(M4s, n_mat, wt, s2, gout, det=False):
+    order = np.array([m.shape[1] for m in M4s], dtype=np.int32)
+    moff = B.bipartite_matrix_offsets(order, n_mat)
+    d_order = torch.tensor(order, device="cuda")
+    d_moff = torch.tensor(moff, device="cuda")
+    d_M = torch.tensor(np.concatenate([m.ravel() for m in M4s]), device="cuda")
+    nc = len(M4s)
+    out = torch.full((nc,), float("nan"), dtype=torch.float64, device="cuda")
+    gM = torch.full_like(d_M, float("nan"))
+    gs = torch.full((nc, n_mat, 2), float("nan"), dtype=torch.float64, device="cuda")
+    g = torch.tensor(gout, dtype=torch.float64, device="cuda")
+    if det:
+        B.cos_connected_det_bipartite_matrices_grad(int(order.max()), d_order, d_moff, s2, d_M, g, out, gM, gs)
+    else:
+        B.cos_connected_sum_bipartite_matrices_grad(int(order.max()), d_order, d_moff, n_mat, wt, s2, d_M, g, out,
+                                                    gM, gs)
+    B.cos_sync_status()
+    gm = gM.cpu().numpy()
+    return (out.cpu().numpy(), [gm[moff[c]:moff[c] + m.size].reshape(m.shape) for c, m in enumerate(M4s)],
+            gs.cpu().numpy())
+
+
+def _val(M4, s2, wt, det):
+    if det:
+        return O.det_clow(M4, s2, prec="q")
+    return O.bip(M4, s2, weight=wt, method="dp4", prec="q")
+
+
+def exact_dM4(M4, s2, wt, det, h=0.25):
+    g = np.zeros_like(M4)
+    for idx in np.ndindex(*M4.shape):
+        Mp = M4.copy(); Mp[idx] += h
+        Mm = M4.copy(); Mm[idx] -= h
+        g[idx] = (_val(Mp, s2, wt, det) - _val(Mm, s2, wt, det)) / (2 * h)
+    return g
+
+
+def exact_dsig2(M4, s2, wt, det):
+    n = M4.shape[1]
+    nf = M4.shape[0]
+    base = np.zeros((nf, 2)) if s2 is None else np.array(s2, dtype=np.float64)
+    out = np.zeros((nf, 2))
+    for l in range(nf):
+        for s in range(2):
+            hs = [0.05 * k for k in range(-n - 1, n + 2)]
+            vals = []
+            for h in hs:
+                t = base.copy(); t[l, s] += h
+                vals.append(_val(M4, t, wt, det))
+            out[l, s] = np.polyfit(hs, vals, n + 1)[-2]
+    return out
+
+
+def close_to(a, b, rel=1e-9):
+    scale = max(np.max(np.abs(b)), 1e-300)
+    return np.all(np.abs(a - b) <= rel * (np.abs(b) + scale))
+
+
+@pytest.mark.parametrize("n,n_mat,wt,shifts,ncfg,det", [
+    (1, 2, 1, True, 3, False), (2, 1, 2, False, 5, False), (3, 2, 1, True, 7, False), (4, 2, 1, False, 3, False),
+    (1, 2, 1, True, 3, True), (2, 2, 1, False, 5, True), (3, 2, 1, True, 4, True), (4, 2, 1, True, 3, True),
+])
+def test_bipartite_grad_vs_exact_differences(n, n_mat, wt, shifts, ncfg, det):
+    M4s = rand_m4(9000 + 10 * n + n_mat + (100 if det else 0), ncfg, n_mat, n)
+    s2 = [[0.08 - 0.05 * l, -0.06 + 0.04 * l] for l in range(n_mat)] if shifts else None
+    gout = np.linspace(0.5, 1.5, ncfg)
+    out, gM, gs = run_bip_grad(M4s, n_mat, wt, s2, gout, det)
+    for c in sorted({0, ncfg - 1}):
+        ref = _val(M4s[c], s2, wt, det)
+        rmass = (O.det_clow(M4s[c], s2, absmode=True) if det
+                 else O.bip(M4s[c], s2, weight=wt, method="sum_dp", absmode=True))
+        assert abs(out[c] - ref) <= bound(n, rmass)
+        dM = gout[c] * exact_dM4(M4s[c], s2, wt, det)
+        assert close_to(gM[c], dM), c
+        assert close_to(gs[c], gout[c] * exact_dsig2(M4s[c], s2, wt, det), rel=1e-7), c
+        if det:   # dc/dalpha_{b,s} = -sum_j dc/dM4_b[j,s,j,s]
+            tr = np.array([[np.trace(dM[b, :, s, :, s]) for s in range(2)] for b in range(2)])
+            assert close_to(gs[c], -tr), c
+
+
+@pytest.mark.parametrize("det", [False, True])
+def test_bipartite_grad_orders_7_8_euler(det):
+    """Orders 7 and 8: c(t M4, t sigma2) = t^(2n) c gives sum M4 dc/dM4 + sum sigma2 dc/dsigma2 = 2n c;
+    the forward value equals the bipartite sweep's bit for bit."""
+    orders = [8, 7, 8]
+    s2 = [[0.07, -0.03], [0.02, 0.05]]
+    M4s = [rand_m4(9500 + c, 1, 2, n)[0] for c, n in enumerate(orders)]
+    out, gM, gs = run_bip_grad(M4s, 2, 1, s2, np.ones(len(M4s)), det)
+    order = np.array(orders, dtype=np.int32)
+    moff = B.bipartite_matrix_offsets(order, 2)
+    ref = torch.empty(len(M4s), dtype=torch.float64, device="cuda")
+    args = (8, torch.tensor(order, device="cuda"), torch.tensor(moff, device="cuda"))
+    d_M = torch.tensor(np.concatenate([m.ravel() for m in M4s]), device="cuda")
+    if det:
+        B.cos_connected_det_bipartite_matrices(*args, s2, d_M, "fp64", ref)
+    else:
+        B.cos_connected_sum_bipartite_matrices(*args, 2, 1, s2, d_M, "fp64", ref)
+    B.cos_sync_status()
+    assert np.array_equal(out, ref.cpu().numpy())
+    for c, n in enumerate(orders):
+        terms = M4s[c] * gM[c]
+        lhs = terms.sum() + float((np.array(s2) * gs[c]).sum())
+        scale = np.abs(terms).sum() + float(np.abs(np.array(s2) * gs[c]).sum()) + 2 * n * abs(out[c])
+        assert abs(lhs - 2 * n * out[c]) <= 1e-9 * scale, (c, n, lhs, 2 * n * out[c])
+
+
+def test_bipartite_grad_rejects_order9():
+    M4s = rand_m4(1, 1, 2, 9)
+    with pytest.raises(B.CosError) as e:
+        run_bip_grad(M4s, 2, 1, None, np.ones(1))
+    assert e.value.status == -2
