@@ -668,8 +668,9 @@ cos_status bip_matrices_body(Workspace *ws, int n_cfg, int n_max, const int32_t 
 // (v,s) -> (v,s) for half-visited v >= 1 gives dsigma_{l,s} -= D O, the shifted start
 // sgn 2 Obar(seed) at layer 1.  Determinant weights (CLOW): the Alg. 1 sweep, the k = 0 close
 // seeded block 1 only, Cbar(full) = gout, and dalpha_{b,s} = -sum_j dM_b[(j,s)][(j,s)].
-// Warps own endpoint vertices v (both sublattices): one writer per dM row, no atomics.
-// Shared memory holds Ms, Md and dM, 3 x 4 n^2 doubles per lane: orders <= 8.
+// Warps own endpoint units (v, s_v), unit v * 2 + s_v modulo the warp count (2n warps, at most
+// 16): one writer per dM row, no atomics.  Shared memory holds Ms, Md and dM, 3 x 4 n^2 doubles
+// per lane, so one CTA per SM: orders <= 8.
 struct BipAdjArgs {
     BipArgs f;
     size_t store_elems;     // forward storage per CTA (every layer of n_max) * 32
@@ -765,11 +766,11 @@ __device__ __forceinline__ void bip_adj_dispatch(int nT, const double *fsrc, dou
 constexpr int kBipAdjMaxN = 8;
 
 template <bool CLOW>
-__global__ void __launch_bounds__(256, 1) dp_bip_adjoint_kernel(const __grid_constant__ BipAdjArgs a) {
+__global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_constant__ BipAdjArgs a) {
     extern __shared__ __align__(16) double smem_ba[];
     __shared__ int s_batch;
     __shared__ uint32_t s_base[2 * kBipAdjMaxN + 3];
-    __shared__ double s_red[8][2][kLanes];
+    __shared__ double s_red[16][2][kLanes];
     const BipArgs &f = a.f;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -846,9 +847,12 @@ __global__ void __launch_bounds__(256, 1) dp_bip_adjoint_kernel(const __grid_con
                                        shifts, active, lam, cfg, f.out, f.status, 0);
             __syncthreads();
         }
-        // reverse sweep: this warp's endpoint vertices, both sublattices
-        uint32_t own = 0u;
-        for (int v = warp; v < n; v += nwarps) own |= 1u << v;
+        // reverse sweep: this warp's endpoint units (v, s_v); own = vertices with an owned unit
+        uint32_t own2 = 0u, own = 0u;
+        for (int u = warp; u < n2; u += nwarps) {
+            own2 |= 1u << u;
+            own |= 1u << (u >> 1);
+        }
         const uint32_t full = (1u << n) - 1u;
         const double gout = active ? a.gout[cfg] : 0.0;
         double gs0 = 0.0, gs1 = 0.0;
@@ -882,7 +886,8 @@ __global__ void __launch_bounds__(256, 1) dp_bip_adjoint_kernel(const __grid_con
                     const uint32_t ss = off1 + (uint32_t)(((hi1 * 2 + sk) * nA + __popc(A & (bk - 1u))) * 2 + sk);
                     const double seed = a1[(size_t)ss * kLanes + lane];
                     cbar = flavor_sum((CLOW && k == 0 && lam == 0) ? 0.0 : seed, nfl, ci);
-                    if (sgrad && ell == 1) {   // vertex 0's shifted start on sublattice S & 1
+                    // vertex 0's shifted start on sublattice S & 1, once: by the owner of that unit
+                    if (sgrad && ell == 1 && ((own2 >> (S & 1u)) & 1u)) {
                         if (S & 1u) gs1 = fma(sgn * 2.0, seed, gs1);
                         else gs0 = fma(sgn * 2.0, seed, gs0);
                     }
@@ -913,6 +918,7 @@ __global__ void __launch_bounds__(256, 1) dp_bip_adjoint_kernel(const __grid_con
                             const uint32_t below = bv - 1u;
                             const int qv = (sgrad && half && v != 0) ? __popc(J & below) + __popc(J & ~A & below) : -1;
                             for (int sv = sv0; sv <= sv1; ++sv) {
+                                if (!((own2 >> (v * 2 + sv)) & 1u)) continue;
                                 const uint32_t slot = rowbase + (uint32_t)(__popc(A & below) * 2 + sv);
                                 const int vrow = (v * 2 + sv) * n2 * kLanes + lane;
                                 double dvo = 0.0;
@@ -972,7 +978,7 @@ static cos_status launch_bip_adjoint(Workspace *ws, const BipLaunch &L, const do
     const size_t store_elems = total_slots * kLanes;
     const size_t adj_slot_elems = (size_t)ho.max_slots * kLanes;
     const size_t per_cta = (store_elems + 2 * adj_slot_elems) * sizeof(double);
-    const int warps = std::max(4, L.n_max);
+    const int warps = std::min(16, std::max(4, 2 * L.n_max));
     const size_t smem = (size_t)3 * 4 * L.n_max * L.n_max * kLanes * sizeof(double);
     auto kern = L.clow ? dp_bip_adjoint_kernel<true> : dp_bip_adjoint_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
