@@ -59,13 +59,14 @@ struct CloseOf<df64> {
     using type = df64;
 };
 
-// Register budgets: MAXT = 256 (two CTAs of up to 8 warps, <= 128 registers), MAXT = 384 (up to
-// 12 warps; FP32 two CTAs, <= 85 registers) and MAXT = 512 (up to 16 warps; <= 128 registers in
-// FP64 with one CTA, <= 64 in FP32 with two).
+// Register budgets: MAXT = 256 (two CTAs of up to 8 warps, <= 128 registers), MAXT = 320 (FP64:
+// two CTAs of up to 10 warps, <= 96 registers), MAXT = 384 (up to 12 warps; FP32 two CTAs, <= 85
+// registers) and MAXT = 512 (up to 16 warps; <= 128 registers in FP64 with one CTA, <= 64 in FP32
+// with two).
 // SUB: all-subsets mode (closes of masks with no half-visited vertex stored through csub_key).
 // CLOW: determinant weights without cycle factors (two spin-block lanes per configuration).
 template <typename T, int MAXT, bool SUB, bool CLOW = false>
-__global__ void __launch_bounds__(MAXT, (MAXT == 256 || sizeof(T) == 4) ? 2 : 1)
+__global__ void __launch_bounds__(MAXT, (MAXT <= 320 || sizeof(T) == 4) ? 2 : 1)
     dp_forward_kernel(const __grid_constant__ DpArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_batch;
@@ -234,9 +235,12 @@ cos_status launch_plan_batches(Workspace *ws, int n_cfg, int n_max, const int32_
 
 template <typename T, bool SUB, bool CLOW = false>
 static auto forward_kernel_for(int threads) {
-    return threads <= 256 ? dp_forward_kernel<T, 256, SUB, CLOW>
-                          : (threads <= 384 ? dp_forward_kernel<T, 384, SUB, CLOW>
-                                            : dp_forward_kernel<T, 512, SUB, CLOW>);
+    if (threads <= 256) return dp_forward_kernel<T, 256, SUB, CLOW>;
+    // FP64 CoS sweep: two CTAs of up to 10 warps (<= 96 registers)
+    if constexpr (std::is_same<T, double>::value && !SUB && !CLOW) {
+        if (threads <= 320) return dp_forward_kernel<T, 320, SUB, CLOW>;
+    }
+    return threads <= 384 ? dp_forward_kernel<T, 384, SUB, CLOW> : dp_forward_kernel<T, 512, SUB, CLOW>;
 }
 
 // Determinant weights (L.clow) reach this launcher in FP64 only: the reduced precisions run
