@@ -35,11 +35,11 @@ WORKLOAD = "su4_mu_broken_n8"
 METRIC = "connected-sum configs/s at order n (FP64 vs mixed), roofline fraction, grad overhead"
 UNIT = "configs/s"
 NOMINAL_FP64_TFLOPS = 1.25
-# DRAM bytes (read + write) of dp_forward_kernel<double> per configuration of the headline
+# DRAM bytes (read + write) of dp_forward_kernel<double, 320> per configuration of the headline
 # workload: ncu dram__bytes_read.sum + dram__bytes_write.sum on a 5 000-configuration launch
-# (8.617 GB + 7.107 GB, profiles/dp_forward_fp64_su4_n8.md); traffic grows in proportion
+# (8.917 GB + 7.099 GB, profiles/dp_forward_fp64_su4_n8.md); traffic grows in proportion
 # to the configurations of a launch.
-HEADLINE_DRAM_BYTES_PER_CFG = (8.616600e9 + 7.107427e9) / 5000
+HEADLINE_DRAM_BYTES_PER_CFG = (8.917352e9 + 7.098890e9) / 5000
 FP64_FMA_PER_CLK_SM = 2.0
 
 
