@@ -6,6 +6,10 @@
 * ``connected_sum_model(mu, alpha, model, configs)``: connected sums from
   vertex coordinates; backward = adjoint DP + chain rule through the
   propagator tables, giving dLoss/dmu_l and dLoss/dalpha_l.
+* ``connected_det(M, alpha, ...)``: SU(2) determinant-weight sums (the DP without
+  cycle factors of Alg. 1); backward = its reverse sweep, dLoss/dM and dLoss/dalpha.
+* ``connected_sum_bipartite(M4, sigma2, ...)`` and ``connected_det_bipartite(M4,
+  alpha2, ...)``: the bipartite sums; backward = the bipartite reverse sweep.
 
 PyTorch only holds tensors and streams here; every arithmetic step runs in the
 CUDA kernels (no host fallback).
@@ -79,3 +83,87 @@ def connected_sum_model(mu, alpha, model, d_cfgs, n_max: int):
     """Connected sums from vertex coordinates for chemical potentials mu and shifts alpha
     (CPU tensors of n_flavors values, differentiable); other model fields from `model`."""
     return _ConnectedSumModel.apply(mu, alpha, model, d_cfgs, n_max)
+
+
+def _host_list(t):
+    return None if t is None else [float(x) for x in t.detach().cpu().reshape(-1)]
+
+
+def _host_rows(t):
+    return None if t is None else [[float(x) for x in row] for row in t.detach().cpu().reshape(-1, 2)]
+
+
+class _ConnectedDet(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, M, alpha, order, moff, n_max):
+        al = _host_list(alpha)
+        out = torch.empty(order.numel(), dtype=torch.float64, device=M.device)
+        B.cos_connected_det_matrices(n_max, order, moff, al, M.detach().contiguous(), "fp64", out)
+        ctx.save_for_backward(M, order, moff)
+        ctx.al = al
+        ctx.alpha_shape = None if alpha is None else alpha.shape
+        ctx.n_max = n_max
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        M, order, moff = ctx.saved_tensors
+        gM = torch.zeros_like(M)
+        need_al = ctx.alpha_shape is not None and ctx.needs_input_grad[1]
+        gal = torch.zeros(order.numel(), 2, dtype=torch.float64, device=M.device) if need_al else None
+        B.cos_connected_det_matrices_grad(ctx.n_max, order, moff, ctx.al, M.detach().contiguous(),
+                                          gout.detach().to(torch.float64).contiguous(), None, gM, gal)
+        ga = gal.sum(0).to("cpu").reshape(ctx.alpha_shape) if need_al else None
+        return gM, ga, None, None, None
+
+
+def connected_det(M, alpha, order, moff, n_max: int):
+    """SU(2) determinant-weight connected sums of packed spin blocks M (flat, [2][n][n] at
+    moff[cfg]); alpha: CPU tensor of the two diagonal shifts (may require grad) or None."""
+    return _ConnectedDet.apply(M, alpha, order, moff, n_max)
+
+
+class _ConnectedBipartite(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, M4, sig2, order, moff, n_max, n_mat, loop_weight, det):
+        s2 = _host_rows(sig2)
+        out = torch.empty(order.numel(), dtype=torch.float64, device=M4.device)
+        if det:
+            B.cos_connected_det_bipartite_matrices(n_max, order, moff, s2, M4.detach().contiguous(), "fp64", out)
+        else:
+            B.cos_connected_sum_bipartite_matrices(n_max, order, moff, n_mat, loop_weight, s2,
+                                                   M4.detach().contiguous(), "fp64", out)
+        ctx.save_for_backward(M4, order, moff)
+        ctx.s2 = s2
+        ctx.sig_shape = None if sig2 is None else sig2.shape
+        ctx.args = (n_max, n_mat, loop_weight, det)
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        M4, order, moff = ctx.saved_tensors
+        n_max, n_mat, loop_weight, det = ctx.args
+        gM = torch.zeros_like(M4)
+        need_s = ctx.sig_shape is not None and ctx.needs_input_grad[1]
+        gs = torch.zeros(order.numel(), n_mat, 2, dtype=torch.float64, device=M4.device) if need_s else None
+        g = gout.detach().to(torch.float64).contiguous()
+        if det:
+            B.cos_connected_det_bipartite_matrices_grad(n_max, order, moff, ctx.s2, M4.detach().contiguous(), g,
+                                                        None, gM, gs)
+        else:
+            B.cos_connected_sum_bipartite_matrices_grad(n_max, order, moff, n_mat, loop_weight, ctx.s2,
+                                                        M4.detach().contiguous(), g, None, gM, gs)
+        gsig = gs.sum(0).to("cpu").reshape(ctx.sig_shape) if need_s else None
+        return gM, gsig, None, None, None, None, None, None
+
+
+def connected_sum_bipartite(M4, sigma2, order, moff, n_max: int, n_mat: int, loop_weight: int = 1):
+    """Bipartite connected sums of packed M4 blocks ([n_mat][2n][2n] at moff[cfg]); sigma2: CPU
+    tensor [n_mat][2] of shift weights (may require grad) or None.  Orders <= 8 for the gradient."""
+    return _ConnectedBipartite.apply(M4, sigma2, order, moff, n_max, n_mat, loop_weight, False)
+
+
+def connected_det_bipartite(M4, alpha2, order, moff, n_max: int):
+    """Bipartite SU(2) determinant-weight sums of packed M4 blocks ([2][2n][2n] at moff[cfg]);
+    alpha2: CPU tensor [2][2] of diagonal shifts (may require grad) or None."""
+    return _ConnectedBipartite.apply(M4, alpha2, order, moff, n_max, 2, 1, True)

@@ -13,6 +13,7 @@ torch = pytest.importorskip("torch")
 
 import oracle as O
 from oracle import honeycomb as HC
+from paper_2507_12349_b300 import autograd as AG
 from paper_2507_12349_b300 import binding as B
 from paper_2507_12349_b300 import inputs as I
 
@@ -310,3 +311,25 @@ def test_bipartite_grad_rejects_order9():
     with pytest.raises(B.CosError) as e:
         run_bip_grad(M4s, 2, 1, None, np.ones(1))
     assert e.value.status == -2
+
+
+@pytest.mark.parametrize("det", [False, True])
+def test_bipartite_autograd_function(det):
+    """torch.autograd through the bipartite sums equals the reverse sweep's gradient, weighted."""
+    M4s = rand_m4(9700 + int(det), 4, 2, 4)
+    order = np.array([4] * 4, dtype=np.int32)
+    moff = B.bipartite_matrix_offsets(order, 2)
+    M4 = torch.tensor(np.concatenate([m.ravel() for m in M4s]), device="cuda", requires_grad=True)
+    s2v = [[0.06, -0.02], [0.03, 0.05]]
+    s2 = torch.tensor(s2v, dtype=torch.float64, requires_grad=True)
+    w = torch.linspace(0.5, 1.5, 4, dtype=torch.float64, device="cuda")
+    d_order, d_moff = torch.tensor(order, device="cuda"), torch.tensor(moff, device="cuda")
+    if det:
+        c = AG.connected_det_bipartite(M4, s2, d_order, d_moff, 4)
+    else:
+        c = AG.connected_sum_bipartite(M4, s2, d_order, d_moff, 4, 2, 1)
+    (c * w).sum().backward()
+    out, gM, gs = run_bip_grad(M4s, 2, 1, s2v, w.cpu().numpy(), det)
+    assert np.array_equal(c.detach().cpu().numpy(), out)
+    assert np.array_equal(M4.grad.cpu().numpy(), np.concatenate([g.ravel() for g in gM]))
+    assert np.allclose(s2.grad.numpy(), gs.sum(0), rtol=1e-14, atol=0)

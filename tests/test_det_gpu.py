@@ -27,6 +27,7 @@ torch = pytest.importorskip("torch")
 import oracle as O
 from oracle import honeycomb as HC
 from oracle import propagators as P
+from paper_2507_12349_b300 import autograd as AG
 from paper_2507_12349_b300 import binding as B
 from paper_2507_12349_b300 import inputs as I
 
@@ -380,3 +381,19 @@ def test_det_subsets_root0_only_and_full_value():
             sub = np.ascontiguousarray(M[:, idx][:, :, idx])
             ref = O.det_clow(sub, al, prec="q")
             assert abs(c_got[ci, S] - ref) <= bound("fp64", len(idx), O.det_clow(sub, al, absmode=True))
+
+
+def test_det_autograd_function():
+    """torch.autograd through connected_det equals the reverse sweep's gradient, weighted."""
+    Ms = rand_sq(8300, 5, 5)
+    order = np.array([5] * 5, dtype=np.int32)
+    moff = B.matrix_offsets(order, 2)
+    M = torch.tensor(np.concatenate([m.ravel() for m in Ms]), device="cuda", requires_grad=True)
+    al = torch.tensor([0.1, -0.05], dtype=torch.float64, requires_grad=True)
+    w = torch.linspace(0.5, 1.5, 5, dtype=torch.float64, device="cuda")
+    c = AG.connected_det(M, al, torch.tensor(order, device="cuda"), torch.tensor(moff, device="cuda"), 5)
+    (c * w).sum().backward()
+    out, gM, ga = run_grad(Ms, [0.1, -0.05], w.cpu().numpy())
+    assert np.array_equal(c.detach().cpu().numpy(), out)
+    assert np.allclose(M.grad.cpu().numpy(), np.concatenate([g.ravel() for g in gM]), rtol=0, atol=0)
+    assert np.allclose(al.grad.numpy(), ga.sum(0), rtol=1e-14, atol=0)
