@@ -235,10 +235,10 @@ def time_steps(torch, fn, steps, flush):
 def native_arm(args):
     import torch
     rank, world, local = dist_env()
+    torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2507_12349_b300 import binding as B
     B.lib()
 
@@ -346,10 +346,16 @@ def native_arm(args):
     B.cos_sync_status()
     h2d = sum(x.numel() * x.element_size() for x in (h_order, h_offset, h_site, h_tau))
     d2h = h_out.numel() * h_out.element_size()
-    e2e_value = world * n_cfg / statistics.mean(e2e_times)
+    e2e_mean = statistics.mean(e2e_times)
+    if world > 1:   # the job's end-to-end time is the slowest rank's
+        te = torch.tensor([e2e_mean], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        e2e_mean = float(te.item())
+    e2e_value = world * n_cfg / e2e_mean
     head_out = out.cpu().numpy()
     extras, keep = {}, {}
-    if not args.no_extras and rank == 0:
+    # the other forms and the CPU baseline are single-GPU measurements (N = 1 only)
+    if not args.no_extras and world == 1:
         extras, keep = measure_forms(torch, B, flush_buf, fp64_peak, sms * 128 * clk * 1e6)
 
     launches_per_step = 1 + 4 + 1   # gather, 4 planner kernels, DP
@@ -383,7 +389,7 @@ def native_arm(args):
     if extras:
         line["forms"] = extras
     if rank == 0:
-        if not args.no_cpu:
+        if not args.no_cpu and world == 1:
             line["cpu_baseline"], line["accuracy"] = oracle_leg(w, args.cpu_seconds, head_out, keep)
         print(json.dumps(line), flush=True)
     if world > 1:
