@@ -236,8 +236,8 @@ cos_status launch_plan_batches(Workspace *ws, int n_cfg, int n_max, const int32_
 template <typename T, bool SUB, bool CLOW = false>
 static auto forward_kernel_for(int threads) {
     if (threads <= 256) return dp_forward_kernel<T, 256, SUB, CLOW>;
-    // FP64 sweeps (CoS and determinant weights): two CTAs of up to 10 warps (<= 96 registers)
-    if constexpr (std::is_same<T, double>::value && !SUB) {
+    // FP64 sweeps (every mode): two CTAs of up to 10 warps (<= 96 registers)
+    if constexpr (std::is_same<T, double>::value) {
         if (threads <= 320) return dp_forward_kernel<T, 320, SUB, CLOW>;
     }
     return threads <= 384 ? dp_forward_kernel<T, 384, SUB, CLOW> : dp_forward_kernel<T, 512, SUB, CLOW>;
