@@ -646,6 +646,7 @@ def measure_det(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
     al = [list(r) for r in hw.model.sigma2]
     hfns = {"det_fp64": lambda: B.cos_connected_det_bipartite_matrices(8, hd[0], hmoff, al, M4, "fp64", hout),
             "det_df64": lambda: B.cos_connected_det_bipartite_matrices(8, hd[0], hmoff, al, M4, "df64", hout),
+            "det_mixed": lambda: B.cos_connected_det_bipartite_matrices(8, hd[0], hmoff, al, M4, "mixed", hout),
             "cos_fp64": lambda: B.cos_connected_sum_bipartite_matrices(8, hd[0], hmoff, 2, 1, None, M4, "fp64", hout)}
     for f in hfns.values():
         f()
@@ -653,7 +654,7 @@ def measure_det(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
     ht = {k: statistics.mean(time_steps(torch, f, 2, lambda: flush_l2(flush_buf))) for k, f in hfns.items()}
     B.cos_sync_status()
     htabs.close()
-    for k in ("det_fp64", "det_df64"):
+    for k in ("det_fp64", "det_df64", "det_mixed"):
         res[f"hc_su2_af_n8_{k}"] = {"configs": hc.n_cfg, "configs_per_s": hc.n_cfg / ht[k], "ms": ht[k] * 1e3,
                                     "cost_vs_cos_fp64": ht[k] / ht["cos_fp64"]}
     # gradients of both bipartite sweeps (reverse sweep over every kept layer)
@@ -764,6 +765,8 @@ def measure_forms(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
     hd = measure_bipartite(torch, B, flush_buf, I.WORKLOADS["hc_su2_af_n8"].n_cfg, "df64")
     hd["frac_fp32_floor"] = hd["tflops"] * 1e12 / 2.0 * DF64_FP32_PER_TERM / fp32_lane_ops
     res["hc_su2_af_n8_bipartite_df64"] = hd
+    res["hc_su2_af_n8_bipartite_mixed"] = measure_bipartite(torch, B, flush_buf, I.WORKLOADS["hc_su2_af_n8"].n_cfg,
+                                                            "mixed")
     det, det_out = measure_det(torch, B, flush_buf, fp64_peak, fp32_lane_ops)
     res.update(det)
     keep["su2_zeeman_n10_det_fp64_vs_oracle"] = ("su2_zeeman_det_n10", det_out)

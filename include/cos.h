@@ -253,8 +253,8 @@ cos_status cos_gather_bipartite(const cos_tables *tables, int n_cfg, const int32
 
 /* Bipartite connected sums of explicit matrices: d_M4 as written by cos_gather_bipartite
  * (blocks [n_mat][2 n_c][2 n_c] at d_moff[c]); h_sigma2 = NULL or host [n_mat][2] shift weights
- * per (flavor, sublattice).  n_max <= COS_BIP_NMAX; precision COS_FP64 or COS_DF64
- * (COS_ERR_UNIMPLEMENTED for COS_MIXED).  Other arguments, outputs and errors as
+ * per (flavor, sublattice).  n_max <= COS_BIP_NMAX; precision COS_FP64, COS_MIXED (FP32
+ * extension, FP64 close, as on the square lattice) or COS_DF64.  Other arguments, outputs and errors as
  * cos_connected_sum_matrices (d_abs_mass: the same DP on |M4|, |sigma| with all signs +). */
 cos_status cos_connected_sum_bipartite_matrices(int n_cfg, int n_max, const int32_t *d_order,
                                                 const int64_t *d_moff, int n_mat, int loop_weight,
@@ -322,7 +322,7 @@ cos_status cos_connected_det_subsets(int n_cfg, int n_max, const int32_t *d_orde
 
 /* Bipartite lattice (Alg. 1 as stated): d_M4 per configuration [2][2 n_c][2 n_c] (spin block,
  * then the layout of cos_gather_bipartite), h_alpha2 = NULL or host [2][2] diagonal shifts per
- * (spin, sublattice); n_max <= COS_BIP_NMAX; precision COS_FP64 or COS_DF64.  Outputs and
+ * (spin, sublattice); n_max <= COS_BIP_NMAX; precision COS_FP64, COS_MIXED or COS_DF64.  Outputs and
  * errors as cos_connected_sum_bipartite_matrices. */
 cos_status cos_connected_det_bipartite_matrices(int n_cfg, int n_max, const int32_t *d_order,
                                                 const int64_t *d_moff, const double *h_alpha2,

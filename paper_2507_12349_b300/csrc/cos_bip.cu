@@ -262,41 +262,78 @@ __device__ __forceinline__ TgtInfo bip_targets(uint32_t A, uint32_t B, uint32_t 
     return ti;
 }
 
-// Arithmetic of the bipartite sweep for a state type: FP64 multiply-adds, or the double-float
+// Arithmetic of the bipartite sweep for a state type T: FP64 multiply-adds; FP32 extensions
+// with the loop closes in FP64 on exactly widened states (mixed precision); or the double-float
 // compensated accumulation of cos_df64.cuh (states stored as the accumulator leaves them).
+//   Acc / first / mad / store: the extension dot products (state type T);
+//   CT: close-matrix element, CAcc / cmad: the loop-closing sum, CV: its flavor-summed value;
+//   seed: CV -> T for the next loop's first state; add: T + T (the k = 0 seed on the
+//   extension's value).
 template <typename T>
 struct BipArith;
 template <>
 struct BipArith<double> {
     using Acc = double;
+    using CT = double;
+    using CAcc = double;
+    using CV = double;
     static __device__ __forceinline__ Acc zero() { return 0.0; }
+    static __device__ __forceinline__ CAcc czero() { return 0.0; }
     static __device__ __forceinline__ Acc first(double x, double y) { return x * y; }
     static __device__ __forceinline__ void mad(Acc &a, double x, double y) { a = fma(x, y, a); }
+    static __device__ __forceinline__ void cmad(CAcc &a, double x, double y) { a = fma(x, y, a); }
     static __device__ __forceinline__ double store(Acc a) { return a; }
-    static __device__ __forceinline__ double close_sum(Acc a, int nfl, int ci) { return flavor_sum(a, nfl, ci); }
+    static __device__ __forceinline__ CV close_sum(CAcc a, int nfl, int ci) { return flavor_sum(a, nfl, ci); }
+    static __device__ __forceinline__ CV cadd(CV a, CV b) { return a + b; }
+    static __device__ __forceinline__ double seed(CV a) { return a; }
     static __device__ __forceinline__ double add(double a, double b) { return a + b; }
-    static __device__ __forceinline__ double to_double(double a) { return a; }
+    static __device__ __forceinline__ double to_double(CV a) { return a; }
+};
+template <>
+struct BipArith<float> {
+    using Acc = float;
+    using CT = double;
+    using CAcc = double;
+    using CV = double;
+    static __device__ __forceinline__ Acc zero() { return 0.0f; }
+    static __device__ __forceinline__ CAcc czero() { return 0.0; }
+    static __device__ __forceinline__ Acc first(float x, float y) { return x * y; }
+    static __device__ __forceinline__ void mad(Acc &a, float x, float y) { a = fmaf(x, y, a); }
+    static __device__ __forceinline__ void cmad(CAcc &a, float x, double y) { a = fma(widen(x), y, a); }
+    static __device__ __forceinline__ float store(Acc a) { return a; }
+    static __device__ __forceinline__ CV close_sum(CAcc a, int nfl, int ci) { return flavor_sum(a, nfl, ci); }
+    static __device__ __forceinline__ CV cadd(CV a, CV b) { return a + b; }
+    static __device__ __forceinline__ float seed(CV a) { return narrow_to(0.0f, a); }
+    static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+    static __device__ __forceinline__ double to_double(CV a) { return a; }
 };
 template <>
 struct BipArith<df64> {
     using Acc = DotAcc;
+    using CT = df64;
+    using CAcc = DotAcc;
+    using CV = df64;
     static __device__ __forceinline__ Acc zero() { return DotAcc{0.0f, 0.0f}; }
+    static __device__ __forceinline__ CAcc czero() { return DotAcc{0.0f, 0.0f}; }
     static __device__ __forceinline__ Acc first(df64 x, df64 y) { return dot_first(x, y); }
     static __device__ __forceinline__ void mad(Acc &a, df64 x, df64 y) { dot_add(a, x, y); }
+    static __device__ __forceinline__ void cmad(CAcc &a, df64 x, df64 y) { dot_add(a, x, y); }
     static __device__ __forceinline__ df64 store(Acc a) { return df64{a.s, a.c}; }
-    static __device__ __forceinline__ df64 close_sum(Acc a, int nfl, int ci) {
+    static __device__ __forceinline__ CV close_sum(CAcc a, int nfl, int ci) {
         return df64_flavor_sum(dot_value(a), nfl, ci);
     }
+    static __device__ __forceinline__ CV cadd(CV a, CV b) { return df64_add(a, b); }
+    static __device__ __forceinline__ df64 seed(CV a) { return a; }
     static __device__ __forceinline__ df64 add(df64 a, df64 b) { return df64_add(a, b); }
-    static __device__ __forceinline__ double to_double(df64 a) { return df64_to_double(a); }
+    static __device__ __forceinline__ double to_double(CV a) { return df64_to_double(a); }
 };
 
 // One row (mu, h, s_h): NV reachable endpoint states, the close, every extension.
 template <typename T, int NV>
 __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict__ dst1, const T *__restrict__ Ms,
-                                        const T *__restrict__ Md, const TgtInfo &ti, int nT, uint32_t Vrow,
-                                        uint32_t A, uint32_t B, uint32_t S, uint32_t rowbase, int h, int sh, int n2,
-                                        bool needclose, int lane, typename BipArith<T>::Acc &csum) {
+                                        const typename BipArith<T>::CT *__restrict__ Md, const TgtInfo &ti, int nT,
+                                        uint32_t Vrow, uint32_t A, uint32_t B, uint32_t S, uint32_t rowbase, int h,
+                                        int sh, int n2, bool needclose, int lane, typename BipArith<T>::CAcc &csum) {
     using Ar = BipArith<T>;
     T o[NV];
     int rs[NV];
@@ -321,7 +358,7 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
     if (needclose) {
         const int hc = (h * 2 + sh) * kLanes;
 #pragma unroll
-        for (int t = 0; t < NV; ++t) Ar::mad(csum, o[t], Md[rs[t] + hc]);
+        for (int t = 0; t < NV; ++t) Ar::cmad(csum, o[t], Md[rs[t] + hc]);
     }
     // this row's target slots, lane-parallel: off1 + ((hidx1 * 2 + s_h) * nA1 + ai1) * 2 + s_j
     const uint32_t hlow = (1u << h) - 1u;
@@ -358,10 +395,11 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
 }
 
 template <typename T>
-__device__ __forceinline__ void bip_row_dispatch(int nv, const T *src, T *dst1, const T *Ms, const T *Md,
-                                                 const TgtInfo &ti, int nT, uint32_t Vrow, uint32_t A, uint32_t B,
-                                                 uint32_t S, uint32_t rowbase, int h, int sh, int n2, bool needclose,
-                                                 int lane, typename BipArith<T>::Acc &csum) {
+__device__ __forceinline__ void bip_row_dispatch(int nv, const T *src, T *dst1, const T *Ms,
+                                                 const typename BipArith<T>::CT *Md, const TgtInfo &ti, int nT,
+                                                 uint32_t Vrow, uint32_t A, uint32_t B, uint32_t S, uint32_t rowbase,
+                                                 int h, int sh, int n2, bool needclose, int lane,
+                                                 typename BipArith<T>::CAcc &csum) {
 #define COS_BROW(K)                                                                                            \
     case K:                                                                                                    \
         bip_row<T, K>(src, dst1, Ms, Md, ti, nT, Vrow, A, B, S, rowbase, h, sh, n2, needclose, lane, csum);    \
@@ -394,9 +432,10 @@ __device__ __forceinline__ void bip_row_dispatch(int nv, const T *src, T *dst1, 
 // the sink.  seedsh = sgn 2 sigma_{l, s} of this lane for vertex 0's shifted start on s.
 template <typename T, bool CLOW>
 __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
-                                         int n, const T *src, T *dst1, const T *Ms, const T *Md, int lane, int ci,
-                                         int nfl, const T seedsh[2], bool shifts, bool active, int lam, int cfg,
-                                         double *out, int *status, int prefetch) {
+                                         int n, const T *src, T *dst1, const T *Ms,
+                                         const typename BipArith<T>::CT *Md, int lane, int ci, int nfl,
+                                         const typename BipArith<T>::CV seedsh[2], bool shifts, bool active, int lam,
+                                         int cfg, double *out, int *status, int prefetch) {
     using Ar = BipArith<T>;
     const uint32_t full = (1u << n) - 1u;
     const uint4 mk = __ldg(tab.masks + mask_index);
@@ -409,13 +448,13 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
     if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
         const uint4 nk = __ldg(tab.masks + next_index);
         const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
-        prefetch_block(reinterpret_cast<const double *>(src), nk.w,
+        prefetch_block(src, nk.w,
                        4u * (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane, prefetch);
     }
     const TgtInfo ti = bip_targets(A, B, S, J, code, tab.rank4, lane);
     const int nT = __popc(J) + __popc(J & ~A);
     const int n2 = 2 * n;
-    typename Ar::Acc csum = Ar::zero();
+    typename Ar::CAcc csum = Ar::czero();
     for (uint32_t hh = H; hh; hh &= hh - 1u) {
         const int h = __ffs(hh) - 1;
         const int hidx = __popc(H & ((1u << h) - 1u));
@@ -431,7 +470,7 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
         }
     }
     if (!needclose) return;   // no half-visited vertex and not full: disconnected, dropped
-    const T C = Ar::close_sum(csum, nfl, ci);
+    const typename Ar::CV C = Ar::close_sum(csum, nfl, ci);
     if (ones) {
         const int k = __ffs(ones) - 1;
         const uint32_t bk = 1u << k;
@@ -442,11 +481,12 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
         const uint32_t off1 = __ldg(tab.rank4 + code1);
         T *tp = dst1 + (size_t)(off1 + (uint32_t)(((hi1 * 2 + sk) * nA + __popc(A & (bk - 1u))) * 2 + sk)) * kLanes +
                 lane;
-        T val = C;
-        if (!CLOW && ell == 1 && shifts) val = Ar::add(val, seedsh[S & 1u]);   // vertex 0 carries a shift point
-        if (CLOW) *tp = (k == 0 && lam == 0) ? Ar::store(Ar::zero()) : val;    // k = 0: block 1 only
-        else if (k == 0) *tp = Ar::add(*tp, val);                               // the extension into 0' wrote it
-        else *tp = val;
+        typename Ar::CV val = C;
+        if (!CLOW && ell == 1 && shifts) val = Ar::cadd(val, seedsh[S & 1u]);   // vertex 0 carries a shift point
+        const T tv = Ar::seed(val);                                              // (mixed: rounded to FP32)
+        if (CLOW) *tp = (k == 0 && lam == 0) ? Ar::store(Ar::zero()) : tv;      // k = 0: block 1 only
+        else if (k == 0) *tp = Ar::add(*tp, tv);                                 // the extension into 0' wrote it
+        else *tp = tv;
     } else if (active && (lam == 0) && out) {
         const double c = CLOW ? Ar::to_double(C) : ldexp(Ar::to_double(C), n - 1);
         out[cfg] = c;
@@ -462,15 +502,16 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int nsm = 4 * a.smem_n * a.smem_n * kLanes;
+    using CT = typename BipArith<T>::CT;
     T *Ms = reinterpret_cast<T *>(smem_bip);   // extension matrices, shifted diagonal
-    T *Md = Ms + nsm;                           // close matrices times sgn w
+    CT *Md = reinterpret_cast<CT *>(smem_bip + ((nsm * sizeof(T) + 15) & ~size_t(15)));   // close: sgn w M
     T *ring = reinterpret_cast<T *>(a.scratch) + (size_t)blockIdx.x * 2 * a.slot_elems;
     const int nfl = a.nf_lanes;
     const int lam = lane % nfl;
     const int ci = lane / nfl;
     const double sgn = a.absmode ? 1.0 : -1.0;
     double sig[2];
-    T seedsh[2];
+    typename BipArith<T>::CV seedsh[2];
     for (int s = 0; s < 2; ++s) {
         sig[s] = a.absmode ? fabs(a.sigma2[lam][s]) : a.sigma2[lam][s];
         to_elem(sgn * 2.0 * sig[s], seedsh[s]);
@@ -569,9 +610,13 @@ static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t str
     ws->last_grid = grid;
     cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "bipartite layer scratch");
     if (st != COS_OK) return st;
-    const size_t smem = 2 * (size_t)4 * L.n_max * L.n_max * kLanes * sizeof(double);   // 8-byte elements
-    auto kern = L.precision == COS_DF64 ? (L.clow ? dp_bip_kernel<df64, true> : dp_bip_kernel<df64, false>)
-                                        : (L.clow ? dp_bip_kernel<double, true> : dp_bip_kernel<double, false>);
+    // extension matrices in the state type, close matrices in FP64 (double-float for df64)
+    const size_t mel = (size_t)4 * L.n_max * L.n_max * kLanes;
+    const size_t es = L.precision == COS_MIXED ? sizeof(float) : sizeof(double);
+    const size_t smem = ((mel * es + 15) & ~size_t(15)) + mel * sizeof(double);
+    auto kern = L.precision == COS_DF64    ? (L.clow ? dp_bip_kernel<df64, true> : dp_bip_kernel<df64, false>)
+                : L.precision == COS_MIXED ? (L.clow ? dp_bip_kernel<float, true> : dp_bip_kernel<float, false>)
+                                           : (L.clow ? dp_bip_kernel<double, true> : dp_bip_kernel<double, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "bipartite smem attribute");
     BipArgs a;
@@ -623,9 +668,9 @@ static cos_status check_bip(int n_cfg, int n_max, const int32_t *d_order, const 
         set_error(std::string(fn) + ": n_max outside [1, 9]");
         return COS_ERR_ORDER;
     }
-    if (precision != COS_FP64 && precision != COS_DF64) {
-        set_error(std::string(fn) + ": bipartite sums run in COS_FP64 or COS_DF64");
-        return COS_ERR_UNIMPLEMENTED;
+    if (precision != COS_FP64 && precision != COS_MIXED && precision != COS_DF64) {
+        set_error(std::string(fn) + ": unknown precision");
+        return COS_ERR_ARG;
     }
     if (n_cfg > 0 && (!d_order || !d_moff || !d_M4 || !d_out)) {
         set_error(std::string(fn) + ": null device pointer");

@@ -293,9 +293,9 @@ extern "C" cos_status cos_connected_sum_bipartite_batch(const cos_tables *t, int
         set_error(std::string(fn) + ": n_max outside [1, 9]");
         return COS_ERR_ORDER;
     }
-    if (precision != COS_FP64 && precision != COS_DF64) {
-        set_error(std::string(fn) + ": bipartite sums run in COS_FP64 or COS_DF64");
-        return COS_ERR_UNIMPLEMENTED;
+    if (precision != COS_FP64 && precision != COS_MIXED && precision != COS_DF64) {
+        set_error(std::string(fn) + ": unknown precision");
+        return COS_ERR_ARG;
     }
     if (n_cfg == 0) return COS_OK;
     if (!d_order || !d_offset || !d_site || !d_tau || !d_out) {

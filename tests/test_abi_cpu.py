@@ -61,7 +61,7 @@ def test_argument_errors_are_synchronous():
     assert lib.cos_connected_det_matrices(1, 4, fake, fake, None, fake, 9, fake, None, None) == -1
     assert lib.cos_connected_det_matrices(0, 4, None, None, None, None, 0, None, None, None) == 0
     assert lib.cos_connected_det_bipartite_matrices(1, 10, fake, fake, None, fake, 0, fake, None, None) == -2
-    assert lib.cos_connected_det_bipartite_matrices(1, 4, fake, fake, None, fake, 1, fake, None, None) == -6
+    assert lib.cos_connected_det_bipartite_matrices(1, 4, fake, fake, None, fake, 7, fake, None, None) == -1
     assert lib.cos_connected_det_bipartite_matrices(1, 4, None, None, None, None, 0, None, None, None) == -1
     assert lib.cos_connected_det_matrices_grad(1, 13, None, None, None, None, None, None, None, None, None) == -2
     assert lib.cos_connected_det_matrices_grad(1, 4, None, None, None, None, None, None, None, None, None) == -1
@@ -182,7 +182,7 @@ def test_bipartite_argument_errors():
     import ctypes
     fake = ctypes.c_void_p(256)     # never dereferenced: rejected before any launch
     assert lib.cos_connected_sum_bipartite_matrices(1, 10, fake, fake, 1, 1, None, fake, 0, fake, None, None) == -2
-    assert lib.cos_connected_sum_bipartite_matrices(1, 4, fake, fake, 1, 1, None, fake, 1, fake, None, None) == -6
+    assert lib.cos_connected_sum_bipartite_matrices(1, 4, fake, fake, 1, 1, None, fake, 7, fake, None, None) == -1
     assert lib.cos_connected_sum_bipartite_matrices(1, 4, None, fake, 1, 1, None, fake, 0, fake, None, None) == -1
     assert lib.cos_connected_sum_bipartite_matrices(0, 4, None, None, 1, 1, None, None, 0, None, None, None) == 0
     assert lib.cos_connected_sum_bipartite_batch(None, 1, 4, fake, fake, fake, fake, 0, fake, None, None) == -1

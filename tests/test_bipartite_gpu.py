@@ -6,6 +6,8 @@ brute force and the sublattice-resolved DP of Alg. 1-2 in test_oracle_bip_pins.
 Tolerance: |err| <= 64 n 2^-53 mass, the FP64 bound of the square-lattice tests; the mass
 (the same DP on |M4|, |sigma| with all signs +) sums the assignments' masses.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -33,6 +35,12 @@ def rand_m4(seed, ncfg, nf, n, scale=0.9):
 
 def df64_bound(n, mass):
     return (16 * n * n + 64 * n) * 2.0 ** -48 * mass
+
+
+def mixed_bound(n, mass):
+    """FP32 extension, FP64 close: a few FP32 ulps per visited point of every term (2n), and
+    the rounding of dot products of up to 2n - 1 states (log2 of the fan-in)."""
+    return (2 * n + math.log2(64 * n)) * 2.0 ** -24 * mass
 
 
 def run(M4s, n_mat, wt, sigma2, abs_mass=False, n_max=None, precision="fp64"):
@@ -78,6 +86,18 @@ def test_bipartite_df64_matches_oracle(n, n_mat, wt, shifts, ncfg):
         rmass = O.bip(M4s[c], s2, weight=wt, method="sum_dp", absmode=True)
         assert abs(got[c] - ref) <= df64_bound(n, rmass), (c, got[c], ref, rmass)
         assert abs(mass[c] - rmass) <= df64_bound(n, rmass)
+
+
+@pytest.mark.parametrize("n,n_mat,wt,shifts,ncfg", CASES[::2])
+def test_bipartite_mixed_matches_oracle(n, n_mat, wt, shifts, ncfg):
+    M4s = rand_m4(600 + 10 * n + n_mat, ncfg, n_mat, n)
+    s2 = np.array([[0.1 - 0.03 * l, -0.05 + 0.02 * l] for l in range(n_mat)]) if shifts else None
+    got, mass = run(M4s, n_mat, wt, None if s2 is None else s2.tolist(), abs_mass=True, precision="mixed")
+    for c in sorted({0, ncfg // 2, ncfg - 1}):
+        ref = O.bip(M4s[c], s2, weight=wt, method="sum_dp", prec="ld")
+        rmass = O.bip(M4s[c], s2, weight=wt, method="sum_dp", absmode=True)
+        assert abs(got[c] - ref) <= mixed_bound(n, rmass), (c, got[c], ref, rmass)
+        assert mass[c] == pytest.approx(rmass, rel=1e-5)
 
 
 def test_bipartite_uneven_orders_and_order9():
@@ -180,9 +200,12 @@ def test_workload_honeycomb_order8_sampled():
     d = B.configs_to_device(cfgs)
     out = torch.full((nc,), float("nan"), dtype=torch.float64, device="cuda")
     B.cos_connected_sum_bipartite_batch(tabs, 8, *d, "fp64", out)
+    outm = torch.full_like(out, float("nan"))
+    B.cos_connected_sum_bipartite_batch(tabs, 8, *d, "mixed", outm)
     B.cos_sync_status()
     got = out.cpu().numpy()
-    assert np.all(np.isfinite(got))
+    gotm = outm.cpu().numpy()
+    assert np.all(np.isfinite(got)) and np.all(np.isfinite(gotm))
     otabs = HC.hc_model_tables(w.model)
     s2 = np.array(w.model.sigma2)
     for c in (0, nc // 2, nc - 1):
@@ -191,6 +214,7 @@ def test_workload_honeycomb_order8_sampled():
         ref = O.bip(M4, s2, method="sum_dp", prec="ld")
         rmass = O.bip(M4, s2, method="sum_dp", absmode=True)
         assert abs(got[c] - ref) <= max(1e-10 * abs(ref), bound(8, rmass)), (c, got[c], ref, rmass)
+        assert abs(gotm[c] - ref) <= mixed_bound(8, rmass), (c, gotm[c], ref, rmass)
     tabs.close()
 
 
