@@ -43,6 +43,17 @@ HEADLINE_DRAM_BYTES_PER_CFG = (8.917352e9 + 7.098890e9) / 5000
 FP64_FMA_PER_CLK_SM = 2.0
 
 
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on the B300s (MEASURED_PEAKS.json beside this file),
+    else the earlier single B300 measurement."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (copy bandwidth)"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -323,6 +334,9 @@ def native_arm(args):
     # per forward multiply-add, so three times the forward's algorithmic flops.
     flops_launch = algorithmic_flops(B, cfgs.order, n_mat, sigma is not None) * (3 if args.grad else 1)
     achieved = flops_launch / dp_avg
+    traffic = (HEADLINE_DRAM_BYTES_PER_CFG * n_cfg
+               if args.workload == WORKLOAD and args.precision == "fp64" and not args.grad else None)
+    hbm_gbs, hbm_src = measured_hbm_gbs()
 
     # end to end through the public call with host buffers (pinned), copies inside the region
     h_order = torch.tensor(cfgs.order).pin_memory()
@@ -378,9 +392,12 @@ def native_arm(args):
                                                            "df64": "df64"}[args.precision]),
                      "flops_per_launch": flops_launch,
                      "launch_ms": dp_avg * 1e3,
-                     "traffic": (HEADLINE_DRAM_BYTES_PER_CFG * n_cfg
-                                 if args.workload == WORKLOAD and args.precision == "fp64" and not args.grad else None),
-                     "traffic_source": "ncu DRAM bytes of a 5000-configuration launch, scaled by configurations"},
+                     "traffic": traffic,
+                     "traffic_source": "ncu DRAM bytes of a 5000-configuration launch, scaled by configurations",
+                     # the other roof: DRAM rate of the same launch against the measured copy bandwidth
+                     "dram_gbs": (traffic / dp_avg / 1e9) if traffic else None,
+                     "hbm_peak_gbs": hbm_gbs, "hbm_peak_source": hbm_src,
+                     "dram_frac": (traffic / dp_avg / 1e9 / hbm_gbs) if traffic else None},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
