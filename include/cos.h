@@ -302,6 +302,17 @@ cos_status cos_connected_det_matrices(int n_cfg, int n_max, const int32_t *d_ord
                                       const double *h_alpha, const double *d_M, cos_precision precision,
                                       double *d_out, double *d_abs_mass, cos_stream_t stream);
 
+/* Gather + determinant-weight sweep from vertex coordinates: SU(2) tables of
+ * cos_build_propagators (two flavors: spin up, spin down; tables collapsed to one matrix for
+ * equal chemical potentials serve both blocks), built with alpha = 0 (the diagonal shifts of
+ * determinant weights are h_alpha, not the tables' dispersion shift).  Other arguments as
+ * cos_connected_sum_batch and cos_connected_det_matrices; COS_ERR_ARG for tables with another
+ * flavor count. */
+cos_status cos_connected_det_batch(const cos_tables *tables, int n_cfg, int n_max, const int32_t *d_order,
+                                   const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
+                                   const double *h_alpha, cos_precision precision, double *d_out,
+                                   double *d_abs_mass, cos_stream_t stream);
+
 /* Gradient of the square-lattice determinant-weight sums by the reverse sweep (the adjoint of
  * Alg. 1 as merged above; the forward sweep is re-run with every layer kept):
  * d_gout[c]  dLoss/dc;  d_out NULL or receives c;  d_gM NULL or dLoss/dM at d_moff[c] as

@@ -33,7 +33,7 @@ EXPORTS = [
     "cos_build_propagators_honeycomb", "cos_gather_bipartite", "cos_connected_sum_bipartite_matrices",
     "cos_connected_sum_bipartite_batch", "cos_bipartite_structure",
     "cos_connected_det_matrices", "cos_connected_det_bipartite_matrices", "cos_connected_det_matrices_grad",
-    "cos_connected_det_subsets", "cos_connected_sum_bipartite_matrices_grad",
+    "cos_connected_det_subsets", "cos_connected_det_batch", "cos_connected_sum_bipartite_matrices_grad",
     "cos_connected_det_bipartite_matrices_grad",
     "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_sync_status", "cos_status_string",
     "cos_last_error", "cos_structure", "cos_peak_probe",
@@ -251,6 +251,17 @@ def cos_connected_det_matrices(n_max: int, order, moff, alpha: Optional[Sequence
     _check(lib().cos_connected_det_matrices(int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(moff, "i64"), al,
                                             _ptr(M, "f64"), PRECISIONS[precision], _ptr(out, "f64"),
                                             _ptr(abs_mass, "f64"), _stream(stream)), "cos_connected_det_matrices")
+
+
+def cos_connected_det_batch(tables: Tables, n_max: int, order, offset, site, tau, alpha, precision: str, out,
+                            abs_mass=None, stream=None):
+    """Gather + SU(2) determinant-weight sums from vertex coordinates (SU(2) tables built with
+    alpha = 0; alpha: None or the two diagonal shifts)."""
+    al = None if alpha is None else (ctypes.c_double * 2)(*[float(x) for x in alpha])
+    _check(lib().cos_connected_det_batch(tables.handle, int(order.numel()), int(n_max), _ptr(order, "i32"),
+                                         _ptr(offset, "i64"), _ptr(site, "i32"), _ptr(tau, "f64"), al,
+                                         PRECISIONS[precision], _ptr(out, "f64"), _ptr(abs_mass, "f64"),
+                                         _stream(stream)), "cos_connected_det_batch")
 
 
 def cos_connected_det_matrices_grad(n_max: int, order, moff, alpha: Optional[Sequence[float]], M, gout, out=None,

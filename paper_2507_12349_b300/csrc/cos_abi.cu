@@ -424,6 +424,72 @@ cos_status batch_body(Workspace *ws, const cos_tables *t, int n_cfg, int n_max, 
 }
 }  // namespace cosdp
 
+namespace cosdp {
+namespace {
+// Symmetric SU(2) tables hold one matrix per configuration: copy it into the spin-down block,
+// [2][n_c][n_c] at c * stride.
+__global__ void dup_spin_block_kernel(int n_cfg, const int32_t *__restrict__ order, int64_t stride,
+                                      double *__restrict__ M) {
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_cfg; c += warps) {
+        const int n = order[c];
+        if (n < 1 || n > COS_NMAX) continue;
+        double *b = M + (int64_t)c * stride;
+        for (int e = lane; e < n * n; e += 32) b[n * n + e] = b[e];
+    }
+}
+}  // namespace
+}  // namespace cosdp
+
+extern "C" cos_status cos_connected_det_batch(const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order,
+                                              const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
+                                              const double *h_alpha, cos_precision precision, double *d_out,
+                                              double *d_abs_mass, cos_stream_t stream) {
+    const char *fn = "cos_connected_det_batch";
+    cos_status st = check_batch(t, n_cfg, n_max, d_order, d_offset, d_site, d_tau, precision, d_out, fn);
+    if (st != COS_OK) return st;
+    if (t->model.n_flavors != 2) {
+        set_error(std::string(fn) + ": determinant weights need SU(2) tables (two flavors)");
+        return COS_ERR_ARG;
+    }
+    if (n_cfg == 0) return COS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::string err;
+    Workspace *ws = get_workspace(s, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    const int64_t stride = (int64_t)2 * n_max * n_max;
+    st = ensure((void **)&ws->M, &ws->M_cap, (size_t)n_cfg * stride, sizeof(double), "matrix workspace");
+    if (st != COS_OK) return st;
+    st = launch_gather(t, n_cfg, d_order, d_offset, d_site, d_tau, nullptr, stride, ws->M, ws->status, s);
+    if (st != COS_OK) return st;
+    if (t->n_mat == 1) {
+        int nsm = 1;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
+        const int blocks = std::max(1, std::min((n_cfg * 32 + 255) / 256, 8 * nsm));
+        dup_spin_block_kernel<<<blocks, 256, 0, s>>>(n_cfg, d_order, stride, ws->M);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "spin block copy launch");
+    }
+    DpLaunch L;
+    L.n_cfg = n_cfg;
+    L.n_max = n_max;
+    L.order = d_order;
+    L.M = ws->M;
+    L.moff = nullptr;
+    L.mstride = stride;
+    L.n_mat = 2;
+    L.loop_weight = 1;
+    for (int b = 0; b < 2; ++b) L.sigma[b] = h_alpha ? h_alpha[b] : 0.0;   // the diagonal shifts
+    L.clow = true;
+    L.precision = precision;
+    L.out = d_out;
+    return run_dp(ws, L, d_abs_mass, s);
+}
+
 extern "C" cos_status cos_connected_sum_batch(const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order,
                                               const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
                                               cos_precision precision, double *d_out, double *d_abs_mass,

@@ -403,3 +403,32 @@ def test_det_autograd_function():
     assert np.array_equal(c.detach().cpu().numpy(), out)
     assert np.allclose(M.grad.cpu().numpy(), np.concatenate([g.ravel() for g in gM]), rtol=0, atol=0)
     assert np.allclose(al.grad.numpy(), ga.sum(0), rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("sym", [False, True])
+def test_det_batch_from_coordinates(sym):
+    """Gather + determinant sweep in one call, against the oracle's gather and Alg. 1; with
+    equal chemical potentials the collapsed tables serve both spin blocks."""
+    w = I.WORKLOADS["su2_zeeman_det_n10"]
+    m = w.model
+    model = I.Model(m.L, m.t, m.beta, m.U, (0.1, 0.1) if sym else m.mu, (0.0, 0.0), m.n_tau)
+    cfgs = I.make_configs(model, 3, 8, 300, 17)
+    tabs = B.tables_for(model)
+    assert tabs.info().n_mat == (1 if sym else 2)
+    d = B.configs_to_device(cfgs)
+    al = [0.07, -0.03]
+    out = torch.full((300,), float("nan"), dtype=torch.float64, device="cuda")
+    mass = torch.full_like(out, float("nan"))
+    B.cos_connected_det_batch(tabs, 8, *d, al, "fp64", out, mass)
+    B.cos_sync_status()
+    got, gmass = out.cpu().numpy(), mass.cpu().numpy()
+    otabs = P.model_tables(model)
+    if sym:
+        otabs = np.concatenate([otabs[:1], otabs[:1]])
+    for c, Mc in zip((0, 150, 299), P.gather(otabs, cfgs, model.L, model.beta, (0, 150, 299))):
+        n = int(cfgs.order[c])
+        ref = O.det_clow(Mc, al, prec="ld")
+        rmass = O.det_clow(Mc, al, absmode=True)
+        assert abs(got[c] - ref) <= bound("fp64", n, rmass) + 1e-13 * rmass, (c, got[c], ref)
+        assert gmass[c] == pytest.approx(rmass, rel=1e-10)
+    tabs.close()
