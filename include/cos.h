@@ -322,6 +322,23 @@ cos_status cos_connected_det_matrices_grad(int n_cfg, int n_max, const int32_t *
                                            const double *h_alpha, const double *d_M, const double *d_gout,
                                            double *d_out, double *d_gM, double *d_galpha, cos_stream_t stream);
 
+/* Gradient of the determinant-weight sums from vertex coordinates (the reverse sweep of
+ * cos_connected_det_matrices_grad on the gathered blocks, then the chain rule through the
+ * tables as cos_connected_sum_grad):
+ *   d_gM / d_gmoff  NULL, or dLoss/dM written at d_gmoff[c] as [2][n_c][n_c] (both spin
+ *                   blocks, also for collapsed tables, where the blocks are equal);
+ *   d_gmu           NULL or [n_cfg][2]: dLoss/dmu_b = sum_ij dLoss/dM^b_ij dM^b_ij/dmu_b; for
+ *                   collapsed tables the derivative of the common matrix (the two blocks'
+ *                   sum) split evenly over the two spins;
+ *   d_galpha        NULL or [n_cfg][2]: dLoss/dalpha_b of the diagonal shifts h_alpha
+ *                   (= -trace of dLoss/dM_b).
+ * Other arguments as cos_connected_det_batch; FP64 only; builds the dG0/dmu table on first use
+ * when d_gmu is given. */
+cos_status cos_connected_det_grad(const cos_tables *tables, int n_cfg, int n_max, const int32_t *d_order,
+                                  const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
+                                  const double *h_alpha, const double *d_gout, double *d_out, double *d_gM,
+                                  const int64_t *d_gmoff, double *d_gmu, double *d_galpha, cos_stream_t stream);
+
 /* Every vertex subset (the all-subsets mode of cos_connected_sum_subsets for determinant
  * weights): d_c[c * 2^n_max + S] = c(S), the connected part of det(A_up[S]) det(A_dn[S]) (the
  * close of the Alg. 1 sweep at the mask 2 1_S, rooted at min S); with d_a, a(S) =

@@ -123,6 +123,40 @@ def connected_det(M, alpha, order, moff, n_max: int):
     return _ConnectedDet.apply(M, alpha, order, moff, n_max)
 
 
+class _ConnectedDetModel(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, mu, alpha, model, d_cfgs, n_max):
+        tabs = B.cos_build_propagators(model.L, model.t, model.beta, model.U, [float(x) for x in mu], [0.0, 0.0],
+                                       model.n_tau)
+        order, offset, site, tau = d_cfgs
+        al = _host_list(alpha)
+        out = torch.empty(order.numel(), dtype=torch.float64, device=order.device)
+        B.cos_connected_det_batch(tabs, n_max, order, offset, site, tau, al, "fp64", out)
+        ctx.tabs = tabs
+        ctx.al = al
+        ctx.d_cfgs = d_cfgs
+        ctx.n_max = n_max
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        order, offset, site, tau = ctx.d_cfgs
+        n = order.numel()
+        gmu = torch.empty(n, 2, dtype=torch.float64, device=order.device)
+        gal = torch.empty_like(gmu)
+        B.cos_connected_det_grad(ctx.tabs, ctx.n_max, order, offset, site, tau, ctx.al,
+                                 gout.detach().to(torch.float64).contiguous(), gmu=gmu, galpha=gal)
+        ctx.tabs.close()
+        return gmu.sum(0).cpu(), gal.sum(0).cpu(), None, None, None
+
+
+def connected_det_model(mu, alpha, model, d_cfgs, n_max: int):
+    """SU(2) determinant-weight connected sums from vertex coordinates for the spin chemical
+    potentials mu and the diagonal shifts alpha (CPU tensors of 2 values, differentiable); the
+    tables are built at mu with no dispersion shift; other model fields from `model`."""
+    return _ConnectedDetModel.apply(mu, alpha, model, d_cfgs, n_max)
+
+
 class _ConnectedBipartite(torch.autograd.Function):
     @staticmethod
     def forward(ctx, M4, sig2, order, moff, n_max, n_mat, loop_weight, det):

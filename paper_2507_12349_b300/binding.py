@@ -34,7 +34,7 @@ EXPORTS = [
     "cos_connected_sum_bipartite_batch", "cos_bipartite_structure",
     "cos_connected_det_matrices", "cos_connected_det_bipartite_matrices", "cos_connected_det_matrices_grad",
     "cos_connected_det_subsets", "cos_connected_det_batch", "cos_connected_sum_bipartite_matrices_grad",
-    "cos_connected_det_bipartite_matrices_grad",
+    "cos_connected_det_bipartite_matrices_grad", "cos_connected_det_grad",
     "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_sync_status", "cos_status_string",
     "cos_last_error", "cos_structure", "cos_peak_probe",
     "cos_plan_create_batch", "cos_plan_create_matrices", "cos_plan_launch", "cos_plan_status", "cos_plan_grid",
@@ -273,6 +273,18 @@ def cos_connected_det_matrices_grad(n_max: int, order, moff, alpha: Optional[Seq
                                                  _ptr(moff, "i64"), al, _ptr(M, "f64"), _ptr(gout, "f64"),
                                                  _ptr(out, "f64"), _ptr(gM, "f64"), _ptr(galpha, "f64"),
                                                  _stream(stream)), "cos_connected_det_matrices_grad")
+
+
+def cos_connected_det_grad(tables: Tables, n_max: int, order, offset, site, tau, alpha, gout, out=None, gM=None,
+                           gmoff=None, gmu=None, galpha=None, stream=None):
+    """Gradient of the SU(2) determinant-weight sums from vertex coordinates: dLoss/dM ([2][n_c][n_c]
+    at gmoff), dLoss/dmu and dLoss/dalpha ([n_cfg][2]) for dLoss/dc = gout."""
+    al = None if alpha is None else (ctypes.c_double * 2)(*[float(x) for x in alpha])
+    _check(lib().cos_connected_det_grad(tables.handle, int(order.numel()), int(n_max), _ptr(order, "i32"),
+                                        _ptr(offset, "i64"), _ptr(site, "i32"), _ptr(tau, "f64"), al,
+                                        _ptr(gout, "f64"), _ptr(out, "f64"), _ptr(gM, "f64"), _ptr(gmoff, "i64"),
+                                        _ptr(gmu, "f64"), _ptr(galpha, "f64"), _stream(stream)),
+           "cos_connected_det_grad")
 
 
 def cos_connected_det_subsets(n_max: int, order, moff, alpha: Optional[Sequence[float]], M, c_out, a_out=None,

@@ -434,13 +434,114 @@ __global__ void dup_spin_block_kernel(int n_cfg, const int32_t *__restrict__ ord
     const int lane = threadIdx.x & 31;
     for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_cfg; c += warps) {
         const int n = order[c];
-        if (n < 1 || n > COS_NMAX) continue;
+        if (n < 1 || n > COS_NMAX || (int64_t)2 * n * n > stride) continue;
         double *b = M + (int64_t)c * stride;
         for (int e = lane; e < n * n; e += 32) b[n * n + e] = b[e];
     }
 }
+// dc/dM of a configuration from the stride layout [2][n_c][n_c] at c * stride into the caller's
+// blocks at gmoff[c].
+__global__ void copy_spin_blocks_kernel(int n_cfg, const int32_t *__restrict__ order, int64_t stride,
+                                        const double *__restrict__ src, const int64_t *__restrict__ gmoff,
+                                        double *__restrict__ dst) {
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_cfg; c += warps) {
+        const int n = order[c];
+        if (n < 1 || n > COS_NMAX || (int64_t)2 * n * n > stride) continue;
+        for (int e = lane; e < 2 * n * n; e += 32) dst[gmoff[c] + e] = src[(int64_t)c * stride + e];
+    }
+}
+
+// Collapsed (symmetric) tables: both spin blocks came from one matrix, so dc/dM of that matrix
+// is the sum of the two blocks' gradients (folded into block 0 for the chain rule).
+__global__ void fold_spin_blocks_kernel(int n_cfg, const int32_t *__restrict__ order, int64_t stride,
+                                        double *__restrict__ g) {
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_cfg; c += warps) {
+        const int n = order[c];
+        if (n < 1 || n > COS_NMAX || (int64_t)2 * n * n > stride) continue;
+        double *b = g + (int64_t)c * stride;
+        for (int e = lane; e < n * n; e += 32) b[e] += b[n * n + e];
+    }
+}
 }  // namespace
 }  // namespace cosdp
+
+extern "C" cos_status cos_connected_det_grad(const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order,
+                                             const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
+                                             const double *h_alpha, const double *d_gout, double *d_out,
+                                             double *d_gM, const int64_t *d_gmoff, double *d_gmu,
+                                             double *d_galpha, cos_stream_t stream) {
+    const char *fn = "cos_connected_det_grad";
+    cos_status st = check_common(n_cfg, n_max, COS_FP64, fn);
+    if (st != COS_OK) return st;
+    if (!t || t->bipartite || t->model.n_flavors != 2) {
+        set_error(std::string(fn) + ": needs SU(2) square-lattice tables (two flavors)");
+        return COS_ERR_ARG;
+    }
+    if (n_cfg == 0) return COS_OK;
+    if (!d_order || !d_offset || !d_site || !d_tau || !d_gout || (d_gM && !d_gmoff)) {
+        set_error(std::string(fn) + ": null device pointer (d_gM needs d_gmoff)");
+        return COS_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::string err;
+    Workspace *ws = get_workspace(s, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    if (d_gmu) {
+        st = ensure_dtables(const_cast<cos_tables *>(t), s);
+        if (st != COS_OK) return st;
+    }
+    const int64_t stride = (int64_t)2 * n_max * n_max;
+    st = ensure((void **)&ws->M, &ws->M_cap, (size_t)n_cfg * stride, sizeof(double), "matrix workspace");
+    if (st == COS_OK) st = ensure((void **)&ws->gM, &ws->gM_cap, (size_t)n_cfg * stride, sizeof(double), "gradient workspace");
+    if (st == COS_OK) st = ensure((void **)&ws->gsig, &ws->gsig_cap, (size_t)n_cfg * 2, sizeof(double), "alpha gradient");
+    if (st != COS_OK) return st;
+    st = launch_gather(t, n_cfg, d_order, d_offset, d_site, d_tau, nullptr, stride, ws->M, ws->status, s);
+    if (st != COS_OK) return st;
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
+    const int blocks = std::max(1, std::min((n_cfg * 32 + 255) / 256, 8 * nsm));
+    if (t->n_mat == 1) dup_spin_block_kernel<<<blocks, 256, 0, s>>>(n_cfg, d_order, stride, ws->M);
+    DpLaunch L;
+    L.n_cfg = n_cfg;
+    L.n_max = n_max;
+    L.order = d_order;
+    L.M = ws->M;
+    L.moff = nullptr;
+    L.mstride = stride;
+    L.n_mat = 2;
+    L.loop_weight = 1;
+    for (int b = 0; b < 2; ++b) L.sigma[b] = h_alpha ? h_alpha[b] : 0.0;
+    L.clow = true;
+    L.precision = COS_FP64;
+    L.out = d_out;
+    st = launch_plan_batches(ws, n_cfg, n_max, d_order, kLanes / 2, s);
+    if (st != COS_OK) return st;
+    st = launch_adjoint(ws, L, d_gout, ws->gM, nullptr, stride, ws->gsig, s);
+    if (st != COS_OK) return st;
+    if (d_gM) copy_spin_blocks_kernel<<<blocks, 256, 0, s>>>(n_cfg, d_order, stride, ws->gM, d_gmoff, d_gM);
+    if (d_galpha) {
+        cudaError_t e = cudaMemcpyAsync(d_galpha, ws->gsig, (size_t)n_cfg * 2 * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "alpha gradient copy");
+    }
+    if (d_gmu) {
+        if (t->n_mat == 1) fold_spin_blocks_kernel<<<blocks, 256, 0, s>>>(n_cfg, d_order, stride, ws->gM);
+        // dc/dmu_b through the dG/dmu tables (the tables' dispersion shift alpha is 0 here)
+        st = launch_chain(t, n_cfg, d_order, d_offset, d_site, d_tau, ws->gM, nullptr, stride, ws->gsig, d_gmu,
+                          nullptr, s);
+        if (st != COS_OK) return st;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "determinant gradient launches");
+    return COS_OK;
+}
 
 extern "C" cos_status cos_connected_det_batch(const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order,
                                               const int64_t *d_offset, const int32_t *d_site, const double *d_tau,

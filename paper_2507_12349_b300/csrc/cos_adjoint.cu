@@ -313,7 +313,7 @@ __global__ void chain_kernel(const double *__restrict__ dG, int L, int n_tau, do
     const double scale = (double)(n_tau - 1) / beta;
     for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_cfg; c += warps) {
         const int n = order[c];
-        if (n < 1 || n > COS_NMAX) continue;
+        if (n < 1 || n > COS_NMAX || (!gmoff && (int64_t)n_mat * n * n > gmstride)) continue;
         const int64_t o = offset[c];
         const double *g = gM + (gmoff ? gmoff[c] : (int64_t)c * gmstride);
         for (int l = 0; l < n_mat; ++l) {

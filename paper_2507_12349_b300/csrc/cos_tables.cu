@@ -84,7 +84,8 @@ __global__ void gather_kernel(const double *__restrict__ G, int L, int n_tau, do
     const double scale = (double)(n_tau - 1) / beta;
     for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_cfg; c += warps) {
         const int n = order[c];
-        if (n < 1 || n > COS_NMAX) {
+        // an order above the stride layout's n_max would spill into the next configuration
+        if (n < 1 || n > COS_NMAX || (!moff && (int64_t)n_mat * n * n > mstride)) {
             if (lane == 0) atomicOr(status, kStatusOrder);
             continue;
         }

@@ -64,6 +64,10 @@ def test_argument_errors_are_synchronous():
     assert lib.cos_connected_det_bipartite_matrices(1, 4, fake, fake, None, fake, 7, fake, None, None) == -1
     assert lib.cos_connected_det_bipartite_matrices(1, 4, None, None, None, None, 0, None, None, None) == -1
     assert lib.cos_connected_det_batch(None, 1, 4, fake, fake, fake, fake, None, 0, fake, None, None) == -1
+    assert lib.cos_connected_det_grad(None, 1, 4, fake, fake, fake, fake, None, fake, None, None, None, None, None,
+                                      None) == -1
+    assert lib.cos_connected_det_grad(None, 1, 13, fake, fake, fake, fake, None, fake, None, None, None, None, None,
+                                      None) == -2
     assert lib.cos_connected_det_matrices_grad(1, 13, None, None, None, None, None, None, None, None, None) == -2
     assert lib.cos_connected_det_matrices_grad(1, 4, None, None, None, None, None, None, None, None, None) == -1
     assert lib.cos_connected_det_matrices_grad(0, 4, None, None, None, None, None, None, None, None, None) == 0

@@ -432,3 +432,95 @@ def test_det_batch_from_coordinates(sym):
         assert abs(got[c] - ref) <= bound("fp64", n, rmass) + 1e-13 * rmass, (c, got[c], ref)
         assert gmass[c] == pytest.approx(rmass, rel=1e-10)
     tabs.close()
+
+
+@pytest.mark.parametrize("sym", [False, True])
+def test_det_grad_from_coordinates(sym):
+    """dLoss/dM, dLoss/dalpha and dLoss/dmu from vertex coordinates.  dM and dalpha: the same
+    reverse sweep as the matrices entry on the blocks cos_gather writes (bitwise).  dmu: a
+    central difference of the oracle pipeline (tables, gather and Alg. 1 rebuilt at mu +- h);
+    collapsed tables (equal chemical potentials) move both spins together and split the
+    derivative evenly."""
+    base = I.WORKLOADS["su2_zeeman_det_n10"].model
+    mu = [0.1, 0.1] if sym else [-0.15, 0.2]
+    model = I.Model(base.L, base.t, base.beta, base.U, tuple(mu), (0.0, 0.0), base.n_tau)
+    nc = 40
+    cfgs = I.make_configs(model, 3, 6, nc, 23)
+    tabs = B.tables_for(model)
+    n_mat = tabs.info().n_mat
+    assert n_mat == (1 if sym else 2)
+    d = B.configs_to_device(cfgs)
+    al = [0.06, -0.04]
+    order = cfgs.order.astype(np.int32)
+    gmoff = B.matrix_offsets(order, 2)
+    gout = np.linspace(0.5, 1.5, nc)
+    out = torch.full((nc,), float("nan"), dtype=torch.float64, device="cuda")
+    gM = torch.full((int(2 * (order.astype(np.int64) ** 2).sum()),), float("nan"), dtype=torch.float64,
+                    device="cuda")
+    gmu = torch.full((nc, 2), float("nan"), dtype=torch.float64, device="cuda")
+    ga = torch.full_like(gmu, float("nan"))
+    B.cos_connected_det_grad(tabs, 6, *d, al, torch.tensor(gout, device="cuda"), out, gM,
+                             torch.tensor(gmoff, device="cuda"), gmu, ga)
+    B.cos_sync_status()
+    out, gM, gmu, ga = (x.cpu().numpy() for x in (out, gM, gmu, ga))
+
+    moff = B.matrix_offsets(order, n_mat)
+    Mg = torch.empty(int(n_mat * (order.astype(np.int64) ** 2).sum()), dtype=torch.float64, device="cuda")
+    B.cos_gather(tabs, *d, torch.tensor(moff, device="cuda"), Mg)
+    host = Mg.cpu().numpy()
+    Ms = []
+    for c in range(nc):
+        n = int(order[c])
+        blk = host[moff[c]:moff[c] + n_mat * n * n].reshape(n_mat, n, n)
+        Ms.append(np.ascontiguousarray(np.concatenate([blk, blk]) if n_mat == 1 else blk))
+    ref_out, ref_gM, ref_ga = run_grad(Ms, al, gout)
+    assert np.array_equal(out, ref_out)
+    assert np.array_equal(gM, np.concatenate([g.ravel() for g in ref_gM]))
+    assert np.array_equal(ga, ref_ga)
+
+    def oracle_c(mu2, c):
+        m = I.Model(model.L, model.t, model.beta, model.U, tuple(mu2), (0.0, 0.0), model.n_tau)
+        t = P.model_tables(m)
+        if t.shape[0] == 1:
+            t = np.concatenate([t, t])
+        o, n = int(cfgs.offset[c]), int(cfgs.order[c])
+        return O.det_clow(P.gather_one(t, cfgs.site[o:o + n], cfgs.tau[o:o + n], m.L, m.beta), al, prec="ld")
+
+    h = 1e-6
+    for c in (0, nc // 2, nc - 1):
+        for b in range(2):
+            if sym:
+                fd = (oracle_c([x + h for x in mu], c) - oracle_c([x - h for x in mu], c)) / (2 * h) / 2
+            else:
+                p = list(mu); p[b] += h
+                q = list(mu); q[b] -= h
+                fd = (oracle_c(p, c) - oracle_c(q, c)) / (2 * h)
+            want = gout[c] * fd
+            assert gmu[c, b] == pytest.approx(want, rel=2e-5, abs=1e-7 * max(1.0, abs(want))), (c, b, gmu[c, b], want)
+    tabs.close()
+
+
+def test_det_model_autograd():
+    """connected_det_model: the forward equals cos_connected_det_batch, and mu.grad / alpha.grad
+    are the per-configuration gradients of cos_connected_det_grad summed with the weights."""
+    base = I.WORKLOADS["su2_zeeman_det_n10"].model
+    mu = [-0.1, 0.25]
+    model = I.Model(base.L, base.t, base.beta, base.U, tuple(mu), (0.0, 0.0), base.n_tau)
+    cfgs = I.make_configs(model, 4, 7, 64, 5)
+    d = B.configs_to_device(cfgs)
+    mu_t = torch.tensor(mu, dtype=torch.float64, requires_grad=True)
+    al_t = torch.tensor([0.03, 0.08], dtype=torch.float64, requires_grad=True)
+    c = AG.connected_det_model(mu_t, al_t, model, d, 7)
+    w = torch.linspace(-1.0, 2.0, 64, dtype=torch.float64, device="cuda")
+    (c * w).sum().backward()
+    tabs = B.tables_for(model)
+    ref = torch.empty(64, dtype=torch.float64, device="cuda")
+    B.cos_connected_det_batch(tabs, 7, *d, [0.03, 0.08], "fp64", ref)
+    gmu = torch.empty(64, 2, dtype=torch.float64, device="cuda")
+    gal = torch.empty_like(gmu)
+    B.cos_connected_det_grad(tabs, 7, *d, [0.03, 0.08], w, gmu=gmu, galpha=gal)
+    B.cos_sync_status()
+    tabs.close()
+    assert np.array_equal(c.detach().cpu().numpy(), ref.cpu().numpy())
+    assert np.allclose(mu_t.grad.numpy(), gmu.sum(0).cpu().numpy(), rtol=1e-14, atol=0)
+    assert np.allclose(al_t.grad.numpy(), gal.sum(0).cpu().numpy(), rtol=1e-14, atol=0)
