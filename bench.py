@@ -674,6 +674,20 @@ def measure_det(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
     for k in ("det_fp64", "det_df64", "det_mixed"):
         res[f"hc_su2_af_n8_{k}"] = {"configs": hc.n_cfg, "configs_per_s": hc.n_cfg / ht[k], "ms": ht[k] * 1e3,
                                     "cost_vs_cos_fp64": ht[k] / ht["cos_fp64"]}
+    # every vertex subset of both bipartite sweeps: c(S) of all 255 subsets (8 rooted derived
+    # problems per configuration) and a(S) by the subset exponential, against the plain call
+    hcs = torch.empty(hc.n_cfg * 256, dtype=torch.float64, device="cuda")
+    has = torch.empty_like(hcs)
+    sfns = {"cos_fp64": lambda: B.cos_connected_sum_bipartite_subsets(8, hd[0], hmoff, 2, 1, None, M4, hcs, has),
+            "det_fp64": lambda: B.cos_connected_det_bipartite_subsets(8, hd[0], hmoff, al, M4, hcs, has)}
+    for k, f in sfns.items():
+        f()
+        B.cos_sync_status()
+        tsk = statistics.mean(time_steps(torch, f, 1, lambda: flush_l2(flush_buf)))
+        B.cos_sync_status()
+        res[f"hc_su2_af_n8_{k.split('_')[0]}_all_subsets_fp64"] = {
+            "configs": hc.n_cfg, "configs_per_s": hc.n_cfg / tsk, "ms": tsk * 1e3, "cost_vs_plain": tsk / ht[k]}
+    del hcs, has
     # gradients of both bipartite sweeps (reverse sweep over every kept layer)
     hg = torch.ones(hc.n_cfg, dtype=torch.float64, device="cuda")
     gM4 = torch.empty_like(M4)

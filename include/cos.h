@@ -282,6 +282,20 @@ cos_status cos_connected_sum_bipartite_batch(const cos_tables *tables, int n_cfg
                                              cos_precision precision, double *d_out,
                                              double *d_abs_mass, cos_stream_t stream);
 
+/* Every vertex subset on a bipartite lattice (the all-subsets mode of
+ * cos_connected_sum_subsets on the sublattice-resolved sweep): d_c[c * 2^n_max + S] = c(S),
+ * the connected sum of the sub-configuration S summed over its sublattice assignments (the
+ * close of a mask with every vertex of S fully visited and no half-visited vertex, Methods A
+ * and Alg. 1-2), and with d_a, a(S) by the subset exponential.  Layout of d_M4 / h_sigma2 as
+ * cos_connected_sum_bipartite_matrices; all_roots, layout of d_c / d_a, workspace and errors
+ * as cos_connected_sum_subsets; n_max <= COS_BIP_NMAX; COS_FP64 only (COS_ERR_UNIMPLEMENTED
+ * for the other precisions). */
+cos_status cos_connected_sum_bipartite_subsets(int n_cfg, int n_max, const int32_t *d_order,
+                                               const int64_t *d_moff, int n_mat, int loop_weight,
+                                               const double *h_sigma2, const double *d_M4,
+                                               cos_precision precision, int all_roots, double *d_c,
+                                               double *d_a, cos_stream_t stream);
+
 /* ------------------------------------------------------------------ SU(2) determinant weights
  * Connected sums of an SU(2) model whose diagrams are weighted by determinants (the
  * interaction (n_up - alpha_up)(n_dn - alpha_dn), Methods A): the sum of all diagrams of a
@@ -364,6 +378,16 @@ cos_status cos_connected_det_bipartite_matrices_grad(int n_cfg, int n_max, const
                                                      const int64_t *d_moff, const double *h_alpha2,
                                                      const double *d_M4, const double *d_gout, double *d_out,
                                                      double *d_gM4, double *d_galpha2, cos_stream_t stream);
+
+/* Every vertex subset of the bipartite determinant-weight sums: d_c[c * 2^n_max + S] = c(S),
+ * the connected part of sum_s det(A_up[S,s]) det(A_dn[S,s]) over the sublattice assignments s
+ * of S (the close of the Alg. 1 sweep at the mask with S fully visited), and with d_a, a(S)
+ * itself by the subset exponential.  d_M4 / h_alpha2 as cos_connected_det_bipartite_matrices;
+ * everything else as cos_connected_sum_bipartite_subsets. */
+cos_status cos_connected_det_bipartite_subsets(int n_cfg, int n_max, const int32_t *d_order,
+                                               const int64_t *d_moff, const double *h_alpha2,
+                                               const double *d_M4, cos_precision precision, int all_roots,
+                                               double *d_c, double *d_a, cos_stream_t stream);
 
 /* ------------------------------------------------------------------ adjoint DP
  * Gradient of the connected sums by the reverse (adjoint) DP: the forward DP is re-run with

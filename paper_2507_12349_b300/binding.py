@@ -34,7 +34,8 @@ EXPORTS = [
     "cos_connected_sum_bipartite_batch", "cos_bipartite_structure",
     "cos_connected_det_matrices", "cos_connected_det_bipartite_matrices", "cos_connected_det_matrices_grad",
     "cos_connected_det_subsets", "cos_connected_det_batch", "cos_connected_sum_bipartite_matrices_grad",
-    "cos_connected_det_bipartite_matrices_grad", "cos_connected_det_grad",
+    "cos_connected_det_bipartite_matrices_grad", "cos_connected_det_grad", "cos_connected_sum_bipartite_subsets",
+    "cos_connected_det_bipartite_subsets",
     "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_sync_status", "cos_status_string",
     "cos_last_error", "cos_structure", "cos_peak_probe",
     "cos_plan_create_batch", "cos_plan_create_matrices", "cos_plan_launch", "cos_plan_status", "cos_plan_grid",
@@ -296,6 +297,29 @@ def cos_connected_det_subsets(n_max: int, order, moff, alpha: Optional[Sequence[
                                            _ptr(M, "f64"), PRECISIONS["fp64"], int(bool(all_roots)),
                                            _ptr(c_out, "f64"), _ptr(a_out, "f64"), _stream(stream)),
            "cos_connected_det_subsets")
+
+
+def cos_connected_sum_bipartite_subsets(n_max: int, order, moff, n_mat: int, loop_weight: int, sigma2, M4, c_out,
+                                        a_out=None, all_roots: bool = True, stream=None):
+    """c(S) (and a(S) when a_out is given) of every vertex subset S on a bipartite lattice: M4
+    holds [n_mat][2 n_c][2 n_c] per configuration at moff; c_out / a_out are [n_cfg * 2^n_max]
+    float64, entry c * 2^n_max + S."""
+    _check(lib().cos_connected_sum_bipartite_subsets(int(order.numel()), int(n_max), _ptr(order, "i32"),
+                                                     _ptr(moff, "i64"), int(n_mat), int(loop_weight),
+                                                     _sig2(sigma2, n_mat), _ptr(M4, "f64"), PRECISIONS["fp64"],
+                                                     int(bool(all_roots)), _ptr(c_out, "f64"), _ptr(a_out, "f64"),
+                                                     _stream(stream)), "cos_connected_sum_bipartite_subsets")
+
+
+def cos_connected_det_bipartite_subsets(n_max: int, order, moff, alpha2, M4, c_out, a_out=None,
+                                        all_roots: bool = True, stream=None):
+    """c(S) (and a(S) when a_out is given) of every vertex subset S for bipartite determinant
+    weights: M4 [2][2 n_c][2 n_c] per configuration; alpha2 None or 2 x 2 (spin, sublattice)."""
+    _check(lib().cos_connected_det_bipartite_subsets(int(order.numel()), int(n_max), _ptr(order, "i32"),
+                                                     _ptr(moff, "i64"), _sig2(alpha2, 2), _ptr(M4, "f64"),
+                                                     PRECISIONS["fp64"], int(bool(all_roots)), _ptr(c_out, "f64"),
+                                                     _ptr(a_out, "f64"), _stream(stream)),
+           "cos_connected_det_bipartite_subsets")
 
 
 def cos_connected_det_bipartite_matrices(n_max: int, order, moff, alpha2, M4, precision: str, out, abs_mass=None,

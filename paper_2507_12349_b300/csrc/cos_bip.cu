@@ -226,6 +226,8 @@ struct BipArgs {
     int prefetch;
     double *out;
     int *status;
+    double *csub;               // nullable (all-subsets mode): c(S) at csub[base + (S << shift)]
+    const int64_t *csub_key;    // per configuration: (base << 4) | shift
 };
 
 // Extension targets of one mask, one lane per target (q < T = |J| + |J \ A|, at most 2n):
@@ -430,12 +432,16 @@ __device__ __forceinline__ void bip_row_dispatch(int nv, const T *src, T *dst1, 
 
 // One interaction mask: its rows, the flavor sum of the close, the seed of the next loop or
 // the sink.  seedsh = sgn 2 sigma_{l, s} of this lane for vertex 0's shifted start on s.
-template <typename T, bool CLOW>
+// SUB: all-subsets mode.  A mask with no half-visited vertex closes the connected covers of
+// its full set B (times 2^(|B|-1) for cycle factors); its close is stored at csub[B << cshift]
+// (csub: this lane's output base, valid on active lanes), also where the sweep itself drops it.
+template <typename T, bool CLOW, bool SUB = false>
 __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
                                          int n, const T *src, T *dst1, const T *Ms,
                                          const typename BipArith<T>::CT *Md, int lane, int ci, int nfl,
                                          const typename BipArith<T>::CV seedsh[2], bool shifts, bool active, int lam,
-                                         int cfg, double *out, int *status, int prefetch) {
+                                         int cfg, double *out, int *status, int prefetch, double *csub = nullptr,
+                                         int cshift = 0) {
     using Ar = BipArith<T>;
     const uint32_t full = (1u << n) - 1u;
     const uint4 mk = __ldg(tab.masks + mask_index);
@@ -444,7 +450,8 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
     const uint32_t H = head_set(B, ones);
     const uint32_t J = full & ~B & (CLOW ? ~(ones & 1u) : 0xFFFFFFFFu);   // CLOW: not onto the head point
     const int nA = __popc(A);
-    const bool needclose = (ones != 0u) || (B == full);
+    const bool dead = (ones == 0u) && (B != full);
+    const bool needclose = !dead || SUB;
     if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
         const uint4 nk = __ldg(tab.masks + next_index);
         const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
@@ -471,6 +478,13 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
     }
     if (!needclose) return;   // no half-visited vertex and not full: disconnected, dropped
     const typename Ar::CV C = Ar::close_sum(csum, nfl, ci);
+    if (SUB && ones == 0u) {
+        if (active && lam == 0) {
+            const double c = Ar::to_double(C);
+            csub[(int64_t)B << cshift] = CLOW ? c : ldexp(c, __popc(B) - 1);
+        }
+        if (dead) return;
+    }
     if (ones) {
         const int k = __ffs(ones) - 1;
         const uint32_t bk = 1u << k;
@@ -494,7 +508,7 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
     }
 }
 
-template <typename T, bool CLOW>
+template <typename T, bool CLOW, bool SUB = false>
 __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ BipArgs a) {
     extern __shared__ __align__(16) unsigned char smem_bip[];
     __shared__ int s_batch;
@@ -532,6 +546,13 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
         const int n2 = 2 * n;
         const double *Mc = nullptr;
         if (active) Mc = a.M + a.moff[cfg] + (size_t)lam * n2 * n2;
+        double *cs = nullptr;
+        int csh = 0;
+        if (SUB && active) {
+            const int64_t key = a.csub_key[cfg];
+            cs = a.csub + (key >> 4);
+            csh = (int)(key & 15);
+        }
         const double cfac = sgn * a.loop_weight;
         for (int e = warp; e < n2 * n2; e += nwarps) {
             double val = active ? Mc[e] : 0.0;
@@ -563,8 +584,9 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
             const uint32_t first = tab.layer_first[ell];
             const uint32_t cnt = tab.layer_count[ell];
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
-                bip_mask<T, CLOW>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src, dst1,
-                            Ms, Md, lane, ci, nfl, seedsh, shifts, active, lam, cfg, a.out, a.status, a.prefetch);
+                bip_mask<T, CLOW, SUB>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src,
+                                       dst1, Ms, Md, lane, ci, nfl, seedsh, shifts, active, lam, cfg, a.out, a.status,
+                                       a.prefetch, cs, csh);
             __syncthreads();
         }
     }
@@ -586,6 +608,9 @@ struct BipLaunch {
     bool absmode = false;
     int precision = COS_FP64;
     bool clow = false;   // determinant weights without cycle factors (n_mat = 2 spin blocks)
+    double *csub = nullptr;              // all-subsets mode (FP64): see BipArgs
+    const int64_t *csub_key = nullptr;
+    bool allow_empty = false;            // order 0 = empty derived problem (skipped by the planner)
 };
 
 static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t stream) {
@@ -614,7 +639,8 @@ static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t str
     const size_t mel = (size_t)4 * L.n_max * L.n_max * kLanes;
     const size_t es = L.precision == COS_MIXED ? sizeof(float) : sizeof(double);
     const size_t smem = ((mel * es + 15) & ~size_t(15)) + mel * sizeof(double);
-    auto kern = L.precision == COS_DF64    ? (L.clow ? dp_bip_kernel<df64, true> : dp_bip_kernel<df64, false>)
+    auto kern = L.csub                     ? (L.clow ? dp_bip_kernel<double, true, true> : dp_bip_kernel<double, false, true>)
+                : L.precision == COS_DF64  ? (L.clow ? dp_bip_kernel<df64, true> : dp_bip_kernel<df64, false>)
                 : L.precision == COS_MIXED ? (L.clow ? dp_bip_kernel<float, true> : dp_bip_kernel<float, false>)
                                            : (L.clow ? dp_bip_kernel<double, true> : dp_bip_kernel<double, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -639,6 +665,8 @@ static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t str
     a.prefetch = 1;
     a.out = L.out;
     a.status = ws->status;
+    a.csub = L.csub;
+    a.csub_key = L.csub_key;
     e = cudaMemsetAsync(ws->queue, 0, sizeof(int), stream);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
     kern<<<grid, 512, smem, stream>>>(a);
@@ -648,7 +676,7 @@ static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t str
 }
 
 static cos_status run_bip(Workspace *ws, BipLaunch L, double *d_abs_mass, cudaStream_t stream) {
-    cos_status st = launch_plan_batches(ws, L.n_cfg, L.n_max, L.order, kLanes / L.n_mat, stream);
+    cos_status st = launch_plan_batches(ws, L.n_cfg, L.n_max, L.order, kLanes / L.n_mat, stream, L.allow_empty);
     if (st != COS_OK) return st;
     st = launch_bip(ws, L, stream);
     if (st != COS_OK || !d_abs_mass) return st;
@@ -700,6 +728,30 @@ cos_status bip_matrices_body(Workspace *ws, int n_cfg, int n_max, const int32_t 
         }
     L.out = d_out;
     return run_bip(ws, L, d_abs_mass, stream);
+}
+
+cos_status bip_subsets_dp(Workspace *ws, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                          int n_mat, int loop_weight, const double *h_sigma2, const double *d_M4, bool clow,
+                          double *d_csub, const int64_t *d_csub_key, bool allow_empty, cudaStream_t stream) {
+    BipLaunch L;
+    L.clow = clow;
+    L.precision = COS_FP64;
+    L.n_cfg = n_cfg;
+    L.n_max = n_max;
+    L.order = d_order;
+    L.M = d_M4;
+    L.moff = d_moff;
+    L.n_mat = n_mat;
+    L.loop_weight = loop_weight;
+    for (int l = 0; l < n_mat; ++l)
+        for (int s = 0; s < 2; ++s) {
+            L.sigma2[l][s] = h_sigma2 ? h_sigma2[l * 2 + s] : 0.0;
+            if (L.sigma2[l][s] != 0.0) L.shifts = true;
+        }
+    L.csub = d_csub;
+    L.csub_key = d_csub_key;
+    L.allow_empty = allow_empty;
+    return run_bip(ws, L, nullptr, stream);
 }
 
 // ------------------------------------------------------------------ reverse (adjoint) sweep

@@ -221,6 +221,11 @@ cos_status bip_matrices_body(Workspace *ws, int n_cfg, int n_max, const int32_t 
                              int n_mat, int loop_weight, const double *h_sigma2, const double *d_M4,
                              cos_precision precision, double *d_out, double *d_abs_mass, cudaStream_t stream,
                              bool clow = false);
+// Bipartite sweep in the all-subsets mode (FP64): planner (allow_empty: order-0 derived
+// problems skipped) + DP, c(S) written through d_csub / d_csub_key.
+cos_status bip_subsets_dp(Workspace *ws, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                          int n_mat, int loop_weight, const double *h_sigma2, const double *d_M4, bool clow,
+                          double *d_csub, const int64_t *d_csub_key, bool allow_empty, cudaStream_t stream);
 
 cos_status launch_gather(const cos_tables *t, int n_cfg, const int32_t *order, const int64_t *offset,
                          const int32_t *site, const double *tau, const int64_t *moff, int64_t mstride,

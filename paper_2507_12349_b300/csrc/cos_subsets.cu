@@ -1,5 +1,6 @@
 // All-subsets mode: the connected sum c(S) of every vertex subset S of each configuration, and
-// optionally the full sum a(S) over all (connected or not) decorated covers of S.
+// optionally the full sum a(S) over all (connected or not) decorated covers of S; square and
+// bipartite lattices, cycle factors or determinant weights.
 //
 // Connected sums.  The merged DP rooted at vertex 0 reaches, for every S containing 0, the
 // interaction mask mu = 2 * 1_S with no half-visited vertex left: its close is the sum over the
@@ -69,6 +70,39 @@ __global__ void subset_roots_kernel(int n_cfg, int n_max, int n_mat, const int32
             const int l = e / per, r = e % per;
             const int v = r / nd_ord, j = r % nd_ord;
             sub_M[dst + e] = src[(int64_t)l * nc * nc + (int64_t)(v + m) * nc + (j + m)];
+        }
+    }
+}
+
+// Bipartite layout: per flavor [2 n_c][2 n_c] with index (i * 2 + s); root m keeps rows and
+// columns 2m.. (vertices m.., both sublattices).  Derived problem d = c * n_max + m as above.
+__global__ void bip_subset_roots_kernel(int n_cfg, int n_max, int n_mat, const int32_t *order, const int64_t *moff,
+                                        const double *M4, int32_t *sub_order, int64_t *sub_moff, int64_t *sub_key,
+                                        double *sub_M) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nd = (int64_t)n_cfg * n_max;
+    const int64_t blk = 4 * root_offset(n_max, n_mat, n_max);
+    for (int64_t d = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; d < nd;
+         d += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t c = d / n_max;
+        const int m = (int)(d % n_max);
+        const int nc = order[c];
+        const bool valid = nc >= 1 && nc <= n_max;
+        const int nd_ord = (valid && m < nc) ? nc - m : 0;
+        const int64_t dst = c * blk + 4 * root_offset(n_max, n_mat, m);
+        if (lane == 0) {
+            sub_order[d] = valid ? nd_ord : (m == 0 ? -1 : 0);
+            sub_moff[d] = dst;
+            sub_key[d] = (((c << n_max)) << 4) | m;
+        }
+        if (nd_ord == 0) continue;
+        const double *src = M4 + moff[c];
+        const int w = 2 * nd_ord, wc = 2 * nc;
+        const int per = w * w;
+        for (int e = lane; e < n_mat * per; e += 32) {
+            const int l = e / per, r = e % per;
+            const int row = r / w, col = r % w;
+            sub_M[dst + e] = src[(int64_t)l * wc * wc + (int64_t)(row + 2 * m) * wc + (col + 2 * m)];
         }
     }
 }
@@ -222,9 +256,109 @@ static cos_status subsets_body(const char *fn, int n_cfg, int n_max, const int32
     return COS_OK;
 }
 
+// Bipartite lattices: the same mode on the sublattice-resolved sweep (FP64).  Orders up to
+// COS_BIP_NMAX; h_sigma2 [n_mat][2] (cycle factors) or the [2][2] diagonal shifts (clow).
+static cos_status bip_subsets_body(const char *fn, int n_cfg, int n_max, const int32_t *d_order,
+                                   const int64_t *d_moff, int n_mat, int loop_weight, const double *h_sigma2,
+                                   const double *d_M4, cos_precision precision, int all_roots, double *d_c,
+                                   double *d_a, bool clow, cudaStream_t s) {
+    if (n_cfg < 0 || n_mat < 1 || n_mat > COS_MAX_FLAVORS || loop_weight < 1) {
+        set_error(std::string(fn) + ": n_cfg < 0, n_mat outside [1, 8] or loop_weight < 1");
+        return COS_ERR_ARG;
+    }
+    if (n_max < 1 || n_max > COS_BIP_NMAX) {
+        set_error(std::string(fn) + ": n_max outside [1, 9]");
+        return COS_ERR_ORDER;
+    }
+    if (precision != COS_FP64) {
+        set_error(std::string(fn) + ": the bipartite all-subsets mode runs in COS_FP64");
+        return precision == COS_MIXED || precision == COS_DF64 ? COS_ERR_UNIMPLEMENTED : COS_ERR_ARG;
+    }
+    if (all_roots != 0 && all_roots != 1) {
+        set_error(std::string(fn) + ": all_roots must be 0 or 1");
+        return COS_ERR_ARG;
+    }
+    if (d_a && !all_roots) {
+        set_error(std::string(fn) + ": the full sums a(S) need every root (all_roots = 1)");
+        return COS_ERR_ARG;
+    }
+    if (n_cfg > 0 && (!d_order || !d_moff || !d_M4 || !d_c)) {
+        set_error(std::string(fn) + ": null device pointer");
+        return COS_ERR_ARG;
+    }
+    if (n_cfg == 0) return COS_OK;
+    if (all_roots && (int64_t)n_cfg * n_max > (int64_t)INT32_MAX) {
+        set_error(std::string(fn) + ": n_cfg * n_max exceeds the derived-problem limit 2^31 - 1");
+        return COS_ERR_ARG;
+    }
+    std::string err;
+    Workspace *ws = get_workspace(s, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    const int nsm = sm_count_of(ws->device);
+    const int threads = 256;
+    const int64_t total = (int64_t)n_cfg << n_max;
+    const int pf_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + threads - 1) / threads, 8LL * nsm));
+    subset_prefill_kernel<<<pf_blocks, threads, 0, s>>>(n_cfg, n_max, d_order, d_c);
+    cos_status st;
+    if (all_roots) {
+        const size_t nd = (size_t)n_cfg * n_max;
+        const size_t mdoubles = (size_t)n_cfg * (size_t)(4 * root_offset(n_max, n_mat, n_max));
+        st = ensure((void **)&ws->sub_order, &ws->sub_cap, nd, sizeof(int32_t), "subset orders");
+        if (st == COS_OK) st = ensure((void **)&ws->sub_moff, &ws->sub_moff_cap, nd, sizeof(int64_t), "subset offsets");
+        if (st == COS_OK) st = ensure((void **)&ws->sub_key, &ws->sub_key_cap, nd, sizeof(int64_t), "subset keys");
+        if (st == COS_OK) st = ensure((void **)&ws->sub_M, &ws->sub_M_cap, mdoubles, sizeof(double), "subset matrices");
+        if (st != COS_OK) return st;
+        const int rb = (int)std::max<size_t>(1, std::min<size_t>((nd * 32 + threads - 1) / threads, 8 * (size_t)nsm));
+        bip_subset_roots_kernel<<<rb, threads, 0, s>>>(n_cfg, n_max, n_mat, d_order, d_moff, d_M4, ws->sub_order,
+                                                       ws->sub_moff, ws->sub_key, ws->sub_M);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "bipartite subset set-up launch");
+        st = bip_subsets_dp(ws, (int)nd, n_max, ws->sub_order, ws->sub_moff, n_mat, loop_weight, h_sigma2, ws->sub_M,
+                            clow, d_c, ws->sub_key, true, s);
+    } else {
+        st = ensure((void **)&ws->sub_key, &ws->sub_key_cap, (size_t)n_cfg, sizeof(int64_t), "subset keys");
+        if (st != COS_OK) return st;
+        const int kb = std::max(1, std::min((n_cfg + threads - 1) / threads, 8 * nsm));
+        subset_keys_kernel<<<kb, threads, 0, s>>>(n_cfg, n_max, ws->sub_key);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "bipartite subset set-up launch");
+        st = bip_subsets_dp(ws, n_cfg, n_max, d_order, d_moff, n_mat, loop_weight, h_sigma2, d_M4, clow, d_c,
+                            ws->sub_key, false, s);
+    }
+    if (st != COS_OK || !d_a) return st;
+    const size_t smem = ((size_t)2 << n_max) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(subset_exp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "subset exponential smem attribute");
+    const int eb = std::max(1, std::min(n_cfg, 16 * nsm));
+    subset_exp_kernel<<<eb, threads, smem, s>>>(n_cfg, n_max, d_order, d_c, d_a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "subset exponential launch");
+    return COS_OK;
+}
+
 }  // namespace cosdp
 
 using namespace cosdp;
+
+extern "C" cos_status cos_connected_sum_bipartite_subsets(int n_cfg, int n_max, const int32_t *d_order,
+                                                          const int64_t *d_moff, int n_mat, int loop_weight,
+                                                          const double *h_sigma2, const double *d_M4,
+                                                          cos_precision precision, int all_roots, double *d_c,
+                                                          double *d_a, cos_stream_t stream) {
+    return bip_subsets_body("cos_connected_sum_bipartite_subsets", n_cfg, n_max, d_order, d_moff, n_mat, loop_weight,
+                            h_sigma2, d_M4, precision, all_roots, d_c, d_a, false, (cudaStream_t)stream);
+}
+
+extern "C" cos_status cos_connected_det_bipartite_subsets(int n_cfg, int n_max, const int32_t *d_order,
+                                                          const int64_t *d_moff, const double *h_alpha2,
+                                                          const double *d_M4, cos_precision precision, int all_roots,
+                                                          double *d_c, double *d_a, cos_stream_t stream) {
+    return bip_subsets_body("cos_connected_det_bipartite_subsets", n_cfg, n_max, d_order, d_moff, 2, 1, h_alpha2,
+                            d_M4, precision, all_roots, d_c, d_a, true, (cudaStream_t)stream);
+}
 
 extern "C" cos_status cos_connected_sum_subsets(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
                                                 int n_mat, int loop_weight, const double *h_sigma,
