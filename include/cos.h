@@ -265,8 +265,9 @@ cos_status cos_connected_sum_bipartite_matrices(int n_cfg, int n_max, const int3
 /* Gradient of the bipartite sums by the reverse sweep (the forward sweep re-run with every
  * layer kept, then walked backwards): d_gout[c] = dLoss/dc; d_out NULL or receives c;
  * d_gM4 NULL or dLoss/dM4 (layout and offsets of d_M4); d_gsigma2 NULL or [n_cfg][n_mat][2]
- * dLoss/dsigma_{l,s} (also at sigma = 0).  n_max <= 8 (three 2n x 2n matrices per lane in shared
- * memory; COS_ERR_ORDER above); FP64.  Other arguments as
+ * dLoss/dsigma_{l,s} (also at sigma = 0).  n_max <= COS_BIP_NMAX (up to 8 the dLoss/dM4
+ * accumulators sit in shared memory beside the two matrix copies, at 9 in the workspace:
+ * 4 (2 n_max)^2 x 32 doubles per CTA more); FP64.  Other arguments as
  * cos_connected_sum_bipartite_matrices. */
 cos_status cos_connected_sum_bipartite_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
                                                      const int64_t *d_moff, int n_mat, int loop_weight,
@@ -373,7 +374,7 @@ cos_status cos_connected_det_bipartite_matrices(int n_cfg, int n_max, const int3
 
 /* Gradient of the bipartite determinant-weight sums (the adjoint of the Alg. 1 sweep):
  * d_galpha2 NULL or [n_cfg][2][2] dLoss/dalpha_{b,s} (= minus the sublattice-s trace of
- * dLoss/dM4_b); other outputs as cos_connected_sum_bipartite_matrices_grad; n_max <= 8, FP64. */
+ * dLoss/dM4_b); other outputs and limits as cos_connected_sum_bipartite_matrices_grad; FP64. */
 cos_status cos_connected_det_bipartite_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
                                                      const int64_t *d_moff, const double *h_alpha2,
                                                      const double *d_M4, const double *d_gout, double *d_out,

@@ -767,7 +767,7 @@ cos_status bip_subsets_dp(Workspace *ws, int n_cfg, int n_max, const int32_t *d_
 // seeded block 1 only, Cbar(full) = gout, and dalpha_{b,s} = -sum_j dM_b[(j,s)][(j,s)].
 // Warps own endpoint units (v, s_v), unit v * 2 + s_v modulo the warp count (2n warps, at most
 // 16): one writer per dM row, no atomics.  Shared memory holds Ms, Md and dM, 3 x 4 n^2 doubles
-// per lane, so one CTA per SM: orders <= 8.
+// per lane, so one CTA per SM; at order 9 dM moves to the CTA's global scratch.
 struct BipAdjArgs {
     BipArgs f;
     size_t store_elems;     // forward storage per CTA (every layer of n_max) * 32
@@ -775,6 +775,7 @@ struct BipAdjArgs {
     const double *gout;
     double *gM;             // NULL or dLoss/dM4, layout of M4
     double *gsig;           // NULL or [n_cfg][n_mat][2]
+    int dm_global;          // dM in the CTA's global scratch (after the adjoint slots), not shared memory
 };
 
 // Targets q in [Q0, Q1) of one endpoint (v, s_v): loads first, then the multiply-adds.
@@ -854,13 +855,19 @@ __device__ __forceinline__ void bip_adj_dispatch(int nT, const double *fsrc, dou
         COS_BADJ(14)
         COS_BADJ(15)
         COS_BADJ(16)
-        default:
+        COS_BADJ(17)
+        COS_BADJ(18)
+        default:   // larger counts do not occur (at most 2 n - 1 targets, n <= COS_BIP_NMAX)
             break;
     }
 #undef COS_BADJ
 }
 
-constexpr int kBipAdjMaxN = 8;
+constexpr int kBipAdjMaxN = COS_BIP_NMAX;
+// Largest order whose dM accumulators fit in shared memory beside Ms and Md (3 x 4 n^2 doubles
+// per lane); above it dM lives in the CTA's global scratch, [(v,s)][(j,t)][lane] as in shared
+// memory (coalesced per warp, mostly L1 / L2 resident).
+constexpr int kBipAdjSmemMaxN = 8;
 
 template <bool CLOW>
 __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_constant__ BipAdjArgs a) {
@@ -875,9 +882,11 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
     const int nsm = 4 * f.smem_n * f.smem_n * kLanes;
     double *Ms = smem_ba;             // extension matrices (shifted diagonal)
     double *Md = smem_ba + nsm;       // close matrices times sgn w
-    double *dM = smem_ba + 2 * nsm;   // dc/dM accumulators [(v,s)][(j,t)][lane]
-    double *store = reinterpret_cast<double *>(f.scratch) + (size_t)blockIdx.x * (a.store_elems + 2 * a.adj_slot_elems);
+    double *store = reinterpret_cast<double *>(f.scratch) +
+                    (size_t)blockIdx.x * (a.store_elems + 2 * a.adj_slot_elems + (a.dm_global ? (size_t)nsm : 0));
     double *adj = store + a.store_elems;
+    // dc/dM accumulators [(v,s)][(j,t)][lane]
+    double *dM = a.dm_global ? adj + 2 * a.adj_slot_elems : smem_ba + 2 * nsm;
     const int nfl = f.nf_lanes;
     const int lam = lane % nfl;
     const int ci = lane / nfl;
@@ -1074,9 +1083,11 @@ static cos_status launch_bip_adjoint(Workspace *ws, const BipLaunch &L, const do
     for (int l = 0; l <= 2 * L.n_max; ++l) total_slots += ho.layer_slots[l];
     const size_t store_elems = total_slots * kLanes;
     const size_t adj_slot_elems = (size_t)ho.max_slots * kLanes;
-    const size_t per_cta = (store_elems + 2 * adj_slot_elems) * sizeof(double);
+    const bool dm_global = L.n_max > kBipAdjSmemMaxN;
+    const size_t mat_elems = (size_t)4 * L.n_max * L.n_max * kLanes;
+    const size_t per_cta = (store_elems + 2 * adj_slot_elems + (dm_global ? mat_elems : 0)) * sizeof(double);
     const int warps = std::min(16, std::max(4, 2 * L.n_max));
-    const size_t smem = (size_t)3 * 4 * L.n_max * L.n_max * kLanes * sizeof(double);
+    const size_t smem = (dm_global ? 2 : 3) * mat_elems * sizeof(double);
     auto kern = L.clow ? dp_bip_adjoint_kernel<true> : dp_bip_adjoint_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "bipartite adjoint smem attribute");
@@ -1117,6 +1128,7 @@ static cos_status launch_bip_adjoint(Workspace *ws, const BipLaunch &L, const do
     a.gout = gout;
     a.gM = gM;
     a.gsig = gsig;
+    a.dm_global = dm_global ? 1 : 0;
     e = cudaMemsetAsync(ws->queue, 0, sizeof(int), stream);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
     kern<<<grid, warps * 32, smem, stream>>>(a);
@@ -1131,11 +1143,6 @@ static cos_status bip_grad_body(const char *fn, int n_cfg, int n_max, const int3
                                 cudaStream_t stream) {
     cos_status st = check_bip(n_cfg, n_max, d_order, d_moff, n_mat, loop_weight, d_M4, COS_FP64, d_gout, fn);
     if (st != COS_OK) return st;
-    if (n_max > kBipAdjMaxN) {
-        set_error(std::string(fn) + ": the bipartite gradient keeps three 2n x 2n matrices per lane in shared "
-                                    "memory: n_max <= 8");
-        return COS_ERR_ORDER;
-    }
     if (n_cfg == 0) return COS_OK;
     std::string err;
     Workspace *ws = get_workspace(stream, &err);

@@ -80,7 +80,7 @@ def test_argument_errors_are_synchronous():
     assert lib.cos_connected_det_matrices_grad(1, 4, None, None, None, None, None, None, None, None, None) == -1
     assert lib.cos_connected_det_matrices_grad(0, 4, None, None, None, None, None, None, None, None, None) == 0
     assert lib.cos_connected_det_subsets(1, 4, fake, fake, None, fake, 1, 1, fake, None, None) == -6
-    assert lib.cos_connected_sum_bipartite_matrices_grad(1, 9, fake, fake, 2, 1, None, fake, fake, None, None, None,
+    assert lib.cos_connected_sum_bipartite_matrices_grad(1, 10, fake, fake, 2, 1, None, fake, fake, None, None, None,
                                                          None) == -2
     assert lib.cos_connected_det_bipartite_matrices_grad(0, 4, None, None, None, None, None, None, None, None,
                                                          None) == 0

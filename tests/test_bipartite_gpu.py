@@ -224,8 +224,9 @@ def test_workload_honeycomb_order8_sampled():
 # the __float128 oracle are exact up to rounding; dc/dsigma2 (dc/dalpha2) from an exact
 # polynomial fit; tolerance |err| <= 1e-9 (|ref| + largest reference entry).
 
-def run_bip_grad(M4s, n_mat, wt, s2, gout, det=False):
+def run_bip_grad(M4s, n_mat, wt, s2, gout, det=False, n_max=None):
     order = np.array([m.shape[1] for m in M4s], dtype=np.int32)
+    n_max = int(order.max()) if n_max is None else n_max
     moff = B.bipartite_matrix_offsets(order, n_mat)
     d_order = torch.tensor(order, device="cuda")
     d_moff = torch.tensor(moff, device="cuda")
@@ -236,10 +237,9 @@ def run_bip_grad(M4s, n_mat, wt, s2, gout, det=False):
     gs = torch.full((nc, n_mat, 2), float("nan"), dtype=torch.float64, device="cuda")
     g = torch.tensor(gout, dtype=torch.float64, device="cuda")
     if det:
-        B.cos_connected_det_bipartite_matrices_grad(int(order.max()), d_order, d_moff, s2, d_M, g, out, gM, gs)
+        B.cos_connected_det_bipartite_matrices_grad(n_max, d_order, d_moff, s2, d_M, g, out, gM, gs)
     else:
-        B.cos_connected_sum_bipartite_matrices_grad(int(order.max()), d_order, d_moff, n_mat, wt, s2, d_M, g, out,
-                                                    gM, gs)
+        B.cos_connected_sum_bipartite_matrices_grad(n_max, d_order, d_moff, n_mat, wt, s2, d_M, g, out, gM, gs)
     B.cos_sync_status()
     gm = gM.cpu().numpy()
     return (out.cpu().numpy(), [gm[moff[c]:moff[c] + m.size].reshape(m.shape) for c, m in enumerate(M4s)],
@@ -330,11 +330,50 @@ def test_bipartite_grad_orders_7_8_euler(det):
         assert abs(lhs - 2 * n * out[c]) <= 1e-9 * scale, (c, n, lhs, 2 * n * out[c])
 
 
-def test_bipartite_grad_rejects_order9():
-    M4s = rand_m4(1, 1, 2, 9)
-    with pytest.raises(B.CosError) as e:
-        run_bip_grad(M4s, 2, 1, None, np.ones(1))
-    assert e.value.status == -2
+@pytest.mark.parametrize("det", [False, True])
+def test_bipartite_grad_global_accumulators_bitwise(det):
+    """n_max = 9 keeps dc/dM4 in the workspace instead of shared memory: on orders up to 8 the
+    gradient is bit for bit that of the shared-memory sweep (n_max = 8)."""
+    orders = [8, 5, 8, 7]
+    s2 = [[0.05, -0.04], [0.03, 0.06]]
+    M4s = [rand_m4(9600 + c, 1, 2, n)[0] for c, n in enumerate(orders)]
+    gout = np.linspace(0.7, 1.3, len(M4s))
+    a = run_bip_grad(M4s, 2, 1, s2, gout, det, n_max=8)
+    b = run_bip_grad(M4s, 2, 1, s2, gout, det, n_max=9)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+    for x, y in zip(a[1], b[1]):
+        assert np.array_equal(x, y)
+
+
+def test_bipartite_grad_order9():
+    """Order 9 (accumulators in the workspace): Euler's relation for both sweeps, the forward
+    values equal the bipartite sweeps' bit for bit, and the CoS relation carried to the
+    gradient: with two flavors, loop weight 1 and no shifts dc_CoS/dM4 = 2^9 dc_det/dM4."""
+    M4s = rand_m4(9650, 2, 2, 9, 0.8)
+    order = np.array([9, 9], dtype=np.int32)
+    moff = B.bipartite_matrix_offsets(order, 2)
+    d_M = torch.tensor(np.concatenate([m.ravel() for m in M4s]), device="cuda")
+    args = (9, torch.tensor(order, device="cuda"), torch.tensor(moff, device="cuda"))
+    s2 = [[0.06, -0.03], [0.02, 0.04]]
+    for det in (False, True):
+        out, gM, gs = run_bip_grad(M4s, 2, 1, s2, np.ones(2), det)
+        ref = torch.empty(2, dtype=torch.float64, device="cuda")
+        if det:
+            B.cos_connected_det_bipartite_matrices(*args, s2, d_M, "fp64", ref)
+        else:
+            B.cos_connected_sum_bipartite_matrices(*args, 2, 1, s2, d_M, "fp64", ref)
+        B.cos_sync_status()
+        assert np.array_equal(out, ref.cpu().numpy())
+        for c in range(2):
+            terms = M4s[c] * gM[c]
+            lhs = terms.sum() + float((np.array(s2) * gs[c]).sum())
+            scale = np.abs(terms).sum() + float(np.abs(np.array(s2) * gs[c]).sum()) + 18 * abs(out[c])
+            assert abs(lhs - 18 * out[c]) <= 1e-9 * scale, (det, c, lhs, 18 * out[c])
+    _, g_cos, _ = run_bip_grad(M4s, 2, 1, None, np.ones(2), False)
+    _, g_det, _ = run_bip_grad(M4s, 2, 1, None, np.ones(2), True)
+    for c in range(2):
+        scale = np.abs(g_cos[c]).max()
+        assert np.max(np.abs(g_cos[c] - 2.0 ** 9 * g_det[c])) <= 1e-9 * scale, c
 
 
 @pytest.mark.parametrize("det", [False, True])
