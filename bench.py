@@ -828,7 +828,8 @@ def measure_forms(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
 
 def bipartite_arm(args):
     """Profiling runs of the bipartite path alone: the honeycomb workload's gather + DP from
-    vertex coordinates, at its order or --order, --n-cfg configurations, CUDA-event timing."""
+    vertex coordinates, at its order or --order, --n-cfg configurations, CUDA-event timing;
+    with --subsets, gather + the all-subsets mode (c(S) and a(S) of every subset, FP64)."""
     import torch
     from paper_2507_12349_b300 import binding as B
     B.lib()
@@ -842,6 +843,18 @@ def bipartite_arm(args):
     out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
     flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     fn = lambda: B.cos_connected_sum_bipartite_batch(tabs, n, *d, args.precision, out)
+    if args.subsets:
+        moff = torch.as_tensor(B.bipartite_matrix_offsets(cfgs.order, n_mat), device="cuda")
+        M4 = torch.empty(n_cfg * n_mat * 4 * n * n, dtype=torch.float64, device="cuda")
+        c = torch.empty(n_cfg << n, dtype=torch.float64, device="cuda")
+        a = torch.empty_like(c)
+        info = tabs.info()   # the tables' shift weights and loop weight, as the batch call uses them
+        sig2 = [[info.sigma2[l][s] for s in range(2)] for l in range(n_mat)]
+        wt = info.n_flavors if info.symmetric else 1
+
+        def fn():
+            B.cos_gather_bipartite(tabs, *d, moff, M4)
+            B.cos_connected_sum_bipartite_subsets(n, d[0], moff, n_mat, wt, sig2, M4, c, a)
     for _ in range(max(1, args.warmup)):
         fn()
     B.cos_sync_status()
@@ -850,10 +863,12 @@ def bipartite_arm(args):
     s = B.cos_bipartite_structure(n)
     t = statistics.mean(ts)
     fl = n_cfg * n_mat * 2.0 * (s.fma_ext + s.fma_close)
-    print(json.dumps({"metric": "bipartite connected-sum configs/s (honeycomb, sublattices summed)",
+    print(json.dumps({"metric": ("bipartite all-subsets configs/s (c(S), a(S) of every subset)" if args.subsets else
+                                 "bipartite connected-sum configs/s (honeycomb, sublattices summed)"),
                       "value": n_cfg / t, "unit": "configs/s", "order": n, "configs": n_cfg,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
-                      "tflops": fl / t / 1e12, "dtype": {"fp64": "f64", "df64": "f32 pairs (df64)"}.get(
+                      "tflops": None if args.subsets else fl / t / 1e12,
+                      "dtype": "f64" if args.subsets else {"fp64": "f64", "df64": "f32 pairs (df64)"}.get(
                           args.precision, args.precision)}), flush=True)
     tabs.close()
 
