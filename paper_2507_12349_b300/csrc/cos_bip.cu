@@ -1098,8 +1098,10 @@ static cos_status launch_bip_adjoint(Workspace *ws, const BipLaunch &L, const do
     int grid = std::max(1, std::min(nsm, max_batches));
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+        // every layer of the largest order is kept per CTA (GBs at the top orders): as many CTAs
+        // as fit in the free memory
         const size_t avail = ws->scratch_bytes + (size_t)(0.85 * (double)free_b);
-        while (grid > 1 && (size_t)grid * per_cta > avail) grid = std::max(1, grid / 2);
+        grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)grid, avail / per_cta));
     }
     ws->last_grid = grid;
     cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "bipartite adjoint scratch");
