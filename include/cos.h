@@ -246,7 +246,8 @@ cos_status cos_build_propagators_honeycomb(const cos_honeycomb_model *model, cos
 /* M4^l[(i,s)][(j,t)] = G_l^{st}(R_i - R_j, tau_i - tau_j) (same interpolation and dt <= 0 reading
  * as cos_gather).  Per configuration c the block [n_mat][2 n_c][2 n_c] (row index i*2 + s,
  * column j*2 + t, s, t = 0 for A, 1 for B) starts at d_moff[c] in d_M4.  d_site[k] is the unit
- * cell r_1 + L r_2 in [0, L^2).  Orders in [1, COS_BIP_NMAX]. */
+ * cell r_1 + L r_2 in [0, L^2).  Orders in [1, COS_BIP_NMAX]; a configuration with another
+ * order or a negative d_moff[c] is skipped and reported through the status word. */
 cos_status cos_gather_bipartite(const cos_tables *tables, int n_cfg, const int32_t *d_order,
                                 const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
                                 const int64_t *d_moff, double *d_M4, cos_stream_t stream);
@@ -371,6 +372,18 @@ cos_status cos_connected_det_bipartite_matrices(int n_cfg, int n_max, const int3
                                                 const int64_t *d_moff, const double *h_alpha2,
                                                 const double *d_M4, cos_precision precision,
                                                 double *d_out, double *d_abs_mass, cos_stream_t stream);
+
+/* Gather + bipartite determinant-weight sweep from vertex coordinates: two-flavor (spin up,
+ * spin down) honeycomb tables of cos_build_propagators_honeycomb (tables collapsed to one
+ * matrix for equal spins serve both blocks); the diagonal shifts of the determinant weights
+ * are h_alpha2 (NULL or host [2][2], spin then sublattice), not the tables' shift weights.
+ * Other arguments as cos_connected_sum_bipartite_batch and cos_connected_det_bipartite_matrices;
+ * COS_ERR_ARG for tables with another flavor count. */
+cos_status cos_connected_det_bipartite_batch(const cos_tables *tables, int n_cfg, int n_max,
+                                             const int32_t *d_order, const int64_t *d_offset,
+                                             const int32_t *d_site, const double *d_tau,
+                                             const double *h_alpha2, cos_precision precision,
+                                             double *d_out, double *d_abs_mass, cos_stream_t stream);
 
 /* Gradient of the bipartite determinant-weight sums (the adjoint of the Alg. 1 sweep):
  * d_galpha2 NULL or [n_cfg][2][2] dLoss/dalpha_{b,s} (= minus the sublattice-s trace of

@@ -105,7 +105,8 @@ __global__ void hc_gather_kernel(const double *__restrict__ G, int L, int n_tau,
     const double scale = (double)(n_tau - 1) / beta;
     for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_cfg; c += warps) {
         const int n = order[c];
-        if (n < 1 || n > COS_BIP_NMAX) {
+        // a negative offset marks an order above the caller's n_max (its slot would overflow)
+        if (n < 1 || n > COS_BIP_NMAX || moff[c] < 0) {
             if (lane == 0) atomicOr(status, kStatusOrder);
             continue;
         }
@@ -193,8 +194,24 @@ cos_status launch_gather_bip(const cos_tables *t, int n_cfg, const int32_t *orde
 }  // namespace
 
 // Device work of the coordinates path: per-configuration matrix offsets, gather, DP.
-__global__ void hc_moff_kernel(int n_cfg, int n_mat, const int32_t *order, int64_t *moff, int64_t stride) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cfg; c += gridDim.x * blockDim.x) moff[c] = c * stride;
+// Slot offsets of the batch entry's own matrix layout (stride = the slot of order n_max); -1 for
+// an order outside [1, n_max], which the gather then skips and flags.
+__global__ void hc_moff_kernel(int n_cfg, int n_max, const int32_t *order, int64_t *moff, int64_t stride) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cfg; c += gridDim.x * blockDim.x)
+        moff[c] = (order[c] >= 1 && order[c] <= n_max) ? (int64_t)c * stride : -1;
+}
+
+// Collapsed (symmetric) tables serve both spin blocks: copy block 0 ([2n][2n]) into block 1.
+__global__ void hc_dup_block_kernel(int n_cfg, const int32_t *order, const int64_t *moff, double *M) {
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_cfg; c += warps) {
+        const int n = order[c];
+        if (n < 1 || n > COS_BIP_NMAX || moff[c] < 0) continue;
+        const int nn = 4 * n * n;
+        double *b = M + moff[c];
+        for (int e = lane; e < nn; e += 32) b[nn + e] = b[e];
+    }
 }
 
 }  // namespace cosdp
@@ -316,7 +333,7 @@ extern "C" cos_status cos_connected_sum_bipartite_batch(const cos_tables *t, int
     if (st != COS_OK) return st;
     int nsm = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
-    hc_moff_kernel<<<std::max(1, std::min((n_cfg + 255) / 256, 8 * nsm)), 256, 0, s>>>(n_cfg, n_mat, d_order,
+    hc_moff_kernel<<<std::max(1, std::min((n_cfg + 255) / 256, 8 * nsm)), 256, 0, s>>>(n_cfg, n_max, d_order,
                                                                                        ws->moff, stride);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "bipartite offsets");
@@ -330,4 +347,60 @@ extern "C" cos_status cos_connected_sum_bipartite_batch(const cos_tables *t, int
     const int loop_weight = t->symmetric ? t->model.n_flavors : 1;
     return bip_matrices_body(ws, n_cfg, n_max, d_order, ws->moff, n_mat, loop_weight, sig2, ws->M, precision, d_out,
                              d_abs_mass, s);
+}
+
+extern "C" cos_status cos_connected_det_bipartite_batch(const cos_tables *t, int n_cfg, int n_max,
+                                                        const int32_t *d_order, const int64_t *d_offset,
+                                                        const int32_t *d_site, const double *d_tau,
+                                                        const double *h_alpha2, cos_precision precision,
+                                                        double *d_out, double *d_abs_mass, cos_stream_t stream) {
+    const char *fn = "cos_connected_det_bipartite_batch";
+    if (!t || !t->bipartite || t->model.n_flavors != 2) {
+        set_error(std::string(fn) + ": needs two-flavor (spin up, spin down) honeycomb tables");
+        return COS_ERR_ARG;
+    }
+    if (n_cfg < 0) {
+        set_error(std::string(fn) + ": n_cfg < 0");
+        return COS_ERR_ARG;
+    }
+    if (n_max < 1 || n_max > COS_BIP_NMAX) {
+        set_error(std::string(fn) + ": n_max outside [1, 9]");
+        return COS_ERR_ORDER;
+    }
+    if (precision != COS_FP64 && precision != COS_MIXED && precision != COS_DF64) {
+        set_error(std::string(fn) + ": unknown precision");
+        return COS_ERR_ARG;
+    }
+    if (n_cfg == 0) return COS_OK;
+    if (!d_order || !d_offset || !d_site || !d_tau || !d_out) {
+        set_error(std::string(fn) + ": null device pointer");
+        return COS_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::string err;
+    Workspace *ws = get_workspace(s, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    const int64_t stride = (int64_t)2 * 4 * n_max * n_max;   // two spin blocks per configuration
+    cos_status st = ensure((void **)&ws->M, &ws->M_cap, (size_t)n_cfg * stride, sizeof(double), "bipartite matrices");
+    if (st == COS_OK) st = ensure((void **)&ws->moff, &ws->moff_cap, (size_t)n_cfg, sizeof(int64_t), "matrix offsets");
+    if (st != COS_OK) return st;
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
+    const int blocks = std::max(1, std::min((n_cfg + 255) / 256, 8 * nsm));
+    hc_moff_kernel<<<blocks, 256, 0, s>>>(n_cfg, n_max, d_order, ws->moff, stride);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "bipartite offsets");
+    st = launch_gather_bip(t, n_cfg, d_order, d_offset, d_site, d_tau, ws->moff, ws->M, ws->status, s);
+    if (st != COS_OK) return st;
+    if (t->n_mat == 1) {
+        const int wblocks = std::max(1, std::min((n_cfg * 32 + 255) / 256, 8 * nsm));
+        hc_dup_block_kernel<<<wblocks, 256, 0, s>>>(n_cfg, d_order, ws->moff, ws->M);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "spin block copy");
+    }
+    return bip_matrices_body(ws, n_cfg, n_max, d_order, ws->moff, 2, 1, h_alpha2, ws->M, precision, d_out,
+                             d_abs_mass, s, true);
 }

@@ -524,3 +524,48 @@ def test_det_model_autograd():
     assert np.array_equal(c.detach().cpu().numpy(), ref.cpu().numpy())
     assert np.allclose(mu_t.grad.numpy(), gmu.sum(0).cpu().numpy(), rtol=1e-14, atol=0)
     assert np.allclose(al_t.grad.numpy(), gal.sum(0).cpu().numpy(), rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("sym", [False, True])
+def test_det_bipartite_batch_from_coordinates(sym):
+    """Gather + bipartite determinant sweep in one call: bit for bit the two-step path
+    (cos_gather_bipartite, then the matrices entry) and, on samples, the oracle's gather with
+    Alg. 1; with equal spins the collapsed tables serve both blocks."""
+    m = I.WORKLOADS["hc_su2_af_n8"].model
+    model = I.HoneycombModel(m.L, m.t, m.beta, m.U, m.mu, m.alpha, (0.25, 0.25) if sym else m.delta, m.n_tau)
+    nc = 300
+    cfgs = I.make_configs(model, 3, 7, nc, 19)
+    tabs = B.honeycomb_tables_for(model)
+    n_mat = tabs.info().n_mat
+    assert n_mat == (1 if sym else 2)
+    d = B.configs_to_device(cfgs)
+    al = [[0.05, -0.03], [0.02, 0.06]]
+    out = torch.full((nc,), float("nan"), dtype=torch.float64, device="cuda")
+    mass = torch.full_like(out, float("nan"))
+    B.cos_connected_det_bipartite_batch(tabs, 7, *d, al, "fp64", out, mass)
+    order = cfgs.order.astype(np.int32)
+    moff = B.bipartite_matrix_offsets(order, n_mat)
+    M4 = torch.empty(int(n_mat * 4 * (order.astype(np.int64) ** 2).sum()), dtype=torch.float64, device="cuda")
+    B.cos_gather_bipartite(tabs, *d, torch.tensor(moff, device="cuda"), M4)
+    host = M4.cpu().numpy()
+    blocks = []
+    for c in range(nc):
+        w2 = 4 * int(order[c]) ** 2
+        b = host[moff[c]:moff[c] + n_mat * w2]
+        blocks.append(np.concatenate([b, b]) if n_mat == 1 else b)
+    moff2 = torch.tensor(B.bipartite_matrix_offsets(order, 2), device="cuda")
+    ref = torch.full_like(out, float("nan"))
+    rmass = torch.full_like(out, float("nan"))
+    B.cos_connected_det_bipartite_matrices(7, d[0], moff2, al, torch.tensor(np.concatenate(blocks), device="cuda"),
+                                           "fp64", ref, rmass)
+    B.cos_sync_status()
+    tabs.close()
+    got, gmass = out.cpu().numpy(), mass.cpu().numpy()
+    assert np.array_equal(got, ref.cpu().numpy()) and np.array_equal(gmass, rmass.cpu().numpy())
+    otabs = HC.hc_model_tables(model)
+    for c in (0, nc // 2, nc - 1):
+        o, n = int(cfgs.offset[c]), int(cfgs.order[c])
+        G4 = HC.hc_gather_one(otabs, cfgs.site[o:o + n], cfgs.tau[o:o + n], model.L, model.beta)
+        r = O.det_clow(G4, al, prec="ld")
+        rm = O.det_clow(G4, al, absmode=True)
+        assert abs(got[c] - r) <= bound("fp64", n, rm) + 1e-13 * rm, (c, got[c], r)
