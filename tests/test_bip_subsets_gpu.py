@@ -207,11 +207,12 @@ def test_other_precisions_are_rejected():
 
 
 def test_honeycomb_workload_order8_sampled():
-    """The honeycomb workload's gathered matrices (SU(2), staggered shift, n = 8), determinant
-    weights: c(V) equals the plain call bitwise; sampled subsets of two configurations against
-    Alg. 1 of the oracle on the oracle's own gather."""
+    """The honeycomb workload at the benchmark's size (2 x 10^4 configurations, SU(2),
+    staggered shift, n = 8), determinant weights, in the call the bench times: c(V) equals the
+    plain call bitwise; sampled subsets of three configurations against Alg. 1 of the oracle on
+    the oracle's own gather."""
     w = I.WORKLOADS["hc_su2_af_n8"]
-    nc = 2000
+    nc = w.n_cfg
     cfgs = I.workload_configs(w, nc)
     tabs = B.honeycomb_tables_for(w.model)
     d = B.configs_to_device(cfgs)
@@ -232,7 +233,7 @@ def test_honeycomb_workload_order8_sampled():
     assert np.array_equal(c[:, 255], out.cpu().numpy())
     otabs = HC.hc_model_tables(w.model)
     rng = np.random.default_rng(8)
-    for k in (0, nc - 1):
+    for k in (0, nc // 2, nc - 1):
         o = int(cfgs.offset[k])
         G4 = HC.hc_gather_one(otabs, cfgs.site[o:o + 8], cfgs.tau[o:o + 8], w.model.L, w.model.beta)
         for S in [255, 1, 128] + [int(x) for x in rng.choice(np.arange(2, 255), 8, replace=False)]:
