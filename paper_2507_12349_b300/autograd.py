@@ -193,7 +193,7 @@ class _ConnectedBipartite(torch.autograd.Function):
 
 def connected_sum_bipartite(M4, sigma2, order, moff, n_max: int, n_mat: int, loop_weight: int = 1):
     """Bipartite connected sums of packed M4 blocks ([n_mat][2n][2n] at moff[cfg]); sigma2: CPU
-    tensor [n_mat][2] of shift weights (may require grad) or None.  Orders <= 8 for the gradient."""
+    tensor [n_mat][2] of shift weights (may require grad) or None.  Orders up to 9, as the forward."""
     return _ConnectedBipartite.apply(M4, sigma2, order, moff, n_max, n_mat, loop_weight, False)
 
 
