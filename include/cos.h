@@ -373,6 +373,27 @@ cos_status cos_connected_det_bipartite_matrices(int n_cfg, int n_max, const int3
                                                 const double *d_M4, cos_precision precision,
                                                 double *d_out, double *d_abs_mass, cos_stream_t stream);
 
+/* Gradient of the bipartite sums from vertex coordinates (honeycomb tables): gather, the
+ * reverse sweep of cos_connected_sum_bipartite_matrices_grad, then the chain rule through
+ * the tables (no counterpart in the paper, which computes no gradients):
+ *   dc/dmu_l    = sum over (i,s),(j,t) of dc/dM4_l[(i,s)][(j,t)] dG_l^{st}/dmu (the gather's
+ *                 interpolation of a dG/dmu table: the same 2 x 2 matrix function with
+ *                 f(E) = exp(-E tau)(1 - n_F(E)) replaced by its mu derivative), G depending
+ *                 on mu_l - alpha_l;
+ *   dc/dalpha_l = -(that sum) + (dc/dsigma_{l,A} + dc/dsigma_{l,B}) / U, sigma_{l,A/B} =
+ *                 (alpha_l +- delta_l) / U.
+ * For collapsed (symmetric) tables the common derivative is split evenly over the flavors.
+ * d_gM4 / d_gmoff: NULL, or dLoss/dM4 written at d_gmoff[c] as [n_mat][2 n_c][2 n_c].
+ * d_gmu, d_galpha: NULL or [n_cfg][n_flavors] (per configuration, scaled by d_gout[c]).
+ * Builds the dG/dmu table on first use (synchronizing `stream`).  Other arguments, limits
+ * and errors as cos_connected_sum_bipartite_batch and
+ * cos_connected_sum_bipartite_matrices_grad; FP64. */
+cos_status cos_connected_sum_bipartite_grad(const cos_tables *tables, int n_cfg, int n_max,
+                                            const int32_t *d_order, const int64_t *d_offset,
+                                            const int32_t *d_site, const double *d_tau, const double *d_gout,
+                                            double *d_out, double *d_gM4, const int64_t *d_gmoff,
+                                            double *d_gmu, double *d_galpha, cos_stream_t stream);
+
 /* Gather + bipartite determinant-weight sweep from vertex coordinates: two-flavor (spin up,
  * spin down) honeycomb tables of cos_build_propagators_honeycomb (tables collapsed to one
  * matrix for equal spins serve both blocks); the diagonal shifts of the determinant weights

@@ -28,9 +28,20 @@ __device__ __forceinline__ double tau_w(double E, double tau, double beta) {
     return exp(E * (beta - tau)) / (1.0 + exp(beta * E));
 }
 
+// n_F(E) = 1 / (1 + exp(beta E)), overflow-free.
+__device__ __forceinline__ double fermi(double E, double beta) {
+    if (E >= 0.0) {
+        const double x = exp(-beta * E);
+        return x / (1.0 + x);
+    }
+    return 1.0 / (1.0 + exp(beta * E));
+}
+
 // W0, Wg for every (matrix, momentum, tau point), and eps(k) (Re, Im) per momentum.
+// deriv: their derivatives with respect to mu instead.  E = -m +- r with m = mu - alpha, so
+// d f(E) / d mu = -f'(E) = f(E) (tau - beta n_F(E)); d and eps(k), hence r, do not depend on mu.
 __global__ void hc_weight_kernel(int L, int n_mat, int n_tau, double t, double beta, const double *dm,
-                                 double *W0, double *Wg, double *eps_re, double *eps_im) {
+                                 double *W0, double *Wg, double *eps_re, double *eps_im, int deriv) {
     const int LL = L * L;
     const size_t total = (size_t)n_mat * LL * n_tau;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
@@ -43,7 +54,11 @@ __global__ void hc_weight_kernel(int L, int n_mat, int n_tau, double t, double b
         const double d = dm[2 * l], mm = dm[2 * l + 1];
         const double r = sqrt(d * d + re * re + im * im);
         const double tau = beta * m / (n_tau - 1);
-        const double fp = tau_w(-mm + r, tau, beta), fm = tau_w(-mm - r, tau, beta);
+        double fp = tau_w(-mm + r, tau, beta), fm = tau_w(-mm - r, tau, beta);
+        if (deriv) {
+            fp *= tau - beta * fermi(-mm + r, beta);
+            fm *= tau - beta * fermi(-mm - r, beta);
+        }
         W0[i] = 0.5 * (fp + fm);
         Wg[i] = r > 0.0 ? (fp - fm) / (2.0 * r) : 0.0;
         if (l == 0 && m == 0) {
@@ -141,7 +156,8 @@ __global__ void hc_gather_kernel(const double *__restrict__ G, int L, int n_tau,
     }
 }
 
-cos_status build_hc_tables(cos_tables *t, cudaStream_t stream) {
+// deriv: the dG/dmu tables (into d_dG) instead of G.
+cos_status build_hc_tables(cos_tables *t, cudaStream_t stream, bool deriv = false) {
     const int L = t->model.L, LL = L * L, n_tau = t->model.n_tau, n_mat = t->n_mat;
     const size_t nW = (size_t)n_mat * LL * n_tau;
     double *d_dm = nullptr, *d_W0 = nullptr, *d_Wg = nullptr, *d_er = nullptr, *d_ei = nullptr;
@@ -155,15 +171,16 @@ cos_status build_hc_tables(cos_tables *t, cudaStream_t stream) {
     if (e == cudaSuccess) e = cudaMalloc(&d_Wg, sizeof(double) * nW);
     if (e == cudaSuccess) e = cudaMalloc(&d_er, sizeof(double) * LL);
     if (e == cudaSuccess) e = cudaMalloc(&d_ei, sizeof(double) * LL);
-    if (e == cudaSuccess) e = cudaMalloc(&t->d_G, sizeof(double) * nW * 4);
+    double **dst = deriv ? &t->d_dG : &t->d_G;
+    if (e == cudaSuccess) e = cudaMalloc(dst, sizeof(double) * nW * 4);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_dm, h_dm, sizeof(double) * 2 * n_mat, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) {
         const int wb = (int)std::min<size_t>((nW + 255) / 256, 65535);
         hc_weight_kernel<<<wb, 256, 0, stream>>>(L, n_mat, n_tau, t->model.t, t->model.beta, d_dm, d_W0, d_Wg, d_er,
-                                                 d_ei);
+                                                 d_ei, deriv ? 1 : 0);
         const int kb = (int)std::min<size_t>((4 * nW + 255) / 256, 65535);
         hc_ksum_kernel<<<kb, 256, 2 * L * sizeof(double), stream>>>(L, n_mat, n_tau, d_dm, d_W0, d_Wg, d_er, d_ei,
-                                                                     t->d_G);
+                                                                     *dst);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
@@ -172,7 +189,13 @@ cos_status build_hc_tables(cos_tables *t, cudaStream_t stream) {
     cudaFree(d_Wg);
     cudaFree(d_er);
     cudaFree(d_ei);
-    if (e != cudaSuccess) return cuda_fail(e, "honeycomb tables");
+    if (e != cudaSuccess) {
+        if (deriv) {   // no half-built derivative table is left behind for a later call
+            cudaFree(t->d_dG);
+            t->d_dG = nullptr;
+        }
+        return cuda_fail(e, "honeycomb tables");
+    }
     return COS_OK;
 }
 
@@ -199,6 +222,80 @@ cos_status launch_gather_bip(const cos_tables *t, int n_cfg, const int32_t *orde
 __global__ void hc_moff_kernel(int n_cfg, int n_max, const int32_t *order, int64_t *moff, int64_t stride) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cfg; c += gridDim.x * blockDim.x)
         moff[c] = (order[c] >= 1 && order[c] <= n_max) ? (int64_t)c * stride : -1;
+}
+
+// Chain rule through the honeycomb tables, one warp per configuration:
+//   dc/dmu_l = sum over (i,s),(j,t) of dc/dM4_l[(i,s)][(j,t)] dG_l^{st}/dmu (the gather's
+//   interpolation of the dG/dmu table), and dc/dalpha_l = -(that sum) + (dc/dsigma_{l,A} +
+//   dc/dsigma_{l,B}) / U, since sigma_{l,A/B} = (alpha_l +- delta_l) / U and G depends on mu - alpha.
+// Collapsed (symmetric) tables: the common derivative split evenly over the flavors.
+__global__ void hc_chain_kernel(const double *__restrict__ dG, int L, int n_tau, double beta, int n_mat,
+                                int n_flavors, int symmetric, double U, int n_cfg, const int32_t *__restrict__ order,
+                                const int64_t *__restrict__ offset, const int32_t *__restrict__ site,
+                                const double *__restrict__ tau, const double *__restrict__ gM,
+                                const int64_t *__restrict__ moff, const double *__restrict__ gsig2,
+                                double *__restrict__ gmu, double *__restrict__ galpha) {
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int LL = L * L;
+    const double scale = (double)(n_tau - 1) / beta;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_cfg; c += warps) {
+        const int n = order[c];
+        if (n < 1 || n > COS_BIP_NMAX || moff[c] < 0) continue;
+        const int64_t o = offset[c];
+        const int n2 = 2 * n, nn = n2 * n2;
+        const double *g = gM + moff[c];
+        for (int l = 0; l < n_mat; ++l) {
+            double acc = 0.0;
+            for (int e = lane; e < nn; e += 32) {
+                const int rr = e / n2, cc = e % n2;
+                const int i = rr >> 1, s = rr & 1, j = cc >> 1, tt = cc & 1;
+                const int si = site[o + i], sj = site[o + j];
+                if (si < 0 || si >= LL || sj < 0 || sj >= LL) continue;
+                const int d1 = ((si % L) - (sj % L) + L) % L;
+                const int d2 = ((si / L) - (sj / L) + L) % L;
+                const double dt = tau[o + i] - tau[o + j];
+                double sg = 1.0, tv = dt;
+                if (dt <= 0.0) {
+                    sg = -1.0;
+                    tv = dt + beta;
+                }
+                const double x = tv * scale;
+                int m = (int)floor(x);
+                m = max(0, min(m, n_tau - 2));
+                const double f = x - m;
+                const double *row = dG + ((((size_t)l * 2 + s) * 2 + tt) * LL + d1 + L * d2) * n_tau + m;
+                acc = fma(g[(size_t)l * nn + e], sg * fma(f, row[1] - row[0], row[0]), acc);
+            }
+            for (int w = 16; w >= 1; w >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, w);
+            if (lane == 0) {
+                const double gs = gsig2 ? gsig2[((int64_t)c * n_mat + l) * 2] + gsig2[((int64_t)c * n_mat + l) * 2 + 1]
+                                        : 0.0;
+                if (symmetric) {
+                    for (int q = 0; q < n_flavors; ++q) {
+                        if (gmu) gmu[(int64_t)c * n_flavors + q] = acc / n_flavors;
+                        if (galpha) galpha[(int64_t)c * n_flavors + q] = (-acc + gs / U) / n_flavors;
+                    }
+                } else {
+                    if (gmu) gmu[(int64_t)c * n_flavors + l] = acc;
+                    if (galpha) galpha[(int64_t)c * n_flavors + l] = -acc + gs / U;
+                }
+            }
+        }
+    }
+}
+
+// dc/dM4 from the entry's stride layout (moff) into the caller's blocks at gmoff.
+__global__ void hc_copy_blocks_kernel(int n_cfg, int n_mat, const int32_t *order, const int64_t *moff,
+                                      const double *src, const int64_t *gmoff, double *dst) {
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_cfg; c += warps) {
+        const int n = order[c];
+        if (n < 1 || n > COS_BIP_NMAX || moff[c] < 0) continue;
+        const int cnt = n_mat * 4 * n * n;
+        for (int e = lane; e < cnt; e += 32) dst[gmoff[c] + e] = src[moff[c] + e];
+    }
 }
 
 // Collapsed (symmetric) tables serve both spin blocks: copy block 0 ([2n][2n]) into block 1.
@@ -403,4 +500,76 @@ extern "C" cos_status cos_connected_det_bipartite_batch(const cos_tables *t, int
     }
     return bip_matrices_body(ws, n_cfg, n_max, d_order, ws->moff, 2, 1, h_alpha2, ws->M, precision, d_out,
                              d_abs_mass, s, true);
+}
+
+extern "C" cos_status cos_connected_sum_bipartite_grad(const cos_tables *t, int n_cfg, int n_max,
+                                                       const int32_t *d_order, const int64_t *d_offset,
+                                                       const int32_t *d_site, const double *d_tau,
+                                                       const double *d_gout, double *d_out, double *d_gM4,
+                                                       const int64_t *d_gmoff, double *d_gmu, double *d_galpha,
+                                                       cos_stream_t stream) {
+    const char *fn = "cos_connected_sum_bipartite_grad";
+    if (!t || !t->bipartite) {
+        set_error(std::string(fn) + ": tables missing or not bipartite");
+        return COS_ERR_ARG;
+    }
+    if (n_cfg < 0) {
+        set_error(std::string(fn) + ": n_cfg < 0");
+        return COS_ERR_ARG;
+    }
+    if (n_max < 1 || n_max > COS_BIP_NMAX) {
+        set_error(std::string(fn) + ": n_max outside [1, 9]");
+        return COS_ERR_ORDER;
+    }
+    if (n_cfg == 0) return COS_OK;
+    if (!d_order || !d_offset || !d_site || !d_tau || !d_gout || (d_gM4 && !d_gmoff)) {
+        set_error(std::string(fn) + ": null device pointer (d_gM4 needs d_gmoff)");
+        return COS_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::string err;
+    Workspace *ws = get_workspace(s, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    cos_tables *tm = const_cast<cos_tables *>(t);
+    if ((d_gmu || d_galpha) && !tm->d_dG) {
+        cos_status st = build_hc_tables(tm, s, true);
+        if (st != COS_OK) return st;
+    }
+    const int n_mat = t->n_mat;
+    const int64_t stride = (int64_t)n_mat * 4 * n_max * n_max;
+    cos_status st = ensure((void **)&ws->M, &ws->M_cap, (size_t)n_cfg * stride, sizeof(double), "bipartite matrices");
+    if (st == COS_OK) st = ensure((void **)&ws->moff, &ws->moff_cap, (size_t)n_cfg, sizeof(int64_t), "matrix offsets");
+    if (st == COS_OK) st = ensure((void **)&ws->gM, &ws->gM_cap, (size_t)n_cfg * stride, sizeof(double), "gradient");
+    if (st == COS_OK)
+        st = ensure((void **)&ws->gsig, &ws->gsig_cap, (size_t)n_cfg * n_mat * 2, sizeof(double), "shift gradient");
+    if (st != COS_OK) return st;
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
+    hc_moff_kernel<<<std::max(1, std::min((n_cfg + 255) / 256, 8 * nsm)), 256, 0, s>>>(n_cfg, n_max, d_order,
+                                                                                       ws->moff, stride);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "bipartite offsets");
+    st = launch_gather_bip(t, n_cfg, d_order, d_offset, d_site, d_tau, ws->moff, ws->M, ws->status, s);
+    if (st != COS_OK) return st;
+    double sig2[2 * COS_MAX_FLAVORS];
+    for (int l = 0; l < n_mat; ++l) {
+        sig2[2 * l] = t->sigma2[l][0];
+        sig2[2 * l + 1] = t->sigma2[l][1];
+    }
+    const int loop_weight = t->symmetric ? t->model.n_flavors : 1;
+    st = bip_grad_dp(fn, n_cfg, n_max, d_order, ws->moff, n_mat, loop_weight, sig2, ws->M, d_gout, d_out, ws->gM,
+                     ws->gsig, s);
+    if (st != COS_OK) return st;
+    const int wblocks = std::max(1, std::min((n_cfg * 32 + 255) / 256, 8 * nsm));
+    if (d_gM4) hc_copy_blocks_kernel<<<wblocks, 256, 0, s>>>(n_cfg, n_mat, d_order, ws->moff, ws->gM, d_gmoff, d_gM4);
+    if (d_gmu || d_galpha)
+        hc_chain_kernel<<<wblocks, 256, 0, s>>>(t->d_dG, t->model.L, t->model.n_tau, t->model.beta, n_mat,
+                                                 t->model.n_flavors, t->symmetric, t->model.U, n_cfg, d_order,
+                                                 d_offset, d_site, d_tau, ws->gM, ws->moff, ws->gsig, d_gmu, d_galpha);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "bipartite chain rule launches");
+    return COS_OK;
 }

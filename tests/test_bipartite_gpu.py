@@ -396,3 +396,77 @@ def test_bipartite_autograd_function(det):
     assert np.array_equal(c.detach().cpu().numpy(), out)
     assert np.array_equal(M4.grad.cpu().numpy(), np.concatenate([g.ravel() for g in gM]))
     assert np.allclose(s2.grad.numpy(), gs.sum(0), rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("sym", [False, True])
+def test_bipartite_grad_from_coordinates(sym):
+    """dLoss/dM4 from vertex coordinates is the matrices entry's on the blocks
+    cos_gather_bipartite writes (bitwise); dLoss/dmu and dLoss/dalpha match central differences
+    of the oracle pipeline (honeycomb tables, gather, the sum over sublattice assignments)
+    rebuilt at mu +- h and alpha +- h.  Collapsed tables move every flavor together and split
+    the derivative evenly."""
+    base = I.WORKLOADS["hc_su2_af_n8"].model
+    mu = [0.1, 0.1] if sym else [-0.15, 0.2]
+    alpha = [0.05, 0.05] if sym else [0.1, -0.05]
+    delta = (0.25, 0.25) if sym else base.delta
+    mk = lambda m, a: I.HoneycombModel(base.L, base.t, base.beta, base.U, tuple(m), tuple(a), delta, base.n_tau)
+    model = mk(mu, alpha)
+    nc = 24
+    cfgs = I.make_configs(model, 3, 5, nc, 31)
+    tabs = B.honeycomb_tables_for(model)
+    info = tabs.info()
+    n_mat = info.n_mat
+    assert n_mat == (1 if sym else 2)
+    d = B.configs_to_device(cfgs)
+    order = cfgs.order.astype(np.int32)
+    total = int(n_mat * 4 * (order.astype(np.int64) ** 2).sum())
+    gmoff = torch.tensor(B.bipartite_matrix_offsets(order, n_mat), device="cuda")
+    gout = np.linspace(0.5, 1.5, nc)
+    g = torch.tensor(gout, device="cuda")
+    nan = float("nan")
+    out = torch.full((nc,), nan, dtype=torch.float64, device="cuda")
+    gM = torch.full((total,), nan, dtype=torch.float64, device="cuda")
+    gmu = torch.full((nc, 2), nan, dtype=torch.float64, device="cuda")
+    ga = torch.full_like(gmu, nan)
+    B.cos_connected_sum_bipartite_grad(tabs, 5, *d, g, out, gM, gmoff, gmu, ga)
+    M4 = torch.empty(total, dtype=torch.float64, device="cuda")
+    B.cos_gather_bipartite(tabs, *d, gmoff, M4)
+    s2 = [[info.sigma2[l][s] for s in range(2)] for l in range(n_mat)]
+    wt = info.n_flavors if info.symmetric else 1
+    out2 = torch.full_like(out, nan)
+    gM2 = torch.full_like(gM, nan)
+    B.cos_connected_sum_bipartite_matrices_grad(5, d[0], gmoff, n_mat, wt, s2, M4, g, out2, gM2, None)
+    B.cos_sync_status()
+    tabs.close()
+    assert np.array_equal(out.cpu().numpy(), out2.cpu().numpy())
+    assert np.array_equal(gM.cpu().numpy(), gM2.cpu().numpy())
+    gmu, ga = gmu.cpu().numpy(), ga.cpu().numpy()
+
+    picks = (0, nc // 2, nc - 1)
+
+    def oracle_c(m2, a2):
+        m = mk(m2, a2)
+        t = HC.hc_model_tables(m)
+        vals = []
+        for c in picks:
+            o, n = int(cfgs.offset[c]), int(cfgs.order[c])
+            G4 = HC.hc_gather_one(t, cfgs.site[o:o + n], cfgs.tau[o:o + n], m.L, m.beta)
+            vals.append(O.bip(G4, np.array(m.sigma2), method="sum_dp", prec="ld"))
+        return np.array(vals)
+
+    h = 1e-6
+    for which, base_v, got in (("mu", mu, gmu), ("alpha", alpha, ga)):
+        for l in range(2):
+            if sym:
+                p = [x + h for x in base_v]
+                q = [x - h for x in base_v]
+            else:
+                p = list(base_v); p[l] += h
+                q = list(base_v); q[l] -= h
+            args_p = (p, alpha) if which == "mu" else (mu, p)
+            args_q = (q, alpha) if which == "mu" else (mu, q)
+            fd = (oracle_c(*args_p) - oracle_c(*args_q)) / (2 * h) / (2 if sym else 1)
+            for k, c in enumerate(picks):
+                want = gout[c] * fd[k]
+                assert got[c, l] == pytest.approx(want, rel=2e-5, abs=1e-7 * max(1.0, abs(want))), \
+                    (which, l, c, got[c, l], want)
