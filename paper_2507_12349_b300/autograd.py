@@ -201,3 +201,35 @@ def connected_det_bipartite(M4, alpha2, order, moff, n_max: int):
     """Bipartite SU(2) determinant-weight sums of packed M4 blocks ([2][2n][2n] at moff[cfg]);
     alpha2: CPU tensor [2][2] of diagonal shifts (may require grad) or None."""
     return _ConnectedBipartite.apply(M4, alpha2, order, moff, n_max, 2, 1, True)
+
+
+class _ConnectedBipartiteModel(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, mu, alpha, model, d_cfgs, n_max):
+        tabs = B.cos_build_propagators_honeycomb(model.L, model.t, model.beta, model.U, [float(x) for x in mu],
+                                                 [float(x) for x in alpha], list(model.delta), model.n_tau)
+        order, offset, site, tau = d_cfgs
+        out = torch.empty(order.numel(), dtype=torch.float64, device=order.device)
+        B.cos_connected_sum_bipartite_batch(tabs, n_max, order, offset, site, tau, "fp64", out)
+        ctx.tabs = tabs
+        ctx.d_cfgs = d_cfgs
+        ctx.n_max = n_max
+        ctx.nf = len(mu)
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        order, offset, site, tau = ctx.d_cfgs
+        gmu = torch.empty(order.numel(), ctx.nf, dtype=torch.float64, device=order.device)
+        gal = torch.empty_like(gmu)
+        B.cos_connected_sum_bipartite_grad(ctx.tabs, ctx.n_max, order, offset, site, tau,
+                                           gout.detach().to(torch.float64).contiguous(), gmu=gmu, galpha=gal)
+        ctx.tabs.close()
+        return gmu.sum(0).cpu(), gal.sum(0).cpu(), None, None, None
+
+
+def connected_sum_bipartite_model(mu, alpha, model, d_cfgs, n_max: int):
+    """Bipartite (honeycomb) connected sums from vertex coordinates for chemical potentials mu
+    and uniform shifts alpha (CPU tensors of n_flavors values, differentiable); the staggered
+    shifts delta and the other fields from the inputs.HoneycombModel `model`."""
+    return _ConnectedBipartiteModel.apply(mu, alpha, model, d_cfgs, n_max)

@@ -470,3 +470,31 @@ def test_bipartite_grad_from_coordinates(sym):
                 want = gout[c] * fd[k]
                 assert got[c, l] == pytest.approx(want, rel=2e-5, abs=1e-7 * max(1.0, abs(want))), \
                     (which, l, c, got[c, l], want)
+
+
+def test_bipartite_model_autograd():
+    """connected_sum_bipartite_model: the forward equals cos_connected_sum_bipartite_batch bit for
+    bit, and mu.grad / alpha.grad are cos_connected_sum_bipartite_grad's per-configuration
+    gradients summed with the weights."""
+    base = I.WORKLOADS["hc_su2_af_n8"].model
+    mu, alpha = [-0.1, 0.15], [0.05, -0.02]
+    model = I.HoneycombModel(base.L, base.t, base.beta, base.U, tuple(mu), tuple(alpha), base.delta, base.n_tau)
+    nc = 48
+    cfgs = I.make_configs(model, 3, 6, nc, 41)
+    d = B.configs_to_device(cfgs)
+    mu_t = torch.tensor(mu, dtype=torch.float64, requires_grad=True)
+    al_t = torch.tensor(alpha, dtype=torch.float64, requires_grad=True)
+    c = AG.connected_sum_bipartite_model(mu_t, al_t, model, d, 6)
+    w = torch.linspace(-1.0, 2.0, nc, dtype=torch.float64, device="cuda")
+    (c * w).sum().backward()
+    tabs = B.honeycomb_tables_for(model)
+    ref = torch.empty(nc, dtype=torch.float64, device="cuda")
+    B.cos_connected_sum_bipartite_batch(tabs, 6, *d, "fp64", ref)
+    gmu = torch.empty(nc, 2, dtype=torch.float64, device="cuda")
+    gal = torch.empty_like(gmu)
+    B.cos_connected_sum_bipartite_grad(tabs, 6, *d, w, gmu=gmu, galpha=gal)
+    B.cos_sync_status()
+    tabs.close()
+    assert np.array_equal(c.detach().cpu().numpy(), ref.cpu().numpy())
+    assert np.allclose(mu_t.grad.numpy(), gmu.sum(0).cpu().numpy(), rtol=1e-14, atol=0)
+    assert np.allclose(al_t.grad.numpy(), gal.sum(0).cpu().numpy(), rtol=1e-14, atol=0)
