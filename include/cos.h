@@ -414,6 +414,25 @@ cos_status cos_connected_det_bipartite_matrices_grad(int n_cfg, int n_max, const
                                                      const double *d_M4, const double *d_gout, double *d_out,
                                                      double *d_gM4, double *d_galpha2, cos_stream_t stream);
 
+/* Gradient of the bipartite determinant-weight sums from vertex coordinates (no counterpart
+ * in the paper, which computes no gradients): the gather of cos_connected_det_bipartite_batch,
+ * the reverse sweep of cos_connected_det_bipartite_matrices_grad, then the chain rule through
+ * the honeycomb tables as cos_connected_sum_bipartite_grad:
+ *   d_gM4 / d_gmoff  NULL, or dLoss/dM4 written at d_gmoff[c] as [2][2 n_c][2 n_c] (both spin
+ *                    blocks, also for collapsed tables, where the blocks are equal);
+ *   d_gmu            NULL or [n_cfg][2]: dLoss/dmu_b; for collapsed tables the derivative of
+ *                    the common matrix (the blocks' sum) split evenly over the two spins;
+ *   d_galpha2        NULL or [n_cfg][2][2]: dLoss/dalpha_{b,s} of the diagonal shifts h_alpha2
+ *                    (= minus the sublattice-s trace of dLoss/dM4_b).
+ * Builds the dG/dmu table on first use when d_gmu is given (synchronizing `stream`).  Other
+ * arguments and errors as cos_connected_det_bipartite_batch; FP64. */
+cos_status cos_connected_det_bipartite_grad(const cos_tables *tables, int n_cfg, int n_max,
+                                            const int32_t *d_order, const int64_t *d_offset,
+                                            const int32_t *d_site, const double *d_tau, const double *h_alpha2,
+                                            const double *d_gout, double *d_out, double *d_gM4,
+                                            const int64_t *d_gmoff, double *d_gmu, double *d_galpha2,
+                                            cos_stream_t stream);
+
 /* Every vertex subset of the bipartite determinant-weight sums: d_c[c * 2^n_max + S] = c(S),
  * the connected part of sum_s det(A_up[S,s]) det(A_dn[S,s]) over the sublattice assignments s
  * of S (the close of the Alg. 1 sweep at the mask with S fully visited), and with d_a, a(S)

@@ -36,6 +36,7 @@ EXPORTS = [
     "cos_connected_det_subsets", "cos_connected_det_batch", "cos_connected_sum_bipartite_matrices_grad",
     "cos_connected_det_bipartite_matrices_grad", "cos_connected_det_grad", "cos_connected_sum_bipartite_subsets",
     "cos_connected_det_bipartite_subsets", "cos_connected_det_bipartite_batch", "cos_connected_sum_bipartite_grad",
+    "cos_connected_det_bipartite_grad",
     "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_sync_status", "cos_status_string",
     "cos_last_error", "cos_structure", "cos_peak_probe",
     "cos_plan_create_batch", "cos_plan_create_matrices", "cos_plan_launch", "cos_plan_status", "cos_plan_grid",
@@ -331,6 +332,18 @@ def cos_connected_sum_bipartite_grad(tables: Tables, n_max: int, order, offset, 
                                                   _ptr(gout, "f64"), _ptr(out, "f64"), _ptr(gM4, "f64"),
                                                   _ptr(gmoff, "i64"), _ptr(gmu, "f64"), _ptr(galpha, "f64"),
                                                   _stream(stream)), "cos_connected_sum_bipartite_grad")
+
+
+def cos_connected_det_bipartite_grad(tables: Tables, n_max: int, order, offset, site, tau, alpha2, gout, out=None,
+                                     gM4=None, gmoff=None, gmu=None, galpha2=None, stream=None):
+    """Gradient of the bipartite determinant-weight sums from vertex coordinates: dLoss/dM4
+    ([2][2 n_c][2 n_c] at gmoff), dLoss/dmu ([n_cfg][2]) and dLoss/dalpha2 ([n_cfg][2][2])."""
+    _check(lib().cos_connected_det_bipartite_grad(tables.handle, int(order.numel()), int(n_max), _ptr(order, "i32"),
+                                                  _ptr(offset, "i64"), _ptr(site, "i32"), _ptr(tau, "f64"),
+                                                  _sig2(alpha2, 2), _ptr(gout, "f64"), _ptr(out, "f64"),
+                                                  _ptr(gM4, "f64"), _ptr(gmoff, "i64"), _ptr(gmu, "f64"),
+                                                  _ptr(galpha2, "f64"), _stream(stream)),
+           "cos_connected_det_bipartite_grad")
 
 
 def cos_connected_det_bipartite_batch(tables: Tables, n_max: int, order, offset, site, tau, alpha2, precision: str,

@@ -1175,9 +1175,9 @@ static cos_status bip_grad_body(const char *fn, int n_cfg, int n_max, const int3
 
 cos_status bip_grad_dp(const char *fn, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
                        int n_mat, int loop_weight, const double *h_sigma2, const double *d_M4, const double *d_gout,
-                       double *d_out, double *d_gM4, double *d_gsigma2, cudaStream_t stream) {
+                       double *d_out, double *d_gM4, double *d_gsigma2, cudaStream_t stream, bool clow) {
     return bip_grad_body(fn, n_cfg, n_max, d_order, d_moff, n_mat, loop_weight, h_sigma2, d_M4, d_gout, d_out, d_gM4,
-                         d_gsigma2, false, stream);
+                         d_gsigma2, clow, stream);
 }
 
 }  // namespace cosdp

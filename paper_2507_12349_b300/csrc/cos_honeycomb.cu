@@ -311,6 +311,20 @@ __global__ void hc_dup_block_kernel(int n_cfg, const int32_t *order, const int64
     }
 }
 
+// Collapsed tables: both spin blocks came from one matrix, so its gradient is the blocks' sum
+// (folded into block 0 for the chain rule).
+__global__ void hc_fold_block_kernel(int n_cfg, const int32_t *order, const int64_t *moff, double *g) {
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_cfg; c += warps) {
+        const int n = order[c];
+        if (n < 1 || n > COS_BIP_NMAX || moff[c] < 0) continue;
+        const int nn = 4 * n * n;
+        double *b = g + moff[c];
+        for (int e = lane; e < nn; e += 32) b[e] += b[nn + e];
+    }
+}
+
 }  // namespace cosdp
 
 using namespace cosdp;
@@ -571,5 +585,77 @@ extern "C" cos_status cos_connected_sum_bipartite_grad(const cos_tables *t, int 
                                                  d_offset, d_site, d_tau, ws->gM, ws->moff, ws->gsig, d_gmu, d_galpha);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "bipartite chain rule launches");
+    return COS_OK;
+}
+
+extern "C" cos_status cos_connected_det_bipartite_grad(const cos_tables *t, int n_cfg, int n_max,
+                                                       const int32_t *d_order, const int64_t *d_offset,
+                                                       const int32_t *d_site, const double *d_tau,
+                                                       const double *h_alpha2, const double *d_gout, double *d_out,
+                                                       double *d_gM4, const int64_t *d_gmoff, double *d_gmu,
+                                                       double *d_galpha2, cos_stream_t stream) {
+    const char *fn = "cos_connected_det_bipartite_grad";
+    if (!t || !t->bipartite || t->model.n_flavors != 2) {
+        set_error(std::string(fn) + ": needs two-flavor (spin up, spin down) honeycomb tables");
+        return COS_ERR_ARG;
+    }
+    if (n_cfg < 0) {
+        set_error(std::string(fn) + ": n_cfg < 0");
+        return COS_ERR_ARG;
+    }
+    if (n_max < 1 || n_max > COS_BIP_NMAX) {
+        set_error(std::string(fn) + ": n_max outside [1, 9]");
+        return COS_ERR_ORDER;
+    }
+    if (n_cfg == 0) return COS_OK;
+    if (!d_order || !d_offset || !d_site || !d_tau || !d_gout || (d_gM4 && !d_gmoff)) {
+        set_error(std::string(fn) + ": null device pointer (d_gM4 needs d_gmoff)");
+        return COS_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::string err;
+    Workspace *ws = get_workspace(s, &err);
+    if (!ws) {
+        set_error(err);
+        return COS_ERR_CUDA;
+    }
+    cos_tables *tm = const_cast<cos_tables *>(t);
+    if (d_gmu && !tm->d_dG) {
+        cos_status st = build_hc_tables(tm, s, true);
+        if (st != COS_OK) return st;
+    }
+    const int64_t stride = (int64_t)2 * 4 * n_max * n_max;   // two spin blocks per configuration
+    cos_status st = ensure((void **)&ws->M, &ws->M_cap, (size_t)n_cfg * stride, sizeof(double), "bipartite matrices");
+    if (st == COS_OK) st = ensure((void **)&ws->moff, &ws->moff_cap, (size_t)n_cfg, sizeof(int64_t), "matrix offsets");
+    if (st == COS_OK) st = ensure((void **)&ws->gM, &ws->gM_cap, (size_t)n_cfg * stride, sizeof(double), "gradient");
+    if (st == COS_OK) st = ensure((void **)&ws->gsig, &ws->gsig_cap, (size_t)n_cfg * 4, sizeof(double), "alpha gradient");
+    if (st != COS_OK) return st;
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
+    hc_moff_kernel<<<std::max(1, std::min((n_cfg + 255) / 256, 8 * nsm)), 256, 0, s>>>(n_cfg, n_max, d_order,
+                                                                                       ws->moff, stride);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "bipartite offsets");
+    st = launch_gather_bip(t, n_cfg, d_order, d_offset, d_site, d_tau, ws->moff, ws->M, ws->status, s);
+    if (st != COS_OK) return st;
+    const int wblocks = std::max(1, std::min((n_cfg * 32 + 255) / 256, 8 * nsm));
+    if (t->n_mat == 1) hc_dup_block_kernel<<<wblocks, 256, 0, s>>>(n_cfg, d_order, ws->moff, ws->M);
+    st = bip_grad_dp(fn, n_cfg, n_max, d_order, ws->moff, 2, 1, h_alpha2, ws->M, d_gout, d_out, ws->gM, ws->gsig, s,
+                     true);
+    if (st != COS_OK) return st;
+    if (d_gM4) hc_copy_blocks_kernel<<<wblocks, 256, 0, s>>>(n_cfg, 2, d_order, ws->moff, ws->gM, d_gmoff, d_gM4);
+    if (d_galpha2) {
+        e = cudaMemcpyAsync(d_galpha2, ws->gsig, (size_t)n_cfg * 4 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "alpha gradient copy");
+    }
+    if (d_gmu) {
+        if (t->n_mat == 1) hc_fold_block_kernel<<<wblocks, 256, 0, s>>>(n_cfg, d_order, ws->moff, ws->gM);
+        // dc/dmu_b through the dG/dmu tables; the tables' own shift weights play no part here
+        hc_chain_kernel<<<wblocks, 256, 0, s>>>(t->d_dG, t->model.L, t->model.n_tau, t->model.beta, t->n_mat, 2,
+                                                 t->symmetric, t->model.U, n_cfg, d_order, d_offset, d_site, d_tau,
+                                                 ws->gM, ws->moff, nullptr, d_gmu, nullptr);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "determinant gradient launches");
     return COS_OK;
 }

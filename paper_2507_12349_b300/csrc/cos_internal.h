@@ -221,10 +221,11 @@ cos_status bip_matrices_body(Workspace *ws, int n_cfg, int n_max, const int32_t 
                              int n_mat, int loop_weight, const double *h_sigma2, const double *d_M4,
                              cos_precision precision, double *d_out, double *d_abs_mass, cudaStream_t stream,
                              bool clow = false);
-// Bipartite reverse sweep (cycle factors, FP64) on matrices at d_moff; dc/dM4 at the same offsets.
+// Bipartite reverse sweep (FP64) on matrices at d_moff; dc/dM4 at the same offsets.  clow:
+// determinant weights (n_mat = 2 spin blocks, h_sigma2 = the diagonal shifts alpha2).
 cos_status bip_grad_dp(const char *fn, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
                        int n_mat, int loop_weight, const double *h_sigma2, const double *d_M4, const double *d_gout,
-                       double *d_out, double *d_gM4, double *d_gsigma2, cudaStream_t stream);
+                       double *d_out, double *d_gM4, double *d_gsigma2, cudaStream_t stream, bool clow = false);
 // Bipartite sweep in the all-subsets mode (FP64): planner (allow_empty: order-0 derived
 // problems skipped) + DP, c(S) written through d_csub / d_csub_key.
 cos_status bip_subsets_dp(Workspace *ws, int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,

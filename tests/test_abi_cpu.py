@@ -67,6 +67,8 @@ def test_argument_errors_are_synchronous():
     assert lib.cos_connected_det_bipartite_batch(None, 1, 4, fake, fake, fake, fake, None, 0, fake, None, None) == -1
     assert lib.cos_connected_sum_bipartite_grad(None, 1, 4, fake, fake, fake, fake, fake, None, None, None, None, None,
                                                 None) == -1
+    assert lib.cos_connected_det_bipartite_grad(None, 1, 4, fake, fake, fake, fake, None, fake, None, None, None, None,
+                                                None, None) == -1
     # bipartite all-subsets: orders up to 9, FP64 only, all_roots 0 or 1
     assert lib.cos_connected_sum_bipartite_subsets(1, 10, fake, fake, 1, 1, None, fake, 0, 1, fake, None, None) == -2
     assert lib.cos_connected_sum_bipartite_subsets(1, 4, fake, fake, 1, 1, None, fake, 1, 1, fake, None, None) == -6

@@ -569,3 +569,76 @@ def test_det_bipartite_batch_from_coordinates(sym):
         r = O.det_clow(G4, al, prec="ld")
         rm = O.det_clow(G4, al, absmode=True)
         assert abs(got[c] - r) <= bound("fp64", n, rm) + 1e-13 * rm, (c, got[c], r)
+
+
+@pytest.mark.parametrize("sym", [False, True])
+def test_det_bipartite_grad_from_coordinates(sym):
+    """Bipartite determinant weights from vertex coordinates: dLoss/dM4 and dLoss/dalpha2 bit
+    for bit the matrices entry's on the gathered blocks; dLoss/dmu against central differences
+    of the oracle pipeline (honeycomb tables, gather, Alg. 1) rebuilt at mu +- h; collapsed
+    tables move both spins together and split the derivative evenly."""
+    m0 = I.WORKLOADS["hc_su2_af_n8"].model
+    mu = [0.1, 0.1] if sym else [-0.15, 0.2]
+    delta = (0.25, 0.25) if sym else m0.delta
+    mk = lambda m: I.HoneycombModel(m0.L, m0.t, m0.beta, m0.U, tuple(m), (0.0, 0.0), delta, m0.n_tau)
+    model = mk(mu)
+    nc = 24
+    cfgs = I.make_configs(model, 3, 5, nc, 37)
+    tabs = B.honeycomb_tables_for(model)
+    n_mat = tabs.info().n_mat
+    assert n_mat == (1 if sym else 2)
+    d = B.configs_to_device(cfgs)
+    al = [[0.05, -0.03], [0.02, 0.06]]
+    order = cfgs.order.astype(np.int32)
+    moff2 = torch.tensor(B.bipartite_matrix_offsets(order, 2), device="cuda")
+    total2 = int(8 * (order.astype(np.int64) ** 2).sum())
+    gout = np.linspace(0.5, 1.5, nc)
+    g = torch.tensor(gout, device="cuda")
+    nan = float("nan")
+    out = torch.full((nc,), nan, dtype=torch.float64, device="cuda")
+    gM = torch.full((total2,), nan, dtype=torch.float64, device="cuda")
+    gmu = torch.full((nc, 2), nan, dtype=torch.float64, device="cuda")
+    ga = torch.full((nc, 2, 2), nan, dtype=torch.float64, device="cuda")
+    B.cos_connected_det_bipartite_grad(tabs, 5, *d, al, g, out, gM, moff2, gmu, ga)
+    moff = B.bipartite_matrix_offsets(order, n_mat)
+    M4 = torch.empty(int(n_mat * 4 * (order.astype(np.int64) ** 2).sum()), dtype=torch.float64, device="cuda")
+    B.cos_gather_bipartite(tabs, *d, torch.tensor(moff, device="cuda"), M4)
+    host = M4.cpu().numpy()
+    blocks = []
+    for c in range(nc):
+        b = host[moff[c]:moff[c] + n_mat * 4 * int(order[c]) ** 2]
+        blocks.append(np.concatenate([b, b]) if n_mat == 1 else b)
+    out2 = torch.full_like(out, nan)
+    gM2 = torch.full_like(gM, nan)
+    ga2 = torch.full_like(ga, nan)
+    B.cos_connected_det_bipartite_matrices_grad(5, d[0], moff2, al, torch.tensor(np.concatenate(blocks), device="cuda"),
+                                                g, out2, gM2, ga2)
+    B.cos_sync_status()
+    tabs.close()
+    assert np.array_equal(out.cpu().numpy(), out2.cpu().numpy())
+    assert np.array_equal(gM.cpu().numpy(), gM2.cpu().numpy())
+    assert np.array_equal(ga.cpu().numpy(), ga2.cpu().numpy())
+    gmu = gmu.cpu().numpy()
+    picks = (0, nc // 2, nc - 1)
+
+    def oracle_c(m2):
+        m = mk(m2)
+        t = HC.hc_model_tables(m)
+        vals = []
+        for c in picks:
+            o, n = int(cfgs.offset[c]), int(cfgs.order[c])
+            G4 = HC.hc_gather_one(t, cfgs.site[o:o + n], cfgs.tau[o:o + n], m.L, m.beta)
+            vals.append(O.det_clow(G4, al, prec="ld"))
+        return np.array(vals)
+
+    h = 1e-6
+    for b in range(2):
+        if sym:
+            fd = (oracle_c([x + h for x in mu]) - oracle_c([x - h for x in mu])) / (2 * h) / 2
+        else:
+            p = list(mu); p[b] += h
+            q = list(mu); q[b] -= h
+            fd = (oracle_c(p) - oracle_c(q)) / (2 * h)
+        for k, c in enumerate(picks):
+            want = gout[c] * fd[k]
+            assert gmu[c, b] == pytest.approx(want, rel=2e-5, abs=1e-7 * max(1.0, abs(want))), (b, c, gmu[c, b], want)
