@@ -233,3 +233,38 @@ def connected_sum_bipartite_model(mu, alpha, model, d_cfgs, n_max: int):
     and uniform shifts alpha (CPU tensors of n_flavors values, differentiable); the staggered
     shifts delta and the other fields from the inputs.HoneycombModel `model`."""
     return _ConnectedBipartiteModel.apply(mu, alpha, model, d_cfgs, n_max)
+
+
+class _ConnectedDetBipartiteModel(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, mu, alpha2, model, d_cfgs, n_max):
+        tabs = B.cos_build_propagators_honeycomb(model.L, model.t, model.beta, model.U, [float(x) for x in mu],
+                                                 [0.0, 0.0], list(model.delta), model.n_tau)
+        order, offset, site, tau = d_cfgs
+        al = _host_rows(alpha2)
+        out = torch.empty(order.numel(), dtype=torch.float64, device=order.device)
+        B.cos_connected_det_bipartite_batch(tabs, n_max, order, offset, site, tau, al, "fp64", out)
+        ctx.tabs = tabs
+        ctx.al = al
+        ctx.d_cfgs = d_cfgs
+        ctx.n_max = n_max
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        order, offset, site, tau = ctx.d_cfgs
+        n = order.numel()
+        gmu = torch.empty(n, 2, dtype=torch.float64, device=order.device)
+        gal = torch.empty(n, 2, 2, dtype=torch.float64, device=order.device)
+        B.cos_connected_det_bipartite_grad(ctx.tabs, ctx.n_max, order, offset, site, tau, ctx.al,
+                                           gout.detach().to(torch.float64).contiguous(), gmu=gmu, galpha2=gal)
+        ctx.tabs.close()
+        return gmu.sum(0).cpu(), gal.sum(0).cpu(), None, None, None
+
+
+def connected_det_bipartite_model(mu, alpha2, model, d_cfgs, n_max: int):
+    """Bipartite determinant-weight connected sums from vertex coordinates for the spin chemical
+    potentials mu (CPU tensor of 2 values) and the diagonal shifts alpha2 (CPU tensor [2][2],
+    spin then sublattice), both differentiable; the honeycomb tables are built at mu with the
+    staggered shifts delta of the inputs.HoneycombModel `model` and no uniform shift."""
+    return _ConnectedDetBipartiteModel.apply(mu, alpha2, model, d_cfgs, n_max)

@@ -642,3 +642,31 @@ def test_det_bipartite_grad_from_coordinates(sym):
         for k, c in enumerate(picks):
             want = gout[c] * fd[k]
             assert gmu[c, b] == pytest.approx(want, rel=2e-5, abs=1e-7 * max(1.0, abs(want))), (b, c, gmu[c, b], want)
+
+
+def test_det_bipartite_model_autograd():
+    """connected_det_bipartite_model: the forward equals cos_connected_det_bipartite_batch bit for
+    bit; mu.grad and alpha2.grad are the per-configuration gradients summed with the weights."""
+    m0 = I.WORKLOADS["hc_su2_af_n8"].model
+    mu = [-0.1, 0.15]
+    model = I.HoneycombModel(m0.L, m0.t, m0.beta, m0.U, tuple(mu), (0.0, 0.0), m0.delta, m0.n_tau)
+    nc = 48
+    cfgs = I.make_configs(model, 3, 6, nc, 43)
+    d = B.configs_to_device(cfgs)
+    al = [[0.04, -0.02], [0.03, 0.05]]
+    mu_t = torch.tensor(mu, dtype=torch.float64, requires_grad=True)
+    al_t = torch.tensor(al, dtype=torch.float64, requires_grad=True)
+    c = AG.connected_det_bipartite_model(mu_t, al_t, model, d, 6)
+    w = torch.linspace(-1.0, 2.0, nc, dtype=torch.float64, device="cuda")
+    (c * w).sum().backward()
+    tabs = B.honeycomb_tables_for(model)
+    ref = torch.empty(nc, dtype=torch.float64, device="cuda")
+    B.cos_connected_det_bipartite_batch(tabs, 6, *d, al, "fp64", ref)
+    gmu = torch.empty(nc, 2, dtype=torch.float64, device="cuda")
+    gal = torch.empty(nc, 2, 2, dtype=torch.float64, device="cuda")
+    B.cos_connected_det_bipartite_grad(tabs, 6, *d, al, w, gmu=gmu, galpha2=gal)
+    B.cos_sync_status()
+    tabs.close()
+    assert np.array_equal(c.detach().cpu().numpy(), ref.cpu().numpy())
+    assert np.allclose(mu_t.grad.numpy(), gmu.sum(0).cpu().numpy(), rtol=1e-14, atol=0)
+    assert np.allclose(al_t.grad.numpy(), gal.sum(0).cpu().numpy(), rtol=1e-14, atol=0)
