@@ -184,8 +184,14 @@ cos_status cos_connected_sum_matrices(int n_cfg, int n_max, const int32_t *d_ord
  *   - Limits: n_max <= 10, and the batch must fit the array (roughly 20 B per configuration
  *     plus one layer ring of 2 x max-layer-slots x 32 x 8 B); larger requests return
  *     COS_ERR_ORDER / COS_ERR_ARG with a message, without launching anything.
- *   - The first call on a device sets the array up (device address, DP structure copy,
- *     synchronizing `stream` once); make that first call before any stream capture.
+ *   - The array is device memory of this library's module, loaded on a device by the first
+ *     call there (under the runtime's default lazy module loading): that call takes the
+ *     128 MiB from the device's free memory, then sets the array up (device address, DP
+ *     structure copy, synchronizing `stream` once).  Make that first call before a memory
+ *     pool claims the device's free memory, and before any stream capture; later calls
+ *     allocate nothing.
+ *   - Mixed and double-float run the one-configuration-per-lane forward kernels (the regular
+ *     call runs the pair kernels), in launch shapes tuned for the regular call.
  *   - Every call reuses the same array and leaves its contents behind; calls whose work
  *     overlaps on the GPU (other streams, other host threads) race with each other.
  *   - Outputs are set to NaN first; a configuration whose order lies outside [1, n_max]

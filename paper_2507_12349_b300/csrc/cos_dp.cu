@@ -8,7 +8,7 @@
 //     round robin); layers are separated by __syncthreads.  Persistent CTAs pull batches from a
 //     queue ordered by decreasing order n (largest work first).
 //   * The batch's matrices sit in shared memory as [v][j][lane]; layer states live in a per-CTA
-//     global ring of 2 (3 with shift parameters) layer slots laid out [slot][lane].
+//     global ring of 2 layer slots laid out [slot][lane].
 //
 // Recurrence (push form, per row = mask mu, head h, lane flavor l, endpoints v in Vrow):
 //   close   csum(mu)            += sum_v O(mu,h,v) Md[v][h]     Md = sgn w M   (Alg. 2 Close)

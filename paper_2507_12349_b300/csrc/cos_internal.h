@@ -182,7 +182,7 @@ struct RawBuffers {
 cos_status launch_plan_raw(const RawBuffers &rb, int n_cfg, int n_max, const int32_t *order, int cpb, int device,
                            cudaStream_t stream);
 cos_status launch_dp_raw(const RawBuffers &rb, const DpLaunch &a, cudaStream_t stream);
-int dp_slots(const DpLaunch &a);            // layer slots of the ring (2, or 3 with shifts)
+int dp_slots(const DpLaunch &a);            // layer slots of the ring: always 2 (shifts ride on the diagonal)
 // Mixed and double-float precision run two configurations per lane (cos_dp_pair.cu) except
 // in the all-subsets mode; configurations per batch follow the kernel the launch selects.
 bool dp_uses_pair(const DpLaunch &a);

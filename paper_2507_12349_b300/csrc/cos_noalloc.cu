@@ -4,13 +4,23 @@
 // device, a host process that must not grow its footprint after start-up, or a plug-in that
 // is handed a stream and buffers but no allocator.  For them this file keeps every scratch
 // buffer of the DP -- planner tables, work queue, the per-order DP structure and the layer
-// ring -- in one file-scope device array of fixed size, reserved when the library's module is
-// loaded and held by every GPU that loads the library until the process exits.
+// ring -- in one file-scope device array of fixed size.  This file is its own CUDA module
+// (no kernels of its own), and under the runtime's lazy module loading (the default) that
+// module -- and with it the 128 MiB array -- is loaded on a device by the first
+// cudaGetSymbolAddress, i.e. during the first call of the entry point on that device.  From
+// then on the device holds the array until the process exits.
 //
 // The array's name is only a host-side stand-in for the device symbol; its device address is
 // obtained once per device with cudaGetSymbolAddress (with that device current) and passed to
-// the kernels.  The first call on a device performs that set-up (symbol address, copy of the
-// DP structure tables); make that first call before any stream capture.
+// the kernels.  The first call on a device performs that set-up (module load, symbol address,
+// copy of the DP structure tables); make that first call before a memory pool claims the
+// device's free memory and before any stream capture.
+//
+// Kernels: the planner and the forward kernels of cos_dp.cu with one configuration per lane
+// in every precision (FP64 dp_forward_kernel<double>, mixed <float>, double-float <df64>),
+// not the two- and four-per-lane pair kernels the regular mixed and double-float calls use;
+// warps per CTA come from the tuning line of (n_max, precision), which was measured for the
+// regular call's kernel, so the mixed and double-float launch shapes here are untuned.
 #include <algorithm>
 #include <cstring>
 #include <mutex>

@@ -374,3 +374,36 @@ def test_gather_uses_displacement_and_equal_time_convention():
     assert P.displacement(0, 15, 4) == 5
     assert M[0, 0, 2] == pytest.approx(-P.interp(tabs[0], 5, 0.4, 2.0) * 1.0)
     assert M[0, 2, 0] == pytest.approx(P.interp(tabs[0], P.displacement(15, 0, 4), 1.6, 2.0))
+
+
+# ------------------------------------------------------------------ the batch driver
+
+@pytest.mark.parametrize("prec", ["d", "ld"])
+@pytest.mark.parametrize("n,nf,shifts,weight", [(3, 1, False, 3), (5, 3, True, 1), (6, 4, False, 1),
+                                                (7, 1, True, 6), (4, 2, True, 2)])
+def test_dp_batch_equals_dp_per_configuration(prec, n, nf, shifts, weight):
+    """The OpenMP batch driver (which feeds the timed CPU baseline and every accuracy figure of
+    the benchmark) returns, configuration by configuration, exactly the (hi, lo) pair of the
+    pinned single-configuration DP: different matrices per configuration of one order, shift
+    weights on and off, loop weights above 1, the absolute-mass mode, one thread and all
+    threads.  A stride, offset or sigma-handling slip in the driver changes some bits."""
+    rng = np.random.default_rng(1000 * n + 10 * nf + weight)
+    n_cfg = 37                                       # not a multiple of any thread count
+    Ms = rng.uniform(-0.9, 0.9, size=(n_cfg, nf, n, n))
+    sig = list(rng.uniform(-0.3, 0.3, size=nf)) if shifts else None
+    for absmode in (False, True):
+        want = [O.dp(Ms[c], sig, weight=weight, absmode=absmode, prec=prec, pair=True) for c in range(n_cfg)]
+        for threads in (1, 0):
+            hi, lo, used = O.dp_batch(Ms, sig, weight, absmode=absmode, prec=prec, nthreads=threads)
+            assert used >= 1 and (threads != 1 or used == 1)
+            assert [(float(h), float(l)) for h, l in zip(hi, lo)] == want
+    # each configuration's own matrices: permuting the batch permutes the results
+    perm = rng.permutation(n_cfg)
+    hi, lo, _ = O.dp_batch(Ms, sig, weight, prec=prec)
+    hp, lp, _ = O.dp_batch(Ms[perm], sig, weight, prec=prec)
+    assert np.array_equal(hp, hi[perm]) and np.array_equal(lp, lo[perm])
+
+
+def test_dp_batch_rejects_unsupported_order():
+    with pytest.raises(ValueError):
+        O.dp_batch(np.zeros((2, 1, 13, 13)))

@@ -301,7 +301,8 @@ def workload_check(name, n_cfg, sample, prec="fp64", rel=1e-10, graph=False):
 
 
 def test_workload_su2_order4_all_configs():
-    errs = workload_check("su2_sym_n4", None, 200)
+    errs = workload_check("su2_sym_n4", None, I.WORKLOADS["su2_sym_n4"].n_cfg)
+    assert len(errs) == I.WORKLOADS["su2_sym_n4"].n_cfg
     assert max(errs) < 1e-10
 
 

@@ -75,3 +75,82 @@ def test_noalloc_rejects_orders_beyond_its_workspace():
     with pytest.raises(B.CosError) as ei:
         B.cos_connected_sum_matrices_noalloc(11, order, moff, 1, 2, None, M, "fp64", out)
     assert ei.value.status == -2
+
+
+def test_noalloc_order_above_n_max_stays_nan():
+    """A configuration whose order exceeds n_max is skipped by the planner and keeps the NaN
+    the call writes first; the others are computed as usual."""
+    order, moff, M = _case(21, 40, 2, [4, 6])
+    order[7] = 7                                   # above n_max = 6; its matrices are never read
+    out = torch.zeros(40, dtype=torch.float64, device="cuda")
+    ref = torch.zeros_like(out)
+    keep = torch.ones(40, dtype=torch.bool)
+    keep[7] = False
+    B.cos_connected_sum_matrices_noalloc(6, order, moff, 2, 1, None, M, "fp64", out)
+    torch.cuda.synchronize()
+    sub = torch.arange(40, device="cuda")[keep.cuda()]
+    ref_sub = torch.zeros(len(sub), dtype=torch.float64, device="cuda")
+    B.cos_connected_sum_matrices(6, order[sub].contiguous(), moff[sub].contiguous(), 2, 1, None, M, "fp64", ref_sub)
+    B.cos_sync_status()
+    got = out.cpu().numpy()
+    assert np.isnan(got[7])
+    assert np.array_equal(got[keep.numpy()], ref_sub.cpu().numpy())
+
+
+def test_noalloc_rejects_batch_too_large_for_the_array():
+    """At n_max = 10 one FP64 layer ring takes about 59 MB of the 128 MiB array; 20 million
+    configurations need another 90 MB of batch tables, so the call returns COS_ERR_ARG
+    before launching anything.  (The buffers are sized so that every access of a launch
+    would stay in bounds even if the check were missing.)"""
+    ncfg = 20_000_000
+    order = torch.full((ncfg,), 10, dtype=torch.int32, device="cuda")
+    moff = torch.zeros(ncfg, dtype=torch.int64, device="cuda")
+    M = torch.full((100,), 0.1, dtype=torch.float64, device="cuda")
+    out = torch.zeros(ncfg, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.CosError) as ei:
+        B.cos_connected_sum_matrices_noalloc(10, order, moff, 1, 2, None, M, "fp64", out)
+    assert ei.value.status == -1
+    assert "too large" in str(ei.value)
+    torch.cuda.synchronize()
+    assert float(out.abs().max().item()) == 0.0    # nothing was written
+
+
+_FRESH_PROCESS = r"""
+import os, sys, numpy as np, torch
+sys.path.insert(0, os.environ["COS_REPO_ROOT"])
+from paper_2507_12349_b300 import binding as B
+B.lib()
+torch.cuda.init()
+n_cfg, n = 64, 8
+order = torch.full((n_cfg,), n, dtype=torch.int32, device="cuda")
+moff = torch.arange(n_cfg, dtype=torch.int64, device="cuda") * n * n
+M = torch.rand(n_cfg * n * n, dtype=torch.float64, device="cuda", generator=None) * 0.4
+out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+B.cos_connected_sum_matrices_noalloc(n, order, moff, 1, 2, None, M, "fp64", out)
+torch.cuda.synchronize()
+free1 = torch.cuda.mem_get_info()[0]
+for _ in range(5):
+    B.cos_connected_sum_matrices_noalloc(n, order, moff, 1, 2, None, M, "fp64", out)
+torch.cuda.synchronize()
+free2 = torch.cuda.mem_get_info()[0]
+print(free0, free1, free2)
+"""
+
+
+def test_noalloc_first_call_takes_the_array_and_later_calls_allocate_nothing():
+    """In a fresh process under lazy module loading: free device memory drops by the 128 MiB
+    array (plus a little kernel code) at the first call, and not at all over five more."""
+    import os
+    import subprocess
+    import sys
+    env = dict(os.environ, CUDA_MODULE_LOADING="LAZY",
+               COS_REPO_ROOT=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    r = subprocess.run([sys.executable, "-c", _FRESH_PROCESS], env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    free0, free1, free2 = (int(x) for x in r.stdout.split()[-3:])
+    mib = 1 << 20
+    assert 128 * mib <= free0 - free1 <= 192 * mib, (free0, free1)
+    assert free2 == free1
