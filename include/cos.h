@@ -50,7 +50,9 @@ typedef enum {
     COS_ERR_ARG = -1,           /* null pointer, negative count, bad enum */
     COS_ERR_ORDER = -2,         /* an order n < 1 or n > n_max (or > COS_NMAX) */
     COS_ERR_CUDA = -3,          /* a CUDA call failed (message: cos_last_error) */
-    COS_ERR_TIMEOUT = -4,       /* a bounded device-side wait gave up */
+    COS_ERR_TIMEOUT = -4,       /* reserved: no call of this library waits on the device (the
+                                   persistent kernels take batches from an atomic counter and
+                                   never spin on a flag), so none returns it */
     COS_ERR_NONFINITE = -5,     /* a result was NaN or infinite */
     COS_ERR_UNIMPLEMENTED = -6,
     COS_ERR_NOMEM = -7          /* device workspace could not be allocated */
@@ -547,20 +549,6 @@ cos_status cos_structure(int n, cos_structure_info *info);
 /* Counts of the bipartite structure at order n (host only): masks, slots (4 |H| |A| per
  * mask), max_layer_slots, reachable states and multiply-adds per flavor array. */
 cos_status cos_bipartite_structure(int n, cos_structure_info *info);
-
-/* ------------------------------------------------------------------ measurement
- * Peak-throughput probe (no counterpart in the paper; it supplies the roofline
- * denominator of the FP64 / FP32 pipes).  kind 0: FP64 FMA, 8 independent chains
- * per thread; kind 1: FP32 FMA, 16 chains; kinds 2, 3, 4: FP64 with 4, 16, 32 chains.  Work = 2 * blocks * threads * chains
- * * iters flops.  d_sink: device buffer of `blocks` elements of the probed type
- * (written only if a chain hits an impossible value).  Time it with CUDA events. */
-cos_status cos_peak_probe(int kind, int blocks, int threads, int iters, void *d_sink, cos_stream_t stream);
-
-/* Verification of the integer-pipe FP32 <-> FP64 conversions used by the mixed-precision DP
- * (no counterpart in the paper): d_narrowed[i] = d_in64[i] rounded to FP32 (nearest even),
- * d_widened[i] = d_in32[i] widened to FP64, exactly as the kernels compute them. */
-cos_status cos_convert_check(int64_t n, const double *d_in64, const float *d_in32, float *d_narrowed,
-                             double *d_widened, cos_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -38,9 +38,9 @@ EXPORTS = [
     "cos_connected_det_bipartite_subsets", "cos_connected_det_bipartite_batch", "cos_connected_sum_bipartite_grad",
     "cos_connected_det_bipartite_grad",
     "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_sync_status", "cos_status_string",
-    "cos_last_error", "cos_structure", "cos_peak_probe",
+    "cos_last_error", "cos_structure",
     "cos_plan_create_batch", "cos_plan_create_matrices", "cos_plan_launch", "cos_plan_status", "cos_plan_grid",
-    "cos_plan_destroy", "cos_set_tuning", "cos_get_tuning", "cos_autotune", "cos_convert_check",
+    "cos_plan_destroy", "cos_set_tuning", "cos_get_tuning", "cos_autotune",
 ]
 
 
@@ -110,8 +110,6 @@ def lib(build: bool = True):
         L.cos_last_error.argtypes = []
         L.cos_last_error.restype = ctypes.c_char_p
         L.cos_structure.argtypes = [i32, ctypes.POINTER(cos_structure_info)]
-        L.cos_peak_probe.argtypes = [i32, i32, i32, i32, vp, vp]
-        L.cos_convert_check.argtypes = [i64, vp, vp, vp, vp, vp]
         L.cos_plan_create_batch.argtypes = [vp, i32, i32, vp, vp, vp, vp, i32, vp, vp, vp, ctypes.POINTER(vp)]
         L.cos_plan_create_matrices.argtypes = [i32, i32, vp, vp, i32, i32, dptr, vp, i32, vp, vp, vp,
                                                ctypes.POINTER(vp)]
@@ -517,14 +515,39 @@ def matrix_offsets(order: np.ndarray, n_mat: int) -> np.ndarray:
     return off
 
 
-def cos_peak_probe(kind: int, blocks: int, threads: int, iters: int, sink, stream=None):
-    _check(lib().cos_peak_probe(int(kind), int(blocks), int(threads), int(iters), _ptr(sink), _stream(stream)),
-           "cos_peak_probe")
+_instr = None
 
 
-def cos_convert_check(in64, in32, narrowed, widened, stream=None):
-    _check(lib().cos_convert_check(int(in64.numel()), _ptr(in64, "f64"), _ptr(in32), _ptr(narrowed),
-                                   _ptr(widened, "f64"), _stream(stream)), "cos_convert_check")
+def instr_lib():
+    """The benchmark's and tests' instruments (FMA probe, conversion check), built beside
+    libcos.so into libcos_instr.so; not part of the library's interface."""
+    global _instr
+    if _instr is None:
+        lib()   # builds both libraries when sources changed
+        L = ctypes.CDLL(os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcos_instr.so"))
+        vp = ctypes.c_void_p
+        L.cos_instr_fma_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
+        L.cos_instr_fma_probe.restype = ctypes.c_int
+        L.cos_instr_convert_check.argtypes = [ctypes.c_int64, vp, vp, vp, vp, vp]
+        L.cos_instr_convert_check.restype = ctypes.c_int
+        _instr = L
+    return _instr
+
+
+def _instr_check(rc: int, where: str):
+    if rc != 0:
+        raise RuntimeError(f"{where}: {'bad argument' if rc < 0 else 'CUDA error %d' % rc}")
+
+
+def fma_probe(kind: int, blocks: int, threads: int, iters: int, sink, stream=None):
+    _instr_check(instr_lib().cos_instr_fma_probe(int(kind), int(blocks), int(threads), int(iters), _ptr(sink),
+                                                 _stream(stream)), "cos_instr_fma_probe")
+
+
+def convert_check(in64, in32, narrowed, widened, stream=None):
+    _instr_check(instr_lib().cos_instr_convert_check(int(in64.numel()), _ptr(in64, "f64"), _ptr(in32),
+                                                     _ptr(narrowed), _ptr(widened, "f64"), _stream(stream)),
+                 "cos_instr_convert_check")
 
 
 def measure_peak(kind: int = 0, iters: int = 4096, reps: int = 3, sweep: bool = False):
@@ -544,12 +567,12 @@ def measure_peak(kind: int = 0, iters: int = 4096, reps: int = 3, sweep: bool = 
         chains = chains_of[k]
         sink = torch.zeros(blocks, dtype=torch.float64 if k != 1 else torch.float32, device="cuda")
         it = max(64, iters * 8 // chains)
-        cos_peak_probe(k, blocks, threads, 64, sink)               # warm-up
+        fma_probe(k, blocks, threads, 64, sink)                    # warm-up
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record()
-            cos_peak_probe(k, blocks, threads, it, sink)
+            fma_probe(k, blocks, threads, it, sink)
             e1.record()
             torch.cuda.synchronize()
             sec = e0.elapsed_time(e1) * 1e-3

@@ -9,6 +9,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libcos.so")
+# measurement and verification instruments for the benchmark and the tests (not part of libcos)
+INSTR_LIB = os.path.join(PKG, "libcos_instr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -16,15 +18,19 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def instr_sources():
+    return sorted(glob.glob(os.path.join(CSRC, "instr", "*.cu")))
+
+
 def deps():
-    return (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
-            + glob.glob(os.path.join(INCLUDE, "*.h")))
+    return (sources() + instr_sources() + glob.glob(os.path.join(CSRC, "*.h"))
+            + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(INSTR_LIB)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(INSTR_LIB))
     return all(os.path.getmtime(d) <= t for d in deps())
 
 
@@ -45,12 +51,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
         subprocess.check_call([nvcc, *flags, "-c", "-o", obj, src])
         return obj
 
-    srcs = sources()
-    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-    os.replace(tmp, LIB)
+    srcs, isrcs = sources(), instr_sources()
+    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs) + len(isrcs), os.cpu_count() or 1))) as ex:
+        objs = list(ex.map(compile_one, srcs + isrcs))
+    for target, o in ((LIB, objs[:len(srcs)]), (INSTR_LIB, objs[len(srcs):])):
+        tmp = target + ".tmp%d" % os.getpid()
+        subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *o, "-lcudart"])
+        os.replace(tmp, target)
     return LIB
 
 

@@ -261,10 +261,6 @@ extern "C" cos_status cos_sync_status(cos_stream_t stream) {
         set_error("device: site out of range");
         return COS_ERR_ARG;
     }
-    if (word & kStatusTimeout) {
-        set_error("device: bounded wait gave up");
-        return COS_ERR_TIMEOUT;
-    }
     if (word & kStatusNonFinite) {
         set_error("device: non-finite result");
         return COS_ERR_NONFINITE;

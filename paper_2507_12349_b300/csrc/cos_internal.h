@@ -19,7 +19,6 @@ enum : int {
     kStatusOrder = 1,
     kStatusSite = 2,
     kStatusNonFinite = 4,
-    kStatusTimeout = 8,
 };
 
 // One interaction mask mu in {0,1,2}^n with mu_0 >= 1, as stored on the device.

@@ -1,0 +1,73 @@
+// Measurement and verification instruments used by the benchmark and the tests.  They are
+// built into their own library (libcos_instr.so) beside libcos.so and are not part of the
+// library's interface: nothing in libcos calls them, and include/ declares none of them.
+//
+//   cos_instr_fma_probe     independent FMA chains per thread (enough warps to fill every SM
+//                           sub-partition): the measured throughput of the FP64 / FP32 pipes
+//                           that the benchmark reports beside the unit-count peaks.
+//   cos_instr_convert_check applies the integer-pipe FP32 <-> FP64 conversions of the mixed
+//                           precision DP (widen / narrow_to of cos_dp_device.cuh, the very
+//                           device functions the kernels inline) elementwise, so that a test
+//                           can compare them bit for bit with the conversion instructions.
+//
+// Both return 0 or the CUDA error code of the failed launch (negative for a bad argument).
+#include <algorithm>
+
+#include "cos_dp_device.cuh"
+
+namespace cosinstr {
+
+template <typename T, int CHAINS>
+__global__ void fma_probe_kernel(int iters, T *sink) {
+    T a[CHAINS];
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) a[c] = (T)(threadIdx.x + c) * (T)1e-3;
+    const T b = (T)0.999999, d = (T)1e-7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < CHAINS; ++c) a[c] = a[c] * b + d;   // contracted to one FMA
+    }
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) s += a[c];
+    if (s == (T)-1.2345) sink[blockIdx.x] = s;   // never true; keeps the chains live
+}
+
+__global__ void convert_check_kernel(int64_t n, const double *in64, const float *in32, float *narrowed,
+                                     double *widened) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        narrowed[i] = cosdp::narrow_to(0.0f, in64[i]);
+        widened[i] = cosdp::widen(in32[i]);
+    }
+}
+
+}  // namespace cosinstr
+
+// kind 0 / 1: FP64 / FP32 with 8 / 16 chains per thread; kind 2, 3, 4: FP64 with 4, 16, 32
+// chains (a sweep over instruction-level parallelism).  Work = 2 * blocks * threads * chains *
+// iters flops; d_sink holds `blocks` elements of the probed type.
+extern "C" int cos_instr_fma_probe(int kind, int blocks, int threads, int iters, void *d_sink, void *stream) {
+    using namespace cosinstr;
+    if (blocks < 1 || threads < 32 || threads > 1024 || iters < 1 || !d_sink || kind < 0 || kind > 4) return -1;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (kind) {
+        case 0: fma_probe_kernel<double, 8><<<blocks, threads, 0, s>>>(iters, (double *)d_sink); break;
+        case 1: fma_probe_kernel<float, 16><<<blocks, threads, 0, s>>>(iters, (float *)d_sink); break;
+        case 2: fma_probe_kernel<double, 4><<<blocks, threads, 0, s>>>(iters, (double *)d_sink); break;
+        case 3: fma_probe_kernel<double, 16><<<blocks, threads, 0, s>>>(iters, (double *)d_sink); break;
+        default: fma_probe_kernel<double, 32><<<blocks, threads, 0, s>>>(iters, (double *)d_sink); break;
+    }
+    return (int)cudaGetLastError();
+}
+
+// d_narrowed[i] = d_in64[i] rounded to FP32 (nearest even), d_widened[i] = d_in32[i] widened
+// to FP64, exactly as the DP kernels compute them.
+extern "C" int cos_instr_convert_check(int64_t n, const double *d_in64, const float *d_in32, float *d_narrowed,
+                                       double *d_widened, void *stream) {
+    using namespace cosinstr;
+    if (n < 0 || (n > 0 && (!d_in64 || !d_in32 || !d_narrowed || !d_widened))) return -1;
+    if (n == 0) return 0;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    convert_check_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(n, d_in64, d_in32, d_narrowed, d_widened);
+    return (int)cudaGetLastError();
+}

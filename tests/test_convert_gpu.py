@@ -30,7 +30,7 @@ def test_narrow_and_widen_bitwise():
     d32 = torch.tensor(x32, device="cuda")
     narrowed = torch.empty(x64.size, dtype=torch.float32, device="cuda")
     widened = torch.empty(x64.size, dtype=torch.float64, device="cuda")
-    B.cos_convert_check(d64, d32, narrowed, widened)
+    B.convert_check(d64, d32, narrowed, widened)
     torch.cuda.synchronize()
     ref_n = d64.to(torch.float32)
     ref_w = d32.to(torch.float64)
