@@ -1,12 +1,15 @@
 """Benchmark of the connected-sum hot path on B300.
 
-Workload (the configuration the metric is quoted on): SU(4) square-lattice
-Hubbard model with flavor-dependent chemical potentials mu = (-0.3, -0.1, 0.1,
-0.3), L = 16, t = 1, beta = 4, U = 1.5, order n = 8, 10^5 configurations with
-sites uniform on the torus and tau uniform in [0, beta) (seed 1), FP64,
-per-flavor tables of 1024 tau points.  One step = propagator gather + the
-whole DP (seed, clow extension, loop closing, sink) for all 10^5
-configurations, inputs resident in HBM.
+Headline workload: SU(6) symmetric square-lattice Hubbard model, mu = 0.1, L = 32, t = 1,
+beta = 6, U = 1, orders n drawn uniformly from 4..12 per configuration, 2 x 10^5
+configurations (sites uniform on the torus, tau uniform in [0, beta), seed 3), FP64, tables
+of 1024 tau points.  One step = one launch of the CUDA-graph plan that holds the device
+planner, the propagator gather and the whole DP (seed, clow extension, loop closing, sink)
+as one persistent launch over every order, inputs resident in HBM.
+
+The other forms of the path (FP64 / mixed / double-float at orders 4, 8 and 10, the
+gradient at order 10, one configuration per launch, and the NEXT modes) are timed on the
+same GPU after the headline, each with its own clock record; see `measure_forms`.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
        [--no-extras]
@@ -31,22 +34,21 @@ sys.path.insert(0, ROOT)
 
 from paper_2507_12349_b300 import inputs as I  # noqa: E402
 
-WORKLOAD = "su4_mu_broken_n8"
+WORKLOAD = "su6_sym_uneven_n4_12"
 METRIC = "connected-sum configs/s at order n (FP64 vs mixed), roofline fraction, grad overhead"
 UNIT = "configs/s"
 NOMINAL_FP64_TFLOPS = 1.25
-# DRAM bytes (read + write) of dp_forward_kernel<double, 320> per configuration of the headline
-# workload: ncu dram__bytes_read.sum + dram__bytes_write.sum on a 5 000-configuration launch
-# (8.917 GB + 7.099 GB, profiles/dp_forward_fp64_su4_n8.md); traffic grows in proportion
-# to the configurations of a launch.
-HEADLINE_DRAM_BYTES_PER_CFG = (8.917352e9 + 7.098890e9) / 5000
-FP64_FMA_PER_CLK_SM = 2.0
+FP64_FMA_PER_CLK_SM = 2.0      # FP64 FMA lanes per clock per SM (ncu pipe counters of the FMA probe)
+FP32_FMA_PER_CLK_SM = 128.0
+# FP32 instructions a double-float term needs at least (the Dot2 step: 1 multiply, 3 FMA,
+# 8 additions; the first term of a dot product fewer): the FP32-pipe floor of that mode.
+DF64_FP32_PER_TERM = 11.5
 
 
 def measured_hbm_gbs():
     """HBM copy bandwidth measured on the B300s (MEASURED_PEAKS.json beside this file),
     else the earlier single B300 measurement."""
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             return float(json.load(f)["hbm_gbs"]), "measured (copy bandwidth)"
@@ -61,7 +63,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--no-extras", action="store_true", help="only the headline workload (for launch lists)")
-    p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
+    p.add_argument("--form-steps", type=int, default=10, help="timed steps of each order-4/8/10 form (median)")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of each CPU oracle sample")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
     p.add_argument("--n-cfg", type=int, default=0, help="smaller configuration count (profiling runs only)")
     p.add_argument("--workload", default=WORKLOAD,
@@ -77,7 +80,7 @@ def parse():
                         "of the order-10 Zeeman workload")
     p.add_argument("--subsets", action="store_true",
                    help="profiling runs only: time the all-subsets call (c(S) and a(S) of every vertex subset) "
-                        "on the headline workload's gathered matrices")
+                        "on the order-8 SU(4) workload's gathered matrices")
     p.add_argument("--order", type=int, default=0, help="with --bipartite or --det: order of the configurations")
     return p.parse_args()
 
@@ -89,22 +92,40 @@ def dist_env():
     return rank, world, local
 
 
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 # ------------------------------------------------------------------ CPU oracle (reported baseline)
 
-def oracle_values(w, cfgs, absmode=False, prec="d"):
-    """Oracle connected sums (numpy gather + C DP in double, or `prec`, OpenMP) of `cfgs` (one
-    order)."""
-    import oracle as O
+def _oracle_model_args(w):
     from oracle import propagators as P
     model = w.model
     tabs = P.model_tables(model)
     wt, sig = 1, list(model.sigma)
     if model.symmetric:
         tabs, wt, sig = tabs[:1], model.n_flavors, sig[:1]
-    sig = sig if any(sig) else None
-    Ms = np.stack(P.gather(tabs, cfgs, model.L, model.beta))
-    hi, lo, threads = O.dp_batch(Ms, sig, wt, absmode=absmode, prec=prec, nthreads=0)
-    return hi + lo, threads
+    return tabs, wt, (sig if any(sig) else None)
+
+
+def oracle_values(w, cfgs, absmode=False, prec="d", nthreads=0):
+    """Oracle connected sums of `cfgs` (numpy gather + the C DP in double, or `prec`, OpenMP
+    over configurations), any mix of orders.  Returns (values, threads used)."""
+    import oracle as O
+    from oracle import propagators as P
+    tabs, wt, sig = _oracle_model_args(w)
+    Ms = P.gather(tabs, cfgs, w.model.L, w.model.beta)
+    vals = np.zeros(cfgs.n_cfg)
+    threads = 1
+    for n in np.unique(cfgs.order):
+        idx = np.flatnonzero(cfgs.order == n)
+        hi, lo, threads = O.dp_batch(np.stack([Ms[i] for i in idx]), sig, wt, absmode=absmode, prec=prec,
+                                     nthreads=nthreads)
+        vals[idx] = hi + lo
+    return vals, threads
 
 
 def det_oracle_values(w, cfgs, absmode=False):
@@ -116,22 +137,54 @@ def det_oracle_values(w, cfgs, absmode=False):
     return np.array([O.det_clow(M, absmode=absmode) for M in P.gather(tabs, cfgs, w.model.L, w.model.beta)])
 
 
-def cpu_oracle_rate(w, budget_s: float, n_limit: int | None = None):
-    """Oracle on a bounded sample of the workload (the first configurations of its seeded
-    stream).  Returns (configs/s, threads, sample size, oracle values)."""
-    probe = I.workload_configs(w, 8)
+def cpu_oracle_rate(w, budget_s: float, nthreads: int = 0):
+    """Oracle on a bounded sample of the workload: the first configurations of its seeded
+    stream, as many as `budget_s` seconds allow (estimated from a probe of 9).  Returns
+    (configs/s, threads, sample size, oracle values)."""
+    probe = I.workload_configs(w, 9)
     t0 = time.perf_counter()
-    oracle_values(w, probe)
-    per_cfg = (time.perf_counter() - t0) / 8.0
-    n = max(8, int(budget_s / max(per_cfg, 1e-6)))
-    if n_limit:
-        n = min(n, n_limit)
-    n = min(n, w.n_cfg)
+    oracle_values(w, probe, nthreads=nthreads)
+    per_cfg = (time.perf_counter() - t0) / 9.0
+    n = int(min(w.n_cfg, max(9, budget_s / max(per_cfg, 1e-7))))
     cfgs = I.workload_configs(w, n)
     t0 = time.perf_counter()
-    vals, threads = oracle_values(w, cfgs)
+    vals, threads = oracle_values(w, cfgs, nthreads=nthreads)
     dt = time.perf_counter() - t0
     return n / dt, threads, n, vals
+
+
+def brute_rate_order4(budget_s: float):
+    """Tier-0 oracle (every decorated cover enumerated, union-find connectivity) on the
+    order-4 SU(2) workload, one configuration at a time on one core."""
+    import oracle as O
+    from oracle import propagators as P
+    w = I.WORKLOADS["su2_sym_n4"]
+    tabs = P.model_tables(w.model)
+    cfgs = I.workload_configs(w, 400)
+    Ms = P.gather(tabs, cfgs, w.model.L, w.model.beta)
+    t0 = time.perf_counter()
+    k = 0
+    while k < len(Ms) and time.perf_counter() - t0 < budget_s:
+        O.brute(O.tiled(Ms[k]))   # both flavors' (equal) matrices: loop weight = the flavor sum
+        k += 1
+    return k / (time.perf_counter() - t0), k
+
+
+def cpu_baseline(w, budget_s: float):
+    """The oracle as it stands on the host's cores: tier 2 (the merged DP in double) on every
+    visible core and on one core, plus tier 0 (brute force) at order 4."""
+    rate, threads, n, vals = cpu_oracle_rate(w, budget_s)
+    rate1, _, n1, _ = cpu_oracle_rate(w, budget_s / 2, nthreads=1)
+    brute, nb = brute_rate_order4(min(5.0, budget_s / 2))
+    base = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"the first {n} configurations of the {w.name} workload (numpy gather + the C merged "
+                      f"DP in double, OpenMP over configurations)",
+            "host_cores_visible": host_cores(),
+            "value_1core": rate1, "sample_1core": f"the first {n1} configurations, one thread",
+            "brute_force_order4": {"value": brute, "unit": UNIT, "cores": 1, "configs": nb,
+                                   "workload": "su2_sym_n4",
+                                   "kind": "oracle tier 0: every decorated cover of 8 points, union-find"}}
+    return base, vals
 
 
 def reference_arm(args):
@@ -153,11 +206,11 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": 8, "n_flavors": 4, "n_cfg_sample": sample, "L": 16, "beta": 4.0,
-                   "n_tau": 1024, "precision": "fp64"},
+        "config": {"workload": WORKLOAD, "n": "4..12", "n_flavors": 6, "n_cfg_sample": sample, "L": 32,
+                   "beta": 6.0, "n_tau": 1024, "precision": "fp64"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{sample} configurations of the n=8 SU(4) workload per step "
-                                   f"(numpy gather + C DP in double, OpenMP)"},
+                         "sample": f"the first {sample} configurations of the uneven order-4..12 SU(6) workload "
+                                   f"per step (numpy gather + C DP in double, OpenMP)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -170,9 +223,10 @@ class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    gpu = 0
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, gpu_index: int | None = None):
+        self.gpu = ClockSampler.gpu if gpu_index is None else gpu_index
         self.proc = None
         self.path = None
 
@@ -210,17 +264,43 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def algorithmic_flops(B, order: np.ndarray, n_mat: int, shifts: bool) -> float:
-    """FP64-equivalent flops the DP must do: 2 per multiply-add of the extension dot products
-    and loop-closing sums over reachable states (shift points ride on the shifted diagonal of
-    the extension matrices and add no work)."""
-    del shifts
-    total = 0.0
+class Peaks:
+    """Roofline denominators at a sampled SM clock: the FP64 and FP32 pipes from unit counts
+    (148 SMs x lanes per clock x 2 flop), HBM from the measured copy bandwidth."""
+
+    def __init__(self, sms: int):
+        self.sms = sms
+        self.hbm_gbs, self.hbm_src = measured_hbm_gbs()
+
+    def clk(self, clocks) -> float:
+        return (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz") or 2032.0
+
+    def fp64(self, clocks) -> float:
+        return self.sms * FP64_FMA_PER_CLK_SM * 2.0 * self.clk(clocks) * 1e6
+
+    def fp32_lane_ops(self, clocks) -> float:
+        return self.sms * FP32_FMA_PER_CLK_SM * self.clk(clocks) * 1e6
+
+    def fp32(self, clocks) -> float:
+        return 2.0 * self.fp32_lane_ops(clocks)
+
+
+def dp_counts(B, order: np.ndarray, n_mat: int, state_bytes: int):
+    """Algorithmic work of the DP over a batch: FP64-equivalent flops (2 per multiply-add of
+    the extension dot products and loop-closing sums over reachable states; shift points
+    ride on the shifted diagonal and add no work), the loop-closing flops alone, and the
+    layer traffic of the kernels (every reachable state written once and read once)."""
+    flops = close = traffic = 0.0
     for n in np.unique(order):
         s = B.cos_structure(int(n))
-        cnt = int((order == n).sum())
-        total += cnt * n_mat * 2.0 * (s.fma_ext + s.fma_close)
-    return total
+        cnt = int((order == n).sum()) * n_mat
+        flops += cnt * 2.0 * (s.fma_ext + s.fma_close)
+        close += cnt * 2.0 * s.fma_close
+        traffic += cnt * 2.0 * s.states * state_bytes
+    return {"flops": flops, "close_flops": close, "traffic": traffic}
+
+
+STATE_BYTES = {"fp64": 8, "mixed": 4, "df64": 8}
 
 
 def flush_l2(buf):
@@ -228,7 +308,7 @@ def flush_l2(buf):
 
 
 def time_steps(torch, fn, steps, flush):
-    """Per-step CUDA-event times (flush between steps, untimed)."""
+    """Per-step CUDA-event times on the current stream (L2 flushed before each step, untimed)."""
     stream = torch.cuda.current_stream()
     times = []
     for _ in range(steps):
@@ -243,10 +323,52 @@ def time_steps(torch, fn, steps, flush):
     return times
 
 
+def timed_form(torch, fn, steps, flush, warm=1):
+    """A form's timing: `warm` untimed calls, then `steps` event-timed steps with the clocks
+    sampled over them.  Returns (median seconds, all step times, clock record)."""
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    sampler = ClockSampler()
+    sampler.start()
+    time.sleep(0.25)
+    ts = time_steps(torch, fn, steps, flush)
+    clocks = sampler.stop()
+    return statistics.median(ts), ts, clocks
+
+
+def rooflines(r, counts, t, prec, peaks, clocks):
+    """Add the form's roofline fractions: FP64 -> the FP64 pipe; mixed -> the FP64 pipe for
+    the close, the FP32 pipe for the extension and HBM for the layer traffic (whichever is
+    lowest binds); double-float -> the FP32 floor of its compensated terms and HBM."""
+    hbm = counts["traffic"] / t / 1e9
+    r["dram_gbs_model"] = hbm
+    r["frac_hbm"] = hbm / peaks.hbm_gbs
+    if prec == "fp64":
+        r["tflops"] = counts["flops"] / t / 1e12
+        r["frac_fp64_peak"] = counts["flops"] / t / peaks.fp64(clocks)
+    elif prec == "mixed":
+        ext = counts["flops"] - counts["close_flops"]
+        r["fp64_close_tflops"] = counts["close_flops"] / t / 1e12
+        r["frac_fp64_peak_close"] = counts["close_flops"] / t / peaks.fp64(clocks)
+        r["fp32_ext_tflops"] = ext / t / 1e12
+        r["frac_fp32_peak_ext"] = ext / t / peaks.fp32(clocks)
+        r["binding_roof"] = max((("hbm", r["frac_hbm"]), ("fp64_close", r["frac_fp64_peak_close"]),
+                                 ("fp32_ext", r["frac_fp32_peak_ext"])), key=lambda kv: kv[1])[0]
+    else:
+        terms = counts["flops"] / 2.0
+        r["tflops_equiv"] = counts["flops"] / t / 1e12
+        r["frac_fp32_floor"] = terms * DF64_FP32_PER_TERM / t / peaks.fp32_lane_ops(clocks)
+    return r
+
+
+# ------------------------------------------------------------------ native arm
+
 def native_arm(args):
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    ClockSampler.gpu = local
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -255,7 +377,7 @@ def native_arm(args):
 
     w = I.WORKLOADS[args.workload]
     n_cfg = args.n_cfg if args.n_cfg > 0 else w.n_cfg
-    # weak scaling: every rank takes its own 10^5 configurations of the seeded stream
+    # weak scaling: every rank takes its own configurations of the seeded stream
     cfgs = I.workload_configs(w, n_cfg, first_cfg=rank * n_cfg)
     tabs = B.tables_for(w.model)
     d_order, d_offset, d_site, d_tau = B.configs_to_device(cfgs)
@@ -265,38 +387,46 @@ def native_arm(args):
     loop_weight = w.model.n_flavors if inf.symmetric else 1
     sigma = list(inf.sigma)[:n_mat]
     sigma = sigma if any(sigma) else None
-    stride = n_mat * n_max * n_max
-    d_moff = torch.arange(n_cfg, dtype=torch.int64, device="cuda") * stride
-    d_M = torch.empty(n_cfg * stride, dtype=torch.float64, device="cuda")
     out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
-    if args.grad:
-        d_gout = torch.ones(n_cfg, dtype=torch.float64, device="cuda")
-        d_gM = torch.empty_like(d_M)
-        d_gsig = torch.empty(n_cfg, n_mat, dtype=torch.float64, device="cuda")
     flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2 (126 MB)
-    stream = torch.cuda.current_stream()
-
-    # a step, with CUDA events between the gather and the DP (same stream)
-    dp_times = []
-
-    def step():
-        B.cos_gather(tabs, d_order, d_offset, d_site, d_tau, d_moff, d_M)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peaks = Peaks(sms)
+    counts = dp_counts(B, cfgs.order, n_mat, STATE_BYTES[args.precision])
+    graph = args.workload == WORKLOAD and not args.grad
+    plan = None
+    if graph:
+        # the headline's launch form: planner + gather + DP frozen into one CUDA graph
+        plan = B.cos_plan_create_batch(tabs, n_max, d_order, d_offset, d_site, d_tau, args.precision, out)
+        step = plan.launch
+        kernel = "dp_forward_kernel<double> (CUDA-graph step: 4 planner kernels, gather, DP)"
+        launches_per_step = 6
+    else:
+        # profiling runs of another workload: gather, then the DP call on the gathered matrices
+        stride = n_mat * n_max * n_max
+        d_moff = torch.arange(n_cfg, dtype=torch.int64, device="cuda") * stride
+        d_M = torch.empty(n_cfg * stride, dtype=torch.float64, device="cuda")
         if args.grad:
-            B.cos_connected_sum_matrices_grad(n_max, d_order, d_moff, n_mat, loop_weight, sigma, d_M, d_gout, out,
-                                              d_gM, d_gsig)
-        else:
-            B.cos_connected_sum_matrices(n_max, d_order, d_moff, n_mat, loop_weight, sigma, d_M, args.precision,
-                                         out)
-        ev1.record(stream)
-        dp_times.append((ev0, ev1))
+            d_gout = torch.ones(n_cfg, dtype=torch.float64, device="cuda")
+            d_gM = torch.empty_like(d_M)
+            d_gsig = torch.empty(n_cfg, n_mat, dtype=torch.float64, device="cuda")
+
+        def step():
+            B.cos_gather(tabs, d_order, d_offset, d_site, d_tau, d_moff, d_M)
+            if args.grad:
+                B.cos_connected_sum_matrices_grad(n_max, d_order, d_moff, n_mat, loop_weight, sigma, d_M, d_gout,
+                                                  out, d_gM, d_gsig)
+            else:
+                B.cos_connected_sum_matrices(n_max, d_order, d_moff, n_mat, loop_weight, sigma, d_M,
+                                             args.precision, out)
+        kernel = ("dp_adjoint_kernel (step: gather + the gradient call)" if args.grad else
+                  "dp_forward_kernel<%s> (step: gather + planner + DP)" % args.precision)
+        launches_per_step = 1 + 4 + (1 if not args.grad else 1)
 
     for _ in range(max(3, args.warmup)):
         step()
     B.cos_sync_status()
-    dp_times.clear()
+    if plan is not None:
+        plan.status()
 
     # FMA probe on this GPU (reported beside the unit-count peak below)
     probe = B.measure_peak(0)
@@ -315,50 +445,44 @@ def native_arm(args):
     if world > 1:
         torch.distributed.barrier()
     B.cos_sync_status()
+    if plan is not None:
+        plan.status()
     total = sum(times)
     if world > 1:
         t = torch.tensor([total], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total = float(t.item())
     value = world * n_cfg * args.steps / total
-    # FP64 roofline denominator from unit counts and the clock seen in the timed region: the
-    # FP64 pipe retires 2 FMA lanes per clock per SM (ncu: the FMA probe issues 1.68 FP64
-    # lanes per SM-cycle at 84.2 % sm__pipe_fp64_cycles_active), 2 flop per FMA.
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    clk = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2032.0
-    fp64_peak = sms * FP64_FMA_PER_CLK_SM * 2.0 * clk * 1e6
-    peak_source = (f"unit count: {sms} SMs x {FP64_FMA_PER_CLK_SM} FP64 FMA/clk/SM x 2 flop x "
-                   f"{clk:.0f} MHz (median SM clock in the timed region)")
-    dp_avg = statistics.mean(a.elapsed_time(b) * 1e-3 for a, b in dp_times)
+    step_mean = total / args.steps
+    head_out = out.cpu().numpy()
     # The gradient call runs the forward sweep and its reverse: two multiply-adds (Obar and dM)
     # per forward multiply-add, so three times the forward's algorithmic flops.
-    flops_launch = algorithmic_flops(B, cfgs.order, n_mat, sigma is not None) * (3 if args.grad else 1)
-    achieved = flops_launch / dp_avg
-    traffic = (HEADLINE_DRAM_BYTES_PER_CFG * n_cfg
-               if args.workload == WORKLOAD and args.precision == "fp64" and not args.grad else None)
-    hbm_gbs, hbm_src = measured_hbm_gbs()
+    flops_step = counts["flops"] * (3 if args.grad else 1)
+    fp64_peak = peaks.fp64(clocks)
+    achieved = flops_step / step_mean
+    hbm_model = counts["traffic"] / step_mean / 1e9
 
     # end to end through the public call with host buffers (pinned), copies inside the region
-    h_order = torch.tensor(cfgs.order).pin_memory()
-    h_offset = torch.tensor(cfgs.offset).pin_memory()
-    h_site = torch.tensor(cfgs.site).pin_memory()
-    h_tau = torch.tensor(cfgs.tau).pin_memory()
+    h_in = [torch.tensor(x).pin_memory() for x in (cfgs.order, cfgs.offset, cfgs.site, cfgs.tau)]
     h_out = torch.empty(n_cfg, dtype=torch.float64).pin_memory()
-    e_order, e_offset, e_site, e_tau = (torch.empty_like(x, device="cuda") for x in (h_order, h_offset, h_site, h_tau))
+    dev_in = (d_order, d_offset, d_site, d_tau)
     e_out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
 
     def e2e_step():
-        for dst, src in ((e_order, h_order), (e_offset, h_offset), (e_site, h_site), (e_tau, h_tau)):
+        for dst, src in zip(dev_in, h_in):
             dst.copy_(src, non_blocking=True)
-        B.cos_connected_sum_batch(tabs, n_max, e_order, e_offset, e_site, e_tau, args.precision, e_out)
-        h_out.copy_(e_out, non_blocking=True)
+        if plan is not None:
+            plan.launch()
+            h_out.copy_(out, non_blocking=True)
+        else:
+            B.cos_connected_sum_batch(tabs, n_max, *dev_in, args.precision, e_out)
+            h_out.copy_(e_out, non_blocking=True)
 
-    for _ in range(2):
-        e2e_step()
+    e2e_step()
     torch.cuda.synchronize()
-    e2e_times = time_steps(torch, e2e_step, max(2, min(args.steps, 5)), lambda: flush_l2(flush_buf))
+    e2e_times = time_steps(torch, e2e_step, max(2, min(args.steps, 4)), lambda: flush_l2(flush_buf))
     B.cos_sync_status()
-    h2d = sum(x.numel() * x.element_size() for x in (h_order, h_offset, h_site, h_tau))
+    h2d = sum(x.numel() * x.element_size() for x in h_in)
     d2h = h_out.numel() * h_out.element_size()
     e2e_mean = statistics.mean(e2e_times)
     if world > 1:   # the job's end-to-end time is the slowest rank's
@@ -366,48 +490,60 @@ def native_arm(args):
         torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
         e2e_mean = float(te.item())
     e2e_value = world * n_cfg / e2e_mean
-    head_out = out.cpu().numpy()
+    if plan is not None:
+        plan.close()
+
     extras, keep = {}, {}
     # the other forms and the CPU baseline are single-GPU measurements (N = 1 only)
     if not args.no_extras and world == 1:
-        extras, keep = measure_forms(torch, B, flush_buf, fp64_peak, sms * 128 * clk * 1e6)
+        extras, keep = measure_forms(torch, B, flush_buf, peaks, args.form_steps)
 
-    launches_per_step = 1 + 4 + 1   # gather, 4 planner kernels, DP
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": 1e3 * step_mean, "ms_per_step_median": 1e3 * statistics.median(times),
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32 extension / f64 close",
                                                        "df64": "f32 pairs (df64)"}[args.precision], "data": "synthetic",
-        "config": {"workload": args.workload, "n": n_max, "n_flavors": w.model.n_flavors, "n_cfg_per_gpu": n_cfg,
+        "config": {"workload": args.workload,
+                   "n": (f"{w.n_lo}..{w.n_hi} uniform" if w.n_lo != w.n_hi else w.n_lo),
+                   "n_flavors": w.model.n_flavors, "n_cfg_per_gpu": n_cfg,
                    "L": w.model.L, "beta": w.model.beta, "U": w.model.U, "mu": list(w.model.mu),
                    "alpha": list(w.model.alpha), "n_tau": w.model.n_tau, "precision": args.precision,
+                   "launch": "one CUDA-graph launch per step" if graph else "gather + DP call per step",
                    "full_size": n_cfg == w.n_cfg,
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"configs sharded x{world}"},
         "roofline": {"bound": "alu", "pipe": "fp64 fma", "achieved": achieved / 1e12,
                      "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                     "peak_source": peak_source, "probe_tflops": probe / 1e12,
+                     "peak_source": (f"unit count: {sms} SMs x {FP64_FMA_PER_CLK_SM} FP64 FMA/clk/SM x 2 flop x "
+                                     f"{peaks.clk(clocks):.0f} MHz (median SM clock in the timed region); "
+                                     f"MEASURED_PEAKS.json has no FP64 figure"),
+                     "probe_tflops": probe / 1e12,
                      "peak_nominal": NOMINAL_FP64_TFLOPS, "frac_of_nominal": achieved / 1e12 / NOMINAL_FP64_TFLOPS,
-                     "kernel": ("dp_adjoint_kernel<sigma grad>" if args.grad else
-                                "dp_forward_kernel<%s>" % {"fp64": "double", "mixed": "float",
-                                                           "df64": "df64"}[args.precision]),
-                     "flops_per_launch": flops_launch,
-                     "launch_ms": dp_avg * 1e3,
-                     "traffic": traffic,
-                     "traffic_source": "ncu DRAM bytes of a 5000-configuration launch, scaled by configurations",
-                     # the other roof: DRAM rate of the same launch against the measured copy bandwidth
-                     "dram_gbs": (traffic / dp_avg / 1e9) if traffic else None,
-                     "hbm_peak_gbs": hbm_gbs, "hbm_peak_source": hbm_src,
-                     "dram_frac": (traffic / dp_avg / 1e9 / hbm_gbs) if traffic else None},
+                     "kernel": kernel,
+                     "achieved_over": "the whole timed step (event pair around each step); the DP kernel is "
+                                      "over 99 % of it, so this is a lower bound on the kernel's own rate",
+                     "flops_per_launch": flops_step,
+                     "launch_ms": step_mean * 1e3,
+                     "traffic": counts["traffic"],
+                     "traffic_source": "model: every reachable DP state written once and read once "
+                                       "(cos_structure states x lanes x state bytes x 2); ncu DRAM bytes of the "
+                                       "same launch are the cross-check",
+                     # the other roof: the modelled DRAM rate of the same launch against the copy bandwidth
+                     "dram_gbs": hbm_model, "hbm_peak_gbs": peaks.hbm_gbs, "hbm_peak_source": peaks.hbm_src,
+                     "dram_frac": hbm_model / peaks.hbm_gbs},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "wall_s_timed_region": t_wall,
     }
+    if args.grad:
+        line["roofline"]["traffic"] = None
+        line["roofline"]["traffic_source"] = "gradient: the kept forward layers and the adjoint ring (not modelled)"
     if extras:
         line["forms"] = extras
     if rank == 0:
         if not args.no_cpu and world == 1:
-            line["cpu_baseline"], line["accuracy"] = oracle_leg(w, args.cpu_seconds, head_out, keep)
+            line["cpu_baseline"], line["accuracy"] = oracle_leg(w, args.cpu_seconds, head_out, keep, args)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
@@ -421,20 +557,24 @@ def error_stats(got, ref, mass=None):
     out = {"configs": int(len(ref)), "median_rel_err": float(np.median(rel)), "max_rel_err": float(np.max(rel))}
     if mass is not None:
         em = np.abs(got - ref) / mass
-        out.update({"max_err_over_mass": float(np.max(em)), "median_kappa": float(np.median(mass / np.abs(ref))),
-                    "max_kappa": float(np.max(mass / np.abs(ref)))})
+        kap = mass / np.abs(ref)
+        out.update({"max_err_over_mass": float(np.max(em)), "median_kappa": float(np.median(kap)),
+                    "max_kappa": float(np.max(kap))})
+        ok = kap <= 1e5
+        if ok.any():
+            out["max_rel_err_kappa_le_1e5"] = float(np.max(rel[ok]))
     return out
 
 
-def oracle_leg(w, budget, head_out, keep):
+def oracle_leg(w, budget, head_out, keep, args):
     """The CPU oracle on the host cores: its throughput on a bounded sample of the headline
-    workload, and the error of the GPU results of the same configurations against it (FP64
-    headline; mixed-precision forms against the FP64 oracle, per configuration)."""
-    rate, threads, n, vals = cpu_oracle_rate(w, budget)
-    base = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n} configurations of the n=8 SU(4) workload (numpy gather + C DP in double, OpenMP)"}
-    mass, _ = oracle_values(w, I.workload_configs(w, n), absmode=True)
-    acc = {"su4_n8_fp64_vs_oracle": error_stats(head_out[:n], vals, mass)}
+    workload, and the error of the GPU results of the same configurations against it; the
+    other forms' results against the FP64 (or long-double) oracle, per configuration."""
+    base, vals = cpu_baseline(w, budget)
+    n = len(vals)
+    cfgs = I.workload_configs(w, n)
+    mass, _ = oracle_values(w, cfgs, absmode=True)
+    acc = {f"{w.name}_{args.precision}_vs_oracle": error_stats(head_out[:n], vals, mass)}
     for name, (wname, got) in keep.items():
         wk = I.WORKLOADS[wname]
         if name.endswith("_by_order"):
@@ -501,12 +641,104 @@ def accuracy_by_order(w, got, mats):
     return out
 
 
-def measure_adjoint(torch, B, flush_buf, n_cfg):
-    """Gradient overhead on the adjoint workload (SU(4), mu broken, n = 10): the gradient call
-    (forward recomputed with every layer kept + reverse DP + chain rule to mu, alpha) against
-    the forward call on the same configurations."""
+# ------------------------------------------------------------------ forms
+
+def measure_forms(torch, B, flush_buf, peaks, steps):
+    """The other forms of the path on the same GPU, each timed over `steps` event-timed steps
+    (median) with its own clock record: FP64 vs mixed vs double-float at orders 8 and 10,
+    order 4 as a plain call and as a graph launch, the adjoint at order 10 against its
+    forward, the plain FP64 form with one configuration per launch, and the NEXT modes
+    (all subsets, bipartite, determinant weights; fewer steps).  Returns the measurements
+    and the GPU outputs kept for the oracle leg's error statistics."""
+    res, keep = {}, {}
+    flush = lambda: flush_l2(flush_buf)
+
+    def run(name, prec, graph=False, n_cfg=None):
+        w = I.WORKLOADS[name]
+        cfgs = I.workload_configs(w, n_cfg)
+        tabs = B.tables_for(w.model)
+        d = B.configs_to_device(cfgs)
+        out = torch.empty(cfgs.n_cfg, dtype=torch.float64, device="cuda")
+        nmax = int(cfgs.order.max())
+        n_mat = tabs.info().n_mat
+        if graph:
+            plan = B.cos_plan_create_batch(tabs, nmax, *d, prec, out)
+            fn = plan.launch
+        else:
+            fn = lambda: B.cos_connected_sum_batch(tabs, nmax, *d, prec, out)
+        t, ts, clocks = timed_form(torch, fn, steps, flush)
+        if graph:
+            plan.status()
+            plan.close()
+        B.cos_sync_status()
+        tabs.close()
+        counts = dp_counts(B, cfgs.order, n_mat, STATE_BYTES[prec])
+        r = {"configs": cfgs.n_cfg, "configs_per_s": cfgs.n_cfg / t, "ms_median": t * 1e3,
+             "ms_min": min(ts) * 1e3, "ms_max": max(ts) * 1e3, "steps": len(ts), "clocks": clocks,
+             "launch_shape_n_max": dict(zip(("warps", "ctas_per_sm", "prefetch"), B.cos_get_tuning(nmax, prec, n_mat)))}
+        rooflines(r, counts, t, prec, peaks, clocks)
+        if graph:
+            r["cuda_graph"] = True
+        return r, out.cpu().numpy()
+
+    # SU(2) symmetric, order 4, 10^4 configurations: latency- and launch-bound (about 15 us of
+    # FP64 work), one plain call and one CUDA-graph plan launch
+    res["su2_n4_fp64"], _ = run("su2_sym_n4", "fp64")
+    res["su2_n4_fp64_graph"], _ = run("su2_sym_n4", "fp64", graph=True)
+    # SU(4), mu broken, order 8, 10^5 configurations: FP64, mixed, double-float
+    res["su4_n8_fp64"], keep_f8 = run("su4_mu_broken_n8", "fp64")
+    keep["su4_n8_fp64_vs_fp64_oracle"] = ("su4_mu_broken_n8", keep_f8)
+    res["su4_n8_mixed"], keep_n8 = run("su4_mu_broken_n8", "mixed")
+    keep["su4_n8_mixed_vs_fp64_oracle"] = ("su4_mu_broken_n8", keep_n8)
+    res["su4_n8_df64"], keep_df8 = run("su4_mu_broken_n8", "df64")
+    keep["su4_n8_df64_vs_fp64_oracle"] = ("su4_mu_broken_n8", keep_df8)
+    # SU(3) with shifts, order 10, 10^5 configurations: mixed (the workload's precision), FP64, df64
+    res["su3_shift_n10_mixed"], keep_n10 = run("su3_shift_mixed_n10", "mixed")
+    keep["su3_shift_n10_mixed_vs_fp64_oracle"] = ("su3_shift_mixed_n10", keep_n10)
+    res["su3_shift_n10_fp64"], keep_f10 = run("su3_shift_mixed_n10", "fp64")
+    keep["su3_shift_n10_fp64_vs_oracle_ld"] = ("su3_shift_mixed_n10", keep_f10)
+    res["su3_shift_n10_df64"], keep_df10 = run("su3_shift_mixed_n10", "df64")
+    keep["su3_shift_n10_df64_vs_fp64_oracle"] = ("su3_shift_mixed_n10", keep_df10)
+    res["su3_shift_n10_mixed"]["speedup_vs_fp64"] = (res["su3_shift_n10_mixed"]["configs_per_s"]
+                                                     / res["su3_shift_n10_fp64"]["configs_per_s"])
+    res["su3_shift_n10_df64"]["speedup_vs_fp64"] = (res["su3_shift_n10_df64"]["configs_per_s"]
+                                                    / res["su3_shift_n10_fp64"]["configs_per_s"])
+    # the headline's outputs per order against the oracle DP on the same gathered matrices
+    wu = I.WORKLOADS[WORKLOAD]
+    cu = I.workload_configs(wu, 4000)
+    tabs = B.tables_for(wu.model)
+    d = B.configs_to_device(cu)
+    out_u = torch.empty(cu.n_cfg, dtype=torch.float64, device="cuda")
+    B.cos_connected_sum_batch(tabs, 12, *d, "fp64", out_u)
+    B.cos_sync_status()
+    tabs.close()
+    mats = {n: (idx, gathered_matrices(torch, B, wu, idx)) for n, idx in sample_by_order(wu, 4000).items() if idx}
+    keep["su6_uneven_fp64_by_order"] = (WORKLOAD, (out_u.cpu().numpy(), mats))
+    res["su4_n10_adjoint"] = measure_adjoint(torch, B, flush, peaks, steps)
+    res["su4_n8_fp64_one_config_per_launch"] = measure_one_per_launch(torch, B)
+    # NEXT modes: fewer steps each (their sizes match the rows above)
+    nsteps = max(2, steps // 3)
+    res["su4_n8_all_subsets_fp64"] = measure_subsets(torch, B, flush, nsteps)
+    for prec in ("fp64", "df64", "mixed"):
+        hb = measure_bipartite(torch, B, flush, I.WORKLOADS["hc_su2_af_n8"].n_cfg, prec, nsteps)
+        if prec == "fp64":
+            hb["frac_fp64_peak"] = hb["tflops"] * 1e12 / peaks.fp64(hb["clocks"])
+        elif prec == "df64":
+            hb["frac_fp32_floor"] = hb["tflops"] * 1e12 / 2.0 * DF64_FP32_PER_TERM / peaks.fp32_lane_ops(hb["clocks"])
+        res[f"hc_su2_af_n8_bipartite_{prec}"] = hb
+    det, det_out = measure_det(torch, B, flush, peaks, nsteps)
+    res.update(det)
+    keep["su2_zeeman_n10_det_fp64_vs_oracle"] = ("su2_zeeman_det_n10", det_out)
+    return res, keep
+
+
+def measure_adjoint(torch, B, flush, peaks, steps):
+    """Gradient overhead on the adjoint workload (SU(4), mu broken, n = 10, 5 x 10^4
+    configurations): the gradient call (forward recomputed + reverse DP + chain rule to mu,
+    alpha) against the forward call on the same configurations, each timed over `steps`."""
     w = I.WORKLOADS["su4_adjoint_n10"]
-    cfgs = I.workload_configs(w, n_cfg)
+    cfgs = I.workload_configs(w)
+    n_cfg = cfgs.n_cfg
     tabs = B.tables_for(w.model)
     d = B.configs_to_device(cfgs)
     out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
@@ -515,24 +747,55 @@ def measure_adjoint(torch, B, flush_buf, n_cfg):
     gal = torch.empty_like(gmu)
     fwd = lambda: B.cos_connected_sum_batch(tabs, 10, *d, "fp64", out)
     grad = lambda: B.cos_connected_sum_grad(tabs, 10, *d, gout, gmu=gmu, galpha=gal)
-    fwd()
-    grad()      # full-size warm-up: sizes every workspace before the timed calls
-    B.cos_sync_status()
-    tf = statistics.mean(time_steps(torch, fwd, 1, lambda: flush_l2(flush_buf)))
-    tg = statistics.mean(time_steps(torch, grad, 1, lambda: flush_l2(flush_buf)))
+    tf, _, cf = timed_form(torch, fwd, steps, flush)
+    tg, tgs, cg = timed_form(torch, grad, steps, flush)
     B.cos_sync_status()
     tabs.close()
-    fl = 3 * algorithmic_flops(B, cfgs.order, 4, False)   # forward sweep + reverse (2 multiply-adds per edge)
+    fl = dp_counts(B, cfgs.order, 4, 8)["flops"]
     return {"configs": n_cfg, "forward_configs_per_s": n_cfg / tf, "grad_configs_per_s": n_cfg / tg,
-            "grad_overhead": tg / tf, "grad_tflops": fl / tg / 1e12}
+            "grad_overhead": tg / tf, "forward_ms_median": tf * 1e3, "grad_ms_median": tg * 1e3,
+            "grad_ms_min": min(tgs) * 1e3, "steps": steps,
+            "grad_tflops": 3 * fl / tg / 1e12, "frac_fp64_peak": 3 * fl / tg / peaks.fp64(cg),
+            "forward_frac_fp64_peak": fl / tf / peaks.fp64(cf),
+            "work": "gradient = forward recompute + reverse sweep (2 multiply-adds per forward one): 3x the "
+                    "forward's algorithmic flops",
+            "clocks_forward": cf, "clocks": cg}
 
 
-def measure_subsets(torch, B, flush_buf, n_cfg):
-    """All-subsets mode on the headline workload (SU(4), mu broken, n = 8): c(S) of all 255
-    vertex subsets and a(S) by the GPU subset exponential, against the plain call (c(V) only)
-    on the same gathered matrices.  Also the root-0 by-product (c(S) for S containing vertex 0)."""
-    w = I.WORKLOADS[WORKLOAD]
-    cfgs = I.workload_configs(w, n_cfg)
+def measure_one_per_launch(torch, B):
+    """The plain FP64 per-configuration form: one configuration per call, no graph (200
+    calls of the order-8 SU(4) workload)."""
+    w = I.WORKLOADS["su4_mu_broken_n8"]
+    cfgs = I.workload_configs(w, 200)
+    tabs = B.tables_for(w.model)
+    d = B.configs_to_device(cfgs)
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    zero = torch.zeros(1, dtype=torch.int64, device="cuda")
+    per = []
+    for c in range(200):
+        o = int(cfgs.offset[c])
+        per.append((d[0][c:c + 1], zero, d[2][o:o + 8], d[3][o:o + 8]))
+    B.cos_connected_sum_batch(tabs, 8, *per[0], "fp64", out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for a in per:
+        B.cos_connected_sum_batch(tabs, 8, *a, "fp64", out)
+    e1.record()
+    e1.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3
+    B.cos_sync_status()
+    tabs.close()
+    return {"configs": 200, "configs_per_s": 200 / t}
+
+
+def measure_subsets(torch, B, flush, steps):
+    """All-subsets mode on the order-8 SU(4) workload: c(S) of all 255 vertex subsets and
+    a(S) by the GPU subset exponential, against the plain call (c(V) only) on the same
+    gathered matrices.  Also the root-0 by-product (c(S) for S containing vertex 0)."""
+    w = I.WORKLOADS["su4_mu_broken_n8"]
+    cfgs = I.workload_configs(w)
+    n_cfg = cfgs.n_cfg
     tabs = B.tables_for(w.model)
     n_mat = tabs.info().n_mat
     d = B.configs_to_device(cfgs)
@@ -545,18 +808,17 @@ def measure_subsets(torch, B, flush_buf, n_cfg):
     plain = lambda: B.cos_connected_sum_matrices(8, d[0], moff, n_mat, 1, None, M, "fp64", out)
     root0 = lambda: B.cos_connected_sum_subsets(8, d[0], moff, n_mat, 1, None, M, "fp64", c, None, False)
     full = lambda: B.cos_connected_sum_subsets(8, d[0], moff, n_mat, 1, None, M, "fp64", c, a, True)
-    for f in (plain, root0, full):
-        f()
-    B.cos_sync_status()
-    tp, t0, tf = (statistics.mean(time_steps(torch, f, 2, lambda: flush_l2(flush_buf))) for f in (plain, root0, full))
+    tp, _, _ = timed_form(torch, plain, steps, flush)
+    t0, _, _ = timed_form(torch, root0, steps, flush)
+    tf, _, clocks = timed_form(torch, full, steps, flush)
     B.cos_sync_status()
     tabs.close()
     return {"configs": n_cfg, "plain_configs_per_s": n_cfg / tp, "root0_configs_per_s": n_cfg / t0,
             "all_subsets_configs_per_s": n_cfg / tf, "all_subsets_cost_vs_plain": tf / tp,
-            "root0_cost_vs_plain": t0 / tp}
+            "root0_cost_vs_plain": t0 / tp, "steps": steps, "clocks": clocks}
 
 
-def measure_bipartite(torch, B, flush_buf, n_cfg, precision="fp64"):
+def measure_bipartite(torch, B, flush, n_cfg, precision, steps):
     """Honeycomb workload (SU(2), antiferromagnetic staggered shift, n = 8; sublattices summed
     per vertex by the sublattice-resolved DP): gather + bipartite DP from vertex coordinates."""
     w = I.WORKLOADS["hc_su2_af_n8"]
@@ -566,15 +828,13 @@ def measure_bipartite(torch, B, flush_buf, n_cfg, precision="fp64"):
     d = B.configs_to_device(cfgs)
     out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
     fn = lambda: B.cos_connected_sum_bipartite_batch(tabs, 8, *d, precision, out)
-    fn()
-    B.cos_sync_status()
-    t = statistics.mean(time_steps(torch, fn, 2, lambda: flush_l2(flush_buf)))
+    t, _, clocks = timed_form(torch, fn, steps, flush)
     B.cos_sync_status()
     s = B.cos_bipartite_structure(8)
     fl = n_cfg * n_mat * 2.0 * (s.fma_ext + s.fma_close)
     tabs.close()
-    return {"configs": n_cfg, "configs_per_s": n_cfg / t, "tflops": fl / t / 1e12, "ms": t * 1e3,
-            "assignments_per_config": 256}
+    return {"configs": n_cfg, "configs_per_s": n_cfg / t, "tflops": fl / t / 1e12, "ms_median": t * 1e3,
+            "assignments_per_config": 256, "steps": steps, "clocks": clocks}
 
 
 def det_fma(B, n: int) -> int:
@@ -587,7 +847,7 @@ def det_fma(B, n: int) -> int:
     return s.fma_ext - saved + s.fma_close
 
 
-def measure_det(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
+def measure_det(torch, B, flush, peaks, steps):
     """SU(2) determinant weights by the DP without cycle factors (Alg. 1): the order-10 square
     workload with a Zeeman-split chemical potential (gather + DP on the same matrices in
     FP64, double-float and mixed precision, against the CoS DP of the same two matrices, which
@@ -606,47 +866,44 @@ def measure_det(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
     fns = {p: (lambda p=p: B.cos_connected_det_matrices(n, d[0], moff, None, M, p, outs[p]))
            for p in ("fp64", "df64", "mixed")}
     fns["cos"] = lambda: B.cos_connected_sum_matrices(n, d[0], moff, 2, 1, None, M, "fp64", outs["cos"])
-    for f in fns.values():
-        f()
-    B.cos_sync_status()
-    ts = {p: statistics.mean(time_steps(torch, f, 2, lambda: flush_l2(flush_buf))) for p, f in fns.items()}
+    ts, cl = {}, {}
+    for p, f in fns.items():
+        ts[p], _, cl[p] = timed_form(torch, f, steps, flush)
     B.cos_sync_status()
     fl = n_cfg * 2 * 2.0 * det_fma(B, n)
     for p in ("fp64", "df64", "mixed"):
-        r = {"configs": n_cfg, "configs_per_s": n_cfg / ts[p], "ms": ts[p] * 1e3,
-             "cost_vs_cos_fp64": ts[p] / ts["cos"]}
+        r = {"configs": n_cfg, "configs_per_s": n_cfg / ts[p], "ms_median": ts[p] * 1e3,
+             "cost_vs_cos_fp64": ts[p] / ts["cos"], "steps": steps, "clocks": cl[p]}
         if p == "fp64":
             r["tflops"] = fl / ts[p] / 1e12
-            r["frac_fp64_peak"] = fl / ts[p] / fp64_peak
+            r["frac_fp64_peak"] = fl / ts[p] / peaks.fp64(cl[p])
         elif p == "df64":
-            r["frac_fp32_floor"] = fl / 2.0 * DF64_FP32_PER_TERM / ts[p] / fp32_lane_ops
+            r["frac_fp32_floor"] = fl / 2.0 * DF64_FP32_PER_TERM / ts[p] / peaks.fp32_lane_ops(cl[p])
         else:
             s = B.cos_structure(n)
-            r["frac_fp64_peak_close"] = n_cfg * 2 * 2.0 * s.fma_close / ts[p] / fp64_peak
+            r["frac_fp64_peak_close"] = n_cfg * 2 * 2.0 * s.fma_close / ts[p] / peaks.fp64(cl[p])
         res[f"su2_zeeman_n10_det_{p}"] = r
     # gradient (reverse sweep of the determinant weights): dc/dM and dc/dalpha of every configuration
     gout = torch.ones(n_cfg, dtype=torch.float64, device="cuda")
     gM = torch.empty_like(M)
     ga = torch.empty(n_cfg, 2, dtype=torch.float64, device="cuda")
     gfn = lambda: B.cos_connected_det_matrices_grad(n, d[0], moff, None, M, gout, None, gM, ga)
-    gfn()
-    B.cos_sync_status()
-    tg = statistics.mean(time_steps(torch, gfn, 1, lambda: flush_l2(flush_buf)))
+    tg, _, cg = timed_form(torch, gfn, steps, flush)
     B.cos_sync_status()
     # every vertex subset: c(S) and a(S) = det(A_up[S]) det(A_dn[S]) (CDet's set of minors)
     cs = torch.empty(n_cfg << n, dtype=torch.float64, device="cuda")
     as_ = torch.empty_like(cs)
     sfn = lambda: B.cos_connected_det_subsets(n, d[0], moff, None, M, cs, as_, True)
-    sfn()
-    B.cos_sync_status()
-    tsub = statistics.mean(time_steps(torch, sfn, 1, lambda: flush_l2(flush_buf)))
+    tsub, _, csub = timed_form(torch, sfn, steps, flush)
     B.cos_sync_status()
     res["su2_zeeman_n10_det_all_subsets_fp64"] = {"configs": n_cfg, "configs_per_s": n_cfg / tsub,
-                                                  "ms": tsub * 1e3, "cost_vs_plain": tsub / ts["fp64"]}
+                                                  "ms_median": tsub * 1e3, "cost_vs_plain": tsub / ts["fp64"],
+                                                  "steps": steps, "clocks": csub}
     del cs, as_
-    res["su2_zeeman_n10_det_grad_fp64"] = {"configs": n_cfg, "grad_configs_per_s": n_cfg / tg, "ms": tg * 1e3,
+    res["su2_zeeman_n10_det_grad_fp64"] = {"configs": n_cfg, "grad_configs_per_s": n_cfg / tg, "ms_median": tg * 1e3,
                                            "grad_overhead": tg / ts["fp64"],
-                                           "frac_fp64_peak": 3 * fl / tg / fp64_peak}
+                                           "frac_fp64_peak": 3 * fl / tg / peaks.fp64(cg), "steps": steps,
+                                           "clocks": cg}
     got = outs["fp64"].cpu().numpy()
     cos = outs["cos"].cpu().numpy()
     res["su2_zeeman_n10_det_fp64"]["max_rel_diff_vs_cos_over_2n"] = float(np.max(np.abs(got - cos / 2.0 ** n) / np.abs(got)))
@@ -665,15 +922,14 @@ def measure_det(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
             "det_df64": lambda: B.cos_connected_det_bipartite_matrices(8, hd[0], hmoff, al, M4, "df64", hout),
             "det_mixed": lambda: B.cos_connected_det_bipartite_matrices(8, hd[0], hmoff, al, M4, "mixed", hout),
             "cos_fp64": lambda: B.cos_connected_sum_bipartite_matrices(8, hd[0], hmoff, 2, 1, None, M4, "fp64", hout)}
-    for f in hfns.values():
-        f()
-    B.cos_sync_status()
-    ht = {k: statistics.mean(time_steps(torch, f, 2, lambda: flush_l2(flush_buf))) for k, f in hfns.items()}
+    ht, hcl = {}, {}
+    for k, f in hfns.items():
+        ht[k], _, hcl[k] = timed_form(torch, f, steps, flush)
     B.cos_sync_status()
     htabs.close()
     for k in ("det_fp64", "det_df64", "det_mixed"):
-        res[f"hc_su2_af_n8_{k}"] = {"configs": hc.n_cfg, "configs_per_s": hc.n_cfg / ht[k], "ms": ht[k] * 1e3,
-                                    "cost_vs_cos_fp64": ht[k] / ht["cos_fp64"]}
+        res[f"hc_su2_af_n8_{k}"] = {"configs": hc.n_cfg, "configs_per_s": hc.n_cfg / ht[k], "ms_median": ht[k] * 1e3,
+                                    "cost_vs_cos_fp64": ht[k] / ht["cos_fp64"], "steps": steps, "clocks": hcl[k]}
     # every vertex subset of both bipartite sweeps: c(S) of all 255 subsets (8 rooted derived
     # problems per configuration) and a(S) by the subset exponential, against the plain call
     hcs = torch.empty(hc.n_cfg * 256, dtype=torch.float64, device="cuda")
@@ -681,12 +937,11 @@ def measure_det(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
     sfns = {"cos_fp64": lambda: B.cos_connected_sum_bipartite_subsets(8, hd[0], hmoff, 2, 1, None, M4, hcs, has),
             "det_fp64": lambda: B.cos_connected_det_bipartite_subsets(8, hd[0], hmoff, al, M4, hcs, has)}
     for k, f in sfns.items():
-        f()
-        B.cos_sync_status()
-        tsk = statistics.mean(time_steps(torch, f, 1, lambda: flush_l2(flush_buf)))
+        tsk, _, ck = timed_form(torch, f, steps, flush)
         B.cos_sync_status()
         res[f"hc_su2_af_n8_{k.split('_')[0]}_all_subsets_fp64"] = {
-            "configs": hc.n_cfg, "configs_per_s": hc.n_cfg / tsk, "ms": tsk * 1e3, "cost_vs_plain": tsk / ht[k]}
+            "configs": hc.n_cfg, "configs_per_s": hc.n_cfg / tsk, "ms_median": tsk * 1e3,
+            "cost_vs_plain": tsk / ht[k], "steps": steps, "clocks": ck}
     del hcs, has
     # gradients of both bipartite sweeps (reverse sweep over every kept layer)
     hg = torch.ones(hc.n_cfg, dtype=torch.float64, device="cuda")
@@ -697,134 +952,15 @@ def measure_det(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
             "det_fp64": lambda: B.cos_connected_det_bipartite_matrices_grad(8, hd[0], hmoff, al, M4, hg, None,
                                                                             gM4, gs2)}
     for k, f in gfns.items():
-        f()
-        B.cos_sync_status()
-        tgk = statistics.mean(time_steps(torch, f, 1, lambda: flush_l2(flush_buf)))
+        tgk, _, ck = timed_form(torch, f, steps, flush)
         B.cos_sync_status()
         res[f"hc_su2_af_n8_{k.split('_')[0]}_grad_fp64"] = {"configs": hc.n_cfg, "grad_configs_per_s": hc.n_cfg / tgk,
-                                                           "ms": tgk * 1e3, "grad_overhead": tgk / ht[k]}
+                                                           "ms_median": tgk * 1e3, "grad_overhead": tgk / ht[k],
+                                                           "steps": steps, "clocks": ck}
     return res, got
 
 
-# FP32 instructions a double-float term needs at least (the Dot2 step: 1 multiply, 3 FMA,
-# 8 additions; the first term of a dot product fewer): the FP32-pipe floor of that mode.
-DF64_FP32_PER_TERM = 11.5
-
-
-def close_flops(B, order: np.ndarray, n_mat: int) -> float:
-    """FP64 flops of the loop-closing sums alone (2 per close multiply-add)."""
-    total = 0.0
-    for n in np.unique(order):
-        s = B.cos_structure(int(n))
-        total += int((order == n).sum()) * n_mat * 2.0 * s.fma_close
-    return total
-
-
-def measure_forms(torch, B, flush_buf, fp64_peak: float, fp32_lane_ops: float):
-    """The other forms of the path on the same GPU: FP64 vs mixed vs double-float (df64)
-    precision at orders 8 and 10,
-    the uneven-order batch as one persistent launch in a CUDA graph (autotuned shapes), the
-    adjoint, and the plain FP64 form with one configuration per launch.  Returns the
-    measurements and the GPU outputs kept for the oracle leg's error statistics."""
-    res, keep = {}, {}
-
-    def run(name, n_cfg, prec, steps=2, graph=False):
-        w = I.WORKLOADS[name]
-        cfgs = I.workload_configs(w, n_cfg)
-        tabs = B.tables_for(w.model)
-        d = B.configs_to_device(cfgs)
-        out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
-        nmax = int(cfgs.order.max())
-        n_mat = tabs.info().n_mat
-        if graph:
-            plan = B.cos_plan_create_batch(tabs, nmax, *d, prec, out)
-            fn = plan.launch
-        else:
-            fn = lambda: B.cos_connected_sum_batch(tabs, nmax, *d, prec, out)
-            fn()
-        B.cos_sync_status()
-        ts = time_steps(torch, fn, steps, lambda: flush_l2(flush_buf))
-        if graph:
-            plan.status()
-            plan.close()
-        B.cos_sync_status()
-        fl = algorithmic_flops(B, cfgs.order, n_mat, any(w.model.sigma))
-        t = statistics.mean(ts)
-        tabs.close()
-        r = {"configs": n_cfg, "configs_per_s": n_cfg / t, "tflops": fl / t / 1e12, "ms": t * 1e3,
-             "launch_shape_n_max": dict(zip(("warps", "ctas_per_sm", "prefetch"), B.cos_get_tuning(nmax, prec, n_mat)))}
-        # roofline of the form: FP64 pipe (FP64), FP64 pipe for the close (mixed), FP32 floor
-        # of the compensated terms (double-float); peaks from the headline's clock sample
-        if prec == "fp64":
-            r["frac_fp64_peak"] = fl / t / fp64_peak
-        elif prec == "mixed":
-            cf = close_flops(B, cfgs.order, n_mat)
-            r["fp64_close_tflops"] = cf / t / 1e12
-            r["frac_fp64_peak_close"] = cf / t / fp64_peak
-        else:
-            terms = fl / 2.0
-            r["frac_fp32_floor"] = terms * DF64_FP32_PER_TERM / t / fp32_lane_ops
-        if graph:
-            r["cuda_graph"] = True
-        return r, out.cpu().numpy()
-
-    # SU(2) symmetric, order 4, 10^4 configurations: latency- and launch-bound (about 15 us of
-    # FP64 work), one plain call and one CUDA-graph plan launch
-    res["su2_n4_fp64"], _ = run("su2_sym_n4", 10_000, "fp64", steps=5)
-    res["su2_n4_fp64_graph"], _ = run("su2_sym_n4", 10_000, "fp64", steps=5, graph=True)
-    res["su4_n8_mixed"], keep_n8 = run("su4_mu_broken_n8", 100_000, "mixed")
-    keep["su4_n8_mixed_vs_fp64_oracle"] = ("su4_mu_broken_n8", keep_n8)
-    res["su3_shift_n10_mixed"], keep_n10 = run("su3_shift_mixed_n10", 100_000, "mixed")
-    keep["su3_shift_n10_mixed_vs_fp64_oracle"] = ("su3_shift_mixed_n10", keep_n10)
-    res["su3_shift_n10_fp64"], keep_f10 = run("su3_shift_mixed_n10", 100_000, "fp64", steps=1)
-    keep["su3_shift_n10_fp64_vs_oracle_ld"] = ("su3_shift_mixed_n10", keep_f10)
-    res["su4_n8_df64"], keep_df8 = run("su4_mu_broken_n8", 100_000, "df64")
-    keep["su4_n8_df64_vs_fp64_oracle"] = ("su4_mu_broken_n8", keep_df8)
-    res["su3_shift_n10_df64"], keep_df10 = run("su3_shift_mixed_n10", 100_000, "df64", steps=1)
-    keep["su3_shift_n10_df64_vs_fp64_oracle"] = ("su3_shift_mixed_n10", keep_df10)
-    res["su6_uneven_n4_12_fp64_graph"], keep_un = run("su6_sym_uneven_n4_12", 200_000, "fp64", steps=1, graph=True)
-    wu = I.WORKLOADS["su6_sym_uneven_n4_12"]
-    mats = {n: (idx, gathered_matrices(torch, B, wu, idx)) for n, idx in sample_by_order(wu, 200_000).items() if idx}
-    keep["su6_uneven_fp64_by_order"] = ("su6_sym_uneven_n4_12", (keep_un, mats))
-    adj = measure_adjoint(torch, B, flush_buf, 50_000)
-    adj["frac_fp64_peak"] = adj["grad_tflops"] * 1e12 / fp64_peak
-    res["su4_n10_adjoint"] = adj
-    res["su4_n8_all_subsets_fp64"] = measure_subsets(torch, B, flush_buf, 100_000)
-    hb = measure_bipartite(torch, B, flush_buf, I.WORKLOADS["hc_su2_af_n8"].n_cfg)
-    hb["frac_fp64_peak"] = hb["tflops"] * 1e12 / fp64_peak
-    res["hc_su2_af_n8_bipartite_fp64"] = hb
-    hd = measure_bipartite(torch, B, flush_buf, I.WORKLOADS["hc_su2_af_n8"].n_cfg, "df64")
-    hd["frac_fp32_floor"] = hd["tflops"] * 1e12 / 2.0 * DF64_FP32_PER_TERM / fp32_lane_ops
-    res["hc_su2_af_n8_bipartite_df64"] = hd
-    res["hc_su2_af_n8_bipartite_mixed"] = measure_bipartite(torch, B, flush_buf, I.WORKLOADS["hc_su2_af_n8"].n_cfg,
-                                                            "mixed")
-    det, det_out = measure_det(torch, B, flush_buf, fp64_peak, fp32_lane_ops)
-    res.update(det)
-    keep["su2_zeeman_n10_det_fp64_vs_oracle"] = ("su2_zeeman_det_n10", det_out)
-    # plain FP64 per-configuration form: one configuration per call, no graph
-    w = I.WORKLOADS[WORKLOAD]
-    cfgs = I.workload_configs(w, 200)
-    tabs = B.tables_for(w.model)
-    d = B.configs_to_device(cfgs)
-    out = torch.empty(1, dtype=torch.float64, device="cuda")
-    per = []
-    for c in range(200):
-        o = int(cfgs.offset[c])
-        per.append((d[0][c:c + 1], torch.zeros(1, dtype=torch.int64, device="cuda"), d[2][o:o + 8], d[3][o:o + 8]))
-    B.cos_connected_sum_batch(tabs, 8, *per[0], "fp64", out)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for a in per:
-        B.cos_connected_sum_batch(tabs, 8, *a, "fp64", out)
-    e1.record()
-    e1.synchronize()
-    t = e0.elapsed_time(e1) * 1e-3
-    res["su4_n8_fp64_one_config_per_launch"] = {"configs": 200, "configs_per_s": 200 / t}
-    B.cos_sync_status()
-    tabs.close()
-    return res, keep
-
+# ------------------------------------------------------------------ profiling arms
 
 def bipartite_arm(args):
     """Profiling runs of the bipartite path alone: the honeycomb workload's gather + DP from
@@ -875,11 +1011,11 @@ def bipartite_arm(args):
 
 def subsets_arm(args):
     """Profiling runs of the all-subsets mode alone: gather + cos_connected_sum_subsets with
-    all roots and a(S) on --n-cfg configurations of the headline workload (SU(4), n = 8)."""
+    all roots and a(S) on --n-cfg configurations of the order-8 SU(4) workload."""
     import torch
     from paper_2507_12349_b300 import binding as B
     B.lib()
-    w = I.WORKLOADS[WORKLOAD]
+    w = I.WORKLOADS["su4_mu_broken_n8"]
     n = w.n_lo
     n_cfg = args.n_cfg if args.n_cfg > 0 else w.n_cfg
     cfgs = I.workload_configs(w, n_cfg)

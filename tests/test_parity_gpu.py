@@ -33,6 +33,8 @@ EPS64 = 2.0 ** -53
 EPS32 = 2.0 ** -24
 # Error measures: 1e-10 relative for kappa = mass / |c| <= 1e5; above, the mass-relative bound.
 KAPPA_RELATIVE_TARGET = 1e5
+# Entrywise agreement of the GPU's and the oracle's propagator matrices (independent tables).
+TABLE_ABS = 1e-13
 
 
 def fp64_bound(n, mass):
@@ -256,7 +258,19 @@ def test_order11_invariances_reduced_precision(precision):
 
 def workload_check(name, n_cfg, sample, prec="fp64", rel=1e-10, graph=False):
     """The workload at the benchmark's size and launch form (graph=True: the CUDA-graph plan
-    the benchmark replays), sampled configurations against the oracle."""
+    the benchmark replays), sampled configurations against the oracle.
+
+    Per configuration:
+      * the inputs: the GPU gather's matrices equal the oracle's (its own tables, its own
+        gather) within TABLE_ABS entry by entry (two independent momentum sums differ by
+        rounding);
+      * the DP on identical inputs: the oracle DP (long double) on the GPU's matrices against
+        the GPU result, within the precision's bound (and 1e-10 relative in FP64 for
+        kappa <= 1e5);
+      * end to end, against the oracle DP on its own matrices: every term is a product of
+        entries, so an entrywise input difference <= delta moves c by at most
+        mass(|M| + delta) - mass(|M|) (the absolute-value DP is monotone in every entry);
+        the GPU result lies within that plus the DP bound."""
     w = I.WORKLOADS[name]
     n_cfg = w.n_cfg if n_cfg is None else n_cfg
     cfgs = I.workload_configs(w, n_cfg)
@@ -274,8 +288,12 @@ def workload_check(name, n_cfg, sample, prec="fp64", rel=1e-10, graph=False):
         plan.close()
     else:
         B.cos_connected_sum_batch(tabs, nmax, *d, prec, out)
+    n_mat = tabs.info().n_mat
+    moff = B.matrix_offsets(cfgs.order, n_mat)
+    gM = torch.empty(int(n_mat * (cfgs.order.astype(np.int64) ** 2).sum()), dtype=torch.float64, device="cuda")
+    B.cos_gather(tabs, *d, torch.as_tensor(moff, device="cuda"), gM)
     B.cos_sync_status()
-    got, gmass = out.cpu().numpy(), mass.cpu().numpy()
+    got, gmass, gmat = out.cpu().numpy(), mass.cpu().numpy(), gM.cpu().numpy()
     otabs = P.model_tables(w.model)
     wt = 1
     sig = list(w.model.sigma)
@@ -283,24 +301,30 @@ def workload_check(name, n_cfg, sample, prec="fp64", rel=1e-10, graph=False):
         otabs, wt, sig = otabs[:1], w.model.n_flavors, sig[:1]
     if not any(sig):
         sig = None
+    bound = {"fp64": fp64_bound, "df64": df64_bound, "mixed": mixed_bound}[prec]
     idx = sorted(set(np.linspace(0, n_cfg - 1, sample).astype(int)))
     errs = []
     for c, M in zip(idx, P.gather(otabs, cfgs, w.model.L, w.model.beta, idx)):
         n = int(cfgs.order[c])
-        ref = O.dp(M, sig, weight=wt, prec="ld")
-        rmass = O.dp(M, sig, weight=wt, absmode=True)
+        Mg = gmat[moff[c]:moff[c] + n_mat * n * n].reshape(n_mat, n, n)
+        ref_g = O.dp(Mg, sig, weight=wt, prec="ld")          # identical inputs
+        ref_o = O.dp(M, sig, weight=wt, prec="ld")           # the oracle's own tables
+        rmass = O.dp(Mg, sig, weight=wt, absmode=True)
         assert gmass[c] == pytest.approx(rmass, rel=1e-10 if prec != "mixed" else 1e-5)
-        e = abs(got[c] - ref)
-        # the relative target holds for condition numbers kappa = mass / |c| up to 1e5; beyond
-        # that the mass-relative bound below is the statement (rounding of the mass's terms)
-        if rmass / abs(ref) <= KAPPA_RELATIVE_TARGET:
-            errs.append(e / abs(ref))
+        e = abs(got[c] - ref_g)
+        tol = bound(n, rmass)
         if prec == "fp64":
-            assert e <= max(rel * abs(ref), fp64_bound(n, rmass)), (c, n, got[c], ref, rmass)
-        elif prec == "df64":
-            assert e <= df64_bound(n, rmass), (c, n, got[c], ref, rmass)
-        else:
-            assert e <= mixed_bound(n, rmass), (c, n, got[c], ref, rmass)
+            tol = max(rel * abs(ref_g), tol)
+            # the relative target holds for condition numbers kappa = mass / |c| up to 1e5;
+            # beyond that the mass-relative bound is the statement
+            if rmass / abs(ref_g) <= KAPPA_RELATIVE_TARGET:
+                errs.append(e / abs(ref_g))
+        assert e <= tol, (c, n, got[c], ref_g, rmass)
+        assert np.max(np.abs(Mg - M)) <= TABLE_ABS, (c, np.max(np.abs(Mg - M)))
+        grow = O.dp(np.abs(Mg) + TABLE_ABS, None if sig is None else np.abs(sig), weight=wt, absmode=True,
+                    prec="ld") - O.dp(np.abs(Mg), None if sig is None else np.abs(sig), weight=wt, absmode=True,
+                                      prec="ld")
+        assert abs(got[c] - ref_o) <= grow + tol, (c, n, got[c], ref_o, grow, tol)
     tabs.close()
     return errs
 
