@@ -729,7 +729,46 @@ def measure_forms(torch, B, flush_buf, peaks, steps):
     det, det_out = measure_det(torch, B, flush, peaks, nsteps)
     res.update(det)
     keep["su2_zeeman_n10_det_fp64_vs_oracle"] = ("su2_zeeman_det_n10", det_out)
+    res.update(measure_grad_high_orders(torch, B, flush, peaks, nsteps))
     return res, keep
+
+
+def measure_grad_high_orders(torch, B, flush, peaks, steps, n_cfg=2368):
+    """Gradient at orders 11 and 12 (the adjoint workload's model, SU(4) with mu broken;
+    2368 configurations = 296 batches, two waves of one CTA per SM): the automatic plan, which
+    checkpoints layers where the free memory cannot hold every CTA's layers, against every
+    layer kept with the grid the memory allows."""
+    w = I.WORKLOADS["su4_adjoint_n10"]
+    tabs = B.tables_for(w.model)
+    res = {}
+    for n in (11, 12):
+        cfgs = I.make_configs(w.model, n, n, n_cfg, seed=40 + n)
+        d = B.configs_to_device(cfgs)
+        gout = torch.ones(n_cfg, dtype=torch.float64, device="cuda")
+        out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
+        fn = lambda: B.cos_connected_sum_grad(tabs, n, *d, gout, out)
+        r = {"configs": n_cfg, "steps": steps}
+        fl = dp_counts(B, cfgs.order, 4, 8)["flops"]
+        for mode, key in (("0", "every_layer_kept"), ("", "automatic")):
+            if mode:
+                os.environ["COS_GRAD_CHECKPOINT"] = mode
+            else:
+                os.environ.pop("COS_GRAD_CHECKPOINT", None)
+            t, _, clocks = timed_form(torch, fn, steps, flush)
+            B.cos_sync_status()
+            r[key] = {"grad_configs_per_s": n_cfg / t, "ms_median": t * 1e3, "clocks": clocks,
+                      "frac_fp64_peak_3x_forward": 3 * fl / t / peaks.fp64(clocks)}
+        os.environ.pop("COS_GRAD_CHECKPOINT", None)
+        mask, store, rec = B.cos_grad_checkpoint_plan(n, 0)
+        s = B.cos_structure(n)
+        r["speedup_automatic_vs_kept"] = r["automatic"]["grad_configs_per_s"] / r["every_layer_kept"]["grad_configs_per_s"]
+        r["layer_storage_per_cta_gb"] = s.slots * 32 * 8 / 1e9
+        r["least_storage_plan"] = {"checkpoint_layers": [l for l in range(2, 2 * n + 1) if mask >> l & 1],
+                                   "storage_fraction": store / s.slots,
+                                   "recompute_fraction_of_forward": rec / (s.fma_ext + s.fma_close)}
+        res[f"su4_n{n}_grad_fp64"] = r
+    tabs.close()
+    return res
 
 
 def measure_adjoint(torch, B, flush, peaks, steps):

@@ -466,6 +466,24 @@ cos_status cos_connected_sum_matrices_grad(int n_cfg, int n_max, const int32_t *
                                            const double *d_gout, double *d_out, double *d_gM,
                                            double *d_gsigma, cos_stream_t stream);
 
+/* Memory of the gradient calls.  The reverse sweep needs the forward state of every layer;
+ * each adjoint overwrites the forward state it was formed from, so the kept layers are the
+ * whole workspace: about (states per flavor array) x 32 lanes x 8 B per CTA, 181 MB at n = 10
+ * and 2.2 GB at n = 12.  Where free device memory cannot hold that for every CTA, layers are
+ * checkpointed (the reverse of Alg. 2-3 with the forward recomputed per segment): a set of
+ * checkpoint layers is kept, and the layers between two checkpoints are re-run from the first
+ * before they are reversed.  The launcher picks, per order, the grid and checkpoint set that
+ * give the most throughput within 85 % of the free memory.  The environment variable
+ * COS_GRAD_CHECKPOINT=1 forces the least-storage plan at every order, =0 keeps every layer.
+ *
+ * cos_grad_checkpoint_plan (host only, no device): the plan of order n for a budget of
+ * slots_budget state slots per lane (0: the least storage): *ck_mask bit l = layer l is a
+ * checkpoint (layers are numbered by visited points, 1 .. 2n; 0 = every layer kept),
+ * *store_slots = slots per lane kept (checkpoints plus the largest segment between two),
+ * *recompute_fma = multiply-adds of one flavor array re-run.  COS_ERR_ARG if nothing fits. */
+cos_status cos_grad_checkpoint_plan(int n, int64_t slots_budget, uint32_t *ck_mask, int64_t *store_slots,
+                                    int64_t *recompute_fma);
+
 /* Gradient from vertex coordinates, with the chain rule through the tables:
  *   dc/dmu_l    = sum_ij dc/dM^l_ij  dM^l_ij/dmu_l  (same interpolation of the dG0/dmu table
  *                 as the gather), the tables' xi depends on mu_l - alpha_l;

@@ -37,7 +37,8 @@ EXPORTS = [
     "cos_connected_det_bipartite_matrices_grad", "cos_connected_det_grad", "cos_connected_sum_bipartite_subsets",
     "cos_connected_det_bipartite_subsets", "cos_connected_det_bipartite_batch", "cos_connected_sum_bipartite_grad",
     "cos_connected_det_bipartite_grad",
-    "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_sync_status", "cos_status_string",
+    "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_grad_checkpoint_plan", "cos_sync_status",
+    "cos_status_string",
     "cos_last_error", "cos_structure",
     "cos_plan_create_batch", "cos_plan_create_matrices", "cos_plan_launch", "cos_plan_status", "cos_plan_grid",
     "cos_plan_destroy", "cos_set_tuning", "cos_get_tuning", "cos_autotune",
@@ -110,6 +111,8 @@ def lib(build: bool = True):
         L.cos_last_error.argtypes = []
         L.cos_last_error.restype = ctypes.c_char_p
         L.cos_structure.argtypes = [i32, ctypes.POINTER(cos_structure_info)]
+        L.cos_grad_checkpoint_plan.argtypes = [i32, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32),
+                                               ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.cos_plan_create_batch.argtypes = [vp, i32, i32, vp, vp, vp, vp, i32, vp, vp, vp, ctypes.POINTER(vp)]
         L.cos_plan_create_matrices.argtypes = [i32, i32, vp, vp, i32, i32, dptr, vp, i32, vp, vp, vp,
                                                ctypes.POINTER(vp)]
@@ -493,6 +496,15 @@ def cos_structure(n: int) -> cos_structure_info:
     inf = cos_structure_info()
     _check(lib().cos_structure(int(n), ctypes.byref(inf)), "cos_structure")
     return inf
+
+
+def cos_grad_checkpoint_plan(n: int, slots_budget: int = 0):
+    """(checkpoint layer mask, slots per lane kept, multiply-adds re-run) of the gradient's
+    plan at order n for a budget of state slots per lane (0: the least storage)."""
+    m, st, rc = ctypes.c_uint32(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().cos_grad_checkpoint_plan(int(n), int(slots_budget), ctypes.byref(m), ctypes.byref(st),
+                                          ctypes.byref(rc)), "cos_grad_checkpoint_plan")
+    return m.value, st.value, rc.value
 
 
 # ------------------------------------------------------------------ torch-facing helpers

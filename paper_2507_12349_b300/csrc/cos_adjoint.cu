@@ -13,15 +13,30 @@
 //     dsigma   += sgn D_j O(mu,h,j) for every half-visited j >= 1 (the shifted diagonal), and
 //                 sgn 2 Obar(2e_0, 0, 0) for the shifted start.
 // Every adjoint slot read was written earlier in the same sweep (targets of reachable edges
-// are reachable), so the adjoint ring needs no clearing.
+// are reachable), so nothing needs clearing.
+//
+// Storage.  Obar(mu,h,v) is formed by the one thread that reads O(mu,h,v), from that slot and
+// the next layer's adjoints, and nothing reads O(mu,h,v) afterwards: the adjoint overwrites
+// the forward state in place, so the reverse sweep needs no storage of its own.
+// Checkpointing (memory-bound orders): the layers 1 = s_0 < s_1 < ... < s_m (checkpoints) are
+// kept in a checkpoint area, the interior layers of one segment (s_i, s_{i+1}) in a segment
+// area.  The first forward pass writes every layer to its place (a later segment overwrites an
+// earlier one's interior); the reverse sweep then takes the segments from the last: for every
+// segment but the last it re-runs the forward from its checkpoint to refill the segment area,
+// then reverses its layers.  The plan (which layers are checkpoints) is chosen per order on the
+// host to fit the CTAs' memory with the least recomputation (ck_plan below).
+// Close adjoints: Cbar(mu) is a flavor sum of the seed slot's adjoints, formed once per mask by
+// the warp that owns the seed slot (mu + e_k, k, k) when it computes that slot's adjoint, and
+// left in a small plane of one value per (mask, lane) that the next layer's warps read.
 // Determinant weights (CLOW instantiations, the sweep of Alg. 1 in cos_dp.cu): the forward
 // recompute runs that mode, the reverse sweep skips the first loop's step onto vertex 0, a
 // close at k = 0 fed block 1 only (Cbar = Obar of that lane), the sink's Cbar is gout, and the
-// diagonal shifts sit in both matrix copies, so dc/dalpha_b = -sum_j dc/dM_b[j][j].  dM accumulates in a private
-// shared-memory copy per warp, summed in warp order at the end: no atomics, bitwise
-// reproducible.
+// diagonal shifts sit in both matrix copies, so dc/dalpha_b = -sum_j dc/dM_b[j][j].
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "cos_dp_device.cuh"
 
@@ -29,8 +44,10 @@ namespace cosdp {
 
 struct AdjArgs {
     DpArgs f;
-    size_t store_elems;     // forward storage per CTA (all layers of n_max) * 32
-    size_t adj_slot_elems;  // one adjoint layer slot * 32
+    size_t store_elems;     // layer storage per CTA (checkpoint + segment areas) * 32
+    size_t plane_elems;     // one close-adjoint plane: max masks per layer * 32
+    size_t cta_elems;       // store_elems + 2 planes
+    uint32_t ckmask[COS_NMAX + 1];   // per order: bit l = layer l is a checkpoint (0: every layer kept)
     const double *gout;
     double *gM;
     const int64_t *gmoff;
@@ -45,8 +62,8 @@ struct AdjArgs {
 //   Obar(mu,h,v) = sum_j D_j Ms[v][j] + Cbar Mc[v][h],  dM[v][j] += D_j O,  dM[v][h] += gamma O,
 //   and for half-visited v >= 1 the shifted diagonal: dsigma += sgn D_v O (qv = index of v in J).
 // D_j = Obar(mu + e_j, h, j) is addressed through the mask's lane-parallel target table
-// (mask_targets, shared with the forward push).  Cbar enters last, so its load and flavor sum
-// overlap the row's target loads.
+// (mask_targets, shared with the forward push).  Cbar enters last, so its load overlaps the
+// row's target loads.
 // Extensions q in [Q0, Q1) of one endpoint: loads first, then the multiply-adds.
 template <int Q0, int Q1>
 __device__ __forceinline__ void adj_chunk(const double *__restrict__ a1, const double *__restrict__ Ms,
@@ -77,13 +94,14 @@ __device__ __forceinline__ void adj_chunk(const double *__restrict__ a1, const d
 }
 
 template <bool SG, int NJ>
-__device__ __forceinline__ void adj_endpoint(const double *__restrict__ fsrc, double *__restrict__ aout,
-                                             const double *__restrict__ a1, const double *__restrict__ Ms,
-                                             const double *__restrict__ Mc, double *__restrict__ dM,
-                                             const TgtInfo &ti, uint32_t J, int v, uint32_t slot, int qv, int h, int n,
-                                             double cbar, double gamma, int lane, double &gs) {
+__device__ __forceinline__ double adj_endpoint(double *st, const double *__restrict__ a1,
+                                               const double *__restrict__ Ms, const double *__restrict__ Mc,
+                                               double *__restrict__ dM, const TgtInfo &ti, uint32_t J, int v,
+                                               uint32_t slot, int qv, int h, int n, double cbar, double gamma,
+                                               int lane, double &gs) {
     constexpr int kSplit = 6;   // at most 6 extensions' operands in registers at a time
-    const double o = fsrc[(size_t)slot * kLanes + lane];
+    // the forward state O(mu,h,v), replaced by its adjoint below (same slot, same thread)
+    const double o = st[(size_t)slot * kLanes + lane];
     const int vrow = v * n * kLanes + lane;
     const uint32_t hlow = (1u << h) - 1u;
     uint32_t jr = J;
@@ -100,19 +118,20 @@ __device__ __forceinline__ void adj_endpoint(const double *__restrict__ fsrc, do
     const int vh = vrow + h * kLanes;
     ob = fma(cbar, Mc[vh], ob);
     if ((__double_as_longlong(cbar) << 1) != 0) dM[vh] = fma(gamma, o, dM[vh]);
-    aout[(size_t)slot * kLanes + lane] = ob;
+    st[(size_t)slot * kLanes + lane] = ob;
+    return ob;
 }
 
 // MAXNJ: the largest order the kernel instance runs (larger counts are never dispatched).
 template <bool SG, int MAXNJ>
-__device__ __forceinline__ void adj_endpoint_dispatch(int nJ, const double *fsrc, double *aout, const double *a1,
-                                                      const double *Ms, const double *Mc, double *dM,
-                                                      const TgtInfo &ti, uint32_t J, int v, uint32_t slot, int qv,
-                                                      int h, int n, double cbar, double gamma, int lane, double &gs) {
+__device__ __forceinline__ double adj_endpoint_dispatch(int nJ, double *st, const double *a1, const double *Ms,
+                                                        const double *Mc, double *dM, const TgtInfo &ti, uint32_t J,
+                                                        int v, uint32_t slot, int qv, int h, int n, double cbar,
+                                                        double gamma, int lane, double &gs) {
 #define COS_AEP(K)                                                                                             \
     case K:                                                                                                    \
         if constexpr (K <= MAXNJ)                                                                              \
-            adj_endpoint<SG, K>(fsrc, aout, a1, Ms, Mc, dM, ti, J, v, slot, qv, h, n, cbar, gamma, lane, gs);   \
+            return adj_endpoint<SG, K>(st, a1, Ms, Mc, dM, ti, J, v, slot, qv, h, n, cbar, gamma, lane, gs);   \
         break;
     switch (nJ) {
         COS_AEP(0)
@@ -132,18 +151,34 @@ __device__ __forceinline__ void adj_endpoint_dispatch(int nJ, const double *fsrc
             break;
     }
 #undef COS_AEP
+    return 0.0;
+}
+
+// One layer of the forward sweep (masks split over the warps as in the forward kernel).
+template <bool CLOW>
+__device__ __forceinline__ void adj_forward_layer(const OrderTab &tab, int ell, int n, const double *src, double *dst1,
+                                                  const double *Ms, const double *Mc, int lane, int warp, int nwarps,
+                                                  int ci, int nfl, double sgn, double sig, bool shifts, bool active,
+                                                  int lam, int cfg, double *out, int *status) {
+    const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
+    for (uint32_t mi = warp; mi < cnt; mi += nwarps)
+        fwd_mask<double, false, CLOW>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n,
+                                      src, dst1, Ms, Mc, lane, ci, nfl, sgn, sig, shifts, active, lam, cfg, out,
+                                      status, 1);
 }
 
 // Warps own endpoint vertices (v % warps == warp) in the reverse sweep, so the dM accumulators
 // [v][j][lane] of the CTA have one writer per row v: one shared-memory copy, no atomics, each
 // entry summed in a fixed order (bitwise reproducible).  Every warp walks every mask of a layer
-// and takes the rows' endpoints it owns.  The forward recompute splits masks across warps as
-// in the forward kernel.  MAXT = 320 (orders <= 10, two CTAs per SM) or 384 (one CTA).
+// and takes the rows' endpoints it owns.  The forward passes split masks across warps as in the
+// forward kernel.  MAXT = 320 (orders <= 10, two CTAs per SM) or 384 (one CTA).
 template <bool SG, int MAXT, bool CLOW = false>
 __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(const __grid_constant__ AdjArgs a) {
     extern __shared__ __align__(16) double smem_d[];
     __shared__ int s_batch;
-    __shared__ uint32_t s_base[kMaxLayers + 3];
+    __shared__ uint32_t s_loc[kMaxLayers + 2];   // slot offset of each layer in the CTA's store
+    __shared__ int s_seg[kMaxLayers + 1];        // segment starts: layer 1, then the checkpoints
+    __shared__ int s_nseg;
     __shared__ double s_red[MAXT / 32][kLanes];
     const DpArgs &f = a.f;
     const int lane = threadIdx.x & 31;
@@ -153,8 +188,8 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
     double *Ms = smem_d;              // extension matrices, shifted diagonal
     double *Mc = smem_d + nsm;        // close matrices times sgn w
     double *dM = smem_d + 2 * nsm;    // dc/dM accumulators [v][j][lane]
-    double *store = reinterpret_cast<double *>(f.scratch) + (size_t)blockIdx.x * (a.store_elems + 2 * a.adj_slot_elems);
-    double *adj = store + a.store_elems;
+    double *store = reinterpret_cast<double *>(f.scratch) + (size_t)blockIdx.x * a.cta_elems;
+    double *cplane = store + a.store_elems;   // two planes of close adjoints, by layer parity
     const int nfl = f.nf_lanes;
     const int lam = lane % nfl;
     const int ci = lane / nfl;
@@ -192,88 +227,118 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
             dM[e * kLanes + lane] = 0.0;
         }
         if (threadIdx.x == 0) {
+            // layer places: checkpoints (layer 1 and the plan's layers) back to back, then the
+            // interior layers of one segment back to back after them
+            const uint32_t ck = a.ckmask[n];
+            uint32_t c = 0;
+            int ns = 0;
+            for (int l = 1; l <= 2 * n; ++l)
+                if (l == 1 || ((ck >> l) & 1u)) {
+                    s_loc[l] = c;
+                    c += tab.layer_slots[l];
+                    s_seg[ns++] = l;
+                }
             uint32_t run = 0;
-            for (int l = 0; l <= 2 * n + 2; ++l) {
-                s_base[l] = run;
-                if (l <= 2 * n) run += tab.layer_slots[l];
+            for (int l = 2; l <= 2 * n; ++l) {
+                if ((ck >> l) & 1u) {
+                    run = 0;
+                } else {
+                    s_loc[l] = c + run;
+                    run += tab.layer_slots[l];
+                }
             }
+            s_loc[2 * n + 1] = 0;   // the full mask extends nowhere: never written or read
+            s_nseg = ns;
         }
         __syncthreads();
-        if (warp == 0) store[(size_t)s_base[1] * kLanes + lane] = (CLOW && lam != 0) ? 0.0 : 1.0;
+        if (warp == 0) store[(size_t)s_loc[1] * kLanes + lane] = (CLOW && lam != 0) ? 0.0 : 1.0;
         __syncthreads();
-        // forward sweep, every layer kept
+        // first forward pass: every layer at its place
         for (int ell = 1; ell <= 2 * n; ++ell) {
-            const double *src = store + (size_t)s_base[ell] * kLanes;
-            double *dst1 = store + (size_t)s_base[ell + 1] * kLanes;
-            const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
-            for (uint32_t mi = warp; mi < cnt; mi += nwarps)
-                fwd_mask<double, false, CLOW>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu,
-                                              ell, n, src, dst1, Ms, Mc, lane, ci, nfl, sgn, sig, shifts, active, lam,
-                                              cfg, f.out, f.status, 1);
+            adj_forward_layer<CLOW>(tab, ell, n, store + (size_t)s_loc[ell] * kLanes,
+                                    store + (size_t)s_loc[ell + 1] * kLanes, Ms, Mc, lane, warp, nwarps, ci, nfl, sgn,
+                                    sig, shifts, active, lam, cfg, f.out, f.status);
             __syncthreads();
         }
-        // reverse sweep: this warp's endpoints
+        // reverse sweep, segment by segment from the last: this warp's endpoints
         uint32_t own = 0u;
         for (int v = warp; v < n; v += nwarps) own |= 1u << v;
         const uint32_t full = (1u << n) - 1u;
         const double gout = active ? a.gout[cfg] : 0.0;
         double gs = 0.0;
-        for (int ell = 2 * n; ell >= 1; --ell) {
-            const double *fsrc = store + (size_t)s_base[ell] * kLanes;
-            double *aout = adj + (size_t)(ell & 1) * a.adj_slot_elems;
-            const double *a1 = adj + (size_t)((ell + 1) & 1) * a.adj_slot_elems;
-            const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
-            for (uint32_t mi = 0; mi < cnt && own; ++mi) {
-                const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + first + mi));
-                // the warps take turns to pull a later mask's forward states into L2 ahead of use
-                if (mi + 2 < cnt && (int)((mi + 2) % nwarps) == warp) {
-                    const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + first + mi + 2));
-                    const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
-                    prefetch_block(fsrc, nk.z, (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane, 1);
-                }
-                const uint32_t A = mk.x & 0xFFFFu;
-                if (!(A & own)) continue;   // endpoints are visited vertices
-                const uint32_t B = mk.x >> 16, code = mk.y, off = mk.z;
-                const uint32_t ones = A & ~B;
-                const uint32_t H = head_set(B, ones);
-                const uint32_t J = full & ~B & (CLOW ? ~(ones & 1u) : 0xFFFFFFFFu);
-                const int nA = __popc(A);
-                const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, lane);
-                const int nJ = __popc(J);
-                double cbar = 0.0;
-                if (B == full) {
-                    cbar = CLOW ? gout : ldexp(gout, n - 1);
-                } else if (ones) {
-                    const int k = __ffs(ones) - 1;
-                    const uint32_t bk = 1u << k;
-                    const uint32_t B1 = B | bk;
-                    const int hi1 = __popc(head_set(B1, A & ~B1) & (bk - 1u));
-                    const int ai1 = __popc(A & (bk - 1u));
-                    const uint32_t off1 = __ldg(tab.rank3 + code + c_p3[k]);
-                    const double seed = a1[(size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane];
-                    // (CLOW: the close at k = 0 seeded block 1 only)
-                    cbar = flavor_sum((CLOW && k == 0 && lam == 0) ? 0.0 : seed, nfl, ci);
-                    // shifted start (mask e_0, owned by the warp of vertex 0), weight sgn 2 sigma
-                    if (SG && !CLOW && ell == 1) gs = fma(sgn * 2.0, seed, gs);
-                }
-                // loop weight 1: sgn w Cbar is a sign flip (integer pipe), else one multiply
-                const double gamma = unit_weight ? neg(cbar) : cfac * cbar;
-                for (uint32_t hh = H; hh; hh &= hh - 1u) {
-                    const int h = __ffs(hh) - 1;
-                    const int hidx = __popc(H & ((1u << h) - 1u));
-                    const uint32_t rowoff = off + (uint32_t)(hidx * nA);
-                    for (uint32_t vv = row_vmask(A, ones, h) & own; vv; vv &= vv - 1u) {
-                        const int v = __ffs(vv) - 1;
-                        const uint32_t slot = rowoff + (uint32_t)__popc(A & ((1u << v) - 1u));
-                        // half-visited v >= 1: its index among the extensions (v is in J)
-                        const int qv =
-                            (SG && !CLOW && v != 0 && (ones & (1u << v))) ? __popc(J & ((1u << v) - 1u)) : -1;
-                        adj_endpoint_dispatch<SG, (MAXT <= 320 ? 10 : 12)>(nJ, fsrc, aout, a1, Ms, Mc, dM, ti, J, v, slot, qv, h, n, cbar,
-                                                                      gamma, lane, gs);
-                    }
+        for (int sg = s_nseg - 1; sg >= 0; --sg) {
+            const int lo = s_seg[sg], hi = (sg + 1 < s_nseg) ? s_seg[sg + 1] : 2 * n + 1;
+            // refill the segment area from its checkpoint (the last segment is still in place)
+            if (sg + 1 < s_nseg) {
+                for (int ell = lo; ell <= hi - 2; ++ell) {
+                    adj_forward_layer<CLOW>(tab, ell, n, store + (size_t)s_loc[ell] * kLanes,
+                                            store + (size_t)s_loc[ell + 1] * kLanes, Ms, Mc, lane, warp, nwarps, ci,
+                                            nfl, sgn, sig, shifts, active, lam, cfg, nullptr, f.status);
+                    __syncthreads();
                 }
             }
-            __syncthreads();
+            for (int ell = hi - 1; ell >= lo; --ell) {
+                double *st = store + (size_t)s_loc[ell] * kLanes;          // O(ell), replaced by Obar(ell)
+                const double *a1 = store + (size_t)s_loc[ell + 1] * kLanes;  // Obar(ell + 1)
+                const double *cin = cplane + (size_t)(ell & 1) * a.plane_elems;   // Cbar of this layer's masks
+                double *cout = cplane + (size_t)((ell - 1) & 1) * a.plane_elems;  // Cbar of the layer below
+                const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
+                for (uint32_t mi = 0; mi < cnt && own; ++mi) {
+                    const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + first + mi));
+                    // the warps take turns to pull a later mask's forward states into L2 ahead of use
+                    if (mi + 2 < cnt && (int)((mi + 2) % nwarps) == warp) {
+                        const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + first + mi + 2));
+                        const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
+                        prefetch_block(st, nk.z, (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane,
+                                       1);
+                    }
+                    const uint32_t A = mk.x & 0xFFFFu;
+                    if (!(A & own)) continue;   // endpoints are visited vertices
+                    const uint32_t B = mk.x >> 16, code = mk.y, off = mk.z;
+                    const uint32_t ones = A & ~B;
+                    const uint32_t H = head_set(B, ones);
+                    const uint32_t J = full & ~B & (CLOW ? ~(ones & 1u) : 0xFFFFFFFFu);
+                    const int nA = __popc(A);
+                    const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, lane);
+                    const int nJ = __popc(J);
+                    double cbar = 0.0;
+                    if (B == full) {
+                        cbar = CLOW ? gout : ldexp(gout, n - 1);
+                    } else if (ones) {
+                        cbar = cin[(size_t)mi * kLanes + lane];   // flavor-summed by the seed slot's owner
+                        // shifted start (mask e_0, owned by the warp of vertex 0), weight sgn 2 sigma:
+                        // the adjoint of the seed slot (2 e_0, 0, 0) itself
+                        if (SG && !CLOW && ell == 1) {
+                            const uint32_t off1 = __ldg(tab.rank3 + code + c_p3[0]);
+                            gs = fma(sgn * 2.0, a1[(size_t)off1 * kLanes + lane], gs);
+                        }
+                    }
+                    // loop weight 1: sgn w Cbar is a sign flip (integer pipe), else one multiply
+                    const double gamma = unit_weight ? neg(cbar) : cfac * cbar;
+                    for (uint32_t hh = H; hh; hh &= hh - 1u) {
+                        const int h = __ffs(hh) - 1;
+                        const int hidx = __popc(H & ((1u << h) - 1u));
+                        const uint32_t rowoff = off + (uint32_t)(hidx * nA);
+                        for (uint32_t vv = row_vmask(A, ones, h) & own; vv; vv &= vv - 1u) {
+                            const int v = __ffs(vv) - 1;
+                            const uint32_t slot = rowoff + (uint32_t)__popc(A & ((1u << v) - 1u));
+                            // half-visited v >= 1: its index among the extensions (v is in J)
+                            const int qv =
+                                (SG && !CLOW && v != 0 && (ones & (1u << v))) ? __popc(J & ((1u << v) - 1u)) : -1;
+                            const double ob = adj_endpoint_dispatch<SG, (MAXT <= 320 ? 10 : 12)>(
+                                nJ, st, a1, Ms, Mc, dM, ti, J, v, slot, qv, h, n, cbar, gamma, lane, gs);
+                            if (v == h && ((B >> h) & 1u)) {
+                                // (mu, h, h) with h full is the seed slot of mu - e_h's close (the loop
+                                // opened at h and has not moved): its flavor sum is that mask's Cbar
+                                // (determinant weights: a close at k = 0 seeded block 1 only)
+                                const double fs = flavor_sum((CLOW && h == 0 && lam == 0) ? 0.0 : ob, nfl, ci);
+                                cout[(size_t)__ldg(tab.ord3 + code - c_p3[h]) * kLanes + lane] = fs;
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+            }
         }
         // dM rows are final (every warp passed the last barrier); dsigma: sum over warps in order
         if (active && a.gM) {
@@ -358,6 +423,98 @@ __global__ void chain_kernel(const double *__restrict__ dG, int L, int n_tau, do
 // endpoint in the reverse sweep.
 int adjoint_warps(int n_max) { return std::max(4, std::min(12, n_max)); }
 
+// ------------------------------------------------------------------ checkpoint plans
+//
+// Storage (state slots per lane) and recomputation (multiply-adds of one flavor array) of a set
+// of checkpoint layers, in the layout of dp_adjoint_kernel: layer 1 and the checkpoints back to
+// back, then room for the largest segment interior.  A segment other than the last is re-run
+// from its checkpoint: the forward steps out of its layers s_i .. s_{i+1} - 2.
+struct CkPlan {
+    uint32_t mask = 0;
+    uint64_t store = 0;
+    uint64_t recompute = 0;
+    bool ok = false;
+};
+
+static CkPlan ck_eval(const HostOrder &o, uint32_t mask) {
+    const int L = 2 * o.n;
+    uint64_t ck = o.layer_slots[1], interior = 0, segmax = 0, rec = 0;
+    int start = 1;
+    for (int l = 2; l <= L; ++l) {
+        if ((mask >> l) & 1u) {
+            segmax = std::max(segmax, interior);
+            for (int e = start; e <= l - 2; ++e) rec += o.layer_work[e];
+            start = l;
+            interior = 0;
+            ck += o.layer_slots[l];
+        } else {
+            interior += o.layer_slots[l];
+        }
+    }
+    segmax = std::max(segmax, interior);
+    CkPlan p;
+    p.mask = mask;
+    p.store = ck + segmax;
+    p.recompute = rec;
+    p.ok = true;
+    return p;
+}
+
+constexpr int kMaxCheckpoints = 7;   // enough for the optimum at every order up to 12
+
+// Pareto frontier of the checkpoint sets of order n (every set of at most kMaxCheckpoints layers
+// among 2 .. 2n, and the empty set): increasing storage, strictly decreasing recomputation.  The
+// first point needs the least storage; the last is the empty set (no recomputation).
+static const std::vector<CkPlan> &ck_frontier(int n) {
+    static std::mutex mu;
+    static std::vector<CkPlan> cache[COS_NMAX + 1];
+    std::lock_guard<std::mutex> lk(mu);
+    std::vector<CkPlan> &fr = cache[n];
+    if (!fr.empty()) return fr;
+    const HostOrder &o = host_order(n);
+    std::vector<CkPlan> all;
+    all.push_back(ck_eval(o, 0u));
+    struct Rec {
+        const HostOrder &o;
+        int L;
+        std::vector<CkPlan> &all;
+        void go(int from, int k, uint32_t mask) {
+            for (int l = from; l <= L; ++l) {
+                const uint32_t m = mask | (1u << l);
+                all.push_back(ck_eval(o, m));
+                if (k + 1 < kMaxCheckpoints) go(l + 1, k + 1, m);
+            }
+        }
+    } rec{o, 2 * n, all};
+    rec.go(2, 0, 0u);
+    std::sort(all.begin(), all.end(), [](const CkPlan &a, const CkPlan &b) {
+        return a.store != b.store ? a.store < b.store
+               : a.recompute != b.recompute ? a.recompute < b.recompute : a.mask < b.mask;
+    });
+    for (const CkPlan &c : all)
+        if (fr.empty() || c.recompute < fr.back().recompute) fr.push_back(c);
+    return fr;
+}
+
+// The least recomputation whose storage fits `budget` slots per lane (no checkpoints when every
+// layer fits); budget = 0 asks for the least storage.  ok = false when nothing fits.
+static CkPlan ck_plan(int n, uint64_t budget) {
+    const std::vector<CkPlan> &fr = ck_frontier(n);
+    if (budget == 0) return fr.front();
+    CkPlan best;
+    for (const CkPlan &c : fr)
+        if (c.store <= budget) best = c;   // recomputation decreases along the frontier
+    return best;
+}
+
+// COS_GRAD_CHECKPOINT=1: every order keeps the least storage (recomputing the most); =0: every
+// layer kept whatever the memory; unset: the plan that gives the most throughput within memory.
+static int checkpoint_mode() {
+    const char *e = getenv("COS_GRAD_CHECKPOINT");
+    if (!e || !*e) return -1;
+    return e[0] == '0' ? 0 : 1;
+}
+
 cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, double *gM, const int64_t *gmoff,
                           int64_t gmstride, double *gsig, cudaStream_t stream) {
     std::string err;
@@ -366,15 +523,12 @@ cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, 
         set_error(err);
         return COS_ERR_CUDA;
     }
-    const HostOrder &ho = host_order(L.n_max);
-    size_t total_slots = 0;
-    for (int l = 0; l <= 2 * L.n_max; ++l) total_slots += ho.layer_slots[l];
-    const size_t store_elems = total_slots * kLanes;
-    const size_t adj_slot_elems = (size_t)ho.max_slots * kLanes;
-    const size_t per_cta = (store_elems + 2 * adj_slot_elems) * sizeof(double);
-    const int warps = adjoint_warps(L.n_max);
+    const int n_max = L.n_max;
+    const HostOrder &ho = host_order(n_max);
+    const size_t plane_elems = (size_t)ho.max_masks * kLanes;
+    const int warps = adjoint_warps(n_max);
     const int threads = warps * 32;
-    const size_t smem = (size_t)3 * L.n_max * L.n_max * kLanes * sizeof(double);
+    const size_t smem = (size_t)3 * n_max * n_max * kLanes * sizeof(double);
     const bool sg = gsig != nullptr;
     const bool big = threads > 320;
     auto kern = L.clow ? (big ? dp_adjoint_kernel<false, 384, true> : dp_adjoint_kernel<false, 320, true>)
@@ -391,18 +545,61 @@ cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, 
     }
     const int cpb = kLanes / L.n_mat;
     const int max_batches = (L.n_cfg + cpb - 1) / cpb + COS_NMAX;
-    int grid = std::max(1, std::min(nsm * std::min(per_sm, 2), max_batches));
+    const int gmax = std::max(1, std::min(nsm * std::min(per_sm, 2), max_batches));
     size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-        // every layer of the largest order is kept per CTA (GBs at the top orders): as many CTAs
-        // as fit in the free memory
-        const size_t avail = ws->scratch_bytes + (size_t)(0.85 * (double)free_b);
-        grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)grid, avail / per_cta));
+    size_t avail = (size_t)-1;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) avail = ws->scratch_bytes + (size_t)(0.85 * (double)free_b);
+    const size_t plane_bytes = 2 * plane_elems * sizeof(double);
+    auto slots_budget = [&](int g) -> uint64_t {
+        const size_t per = avail / (size_t)g;
+        return per > plane_bytes ? (per - plane_bytes) / (kLanes * sizeof(double)) : 1;
+    };
+    // Grid and checkpoint plan of the largest order: the most throughput, CTAs x the inverse of
+    // the work per batch (forward, reverse = 2 forwards, and the recomputed segments).
+    const int mode = checkpoint_mode();
+    uint64_t fwd_work = 0;
+    for (int l = 1; l <= 2 * n_max; ++l) fwd_work += ho.layer_work[l];
+    int grid = 1;
+    uint64_t budget = 0;   // slots per lane of every order's plan (0: least storage)
+    if (mode == 1) {
+        const CkPlan p = ck_plan(n_max, 0);
+        grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)gmax, avail / (p.store * kLanes * 8 + plane_bytes)));
+    } else if (mode == 0) {
+        const CkPlan p = ck_eval(ho, 0u);
+        budget = p.store;
+        grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)gmax, avail / (p.store * kLanes * 8 + plane_bytes)));
+    } else {
+        double best_score = -1.0;
+        for (int g = gmax; g >= 1; g = (g > 8 ? g - std::max(1, g / 8) : g - 1)) {
+            const uint64_t b = slots_budget(g);
+            const CkPlan p = ck_plan(n_max, b);
+            if (!p.ok) continue;
+            const double score = (double)g / (3.0 * (double)fwd_work + (double)p.recompute);
+            if (score > best_score * (1.0 + 1e-9)) {
+                best_score = score;
+                grid = g;
+                budget = b;
+            }
+        }
+        if (best_score < 0) {   // not even one CTA fits: least storage, one CTA
+            grid = 1;
+            budget = 0;
+        }
     }
-    cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "adjoint scratch");
-    if (st != COS_OK) return st;
     AdjArgs a;
     memset(&a, 0, sizeof a);
+    uint64_t store_slots = 0;
+    for (int n = 1; n <= n_max; ++n) {
+        const CkPlan p = (mode == 0) ? ck_eval(host_order(n), 0u) : ck_plan(n, budget);
+        const CkPlan q = p.ok ? p : ck_plan(n, 0);
+        a.ckmask[n] = q.mask;
+        store_slots = std::max(store_slots, q.store);
+    }
+    const size_t store_elems = (size_t)store_slots * kLanes;
+    const size_t cta_elems = store_elems + 2 * plane_elems;
+    cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * cta_elems * sizeof(double), 1,
+                           "adjoint scratch");
+    if (st != COS_OK) return st;
     DpArgs &f = a.f;
     f.tabs = tabs;
     f.batches = ws->batches;
@@ -418,18 +615,20 @@ cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, 
     f.shifts = L.shifts ? 1 : 0;
     f.absmode = 0;
     f.scratch = ws->scratch;
-    f.slot_elems = adj_slot_elems;
-    f.nslots = 2;
-    f.smem_n = L.n_max;
+    f.slot_elems = 0;
+    f.nslots = 0;
+    f.smem_n = n_max;
     f.out = L.out;
     f.status = ws->status;
     a.store_elems = store_elems;
-    a.adj_slot_elems = adj_slot_elems;
+    a.plane_elems = plane_elems;
+    a.cta_elems = cta_elems;
     a.gout = gout;
     a.gM = gM;
     a.gmoff = gmoff;
     a.gmstride = gmstride;
     a.gsig = gsig;
+    ws->last_grid = grid;
     e = cudaMemsetAsync(ws->queue, 0, sizeof(int), stream);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
     kern<<<grid, warps * 32, smem, stream>>>(a);
@@ -455,3 +654,24 @@ cos_status launch_chain(const cos_tables *t, int n_cfg, const int32_t *order, co
 }
 
 }  // namespace cosdp
+
+extern "C" cos_status cos_grad_checkpoint_plan(int n, int64_t slots_budget, uint32_t *ck_mask, int64_t *store_slots,
+                                               int64_t *recompute_fma) {
+    if (n < 1 || n > COS_NMAX) {
+        cosdp::set_error("cos_grad_checkpoint_plan: order out of range");
+        return COS_ERR_ORDER;
+    }
+    if (slots_budget < 0 || !ck_mask || !store_slots || !recompute_fma) {
+        cosdp::set_error("cos_grad_checkpoint_plan: invalid argument");
+        return COS_ERR_ARG;
+    }
+    const cosdp::CkPlan p = cosdp::ck_plan(n, (uint64_t)slots_budget);
+    if (!p.ok) {
+        cosdp::set_error("cos_grad_checkpoint_plan: no checkpoint plan fits the budget");
+        return COS_ERR_ARG;
+    }
+    *ck_mask = p.mask;
+    *store_slots = (int64_t)p.store;
+    *recompute_fma = (int64_t)p.recompute;
+    return COS_OK;
+}

@@ -37,10 +37,12 @@ struct MaskRec {
 struct OrderTab {
     const MaskRec *masks;     // grouped by layer, cost-sorted (descending) inside a layer
     const uint32_t *rank3;    // code -> block offset inside its layer
+    const uint32_t *ord3;     // code -> ordinal of the mask inside its layer (null where unused)
     uint32_t layer_first[kMaxLayers + 1];
     uint32_t layer_count[kMaxLayers + 1];
     uint32_t layer_slots[kMaxLayers + 1];
     uint32_t max_slots;
+    uint32_t max_masks;       // most masks in one layer
     uint32_t n;
 };
 
@@ -72,10 +74,13 @@ struct HostOrder {
     int n = 0;
     std::vector<MaskRec> masks;
     std::vector<uint32_t> rank3;
+    std::vector<uint32_t> ord3;
     uint32_t layer_first[kMaxLayers + 1] = {};
     uint32_t layer_count[kMaxLayers + 1] = {};
     uint32_t layer_slots[kMaxLayers + 1] = {};
     uint32_t max_slots = 0;
+    uint32_t max_masks = 0;
+    uint64_t layer_work[kMaxLayers + 1] = {};   // multiply-adds of the sweep out of each layer (one flavor array)
     cos_structure_info info{};
 };
 

@@ -82,6 +82,8 @@ cos_status setup_device(int dev, cudaStream_t stream, DevSetup **out) {
         memcpy(t.layer_count, o.layer_count, sizeof t.layer_count);
         memcpy(t.layer_slots, o.layer_slots, sizeof t.layer_slots);
         t.max_slots = o.max_slots;
+        t.max_masks = o.max_masks;
+        t.ord3 = nullptr;   // used by the gradient only
         t.n = n;
     }
     e = cudaMemcpyAsync(base + tabs_off, tabs, sizeof tabs, cudaMemcpyHostToDevice, stream);

@@ -24,6 +24,7 @@ void build_order(int n, HostOrder &o) {
     for (int i = 1; i <= n + 1; i++) p3[i] = 3 * p3[i - 1];
     const uint32_t full = (1u << n) - 1u;
     o.rank3.assign(p3[n], 0xFFFFFFFFu);
+    o.ord3.assign(p3[n], 0xFFFFFFFFu);
     std::vector<std::vector<MaskRec>> per_layer(2 * n + 1);
     cos_structure_info &info = o.info;
     info = cos_structure_info{};
@@ -53,6 +54,7 @@ void build_order(int n, HostOrder &o) {
             if (needclose) info.fma_close += nv;
             info.mul_shift += popc(Z);
             cost += (uint64_t)nv * (popc(J) + (needclose ? 1 : 0)) + 4;
+            o.layer_work[layer] += (uint64_t)nv * (popc(J) + (needclose ? 1 : 0));
         }
         MaskRec r;
         r.ab = A | (B << 16);
@@ -68,9 +70,11 @@ void build_order(int n, HostOrder &o) {
         auto &v = per_layer[l];
         std::stable_sort(v.begin(), v.end(), [](const MaskRec &a, const MaskRec &b) { return a.cost > b.cost; });
         uint32_t off = 0;
+        uint32_t ordinal = 0;
         for (auto &r : v) {
             r.off = off;
             o.rank3[r.code] = off;
+            o.ord3[r.code] = ordinal++;
             uint32_t A = r.ab & 0xFFFFu, B = r.ab >> 16;
             off += (uint32_t)(popc(head_set(B, A & ~B)) * popc(A));
         }
@@ -78,6 +82,7 @@ void build_order(int n, HostOrder &o) {
         o.layer_count[l] = (uint32_t)v.size();
         o.layer_slots[l] = off;
         o.max_slots = std::max(o.max_slots, off);
+        o.max_masks = std::max(o.max_masks, (uint32_t)v.size());
         first += (uint32_t)v.size();
         o.masks.insert(o.masks.end(), v.begin(), v.end());
     }
@@ -119,21 +124,25 @@ const OrderTab *device_orders(int device, std::string *err) {
         const HostOrder &o = host_order(n);
         OrderTab &t = tabs[n];
         MaskRec *dm = nullptr;
-        uint32_t *dr = nullptr;
+        uint32_t *dr = nullptr, *dq = nullptr;
         cudaError_t e = cudaMalloc(&dm, o.masks.size() * sizeof(MaskRec));
         if (e == cudaSuccess) e = cudaMalloc(&dr, o.rank3.size() * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&dq, o.ord3.size() * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMemcpy(dm, o.masks.data(), o.masks.size() * sizeof(MaskRec), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(dr, o.rank3.data(), o.rank3.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(dq, o.ord3.data(), o.ord3.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             *err = std::string("structure upload: ") + cudaGetErrorString(e);
             return nullptr;
         }
         t.masks = dm;
         t.rank3 = dr;
+        t.ord3 = dq;
         memcpy(t.layer_first, o.layer_first, sizeof t.layer_first);
         memcpy(t.layer_count, o.layer_count, sizeof t.layer_count);
         memcpy(t.layer_slots, o.layer_slots, sizeof t.layer_slots);
         t.max_slots = o.max_slots;
+        t.max_masks = o.max_masks;
         t.n = n;
     }
     OrderTab *d = nullptr;

@@ -238,3 +238,63 @@ def test_grad_mu_alpha_chain_rule_vs_finite_differences(sym):
                 fdv = (oracle_c(model, *((p, alpha) if which == "mu" else (mu, p)), cfgs, 2)
                        - oracle_c(model, *((m, alpha) if which == "mu" else (mu, m)), cfgs, 2)) / (2 * h)
             assert grad[l] == pytest.approx(fdv, rel=2e-5, abs=1e-7 * max(1.0, abs(fdv))), (which, l, grad[l], fdv)
+
+
+# ------------------------------------------------------------------ checkpointed layers
+
+@pytest.mark.parametrize("n,n_mat,wt,shifts", [(6, 2, 1, True), (6, 3, 1, False), (5, 1, 4, True)])
+def test_grad_checkpointed_matches_kept_layers_and_exact_differences(monkeypatch, n, n_mat, wt, shifts):
+    """With the least-storage checkpoint plan forced (segments re-run from their checkpoints)
+    the gradient is bitwise the one with every layer kept, and matches exact central
+    differences of the __float128 oracle."""
+    mask, store, rec = B.cos_grad_checkpoint_plan(n, 0)
+    assert mask != 0 and rec > 0 and store < B.cos_structure(n).slots   # the forced plan does re-run layers
+    Ms = list(I.random_matrices(900 + 10 * n + n_mat, 11, n_mat, n, 0.9))
+    sigma = list(np.linspace(-0.12, 0.17, n_mat)) if shifts else None
+    gout = np.linspace(0.5, 1.5, 11)
+    monkeypatch.setenv("COS_GRAD_CHECKPOINT", "0")
+    out0, gM0, gs0 = gpu_grad(Ms, n_mat, wt, sigma, gout)
+    monkeypatch.setenv("COS_GRAD_CHECKPOINT", "1")
+    out1, gM1, gs1 = gpu_grad(Ms, n_mat, wt, sigma, gout)
+    assert np.array_equal(out0, out1)
+    assert all(np.array_equal(a, b) for a, b in zip(gM0, gM1))
+    assert np.array_equal(gs0, gs1)
+    for c in (0, 10):
+        assert close(gM1[c], gout[c] * exact_dM(Ms[c], sigma, wt)), c
+        assert close(gs1[c], gout[c] * exact_dsigma(Ms[c], sigma, wt), rel=1e-7), c
+
+
+def test_grad_checkpointed_orders_11_12_bitwise(monkeypatch):
+    """Orders 11 and 12 with the least-storage plans forced: bitwise the gradient with every
+    layer kept (uneven orders in one launch, each order with its own plan)."""
+    orders = [12, 11, 12]
+    n_mat = 2
+    sigma = [0.05, -0.08]
+    Ms = [I.random_matrices(1300 + c, 1, n_mat, n, 0.9)[0] for c, n in enumerate(orders)]
+    gout = np.array([1.0, -0.5, 2.0])
+    monkeypatch.setenv("COS_GRAD_CHECKPOINT", "0")
+    out0, gM0, gs0 = gpu_grad(Ms, n_mat, 1, sigma, gout)
+    monkeypatch.setenv("COS_GRAD_CHECKPOINT", "1")
+    out1, gM1, gs1 = gpu_grad(Ms, n_mat, 1, sigma, gout)
+    assert np.array_equal(out0, out1)
+    assert all(np.array_equal(a, b) for a, b in zip(gM0, gM1))
+    assert np.array_equal(gs0, gs1)
+
+
+def test_det_grad_checkpointed_bitwise(monkeypatch):
+    """Determinant weights (the Alg. 1 reverse sweep) with the least-storage plan forced."""
+    n = 8
+    Ms = I.random_matrices(77, 9, 2, n, 0.9)
+    d_order, d_moff, d_M, order, moff = pack(list(Ms), 2)
+    al = [0.1, -0.04]
+    res = []
+    for mode in ("0", "1"):
+        monkeypatch.setenv("COS_GRAD_CHECKPOINT", mode)
+        out = torch.empty(9, dtype=torch.float64, device="cuda")
+        gM = torch.empty_like(d_M)
+        ga = torch.empty(9, 2, dtype=torch.float64, device="cuda")
+        B.cos_connected_det_matrices_grad(n, d_order, d_moff, al, d_M, torch.ones(9, dtype=torch.float64,
+                                                                                 device="cuda"), out, gM, ga)
+        B.cos_sync_status()
+        res.append((out.cpu().numpy(), gM.cpu().numpy(), ga.cpu().numpy()))
+    assert all(np.array_equal(a, b) for a, b in zip(res[0], res[1]))
