@@ -43,6 +43,9 @@ FP32_FMA_PER_CLK_SM = 128.0
 # FP32 instructions a double-float term needs at least (the Dot2 step: 1 multiply, 3 FMA,
 # 8 additions; the first term of a dot product fewer): the FP32-pipe floor of that mode.
 DF64_FP32_PER_TERM = 11.5
+# FP32 instructions of one term of the mixed mode's compensated loop close (FMA TwoProduct with
+# the cross term, TwoSum, error accumulation).
+MIXED_CLOSE_FP32_PER_TERM = 11.0
 
 
 def measured_hbm_gbs():
@@ -348,13 +351,14 @@ def rooflines(r, counts, t, prec, peaks, clocks):
         r["tflops"] = counts["flops"] / t / 1e12
         r["frac_fp64_peak"] = counts["flops"] / t / peaks.fp64(clocks)
     elif prec == "mixed":
-        ext = counts["flops"] - counts["close_flops"]
-        r["fp64_close_tflops"] = counts["close_flops"] / t / 1e12
-        r["frac_fp64_peak_close"] = counts["close_flops"] / t / peaks.fp64(clocks)
-        r["fp32_ext_tflops"] = ext / t / 1e12
-        r["frac_fp32_peak_ext"] = ext / t / peaks.fp32(clocks)
-        r["binding_roof"] = max((("hbm", r["frac_hbm"]), ("fp64_close", r["frac_fp64_peak_close"]),
-                                 ("fp32_ext", r["frac_fp32_peak_ext"])), key=lambda kv: kv[1])[0]
+        # FP32 instructions the mode needs at least: one FMA per extension term and, per close
+        # term, the compensated step (1 multiply, 2 FMA, 8 additions)
+        ext_fma = (counts["flops"] - counts["close_flops"]) / 2.0
+        fp32_inst = ext_fma + MIXED_CLOSE_FP32_PER_TERM * counts["close_flops"] / 2.0
+        r["fp32_ext_tflops"] = 2.0 * ext_fma / t / 1e12
+        r["frac_fp32_floor"] = fp32_inst / t / peaks.fp32_lane_ops(clocks)
+        r["binding_roof"] = "hbm" if r["frac_hbm"] >= r["frac_fp32_floor"] else "fp32"
+        r["frac_binding_roof"] = max(r["frac_hbm"], r["frac_fp32_floor"])
     else:
         terms = counts["flops"] / 2.0
         r["tflops_equiv"] = counts["flops"] / t / 1e12
@@ -920,7 +924,7 @@ def measure_det(torch, B, flush, peaks, steps):
             r["frac_fp32_floor"] = fl / 2.0 * DF64_FP32_PER_TERM / ts[p] / peaks.fp32_lane_ops(cl[p])
         else:
             s = B.cos_structure(n)
-            r["frac_fp64_peak_close"] = n_cfg * 2 * 2.0 * s.fma_close / ts[p] / peaks.fp64(cl[p])
+            r["frac_hbm"] = n_cfg * 2 * 2.0 * s.states * 4 / ts[p] / 1e9 / peaks.hbm_gbs
         res[f"su2_zeeman_n10_det_{p}"] = r
     # gradient (reverse sweep of the determinant weights): dc/dM and dc/dalpha of every configuration
     gout = torch.ones(n_cfg, dtype=torch.float64, device="cuda")

@@ -49,10 +49,15 @@
 
 namespace cosdp {
 
-// State type -> close-matrix type and conversions from the FP64 inputs (once per batch).
+// State type -> close-matrix type (converted from the FP64 inputs once per batch): FP64 for
+// FP64 states, FP32 pairs for FP32 states (the mixed mode's compensated close) and df64 states.
 template <typename T>
 struct CloseOf {
     using type = double;
+};
+template <>
+struct CloseOf<float> {
+    using type = df64;
 };
 template <>
 struct CloseOf<df64> {
@@ -144,8 +149,8 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 320 || sizeof(T) == 4) ? 2 : 1)
                     fwd_mask_df<SUB>(tab, first + mi, next, ell, n, src, dst1, Ms, Md, lane, ci, nfl, seed0, shifts,
                                      active, lam, cfg, a.out, a.status, a.prefetch, cs, csh);
                 else
-                    fwd_mask<T, SUB, CLOW>(tab, first + mi, next, ell, n, src, dst1, Ms, Md, lane, ci, nfl, sgn, sig,
-                                           shifts, active, lam, cfg, a.out, a.status, a.prefetch, cs, csh);
+                    fwd_mask<T, SUB, CLOW, CT>(tab, first + mi, next, ell, n, src, dst1, Ms, Md, lane, ci, nfl, sgn,
+                                               sig, shifts, active, lam, cfg, a.out, a.status, a.prefetch, cs, csh);
             }
             __syncthreads();
         }

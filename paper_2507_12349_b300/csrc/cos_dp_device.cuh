@@ -97,6 +97,39 @@ __device__ __forceinline__ float narrow_to(float, double x) {
 }
 __device__ __forceinline__ double narrow_to(double, double x) { return x; }
 
+__device__ __forceinline__ double close_value(double a) { return a; }
+__device__ __forceinline__ double close_value(const DotAcc &a) { return widen(a.s) + widen(a.c); }
+
+// Loop-closing accumulators.  FP64 states close in FP64 (one FMA per state).  FP32 states (the
+// mixed mode) close with a compensated FP32 dot product (Ogita, Rump and Oishi, "Accurate sum
+// and dot product", SIAM J. Sci. Comput. 26 (2005), Dot2): the close matrices are split into
+// FP32 pairs hi + lo, each term o (hi + lo) adds its leading product with TwoSum and collects
+// the product's exact error (FMA TwoProduct) and the cross term o lo in a second FP32 sum.  The
+// pair (s, c) is widened exactly and added in FP64 once per mask.  Error of a mask's close:
+// at most gamma_N^2 sum |terms| (N terms, gamma_N = N 2^-24 / (1 - N 2^-24)) plus 2^-47 sum
+// |terms| for the matrices' split and the cross terms, so the cancelling close keeps about 47
+// bits while every operation stays on the FP32 pipe (the mixed mode's FP32 extension states
+// carry 2^-24 relative errors of their own).
+template <typename T>
+struct CloseAcc {
+    using type = double;
+};
+template <>
+struct CloseAcc<float> {
+    using type = DotAcc;
+};
+__device__ __forceinline__ void close_init(double &a) { a = 0.0; }
+__device__ __forceinline__ void close_init(DotAcc &a) { a.s = a.c = 0.0f; }
+__device__ __forceinline__ void close_add(double &acc, double o, double m) { acc = fma(o, m, acc); }
+__device__ __forceinline__ void close_add(DotAcc &acc, float o, df64 m) {
+    const float p = __fmul_rn(o, m.hi);
+    float e = __fmaf_rn(o, m.hi, -p);   // o hi - p exactly
+    e = __fmaf_rn(o, m.lo, e);          // plus the cross term
+    float t;
+    acc.s = two_sum(acc.s, p, t);
+    acc.c = __fadd_rn(acc.c, __fadd_rn(e, t));
+}
+
 // -x by flipping the sign bit (integer pipe; FP64 instructions are the scarce resource).
 __device__ __forceinline__ double neg(double x) {
     return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
@@ -181,11 +214,11 @@ __device__ __forceinline__ void push_target(T *__restrict__ dst1, const TgtInfo 
 }
 
 // One row (mu, h): load its NV endpoint states, accumulate the close, push every extension.
-template <typename T, int NV>
+template <typename T, int NV, typename CM, typename CA>
 __device__ __forceinline__ void do_row(const T *__restrict__ src, T *__restrict__ dst1, const T *__restrict__ Ms,
-                                       const double *__restrict__ Md, const TgtInfo &ti, int nJ, uint32_t J,
+                                       const CM *__restrict__ Md, const TgtInfo &ti, int nJ, uint32_t J,
                                        uint32_t Vrow, uint32_t A, uint32_t off, int h, int hidx, int nA, int n,
-                                       bool needclose, int lane, double &csum) {
+                                       bool needclose, int lane, CA &csum) {
     T o[NV];
     int vs[NV];
     const T *row = src + (size_t)(off + (uint32_t)(hidx * nA)) * kLanes + lane;
@@ -199,7 +232,7 @@ __device__ __forceinline__ void do_row(const T *__restrict__ src, T *__restrict_
     }
     if (needclose) {
 #pragma unroll
-        for (int t = 0; t < NV; ++t) csum = fma(widen(o[t]), Md[vs[t] + h * kLanes], csum);
+        for (int t = 0; t < NV; ++t) close_add(csum, o[t], Md[vs[t] + h * kLanes]);
     }
     const uint32_t hlow = (1u << h) - 1u;
     uint32_t jj = J;
@@ -228,11 +261,11 @@ __device__ __forceinline__ void do_row(const T *__restrict__ src, T *__restrict_
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void row_dispatch(int nv, const T *src, T *dst1, const T *Ms, const double *Md,
+template <typename T, typename CM, typename CA>
+__device__ __forceinline__ void row_dispatch(int nv, const T *src, T *dst1, const T *Ms, const CM *Md,
                                              const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow, uint32_t A,
                                              uint32_t off, int h, int hidx, int nA, int n, bool needclose, int lane,
-                                             double &csum) {
+                                             CA &csum) {
 #define COS_ROW(K)                                                                                            \
     case K:                                                                                                   \
         do_row<T, K>(src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, csum);       \
@@ -264,9 +297,9 @@ __device__ __forceinline__ void row_dispatch(int nv, const T *src, T *dst1, cons
 // CLOW: determinant weights without cycle factors (Alg. 1, see cos_dp.cu): lanes are the two
 // spin blocks, the first loop never steps onto vertex 0, its close opens the next loop in the
 // spin-down block only, and the sink takes no 2^(n-1).
-template <typename T, bool SUBSETS = false, bool CLOW = false>
+template <typename T, bool SUBSETS = false, bool CLOW = false, typename CM = double>
 __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
-                                         int n, const T *src, T *dst1, const T *Ms, const double *Md, int lane,
+                                         int n, const T *src, T *dst1, const T *Ms, const CM *Md, int lane,
                                          int ci, int nfl, double sgn, double sig, bool shifts, bool active, int lam,
                                          int cfg, double *out, int *status, int prefetch, double *csub = nullptr,
                                          int cshift = 0) {
@@ -289,7 +322,8 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
         const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
         prefetch_block(src, nk.z, (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane, prefetch);
     }
-    double csum = 0.0;
+    typename CloseAcc<T>::type csum;
+    close_init(csum);
     const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, lane);
     const int nJ = __popc(J);
     for (uint32_t hh = H; hh; hh &= hh - 1u) {
@@ -302,7 +336,7 @@ __device__ __forceinline__ void fwd_mask(const OrderTab &tab, uint32_t mask_inde
     if (!needclose) return;  // disconnected continuation: dropped
     // Flavor sum of the loop-closing weight over the lanes of this configuration; the loop
     // factor sgn * w is already inside Md (the close's copy of the matrices).
-    const double C = flavor_sum(csum, nfl, ci);
+    const double C = flavor_sum(close_value(csum), nfl, ci);
     if (SUBSETS && ones == 0u) {
         if (active && lam == 0) csub[(int64_t)B << cshift] = CLOW ? C : ldexp(C, __popc(B) - 1);
         if (dead) return;

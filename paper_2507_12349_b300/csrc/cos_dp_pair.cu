@@ -6,11 +6,11 @@
 // (the .x and .y components of a float2 state), so each index computation, shared-memory
 // address and branch serves two configurations: a batch holds 2 x floor(32 / n_flavors)
 // configurations.  The arithmetic per configuration is that of dp_forward_kernel<float>:
-// FP32 extension states and accumulation, the FP64 close on exactly widened states, seeds
-// rounded to FP32, flavor sums in FP64 (one butterfly per component, identical bits in every
-// lane of a configuration), and the sink in FP64.  Layout: states [slot][lane] as float2 (8
-// bytes, as FP64), extension matrices [v][j][lane] as float2, close matrices (times sgn w)
-// as double2.
+// FP32 extension states and accumulation, the compensated FP32-pair close (widened and added
+// in FP64 once per mask), seeds rounded to FP32, flavor sums in FP64 (one butterfly per
+// component, identical bits in every lane of a configuration), and the sink in FP64.  Layout
+// (P configurations per lane): states [slot][lane] as P floats, extension matrices
+// [v][j][lane] as P floats, close matrices (times sgn w) as P FP32 pairs.
 //
 // The double-float mode (FP32 pairs) is issue-bound for the same reason and gets the same
 // treatment: df64x2 states (two df64 values, 16 bytes per lane), compensated accumulation
@@ -24,14 +24,15 @@ namespace cosdp {
 
 namespace {
 
-// P floats / doubles of one lane (one per configuration), aligned for single vector accesses.
+// P floats of one lane (one per configuration), aligned for single vector accesses; the close
+// matrices as P FP32 pairs hi + lo (the compensated close of cos_dp_device.cuh).
 template <int P>
 struct __align__(4 * P) FV {
     float v[P];
 };
 template <int P>
-struct __align__(16) DV {
-    double v[P];
+struct __align__(16) CV {
+    float hi[P], lo[P];
 };
 
 // Configurations per lane of the mixed kernel.
@@ -49,10 +50,10 @@ __device__ __forceinline__ void push_target_pair(FV<P> *__restrict__ dst1, const
 
 template <int P, int NV>
 __device__ __forceinline__ void do_row_pair(const FV<P> *__restrict__ src, FV<P> *__restrict__ dst1,
-                                            const FV<P> *__restrict__ Ms, const DV<P> *__restrict__ Md,
+                                            const FV<P> *__restrict__ Ms, const CV<P> *__restrict__ Md,
                                             const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow, uint32_t A,
                                             uint32_t off, int h, int hidx, int nA, int n, bool needclose, int lane,
-                                            DV<P> &csum) {
+                                            DotAcc (&csum)[P]) {
     FV<P> o[NV];
     int vs[NV];
     const FV<P> *row = src + (size_t)(off + (uint32_t)(hidx * nA)) * kLanes + lane;
@@ -67,9 +68,9 @@ __device__ __forceinline__ void do_row_pair(const FV<P> *__restrict__ src, FV<P>
     if (needclose) {
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
-            const DV<P> m = Md[vs[t] + h * kLanes];
+            const CV<P> m = Md[vs[t] + h * kLanes];
 #pragma unroll
-            for (int c = 0; c < P; ++c) csum.v[c] = fma(widen(o[t].v[c]), m.v[c], csum.v[c]);
+            for (int c = 0; c < P; ++c) close_add(csum[c], o[t].v[c], df64{m.hi[c], m.lo[c]});
         }
     }
     const uint32_t hlow = (1u << h) - 1u;
@@ -113,9 +114,9 @@ __device__ __forceinline__ void do_row_pair(const FV<P> *__restrict__ src, FV<P>
 
 template <int P>
 __device__ __forceinline__ void row_dispatch_pair(int nv, const FV<P> *src, FV<P> *dst1, const FV<P> *Ms,
-                                                  const DV<P> *Md, const TgtInfo &ti, int nJ, uint32_t J,
+                                                  const CV<P> *Md, const TgtInfo &ti, int nJ, uint32_t J,
                                                   uint32_t Vrow, uint32_t A, uint32_t off, int h, int hidx, int nA,
-                                                  int n, bool needclose, int lane, DV<P> &csum) {
+                                                  int n, bool needclose, int lane, DotAcc (&csum)[P]) {
 #define COS_ROW_P(K)                                                                                           \
     case K:                                                                                                    \
         do_row_pair<P, K>(src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, csum);  \
@@ -144,7 +145,7 @@ __device__ __forceinline__ void row_dispatch_pair(int nv, const FV<P> *src, FV<P
 template <int P, bool CLOW>
 __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask_index, uint32_t next_index, int ell,
                                               int n, const FV<P> *src, FV<P> *dst1, const FV<P> *Ms,
-                                              const DV<P> *Md, int lane, int ci, int nfl, double sgn, double sig,
+                                              const CV<P> *Md, int lane, int ci, int nfl, double sgn, double sig,
                                               bool shifts, const bool act[P], const int cfg[P], int lam, double *out,
                                               int *status, int prefetch) {
     const uint32_t full = (1u << n) - 1u;
@@ -163,9 +164,9 @@ __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask
         prefetch_block(reinterpret_cast<const double *>(src), (uint32_t)(P / 2) * nk.z, (uint32_t)(P / 2) * ns, lane,
                        prefetch);
     }
-    DV<P> csum;
+    DotAcc csum[P];
 #pragma unroll
-    for (int c = 0; c < P; ++c) csum.v[c] = 0.0;
+    for (int c = 0; c < P; ++c) close_init(csum[c]);
     const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, lane);
     const int nJ = __popc(J);
     for (uint32_t hh = H; hh; hh &= hh - 1u) {
@@ -178,7 +179,7 @@ __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask
     if (!needclose) return;   // no half-visited vertex and not full: disconnected, dropped
     double C[P];
 #pragma unroll
-    for (int c = 0; c < P; ++c) C[c] = flavor_sum(csum.v[c], nfl, ci);
+    for (int c = 0; c < P; ++c) C[c] = flavor_sum(close_value(csum[c]), nfl, ci);
     if (ones) {
         const int k = __ffs(ones) - 1;
         const uint32_t bk = 1u << k;
@@ -406,7 +407,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_kernel(cons
     const int nwarps = blockDim.x >> 5;
     const int nsm = a.smem_n * a.smem_n * kLanes;
     FV<P> *Ms = reinterpret_cast<FV<P> *>(smem_p);
-    DV<P> *Md = reinterpret_cast<DV<P> *>(smem_p + (((size_t)nsm * sizeof(FV<P>) + 15) & ~size_t(15)));
+    CV<P> *Md = reinterpret_cast<CV<P> *>(smem_p + (((size_t)nsm * sizeof(FV<P>) + 15) & ~size_t(15)));
     FV<P> *ring = reinterpret_cast<FV<P> *>(a.scratch) + (size_t)blockIdx.x * a.nslots * a.slot_elems;
     const int nfl = a.nf_lanes;
     const int lam = lane % nfl;
@@ -442,13 +443,16 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_kernel(cons
             const int v = e / n, j = e % n;
             const bool sh = v == j && (CLOW || (j != 0 && shifts));
             FV<P> m;
-            DV<P> d;
+            CV<P> d;
 #pragma unroll
             for (int c = 0; c < P; ++c) {
                 double val = act[c] ? Mp[c][e] : 0.0;
                 if (a.absmode) val = fabs(val);
                 m.v[c] = (float)(sh ? val + dshift : val);
-                d.v[c] = cfac * ((CLOW && sh) ? val + dshift : val);   // CLOW: shifted diagonal in the close too
+                // CLOW: shifted diagonal in the close too
+                const df64 md = df64_from(cfac * ((CLOW && sh) ? val + dshift : val));
+                d.hi[c] = md.hi;
+                d.lo[c] = md.lo;
             }
             Ms[e * kLanes + lane] = m;
             Md[e * kLanes + lane] = d;
@@ -569,7 +573,7 @@ static auto pair_kernel_for(int precision, int threads, bool clow = false) {
 size_t pair_smem_bytes(int precision, int n_max) {
     const size_t msm = (size_t)n_max * n_max * kLanes;
     if (precision == COS_DF64) return 2 * msm * sizeof(df64x2);
-    return ((msm * sizeof(FV<kMixedWidth>) + 15) & ~size_t(15)) + msm * sizeof(DV<kMixedWidth>);
+    return ((msm * sizeof(FV<kMixedWidth>) + 15) & ~size_t(15)) + msm * sizeof(CV<kMixedWidth>);
 }
 
 size_t pair_state_bytes(int precision) { return precision == COS_DF64 ? sizeof(df64x2) : sizeof(FV<kMixedWidth>); }

@@ -6,7 +6,9 @@ Tolerances
     arbitrary inputs the bound is stated against the absolute mass (sum of |term|
     bound, the same DP on |M|): |err| <= 2^-53 * 64 n * mass, a few ulps per
     visited point of every term.
-  * DP, mixed: |err| <= (2n + log2(32 n)) * 2^-24 * mass (FP32 extension, FP64 close).
+  * DP, mixed: |err| <= (2n + log2(32 n)) * 2^-24 * mass (FP32 extension; the loop closes
+    are compensated FP32-pair dot products, each within gamma_N^2 + 2^-47 of its sum of |terms|
+    for N <= n^2 terms, below 1e-9 of the mass at n = 12, which the 2^-24 terms dominate).
   * DP, df64 (FP32 pairs, compensated dot products): |err| <= (16 n^2 + 64 n) * 2^-48 * mass.
     Per dot product of K <= n terms: the matrices' df64 split (2^-48 relative), the FP32
     error accumulator c (of size <= 3K 2^-24 sum|terms|) rounded K times (3K 2^-48), and the
