@@ -97,8 +97,8 @@ template <bool SG, int NJ>
 __device__ __forceinline__ double adj_endpoint(double *st, const double *__restrict__ a1,
                                                const double *__restrict__ Ms, const double *__restrict__ Mc,
                                                double *__restrict__ dM, const TgtInfo &ti, uint32_t J, int v,
-                                               uint32_t slot, int qv, int h, int n, double cbar, double gamma,
-                                               int lane, double &gs) {
+                                               uint32_t slot, int qv, int h, int n, bool live, double cbar,
+                                               double gamma, int lane, double &gs) {
     constexpr int kSplit = 6;   // at most 6 extensions' operands in registers at a time
     // the forward state O(mu,h,v), replaced by its adjoint below (same slot, same thread)
     const double o = st[(size_t)slot * kLanes + lane];
@@ -115,9 +115,13 @@ __device__ __forceinline__ double adj_endpoint(double *st, const double *__restr
         adj_chunk<kSplit, NJ>(a1, Ms, dM, ti, jr, hlow, vrow, o, lane, ob, qv, dv);
     }
     if (SG && qv >= 0) gs = fma(neg(dv), o, gs);   // sgn = -1
-    const int vh = vrow + h * kLanes;
-    ob = fma(cbar, Mc[vh], ob);
-    if ((__double_as_longlong(cbar) << 1) != 0) dM[vh] = fma(gamma, o, dM[vh]);
+    // the close (a mask with a half-visited vertex, or the full mask); a dead mask closes into
+    // nothing (warp-uniform test: no FP64 compare on the scarce pipe)
+    if (live) {
+        const int vh = vrow + h * kLanes;
+        ob = fma(cbar, Mc[vh], ob);
+        dM[vh] = fma(gamma, o, dM[vh]);
+    }
     st[(size_t)slot * kLanes + lane] = ob;
     return ob;
 }
@@ -126,12 +130,13 @@ __device__ __forceinline__ double adj_endpoint(double *st, const double *__restr
 template <bool SG, int MAXNJ>
 __device__ __forceinline__ double adj_endpoint_dispatch(int nJ, double *st, const double *a1, const double *Ms,
                                                         const double *Mc, double *dM, const TgtInfo &ti, uint32_t J,
-                                                        int v, uint32_t slot, int qv, int h, int n, double cbar,
-                                                        double gamma, int lane, double &gs) {
+                                                        int v, uint32_t slot, int qv, int h, int n, bool live,
+                                                        double cbar, double gamma, int lane, double &gs) {
 #define COS_AEP(K)                                                                                             \
     case K:                                                                                                    \
         if constexpr (K <= MAXNJ)                                                                              \
-            return adj_endpoint<SG, K>(st, a1, Ms, Mc, dM, ti, J, v, slot, qv, h, n, cbar, gamma, lane, gs);   \
+            return adj_endpoint<SG, K>(st, a1, Ms, Mc, dM, ti, J, v, slot, qv, h, n, live, cbar, gamma, lane,   \
+                                       gs);                                                                    \
         break;
     switch (nJ) {
         COS_AEP(0)
@@ -283,10 +288,11 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
                 const double *cin = cplane + (size_t)(ell & 1) * a.plane_elems;   // Cbar of this layer's masks
                 double *cout = cplane + (size_t)((ell - 1) & 1) * a.plane_elems;  // Cbar of the layer below
                 const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
-                for (uint32_t mi = 0; mi < cnt && own; ++mi) {
+                int turn = 2 % nwarps;   // (mi + 2) mod warps, kept by increments
+                for (uint32_t mi = 0; mi < cnt && own; ++mi, turn = (turn + 1 == nwarps) ? 0 : turn + 1) {
                     const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + first + mi));
                     // the warps take turns to pull a later mask's forward states into L2 ahead of use
-                    if (mi + 2 < cnt && (int)((mi + 2) % nwarps) == warp) {
+                    if (mi + 2 < cnt && turn == warp) {
                         const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + first + mi + 2));
                         const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
                         prefetch_block(st, nk.z, (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_)), lane,
@@ -301,6 +307,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
                     const int nA = __popc(A);
                     const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, lane);
                     const int nJ = __popc(J);
+                    const bool live = (ones != 0u) || (B == full);
                     double cbar = 0.0;
                     if (B == full) {
                         cbar = CLOW ? gout : ldexp(gout, n - 1);
@@ -326,7 +333,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
                             const int qv =
                                 (SG && !CLOW && v != 0 && (ones & (1u << v))) ? __popc(J & ((1u << v) - 1u)) : -1;
                             const double ob = adj_endpoint_dispatch<SG, (MAXT <= 320 ? 10 : 12)>(
-                                nJ, st, a1, Ms, Mc, dM, ti, J, v, slot, qv, h, n, cbar, gamma, lane, gs);
+                                nJ, st, a1, Ms, Mc, dM, ti, J, v, slot, qv, h, n, live, cbar, gamma, lane, gs);
                             if (v == h && ((B >> h) & 1u)) {
                                 // (mu, h, h) with h full is the seed slot of mu - e_h's close (the loop
                                 // opened at h and has not moved): its flavor sum is that mask's Cbar
