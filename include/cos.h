@@ -212,31 +212,6 @@ cos_status cos_connected_sum_batch(const cos_tables *tables, int n_cfg, int n_ma
                                    cos_precision precision, double *d_out,
                                    double *d_abs_mass, cos_stream_t stream);
 
-/* ------------------------------------------------------------------ all subsets
- * Connected sums of every vertex subset (Methods A: the subset recursion between the sum over
- * all decorated covers a(S) and the sum over connected ones c(S)).  One configuration of n
- * vertices then yields every lower order, as a CDet evaluation does.
- *   d_c  [n_cfg][2^n_max]  c(S) at index c * 2^n_max + S, bit i of S = vertex i.
- *        c(empty) = 0, and sets holding a vertex >= the configuration's order are 0.
- *        all_roots = 1: every nonempty S.  The merged DP of Results A rooted at vertex m on the
- *          trailing principal submatrices M^l[m.., m..] gives c(S) for every S whose smallest
- *          vertex is m (from the closes of the masks with no half-visited vertex); all roots of
- *          all configurations run as one batch of derived problems, about 1.5 times the work
- *          of the order-n DP at n = 10.
- *        all_roots = 0: only the sets containing vertex 0, a by-product of the order-n DP
- *          (which then also closes the masks it otherwise drops); the other entries are NaN.
- *   d_a  NULL, or [n_cfg][2^n_max] receiving a(S) = sum_{T subset of S, min S in T}
- *        c(T) a(S \ T), a(empty) = 1, evaluated in FP64 on the GPU; needs all_roots = 1.
- * Other arguments as cos_connected_sum_matrices (precision applies to the DP; the recursion
- * for a is FP64).  Workspace: besides the DP's, all_roots = 1 holds n_cfg * n_max derived
- * problems and their submatrices (n_mat * n_max (n_max + 1) (2 n_max + 1) / 6 doubles per
- * configuration).  A device-detected order error is reported as for the other entry points;
- * the outputs of that call are then undefined. */
-cos_status cos_connected_sum_subsets(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
-                                     int n_mat, int loop_weight, const double *h_sigma, const double *d_M,
-                                     cos_precision precision, int all_roots, double *d_c, double *d_a,
-                                     cos_stream_t stream);
-
 /* ------------------------------------------------------------------ bipartite lattices
  * Connected sums summed over every sublattice assignment of the vertices (Methods A,
  * bipartite lattices, strategy (i)) by the sublattice-resolved merged DP (Results A; Alg. 1-2):
@@ -260,211 +235,132 @@ cos_status cos_gather_bipartite(const cos_tables *tables, int n_cfg, const int32
                                 const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
                                 const int64_t *d_moff, double *d_M4, cos_stream_t stream);
 
-/* Bipartite connected sums of explicit matrices: d_M4 as written by cos_gather_bipartite
- * (blocks [n_mat][2 n_c][2 n_c] at d_moff[c]); h_sigma2 = NULL or host [n_mat][2] shift weights
- * per (flavor, sublattice).  n_max <= COS_BIP_NMAX; precision COS_FP64, COS_MIXED (FP32
- * extension, FP64 close, as on the square lattice) or COS_DF64.  Other arguments, outputs and errors as
- * cos_connected_sum_matrices (d_abs_mass: the same DP on |M4|, |sigma| with all signs +). */
-cos_status cos_connected_sum_bipartite_matrices(int n_cfg, int n_max, const int32_t *d_order,
-                                                const int64_t *d_moff, int n_mat, int loop_weight,
-                                                const double *h_sigma2, const double *d_M4,
-                                                cos_precision precision, double *d_out,
-                                                double *d_abs_mass, cos_stream_t stream);
-
-/* Gradient of the bipartite sums by the reverse sweep (the forward sweep re-run with every
- * layer kept, then walked backwards): d_gout[c] = dLoss/dc; d_out NULL or receives c;
- * d_gM4 NULL or dLoss/dM4 (layout and offsets of d_M4); d_gsigma2 NULL or [n_cfg][n_mat][2]
- * dLoss/dsigma_{l,s} (also at sigma = 0).  n_max <= COS_BIP_NMAX (up to 8 the dLoss/dM4
- * accumulators sit in shared memory beside the two matrix copies, at 9 in the workspace:
- * 4 (2 n_max)^2 x 32 doubles per CTA more); FP64.  Other arguments as
- * cos_connected_sum_bipartite_matrices. */
-cos_status cos_connected_sum_bipartite_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
-                                                     const int64_t *d_moff, int n_mat, int loop_weight,
-                                                     const double *h_sigma2, const double *d_M4, const double *d_gout,
-                                                     double *d_out, double *d_gM4, double *d_gsigma2,
-                                                     cos_stream_t stream);
-
-/* Gather + bipartite DP from vertex coordinates (honeycomb tables; the loop weight is
- * n_flavors for symmetric tables, else 1). */
-cos_status cos_connected_sum_bipartite_batch(const cos_tables *tables, int n_cfg, int n_max,
-                                             const int32_t *d_order, const int64_t *d_offset,
-                                             const int32_t *d_site, const double *d_tau,
-                                             cos_precision precision, double *d_out,
-                                             double *d_abs_mass, cos_stream_t stream);
-
-/* Every vertex subset on a bipartite lattice (the all-subsets mode of
- * cos_connected_sum_subsets on the sublattice-resolved sweep): d_c[c * 2^n_max + S] = c(S),
- * the connected sum of the sub-configuration S summed over its sublattice assignments (the
- * close of a mask with every vertex of S fully visited and no half-visited vertex, Methods A
- * and Alg. 1-2), and with d_a, a(S) by the subset exponential.  Layout of d_M4 / h_sigma2 as
- * cos_connected_sum_bipartite_matrices; all_roots, layout of d_c / d_a, workspace and errors
- * as cos_connected_sum_subsets; n_max <= COS_BIP_NMAX; COS_FP64 only (COS_ERR_UNIMPLEMENTED
- * for the other precisions). */
-cos_status cos_connected_sum_bipartite_subsets(int n_cfg, int n_max, const int32_t *d_order,
-                                               const int64_t *d_moff, int n_mat, int loop_weight,
-                                               const double *h_sigma2, const double *d_M4,
-                                               cos_precision precision, int all_roots, double *d_c,
-                                               double *d_a, cos_stream_t stream);
-
-/* ------------------------------------------------------------------ SU(2) determinant weights
- * Connected sums of an SU(2) model whose diagrams are weighted by determinants (the
- * interaction (n_up - alpha_up)(n_dn - alpha_dn), Methods A): the sum of all diagrams of a
- * vertex set S is a(S) = det(A_up[S]) det(A_dn[S]) (summed over sublattice assignments on a
- * bipartite lattice), A_b = M_b - diag(alpha_b), and the output is its connected part c(V)
- * (the subset subtraction of Methods A).  Computed by the DP without cycle factors of Results
- * A and Alg. 1: only the interaction mask is tracked, nonphysical clow sequences are kept and
- * cancel, and every vertex has a spin-up point (block 0) and a spin-down point (block 1).
- * For alpha = 0 the CoS sum of the same matrices with n_mat = 2, loop_weight = 1 is 2^n c(V).
+/* ------------------------------------------------------------------ one call per operation
+ * Every connected sum this library computes is described by a cos_problem: the lattice, the
+ * weight of a diagram, the precision, and the input -- vertex coordinates with tables, or
+ * explicit matrices.  cos_forward, cos_grad and cos_subsets take it.  cos_connected_sum_matrices,
+ * cos_connected_sum_batch and cos_connected_sum_grad are the square-lattice, loop-weight
+ * cases of cos_forward / cos_grad under their own names.
  *
- * Square lattice: d_M holds per configuration the two blocks [2][n_c][n_c] (spin up, spin
- * down) at d_moff[c], as written by cos_gather for two-flavor tables; h_alpha = NULL or
- * host [2] diagonal shifts.  Precision COS_FP64, COS_MIXED (FP32 extension, FP64 close) or
- * COS_DF64.  d_abs_mass: NULL, or the same DP on |M| with |alpha| added to the diagonal and
- * every sign + (an upper bound on the sum of |terms| of the DP, nonphysical clows included).
- * Other arguments and errors as cos_connected_sum_matrices. */
-cos_status cos_connected_det_matrices(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
-                                      const double *h_alpha, const double *d_M, cos_precision precision,
-                                      double *d_out, double *d_abs_mass, cos_stream_t stream);
+ * lattice
+ *   COS_SQUARE     one site per vertex; matrices [n_mat][n_c][n_c] per configuration (the
+ *                  layout of cos_gather).
+ *   COS_BIPARTITE  the connected sum summed over every sublattice assignment of the vertices
+ *                  (Methods A, bipartite lattices, strategy (i)) by the sublattice-resolved
+ *                  merged DP (Results A; Alg. 1-2): the interaction mask keeps the sublattice of
+ *                  each half-visited vertex, so the 2^n assignments share one sweep.  Matrices
+ *                  [n_mat][2 n_c][2 n_c] per configuration (the layout of cos_gather_bipartite);
+ *                  orders up to COS_BIP_NMAX.
+ * weights
+ *   COS_LOOPS         CoS: -1 and a flavor weight per closed loop (Alg. 2-3 merged, Results A):
+ *                     the flavor sum over the n_mat matrices times loop_weight (N_f for one
+ *                     symmetric matrix).  Shift weights h_shift: square NULL or [n_mat] sigma_l;
+ *                     bipartite NULL or [n_mat][2] sigma_{l,s} (flavor, sublattice).
+ *   COS_DETERMINANTS  SU(2) with determinant weights (the interaction (n_up - alpha_up)
+ *                     (n_dn - alpha_dn), Methods A): the sum of all diagrams of a vertex set S is
+ *                     a(S) = det(A_up[S]) det(A_dn[S]) (summed over sublattice assignments on a
+ *                     bipartite lattice), A_b = M_b - diag(alpha_b), and the output is its
+ *                     connected part c(V) (the subset subtraction of Methods A), computed by the
+ *                     DP without cycle factors of Results A and Alg. 1 (interaction masks only,
+ *                     nonphysical clow sequences kept, they cancel).  Two matrices per
+ *                     configuration, spin up then spin down (n_mat and loop_weight are not read);
+ *                     h_shift: square NULL or [2] alpha_b, bipartite NULL or [2][2] alpha_{b,s}.
+ *                     For alpha = 0 the COS_LOOPS sum of the same matrices with n_mat = 2 and
+ *                     loop_weight = 1 is 2^n c(V).
+ * input
+ *   tables != NULL  vertex coordinates d_offset, d_site, d_tau (as cos_gather); the matrices are
+ *                   gathered into the library's workspace.  Loop weights take n_mat, the loop
+ *                   weight and the shift weights from the tables (h_shift must be NULL);
+ *                   determinant weights need two-flavor tables built with alpha = 0 (tables
+ *                   collapsed to one matrix for equal chemical potentials serve both spins) and
+ *                   take their diagonal shifts from h_shift.  Square-lattice tables of
+ *                   cos_build_propagators for COS_SQUARE, honeycomb tables for COS_BIPARTITE.
+ *   tables == NULL  explicit matrices d_M at d_moff[c] (in doubles), n_mat and loop_weight as
+ *                   above.
+ * precision: COS_FP64, COS_MIXED (FP32 extension, compensated loop closes) or COS_DF64 for
+ *   cos_forward; COS_FP64 for cos_grad and cos_subsets (COS_ERR_UNIMPLEMENTED otherwise).
+ * Orders must lie in [1, n_max], n_max <= COS_NMAX (COS_BIP_NMAX on the bipartite lattice).
+ * Errors: invalid descriptors return COS_ERR_ARG / COS_ERR_ORDER synchronously; device-detected
+ * errors land in the stream's status word (cos_sync_status). */
+typedef enum { COS_SQUARE = 0, COS_BIPARTITE = 1 } cos_lattice;
+typedef enum { COS_LOOPS = 0, COS_DETERMINANTS = 1 } cos_weights;
 
-/* Gather + determinant-weight sweep from vertex coordinates: SU(2) tables of
- * cos_build_propagators (two flavors: spin up, spin down; tables collapsed to one matrix for
- * equal chemical potentials serve both blocks), built with alpha = 0 (the diagonal shifts of
- * determinant weights are h_alpha, not the tables' dispersion shift).  Other arguments as
- * cos_connected_sum_batch and cos_connected_det_matrices; COS_ERR_ARG for tables with another
- * flavor count. */
-cos_status cos_connected_det_batch(const cos_tables *tables, int n_cfg, int n_max, const int32_t *d_order,
-                                   const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
-                                   const double *h_alpha, cos_precision precision, double *d_out,
-                                   double *d_abs_mass, cos_stream_t stream);
+typedef struct {
+    cos_lattice lattice;
+    cos_weights weights;
+    cos_precision precision;
+    int n_cfg;                  /* configurations (0 allowed) */
+    int n_max;                  /* largest order present */
+    const int32_t *d_order;     /* [n_cfg] orders n_c */
+    const cos_tables *tables;   /* coordinates form: the tables, else NULL */
+    const int64_t *d_offset;    /* coordinates form: first vertex of each configuration */
+    const int32_t *d_site;      /* coordinates form: site (unit cell) of every vertex */
+    const double *d_tau;        /* coordinates form: imaginary time of every vertex */
+    const int64_t *d_moff;      /* matrices form: offset of each configuration's matrices */
+    const double *d_M;          /* matrices form: the matrices */
+    int n_mat;                  /* matrices form, COS_LOOPS: matrices per configuration */
+    int loop_weight;            /* matrices form, COS_LOOPS: weight of a loop beyond the flavor sum */
+    const double *h_shift;      /* host shift weights (see weights), NULL = none */
+} cos_problem;
 
-/* Gradient of the square-lattice determinant-weight sums by the reverse sweep (the adjoint of
- * Alg. 1 as merged above; the forward sweep is re-run with every layer kept):
- * d_gout[c]  dLoss/dc;  d_out NULL or receives c;  d_gM NULL or dLoss/dM at d_moff[c] as
- * [2][n_c][n_c];  d_galpha NULL or [n_cfg][2] dLoss/dalpha_b (= -trace of dLoss/dM_b).
- * Other arguments as cos_connected_det_matrices; FP64 only. */
-cos_status cos_connected_det_matrices_grad(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
-                                           const double *h_alpha, const double *d_M, const double *d_gout,
-                                           double *d_out, double *d_gM, double *d_galpha, cos_stream_t stream);
+/* Connected sums: d_out[c] = c(V) of configuration c; d_abs_mass NULL, or the same DP on |M|
+ * and |shifts| with every sign + (an upper bound of the sum of |terms|, for error
+ * statements).  Configurations of different orders share one persistent launch. */
+cos_status cos_forward(const cos_problem *p, double *d_out, double *d_abs_mass, cos_stream_t stream);
 
-/* Gradient of the determinant-weight sums from vertex coordinates (the reverse sweep of
- * cos_connected_det_matrices_grad on the gathered blocks, then the chain rule through the
- * tables as cos_connected_sum_grad):
- *   d_gM / d_gmoff  NULL, or dLoss/dM written at d_gmoff[c] as [2][n_c][n_c] (both spin
- *                   blocks, also for collapsed tables, where the blocks are equal);
- *   d_gmu           NULL or [n_cfg][2]: dLoss/dmu_b = sum_ij dLoss/dM^b_ij dM^b_ij/dmu_b; for
- *                   collapsed tables the derivative of the common matrix (the two blocks'
- *                   sum) split evenly over the two spins;
- *   d_galpha        NULL or [n_cfg][2]: dLoss/dalpha_b of the diagonal shifts h_alpha
- *                   (= -trace of dLoss/dM_b).
- * Other arguments as cos_connected_det_batch; FP64 only; builds the dG0/dmu table on first use
- * when d_gmu is given. */
-cos_status cos_connected_det_grad(const cos_tables *tables, int n_cfg, int n_max, const int32_t *d_order,
-                                  const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
-                                  const double *h_alpha, const double *d_gout, double *d_out, double *d_gM,
-                                  const int64_t *d_gmoff, double *d_gmu, double *d_galpha, cos_stream_t stream);
+/* Gradients by the reverse (adjoint) DP -- the adjoint of Alg. 2-3 (loop weights) or Alg. 1
+ * (determinant weights) as merged in Results A; the paper computes no gradients:
+ *   d_gout[c]  dLoss/dc of configuration c (the vector the gradient is contracted with);
+ *   d_out      NULL or receives c;
+ *   d_gM       NULL or dLoss/dM: matrices form at d_moff (d_gmoff must be NULL); coordinates
+ *              form at d_gmoff[c] ([n_mat][n_c][n_c], bipartite [n_mat][2 n_c][2 n_c];
+ *              determinant weights both spin blocks, also for collapsed tables);
+ *   d_gshift   NULL or dLoss/d(h_shift) per configuration: [n_cfg][n_mat] sigma (square
+ *              loops), [n_cfg][n_mat][2] sigma2 (bipartite loops), [n_cfg][2] alpha
+ *              (= -trace of dLoss/dM_b) and [n_cfg][2][2] alpha2 (= minus the sublattice
+ *              traces) for determinant weights; computed also at zero shifts.  Coordinates
+ *              form of loop weights: must be NULL (their shifts come from the tables, see
+ *              d_galpha);
+ *   d_gmu      coordinates form: NULL or [n_cfg][n_flavors] dLoss/dmu_l = sum_ij dLoss/dM^l_ij
+ *              dM^l_ij/dmu_l (the gather's interpolation of a dG/dmu table, built on first
+ *              use, synchronizing the stream); for collapsed tables the common derivative is
+ *              split evenly over the flavors;
+ *   d_galpha   coordinates form of loop weights: NULL or [n_cfg][n_flavors] dLoss/dalpha_l =
+ *              -(that sum) + dLoss/dsigma_l / U (sigma_l = alpha_l / U; on the honeycomb
+ *              lattice the two sublattice shifts (alpha_l +- delta_l) / U); must be NULL for
+ *              determinant weights (their alpha is h_shift).
+ * The forward sweep is re-run with every layer kept and walked backwards (see the checkpoint
+ * plans below for the memory it takes); FP64. */
+cos_status cos_grad(const cos_problem *p, const double *d_gout, double *d_out, double *d_gM,
+                    const int64_t *d_gmoff, double *d_gshift, double *d_gmu, double *d_galpha,
+                    cos_stream_t stream);
 
-/* Every vertex subset (the all-subsets mode of cos_connected_sum_subsets for determinant
- * weights): d_c[c * 2^n_max + S] = c(S), the connected part of det(A_up[S]) det(A_dn[S]) (the
- * close of the Alg. 1 sweep at the mask 2 1_S, rooted at min S); with d_a, a(S) =
- * det(A_up[S]) det(A_dn[S]) by the subset exponential.  Layout, all_roots, workspace and
- * errors as cos_connected_sum_subsets; h_alpha as cos_connected_det_matrices; COS_FP64 only. */
-cos_status cos_connected_det_subsets(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
-                                     const double *h_alpha, const double *d_M, cos_precision precision,
-                                     int all_roots, double *d_c, double *d_a, cos_stream_t stream);
-
-/* Bipartite lattice (Alg. 1 as stated): d_M4 per configuration [2][2 n_c][2 n_c] (spin block,
- * then the layout of cos_gather_bipartite), h_alpha2 = NULL or host [2][2] diagonal shifts per
- * (spin, sublattice); n_max <= COS_BIP_NMAX; precision COS_FP64, COS_MIXED or COS_DF64.  Outputs and
- * errors as cos_connected_sum_bipartite_matrices. */
-cos_status cos_connected_det_bipartite_matrices(int n_cfg, int n_max, const int32_t *d_order,
-                                                const int64_t *d_moff, const double *h_alpha2,
-                                                const double *d_M4, cos_precision precision,
-                                                double *d_out, double *d_abs_mass, cos_stream_t stream);
-
-/* Gradient of the bipartite sums from vertex coordinates (honeycomb tables): gather, the
- * reverse sweep of cos_connected_sum_bipartite_matrices_grad, then the chain rule through
- * the tables (no counterpart in the paper, which computes no gradients):
- *   dc/dmu_l    = sum over (i,s),(j,t) of dc/dM4_l[(i,s)][(j,t)] dG_l^{st}/dmu (the gather's
- *                 interpolation of a dG/dmu table: the same 2 x 2 matrix function with
- *                 f(E) = exp(-E tau)(1 - n_F(E)) replaced by its mu derivative), G depending
- *                 on mu_l - alpha_l;
- *   dc/dalpha_l = -(that sum) + (dc/dsigma_{l,A} + dc/dsigma_{l,B}) / U, sigma_{l,A/B} =
- *                 (alpha_l +- delta_l) / U.
- * For collapsed (symmetric) tables the common derivative is split evenly over the flavors.
- * d_gM4 / d_gmoff: NULL, or dLoss/dM4 written at d_gmoff[c] as [n_mat][2 n_c][2 n_c].
- * d_gmu, d_galpha: NULL or [n_cfg][n_flavors] (per configuration, scaled by d_gout[c]).
- * Builds the dG/dmu table on first use (synchronizing `stream`).  Other arguments, limits
- * and errors as cos_connected_sum_bipartite_batch and
- * cos_connected_sum_bipartite_matrices_grad; FP64. */
-cos_status cos_connected_sum_bipartite_grad(const cos_tables *tables, int n_cfg, int n_max,
-                                            const int32_t *d_order, const int64_t *d_offset,
-                                            const int32_t *d_site, const double *d_tau, const double *d_gout,
-                                            double *d_out, double *d_gM4, const int64_t *d_gmoff,
-                                            double *d_gmu, double *d_galpha, cos_stream_t stream);
-
-/* Gather + bipartite determinant-weight sweep from vertex coordinates: two-flavor (spin up,
- * spin down) honeycomb tables of cos_build_propagators_honeycomb (tables collapsed to one
- * matrix for equal spins serve both blocks); the diagonal shifts of the determinant weights
- * are h_alpha2 (NULL or host [2][2], spin then sublattice), not the tables' shift weights.
- * Other arguments as cos_connected_sum_bipartite_batch and cos_connected_det_bipartite_matrices;
- * COS_ERR_ARG for tables with another flavor count. */
-cos_status cos_connected_det_bipartite_batch(const cos_tables *tables, int n_cfg, int n_max,
-                                             const int32_t *d_order, const int64_t *d_offset,
-                                             const int32_t *d_site, const double *d_tau,
-                                             const double *h_alpha2, cos_precision precision,
-                                             double *d_out, double *d_abs_mass, cos_stream_t stream);
-
-/* Gradient of the bipartite determinant-weight sums (the adjoint of the Alg. 1 sweep):
- * d_galpha2 NULL or [n_cfg][2][2] dLoss/dalpha_{b,s} (= minus the sublattice-s trace of
- * dLoss/dM4_b); other outputs and limits as cos_connected_sum_bipartite_matrices_grad; FP64. */
-cos_status cos_connected_det_bipartite_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
-                                                     const int64_t *d_moff, const double *h_alpha2,
-                                                     const double *d_M4, const double *d_gout, double *d_out,
-                                                     double *d_gM4, double *d_galpha2, cos_stream_t stream);
-
-/* Gradient of the bipartite determinant-weight sums from vertex coordinates (no counterpart
- * in the paper, which computes no gradients): the gather of cos_connected_det_bipartite_batch,
- * the reverse sweep of cos_connected_det_bipartite_matrices_grad, then the chain rule through
- * the honeycomb tables as cos_connected_sum_bipartite_grad:
- *   d_gM4 / d_gmoff  NULL, or dLoss/dM4 written at d_gmoff[c] as [2][2 n_c][2 n_c] (both spin
- *                    blocks, also for collapsed tables, where the blocks are equal);
- *   d_gmu            NULL or [n_cfg][2]: dLoss/dmu_b; for collapsed tables the derivative of
- *                    the common matrix (the blocks' sum) split evenly over the two spins;
- *   d_galpha2        NULL or [n_cfg][2][2]: dLoss/dalpha_{b,s} of the diagonal shifts h_alpha2
- *                    (= minus the sublattice-s trace of dLoss/dM4_b).
- * Builds the dG/dmu table on first use when d_gmu is given (synchronizing `stream`).  Other
- * arguments and errors as cos_connected_det_bipartite_batch; FP64. */
-cos_status cos_connected_det_bipartite_grad(const cos_tables *tables, int n_cfg, int n_max,
-                                            const int32_t *d_order, const int64_t *d_offset,
-                                            const int32_t *d_site, const double *d_tau, const double *h_alpha2,
-                                            const double *d_gout, double *d_out, double *d_gM4,
-                                            const int64_t *d_gmoff, double *d_gmu, double *d_galpha2,
-                                            cos_stream_t stream);
-
-/* Every vertex subset of the bipartite determinant-weight sums: d_c[c * 2^n_max + S] = c(S),
- * the connected part of sum_s det(A_up[S,s]) det(A_dn[S,s]) over the sublattice assignments s
- * of S (the close of the Alg. 1 sweep at the mask with S fully visited), and with d_a, a(S)
- * itself by the subset exponential.  d_M4 / h_alpha2 as cos_connected_det_bipartite_matrices;
- * everything else as cos_connected_sum_bipartite_subsets. */
-cos_status cos_connected_det_bipartite_subsets(int n_cfg, int n_max, const int32_t *d_order,
-                                               const int64_t *d_moff, const double *h_alpha2,
-                                               const double *d_M4, cos_precision precision, int all_roots,
-                                               double *d_c, double *d_a, cos_stream_t stream);
+/* Connected sums of every vertex subset (Methods A: the subset recursion between the sum over
+ * all decorated covers a(S) and the sum over connected ones c(S)).  One configuration of n
+ * vertices then yields every lower order, as a CDet evaluation does.  Matrices form only.
+ *   d_c  [n_cfg][2^n_max]  c(S) at index c * 2^n_max + S, bit i of S = vertex i.
+ *        c(empty) = 0, and sets holding a vertex >= the configuration's order are 0.
+ *        all_roots = 1: every nonempty S.  The merged DP rooted at vertex m on the trailing
+ *          principal submatrices M^l[m.., m..] gives c(S) for every S whose smallest vertex is m
+ *          (from the closes of the masks with no half-visited vertex; on a bipartite lattice
+ *          summed over the sublattice assignments of S, with determinant weights the connected
+ *          part of det(A_up[S]) det(A_dn[S])); all roots of all configurations run as one batch
+ *          of derived problems, about 1.5 times the work of the order-n DP at n = 10.
+ *        all_roots = 0: only the sets containing vertex 0, a by-product of the order-n DP
+ *          (which then also closes the masks it otherwise drops); the other entries are NaN.
+ *   d_a  NULL, or [n_cfg][2^n_max] receiving a(S) = sum_{T subset of S, min S in T}
+ *        c(T) a(S \ T), a(empty) = 1 (with determinant weights det(A_up[S]) det(A_dn[S])),
+ *        evaluated in FP64 on the GPU; needs all_roots = 1.
+ * Precision applies to the DP (square loop weights: any; otherwise COS_FP64); the recursion
+ * for a is FP64.  Workspace: besides the DP's, all_roots = 1 holds n_cfg * n_max derived
+ * problems and their submatrices.  A device-detected order error is reported as for the
+ * other entry points; the outputs of that call are then undefined. */
+cos_status cos_subsets(const cos_problem *p, int all_roots, double *d_c, double *d_a, cos_stream_t stream);
 
 /* ------------------------------------------------------------------ adjoint DP
- * Gradient of the connected sums by the reverse (adjoint) DP: the forward DP is re-run with
- * every layer kept, then walked backwards (the adjoint of Alg. 2-3 as merged in Results A).
- * d_gout[c]   dLoss/dc for configuration c (the vector the gradient is contracted with)
- * d_out       NULL or receives c (as cos_connected_sum_matrices, FP64)
- * d_gM        NULL or receives dLoss/dM, same layout and offsets (d_moff) as d_M
- * d_gsigma    NULL or receives dLoss/dsigma_l per configuration, [n_cfg][n_mat] (computed
- *             also at sigma = 0, where shift transitions carry no weight)
- * Other arguments as cos_connected_sum_matrices.  FP64 only. */
-cos_status cos_connected_sum_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
-                                           const int64_t *d_moff, int n_mat, int loop_weight,
-                                           const double *h_sigma, const double *d_M,
-                                           const double *d_gout, double *d_out, double *d_gM,
-                                           double *d_gsigma, cos_stream_t stream);
+ * cos_connected_sum_grad (the gradient of cos_connected_sum_batch) is cos_grad with a
+ * square-lattice, loop-weight cos_problem in the coordinates form; the descriptor call also
+ * takes explicit matrices, bipartite lattices and determinant weights. */
 
 /* Memory of the gradient calls.  The reverse sweep needs the forward state of every layer;
  * each adjoint overwrites the forward state it was formed from, so the kept layers are the

@@ -29,16 +29,9 @@ STATUS = {0: "COS_OK", -1: "COS_ERR_ARG", -2: "COS_ERR_ORDER", -3: "COS_ERR_CUDA
 EXPORTS = [
     "cos_build_propagators", "cos_free_tables", "cos_get_tables_info", "cos_copy_table", "cos_gather",
     "cos_connected_sum_matrices", "cos_connected_sum_matrices_noalloc", "cos_connected_sum_batch",
-    "cos_connected_sum_subsets",
-    "cos_build_propagators_honeycomb", "cos_gather_bipartite", "cos_connected_sum_bipartite_matrices",
-    "cos_connected_sum_bipartite_batch", "cos_bipartite_structure",
-    "cos_connected_det_matrices", "cos_connected_det_bipartite_matrices", "cos_connected_det_matrices_grad",
-    "cos_connected_det_subsets", "cos_connected_det_batch", "cos_connected_sum_bipartite_matrices_grad",
-    "cos_connected_det_bipartite_matrices_grad", "cos_connected_det_grad", "cos_connected_sum_bipartite_subsets",
-    "cos_connected_det_bipartite_subsets", "cos_connected_det_bipartite_batch", "cos_connected_sum_bipartite_grad",
-    "cos_connected_det_bipartite_grad",
-    "cos_connected_sum_matrices_grad", "cos_connected_sum_grad", "cos_grad_checkpoint_plan", "cos_sync_status",
-    "cos_status_string",
+    "cos_build_propagators_honeycomb", "cos_gather_bipartite", "cos_bipartite_structure",
+    "cos_forward", "cos_grad", "cos_subsets",
+    "cos_connected_sum_grad", "cos_grad_checkpoint_plan", "cos_sync_status", "cos_status_string",
     "cos_last_error", "cos_structure",
     "cos_plan_create_batch", "cos_plan_create_matrices", "cos_plan_launch", "cos_plan_status", "cos_plan_grid",
     "cos_plan_destroy", "cos_set_tuning", "cos_get_tuning", "cos_autotune",
@@ -84,6 +77,21 @@ _lib = None
 TUNING_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_b300.txt")
 
 
+COS_SQUARE, COS_BIPARTITE = 0, 1
+COS_LOOPS, COS_DETERMINANTS = 0, 1
+
+
+class cos_problem(ctypes.Structure):
+    """include/cos.h cos_problem: lattice, weight kind, precision, and the input (vertex
+    coordinates with tables, or explicit matrices)."""
+    _fields_ = [("lattice", ctypes.c_int), ("weights", ctypes.c_int), ("precision", ctypes.c_int),
+                ("n_cfg", ctypes.c_int), ("n_max", ctypes.c_int), ("d_order", ctypes.c_void_p),
+                ("tables", ctypes.c_void_p), ("d_offset", ctypes.c_void_p), ("d_site", ctypes.c_void_p),
+                ("d_tau", ctypes.c_void_p), ("d_moff", ctypes.c_void_p), ("d_M", ctypes.c_void_p),
+                ("n_mat", ctypes.c_int), ("loop_weight", ctypes.c_int),
+                ("h_shift", ctypes.POINTER(ctypes.c_double))]
+
+
 def lib(build: bool = True):
     """Load libcos.so (building it from source first if it is missing or stale)."""
     global _lib
@@ -102,7 +110,13 @@ def lib(build: bool = True):
         L.cos_gather.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
         L.cos_connected_sum_matrices.argtypes = [i32, i32, vp, vp, i32, i32, dptr, vp, i32, vp, vp, vp]
         L.cos_connected_sum_matrices_noalloc.argtypes = [i32, i32, vp, vp, i32, i32, dptr, vp, i32, vp, vp, vp]
-        L.cos_connected_sum_matrices_grad.argtypes = [i32, i32, vp, vp, i32, i32, dptr, vp, vp, vp, vp, vp, vp]
+        pp = ctypes.POINTER(cos_problem)
+        L.cos_forward.argtypes = [pp, vp, vp, vp]
+        L.cos_grad.argtypes = [pp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.cos_subsets.argtypes = [pp, i32, vp, vp, vp]
+        L.cos_build_propagators_honeycomb.argtypes = [ctypes.POINTER(cos_honeycomb_model), vp, ctypes.POINTER(vp)]
+        L.cos_gather_bipartite.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.cos_bipartite_structure.argtypes = [i32, ctypes.POINTER(cos_structure_info)]
         L.cos_connected_sum_grad.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.cos_connected_sum_batch.argtypes = [vp, i32, i32, vp, vp, vp, vp, i32, vp, vp, vp]
         L.cos_sync_status.argtypes = [vp]
@@ -232,183 +246,6 @@ def cos_gather_bipartite(tables: Tables, order, offset, site, tau, moff, M4, str
                                       _stream(stream)), "cos_gather_bipartite")
 
 
-def cos_connected_sum_bipartite_matrices(n_max: int, order, moff, n_mat: int, loop_weight: int, sigma2, M4,
-                                         precision: str, out, abs_mass=None, stream=None):
-    """sigma2: None or n_mat x 2 shift weights (flavor, sublattice)."""
-    sig = None
-    if sigma2 is not None:
-        flat = [float(x) for row in sigma2 for x in row]
-        sig = (ctypes.c_double * len(flat))(*flat)
-    _check(lib().cos_connected_sum_bipartite_matrices(int(order.numel()), int(n_max), _ptr(order, "i32"),
-                                                      _ptr(moff, "i64"), int(n_mat), int(loop_weight), sig,
-                                                      _ptr(M4, "f64"), PRECISIONS[precision], _ptr(out, "f64"),
-                                                      _ptr(abs_mass, "f64"), _stream(stream)),
-           "cos_connected_sum_bipartite_matrices")
-
-
-def cos_connected_det_matrices(n_max: int, order, moff, alpha: Optional[Sequence[float]], M, precision: str, out,
-                               abs_mass=None, stream=None):
-    """SU(2) determinant weights (Alg. 1): M holds [2][n_c][n_c] (spin up, spin down) per
-    configuration at moff; alpha None or the two diagonal shifts."""
-    al = None if alpha is None else (ctypes.c_double * 2)(*[float(x) for x in alpha])
-    _check(lib().cos_connected_det_matrices(int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(moff, "i64"), al,
-                                            _ptr(M, "f64"), PRECISIONS[precision], _ptr(out, "f64"),
-                                            _ptr(abs_mass, "f64"), _stream(stream)), "cos_connected_det_matrices")
-
-
-def cos_connected_det_batch(tables: Tables, n_max: int, order, offset, site, tau, alpha, precision: str, out,
-                            abs_mass=None, stream=None):
-    """Gather + SU(2) determinant-weight sums from vertex coordinates (SU(2) tables built with
-    alpha = 0; alpha: None or the two diagonal shifts)."""
-    al = None if alpha is None else (ctypes.c_double * 2)(*[float(x) for x in alpha])
-    _check(lib().cos_connected_det_batch(tables.handle, int(order.numel()), int(n_max), _ptr(order, "i32"),
-                                         _ptr(offset, "i64"), _ptr(site, "i32"), _ptr(tau, "f64"), al,
-                                         PRECISIONS[precision], _ptr(out, "f64"), _ptr(abs_mass, "f64"),
-                                         _stream(stream)), "cos_connected_det_batch")
-
-
-def cos_connected_det_matrices_grad(n_max: int, order, moff, alpha: Optional[Sequence[float]], M, gout, out=None,
-                                    gM=None, galpha=None, stream=None):
-    """Gradient of the SU(2) determinant-weight sums: dLoss/dM (layout of M) and dLoss/dalpha
-    ([n_cfg][2]) for dLoss/dc = gout."""
-    al = None if alpha is None else (ctypes.c_double * 2)(*[float(x) for x in alpha])
-    _check(lib().cos_connected_det_matrices_grad(int(order.numel()), int(n_max), _ptr(order, "i32"),
-                                                 _ptr(moff, "i64"), al, _ptr(M, "f64"), _ptr(gout, "f64"),
-                                                 _ptr(out, "f64"), _ptr(gM, "f64"), _ptr(galpha, "f64"),
-                                                 _stream(stream)), "cos_connected_det_matrices_grad")
-
-
-def cos_connected_det_grad(tables: Tables, n_max: int, order, offset, site, tau, alpha, gout, out=None, gM=None,
-                           gmoff=None, gmu=None, galpha=None, stream=None):
-    """Gradient of the SU(2) determinant-weight sums from vertex coordinates: dLoss/dM ([2][n_c][n_c]
-    at gmoff), dLoss/dmu and dLoss/dalpha ([n_cfg][2]) for dLoss/dc = gout."""
-    al = None if alpha is None else (ctypes.c_double * 2)(*[float(x) for x in alpha])
-    _check(lib().cos_connected_det_grad(tables.handle, int(order.numel()), int(n_max), _ptr(order, "i32"),
-                                        _ptr(offset, "i64"), _ptr(site, "i32"), _ptr(tau, "f64"), al,
-                                        _ptr(gout, "f64"), _ptr(out, "f64"), _ptr(gM, "f64"), _ptr(gmoff, "i64"),
-                                        _ptr(gmu, "f64"), _ptr(galpha, "f64"), _stream(stream)),
-           "cos_connected_det_grad")
-
-
-def cos_connected_det_subsets(n_max: int, order, moff, alpha: Optional[Sequence[float]], M, c_out, a_out=None,
-                              all_roots: bool = True, stream=None):
-    """c(S) (and a(S) = det(A_up[S]) det(A_dn[S]) when a_out is given) of every vertex subset S for
-    determinant weights: c_out / a_out are [n_cfg * 2^n_max] float64, entry c * 2^n_max + S."""
-    al = None if alpha is None else (ctypes.c_double * 2)(*[float(x) for x in alpha])
-    _check(lib().cos_connected_det_subsets(int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(moff, "i64"), al,
-                                           _ptr(M, "f64"), PRECISIONS["fp64"], int(bool(all_roots)),
-                                           _ptr(c_out, "f64"), _ptr(a_out, "f64"), _stream(stream)),
-           "cos_connected_det_subsets")
-
-
-def cos_connected_sum_bipartite_subsets(n_max: int, order, moff, n_mat: int, loop_weight: int, sigma2, M4, c_out,
-                                        a_out=None, all_roots: bool = True, stream=None):
-    """c(S) (and a(S) when a_out is given) of every vertex subset S on a bipartite lattice: M4
-    holds [n_mat][2 n_c][2 n_c] per configuration at moff; c_out / a_out are [n_cfg * 2^n_max]
-    float64, entry c * 2^n_max + S."""
-    _check(lib().cos_connected_sum_bipartite_subsets(int(order.numel()), int(n_max), _ptr(order, "i32"),
-                                                     _ptr(moff, "i64"), int(n_mat), int(loop_weight),
-                                                     _sig2(sigma2, n_mat), _ptr(M4, "f64"), PRECISIONS["fp64"],
-                                                     int(bool(all_roots)), _ptr(c_out, "f64"), _ptr(a_out, "f64"),
-                                                     _stream(stream)), "cos_connected_sum_bipartite_subsets")
-
-
-def cos_connected_det_bipartite_subsets(n_max: int, order, moff, alpha2, M4, c_out, a_out=None,
-                                        all_roots: bool = True, stream=None):
-    """c(S) (and a(S) when a_out is given) of every vertex subset S for bipartite determinant
-    weights: M4 [2][2 n_c][2 n_c] per configuration; alpha2 None or 2 x 2 (spin, sublattice)."""
-    _check(lib().cos_connected_det_bipartite_subsets(int(order.numel()), int(n_max), _ptr(order, "i32"),
-                                                     _ptr(moff, "i64"), _sig2(alpha2, 2), _ptr(M4, "f64"),
-                                                     PRECISIONS["fp64"], int(bool(all_roots)), _ptr(c_out, "f64"),
-                                                     _ptr(a_out, "f64"), _stream(stream)),
-           "cos_connected_det_bipartite_subsets")
-
-
-def cos_connected_sum_bipartite_grad(tables: Tables, n_max: int, order, offset, site, tau, gout, out=None, gM4=None,
-                                     gmoff=None, gmu=None, galpha=None, stream=None):
-    """Gradient of the bipartite sums from vertex coordinates (honeycomb tables): dLoss/dM4
-    ([n_mat][2 n_c][2 n_c] at gmoff), dLoss/dmu and dLoss/dalpha ([n_cfg][n_flavors])."""
-    _check(lib().cos_connected_sum_bipartite_grad(tables.handle, int(order.numel()), int(n_max), _ptr(order, "i32"),
-                                                  _ptr(offset, "i64"), _ptr(site, "i32"), _ptr(tau, "f64"),
-                                                  _ptr(gout, "f64"), _ptr(out, "f64"), _ptr(gM4, "f64"),
-                                                  _ptr(gmoff, "i64"), _ptr(gmu, "f64"), _ptr(galpha, "f64"),
-                                                  _stream(stream)), "cos_connected_sum_bipartite_grad")
-
-
-def cos_connected_det_bipartite_grad(tables: Tables, n_max: int, order, offset, site, tau, alpha2, gout, out=None,
-                                     gM4=None, gmoff=None, gmu=None, galpha2=None, stream=None):
-    """Gradient of the bipartite determinant-weight sums from vertex coordinates: dLoss/dM4
-    ([2][2 n_c][2 n_c] at gmoff), dLoss/dmu ([n_cfg][2]) and dLoss/dalpha2 ([n_cfg][2][2])."""
-    _check(lib().cos_connected_det_bipartite_grad(tables.handle, int(order.numel()), int(n_max), _ptr(order, "i32"),
-                                                  _ptr(offset, "i64"), _ptr(site, "i32"), _ptr(tau, "f64"),
-                                                  _sig2(alpha2, 2), _ptr(gout, "f64"), _ptr(out, "f64"),
-                                                  _ptr(gM4, "f64"), _ptr(gmoff, "i64"), _ptr(gmu, "f64"),
-                                                  _ptr(galpha2, "f64"), _stream(stream)),
-           "cos_connected_det_bipartite_grad")
-
-
-def cos_connected_det_bipartite_batch(tables: Tables, n_max: int, order, offset, site, tau, alpha2, precision: str,
-                                      out, abs_mass=None, stream=None):
-    """Gather + bipartite determinant-weight sums from vertex coordinates (two-flavor honeycomb
-    tables; alpha2: None or the 2 x 2 diagonal shifts, spin then sublattice)."""
-    _check(lib().cos_connected_det_bipartite_batch(tables.handle, int(order.numel()), int(n_max), _ptr(order, "i32"),
-                                                   _ptr(offset, "i64"), _ptr(site, "i32"), _ptr(tau, "f64"),
-                                                   _sig2(alpha2, 2), PRECISIONS[precision], _ptr(out, "f64"),
-                                                   _ptr(abs_mass, "f64"), _stream(stream)),
-           "cos_connected_det_bipartite_batch")
-
-
-def cos_connected_det_bipartite_matrices(n_max: int, order, moff, alpha2, M4, precision: str, out, abs_mass=None,
-                                         stream=None):
-    """SU(2) determinant weights on a bipartite lattice (Alg. 1): M4 holds [2][2 n_c][2 n_c]
-    per configuration at moff; alpha2 None or 2 x 2 diagonal shifts (spin, sublattice)."""
-    al = None
-    if alpha2 is not None:
-        flat = [float(x) for row in alpha2 for x in row]
-        al = (ctypes.c_double * 4)(*flat)
-    _check(lib().cos_connected_det_bipartite_matrices(int(order.numel()), int(n_max), _ptr(order, "i32"),
-                                                      _ptr(moff, "i64"), al, _ptr(M4, "f64"), PRECISIONS[precision],
-                                                      _ptr(out, "f64"), _ptr(abs_mass, "f64"), _stream(stream)),
-           "cos_connected_det_bipartite_matrices")
-
-
-def _sig2(sigma2, n_mat):
-    if sigma2 is None:
-        return None
-    flat = [float(x) for row in sigma2 for x in row]
-    if len(flat) != 2 * n_mat:
-        raise ValueError("sigma2 / alpha2 must hold n_mat x 2 values")
-    return (ctypes.c_double * len(flat))(*flat)
-
-
-def cos_connected_sum_bipartite_matrices_grad(n_max: int, order, moff, n_mat: int, loop_weight: int, sigma2, M4,
-                                              gout, out=None, gM4=None, gsigma2=None, stream=None):
-    """Gradient of the bipartite sums: dLoss/dM4 (layout of M4) and dLoss/dsigma2 ([n_cfg][n_mat][2])."""
-    _check(lib().cos_connected_sum_bipartite_matrices_grad(int(order.numel()), int(n_max), _ptr(order, "i32"),
-                                                           _ptr(moff, "i64"), int(n_mat), int(loop_weight),
-                                                           _sig2(sigma2, n_mat), _ptr(M4, "f64"), _ptr(gout, "f64"),
-                                                           _ptr(out, "f64"), _ptr(gM4, "f64"), _ptr(gsigma2, "f64"),
-                                                           _stream(stream)), "cos_connected_sum_bipartite_matrices_grad")
-
-
-def cos_connected_det_bipartite_matrices_grad(n_max: int, order, moff, alpha2, M4, gout, out=None, gM4=None,
-                                              galpha2=None, stream=None):
-    """Gradient of the bipartite determinant-weight sums: dLoss/dM4 and dLoss/dalpha2 ([n_cfg][2][2])."""
-    _check(lib().cos_connected_det_bipartite_matrices_grad(int(order.numel()), int(n_max), _ptr(order, "i32"),
-                                                           _ptr(moff, "i64"), _sig2(alpha2, 2), _ptr(M4, "f64"),
-                                                           _ptr(gout, "f64"), _ptr(out, "f64"), _ptr(gM4, "f64"),
-                                                           _ptr(galpha2, "f64"), _stream(stream)),
-           "cos_connected_det_bipartite_matrices_grad")
-
-
-def cos_connected_sum_bipartite_batch(tables: Tables, n_max: int, order, offset, site, tau, precision: str, out,
-                                      abs_mass=None, stream=None):
-    _check(lib().cos_connected_sum_bipartite_batch(tables.handle, int(order.numel()), int(n_max), _ptr(order, "i32"),
-                                                   _ptr(offset, "i64"), _ptr(site, "i32"), _ptr(tau, "f64"),
-                                                   PRECISIONS[precision], _ptr(out, "f64"), _ptr(abs_mass, "f64"),
-                                                   _stream(stream)), "cos_connected_sum_bipartite_batch")
-
-
 def cos_bipartite_structure(n: int) -> cos_structure_info:
     inf = cos_structure_info()
     _check(lib().cos_bipartite_structure(int(n), ctypes.byref(inf)), "cos_bipartite_structure")
@@ -449,20 +286,6 @@ def cos_connected_sum_matrices_noalloc(n_max: int, order, moff, n_mat: int, loop
                                                     _stream(stream)), "cos_connected_sum_matrices_noalloc")
 
 
-def cos_connected_sum_subsets(n_max: int, order, moff, n_mat: int, loop_weight: int,
-                              sigma: Optional[Sequence[float]], M, precision: str, c_out, a_out=None,
-                              all_roots: bool = True, stream=None):
-    """c(S) (and a(S) when a_out is given) of every vertex subset S: c_out / a_out are
-    [n_cfg * 2^n_max] float64, entry c * 2^n_max + S (bit i of S = vertex i)."""
-    sig = None
-    if sigma is not None:
-        sig = (ctypes.c_double * n_mat)(*[float(s) for s in sigma])
-    _check(lib().cos_connected_sum_subsets(int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(moff, "i64"),
-                                           int(n_mat), int(loop_weight), sig, _ptr(M, "f64"), PRECISIONS[precision],
-                                           int(bool(all_roots)), _ptr(c_out, "f64"), _ptr(a_out, "f64"),
-                                           _stream(stream)), "cos_connected_sum_subsets")
-
-
 def cos_connected_sum_batch(tables: Tables, n_max: int, order, offset, site, tau, precision: str, out,
                             abs_mass=None, stream=None):
     _check(lib().cos_connected_sum_batch(tables.handle, int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(offset, "i64"),
@@ -470,22 +293,198 @@ def cos_connected_sum_batch(tables: Tables, n_max: int, order, offset, site, tau
                                          _stream(stream)), "cos_connected_sum_batch")
 
 
-def cos_connected_sum_matrices_grad(n_max: int, order, moff, n_mat: int, loop_weight: int,
-                                    sigma: Optional[Sequence[float]], M, gout, out=None, gM=None, gsigma=None,
-                                    stream=None):
-    sig = None
-    if sigma is not None:
-        sig = (ctypes.c_double * n_mat)(*[float(s) for s in sigma])
-    _check(lib().cos_connected_sum_matrices_grad(int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(moff, "i64"), int(n_mat),
-                                                 int(loop_weight), sig, _ptr(M, "f64"), _ptr(gout, "f64"), _ptr(out, "f64"), _ptr(gM, "f64"),
-                                                 _ptr(gsigma, "f64"), _stream(stream)), "cos_connected_sum_matrices_grad")
-
-
 def cos_connected_sum_grad(tables: Tables, n_max: int, order, offset, site, tau, gout, out=None, gM=None,
                            gmoff=None, gmu=None, galpha=None, stream=None):
     _check(lib().cos_connected_sum_grad(tables.handle, int(order.numel()), int(n_max), _ptr(order, "i32"), _ptr(offset, "i64"),
                                         _ptr(site, "i32"), _ptr(tau, "f64"), _ptr(gout, "f64"), _ptr(out, "f64"), _ptr(gM, "f64"), _ptr(gmoff, "i64"),
                                         _ptr(gmu, "f64"), _ptr(galpha, "f64"), _stream(stream)), "cos_connected_sum_grad")
+
+
+# ------------------------------------------------------------------ cos_problem (one call per operation)
+
+def _shifts(shift, count: int):
+    """Host shift weights as a C array of `count` doubles (or NULL)."""
+    if shift is None:
+        return None
+    flat = [float(x) for x in np.asarray(shift, dtype=np.float64).ravel()]
+    if len(flat) != count:
+        raise ValueError(f"expected {count} shift weights, got {len(flat)}")
+    return (ctypes.c_double * count)(*flat)
+
+
+def problem(lattice: int, weights: int, precision: str, n_max: int, order, tables: Optional["Tables"] = None,
+            offset=None, site=None, tau=None, moff=None, M=None, n_mat: int = 0, loop_weight: int = 0,
+            shift=None) -> cos_problem:
+    """A cos_problem for cos_forward / cos_grad / cos_subsets: vertex coordinates (tables,
+    offset, site, tau) or explicit matrices (moff, M, n_mat, loop_weight); `shift` as the
+    weight kind expects (square loops [n_mat], bipartite loops [n_mat][2], determinant weights
+    [2] or [2][2])."""
+    p = cos_problem()
+    p.lattice, p.weights, p.precision = int(lattice), int(weights), PRECISIONS[precision]
+    p.n_cfg, p.n_max = int(order.numel()), int(n_max)
+    p.d_order = _ptr(order, "i32").value
+    h = tables.handle if tables is not None else None
+    p.tables = h.value if isinstance(h, ctypes.c_void_p) else h
+    p.d_offset = _ptr(offset, "i64").value
+    p.d_site = _ptr(site, "i32").value
+    p.d_tau = _ptr(tau, "f64").value
+    p.d_moff = _ptr(moff, "i64").value
+    p.d_M = _ptr(M, "f64").value
+    p.n_mat, p.loop_weight = int(n_mat), int(loop_weight)
+    if shift is not None:
+        count = (2 if weights == COS_DETERMINANTS else int(n_mat)) * (2 if lattice == COS_BIPARTITE else 1)
+        arr = _shifts(shift, count)
+        p.h_shift = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
+        p._keep = arr   # the array lives as long as the descriptor
+    return p
+
+
+def cos_forward(p: cos_problem, out, abs_mass=None, stream=None):
+    _check(lib().cos_forward(ctypes.byref(p), _ptr(out, "f64"), _ptr(abs_mass, "f64"), _stream(stream)), "cos_forward")
+
+
+def cos_grad(p: cos_problem, gout, out=None, gM=None, gmoff=None, gshift=None, gmu=None, galpha=None, stream=None):
+    _check(lib().cos_grad(ctypes.byref(p), _ptr(gout, "f64"), _ptr(out, "f64"), _ptr(gM, "f64"), _ptr(gmoff, "i64"),
+                          _ptr(gshift, "f64"), _ptr(gmu, "f64"), _ptr(galpha, "f64"), _stream(stream)), "cos_grad")
+
+
+def cos_subsets(p: cos_problem, c_out, a_out=None, all_roots: bool = True, stream=None):
+    _check(lib().cos_subsets(ctypes.byref(p), int(bool(all_roots)), _ptr(c_out, "f64"), _ptr(a_out, "f64"),
+                             _stream(stream)), "cos_subsets")
+
+
+# The per-case calls of earlier versions, kept as Python functions over the descriptor calls.
+
+def cos_connected_sum_matrices_grad(n_max: int, order, moff, n_mat: int, loop_weight: int,
+                                    sigma: Optional[Sequence[float]], M, gout, out=None, gM=None, gsigma=None,
+                                    stream=None):
+    """Gradient of the connected sums of explicit matrices: dLoss/dM (layout of M) and
+    dLoss/dsigma ([n_cfg][n_mat]) for dLoss/dc = gout."""
+    cos_grad(problem(COS_SQUARE, COS_LOOPS, "fp64", n_max, order, moff=moff, M=M, n_mat=n_mat,
+                     loop_weight=loop_weight, shift=sigma), gout, out, gM, gshift=gsigma, stream=stream)
+
+
+def cos_connected_sum_subsets(n_max: int, order, moff, n_mat: int, loop_weight: int,
+                              sigma: Optional[Sequence[float]], M, precision: str, c_out, a_out=None,
+                              all_roots: bool = True, stream=None):
+    """c(S) (and a(S) when a_out is given) of every vertex subset S: c_out / a_out are
+    [n_cfg * 2^n_max] float64, entry c * 2^n_max + S (bit i of S = vertex i)."""
+    cos_subsets(problem(COS_SQUARE, COS_LOOPS, precision, n_max, order, moff=moff, M=M, n_mat=n_mat,
+                        loop_weight=loop_weight, shift=sigma), c_out, a_out, all_roots, stream)
+
+
+def cos_connected_sum_bipartite_matrices(n_max: int, order, moff, n_mat: int, loop_weight: int, sigma2, M4,
+                                         precision: str, out, abs_mass=None, stream=None):
+    """Bipartite connected sums of explicit matrices; sigma2: None or n_mat x 2 shift weights
+    (flavor, sublattice)."""
+    cos_forward(problem(COS_BIPARTITE, COS_LOOPS, precision, n_max, order, moff=moff, M=M4, n_mat=n_mat,
+                        loop_weight=loop_weight, shift=sigma2), out, abs_mass, stream)
+
+
+def cos_connected_sum_bipartite_batch(tables: "Tables", n_max: int, order, offset, site, tau, precision: str, out,
+                                      abs_mass=None, stream=None):
+    cos_forward(problem(COS_BIPARTITE, COS_LOOPS, precision, n_max, order, tables, offset, site, tau), out,
+                abs_mass, stream)
+
+
+def cos_connected_sum_bipartite_matrices_grad(n_max: int, order, moff, n_mat: int, loop_weight: int, sigma2, M4,
+                                              gout, out=None, gM4=None, gsigma2=None, stream=None):
+    """Gradient of the bipartite sums: dLoss/dM4 (layout of M4) and dLoss/dsigma2 ([n_cfg][n_mat][2])."""
+    cos_grad(problem(COS_BIPARTITE, COS_LOOPS, "fp64", n_max, order, moff=moff, M=M4, n_mat=n_mat,
+                     loop_weight=loop_weight, shift=sigma2), gout, out, gM4, gshift=gsigma2, stream=stream)
+
+
+def cos_connected_sum_bipartite_grad(tables: "Tables", n_max: int, order, offset, site, tau, gout, out=None, gM4=None,
+                                     gmoff=None, gmu=None, galpha=None, stream=None):
+    """Gradient of the bipartite sums from vertex coordinates (honeycomb tables): dLoss/dM4
+    ([n_mat][2 n_c][2 n_c] at gmoff), dLoss/dmu and dLoss/dalpha ([n_cfg][n_flavors])."""
+    cos_grad(problem(COS_BIPARTITE, COS_LOOPS, "fp64", n_max, order, tables, offset, site, tau), gout, out, gM4,
+             gmoff, None, gmu, galpha, stream)
+
+
+def cos_connected_sum_bipartite_subsets(n_max: int, order, moff, n_mat: int, loop_weight: int, sigma2, M4, c_out,
+                                        a_out=None, all_roots: bool = True, stream=None):
+    """c(S) (and a(S)) of every vertex subset S on a bipartite lattice."""
+    cos_subsets(problem(COS_BIPARTITE, COS_LOOPS, "fp64", n_max, order, moff=moff, M=M4, n_mat=n_mat,
+                        loop_weight=loop_weight, shift=sigma2), c_out, a_out, all_roots, stream)
+
+
+def cos_connected_det_matrices(n_max: int, order, moff, alpha: Optional[Sequence[float]], M, precision: str, out,
+                               abs_mass=None, stream=None):
+    """SU(2) determinant weights (Alg. 1): M holds [2][n_c][n_c] (spin up, spin down) per
+    configuration at moff; alpha None or the two diagonal shifts."""
+    cos_forward(problem(COS_SQUARE, COS_DETERMINANTS, precision, n_max, order, moff=moff, M=M, shift=alpha), out,
+                abs_mass, stream)
+
+
+def cos_connected_det_batch(tables: "Tables", n_max: int, order, offset, site, tau, alpha, precision: str, out,
+                            abs_mass=None, stream=None):
+    """Gather + SU(2) determinant-weight sums from vertex coordinates (SU(2) tables built with
+    alpha = 0; alpha: None or the two diagonal shifts)."""
+    cos_forward(problem(COS_SQUARE, COS_DETERMINANTS, precision, n_max, order, tables, offset, site, tau,
+                        shift=alpha), out, abs_mass, stream)
+
+
+def cos_connected_det_matrices_grad(n_max: int, order, moff, alpha: Optional[Sequence[float]], M, gout, out=None,
+                                    gM=None, galpha=None, stream=None):
+    """Gradient of the SU(2) determinant-weight sums: dLoss/dM (layout of M) and dLoss/dalpha
+    ([n_cfg][2]) for dLoss/dc = gout."""
+    cos_grad(problem(COS_SQUARE, COS_DETERMINANTS, "fp64", n_max, order, moff=moff, M=M, shift=alpha), gout, out,
+             gM, gshift=galpha, stream=stream)
+
+
+def cos_connected_det_grad(tables: "Tables", n_max: int, order, offset, site, tau, alpha, gout, out=None, gM=None,
+                           gmoff=None, gmu=None, galpha=None, stream=None):
+    """Gradient of the SU(2) determinant-weight sums from vertex coordinates: dLoss/dM ([2][n_c][n_c]
+    at gmoff), dLoss/dmu and dLoss/dalpha ([n_cfg][2], alpha the diagonal shifts)."""
+    cos_grad(problem(COS_SQUARE, COS_DETERMINANTS, "fp64", n_max, order, tables, offset, site, tau, shift=alpha),
+             gout, out, gM, gmoff, galpha, gmu, None, stream)
+
+
+def cos_connected_det_subsets(n_max: int, order, moff, alpha: Optional[Sequence[float]], M, c_out, a_out=None,
+                              all_roots: bool = True, stream=None):
+    """c(S) (and a(S) = det(A_up[S]) det(A_dn[S]) when a_out is given) of every vertex subset S
+    for determinant weights."""
+    cos_subsets(problem(COS_SQUARE, COS_DETERMINANTS, "fp64", n_max, order, moff=moff, M=M, shift=alpha), c_out,
+                a_out, all_roots, stream)
+
+
+def cos_connected_det_bipartite_matrices(n_max: int, order, moff, alpha2, M4, precision: str, out, abs_mass=None,
+                                         stream=None):
+    """SU(2) determinant weights on a bipartite lattice (Alg. 1): M4 holds [2][2 n_c][2 n_c]
+    per configuration at moff; alpha2 None or 2 x 2 diagonal shifts (spin, sublattice)."""
+    cos_forward(problem(COS_BIPARTITE, COS_DETERMINANTS, precision, n_max, order, moff=moff, M=M4, shift=alpha2),
+                out, abs_mass, stream)
+
+
+def cos_connected_det_bipartite_batch(tables: "Tables", n_max: int, order, offset, site, tau, alpha2, precision: str,
+                                      out, abs_mass=None, stream=None):
+    """Gather + bipartite determinant-weight sums from vertex coordinates (two-flavor honeycomb
+    tables; alpha2: None or the 2 x 2 diagonal shifts, spin then sublattice)."""
+    cos_forward(problem(COS_BIPARTITE, COS_DETERMINANTS, precision, n_max, order, tables, offset, site, tau,
+                        shift=alpha2), out, abs_mass, stream)
+
+
+def cos_connected_det_bipartite_matrices_grad(n_max: int, order, moff, alpha2, M4, gout, out=None, gM4=None,
+                                              galpha2=None, stream=None):
+    """Gradient of the bipartite determinant-weight sums: dLoss/dM4 and dLoss/dalpha2 ([n_cfg][2][2])."""
+    cos_grad(problem(COS_BIPARTITE, COS_DETERMINANTS, "fp64", n_max, order, moff=moff, M=M4, shift=alpha2), gout,
+             out, gM4, gshift=galpha2, stream=stream)
+
+
+def cos_connected_det_bipartite_grad(tables: "Tables", n_max: int, order, offset, site, tau, alpha2, gout, out=None,
+                                     gM4=None, gmoff=None, gmu=None, galpha2=None, stream=None):
+    """Gradient of the bipartite determinant-weight sums from vertex coordinates: dLoss/dM4
+    ([2][2 n_c][2 n_c] at gmoff), dLoss/dmu ([n_cfg][2]) and dLoss/dalpha2 ([n_cfg][2][2])."""
+    cos_grad(problem(COS_BIPARTITE, COS_DETERMINANTS, "fp64", n_max, order, tables, offset, site, tau, shift=alpha2),
+             gout, out, gM4, gmoff, galpha2, gmu, None, stream)
+
+
+def cos_connected_det_bipartite_subsets(n_max: int, order, moff, alpha2, M4, c_out, a_out=None,
+                                        all_roots: bool = True, stream=None):
+    """c(S) (and a(S)) of every vertex subset S for bipartite determinant weights."""
+    cos_subsets(problem(COS_BIPARTITE, COS_DETERMINANTS, "fp64", n_max, order, moff=moff, M=M4, shift=alpha2),
+                c_out, a_out, all_roots, stream)
 
 
 def cos_sync_status(stream=None):

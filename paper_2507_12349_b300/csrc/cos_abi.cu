@@ -323,7 +323,7 @@ extern "C" cos_status cos_connected_sum_matrices(int n_cfg, int n_max, const int
                          d_abs_mass, (cudaStream_t)stream);
 }
 
-extern "C" cos_status cos_connected_det_matrices(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+COS_INTERNAL_API cos_status cos_connected_det_matrices(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
                                                  const double *h_alpha, const double *d_M, cos_precision precision,
                                                  double *d_out, double *d_abs_mass, cos_stream_t stream) {
     cos_status st = check_matrices(n_cfg, n_max, d_order, d_moff, 2, 1, d_M, precision, d_out,
@@ -465,7 +465,7 @@ __global__ void fold_spin_blocks_kernel(int n_cfg, const int32_t *__restrict__ o
 }  // namespace
 }  // namespace cosdp
 
-extern "C" cos_status cos_connected_det_grad(const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order,
+COS_INTERNAL_API cos_status cos_connected_det_grad(const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order,
                                              const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
                                              const double *h_alpha, const double *d_gout, double *d_out,
                                              double *d_gM, const int64_t *d_gmoff, double *d_gmu,
@@ -539,7 +539,7 @@ extern "C" cos_status cos_connected_det_grad(const cos_tables *t, int n_cfg, int
     return COS_OK;
 }
 
-extern "C" cos_status cos_connected_det_batch(const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order,
+COS_INTERNAL_API cos_status cos_connected_det_batch(const cos_tables *t, int n_cfg, int n_max, const int32_t *d_order,
                                               const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
                                               const double *h_alpha, cos_precision precision, double *d_out,
                                               double *d_abs_mass, cos_stream_t stream) {
@@ -604,7 +604,7 @@ extern "C" cos_status cos_connected_sum_batch(const cos_tables *t, int n_cfg, in
                       (cudaStream_t)stream);
 }
 
-extern "C" cos_status cos_connected_sum_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
+COS_INTERNAL_API cos_status cos_connected_sum_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
                                                       const int64_t *d_moff, int n_mat, int loop_weight,
                                                       const double *h_sigma, const double *d_M, const double *d_gout,
                                                       double *d_out, double *d_gM, double *d_gsigma,
@@ -645,7 +645,7 @@ extern "C" cos_status cos_connected_sum_matrices_grad(int n_cfg, int n_max, cons
     return launch_adjoint(ws, L, d_gout, d_gM, d_moff, 0, d_gsigma, (cudaStream_t)stream);
 }
 
-extern "C" cos_status cos_connected_det_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
+COS_INTERNAL_API cos_status cos_connected_det_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
                                                       const int64_t *d_moff, const double *h_alpha, const double *d_M,
                                                       const double *d_gout, double *d_out, double *d_gM,
                                                       double *d_galpha, cos_stream_t stream) {

@@ -1184,7 +1184,7 @@ cos_status bip_grad_dp(const char *fn, int n_cfg, int n_max, const int32_t *d_or
 
 using namespace cosdp;
 
-extern "C" cos_status cos_connected_sum_bipartite_matrices(int n_cfg, int n_max, const int32_t *d_order,
+COS_INTERNAL_API cos_status cos_connected_sum_bipartite_matrices(int n_cfg, int n_max, const int32_t *d_order,
                                                            const int64_t *d_moff, int n_mat, int loop_weight,
                                                            const double *h_sigma2, const double *d_M4,
                                                            cos_precision precision, double *d_out,
@@ -1202,7 +1202,7 @@ extern "C" cos_status cos_connected_sum_bipartite_matrices(int n_cfg, int n_max,
                              d_out, d_abs_mass, (cudaStream_t)stream, false);
 }
 
-extern "C" cos_status cos_connected_det_bipartite_matrices(int n_cfg, int n_max, const int32_t *d_order,
+COS_INTERNAL_API cos_status cos_connected_det_bipartite_matrices(int n_cfg, int n_max, const int32_t *d_order,
                                                            const int64_t *d_moff, const double *h_alpha2,
                                                            const double *d_M4, cos_precision precision,
                                                            double *d_out, double *d_abs_mass, cos_stream_t stream) {
@@ -1232,7 +1232,7 @@ extern "C" cos_status cos_bipartite_structure(int n, cos_structure_info *info) {
     return COS_OK;
 }
 
-extern "C" cos_status cos_connected_sum_bipartite_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
+COS_INTERNAL_API cos_status cos_connected_sum_bipartite_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
                                                                 const int64_t *d_moff, int n_mat, int loop_weight,
                                                                 const double *h_sigma2, const double *d_M4,
                                                                 const double *d_gout, double *d_out, double *d_gM4,
@@ -1241,7 +1241,7 @@ extern "C" cos_status cos_connected_sum_bipartite_matrices_grad(int n_cfg, int n
                          loop_weight, h_sigma2, d_M4, d_gout, d_out, d_gM4, d_gsigma2, false, (cudaStream_t)stream);
 }
 
-extern "C" cos_status cos_connected_det_bipartite_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
+COS_INTERNAL_API cos_status cos_connected_det_bipartite_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
                                                                 const int64_t *d_moff, const double *h_alpha2,
                                                                 const double *d_M4, const double *d_gout,
                                                                 double *d_out, double *d_gM4, double *d_galpha2,

@@ -403,7 +403,7 @@ extern "C" cos_status cos_gather_bipartite(const cos_tables *t, int n_cfg, const
                              (cudaStream_t)stream);
 }
 
-extern "C" cos_status cos_connected_sum_bipartite_batch(const cos_tables *t, int n_cfg, int n_max,
+COS_INTERNAL_API cos_status cos_connected_sum_bipartite_batch(const cos_tables *t, int n_cfg, int n_max,
                                                         const int32_t *d_order, const int64_t *d_offset,
                                                         const int32_t *d_site, const double *d_tau,
                                                         cos_precision precision, double *d_out, double *d_abs_mass,
@@ -460,7 +460,7 @@ extern "C" cos_status cos_connected_sum_bipartite_batch(const cos_tables *t, int
                              d_abs_mass, s);
 }
 
-extern "C" cos_status cos_connected_det_bipartite_batch(const cos_tables *t, int n_cfg, int n_max,
+COS_INTERNAL_API cos_status cos_connected_det_bipartite_batch(const cos_tables *t, int n_cfg, int n_max,
                                                         const int32_t *d_order, const int64_t *d_offset,
                                                         const int32_t *d_site, const double *d_tau,
                                                         const double *h_alpha2, cos_precision precision,
@@ -516,7 +516,7 @@ extern "C" cos_status cos_connected_det_bipartite_batch(const cos_tables *t, int
                              d_abs_mass, s, true);
 }
 
-extern "C" cos_status cos_connected_sum_bipartite_grad(const cos_tables *t, int n_cfg, int n_max,
+COS_INTERNAL_API cos_status cos_connected_sum_bipartite_grad(const cos_tables *t, int n_cfg, int n_max,
                                                        const int32_t *d_order, const int64_t *d_offset,
                                                        const int32_t *d_site, const double *d_tau,
                                                        const double *d_gout, double *d_out, double *d_gM4,
@@ -588,7 +588,7 @@ extern "C" cos_status cos_connected_sum_bipartite_grad(const cos_tables *t, int 
     return COS_OK;
 }
 
-extern "C" cos_status cos_connected_det_bipartite_grad(const cos_tables *t, int n_cfg, int n_max,
+COS_INTERNAL_API cos_status cos_connected_det_bipartite_grad(const cos_tables *t, int n_cfg, int n_max,
                                                        const int32_t *d_order, const int64_t *d_offset,
                                                        const int32_t *d_site, const double *d_tau,
                                                        const double *h_alpha2, const double *d_gout, double *d_out,

@@ -255,3 +255,82 @@ struct cos_tables {
     std::vector<double> delta;
     double sigma2[COS_MAX_FLAVORS][2] = {};   // honeycomb: shift weight per (flavor, sublattice)
 };
+
+// The per-case implementations behind cos_forward, cos_grad and cos_subsets (cos_api.cu): one
+// per lattice, weight kind and input form.  C linkage, hidden from the library's exports; the
+// public header documents their arguments through cos_problem.
+#define COS_INTERNAL_API extern "C" __attribute__((visibility("hidden")))
+COS_INTERNAL_API cos_status cos_connected_sum_subsets(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                                     int n_mat, int loop_weight, const double *h_sigma, const double *d_M,
+                                     cos_precision precision, int all_roots, double *d_c, double *d_a,
+                                     cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_sum_bipartite_matrices(int n_cfg, int n_max, const int32_t *d_order,
+                                                const int64_t *d_moff, int n_mat, int loop_weight,
+                                                const double *h_sigma2, const double *d_M4,
+                                                cos_precision precision, double *d_out,
+                                                double *d_abs_mass, cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_sum_bipartite_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
+                                                     const int64_t *d_moff, int n_mat, int loop_weight,
+                                                     const double *h_sigma2, const double *d_M4, const double *d_gout,
+                                                     double *d_out, double *d_gM4, double *d_gsigma2,
+                                                     cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_sum_bipartite_batch(const cos_tables *tables, int n_cfg, int n_max,
+                                             const int32_t *d_order, const int64_t *d_offset,
+                                             const int32_t *d_site, const double *d_tau,
+                                             cos_precision precision, double *d_out,
+                                             double *d_abs_mass, cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_sum_bipartite_subsets(int n_cfg, int n_max, const int32_t *d_order,
+                                               const int64_t *d_moff, int n_mat, int loop_weight,
+                                               const double *h_sigma2, const double *d_M4,
+                                               cos_precision precision, int all_roots, double *d_c,
+                                               double *d_a, cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_det_matrices(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                                      const double *h_alpha, const double *d_M, cos_precision precision,
+                                      double *d_out, double *d_abs_mass, cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_det_batch(const cos_tables *tables, int n_cfg, int n_max, const int32_t *d_order,
+                                   const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
+                                   const double *h_alpha, cos_precision precision, double *d_out,
+                                   double *d_abs_mass, cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_det_matrices_grad(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                                           const double *h_alpha, const double *d_M, const double *d_gout,
+                                           double *d_out, double *d_gM, double *d_galpha, cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_det_grad(const cos_tables *tables, int n_cfg, int n_max, const int32_t *d_order,
+                                  const int64_t *d_offset, const int32_t *d_site, const double *d_tau,
+                                  const double *h_alpha, const double *d_gout, double *d_out, double *d_gM,
+                                  const int64_t *d_gmoff, double *d_gmu, double *d_galpha, cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_det_subsets(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+                                     const double *h_alpha, const double *d_M, cos_precision precision,
+                                     int all_roots, double *d_c, double *d_a, cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_det_bipartite_matrices(int n_cfg, int n_max, const int32_t *d_order,
+                                                const int64_t *d_moff, const double *h_alpha2,
+                                                const double *d_M4, cos_precision precision,
+                                                double *d_out, double *d_abs_mass, cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_sum_bipartite_grad(const cos_tables *tables, int n_cfg, int n_max,
+                                            const int32_t *d_order, const int64_t *d_offset,
+                                            const int32_t *d_site, const double *d_tau, const double *d_gout,
+                                            double *d_out, double *d_gM4, const int64_t *d_gmoff,
+                                            double *d_gmu, double *d_galpha, cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_det_bipartite_batch(const cos_tables *tables, int n_cfg, int n_max,
+                                             const int32_t *d_order, const int64_t *d_offset,
+                                             const int32_t *d_site, const double *d_tau,
+                                             const double *h_alpha2, cos_precision precision,
+                                             double *d_out, double *d_abs_mass, cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_det_bipartite_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
+                                                     const int64_t *d_moff, const double *h_alpha2,
+                                                     const double *d_M4, const double *d_gout, double *d_out,
+                                                     double *d_gM4, double *d_galpha2, cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_det_bipartite_grad(const cos_tables *tables, int n_cfg, int n_max,
+                                            const int32_t *d_order, const int64_t *d_offset,
+                                            const int32_t *d_site, const double *d_tau, const double *h_alpha2,
+                                            const double *d_gout, double *d_out, double *d_gM4,
+                                            const int64_t *d_gmoff, double *d_gmu, double *d_galpha2,
+                                            cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_det_bipartite_subsets(int n_cfg, int n_max, const int32_t *d_order,
+                                               const int64_t *d_moff, const double *h_alpha2,
+                                               const double *d_M4, cos_precision precision, int all_roots,
+                                               double *d_c, double *d_a, cos_stream_t stream);
+COS_INTERNAL_API cos_status cos_connected_sum_matrices_grad(int n_cfg, int n_max, const int32_t *d_order,
+                                           const int64_t *d_moff, int n_mat, int loop_weight,
+                                           const double *h_sigma, const double *d_M,
+                                           const double *d_gout, double *d_out, double *d_gM,
+                                           double *d_gsigma, cos_stream_t stream);

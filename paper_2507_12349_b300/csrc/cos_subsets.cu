@@ -343,7 +343,7 @@ static cos_status bip_subsets_body(const char *fn, int n_cfg, int n_max, const i
 
 using namespace cosdp;
 
-extern "C" cos_status cos_connected_sum_bipartite_subsets(int n_cfg, int n_max, const int32_t *d_order,
+COS_INTERNAL_API cos_status cos_connected_sum_bipartite_subsets(int n_cfg, int n_max, const int32_t *d_order,
                                                           const int64_t *d_moff, int n_mat, int loop_weight,
                                                           const double *h_sigma2, const double *d_M4,
                                                           cos_precision precision, int all_roots, double *d_c,
@@ -352,7 +352,7 @@ extern "C" cos_status cos_connected_sum_bipartite_subsets(int n_cfg, int n_max, 
                             h_sigma2, d_M4, precision, all_roots, d_c, d_a, false, (cudaStream_t)stream);
 }
 
-extern "C" cos_status cos_connected_det_bipartite_subsets(int n_cfg, int n_max, const int32_t *d_order,
+COS_INTERNAL_API cos_status cos_connected_det_bipartite_subsets(int n_cfg, int n_max, const int32_t *d_order,
                                                           const int64_t *d_moff, const double *h_alpha2,
                                                           const double *d_M4, cos_precision precision, int all_roots,
                                                           double *d_c, double *d_a, cos_stream_t stream) {
@@ -360,7 +360,7 @@ extern "C" cos_status cos_connected_det_bipartite_subsets(int n_cfg, int n_max, 
                             d_M4, precision, all_roots, d_c, d_a, true, (cudaStream_t)stream);
 }
 
-extern "C" cos_status cos_connected_sum_subsets(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+COS_INTERNAL_API cos_status cos_connected_sum_subsets(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
                                                 int n_mat, int loop_weight, const double *h_sigma,
                                                 const double *d_M, cos_precision precision, int all_roots,
                                                 double *d_c, double *d_a, cos_stream_t stream) {
@@ -368,7 +368,7 @@ extern "C" cos_status cos_connected_sum_subsets(int n_cfg, int n_max, const int3
                         precision, all_roots, d_c, d_a, false, (cudaStream_t)stream);
 }
 
-extern "C" cos_status cos_connected_det_subsets(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
+COS_INTERNAL_API cos_status cos_connected_det_subsets(int n_cfg, int n_max, const int32_t *d_order, const int64_t *d_moff,
                                                 const double *h_alpha, const double *d_M, cos_precision precision,
                                                 int all_roots, double *d_c, double *d_a, cos_stream_t stream) {
     return subsets_body("cos_connected_det_subsets", n_cfg, n_max, d_order, d_moff, 2, 1, h_alpha, d_M, precision,

@@ -19,6 +19,19 @@ def declared_functions():
     return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(cos_\w+)\s*\(", src, flags=re.M)))
 
 
+def prob(lattice, weights, precision, n_cfg, n_max, order=None, tables=None, offset=None, site=None, tau=None,
+         moff=None, M=None, n_mat=0, wt=0, shift=None):
+    """A raw cos_problem with integer device addresses (for argument checks without a device)."""
+    import ctypes
+    p = B.cos_problem()
+    p.lattice, p.weights, p.precision, p.n_cfg, p.n_max = lattice, weights, precision, n_cfg, n_max
+    p.d_order, p.tables, p.d_offset, p.d_site, p.d_tau, p.d_moff, p.d_M = order, tables, offset, site, tau, moff, M
+    p.n_mat, p.loop_weight = n_mat, wt
+    if shift is not None:
+        p.h_shift = ctypes.cast(shift, ctypes.POINTER(ctypes.c_double))
+    return p
+
+
 def test_library_builds_and_exports_every_declared_symbol():
     lib = B.lib()
     decl = declared_functions()
@@ -47,49 +60,54 @@ def test_argument_errors_are_synchronous():
     # empty batch is a no-op
     assert lib.cos_connected_sum_matrices(0, 4, None, None, 1, 1, None, None, 0, None, None, None) == 0
     # all-subsets mode: a(S) needs every root; all_roots is a flag
-    rc = lib.cos_connected_sum_subsets(1, 4, None, None, 1, 1, None, None, 0, 1, None, None, None)
-    assert rc == -1                                     # null pointers
-    fake = ctypes.c_void_p(256)                         # never dereferenced: rejected before any launch
-    rc = lib.cos_connected_sum_subsets(1, 4, fake, fake, 1, 1, None, fake, 0, 0, fake, fake, None)
-    assert rc == -1
-    rc = lib.cos_connected_sum_subsets(1, 4, fake, fake, 1, 1, None, fake, 0, 2, fake, None, None)
-    assert rc == -1
-    assert lib.cos_connected_sum_subsets(0, 4, None, None, 1, 1, None, None, 0, 1, None, None, None) == 0
-    # SU(2) determinant weights: square orders up to 12, bipartite up to 9 and FP64 / df64 only
-    assert lib.cos_connected_det_matrices(1, 13, None, None, None, None, 0, None, None, None) == -2
-    assert lib.cos_connected_det_matrices(1, 4, None, None, None, None, 0, None, None, None) == -1
-    assert lib.cos_connected_det_matrices(1, 4, fake, fake, None, fake, 9, fake, None, None) == -1
-    assert lib.cos_connected_det_matrices(0, 4, None, None, None, None, 0, None, None, None) == 0
-    assert lib.cos_connected_det_bipartite_matrices(1, 10, fake, fake, None, fake, 0, fake, None, None) == -2
-    assert lib.cos_connected_det_bipartite_matrices(1, 4, fake, fake, None, fake, 7, fake, None, None) == -1
-    assert lib.cos_connected_det_bipartite_matrices(1, 4, None, None, None, None, 0, None, None, None) == -1
-    assert lib.cos_connected_det_batch(None, 1, 4, fake, fake, fake, fake, None, 0, fake, None, None) == -1
-    assert lib.cos_connected_det_bipartite_batch(None, 1, 4, fake, fake, fake, fake, None, 0, fake, None, None) == -1
-    assert lib.cos_connected_sum_bipartite_grad(None, 1, 4, fake, fake, fake, fake, fake, None, None, None, None, None,
-                                                None) == -1
-    assert lib.cos_connected_det_bipartite_grad(None, 1, 4, fake, fake, fake, fake, None, fake, None, None, None, None,
-                                                None, None) == -1
-    # bipartite all-subsets: orders up to 9, FP64 only, all_roots 0 or 1
-    assert lib.cos_connected_sum_bipartite_subsets(1, 10, fake, fake, 1, 1, None, fake, 0, 1, fake, None, None) == -2
-    assert lib.cos_connected_sum_bipartite_subsets(1, 4, fake, fake, 1, 1, None, fake, 1, 1, fake, None, None) == -6
-    assert lib.cos_connected_sum_bipartite_subsets(1, 4, fake, fake, 1, 1, None, fake, 0, 2, fake, None, None) == -1
-    assert lib.cos_connected_sum_bipartite_subsets(1, 4, fake, fake, 1, 1, None, fake, 0, 0, fake, fake, None) == -1
-    assert lib.cos_connected_sum_bipartite_subsets(0, 4, None, None, 1, 1, None, None, 0, 1, None, None, None) == 0
-    assert lib.cos_connected_det_bipartite_subsets(1, 4, fake, fake, None, fake, 2, 1, fake, None, None) == -6
-    assert lib.cos_connected_det_bipartite_subsets(1, 4, None, None, None, None, 0, 1, None, None, None) == -1
-    assert lib.cos_connected_det_grad(None, 1, 4, fake, fake, fake, fake, None, fake, None, None, None, None, None,
-                                      None) == -1
-    assert lib.cos_connected_det_grad(None, 1, 13, fake, fake, fake, fake, None, fake, None, None, None, None, None,
-                                      None) == -2
-    assert lib.cos_connected_det_matrices_grad(1, 13, None, None, None, None, None, None, None, None, None) == -2
-    assert lib.cos_connected_det_matrices_grad(1, 4, None, None, None, None, None, None, None, None, None) == -1
-    assert lib.cos_connected_det_matrices_grad(0, 4, None, None, None, None, None, None, None, None, None) == 0
-    assert lib.cos_connected_det_subsets(1, 4, fake, fake, None, fake, 1, 1, fake, None, None) == -6
-    assert lib.cos_connected_sum_bipartite_matrices_grad(1, 10, fake, fake, 2, 1, None, fake, fake, None, None, None,
-                                                         None) == -2
-    assert lib.cos_connected_det_bipartite_matrices_grad(0, 4, None, None, None, None, None, None, None, None,
-                                                         None) == 0
-    assert lib.cos_connected_det_subsets(1, 4, fake, fake, None, fake, 0, 0, fake, fake, None) == -1
+    fake = 256                                          # never dereferenced: rejected before any launch
+    assert lib.cos_subsets(ctypes.byref(prob(0, 0, 0, 1, 4, n_mat=1, wt=1)), 1, None, None, None) == -1
+    assert lib.cos_subsets(ctypes.byref(prob(0, 0, 0, 1, 4, fake, moff=fake, M=fake, n_mat=1, wt=1)), 0, fake, fake,
+                           None) == -1
+    assert lib.cos_subsets(ctypes.byref(prob(0, 0, 0, 1, 4, fake, moff=fake, M=fake, n_mat=1, wt=1)), 2, fake, None,
+                           None) == -1
+    assert lib.cos_subsets(ctypes.byref(prob(0, 0, 0, 0, 4, n_mat=1, wt=1)), 1, None, None, None) == 0
+    # descriptor calls (cos_problem): determinant weights, bipartite lattices, gradients, subsets
+    fw = lambda p, out=None: lib.cos_forward(ctypes.byref(p), out, None, None)
+    gr = lambda p, gout=None, **k: lib.cos_grad(ctypes.byref(p), gout, None, k.get("gM"), k.get("gmoff"),
+                                                k.get("gshift"), k.get("gmu"), k.get("galpha"), None)
+    ss = lambda p, roots, c, a=None: lib.cos_subsets(ctypes.byref(p), roots, c, a, None)
+    assert lib.cos_forward(None, None, None, None) == -1
+    assert fw(prob(5, 0, 0, 1, 4, fake, moff=fake, M=fake), fake) == -1            # unknown lattice
+    assert fw(prob(0, 7, 0, 1, 4, fake, moff=fake, M=fake), fake) == -1            # unknown weight kind
+    # square determinant weights: orders up to 12
+    assert fw(prob(0, 1, 0, 1, 13)) == -2
+    assert fw(prob(0, 1, 0, 1, 4)) == -1
+    assert fw(prob(0, 1, 9, 1, 4, fake, moff=fake, M=fake), fake) == -1           # bad precision
+    assert fw(prob(0, 1, 0, 0, 4)) == 0
+    # bipartite determinant weights: orders up to 9
+    assert fw(prob(1, 1, 0, 1, 10, fake, moff=fake, M=fake), fake) == -2
+    assert fw(prob(1, 1, 7, 1, 4, fake, moff=fake, M=fake), fake) == -1
+    assert fw(prob(1, 1, 0, 1, 4)) == -1
+    # loop weights from coordinates take their shifts from the tables (never dereferenced here)
+    sh = (ctypes.c_double * 4)(0.1, 0.2, 0.3, 0.4)
+    assert fw(prob(0, 0, 0, 1, 4, fake, tables=fake, offset=fake, site=fake, tau=fake, shift=sh), fake) == -1
+    # gradients: FP64 only; the coordinates and matrices forms take their own outputs
+    assert gr(prob(0, 0, 1, 1, 4, fake, moff=fake, M=fake, n_mat=1, wt=1), fake) == -6
+    assert gr(prob(0, 0, 0, 1, 4, fake, tables=fake, offset=fake, site=fake, tau=fake), fake, gshift=fake) == -1
+    assert gr(prob(0, 1, 0, 1, 4, fake, tables=fake, offset=fake, site=fake, tau=fake), fake, galpha=fake) == -1
+    assert gr(prob(0, 0, 0, 1, 4, fake, moff=fake, M=fake, n_mat=1, wt=1), fake, gmoff=fake) == -1
+    assert gr(prob(0, 1, 0, 1, 13)) == -2
+    assert gr(prob(0, 1, 0, 1, 4)) == -1
+    assert gr(prob(0, 1, 0, 0, 4)) == 0
+    assert gr(prob(1, 0, 0, 1, 10, fake, moff=fake, M=fake, n_mat=2, wt=1), fake) == -2
+    assert gr(prob(1, 1, 0, 0, 4)) == 0
+    # every subset: explicit matrices only; bipartite orders up to 9, FP64; all_roots 0 or 1
+    assert ss(prob(0, 0, 0, 1, 4, fake, tables=fake, offset=fake, site=fake, tau=fake), 1, fake) == -6
+    assert ss(prob(1, 0, 0, 1, 10, fake, moff=fake, M=fake, n_mat=1, wt=1), 1, fake) == -2
+    assert ss(prob(1, 0, 1, 1, 4, fake, moff=fake, M=fake, n_mat=1, wt=1), 1, fake) == -6
+    assert ss(prob(1, 0, 0, 1, 4, fake, moff=fake, M=fake, n_mat=1, wt=1), 2, fake) == -1
+    assert ss(prob(1, 0, 0, 1, 4, fake, moff=fake, M=fake, n_mat=1, wt=1), 0, fake, fake) == -1
+    assert ss(prob(1, 0, 0, 0, 4, n_mat=1, wt=1), 1, None) == 0
+    assert ss(prob(1, 1, 2, 1, 4, fake, moff=fake, M=fake), 1, fake) == -6
+    assert ss(prob(1, 1, 0, 1, 4), 1, None) == -1
+    assert ss(prob(0, 1, 1, 1, 4, fake, moff=fake, M=fake), 1, fake) == -6
+    assert ss(prob(0, 1, 0, 1, 4, fake, moff=fake, M=fake), 0, fake, fake) == -1
     assert lib.cos_status_string(-2) == b"order out of range"
     inf = B.cos_structure_info()
     assert lib.cos_structure(0, ctypes.byref(inf)) == -2
@@ -198,11 +216,11 @@ def test_bipartite_structure_counts(n):
 def test_bipartite_argument_errors():
     lib = B.lib()
     import ctypes
-    fake = ctypes.c_void_p(256)     # never dereferenced: rejected before any launch
-    assert lib.cos_connected_sum_bipartite_matrices(1, 10, fake, fake, 1, 1, None, fake, 0, fake, None, None) == -2
-    assert lib.cos_connected_sum_bipartite_matrices(1, 4, fake, fake, 1, 1, None, fake, 7, fake, None, None) == -1
-    assert lib.cos_connected_sum_bipartite_matrices(1, 4, None, fake, 1, 1, None, fake, 0, fake, None, None) == -1
-    assert lib.cos_connected_sum_bipartite_matrices(0, 4, None, None, 1, 1, None, None, 0, None, None, None) == 0
-    assert lib.cos_connected_sum_bipartite_batch(None, 1, 4, fake, fake, fake, fake, 0, fake, None, None) == -1
+    fake = 256     # never dereferenced: rejected before any launch
+    fw = lambda p: lib.cos_forward(ctypes.byref(p), fake, None, None)
+    assert fw(prob(1, 0, 0, 1, 10, fake, moff=fake, M=fake, n_mat=1, wt=1)) == -2
+    assert fw(prob(1, 0, 7, 1, 4, fake, moff=fake, M=fake, n_mat=1, wt=1)) == -1
+    assert fw(prob(1, 0, 0, 1, 4, None, moff=fake, M=fake, n_mat=1, wt=1)) == -1
+    assert lib.cos_forward(ctypes.byref(prob(1, 0, 0, 0, 4, n_mat=1, wt=1)), None, None, None) == 0
     inf = B.cos_structure_info()
     assert lib.cos_bipartite_structure(10, ctypes.byref(inf)) == -2

@@ -199,10 +199,10 @@ def test_other_precisions_are_rejected():
     M = torch.tensor(np.concatenate([m.ravel() for m in M4s]), device="cuda")
     c = torch.empty(2 * 8, dtype=torch.float64, device="cuda")
     lib = B.lib()
+    import ctypes
     for prec in ("mixed", "df64"):
-        rc = lib.cos_connected_sum_bipartite_subsets(2, 3, B._ptr(order, "i32"), B._ptr(moff, "i64"), 1, 1, None,
-                                                     B._ptr(M, "f64"), B.PRECISIONS[prec], 1, B._ptr(c, "f64"),
-                                                     None, None)
+        p = B.problem(B.COS_BIPARTITE, B.COS_LOOPS, prec, 3, order, moff=moff, M=M, n_mat=1, loop_weight=1)
+        rc = lib.cos_subsets(ctypes.byref(p), 1, B._ptr(c, "f64"), None, None)
         assert rc == -6
 
 
