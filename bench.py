@@ -382,7 +382,8 @@ def native_arm(args):
     w = I.WORKLOADS[args.workload]
     n_cfg = args.n_cfg if args.n_cfg > 0 else w.n_cfg
     # weak scaling: every rank takes its own configurations of the seeded stream
-    cfgs = I.workload_configs(w, n_cfg, first_cfg=rank * n_cfg)
+    from paper_2507_12349_b300 import shard
+    cfgs = I.workload_configs(w, n_cfg, first_cfg=shard.weak_block(n_cfg, rank)[0])
     tabs = B.tables_for(w.model)
     d_order, d_offset, d_site, d_tau = B.configs_to_device(cfgs)
     inf = tabs.info()

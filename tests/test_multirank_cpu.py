@@ -35,12 +35,17 @@ def _worker(rank, world, port, order, q):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     start, stop = S.shard_bounds(len(order), rank, world)
-    vals = _values(order[start:stop], first=start) if stop > start else np.zeros(0)
-    acc = S.per_order_accumulators(order[start:stop], vals)
-    tot = S.allreduce_accumulators(acc)
+    # the oracle stands in for the GPU batch call on this rank's slice
+    tot = S.sharded_accumulators(order, lambda a, b: _values(order[a:b], first=a), rank, world)
     q.put((rank, start, stop, tot))
     dist.barrier()
     dist.destroy_process_group()
+
+
+def test_weak_blocks_tile_the_stream():
+    assert [S.weak_block(5, r) for r in range(3)] == [(0, 5), (5, 10), (10, 15)]
+    with pytest.raises(ValueError):
+        S.weak_block(-1, 0)
 
 
 def test_shard_bounds_partition():
