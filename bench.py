@@ -744,6 +744,9 @@ def measure_grad_high_orders(torch, B, flush, peaks, steps, n_cfg=2368):
     checkpoints layers where the free memory cannot hold every CTA's layers, against every
     layer kept with the grid the memory allows."""
     w = I.WORKLOADS["su4_adjoint_n10"]
+    # start from the memory a fresh process would see: the earlier forms' workspaces released
+    B.cos_release_workspace()
+    torch.cuda.empty_cache()
     tabs = B.tables_for(w.model)
     res = {}
     for n in (11, 12):

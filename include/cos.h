@@ -365,14 +365,16 @@ cos_status cos_subsets(const cos_problem *p, int all_roots, double *d_c, double 
 /* Memory of the gradient calls.  The reverse sweep needs the forward state of every layer;
  * each adjoint overwrites the forward state it was formed from, so the kept layers are the
  * whole workspace: about (states per flavor array) x 32 lanes x 8 B per CTA, 181 MB at n = 10
- * and 2.2 GB at n = 12.  Where free device memory cannot hold that for every CTA, layers are
+ * and 2.2 GB at n = 12 on the square lattice, 3.3 GB at n = 9 on the bipartite one (with
+ * 2 x 4 n^2 x 32 doubles of gradient accumulators per CTA there at n = 9).  Where free device
+ * memory cannot hold that for every CTA, layers are
  * checkpointed (the reverse of Alg. 2-3 with the forward recomputed per segment): a set of
  * checkpoint layers is kept, and the layers between two checkpoints are re-run from the first
  * before they are reversed.  The launcher picks, per order, the grid and checkpoint set that
  * give the most throughput within 85 % of the free memory.  The environment variable
  * COS_GRAD_CHECKPOINT=1 forces the least-storage plan at every order, =0 keeps every layer.
  *
- * cos_grad_checkpoint_plan (host only, no device): the plan of order n for a budget of
+ * cos_grad_checkpoint_plan (host only, no device): the square lattice's plan of order n for a budget of
  * slots_budget state slots per lane (0: the least storage): *ck_mask bit l = layer l is a
  * checkpoint (layers are numbered by visited points, 1 .. 2n; 0 = every layer kept),
  * *store_slots = slots per lane kept (checkpoints plus the largest segment between two),
@@ -437,6 +439,13 @@ cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts, cos_preci
  * Synchronizes `stream`, returns and clears the device status word of the
  * calls enqueued on it (COS_OK if none failed). */
 cos_status cos_sync_status(cos_stream_t stream);
+
+/* Frees the device workspace the library keeps for `stream` on the current device (layer
+ * rings and kept layers, gathered matrices, planner tables; it grows to the largest call made
+ * on the stream and stays allocated between calls).  Synchronizes the stream and reports its
+ * status word first, as cos_sync_status; the next call on the stream allocates afresh.  Plans
+ * and the no-allocation entry point keep their own workspaces and are not affected. */
+cos_status cos_release_workspace(cos_stream_t stream);
 const char *cos_status_string(cos_status status);
 /* Message of the last synchronous error in this thread ("" if none). */
 const char *cos_last_error(void);

@@ -31,7 +31,8 @@ EXPORTS = [
     "cos_connected_sum_matrices", "cos_connected_sum_matrices_noalloc", "cos_connected_sum_batch",
     "cos_build_propagators_honeycomb", "cos_gather_bipartite", "cos_bipartite_structure",
     "cos_forward", "cos_grad", "cos_subsets",
-    "cos_connected_sum_grad", "cos_grad_checkpoint_plan", "cos_sync_status", "cos_status_string",
+    "cos_connected_sum_grad", "cos_grad_checkpoint_plan", "cos_sync_status", "cos_release_workspace",
+    "cos_status_string",
     "cos_last_error", "cos_structure",
     "cos_plan_create_batch", "cos_plan_create_matrices", "cos_plan_launch", "cos_plan_status", "cos_plan_grid",
     "cos_plan_destroy", "cos_set_tuning", "cos_get_tuning", "cos_autotune",
@@ -120,6 +121,7 @@ def lib(build: bool = True):
         L.cos_connected_sum_grad.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.cos_connected_sum_batch.argtypes = [vp, i32, i32, vp, vp, vp, vp, i32, vp, vp, vp]
         L.cos_sync_status.argtypes = [vp]
+        L.cos_release_workspace.argtypes = [vp]
         L.cos_status_string.argtypes = [i32]
         L.cos_status_string.restype = ctypes.c_char_p
         L.cos_last_error.argtypes = []
@@ -489,6 +491,11 @@ def cos_connected_det_bipartite_subsets(n_max: int, order, moff, alpha2, M4, c_o
 
 def cos_sync_status(stream=None):
     _check(lib().cos_sync_status(_stream(stream)), "cos_sync_status")
+
+
+def cos_release_workspace(stream=None):
+    """Free the library's device workspace of this stream (after reporting its status)."""
+    _check(lib().cos_release_workspace(_stream(stream)), "cos_release_workspace")
 
 
 def cos_structure(n: int) -> cos_structure_info:

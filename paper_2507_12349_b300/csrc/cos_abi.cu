@@ -236,6 +236,25 @@ extern "C" const char *cos_status_string(cos_status s) {
 
 extern "C" const char *cos_last_error(void) { return t_err.c_str(); }
 
+// Frees the workspace of `stream` on the current device after reporting its status (as
+// cos_sync_status); the next call on the stream allocates a fresh one.
+extern "C" cos_status cos_release_workspace(cos_stream_t stream) {
+    const cos_status st = cos_sync_status(stream);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    Workspace *ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        auto it = g_ws.find(std::make_pair(dev, (cudaStream_t)stream));
+        if (it != g_ws.end()) {
+            ws = it->second;
+            g_ws.erase(it);
+        }
+    }
+    free_workspace(ws);
+    return st;
+}
+
 extern "C" cos_status cos_sync_status(cos_stream_t stream) {
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaStreamSynchronize(s);

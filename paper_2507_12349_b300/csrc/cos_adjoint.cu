@@ -433,29 +433,46 @@ int adjoint_warps(int n_max) { return std::max(4, std::min(12, n_max)); }
 // ------------------------------------------------------------------ checkpoint plans
 //
 // Storage (state slots per lane) and recomputation (multiply-adds of one flavor array) of a set
-// of checkpoint layers, in the layout of dp_adjoint_kernel: layer 1 and the checkpoints back to
-// back, then room for the largest segment interior.  A segment other than the last is re-run
+// of checkpoint layers, in the layout of the adjoint kernels: layer 1 and the checkpoints back
+// to back, then room for the largest segment interior.  A segment other than the last is re-run
 // from its checkpoint: the forward steps out of its layers s_i .. s_{i+1} - 2.
-struct CkPlan {
-    uint32_t mask = 0;
-    uint64_t store = 0;
-    uint64_t recompute = 0;
-    bool ok = false;
+
+// Per-layer slots and sweep work of an order (square lattice: the merged structure; bipartite:
+// the sublattice-resolved one).
+struct LayerProfile {
+    int n = 0;
+    uint64_t slots[kMaxLayers + 1] = {};
+    uint64_t work[kMaxLayers + 1] = {};
 };
 
-static CkPlan ck_eval(const HostOrder &o, uint32_t mask) {
+static LayerProfile layer_profile(int lattice, int n) {
+    LayerProfile p;
+    p.n = n;
+    if (lattice == COS_BIPARTITE) {
+        bip_layer_profile(n, p.slots, p.work);
+    } else {
+        const HostOrder &o = host_order(n);
+        for (int l = 0; l <= 2 * n; ++l) {
+            p.slots[l] = o.layer_slots[l];
+            p.work[l] = o.layer_work[l];
+        }
+    }
+    return p;
+}
+
+static CkPlan ck_eval(const LayerProfile &o, uint32_t mask) {
     const int L = 2 * o.n;
-    uint64_t ck = o.layer_slots[1], interior = 0, segmax = 0, rec = 0;
+    uint64_t ck = o.slots[1], interior = 0, segmax = 0, rec = 0;
     int start = 1;
     for (int l = 2; l <= L; ++l) {
         if ((mask >> l) & 1u) {
             segmax = std::max(segmax, interior);
-            for (int e = start; e <= l - 2; ++e) rec += o.layer_work[e];
+            for (int e = start; e <= l - 2; ++e) rec += o.work[e];
             start = l;
             interior = 0;
-            ck += o.layer_slots[l];
+            ck += o.slots[l];
         } else {
-            interior += o.layer_slots[l];
+            interior += o.slots[l];
         }
     }
     segmax = std::max(segmax, interior);
@@ -469,20 +486,20 @@ static CkPlan ck_eval(const HostOrder &o, uint32_t mask) {
 
 constexpr int kMaxCheckpoints = 7;   // enough for the optimum at every order up to 12
 
-// Pareto frontier of the checkpoint sets of order n (every set of at most kMaxCheckpoints layers
+// Pareto frontier of the checkpoint sets of an order (every set of at most kMaxCheckpoints layers
 // among 2 .. 2n, and the empty set): increasing storage, strictly decreasing recomputation.  The
 // first point needs the least storage; the last is the empty set (no recomputation).
-static const std::vector<CkPlan> &ck_frontier(int n) {
+static const std::vector<CkPlan> &ck_frontier(int lattice, int n) {
     static std::mutex mu;
-    static std::vector<CkPlan> cache[COS_NMAX + 1];
+    static std::vector<CkPlan> cache[2][COS_NMAX + 1];
     std::lock_guard<std::mutex> lk(mu);
-    std::vector<CkPlan> &fr = cache[n];
+    std::vector<CkPlan> &fr = cache[lattice == COS_BIPARTITE ? 1 : 0][n];
     if (!fr.empty()) return fr;
-    const HostOrder &o = host_order(n);
+    const LayerProfile o = layer_profile(lattice, n);
     std::vector<CkPlan> all;
     all.push_back(ck_eval(o, 0u));
     struct Rec {
-        const HostOrder &o;
+        const LayerProfile &o;
         int L;
         std::vector<CkPlan> &all;
         void go(int from, int k, uint32_t mask) {
@@ -503,10 +520,8 @@ static const std::vector<CkPlan> &ck_frontier(int n) {
     return fr;
 }
 
-// The least recomputation whose storage fits `budget` slots per lane (no checkpoints when every
-// layer fits); budget = 0 asks for the least storage.  ok = false when nothing fits.
-static CkPlan ck_plan(int n, uint64_t budget) {
-    const std::vector<CkPlan> &fr = ck_frontier(n);
+CkPlan ck_plan(int lattice, int n, uint64_t budget) {
+    const std::vector<CkPlan> &fr = ck_frontier(lattice, n);
     if (budget == 0) return fr.front();
     CkPlan best;
     for (const CkPlan &c : fr)
@@ -514,9 +529,18 @@ static CkPlan ck_plan(int n, uint64_t budget) {
     return best;
 }
 
+CkPlan ck_full(int lattice, int n) { return ck_frontier(lattice, n).back(); }
+
+uint64_t ck_forward_work(int lattice, int n) {
+    const LayerProfile o = layer_profile(lattice, n);
+    uint64_t w = 0;
+    for (int l = 1; l <= 2 * n; ++l) w += o.work[l];
+    return w;
+}
+
 // COS_GRAD_CHECKPOINT=1: every order keeps the least storage (recomputing the most); =0: every
 // layer kept whatever the memory; unset: the plan that gives the most throughput within memory.
-static int checkpoint_mode() {
+int checkpoint_mode() {
     const char *e = getenv("COS_GRAD_CHECKPOINT");
     if (!e || !*e) return -1;
     return e[0] == '0' ? 0 : 1;
@@ -564,22 +588,21 @@ cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, 
     // Grid and checkpoint plan of the largest order: the most throughput, CTAs x the inverse of
     // the work per batch (forward, reverse = 2 forwards, and the recomputed segments).
     const int mode = checkpoint_mode();
-    uint64_t fwd_work = 0;
-    for (int l = 1; l <= 2 * n_max; ++l) fwd_work += ho.layer_work[l];
+    const uint64_t fwd_work = ck_forward_work(COS_SQUARE, n_max);
     int grid = 1;
     uint64_t budget = 0;   // slots per lane of every order's plan (0: least storage)
     if (mode == 1) {
-        const CkPlan p = ck_plan(n_max, 0);
+        const CkPlan p = ck_plan(COS_SQUARE, n_max, 0);
         grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)gmax, avail / (p.store * kLanes * 8 + plane_bytes)));
     } else if (mode == 0) {
-        const CkPlan p = ck_eval(ho, 0u);
+        const CkPlan p = ck_full(COS_SQUARE, n_max);
         budget = p.store;
         grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)gmax, avail / (p.store * kLanes * 8 + plane_bytes)));
     } else {
         double best_score = -1.0;
         for (int g = gmax; g >= 1; g = (g > 8 ? g - std::max(1, g / 8) : g - 1)) {
             const uint64_t b = slots_budget(g);
-            const CkPlan p = ck_plan(n_max, b);
+            const CkPlan p = ck_plan(COS_SQUARE, n_max, b);
             if (!p.ok) continue;
             const double score = (double)g / (3.0 * (double)fwd_work + (double)p.recompute);
             if (score > best_score * (1.0 + 1e-9)) {
@@ -597,8 +620,8 @@ cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, 
     memset(&a, 0, sizeof a);
     uint64_t store_slots = 0;
     for (int n = 1; n <= n_max; ++n) {
-        const CkPlan p = (mode == 0) ? ck_eval(host_order(n), 0u) : ck_plan(n, budget);
-        const CkPlan q = p.ok ? p : ck_plan(n, 0);
+        const CkPlan p = (mode == 0) ? ck_full(COS_SQUARE, n) : ck_plan(COS_SQUARE, n, budget);
+        const CkPlan q = p.ok ? p : ck_plan(COS_SQUARE, n, 0);
         a.ckmask[n] = q.mask;
         store_slots = std::max(store_slots, q.store);
     }
@@ -672,7 +695,7 @@ extern "C" cos_status cos_grad_checkpoint_plan(int n, int64_t slots_budget, uint
         cosdp::set_error("cos_grad_checkpoint_plan: invalid argument");
         return COS_ERR_ARG;
     }
-    const cosdp::CkPlan p = cosdp::ck_plan(n, (uint64_t)slots_budget);
+    const cosdp::CkPlan p = cosdp::ck_plan(COS_SQUARE, n, (uint64_t)slots_budget);
     if (!p.ok) {
         cosdp::set_error("cos_grad_checkpoint_plan: no checkpoint plan fits the budget");
         return COS_ERR_ARG;

@@ -54,6 +54,7 @@ struct BipHostOrder {
     uint32_t layer_count[kMaxLayers + 1] = {};
     uint32_t layer_slots[kMaxLayers + 1] = {};
     uint32_t max_slots = 0;
+    uint64_t layer_work[kMaxLayers + 1] = {};   // multiply-adds of the sweep out of each layer
     cos_structure_info info{};
 };
 
@@ -101,6 +102,7 @@ void build_bip_order(int n, BipHostOrder &o) {
             info.fma_ext += (int64_t)nrows * nv * T;
             if (needclose) info.fma_close += (int64_t)nrows * nv;
             cost += (uint64_t)nrows * ((uint64_t)nv * (T + (needclose ? 1 : 0)) + 4);
+            o.layer_work[layer] += (uint64_t)nrows * nv * (T + (needclose ? 1 : 0));
         }
         Rec r;
         r.m = make_uint4(A | (B << 16), S, code, 0u);
@@ -756,8 +758,9 @@ cos_status bip_subsets_dp(Workspace *ws, int n_cfg, int n_max, const int32_t *d_
 
 // ------------------------------------------------------------------ reverse (adjoint) sweep
 // Gradient of the bipartite sums, the adjoint of the sweep above (as cos_adjoint.cu is of the
-// square one).  Per batch the CTA re-runs the forward sweep keeping every layer, then walks the
-// layers backwards with Obar = dc/dO:
+// square one).  Per batch the CTA re-runs the forward sweep keeping every layer at its place
+// (checkpointed where memory binds, the segments re-run before they are reversed), then walks
+// the layers backwards with Obar = dc/dO, each adjoint overwriting its forward state:
 //   Obar(mu,h,s_h,v,s_v) = sum_q D_q Ms[(v,s_v)][(j_q,s_q)] + Cbar Md[(v,s_v)][(h,s_h)],
 //   dM[(v,s_v)][(j_q,s_q)] += D_q O,  dM[(v,s_v)][(h,s_h)] += sgn w Cbar O,
 // D_q = Obar of extension target q (the forward's target table), Cbar = the flavor sum of the
@@ -768,10 +771,14 @@ cos_status bip_subsets_dp(Workspace *ws, int n_cfg, int n_max, const int32_t *d_
 // Warps own endpoint units (v, s_v), unit v * 2 + s_v modulo the warp count (2n warps, at most
 // 16): one writer per dM row, no atomics.  Shared memory holds Ms, Md and dM, 3 x 4 n^2 doubles
 // per lane, so one CTA per SM; at order 9 dM moves to the CTA's global scratch.
+// Storage as in the square adjoint (cos_adjoint.cu): each adjoint overwrites the forward state
+// it is formed from, and where memory binds the layers are checkpointed and the segments between
+// two checkpoints re-run from the first before they are reversed.
 struct BipAdjArgs {
     BipArgs f;
-    size_t store_elems;     // forward storage per CTA (every layer of n_max) * 32
-    size_t adj_slot_elems;  // one adjoint layer slot * 32
+    size_t store_elems;     // layer storage per CTA (checkpoint + segment areas) * 32
+    size_t cta_elems;       // store_elems, plus the dM accumulators when they live in global memory
+    uint32_t ckmask[COS_BIP_NMAX + 1];   // per order: bit l = layer l is a checkpoint
     const double *gout;
     double *gM;             // NULL or dLoss/dM4, layout of M4
     double *gsig;           // NULL or [n_cfg][n_mat][2]
@@ -804,12 +811,13 @@ __device__ __forceinline__ void bip_adj_chunk(const double *__restrict__ a1, con
 }
 
 template <int NT>
-__device__ __forceinline__ void bip_adj_endpoint(const double *__restrict__ fsrc, double *__restrict__ aout,
+__device__ __forceinline__ void bip_adj_endpoint(const double *fsrc, double *aout,
                                                  const double *__restrict__ a1, const double *__restrict__ Ms,
                                                  const double *__restrict__ Md, double *__restrict__ dM,
                                                  const TgtInfo &ti, uint32_t tslot, uint32_t slot, int vrow, int hc,
                                                  int qv, double cbar, double gamma, int lane, double &dvout) {
     constexpr int kSplit = 6;
+    // fsrc == aout: the forward state, replaced by its adjoint below (same slot, same thread)
     const double o = fsrc[(size_t)slot * kLanes + lane];
     double ob = 0.0, dv = 0.0;
     if constexpr (NT == 0) {
@@ -873,7 +881,11 @@ template <bool CLOW>
 __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_constant__ BipAdjArgs a) {
     extern __shared__ __align__(16) double smem_ba[];
     __shared__ int s_batch;
-    __shared__ uint32_t s_base[2 * kBipAdjMaxN + 3];
+    __shared__ uint32_t s_loc[2 * kBipAdjMaxN + 2];   // slot offset of each layer in the CTA's store
+    // the batch's schedule: per step a layer, +256 for a forward step (the first pass over every
+    // layer, then the refills of segments), else a reverse step
+    __shared__ int s_ops[6 * kBipAdjMaxN + 2];
+    __shared__ int s_nops;
     __shared__ double s_red[16][2][kLanes];
     const BipArgs &f = a.f;
     const int lane = threadIdx.x & 31;
@@ -882,11 +894,9 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
     const int nsm = 4 * f.smem_n * f.smem_n * kLanes;
     double *Ms = smem_ba;             // extension matrices (shifted diagonal)
     double *Md = smem_ba + nsm;       // close matrices times sgn w
-    double *store = reinterpret_cast<double *>(f.scratch) +
-                    (size_t)blockIdx.x * (a.store_elems + 2 * a.adj_slot_elems + (a.dm_global ? (size_t)nsm : 0));
-    double *adj = store + a.store_elems;
+    double *store = reinterpret_cast<double *>(f.scratch) + (size_t)blockIdx.x * a.cta_elems;
     // dc/dM accumulators [(v,s)][(j,t)][lane]
-    double *dM = a.dm_global ? adj + 2 * a.adj_slot_elems : smem_ba + 2 * nsm;
+    double *dM = a.dm_global ? store + a.store_elems : smem_ba + 2 * nsm;
     const int nfl = f.nf_lanes;
     const int lam = lane % nfl;
     const int ci = lane / nfl;
@@ -929,31 +939,49 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
             dM[e * kLanes + lane] = 0.0;
         }
         if (threadIdx.x == 0) {
+            // layer places: checkpoints (layer 1 and the plan's layers) back to back, then the
+            // interior layers of one segment back to back after them
+            const uint32_t ck = a.ckmask[n];
+            uint32_t c = 0;
+            int seg[2 * kBipAdjMaxN + 1], ns = 0;
+            for (int l = 1; l <= 2 * n; ++l)
+                if (l == 1 || ((ck >> l) & 1u)) {
+                    s_loc[l] = c;
+                    c += tab.layer_slots[l];
+                    seg[ns++] = l;
+                }
             uint32_t run = 0;
-            for (int l = 0; l <= 2 * n + 2; ++l) {
-                s_base[l] = run;
-                if (l <= 2 * n) run += tab.layer_slots[l];
+            for (int l = 2; l <= 2 * n; ++l) {
+                if ((ck >> l) & 1u) {
+                    run = 0;
+                } else {
+                    s_loc[l] = c + run;
+                    run += tab.layer_slots[l];
+                }
             }
+            s_loc[2 * n + 1] = 0;   // the full masks extend nowhere: never written or read
+            // the first forward pass, then the segments from the last: refill (all but the last),
+            // then reverse its layers
+            int no = 0;
+            for (int ell = 1; ell <= 2 * n; ++ell) s_ops[no++] = ell + 256;
+            for (int sg = ns - 1; sg >= 0; --sg) {
+                const int lo = seg[sg], hi = (sg + 1 < ns) ? seg[sg + 1] : 2 * n + 1;
+                if (sg + 1 < ns)
+                    for (int ell = lo; ell <= hi - 2; ++ell) s_ops[no++] = ell + 256;
+                for (int ell = hi - 1; ell >= lo; --ell) s_ops[no++] = ell;
+            }
+            s_nops = no;
         }
         __syncthreads();
         if (warp == 0) {
             for (int s0 = 0; s0 < 2; ++s0) {
                 const uint32_t off = __ldg(tab.rank4 + 1 + s0);
-                store[(size_t)(s_base[1] + off + 3u * (uint32_t)s0) * kLanes + lane] = (CLOW && lam != 0) ? 0.0 : 1.0;
+                store[(size_t)(s_loc[1] + off + 3u * (uint32_t)s0) * kLanes + lane] = (CLOW && lam != 0) ? 0.0 : 1.0;
             }
         }
         __syncthreads();
-        // forward sweep, every layer kept
-        for (int ell = 1; ell <= 2 * n; ++ell) {
-            const double *src = store + (size_t)s_base[ell] * kLanes;
-            double *dst1 = store + (size_t)s_base[ell + 1] * kLanes;
-            const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
-            for (uint32_t mi = warp; mi < cnt; mi += nwarps)
-                bip_mask<double, CLOW>(tab, first + mi, 0xFFFFFFFFu, ell, n, src, dst1, Ms, Md, lane, ci, nfl, seedsh,
-                                       shifts, active, lam, cfg, f.out, f.status, 0);
-            __syncthreads();
-        }
-        // reverse sweep: this warp's endpoint units (v, s_v); own = vertices with an owned unit
+        // the schedule: forward steps split masks over the warps; reverse steps take this warp's
+        // endpoint units (v, s_v); own = vertices with an owned unit
         uint32_t own2 = 0u, own = 0u;
         for (int u = warp; u < n2; u += nwarps) {
             own2 |= 1u << u;
@@ -962,10 +990,26 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
         const uint32_t full = (1u << n) - 1u;
         const double gout = active ? a.gout[cfg] : 0.0;
         double gs0 = 0.0, gs1 = 0.0;
-        for (int ell = 2 * n; ell >= 1; --ell) {
-            const double *fsrc = store + (size_t)s_base[ell] * kLanes;
-            double *aout = adj + (size_t)(ell & 1) * a.adj_slot_elems;
-            const double *a1 = adj + (size_t)((ell + 1) & 1) * a.adj_slot_elems;
+        for (int op = 0; op < s_nops; ++op) {
+            const int step = s_ops[op];
+            if (step >= 256) {
+                // a forward step, every layer to its place: the first pass, or the refill of a
+                // segment from its checkpoint (refills stop below layer 2n, so the sink is
+                // written once, by the first pass)
+                const int ell = step - 256;
+                const double *src = store + (size_t)s_loc[ell] * kLanes;
+                double *dst1 = store + (size_t)s_loc[ell + 1] * kLanes;
+                const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
+                for (uint32_t mi = warp; mi < cnt; mi += nwarps)
+                    bip_mask<double, CLOW>(tab, first + mi, 0xFFFFFFFFu, ell, n, src, dst1, Ms, Md, lane, ci, nfl,
+                                           seedsh, shifts, active, lam, cfg, f.out, f.status, 0);
+                __syncthreads();
+                continue;
+            }
+            const int ell = step;
+            double *aout = store + (size_t)s_loc[ell] * kLanes;   // O(ell), replaced by Obar(ell)
+            const double *fsrc = aout;
+            const double *a1 = store + (size_t)s_loc[ell + 1] * kLanes;
             const uint32_t first = tab.layer_first[ell], cnt = tab.layer_count[ell];
             for (uint32_t mi = 0; mi < cnt && own; ++mi) {
                 const uint4 mk = __ldg(tab.masks + first + mi);
@@ -1078,14 +1122,9 @@ static cos_status launch_bip_adjoint(Workspace *ws, const BipLaunch &L, const do
         set_error(err);
         return COS_ERR_CUDA;
     }
-    const BipHostOrder &ho = bip_host_order(L.n_max);
-    size_t total_slots = 0;
-    for (int l = 0; l <= 2 * L.n_max; ++l) total_slots += ho.layer_slots[l];
-    const size_t store_elems = total_slots * kLanes;
-    const size_t adj_slot_elems = (size_t)ho.max_slots * kLanes;
     const bool dm_global = L.n_max > kBipAdjSmemMaxN;
     const size_t mat_elems = (size_t)4 * L.n_max * L.n_max * kLanes;
-    const size_t per_cta = (store_elems + 2 * adj_slot_elems + (dm_global ? mat_elems : 0)) * sizeof(double);
+    const size_t extra = (dm_global ? mat_elems : 0) * sizeof(double);   // per CTA, beside the layers
     const int warps = std::min(16, std::max(4, 2 * L.n_max));
     const size_t smem = (dm_global ? 2 : 3) * mat_elems * sizeof(double);
     auto kern = L.clow ? dp_bip_adjoint_kernel<true> : dp_bip_adjoint_kernel<false>;
@@ -1095,16 +1134,54 @@ static cos_status launch_bip_adjoint(Workspace *ws, const BipLaunch &L, const do
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
     const int cpb = kLanes / L.n_mat;
     const int max_batches = (L.n_cfg + cpb - 1) / cpb + COS_NMAX;
-    int grid = std::max(1, std::min(nsm, max_batches));
+    const int gmax = std::max(1, std::min(nsm, max_batches));
     size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-        // every layer of the largest order is kept per CTA (GBs at the top orders): as many CTAs
-        // as fit in the free memory
-        const size_t avail = ws->scratch_bytes + (size_t)(0.85 * (double)free_b);
-        grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)grid, avail / per_cta));
+    size_t avail = (size_t)-1;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) avail = ws->scratch_bytes + (size_t)(0.85 * (double)free_b);
+    auto slots_budget = [&](int g) -> uint64_t {
+        const size_t per = avail / (size_t)g;
+        return per > extra ? (per - extra) / (kLanes * sizeof(double)) : 1;
+    };
+    // grid and checkpoint plans: as the square adjoint (most CTAs per unit of work, in memory)
+    const int mode = checkpoint_mode();
+    const uint64_t fwd_work = ck_forward_work(COS_BIPARTITE, L.n_max);
+    int grid = 1;
+    uint64_t budget = 0;
+    if (mode >= 0) {
+        const CkPlan p = mode == 1 ? ck_plan(COS_BIPARTITE, L.n_max, 0) : ck_full(COS_BIPARTITE, L.n_max);
+        if (mode == 0) budget = p.store;
+        grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)gmax, avail / (p.store * kLanes * 8 + extra)));
+    } else {
+        double best_score = -1.0;
+        for (int g = gmax; g >= 1; g = (g > 8 ? g - std::max(1, g / 8) : g - 1)) {
+            const uint64_t b = slots_budget(g);
+            const CkPlan p = ck_plan(COS_BIPARTITE, L.n_max, b);
+            if (!p.ok) continue;
+            const double score = (double)g / (3.0 * (double)fwd_work + (double)p.recompute);
+            if (score > best_score * (1.0 + 1e-9)) {
+                best_score = score;
+                grid = g;
+                budget = b;
+            }
+        }
+        if (best_score < 0) {
+            grid = 1;
+            budget = 0;
+        }
     }
+    uint32_t ckmask[COS_BIP_NMAX + 1] = {};
+    uint64_t store_slots = 0;
+    for (int n = 1; n <= L.n_max; ++n) {
+        const CkPlan p = (mode == 0) ? ck_full(COS_BIPARTITE, n) : ck_plan(COS_BIPARTITE, n, budget);
+        const CkPlan q = p.ok ? p : ck_plan(COS_BIPARTITE, n, 0);
+        ckmask[n] = q.mask;
+        store_slots = std::max(store_slots, q.store);
+    }
+    const size_t store_elems = (size_t)store_slots * kLanes;
+    const size_t cta_elems = store_elems + (dm_global ? mat_elems : 0);
     ws->last_grid = grid;
-    cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "bipartite adjoint scratch");
+    cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * cta_elems * sizeof(double), 1,
+                           "bipartite adjoint scratch");
     if (st != COS_OK) return st;
     BipAdjArgs a;
     memset(&a, 0, sizeof a);
@@ -1121,12 +1198,13 @@ static cos_status launch_bip_adjoint(Workspace *ws, const BipLaunch &L, const do
     memcpy(f.sigma2, L.sigma2, sizeof f.sigma2);
     f.shifts = L.shifts ? 1 : 0;
     f.scratch = ws->scratch;
-    f.slot_elems = adj_slot_elems;
+    f.slot_elems = 0;
     f.smem_n = L.n_max;
     f.out = L.out;
     f.status = ws->status;
     a.store_elems = store_elems;
-    a.adj_slot_elems = adj_slot_elems;
+    a.cta_elems = cta_elems;
+    memcpy(a.ckmask, ckmask, sizeof a.ckmask);
     a.gout = gout;
     a.gM = gM;
     a.gsig = gsig;
@@ -1249,3 +1327,13 @@ COS_INTERNAL_API cos_status cos_connected_det_bipartite_matrices_grad(int n_cfg,
     return bip_grad_body("cos_connected_det_bipartite_matrices_grad", n_cfg, n_max, d_order, d_moff, 2, 1, h_alpha2,
                          d_M4, d_gout, d_out, d_gM4, d_galpha2, true, (cudaStream_t)stream);
 }
+
+namespace cosdp {
+void bip_layer_profile(int n, uint64_t *slots, uint64_t *work) {
+    const BipHostOrder &o = bip_host_order(n);
+    for (int l = 0; l <= 2 * n; ++l) {
+        slots[l] = o.layer_slots[l];
+        work[l] = o.layer_work[l];
+    }
+}
+}  // namespace cosdp

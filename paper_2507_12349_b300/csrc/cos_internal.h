@@ -198,6 +198,21 @@ int pair_max_active_ctas(int precision, int threads, size_t smem);
 size_t dp_smem_bytes(int precision, int n_max);   // forward kernel shared memory of a precision
 size_t dp_state_bytes(const DpLaunch &a);   // bytes per state element
 
+// Checkpoint plans of the gradients' kept layers (cos_adjoint.cu): a set of checkpoint layers
+// (bit l of mask), the slots per lane it keeps (checkpoints + the largest segment interior) and
+// the multiply-adds of one flavor array it re-runs; lattice COS_SQUARE or COS_BIPARTITE.
+struct CkPlan {
+    uint32_t mask = 0;
+    uint64_t store = 0;
+    uint64_t recompute = 0;
+    bool ok = false;
+};
+CkPlan ck_plan(int lattice, int n, uint64_t budget);   // least recomputation within budget (0: least storage)
+CkPlan ck_full(int lattice, int n);                    // every layer kept
+uint64_t ck_forward_work(int lattice, int n);          // multiply-adds of one forward sweep
+int checkpoint_mode();                                  // COS_GRAD_CHECKPOINT: -1 unset, 0 keep all, 1 least storage
+void bip_layer_profile(int n, uint64_t *slots, uint64_t *work);   // per-layer slots / work, bipartite
+
 cos_status launch_adjoint(Workspace *ws, const DpLaunch &a, const double *gout, double *gM, const int64_t *gmoff,
                           int64_t gmstride, double *gsig, cudaStream_t stream);
 cos_status launch_chain(const cos_tables *t, int n_cfg, const int32_t *order, const int64_t *offset,

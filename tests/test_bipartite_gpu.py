@@ -498,3 +498,21 @@ def test_bipartite_model_autograd():
     assert np.array_equal(c.detach().cpu().numpy(), ref.cpu().numpy())
     assert np.allclose(mu_t.grad.numpy(), gmu.sum(0).cpu().numpy(), rtol=1e-14, atol=0)
     assert np.allclose(al_t.grad.numpy(), gal.sum(0).cpu().numpy(), rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("det", [False, True])
+def test_bipartite_grad_checkpointed_bitwise_and_exact(monkeypatch, det):
+    """The bipartite reverse sweep with the least-storage checkpoint plan forced (segments re-run
+    from their checkpoints, each adjoint in place of its forward state): bitwise the gradient
+    with every layer kept, at orders 4-7 in one uneven launch, and exact differences at order 4."""
+    orders = [6, 4, 7, 5, 7]
+    M4s = [rand_m4(9500 + 7 * c + (50 if det else 0), 1, 2, n)[0] for c, n in enumerate(orders)]
+    s2 = [[0.07, -0.04], [0.03, 0.05]]
+    gout = np.array([1.0, 0.5, -1.5, 2.0, 0.75])
+    monkeypatch.setenv("COS_GRAD_CHECKPOINT", "0")
+    a = run_bip_grad(M4s, 2, 1, s2, gout, det)
+    monkeypatch.setenv("COS_GRAD_CHECKPOINT", "1")
+    b = run_bip_grad(M4s, 2, 1, s2, gout, det)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+    assert all(np.array_equal(x, y) for x, y in zip(a[1], b[1]))
+    assert close_to(b[1][1], gout[1] * exact_dM4(M4s[1], s2, 1, det))

@@ -90,3 +90,24 @@ def test_autotune_installs_a_shape_and_keeps_results():
     B.cos_sync_status()
     assert torch.equal(out, ref)     # per-lane arithmetic does not depend on the launch shape
     B.cos_set_tuning(n, "fp64", n_mat, 8, 2, 1)
+
+
+def test_release_workspace_frees_and_recreates():
+    """cos_release_workspace returns the stream's cached workspace to the device; the next call
+    allocates a fresh one and gives the same bits."""
+    import numpy as np
+    n, n_mat, ncfg = 8, 2, 64
+    Ms = I.random_matrices(5, ncfg, n_mat, n, 0.9)
+    order = torch.full((ncfg,), n, dtype=torch.int32, device="cuda")
+    moff = torch.arange(ncfg, dtype=torch.int64, device="cuda") * n_mat * n * n
+    M = torch.tensor(Ms, device="cuda").contiguous()
+    out1 = torch.empty(ncfg, dtype=torch.float64, device="cuda")
+    out2 = torch.empty_like(out1)
+    B.cos_connected_sum_matrices(n, order, moff, n_mat, 1, None, M, "fp64", out1)
+    B.cos_sync_status()
+    free_before = torch.cuda.mem_get_info()[0]
+    B.cos_release_workspace()
+    assert torch.cuda.mem_get_info()[0] > free_before          # the layer ring went back to the device
+    B.cos_connected_sum_matrices(n, order, moff, n_mat, 1, None, M, "fp64", out2)
+    B.cos_sync_status()
+    assert np.array_equal(out1.cpu().numpy(), out2.cpu().numpy())
