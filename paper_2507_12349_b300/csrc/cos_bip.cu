@@ -815,7 +815,7 @@ __device__ __forceinline__ void bip_adj_endpoint(const double *fsrc, double *aou
                                                  const double *__restrict__ a1, const double *__restrict__ Ms,
                                                  const double *__restrict__ Md, double *__restrict__ dM,
                                                  const TgtInfo &ti, uint32_t tslot, uint32_t slot, int vrow, int hc,
-                                                 int qv, double cbar, double gamma, int lane, double &dvout) {
+                                                 int qv, bool live, double cbar, double gamma, int lane, double &gs) {
     constexpr int kSplit = 6;
     // fsrc == aout: the forward state, replaced by its adjoint below (same slot, same thread)
     const double o = fsrc[(size_t)slot * kLanes + lane];
@@ -831,19 +831,24 @@ __device__ __forceinline__ void bip_adj_endpoint(const double *fsrc, double *aou
         bip_adj_chunk<kSplit, 2 * kSplit>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob, qv, dv);
         bip_adj_chunk<2 * kSplit, NT>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob, qv, dv);
     }
-    dvout = qv >= 0 ? dv * o : 0.0;   // D O of the shifted-diagonal step (v,s) -> (v,s)
-    ob = fma(cbar, Md[vrow + hc], ob);
-    if ((__double_as_longlong(cbar) << 1) != 0) dM[vrow + hc] = fma(gamma, o, dM[vrow + hc]);
+    if (qv >= 0) gs = fma(neg(dv), o, gs);   // -D O of the shifted-diagonal step (v,s) -> (v,s)
+    // the close (a mask with a half-visited vertex, or a full mask); a dead mask closes into
+    // nothing (warp-uniform test: no FP64 compare)
+    if (live) {
+        ob = fma(cbar, Md[vrow + hc], ob);
+        dM[vrow + hc] = fma(gamma, o, dM[vrow + hc]);
+    }
     aout[(size_t)slot * kLanes + lane] = ob;
 }
 
 __device__ __forceinline__ void bip_adj_dispatch(int nT, const double *fsrc, double *aout, const double *a1,
                                                  const double *Ms, const double *Md, double *dM, const TgtInfo &ti,
-                                                 uint32_t tslot, uint32_t slot, int vrow, int hc, int qv, double cbar,
-                                                 double gamma, int lane, double &dvout) {
+                                                 uint32_t tslot, uint32_t slot, int vrow, int hc, int qv, bool live,
+                                                 double cbar, double gamma, int lane, double &gs) {
 #define COS_BADJ(K)                                                                                            \
     case K:                                                                                                    \
-        bip_adj_endpoint<K>(fsrc, aout, a1, Ms, Md, dM, ti, tslot, slot, vrow, hc, qv, cbar, gamma, lane, dvout); \
+        bip_adj_endpoint<K>(fsrc, aout, a1, Ms, Md, dM, ti, tslot, slot, vrow, hc, qv, live, cbar, gamma, lane, \
+                            gs);                                                                               \
         break;
     switch (nT) {
         COS_BADJ(0)
@@ -980,16 +985,12 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
             }
         }
         __syncthreads();
+        // dsigma accumulators of this warp's units, per sublattice (summed over warps at the end)
+        s_red[warp][0][lane] = 0.0;
+        s_red[warp][1][lane] = 0.0;
         // the schedule: forward steps split masks over the warps; reverse steps take this warp's
-        // endpoint units (v, s_v); own = vertices with an owned unit
-        uint32_t own2 = 0u, own = 0u;
-        for (int u = warp; u < n2; u += nwarps) {
-            own2 |= 1u << u;
-            own |= 1u << (u >> 1);
-        }
-        const uint32_t full = (1u << n) - 1u;
-        const double gout = active ? a.gout[cfg] : 0.0;
-        double gs0 = 0.0, gs1 = 0.0;
+        // endpoint units (v, s_v).  Only the batch's constants live across it: a reverse step
+        // re-derives its own state, so the forward steps carry no register of the reverse sweep.
         for (int op = 0; op < s_nops; ++op) {
             const int step = s_ops[op];
             if (step >= 256) {
@@ -1007,6 +1008,15 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
                 continue;
             }
             const int ell = step;
+            // own2 = this warp's units (v, s_v), own = the vertices with an owned unit
+            uint32_t own2 = 0u, own = 0u;
+            for (int u = warp; u < n2; u += nwarps) {
+                own2 |= 1u << u;
+                own |= 1u << (u >> 1);
+            }
+            const uint32_t full = (1u << n) - 1u;
+            const double gout = active ? a.gout[cfg] : 0.0;
+            double gs0 = 0.0, gs1 = 0.0;
             double *aout = store + (size_t)s_loc[ell] * kLanes;   // O(ell), replaced by Obar(ell)
             const double *fsrc = aout;
             const double *a1 = store + (size_t)s_loc[ell + 1] * kLanes;
@@ -1022,6 +1032,7 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
                 const int nA = __popc(A);
                 const TgtInfo ti = bip_targets(A, B, S, J, code, tab.rank4, lane);
                 const int nT = __popc(J) + __popc(J & ~A);
+                const bool live = (ones != 0u) || (B == full);
                 double cbar = 0.0;
                 if (B == full) {
                     cbar = CLOW ? gout : ldexp(gout, n - 1);
@@ -1071,15 +1082,16 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
                                 if (!((own2 >> (v * 2 + sv)) & 1u)) continue;
                                 const uint32_t slot = rowbase + (uint32_t)(__popc(A & below) * 2 + sv);
                                 const int vrow = (v * 2 + sv) * n2 * kLanes + lane;
-                                double dvo = 0.0;
-                                bip_adj_dispatch(nT, fsrc, aout, a1, Ms, Md, dM, ti, tslot, slot, vrow, hc, qv, cbar,
-                                                 gamma, lane, dvo);
-                                if (sv) gs1 -= dvo;
-                                else gs0 -= dvo;
+                                bip_adj_dispatch(nT, fsrc, aout, a1, Ms, Md, dM, ti, tslot, slot, vrow, hc, qv, live,
+                                                 cbar, gamma, lane, sv ? gs1 : gs0);
                             }
                         }
                     }
                 }
+            }
+            if (sgrad) {
+                s_red[warp][0][lane] += gs0;
+                s_red[warp][1][lane] += gs1;
             }
             __syncthreads();
         }
@@ -1098,9 +1110,6 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
                 a.gsig[((int64_t)cfg * nfl + lam) * 2 + 1] = -t1;
             }
         } else if (a.gsig) {
-            s_red[warp][0][lane] = gs0;
-            s_red[warp][1][lane] = gs1;
-            __syncthreads();
             if (warp == 0 && active) {
                 double t0 = 0.0, t1 = 0.0;
                 for (int w = 0; w < nwarps; ++w) {
