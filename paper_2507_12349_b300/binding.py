@@ -575,7 +575,7 @@ def measure_peak(kind: int = 0, iters: int = 4096, reps: int = 3, sweep: bool = 
     import torch
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     sms = props.multi_processor_count
-    chains_of = {0: 8, 1: 16, 2: 4, 3: 16, 4: 32}
+    chains_of = {0: 8, 1: 16, 2: 4, 3: 16, 4: 32, 5: 1, 6: 2}
     shapes = [(kind, 256, 8)]
     if sweep and kind == 0:
         shapes = [(k, t, b) for k in (2, 0, 3, 4) for t in (128, 256, 512) for b in (1, 2, 4, 8) if t * b <= 2048]

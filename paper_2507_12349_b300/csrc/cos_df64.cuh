@@ -89,6 +89,59 @@ __device__ __forceinline__ df64 dot_value(DotAcc a) {
     return r;
 }
 
+// ------------------------------------------------------------------ two configurations per instruction
+// The kernels that carry several configurations per lane run the same operation sequence for
+// each of them, so the FP32 arithmetic is issued in packed pairs: sm_100-family packed FP32
+// (.f32x2) performs two round-to-nearest operations in one issue slot, each bit for bit the
+// scalar operation.  A float2 holds one value of configuration pair (x, y).  Subtraction has no
+// CUDA intrinsic; it is the PTX sub.rn.f32x2 instruction.
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long r;
+    const unsigned long long x = (unsigned long long)__float_as_uint(a.x) | ((unsigned long long)__float_as_uint(a.y) << 32);
+    const unsigned long long y = (unsigned long long)__float_as_uint(b.x) | ((unsigned long long)__float_as_uint(b.y) << 32);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+    return make_float2(__uint_as_float((unsigned)r), __uint_as_float((unsigned)(r >> 32)));
+}
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// TwoSum of each component (as two_sum).
+__device__ __forceinline__ float2 two_sum2(float2 a, float2 b, float2 &e) {
+    const float2 s = add2(a, b);
+    const float2 z = sub2(s, a);
+    e = add2(sub2(a, sub2(s, z)), sub2(b, z));
+    return s;
+}
+
+// Compensated dot-product accumulators of two configurations: value = s + c per component.
+struct DotAcc2 {
+    float2 s, c;
+};
+
+// acc += x * y per component, x and y given as (hi, lo) pairs of float2 (dot_add's steps).
+__device__ __forceinline__ void dot_add2(DotAcc2 &acc, float2 xhi, float2 xlo, float2 yhi, float2 ylo) {
+    const float2 p = mul2(xhi, yhi);
+    float2 c = fma2(xhi, yhi, neg2(p));
+    c = fma2(xhi, ylo, c);
+    c = fma2(xlo, yhi, c);
+    float2 e;
+    acc.s = two_sum2(acc.s, p, e);
+    acc.c = add2(acc.c, add2(c, e));
+}
+
+// First term (dot_first's steps).
+__device__ __forceinline__ DotAcc2 dot_first2(float2 xhi, float2 xlo, float2 yhi, float2 ylo) {
+    DotAcc2 a;
+    a.s = mul2(xhi, yhi);
+    float2 c = fma2(xhi, yhi, neg2(a.s));
+    c = fma2(xhi, ylo, c);
+    a.c = fma2(xlo, yhi, c);
+    return a;
+}
+
 // Sum of v over the nfl lanes of configuration ci, identical bits in every lane of the group
 // (df64_add is commutative bit for bit: TwoSum's error term is exact, the lo additions commute).
 __device__ __forceinline__ df64 df64_flavor_sum(df64 v, int nfl, int ci) {

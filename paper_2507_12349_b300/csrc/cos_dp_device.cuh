@@ -130,6 +130,16 @@ __device__ __forceinline__ void close_add(DotAcc &acc, float o, df64 m) {
     acc.c = __fadd_rn(acc.c, __fadd_rn(e, t));
 }
 
+// close_add for two configurations at once (packed FP32, the same operations per component).
+__device__ __forceinline__ void close_add2(DotAcc2 &acc, float2 o, float2 mhi, float2 mlo) {
+    const float2 p = mul2(o, mhi);
+    float2 e = fma2(o, mhi, neg2(p));
+    e = fma2(o, mlo, e);
+    float2 t;
+    acc.s = two_sum2(acc.s, p, t);
+    acc.c = add2(acc.c, add2(e, t));
+}
+
 // -x by flipping the sign bit (integer pipe; FP64 instructions are the scarce resource).
 __device__ __forceinline__ double neg(double x) {
     return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);

@@ -53,7 +53,8 @@ __device__ __forceinline__ void do_row_pair(const FV<P> *__restrict__ src, FV<P>
                                             const FV<P> *__restrict__ Ms, const CV<P> *__restrict__ Md,
                                             const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow, uint32_t A,
                                             uint32_t off, int h, int hidx, int nA, int n, bool needclose, int lane,
-                                            DotAcc (&csum)[P]) {
+                                            DotAcc2 (&csum)[P / 2]) {
+    static_assert(P % 2 == 0, "configurations are taken in packed pairs");
     FV<P> o[NV];
     int vs[NV];
     const FV<P> *row = src + (size_t)(off + (uint32_t)(hidx * nA)) * kLanes + lane;
@@ -70,7 +71,9 @@ __device__ __forceinline__ void do_row_pair(const FV<P> *__restrict__ src, FV<P>
         for (int t = 0; t < NV; ++t) {
             const CV<P> m = Md[vs[t] + h * kLanes];
 #pragma unroll
-            for (int c = 0; c < P; ++c) close_add(csum[c], o[t].v[c], df64{m.hi[c], m.lo[c]});
+            for (int k = 0; k < P / 2; ++k)
+                close_add2(csum[k], make_float2(o[t].v[2 * k], o[t].v[2 * k + 1]),
+                           make_float2(m.hi[2 * k], m.hi[2 * k + 1]), make_float2(m.lo[2 * k], m.lo[2 * k + 1]));
         }
     }
     const uint32_t hlow = (1u << h) - 1u;
@@ -89,9 +92,16 @@ __device__ __forceinline__ void do_row_pair(const FV<P> *__restrict__ src, FV<P>
             const FV<P> ma = Ms[vs[t] + ja * kLanes];
             const FV<P> mb = Ms[vs[t] + jb * kLanes];
 #pragma unroll
-            for (int c = 0; c < P; ++c) {
-                da.v[c] = fmaf(o[t].v[c], ma.v[c], da.v[c]);
-                db.v[c] = fmaf(o[t].v[c], mb.v[c], db.v[c]);
+            for (int k = 0; k < P / 2; ++k) {
+                const float2 ok = make_float2(o[t].v[2 * k], o[t].v[2 * k + 1]);
+                const float2 ra = fma2(ok, make_float2(ma.v[2 * k], ma.v[2 * k + 1]),
+                                       make_float2(da.v[2 * k], da.v[2 * k + 1]));
+                const float2 rb = fma2(ok, make_float2(mb.v[2 * k], mb.v[2 * k + 1]),
+                                       make_float2(db.v[2 * k], db.v[2 * k + 1]));
+                da.v[2 * k] = ra.x;
+                da.v[2 * k + 1] = ra.y;
+                db.v[2 * k] = rb.x;
+                db.v[2 * k + 1] = rb.y;
             }
         }
         push_target_pair<P>(dst1, ti, q, da, hlow, lane);
@@ -106,7 +116,12 @@ __device__ __forceinline__ void do_row_pair(const FV<P> *__restrict__ src, FV<P>
         for (int t = 0; t < NV; ++t) {
             const FV<P> m = Ms[vs[t] + j * kLanes];
 #pragma unroll
-            for (int c = 0; c < P; ++c) d.v[c] = fmaf(o[t].v[c], m.v[c], d.v[c]);
+            for (int k = 0; k < P / 2; ++k) {
+                const float2 r = fma2(make_float2(o[t].v[2 * k], o[t].v[2 * k + 1]),
+                                      make_float2(m.v[2 * k], m.v[2 * k + 1]), make_float2(d.v[2 * k], d.v[2 * k + 1]));
+                d.v[2 * k] = r.x;
+                d.v[2 * k + 1] = r.y;
+            }
         }
         push_target_pair<P>(dst1, ti, q, d, hlow, lane);
     }
@@ -116,7 +131,7 @@ template <int P>
 __device__ __forceinline__ void row_dispatch_pair(int nv, const FV<P> *src, FV<P> *dst1, const FV<P> *Ms,
                                                   const CV<P> *Md, const TgtInfo &ti, int nJ, uint32_t J,
                                                   uint32_t Vrow, uint32_t A, uint32_t off, int h, int hidx, int nA,
-                                                  int n, bool needclose, int lane, DotAcc (&csum)[P]) {
+                                                  int n, bool needclose, int lane, DotAcc2 (&csum)[P / 2]) {
 #define COS_ROW_P(K)                                                                                           \
     case K:                                                                                                    \
         do_row_pair<P, K>(src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, csum);  \
@@ -164,9 +179,9 @@ __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask
         prefetch_block(reinterpret_cast<const double *>(src), (uint32_t)(P / 2) * nk.z, (uint32_t)(P / 2) * ns, lane,
                        prefetch);
     }
-    DotAcc csum[P];
+    DotAcc2 csum[P / 2];
 #pragma unroll
-    for (int c = 0; c < P; ++c) close_init(csum[c]);
+    for (int k = 0; k < P / 2; ++k) csum[k].s = csum[k].c = make_float2(0.0f, 0.0f);
     const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, lane);
     const int nJ = __popc(J);
     for (uint32_t hh = H; hh; hh &= hh - 1u) {
@@ -179,7 +194,11 @@ __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask
     if (!needclose) return;   // no half-visited vertex and not full: disconnected, dropped
     double C[P];
 #pragma unroll
-    for (int c = 0; c < P; ++c) C[c] = flavor_sum(close_value(csum[c]), nfl, ci);
+    for (int c = 0; c < P; ++c) {
+        const DotAcc2 &q = csum[c / 2];
+        const DotAcc acc = (c & 1) ? DotAcc{q.s.y, q.c.y} : DotAcc{q.s.x, q.c.x};
+        C[c] = flavor_sum(close_value(acc), nfl, ci);
+    }
     if (ones) {
         const int k = __ffs(ones) - 1;
         const uint32_t bk = 1u << k;
@@ -216,16 +235,27 @@ __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask
 
 // ---------------------------------------------------------------- double-float, two per lane
 
+// Two df64 values (configurations x and y) of one lane, stored as (hi pair, lo pair) so that each
+// pair is one packed-FP32 operand.
 struct __align__(16) df64x2 {
-    df64 x, y;
+    float2 hi, lo;
 };
+__device__ __forceinline__ df64 dfx(const df64x2 &v) { return df64{v.hi.x, v.lo.x}; }
+__device__ __forceinline__ df64 dfy(const df64x2 &v) { return df64{v.hi.y, v.lo.y}; }
+__device__ __forceinline__ df64x2 dfpair(df64 x, df64 y) {
+    df64x2 r;
+    r.hi = make_float2(x.hi, y.hi);
+    r.lo = make_float2(x.lo, y.lo);
+    return r;
+}
 
-__device__ __forceinline__ void push_target_dfp(df64x2 *__restrict__ dst1, uint32_t tslot, int q, const DotAcc &dx,
-                                                const DotAcc &dy, int lane) {
+// The accumulators are stored as they stand (sum, error) for both configurations.
+__device__ __forceinline__ void push_target_dfp(df64x2 *__restrict__ dst1, uint32_t tslot, int q, const DotAcc2 &d,
+                                                int lane) {
     const uint32_t slot = __shfl_sync(0xFFFFFFFFu, tslot, q);
     df64x2 v;
-    v.x = df64{dx.s, dx.c};
-    v.y = df64{dy.s, dy.c};
+    v.hi = d.s;
+    v.lo = d.c;
     dst1[(size_t)slot * kLanes + lane] = v;
 }
 
@@ -234,7 +264,7 @@ __device__ __forceinline__ void do_row_dfp(const df64x2 *__restrict__ src, df64x
                                            const df64x2 *__restrict__ Ms, const df64x2 *__restrict__ Md,
                                            const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow, uint32_t A,
                                            uint32_t off, int h, int hidx, int nA, int n, bool needclose, int lane,
-                                           DotAcc &cx, DotAcc &cy) {
+                                           DotAcc2 &cc) {
     df64x2 o[NV];
     int vs[NV];
     const df64x2 *row = src + (size_t)(off + (uint32_t)(hidx * nA)) * kLanes + lane;
@@ -250,8 +280,7 @@ __device__ __forceinline__ void do_row_dfp(const df64x2 *__restrict__ src, df64x
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
             const df64x2 m = Md[vs[t] + h * kLanes];
-            dot_add(cx, o[t].x, m.x);
-            dot_add(cy, o[t].y, m.y);
+            dot_add2(cc, o[t].hi, o[t].lo, m.hi, m.lo);
         }
     }
     const uint32_t tslot = row_target_slot(ti, (1u << h) - 1u);
@@ -264,41 +293,38 @@ __device__ __forceinline__ void do_row_dfp(const df64x2 *__restrict__ src, df64x
         jj &= jj - 1u;
         const df64x2 ma0 = Ms[vs[0] + ja * kLanes];
         const df64x2 mb0 = Ms[vs[0] + jb * kLanes];
-        DotAcc ax = dot_first(o[0].x, ma0.x), ay = dot_first(o[0].y, ma0.y);
-        DotAcc bx = dot_first(o[0].x, mb0.x), by = dot_first(o[0].y, mb0.y);
+        DotAcc2 da = dot_first2(o[0].hi, o[0].lo, ma0.hi, ma0.lo);
+        DotAcc2 db = dot_first2(o[0].hi, o[0].lo, mb0.hi, mb0.lo);
 #pragma unroll
         for (int t = 1; t < NV; ++t) {
             const df64x2 ma = Ms[vs[t] + ja * kLanes];
             const df64x2 mb = Ms[vs[t] + jb * kLanes];
-            dot_add(ax, o[t].x, ma.x);
-            dot_add(ay, o[t].y, ma.y);
-            dot_add(bx, o[t].x, mb.x);
-            dot_add(by, o[t].y, mb.y);
+            dot_add2(da, o[t].hi, o[t].lo, ma.hi, ma.lo);
+            dot_add2(db, o[t].hi, o[t].lo, mb.hi, mb.lo);
         }
-        push_target_dfp(dst1, tslot, q, ax, ay, lane);
-        push_target_dfp(dst1, tslot, q + 1, bx, by, lane);
+        push_target_dfp(dst1, tslot, q, da, lane);
+        push_target_dfp(dst1, tslot, q + 1, db, lane);
     }
     if (q < nJ) {
         const int j = __ffs(jj) - 1;
         const df64x2 m0 = Ms[vs[0] + j * kLanes];
-        DotAcc ax = dot_first(o[0].x, m0.x), ay = dot_first(o[0].y, m0.y);
+        DotAcc2 d = dot_first2(o[0].hi, o[0].lo, m0.hi, m0.lo);
 #pragma unroll
         for (int t = 1; t < NV; ++t) {
             const df64x2 m = Ms[vs[t] + j * kLanes];
-            dot_add(ax, o[t].x, m.x);
-            dot_add(ay, o[t].y, m.y);
+            dot_add2(d, o[t].hi, o[t].lo, m.hi, m.lo);
         }
-        push_target_dfp(dst1, tslot, q, ax, ay, lane);
+        push_target_dfp(dst1, tslot, q, d, lane);
     }
 }
 
 __device__ __forceinline__ void row_dispatch_dfp(int nv, const df64x2 *src, df64x2 *dst1, const df64x2 *Ms,
                                                  const df64x2 *Md, const TgtInfo &ti, int nJ, uint32_t J,
                                                  uint32_t Vrow, uint32_t A, uint32_t off, int h, int hidx, int nA,
-                                                 int n, bool needclose, int lane, DotAcc &cx, DotAcc &cy) {
+                                                 int n, bool needclose, int lane, DotAcc2 &cc) {
 #define COS_ROW_DP(K)                                                                                          \
     case K:                                                                                                    \
-        do_row_dfp<K>(src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, cx, cy);    \
+        do_row_dfp<K>(src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, cc);        \
         break;
     switch (nv) {
         COS_ROW_DP(1)
@@ -340,19 +366,19 @@ __device__ __forceinline__ void fwd_mask_dfp(const OrderTab &tab, uint32_t mask_
         const uint32_t ns = (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_));
         prefetch_block(reinterpret_cast<const double *>(src), 2 * nk.z, 2 * ns, lane, prefetch);
     }
-    DotAcc cx = {0.0f, 0.0f}, cy = {0.0f, 0.0f};
+    DotAcc2 cc;
+    cc.s = cc.c = make_float2(0.0f, 0.0f);
     const TgtInfo ti = mask_targets(A, B, J, code, tab.rank3, lane);
     const int nJ = __popc(J);
     for (uint32_t hh = H; hh; hh &= hh - 1u) {
         const int h = __ffs(hh) - 1;
         const int hidx = __popc(H & ((1u << h) - 1u));
         const uint32_t Vrow = row_vmask(A, ones, h);
-        row_dispatch_dfp(__popc(Vrow), src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, cx,
-                         cy);
+        row_dispatch_dfp(__popc(Vrow), src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, cc);
     }
     if (!needclose) return;
-    const df64 Cx = df64_flavor_sum(dot_value(cx), nfl, ci);
-    const df64 Cy = df64_flavor_sum(dot_value(cy), nfl, ci);
+    const df64 Cx = df64_flavor_sum(dot_value(DotAcc{cc.s.x, cc.c.x}), nfl, ci);
+    const df64 Cy = df64_flavor_sum(dot_value(DotAcc{cc.s.y, cc.c.y}), nfl, ci);
     if (ones) {
         const int k = __ffs(ones) - 1;
         const uint32_t bk = 1u << k;
@@ -361,21 +387,17 @@ __device__ __forceinline__ void fwd_mask_dfp(const OrderTab &tab, uint32_t mask_
         const int ai1 = __popc(A & (bk - 1u));
         const uint32_t off1 = __ldg(tab.rank3 + code + c_p3[k]);
         df64x2 *tp = dst1 + (size_t)(off1 + (uint32_t)(hi1 * nA + ai1)) * kLanes + lane;
-        df64x2 val;
-        val.x = Cx;
-        val.y = Cy;
+        df64 vx = Cx, vy = Cy;
         if (!CLOW && ell == 1 && shifts) {   // vertex 0 carries a shift point
-            val.x = df64_add(val.x, seed0);
-            val.y = df64_add(val.y, seed0);
+            vx = df64_add(vx, seed0);
+            vy = df64_add(vy, seed0);
         }
-        if (CLOW && k == 0 && lam == 0) val.x = val.y = df64{0.0f, 0.0f};   // block 1 only
+        if (CLOW && k == 0 && lam == 0) vx = vy = df64{0.0f, 0.0f};   // block 1 only
         if (!CLOW && k == 0) {               // the extension into 0' wrote it
-            df64x2 cur = *tp;
-            cur.x = df64_add(cur.x, val.x);
-            cur.y = df64_add(cur.y, val.y);
-            *tp = cur;
+            const df64x2 cur = *tp;
+            *tp = dfpair(df64_add(dfx(cur), vx), df64_add(dfy(cur), vy));
         } else {
-            *tp = val;
+            *tp = dfpair(vx, vy);
         }
     } else if (lam == 0 && out) {
         if (act_x) {
@@ -526,20 +548,14 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_dfp_kernel(
             }
             const int v = e / n, j = e % n;
             const bool sh = v == j && (CLOW || (j != 0 && shifts));
-            df64x2 m, c;
-            m.x = df64_from(sh ? vx + dshift : vx);
-            m.y = df64_from(sh ? vy + dshift : vy);
-            c.x = df64_from(cfac * ((CLOW && sh) ? vx + dshift : vx));   // CLOW: shifted diagonal in the close too
-            c.y = df64_from(cfac * ((CLOW && sh) ? vy + dshift : vy));
-            Ms[e * kLanes + lane] = m;
-            Md[e * kLanes + lane] = c;
+            Ms[e * kLanes + lane] = dfpair(df64_from(sh ? vx + dshift : vx), df64_from(sh ? vy + dshift : vy));
+            // CLOW: shifted diagonal in the close too
+            Md[e * kLanes + lane] = dfpair(df64_from(cfac * ((CLOW && sh) ? vx + dshift : vx)),
+                                           df64_from(cfac * ((CLOW && sh) ? vy + dshift : vy)));
         }
         if (warp == 0) {
-            df64x2 one;
             const float s0 = (CLOW && lam != 0) ? 0.0f : 1.0f;
-            one.x = df64{s0, 0.0f};
-            one.y = df64{s0, 0.0f};
-            ring[(1 % a.nslots) * a.slot_elems + lane] = one;
+            ring[(1 % a.nslots) * a.slot_elems + lane] = dfpair(df64{s0, 0.0f}, df64{s0, 0.0f});
         }
         __syncthreads();
         for (int ell = 1; ell <= 2 * n; ++ell) {

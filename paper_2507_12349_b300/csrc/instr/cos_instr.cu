@@ -43,19 +43,22 @@ __global__ void convert_check_kernel(int64_t n, const double *in64, const float 
 
 }  // namespace cosinstr
 
-// kind 0 / 1: FP64 / FP32 with 8 / 16 chains per thread; kind 2, 3, 4: FP64 with 4, 16, 32
-// chains (a sweep over instruction-level parallelism).  Work = 2 * blocks * threads * chains *
+// kind 0 / 1: FP64 / FP32 with 8 / 16 chains per thread; kind 2, 3, 4, 5, 6: FP64 with 4, 16,
+// 32, 1, 2 chains (a sweep over instruction-level parallelism; one chain gives the dependent
+// issue latency).  Work = 2 * blocks * threads * chains *
 // iters flops; d_sink holds `blocks` elements of the probed type.
 extern "C" int cos_instr_fma_probe(int kind, int blocks, int threads, int iters, void *d_sink, void *stream) {
     using namespace cosinstr;
-    if (blocks < 1 || threads < 32 || threads > 1024 || iters < 1 || !d_sink || kind < 0 || kind > 4) return -1;
+    if (blocks < 1 || threads < 32 || threads > 1024 || iters < 1 || !d_sink || kind < 0 || kind > 6) return -1;
     cudaStream_t s = (cudaStream_t)stream;
     switch (kind) {
         case 0: fma_probe_kernel<double, 8><<<blocks, threads, 0, s>>>(iters, (double *)d_sink); break;
         case 1: fma_probe_kernel<float, 16><<<blocks, threads, 0, s>>>(iters, (float *)d_sink); break;
         case 2: fma_probe_kernel<double, 4><<<blocks, threads, 0, s>>>(iters, (double *)d_sink); break;
         case 3: fma_probe_kernel<double, 16><<<blocks, threads, 0, s>>>(iters, (double *)d_sink); break;
-        default: fma_probe_kernel<double, 32><<<blocks, threads, 0, s>>>(iters, (double *)d_sink); break;
+        case 4: fma_probe_kernel<double, 32><<<blocks, threads, 0, s>>>(iters, (double *)d_sink); break;
+        case 5: fma_probe_kernel<double, 1><<<blocks, threads, 0, s>>>(iters, (double *)d_sink); break;
+        default: fma_probe_kernel<double, 2><<<blocks, threads, 0, s>>>(iters, (double *)d_sink); break;
     }
     return (int)cudaGetLastError();
 }
