@@ -38,103 +38,90 @@ struct __align__(16) CV {
 // Configurations per lane of the mixed kernel.
 constexpr int kMixedWidth = 4;
 
-template <int P>
-__device__ __forceinline__ void push_target_pair(FV<P> *__restrict__ dst1, const TgtInfo &ti, int q, const FV<P> &d,
-                                                 uint32_t hlow, int lane) {
-    const uint32_t off1 = __shfl_sync(0xFFFFFFFFu, ti.off1, q);
-    const uint32_t meta = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
-    const uint32_t ai1 = meta & 15u, nA1 = (meta >> 4) & 15u;
-    const uint32_t hi1 = (uint32_t)__popc((meta >> 16) & hlow);
-    dst1[(size_t)(off1 + hi1 * nA1 + ai1) * kLanes + lane] = d;
+// 128-bit shared-memory load at a byte address of the shared window (the row steps keep 32-bit
+// addresses per state, so an extension's matrix load costs one add).
+__device__ __forceinline__ float4 lds4(uint32_t addr) {
+    float4 r;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "r"(addr));
+    return r;
 }
 
-template <int P, int NV>
-__device__ __forceinline__ void do_row_pair(const FV<P> *__restrict__ src, FV<P> *__restrict__ dst1,
-                                            const FV<P> *__restrict__ Ms, const CV<P> *__restrict__ Md,
-                                            const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow, uint32_t A,
-                                            uint32_t off, int h, int hidx, int nA, int n, bool needclose, int lane,
-                                            DotAcc2 (&csum)[P / 2]) {
-    static_assert(P % 2 == 0, "configurations are taken in packed pairs");
-    FV<P> o[NV];
-    int vs[NV];
-    const FV<P> *row = src + (size_t)(off + (uint32_t)(hidx * nA)) * kLanes + lane;
+// One row (mu, h) of the mixed mode, four configurations per lane (float4 states: packed pairs
+// (x, y) and (z, w)).  ms / md: shared byte addresses of Ms[0][0][0] and Md[0][0][0]; an entry
+// [v][j] of lane l sits at ((v n + j) 32 + l) times its size (16 bytes, 32 for Md).  The row's
+// target slots are formed lane-parallel once (lane q: extension q) and read with one shuffle per
+// push.
+template <int NV>
+__device__ __forceinline__ void do_row_pair(const FV<4> *__restrict__ src, FV<4> *__restrict__ dst1, uint32_t ms,
+                                            uint32_t md, const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow,
+                                            uint32_t A, uint32_t off, int h, int hidx, int nA, int n, bool needclose,
+                                            int lane, DotAcc2 (&csum)[2]) {
+    float4 o[NV];
+    uint32_t ma[NV];   // byte address of Ms[v_t][0] for this lane
+    const float4 *row = reinterpret_cast<const float4 *>(src) + (size_t)(off + (uint32_t)(hidx * nA)) * kLanes + lane;
     uint32_t vv = Vrow;
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
         const int v = __ffs(vv) - 1;
         vv &= vv - 1u;
         o[t] = row[__popc(A & ((1u << v) - 1u)) * kLanes];
-        vs[t] = v * n * kLanes + lane;
+        ma[t] = ms + (uint32_t)((v * n * kLanes + lane) * 16);
     }
     if (needclose) {
+        // Md[v][h] = 2 (Ms[v][0] - ms) + md + h 32 32 bytes
+        const uint32_t dh = md + (uint32_t)(h * kLanes * 32) - 2u * ms;
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
-            const CV<P> m = Md[vs[t] + h * kLanes];
-#pragma unroll
-            for (int k = 0; k < P / 2; ++k)
-                close_add2(csum[k], make_float2(o[t].v[2 * k], o[t].v[2 * k + 1]),
-                           make_float2(m.hi[2 * k], m.hi[2 * k + 1]), make_float2(m.lo[2 * k], m.lo[2 * k + 1]));
+            const uint32_t a = 2u * ma[t] + dh;
+            const float4 hi = lds4(a), lo = lds4(a + 16u);
+            close_add2(csum[0], make_float2(o[t].x, o[t].y), make_float2(hi.x, hi.y), make_float2(lo.x, lo.y));
+            close_add2(csum[1], make_float2(o[t].z, o[t].w), make_float2(hi.z, hi.w), make_float2(lo.z, lo.w));
         }
     }
-    const uint32_t hlow = (1u << h) - 1u;
+    const uint32_t tslot = row_target_slot(ti, (1u << h) - 1u);
+    float4 *dl = reinterpret_cast<float4 *>(dst1) + lane;
     uint32_t jj = J;
     int q = 0;
     for (; q + 1 < nJ; q += 2) {
-        const int ja = __ffs(jj) - 1;
+        const uint32_t ja = (uint32_t)(__ffs(jj) - 1) * (kLanes * 16);
         jj &= jj - 1u;
-        const int jb = __ffs(jj) - 1;
+        const uint32_t jb = (uint32_t)(__ffs(jj) - 1) * (kLanes * 16);
         jj &= jj - 1u;
-        FV<P> da, db;
-#pragma unroll
-        for (int c = 0; c < P; ++c) da.v[c] = db.v[c] = 0.0f;
+        float2 a0 = make_float2(0.0f, 0.0f), a1 = a0, b0 = a0, b1 = a0;
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
-            const FV<P> ma = Ms[vs[t] + ja * kLanes];
-            const FV<P> mb = Ms[vs[t] + jb * kLanes];
-#pragma unroll
-            for (int k = 0; k < P / 2; ++k) {
-                const float2 ok = make_float2(o[t].v[2 * k], o[t].v[2 * k + 1]);
-                const float2 ra = fma2(ok, make_float2(ma.v[2 * k], ma.v[2 * k + 1]),
-                                       make_float2(da.v[2 * k], da.v[2 * k + 1]));
-                const float2 rb = fma2(ok, make_float2(mb.v[2 * k], mb.v[2 * k + 1]),
-                                       make_float2(db.v[2 * k], db.v[2 * k + 1]));
-                da.v[2 * k] = ra.x;
-                da.v[2 * k + 1] = ra.y;
-                db.v[2 * k] = rb.x;
-                db.v[2 * k + 1] = rb.y;
-            }
+            const float4 ma_ = lds4(ma[t] + ja), mb_ = lds4(ma[t] + jb);
+            const float2 o0 = make_float2(o[t].x, o[t].y), o1 = make_float2(o[t].z, o[t].w);
+            a0 = fma2(o0, make_float2(ma_.x, ma_.y), a0);
+            a1 = fma2(o1, make_float2(ma_.z, ma_.w), a1);
+            b0 = fma2(o0, make_float2(mb_.x, mb_.y), b0);
+            b1 = fma2(o1, make_float2(mb_.z, mb_.w), b1);
         }
-        push_target_pair<P>(dst1, ti, q, da, hlow, lane);
-        push_target_pair<P>(dst1, ti, q + 1, db, hlow, lane);
+        const uint32_t sa = __shfl_sync(0xFFFFFFFFu, tslot, q), sb = __shfl_sync(0xFFFFFFFFu, tslot, q + 1);
+        dl[(size_t)sa * kLanes] = make_float4(a0.x, a0.y, a1.x, a1.y);
+        dl[(size_t)sb * kLanes] = make_float4(b0.x, b0.y, b1.x, b1.y);
     }
     if (q < nJ) {
-        const int j = __ffs(jj) - 1;
-        FV<P> d;
-#pragma unroll
-        for (int c = 0; c < P; ++c) d.v[c] = 0.0f;
+        const uint32_t jo = (uint32_t)(__ffs(jj) - 1) * (kLanes * 16);
+        float2 d0 = make_float2(0.0f, 0.0f), d1 = d0;
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
-            const FV<P> m = Ms[vs[t] + j * kLanes];
-#pragma unroll
-            for (int k = 0; k < P / 2; ++k) {
-                const float2 r = fma2(make_float2(o[t].v[2 * k], o[t].v[2 * k + 1]),
-                                      make_float2(m.v[2 * k], m.v[2 * k + 1]), make_float2(d.v[2 * k], d.v[2 * k + 1]));
-                d.v[2 * k] = r.x;
-                d.v[2 * k + 1] = r.y;
-            }
+            const float4 m = lds4(ma[t] + jo);
+            d0 = fma2(make_float2(o[t].x, o[t].y), make_float2(m.x, m.y), d0);
+            d1 = fma2(make_float2(o[t].z, o[t].w), make_float2(m.z, m.w), d1);
         }
-        push_target_pair<P>(dst1, ti, q, d, hlow, lane);
+        const uint32_t sq = __shfl_sync(0xFFFFFFFFu, tslot, q);
+        dl[(size_t)sq * kLanes] = make_float4(d0.x, d0.y, d1.x, d1.y);
     }
 }
 
-template <int P>
-__device__ __forceinline__ void row_dispatch_pair(int nv, const FV<P> *src, FV<P> *dst1, const FV<P> *Ms,
-                                                  const CV<P> *Md, const TgtInfo &ti, int nJ, uint32_t J,
-                                                  uint32_t Vrow, uint32_t A, uint32_t off, int h, int hidx, int nA,
-                                                  int n, bool needclose, int lane, DotAcc2 (&csum)[P / 2]) {
+__device__ __forceinline__ void row_dispatch_pair(int nv, const FV<4> *src, FV<4> *dst1, uint32_t ms, uint32_t md,
+                                                  const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow, uint32_t A,
+                                                  uint32_t off, int h, int hidx, int nA, int n, bool needclose,
+                                                  int lane, DotAcc2 (&csum)[2]) {
 #define COS_ROW_P(K)                                                                                           \
     case K:                                                                                                    \
-        do_row_pair<P, K>(src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, csum);  \
+        do_row_pair<K>(src, dst1, ms, md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, csum);     \
         break;
     switch (nv) {
         COS_ROW_P(1)
@@ -188,8 +175,9 @@ __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask
         const int h = __ffs(hh) - 1;
         const int hidx = __popc(H & ((1u << h) - 1u));
         const uint32_t Vrow = row_vmask(A, ones, h);
-        row_dispatch_pair<P>(__popc(Vrow), src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose,
-                             lane, csum);
+        row_dispatch_pair(__popc(Vrow), src, dst1, (uint32_t)__cvta_generic_to_shared(Ms),
+                          (uint32_t)__cvta_generic_to_shared(Md), ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose,
+                          lane, csum);
     }
     if (!needclose) return;   // no half-visited vertex and not full: disconnected, dropped
     double C[P];
@@ -259,14 +247,15 @@ __device__ __forceinline__ void push_target_dfp(df64x2 *__restrict__ dst1, uint3
     dst1[(size_t)slot * kLanes + lane] = v;
 }
 
+// One row of the double-float mode.  ms / md: shared byte addresses of Ms and Md (16-byte
+// entries [v][j][lane], as in do_row_pair).
 template <int NV>
-__device__ __forceinline__ void do_row_dfp(const df64x2 *__restrict__ src, df64x2 *__restrict__ dst1,
-                                           const df64x2 *__restrict__ Ms, const df64x2 *__restrict__ Md,
-                                           const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow, uint32_t A,
-                                           uint32_t off, int h, int hidx, int nA, int n, bool needclose, int lane,
-                                           DotAcc2 &cc) {
+__device__ __forceinline__ void do_row_dfp(const df64x2 *__restrict__ src, df64x2 *__restrict__ dst1, uint32_t ms,
+                                           uint32_t md, const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow,
+                                           uint32_t A, uint32_t off, int h, int hidx, int nA, int n, bool needclose,
+                                           int lane, DotAcc2 &cc) {
     df64x2 o[NV];
-    int vs[NV];
+    uint32_t ma[NV];   // byte offset of entry [v_t][0] of this lane
     const df64x2 *row = src + (size_t)(off + (uint32_t)(hidx * nA)) * kLanes + lane;
     uint32_t vv = Vrow;
 #pragma unroll
@@ -274,52 +263,53 @@ __device__ __forceinline__ void do_row_dfp(const df64x2 *__restrict__ src, df64x
         const int v = __ffs(vv) - 1;
         vv &= vv - 1u;
         o[t] = row[__popc(A & ((1u << v) - 1u)) * kLanes];
-        vs[t] = v * n * kLanes + lane;
+        ma[t] = (uint32_t)((v * n * kLanes + lane) * 16);
     }
     if (needclose) {
+        const uint32_t dh = md + (uint32_t)(h * kLanes * 16);
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
-            const df64x2 m = Md[vs[t] + h * kLanes];
-            dot_add2(cc, o[t].hi, o[t].lo, m.hi, m.lo);
+            const float4 m = lds4(ma[t] + dh);
+            dot_add2(cc, o[t].hi, o[t].lo, make_float2(m.x, m.y), make_float2(m.z, m.w));
         }
     }
+#pragma unroll
+    for (int t = 0; t < NV; ++t) ma[t] += ms;
     const uint32_t tslot = row_target_slot(ti, (1u << h) - 1u);
     uint32_t jj = J;
     int q = 0;
     for (; q + 1 < nJ; q += 2) {
-        const int ja = __ffs(jj) - 1;
+        const uint32_t ja = (uint32_t)(__ffs(jj) - 1) * (kLanes * 16);
         jj &= jj - 1u;
-        const int jb = __ffs(jj) - 1;
+        const uint32_t jb = (uint32_t)(__ffs(jj) - 1) * (kLanes * 16);
         jj &= jj - 1u;
-        const df64x2 ma0 = Ms[vs[0] + ja * kLanes];
-        const df64x2 mb0 = Ms[vs[0] + jb * kLanes];
-        DotAcc2 da = dot_first2(o[0].hi, o[0].lo, ma0.hi, ma0.lo);
-        DotAcc2 db = dot_first2(o[0].hi, o[0].lo, mb0.hi, mb0.lo);
+        const float4 ma0 = lds4(ma[0] + ja), mb0 = lds4(ma[0] + jb);
+        DotAcc2 da = dot_first2(o[0].hi, o[0].lo, make_float2(ma0.x, ma0.y), make_float2(ma0.z, ma0.w));
+        DotAcc2 db = dot_first2(o[0].hi, o[0].lo, make_float2(mb0.x, mb0.y), make_float2(mb0.z, mb0.w));
 #pragma unroll
         for (int t = 1; t < NV; ++t) {
-            const df64x2 ma = Ms[vs[t] + ja * kLanes];
-            const df64x2 mb = Ms[vs[t] + jb * kLanes];
-            dot_add2(da, o[t].hi, o[t].lo, ma.hi, ma.lo);
-            dot_add2(db, o[t].hi, o[t].lo, mb.hi, mb.lo);
+            const float4 a_ = lds4(ma[t] + ja), b_ = lds4(ma[t] + jb);
+            dot_add2(da, o[t].hi, o[t].lo, make_float2(a_.x, a_.y), make_float2(a_.z, a_.w));
+            dot_add2(db, o[t].hi, o[t].lo, make_float2(b_.x, b_.y), make_float2(b_.z, b_.w));
         }
         push_target_dfp(dst1, tslot, q, da, lane);
         push_target_dfp(dst1, tslot, q + 1, db, lane);
     }
     if (q < nJ) {
-        const int j = __ffs(jj) - 1;
-        const df64x2 m0 = Ms[vs[0] + j * kLanes];
-        DotAcc2 d = dot_first2(o[0].hi, o[0].lo, m0.hi, m0.lo);
+        const uint32_t jo = (uint32_t)(__ffs(jj) - 1) * (kLanes * 16);
+        const float4 m0 = lds4(ma[0] + jo);
+        DotAcc2 d = dot_first2(o[0].hi, o[0].lo, make_float2(m0.x, m0.y), make_float2(m0.z, m0.w));
 #pragma unroll
         for (int t = 1; t < NV; ++t) {
-            const df64x2 m = Ms[vs[t] + j * kLanes];
-            dot_add2(d, o[t].hi, o[t].lo, m.hi, m.lo);
+            const float4 m = lds4(ma[t] + jo);
+            dot_add2(d, o[t].hi, o[t].lo, make_float2(m.x, m.y), make_float2(m.z, m.w));
         }
         push_target_dfp(dst1, tslot, q, d, lane);
     }
 }
 
-__device__ __forceinline__ void row_dispatch_dfp(int nv, const df64x2 *src, df64x2 *dst1, const df64x2 *Ms,
-                                                 const df64x2 *Md, const TgtInfo &ti, int nJ, uint32_t J,
+__device__ __forceinline__ void row_dispatch_dfp(int nv, const df64x2 *src, df64x2 *dst1, uint32_t Ms, uint32_t Md,
+                                                 const TgtInfo &ti, int nJ, uint32_t J,
                                                  uint32_t Vrow, uint32_t A, uint32_t off, int h, int hidx, int nA,
                                                  int n, bool needclose, int lane, DotAcc2 &cc) {
 #define COS_ROW_DP(K)                                                                                          \
@@ -374,7 +364,9 @@ __device__ __forceinline__ void fwd_mask_dfp(const OrderTab &tab, uint32_t mask_
         const int h = __ffs(hh) - 1;
         const int hidx = __popc(H & ((1u << h) - 1u));
         const uint32_t Vrow = row_vmask(A, ones, h);
-        row_dispatch_dfp(__popc(Vrow), src, dst1, Ms, Md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, cc);
+        row_dispatch_dfp(__popc(Vrow), src, dst1, (uint32_t)__cvta_generic_to_shared(Ms),
+                         (uint32_t)__cvta_generic_to_shared(Md), ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose,
+                         lane, cc);
     }
     if (!needclose) return;
     const df64 Cx = df64_flavor_sum(dot_value(DotAcc{cc.s.x, cc.c.x}), nfl, ci);
@@ -416,7 +408,7 @@ __device__ __forceinline__ void fwd_mask_dfp(const OrderTab &tab, uint32_t mask_
 }  // namespace
 
 // MAXT = 256 (two CTAs of up to 8 warps, <= 128 registers), 384 (two CTAs of up to 12 warps,
-// <= 85) or 512 (one CTA of up to 16 warps, <= 128).
+// <= 85), 512 (one CTA of up to 16 warps, <= 128) or 640 (one CTA of up to 20 warps, <= 102).
 template <int MAXT, bool CLOW>
 __global__ void __launch_bounds__(MAXT, MAXT <= 384 ? 2 : 1) dp_pair_dfp_kernel(const __grid_constant__ DpArgs a);
 
@@ -576,10 +568,11 @@ template <bool CLOW>
 static auto pair_kernel_mode(int precision, int threads) {
     if (precision == COS_DF64)
         return threads <= 256 ? dp_pair_dfp_kernel<256, CLOW>
-                              : (threads <= 384 ? dp_pair_dfp_kernel<384, CLOW> : dp_pair_dfp_kernel<512, CLOW>);
+               : threads <= 384 ? dp_pair_dfp_kernel<384, CLOW>
+               : threads <= 512 ? dp_pair_dfp_kernel<512, CLOW> : dp_pair_dfp_kernel<640, CLOW>;
     return threads <= 256 ? dp_pair_kernel<kMixedWidth, 256, CLOW>
-                          : (threads <= 384 ? dp_pair_kernel<kMixedWidth, 384, CLOW>
-                                            : dp_pair_kernel<kMixedWidth, 512, CLOW>);
+           : threads <= 384 ? dp_pair_kernel<kMixedWidth, 384, CLOW>
+           : threads <= 512 ? dp_pair_kernel<kMixedWidth, 512, CLOW> : dp_pair_kernel<kMixedWidth, 640, CLOW>;
 }
 
 static auto pair_kernel_for(int precision, int threads, bool clow = false) {

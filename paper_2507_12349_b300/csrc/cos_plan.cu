@@ -285,11 +285,11 @@ extern "C" cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts
         // candidates: every (warps, ctas) the occupancy calculator admits, with prefetch into L2;
         // then the best shape again with prefetch off and with prefetch into L1
         std::vector<Tuning> cands;
-        const int warp_c[] = {2, 4, 8, 10, 12, 16};
+        const int warp_c[] = {2, 4, 8, 10, 12, 16, 20};
         const int cta_c[] = {1, 2, 3, 4};
         for (int w : warp_c)
             for (int c : cta_c)
-                if (dp_max_active_ctas(precision, w * 32, smem) >= c) {
+                if ((w <= 16 || precision != COS_FP64) && dp_max_active_ctas(precision, w * 32, smem) >= c) {
                     Tuning cand;
                     cand.warps = w;
                     cand.ctas_per_sm = c;
