@@ -420,7 +420,9 @@ cos_status cos_plan_destroy(cos_plan *plan);
 /* Launch shape of the DP kernel per (order n_max of the launch, precision, matrices per
  * configuration): warps per CTA (1..16), resident CTAs per SM (1..8) and whether a warp
  * prefetches the states of its next mask while it computes the current one (prefetch:
- * 0 = off, 1 = into L2, 2 = into L1).  A launch mixing
+ * 0 = off, 1 = into L2, 2 = into L1; 3 = the mixed and double-float kernels pull each next row's
+ * states into L1 while a row computes, 4 = 3 plus the next mask into L2; the FP64 kernel treats
+ * 3 and 4 as 2).  A launch mixing
  * orders uses the shape of its largest order, which dominates its work (a factor 3-4 per
  * order).  cos_autotune times every shape the occupancy calculator admits on n_cfg
  * synthetic configurations of order n (device buffers allocated for the run), installs the

@@ -105,7 +105,7 @@ void load_tune_file_locked() {
             Tuning t;
             t.warps = w;
             t.ctas_per_sm = c;
-            t.prefetch = got >= 7 ? (pf < 0 ? 0 : (pf > 2 ? 2 : pf)) : 1;
+            t.prefetch = got >= 7 ? (pf < 0 ? 0 : (pf > 4 ? 4 : pf)) : 1;
             g_tune[tune_key(n, prec, nf)] = t;
         }
     }

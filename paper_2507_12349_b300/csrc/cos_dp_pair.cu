@@ -46,6 +46,16 @@ __device__ __forceinline__ float4 lds4(uint32_t addr) {
     return r;
 }
 
+// Pulls `nslots` state slots from slot `off` on (16 bytes per lane: four 128-byte lines a slot)
+// into L1, one line per lane and instruction.  Used one row ahead (prefetch mode 3): the loads of
+// a row are issued together and the warp then computes with nothing in flight, so a warp would
+// otherwise keep about one row of DRAM reads outstanding.
+__device__ __forceinline__ void prefetch_rows_l1(const void *src, uint32_t off, uint32_t nslots, int lane) {
+    const char *base = reinterpret_cast<const char *>(src) + (size_t)off * (kLanes * 16);
+    for (uint32_t l = (uint32_t)lane; l < 4u * nslots; l += kLanes)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(base + (size_t)l * 128));
+}
+
 // One row (mu, h) of the mixed mode, four configurations per lane (float4 states: packed pairs
 // (x, y) and (z, w)).  ms / md: shared byte addresses of Ms[0][0][0] and Md[0][0][0]; an entry
 // [v][j] of lane l sits at ((v n + j) 32 + l) times its size (16 bytes, 32 for Md).  The row's
@@ -158,13 +168,13 @@ __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask
     const uint32_t J = full & ~B & (CLOW ? ~(ones & 1u) : 0xFFFFFFFFu);
     const int nA = __popc(A);
     const bool needclose = (ones != 0u) || (B == full);
-    if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
+    if ((prefetch == 1 || prefetch == 2 || prefetch == 4) && next_index != 0xFFFFFFFFu) {
         // P * 4-byte states: P / 2 rows of 256 bytes per state slot
         const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + next_index));
         const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
         const uint32_t ns = (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_));
         prefetch_block(reinterpret_cast<const double *>(src), (uint32_t)(P / 2) * nk.z, (uint32_t)(P / 2) * ns, lane,
-                       prefetch);
+                       prefetch == 4 ? 1 : prefetch);
     }
     DotAcc2 csum[P / 2];
 #pragma unroll
@@ -175,6 +185,14 @@ __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask
         const int h = __ffs(hh) - 1;
         const int hidx = __popc(H & ((1u << h) - 1u));
         const uint32_t Vrow = row_vmask(A, ones, h);
+        if (prefetch >= 3) {   // the next row of this mask, else the first row of the warp's next mask
+            if (hh & (hh - 1u)) {
+                prefetch_rows_l1(src, off + (uint32_t)((hidx + 1) * nA), (uint32_t)nA, lane);
+            } else if (next_index != 0xFFFFFFFFu) {
+                const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + next_index));
+                prefetch_rows_l1(src, nk.z, (uint32_t)__popc(nk.x & 0xFFFFu), lane);
+            }
+        }
         row_dispatch_pair(__popc(Vrow), src, dst1, (uint32_t)__cvta_generic_to_shared(Ms),
                           (uint32_t)__cvta_generic_to_shared(Md), ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose,
                           lane, csum);
@@ -349,12 +367,12 @@ __device__ __forceinline__ void fwd_mask_dfp(const OrderTab &tab, uint32_t mask_
     const uint32_t J = full & ~B & (CLOW ? ~(ones & 1u) : 0xFFFFFFFFu);
     const int nA = __popc(A);
     const bool needclose = (ones != 0u) || (B == full);
-    if (prefetch > 0 && next_index != 0xFFFFFFFFu) {
+    if ((prefetch == 1 || prefetch == 2 || prefetch == 4) && next_index != 0xFFFFFFFFu) {
         // 16-byte states: two 256-byte lines per warp row, fetched as two double-sized rows
         const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + next_index));
         const uint32_t nA_ = nk.x & 0xFFFFu, nB_ = nk.x >> 16;
         const uint32_t ns = (uint32_t)(__popc(head_set(nB_, nA_ & ~nB_)) * __popc(nA_));
-        prefetch_block(reinterpret_cast<const double *>(src), 2 * nk.z, 2 * ns, lane, prefetch);
+        prefetch_block(reinterpret_cast<const double *>(src), 2 * nk.z, 2 * ns, lane, prefetch == 4 ? 1 : prefetch);
     }
     DotAcc2 cc;
     cc.s = cc.c = make_float2(0.0f, 0.0f);
@@ -364,6 +382,14 @@ __device__ __forceinline__ void fwd_mask_dfp(const OrderTab &tab, uint32_t mask_
         const int h = __ffs(hh) - 1;
         const int hidx = __popc(H & ((1u << h) - 1u));
         const uint32_t Vrow = row_vmask(A, ones, h);
+        if (prefetch >= 3) {   // the next row of this mask, else the first row of the warp's next mask
+            if (hh & (hh - 1u)) {
+                prefetch_rows_l1(src, off + (uint32_t)((hidx + 1) * nA), (uint32_t)nA, lane);
+            } else if (next_index != 0xFFFFFFFFu) {
+                const uint4 nk = __ldg(reinterpret_cast<const uint4 *>(tab.masks + next_index));
+                prefetch_rows_l1(src, nk.z, (uint32_t)__popc(nk.x & 0xFFFFu), lane);
+            }
+        }
         row_dispatch_dfp(__popc(Vrow), src, dst1, (uint32_t)__cvta_generic_to_shared(Ms),
                          (uint32_t)__cvta_generic_to_shared(Md), ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose,
                          lane, cc);

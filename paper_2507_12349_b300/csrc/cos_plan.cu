@@ -226,7 +226,7 @@ extern "C" cos_status cos_set_tuning(int n, cos_precision precision, int n_mat, 
     Tuning t;
     t.warps = warps;
     t.ctas_per_sm = ctas_per_sm;
-    t.prefetch = prefetch < 0 ? 0 : (prefetch > 2 ? 2 : prefetch);
+    t.prefetch = prefetch < 0 ? 0 : (prefetch > 4 ? 4 : prefetch);
     set_tuning(n, precision, n_mat, t);
     return COS_OK;
 }
@@ -283,7 +283,7 @@ extern "C" cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts
         fill_layout_kernel<<<64, 256, 0, s>>>(order, moff, n_cfg, n, stride);
         const size_t smem = dp_smem_bytes(precision, n);
         // candidates: every (warps, ctas) the occupancy calculator admits, with prefetch into L2;
-        // then the best shape again with prefetch off and with prefetch into L1
+        // then the best shape again with prefetch off, into L1, and (mixed, double-float) one row ahead
         std::vector<Tuning> cands;
         const int warp_c[] = {2, 4, 8, 10, 12, 16, 20};
         const int cta_c[] = {1, 2, 3, 4};
@@ -326,7 +326,8 @@ extern "C" cos_status cos_autotune(int n, int n_mat, int loop_weight, int shifts
         }
         if (st == COS_OK && best_t < 1e300) {
             const Tuning shape = best;
-            for (int pf : {0, 2}) {
+            for (int pf : {0, 2, 3, 4}) {
+                if (pf >= 3 && precision == COS_FP64) continue;   // row-ahead: the pair kernels' modes
                 Tuning alt = shape;
                 alt.prefetch = pf;
                 double t = 0.0;
