@@ -85,6 +85,9 @@ def parse():
                    help="profiling runs only: time the all-subsets call (c(S) and a(S) of every vertex subset) "
                         "on the order-8 SU(4) workload's gathered matrices")
     p.add_argument("--order", type=int, default=0, help="with --bipartite or --det: order of the configurations")
+    p.add_argument("--probe", action="store_true",
+                   help="print the GPU's FP64 FMA rates (by chains per thread and warps per SM) and the DRAM rate "
+                        "of scattered 512-byte row traffic (by warps per SM and rows in flight), one JSON line each")
     return p.parse_args()
 
 
@@ -1130,6 +1133,12 @@ def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.probe:
+        import torch
+        from paper_2507_12349_b300 import binding as B
+        torch.cuda.set_device(0)
+        for r in B.probe_sweep():
+            print(json.dumps(r), flush=True)
     elif args.bipartite:
         bipartite_arm(args)
     elif args.det:

@@ -537,7 +537,7 @@ _instr = None
 
 
 def instr_lib():
-    """The benchmark's and tests' instruments (FMA probe, conversion check), built beside
+    """The benchmark's and tests' instruments (FMA probe, scattered-row traffic, conversion check), built beside
     libcos.so into libcos_instr.so; not part of the library's interface."""
     global _instr
     if _instr is None:
@@ -548,6 +548,9 @@ def instr_lib():
         L.cos_instr_fma_probe.restype = ctypes.c_int
         L.cos_instr_convert_check.argtypes = [ctypes.c_int64, vp, vp, vp, vp, vp]
         L.cos_instr_convert_check.restype = ctypes.c_int
+        L.cos_instr_row_traffic.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
+                                            ctypes.c_int64, vp]
+        L.cos_instr_row_traffic.restype = ctypes.c_int
         _instr = L
     return _instr
 
@@ -560,6 +563,64 @@ def _instr_check(rc: int, where: str):
 def fma_probe(kind: int, blocks: int, threads: int, iters: int, sink, stream=None):
     _instr_check(instr_lib().cos_instr_fma_probe(int(kind), int(blocks), int(threads), int(iters), _ptr(sink),
                                                  _stream(stream)), "cos_instr_fma_probe")
+
+
+def row_traffic(mode: int, ilp: int, blocks: int, threads: int, iters: int, src, dst, stream=None):
+    """Scattered 512-byte rows (mode 0 read + write, 1 read, 2 write) over src / dst (equal
+    byte sizes, a multiple of 512)."""
+    nrows = min(src.numel() * src.element_size(), dst.numel() * dst.element_size()) // 512
+    _instr_check(instr_lib().cos_instr_row_traffic(int(mode), int(ilp), int(blocks), int(threads), int(iters),
+                                                   _ptr(src), _ptr(dst), int(nrows), _stream(stream)),
+                 "cos_instr_row_traffic")
+
+
+def probe_sweep(gib: int = 4):
+    """Issue-side rates of this GPU, for the design of the DP kernels: the FP64 FMA rate by
+    independent chains per thread and warps per SM (one CTA per SM), and the DRAM rate of
+    scattered 512-byte row traffic by warps per SM and rows in flight per warp (two buffers of
+    `gib` GiB).  Returns a list of result dicts."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    clock = 2.032e9
+    out = []
+
+    def best_ms(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    for kind, chains in ((5, 1), (6, 2), (2, 4), (0, 8), (3, 16)):
+        for threads in (32, 64, 96, 128, 256, 512):
+            sink = torch.zeros(sms, dtype=torch.float64, device="cuda")
+            it = 4096
+            ms = best_ms(lambda: fma_probe(kind, sms, threads, it, sink))
+            tf = 2.0 * sms * threads * chains * it / (ms * 1e-3) / 1e12
+            out.append({"probe": "fp64_fma", "chains_per_thread": chains, "warps_per_sm": threads // 32,
+                        "tflops": tf, "lanes_per_clk_per_sm_at_2032mhz": tf * 1e12 / 2 / sms / clock})
+    nbytes = gib << 30
+    a = torch.zeros(nbytes // 4, dtype=torch.float32, device="cuda")
+    b = torch.zeros_like(a)
+    iters = 64
+    for threads in (256, 512, 1024):
+        for ilp in (1, 4, 8):
+            ms = best_ms(lambda: row_traffic(0, ilp, sms, threads, iters, a, b))
+            moved = sms * threads / 32 * iters * ilp * 512 * 2
+            out.append({"probe": "row_traffic_read_write", "warps_per_sm": threads // 32, "rows_in_flight": ilp,
+                        "gb_per_s": moved / (ms * 1e-3) / 1e9})
+    for mode, name in ((1, "row_traffic_read"), (2, "row_traffic_write")):
+        ms = best_ms(lambda: row_traffic(mode, 8, sms, 1024, iters, a, b))
+        moved = sms * 1024 / 32 * iters * 8 * 512
+        out.append({"probe": name, "warps_per_sm": 32, "rows_in_flight": 8, "gb_per_s": moved / (ms * 1e-3) / 1e9})
+    del a, b
+    return out
 
 
 def convert_check(in64, in32, narrowed, widened, stream=None):

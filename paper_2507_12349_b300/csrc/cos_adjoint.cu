@@ -59,8 +59,10 @@ struct AdjArgs {
 // NJ = |J| extensions (templated: every load is issued up front and no FP64 instruction is
 // predicated off -- on B300 an FP64 instruction costs 16 SM cycles whether or not its lanes
 // are enabled):
-//   Obar(mu,h,v) = sum_j D_j Ms[v][j] + Cbar Mc[v][h],  dM[v][j] += D_j O,  dM[v][h] += gamma O,
-//   and for half-visited v >= 1 the shifted diagonal: dsigma += sgn D_v O (qv = index of v in J).
+//   Obar(mu,h,v) = sum_j D_j Ms[v][j] + Cbar Mc[v][h],  dM[v][j] += D_j O,  dM[v][h] += gamma O.
+// The close's own diagonal term (v = h) goes to dMd[h] instead of dM[h][h], so that dM[v][v]
+// holds only the extension terms D_v O, whose sum over v >= 1 is dc/dsigma / sgn (the shifted
+// diagonal): dsigma costs no multiply-add in the sweep.
 // D_j = Obar(mu + e_j, h, j) is addressed through the mask's lane-parallel target table
 // (mask_targets, shared with the forward push).  Cbar enters last, so its load overlaps the
 // row's target loads.
@@ -68,7 +70,7 @@ struct AdjArgs {
 template <int Q0, int Q1>
 __device__ __forceinline__ void adj_chunk(const double *__restrict__ a1, const double *__restrict__ Ms,
                                           double *__restrict__ dM, const TgtInfo &ti, uint32_t &jr, uint32_t hlow,
-                                          int vrow, double o, int lane, double &ob, int qv, double &dv) {
+                                          int vrow, double o, int lane, double &ob) {
     constexpr int K = Q1 - Q0;
     double D[K], Mv[K], G[K];
     int js[K];
@@ -89,54 +91,52 @@ __device__ __forceinline__ void adj_chunk(const double *__restrict__ a1, const d
     for (int u = 0; u < K; ++u) {
         ob = fma(D[u], Mv[u], ob);
         dM[vrow + js[u] * kLanes] = fma(D[u], o, G[u]);
-        dv = (Q0 + u == qv) ? D[u] : dv;   // register select, no FP64 op
     }
 }
 
-template <bool SG, int NJ>
+template <int NJ>
 __device__ __forceinline__ double adj_endpoint(double *st, const double *__restrict__ a1,
                                                const double *__restrict__ Ms, const double *__restrict__ Mc,
-                                               double *__restrict__ dM, const TgtInfo &ti, uint32_t J, int v,
-                                               uint32_t slot, int qv, int h, int n, bool live, double cbar,
-                                               double gamma, int lane, double &gs) {
+                                               double *__restrict__ dM, double *__restrict__ dMd, const TgtInfo &ti,
+                                               uint32_t J, int v, uint32_t slot, int h, int n, bool live,
+                                               double cbar, double gamma, int lane) {
     constexpr int kSplit = 6;   // at most 6 extensions' operands in registers at a time
     // the forward state O(mu,h,v), replaced by its adjoint below (same slot, same thread)
     const double o = st[(size_t)slot * kLanes + lane];
     const int vrow = v * n * kLanes + lane;
     const uint32_t hlow = (1u << h) - 1u;
     uint32_t jr = J;
-    double ob = 0.0, dv = 0.0;
+    double ob = 0.0;
     if constexpr (NJ == 0) {
         // full mask: the close into the sink only
     } else if constexpr (NJ <= kSplit) {
-        adj_chunk<0, NJ>(a1, Ms, dM, ti, jr, hlow, vrow, o, lane, ob, qv, dv);
+        adj_chunk<0, NJ>(a1, Ms, dM, ti, jr, hlow, vrow, o, lane, ob);
     } else {
-        adj_chunk<0, kSplit>(a1, Ms, dM, ti, jr, hlow, vrow, o, lane, ob, qv, dv);
-        adj_chunk<kSplit, NJ>(a1, Ms, dM, ti, jr, hlow, vrow, o, lane, ob, qv, dv);
+        adj_chunk<0, kSplit>(a1, Ms, dM, ti, jr, hlow, vrow, o, lane, ob);
+        adj_chunk<kSplit, NJ>(a1, Ms, dM, ti, jr, hlow, vrow, o, lane, ob);
     }
-    if (SG && qv >= 0) gs = fma(neg(dv), o, gs);   // sgn = -1
     // the close (a mask with a half-visited vertex, or the full mask); a dead mask closes into
     // nothing (warp-uniform test: no FP64 compare on the scarce pipe)
     if (live) {
         const int vh = vrow + h * kLanes;
         ob = fma(cbar, Mc[vh], ob);
-        dM[vh] = fma(gamma, o, dM[vh]);
+        double *dp = (v == h) ? dMd + h * kLanes + lane : dM + vh;   // integer select of the address
+        *dp = fma(gamma, o, *dp);
     }
     st[(size_t)slot * kLanes + lane] = ob;
     return ob;
 }
 
 // MAXNJ: the largest order the kernel instance runs (larger counts are never dispatched).
-template <bool SG, int MAXNJ>
+template <int MAXNJ>
 __device__ __forceinline__ double adj_endpoint_dispatch(int nJ, double *st, const double *a1, const double *Ms,
-                                                        const double *Mc, double *dM, const TgtInfo &ti, uint32_t J,
-                                                        int v, uint32_t slot, int qv, int h, int n, bool live,
-                                                        double cbar, double gamma, int lane, double &gs) {
+                                                        const double *Mc, double *dM, double *dMd, const TgtInfo &ti,
+                                                        uint32_t J, int v, uint32_t slot, int h, int n, bool live,
+                                                        double cbar, double gamma, int lane) {
 #define COS_AEP(K)                                                                                             \
     case K:                                                                                                    \
         if constexpr (K <= MAXNJ)                                                                              \
-            return adj_endpoint<SG, K>(st, a1, Ms, Mc, dM, ti, J, v, slot, qv, h, n, live, cbar, gamma, lane,   \
-                                       gs);                                                                    \
+            return adj_endpoint<K>(st, a1, Ms, Mc, dM, dMd, ti, J, v, slot, h, n, live, cbar, gamma, lane);   \
         break;
     switch (nJ) {
         COS_AEP(0)
@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
     const int nsm = f.smem_n * f.smem_n * kLanes;
     double *Ms = smem_d;              // extension matrices, shifted diagonal
     double *Mc = smem_d + nsm;        // close matrices times sgn w
-    double *dM = smem_d + 2 * nsm;    // dc/dM accumulators [v][j][lane]
+    double *dM = smem_d + 2 * nsm;    // dc/dM accumulators [v][j][lane] (diagonal: extensions only)
+    double *dMd = smem_d + 3 * nsm;   // the closes' diagonal terms [h][lane]
     double *store = reinterpret_cast<double *>(f.scratch) + (size_t)blockIdx.x * a.cta_elems;
     double *cplane = store + a.store_elems;   // two planes of close adjoints, by layer parity
     const int nfl = f.nf_lanes;
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
                 Mc[e * kLanes + lane] = cfac * val;
             }
             dM[e * kLanes + lane] = 0.0;
+            if (v == j) dMd[v * kLanes + lane] = 0.0;
         }
         if (threadIdx.x == 0) {
             // layer places: checkpoints (layer 1 and the plan's layers) back to back, then the
@@ -329,11 +331,8 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
                         for (uint32_t vv = row_vmask(A, ones, h) & own; vv; vv &= vv - 1u) {
                             const int v = __ffs(vv) - 1;
                             const uint32_t slot = rowoff + (uint32_t)__popc(A & ((1u << v) - 1u));
-                            // half-visited v >= 1: its index among the extensions (v is in J)
-                            const int qv =
-                                (SG && !CLOW && v != 0 && (ones & (1u << v))) ? __popc(J & ((1u << v) - 1u)) : -1;
-                            const double ob = adj_endpoint_dispatch<SG, (MAXT <= 320 ? 10 : 12)>(
-                                nJ, st, a1, Ms, Mc, dM, ti, J, v, slot, qv, h, n, live, cbar, gamma, lane, gs);
+                            const double ob = adj_endpoint_dispatch<(MAXT <= 320 ? 10 : 12)>(
+                                nJ, st, a1, Ms, Mc, dM, dMd, ti, J, v, slot, h, n, live, cbar, gamma, lane);
                             if (v == h && ((B >> h) & 1u)) {
                                 // (mu, h, h) with h full is the seed slot of mu - e_h's close (the loop
                                 // opened at h and has not moved): its flavor sum is that mask's Cbar
@@ -350,20 +349,26 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
         // dM rows are final (every warp passed the last barrier); dsigma: sum over warps in order
         if (active && a.gM) {
             const int64_t gb = (a.gmoff ? a.gmoff[cfg] : (int64_t)cfg * a.gmstride) + (int64_t)lam * n * n;
-            for (int e = warp; e < n * n; e += nwarps) a.gM[gb + e] = dM[e * kLanes + lane];
+            for (int e = warp; e < n * n; e += nwarps) {
+                const int v = e / n;
+                const double d = dM[e * kLanes + lane];
+                a.gM[gb + e] = (v == e % n) ? d + dMd[v * kLanes + lane] : d;
+            }
         }
         if (CLOW && a.gsig) {   // dc/dalpha_b = -trace(dc/dM_b)
             if (warp == 0 && active) {
                 double t = 0.0;
-                for (int j = 0; j < n; ++j) t += dM[(j * n + j) * kLanes + lane];
+                for (int j = 0; j < n; ++j) t += dM[(j * n + j) * kLanes + lane] + dMd[j * kLanes + lane];
                 a.gsig[(int64_t)cfg * nfl + lam] = -t;
             }
         } else if (SG) {
+            // dsigma = sgn sum_{v >= 1} (extension part of dc/dM[v][v]) + the shifted start
             s_red[warp][lane] = gs;
             __syncthreads();
             if (warp == 0 && active && a.gsig) {
                 double s = 0.0;
                 for (int w = 0; w < nwarps; ++w) s += s_red[w][lane];
+                for (int v = 1; v < n; ++v) s = fma(sgn, dM[(v * n + v) * kLanes + lane], s);
                 a.gsig[(int64_t)cfg * nfl + lam] = s;
             }
         }
@@ -559,7 +564,7 @@ cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, 
     const size_t plane_elems = (size_t)ho.max_masks * kLanes;
     const int warps = adjoint_warps(n_max);
     const int threads = warps * 32;
-    const size_t smem = (size_t)3 * n_max * n_max * kLanes * sizeof(double);
+    const size_t smem = ((size_t)3 * n_max * n_max + n_max) * kLanes * sizeof(double);
     const bool sg = gsig != nullptr;
     const bool big = threads > 320;
     auto kern = L.clow ? (big ? dp_adjoint_kernel<false, 384, true> : dp_adjoint_kernel<false, 320, true>)

@@ -224,3 +224,19 @@ def test_bipartite_argument_errors():
     assert lib.cos_forward(ctypes.byref(prob(1, 0, 0, 0, 4, n_mat=1, wt=1)), None, None, None) == 0
     inf = B.cos_structure_info()
     assert lib.cos_bipartite_structure(10, ctypes.byref(inf)) == -2
+
+
+def test_instrument_library_exports_and_rejects_bad_arguments():
+    """The benchmark's instruments live in their own library (not libcos): it loads without a
+    device, exports its three entry points, and turns bad arguments into -1 before any launch."""
+    L = B.instr_lib()
+    for name in ("cos_instr_fma_probe", "cos_instr_row_traffic", "cos_instr_convert_check"):
+        assert hasattr(L, name), name
+        assert not hasattr(B.lib(), name), name
+    assert L.cos_instr_fma_probe(9, 1, 32, 1, 8, None) == -1          # unknown kind
+    assert L.cos_instr_fma_probe(0, 1, 16, 1, 8, None) == -1          # fewer than a warp
+    assert L.cos_instr_row_traffic(3, 1, 1, 32, 1, 8, 8, 1, None) == -1   # unknown mode
+    assert L.cos_instr_row_traffic(0, 2, 1, 32, 1, 8, 8, 1, None) == -1   # unsupported rows in flight
+    assert L.cos_instr_row_traffic(0, 1, 1, 32, 1, 8, 8, 0, None) == -1   # no rows
+    assert L.cos_instr_row_traffic(0, 1, 1, 32, 1, None, 8, 1, None) == -1
+    assert L.cos_instr_convert_check(-1, None, None, None, None, None) == -1
