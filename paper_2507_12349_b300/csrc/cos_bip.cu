@@ -789,7 +789,7 @@ struct BipAdjArgs {
 template <int Q0, int Q1>
 __device__ __forceinline__ void bip_adj_chunk(const double *__restrict__ a1, const double *__restrict__ Ms,
                                               double *__restrict__ dM, const TgtInfo &ti, uint32_t tslot, int vrow,
-                                              double o, int lane, double &ob, int qv, double &dv) {
+                                              double o, int lane, double &ob) {
     constexpr int K = Q1 - Q0;
     double D[K], Mv[K], G[K];
     int cs[K];
@@ -806,7 +806,6 @@ __device__ __forceinline__ void bip_adj_chunk(const double *__restrict__ a1, con
     for (int u = 0; u < K; ++u) {
         ob = fma(D[u], Mv[u], ob);
         dM[vrow + cs[u]] = fma(D[u], o, G[u]);
-        dv = (Q0 + u == qv) ? D[u] : dv;   // register select
     }
 }
 
@@ -814,41 +813,40 @@ template <int NT>
 __device__ __forceinline__ void bip_adj_endpoint(const double *fsrc, double *aout,
                                                  const double *__restrict__ a1, const double *__restrict__ Ms,
                                                  const double *__restrict__ Md, double *__restrict__ dM,
-                                                 const TgtInfo &ti, uint32_t tslot, uint32_t slot, int vrow, int hc,
-                                                 int qv, bool live, double cbar, double gamma, int lane, double &gs) {
+                                                 double *__restrict__ cdp, const TgtInfo &ti, uint32_t tslot,
+                                                 uint32_t slot, int vrow, int hc, bool live, double cbar, double gamma,
+                                                 int lane) {
     constexpr int kSplit = 6;
     // fsrc == aout: the forward state, replaced by its adjoint below (same slot, same thread)
     const double o = fsrc[(size_t)slot * kLanes + lane];
-    double ob = 0.0, dv = 0.0;
+    double ob = 0.0;
     if constexpr (NT == 0) {
     } else if constexpr (NT <= kSplit) {
-        bip_adj_chunk<0, NT>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob, qv, dv);
+        bip_adj_chunk<0, NT>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob);
     } else if constexpr (NT <= 2 * kSplit) {
-        bip_adj_chunk<0, kSplit>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob, qv, dv);
-        bip_adj_chunk<kSplit, NT>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob, qv, dv);
+        bip_adj_chunk<0, kSplit>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob);
+        bip_adj_chunk<kSplit, NT>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob);
     } else {
-        bip_adj_chunk<0, kSplit>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob, qv, dv);
-        bip_adj_chunk<kSplit, 2 * kSplit>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob, qv, dv);
-        bip_adj_chunk<2 * kSplit, NT>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob, qv, dv);
+        bip_adj_chunk<0, kSplit>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob);
+        bip_adj_chunk<kSplit, 2 * kSplit>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob);
+        bip_adj_chunk<2 * kSplit, NT>(a1, Ms, dM, ti, tslot, vrow, o, lane, ob);
     }
-    if (qv >= 0) gs = fma(neg(dv), o, gs);   // -D O of the shifted-diagonal step (v,s) -> (v,s)
     // the close (a mask with a half-visited vertex, or a full mask); a dead mask closes into
     // nothing (warp-uniform test: no FP64 compare)
     if (live) {
         ob = fma(cbar, Md[vrow + hc], ob);
-        dM[vrow + hc] = fma(gamma, o, dM[vrow + hc]);
+        *cdp = fma(gamma, o, *cdp);   // dM[(v,s)][(h,t)], or the closes' diagonal array when equal
     }
     aout[(size_t)slot * kLanes + lane] = ob;
 }
 
 __device__ __forceinline__ void bip_adj_dispatch(int nT, const double *fsrc, double *aout, const double *a1,
-                                                 const double *Ms, const double *Md, double *dM, const TgtInfo &ti,
-                                                 uint32_t tslot, uint32_t slot, int vrow, int hc, int qv, bool live,
-                                                 double cbar, double gamma, int lane, double &gs) {
+                                                 const double *Ms, const double *Md, double *dM, double *cdp,
+                                                 const TgtInfo &ti, uint32_t tslot, uint32_t slot, int vrow, int hc,
+                                                 bool live, double cbar, double gamma, int lane) {
 #define COS_BADJ(K)                                                                                            \
     case K:                                                                                                    \
-        bip_adj_endpoint<K>(fsrc, aout, a1, Ms, Md, dM, ti, tslot, slot, vrow, hc, qv, live, cbar, gamma, lane, \
-                            gs);                                                                               \
+        bip_adj_endpoint<K>(fsrc, aout, a1, Ms, Md, dM, cdp, ti, tslot, slot, vrow, hc, live, cbar, gamma, lane); \
         break;
     switch (nT) {
         COS_BADJ(0)
@@ -892,6 +890,9 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
     __shared__ int s_ops[6 * kBipAdjMaxN + 2];
     __shared__ int s_nops;
     __shared__ double s_red[16][2][kLanes];
+    // the closes' diagonal terms dM[(h,t)][(h,t)], kept apart so that the diagonal of dM holds only
+    // extension terms (their sum over v >= 1 per sublattice is dc/dsigma / sgn)
+    __shared__ double s_dmd[2 * kBipAdjMaxN][kLanes];
     const BipArgs &f = a.f;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -942,6 +943,7 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
                 Md[e * kLanes + lane] = cfac * val;
             }
             dM[e * kLanes + lane] = 0.0;
+            if (r == c) s_dmd[r][lane] = 0.0;
         }
         if (threadIdx.x == 0) {
             // layer places: checkpoints (layer 1 and the plan's layers) back to back, then the
@@ -1075,15 +1077,14 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
                             const bool half = (ones & bv) != 0;
                             const int sv0 = half ? (int)((S >> v) & 1u) : (v == h ? sh : 0);
                             const int sv1 = (half || v == h) ? sv0 : 1;
-                            // a half-visited v >= 1 is its own extension target (index qv)
                             const uint32_t below = bv - 1u;
-                            const int qv = (sgrad && half && v != 0) ? __popc(J & below) + __popc(J & ~A & below) : -1;
                             for (int sv = sv0; sv <= sv1; ++sv) {
                                 if (!((own2 >> (v * 2 + sv)) & 1u)) continue;
                                 const uint32_t slot = rowbase + (uint32_t)(__popc(A & below) * 2 + sv);
                                 const int vrow = (v * 2 + sv) * n2 * kLanes + lane;
-                                bip_adj_dispatch(nT, fsrc, aout, a1, Ms, Md, dM, ti, tslot, slot, vrow, hc, qv, live,
-                                                 cbar, gamma, lane, sv ? gs1 : gs0);
+                                double *cdp = (v == h && sv == sh) ? &s_dmd[h * 2 + sh][lane] : dM + vrow + hc;
+                                bip_adj_dispatch(nT, fsrc, aout, a1, Ms, Md, dM, cdp, ti, tslot, slot, vrow, hc, live,
+                                                 cbar, gamma, lane);
                             }
                         }
                     }
@@ -1097,14 +1098,18 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
         }
         if (active && a.gM) {
             const int64_t gb = f.moff[cfg] + (int64_t)lam * n2 * n2;
-            for (int e = warp; e < n2 * n2; e += nwarps) a.gM[gb + e] = dM[e * kLanes + lane];
+            for (int e = warp; e < n2 * n2; e += nwarps) {
+                const int r = e / n2;
+                const double d = dM[e * kLanes + lane];
+                a.gM[gb + e] = (r == e % n2) ? d + s_dmd[r][lane] : d;
+            }
         }
         if (CLOW) {
             if (a.gsig && warp == 0 && active) {   // dc/dalpha_{b,s} = -sum_j dc/dM_b[(j,s)][(j,s)]
                 double t0 = 0.0, t1 = 0.0;
                 for (int j = 0; j < n; ++j) {
-                    t0 += dM[((2 * j) * n2 + 2 * j) * kLanes + lane];
-                    t1 += dM[((2 * j + 1) * n2 + 2 * j + 1) * kLanes + lane];
+                    t0 += dM[((2 * j) * n2 + 2 * j) * kLanes + lane] + s_dmd[2 * j][lane];
+                    t1 += dM[((2 * j + 1) * n2 + 2 * j + 1) * kLanes + lane] + s_dmd[2 * j + 1][lane];
                 }
                 a.gsig[((int64_t)cfg * nfl + lam) * 2] = -t0;
                 a.gsig[((int64_t)cfg * nfl + lam) * 2 + 1] = -t1;
@@ -1115,6 +1120,11 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
                 for (int w = 0; w < nwarps; ++w) {
                     t0 += s_red[w][0][lane];
                     t1 += s_red[w][1][lane];
+                }
+                // the shifted diagonal (v >= 1): sgn times the extension part of dc/dM[(v,s)][(v,s)]
+                for (int v = 1; v < n; ++v) {
+                    t0 = fma(sgn, dM[((2 * v) * n2 + 2 * v) * kLanes + lane], t0);
+                    t1 = fma(sgn, dM[((2 * v + 1) * n2 + 2 * v + 1) * kLanes + lane], t1);
                 }
                 a.gsig[((int64_t)cfg * nfl + lam) * 2] = t0;
                 a.gsig[((int64_t)cfg * nfl + lam) * 2 + 1] = t1;
