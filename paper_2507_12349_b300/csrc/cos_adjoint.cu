@@ -177,14 +177,14 @@ __device__ __forceinline__ void adj_forward_layer(const OrderTab &tab, int ell, 
 // entry summed in a fixed order (bitwise reproducible).  Every warp walks every mask of a layer
 // and takes the rows' endpoints it owns.  The forward passes split masks across warps as in the
 // forward kernel.  MAXT = 320 (orders <= 10, two CTAs per SM) or 384 (one CTA).
-template <bool SG, int MAXT, bool CLOW = false>
+// UW: loop weight 1, so sgn w Cbar is a sign flip (no FP64 instruction).
+template <bool SG, int MAXT, bool CLOW = false, bool UW = true>
 __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(const __grid_constant__ AdjArgs a) {
     extern __shared__ __align__(16) double smem_d[];
     __shared__ int s_batch;
     __shared__ uint32_t s_loc[kMaxLayers + 2];   // slot offset of each layer in the CTA's store
     __shared__ int s_seg[kMaxLayers + 1];        // segment starts: layer 1, then the checkpoints
     __shared__ int s_nseg;
-    __shared__ double s_red[MAXT / 32][kLanes];
     const DpArgs &f = a.f;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -203,7 +203,6 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
     const double sig = f.sigma[lam];
     const bool shifts = f.shifts != 0;
     const double cfac = sgn * f.loop_weight;
-    const bool unit_weight = f.loop_weight == 1.0;
     const int nbatch = *f.n_batches;
 
     for (;;) {
@@ -272,7 +271,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
         for (int v = warp; v < n; v += nwarps) own |= 1u << v;
         const uint32_t full = (1u << n) - 1u;
         const double gout = active ? a.gout[cfg] : 0.0;
-        double gs = 0.0;
+        const double cbar_full = CLOW ? gout : ldexp(gout, n - 1);   // Cbar of the full mask (the sink)
         for (int sg = s_nseg - 1; sg >= 0; --sg) {
             const int lo = s_seg[sg], hi = (sg + 1 < s_nseg) ? s_seg[sg + 1] : 2 * n + 1;
             // refill the segment area from its checkpoint (the last segment is still in place)
@@ -312,18 +311,11 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
                     const bool live = (ones != 0u) || (B == full);
                     double cbar = 0.0;
                     if (B == full) {
-                        cbar = CLOW ? gout : ldexp(gout, n - 1);
+                        cbar = cbar_full;
                     } else if (ones) {
                         cbar = cin[(size_t)mi * kLanes + lane];   // flavor-summed by the seed slot's owner
-                        // shifted start (mask e_0, owned by the warp of vertex 0), weight sgn 2 sigma:
-                        // the adjoint of the seed slot (2 e_0, 0, 0) itself
-                        if (SG && !CLOW && ell == 1) {
-                            const uint32_t off1 = __ldg(tab.rank3 + code + c_p3[0]);
-                            gs = fma(sgn * 2.0, a1[(size_t)off1 * kLanes + lane], gs);
-                        }
                     }
-                    // loop weight 1: sgn w Cbar is a sign flip (integer pipe), else one multiply
-                    const double gamma = unit_weight ? neg(cbar) : cfac * cbar;
+                    const double gamma = UW ? neg(cbar) : cfac * cbar;
                     for (uint32_t hh = H; hh; hh &= hh - 1u) {
                         const int h = __ffs(hh) - 1;
                         const int hidx = __popc(H & ((1u << h) - 1u));
@@ -362,12 +354,11 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 320 ? 2 : 1) dp_adjoint_kernel(c
                 a.gsig[(int64_t)cfg * nfl + lam] = -t;
             }
         } else if (SG) {
-            // dsigma = sgn sum_{v >= 1} (extension part of dc/dM[v][v]) + the shifted start
-            s_red[warp][lane] = gs;
-            __syncthreads();
+            // dsigma = sgn 2 Obar(2 e_0, 0, 0) (the shifted start: the seed slot of mask e_0's close,
+            // mask code 1 + 3^0 in layer 2, still in place) + sgn sum_{v >= 1} (extension part of
+            // dc/dM[v][v])
             if (warp == 0 && active && a.gsig) {
-                double s = 0.0;
-                for (int w = 0; w < nwarps; ++w) s += s_red[w][lane];
+                double s = sgn * 2.0 * store[(size_t)(s_loc[2] + __ldg(tab.rank3 + 2u)) * kLanes + lane];
                 for (int v = 1; v < n; ++v) s = fma(sgn, dM[(v * n + v) * kLanes + lane], s);
                 a.gsig[(int64_t)cfg * nfl + lam] = s;
             }
@@ -567,9 +558,13 @@ cos_status launch_adjoint(Workspace *ws, const DpLaunch &L, const double *gout, 
     const size_t smem = ((size_t)3 * n_max * n_max + n_max) * kLanes * sizeof(double);
     const bool sg = gsig != nullptr;
     const bool big = threads > 320;
+    const bool uw = L.loop_weight == 1;
     auto kern = L.clow ? (big ? dp_adjoint_kernel<false, 384, true> : dp_adjoint_kernel<false, 320, true>)
-                       : sg ? (big ? dp_adjoint_kernel<true, 384> : dp_adjoint_kernel<true, 320>)
-                            : (big ? dp_adjoint_kernel<false, 384> : dp_adjoint_kernel<false, 320>);
+                : uw   ? (sg ? (big ? dp_adjoint_kernel<true, 384> : dp_adjoint_kernel<true, 320>)
+                             : (big ? dp_adjoint_kernel<false, 384> : dp_adjoint_kernel<false, 320>))
+                       : (sg ? (big ? dp_adjoint_kernel<true, 384, false, false> : dp_adjoint_kernel<true, 320, false, false>)
+                             : (big ? dp_adjoint_kernel<false, 384, false, false>
+                                    : dp_adjoint_kernel<false, 320, false, false>));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint smem attribute");
     int nsm = 1;
