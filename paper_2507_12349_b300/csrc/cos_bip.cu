@@ -880,7 +880,8 @@ constexpr int kBipAdjMaxN = COS_BIP_NMAX;
 // memory (coalesced per warp, mostly L1 / L2 resident).
 constexpr int kBipAdjSmemMaxN = 8;
 
-template <bool CLOW>
+// UW: loop weight 1, so sgn w Cbar is a sign flip (no FP64 instruction).
+template <bool CLOW, bool UW = true>
 __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_constant__ BipAdjArgs a) {
     extern __shared__ __align__(16) double smem_ba[];
     __shared__ int s_batch;
@@ -889,7 +890,6 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
     // layer, then the refills of segments), else a reverse step
     __shared__ int s_ops[6 * kBipAdjMaxN + 2];
     __shared__ int s_nops;
-    __shared__ double s_red[16][2][kLanes];
     // the closes' diagonal terms dM[(h,t)][(h,t)], kept apart so that the diagonal of dM holds only
     // extension terms (their sum over v >= 1 per sublattice is dc/dsigma / sgn)
     __shared__ double s_dmd[2 * kBipAdjMaxN][kLanes];
@@ -913,9 +913,7 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
         seedsh[s2] = sgn * 2.0 * sig[s2];
     }
     const bool shifts = f.shifts != 0 && !CLOW;
-    const bool sgrad = a.gsig != nullptr && !CLOW;   // dc/dsigma, also at sigma = 0
     const double cfac = sgn * f.loop_weight;
-    const bool unit_weight = f.loop_weight == 1.0;
     const int nbatch = *f.n_batches;
     for (;;) {
         __syncthreads();
@@ -987,9 +985,6 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
             }
         }
         __syncthreads();
-        // dsigma accumulators of this warp's units, per sublattice (summed over warps at the end)
-        s_red[warp][0][lane] = 0.0;
-        s_red[warp][1][lane] = 0.0;
         // the schedule: forward steps split masks over the warps; reverse steps take this warp's
         // endpoint units (v, s_v).  Only the batch's constants live across it: a reverse step
         // re-derives its own state, so the forward steps carry no register of the reverse sweep.
@@ -1018,7 +1013,7 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
             }
             const uint32_t full = (1u << n) - 1u;
             const double gout = active ? a.gout[cfg] : 0.0;
-            double gs0 = 0.0, gs1 = 0.0;
+            const double cbar_full = CLOW ? gout : ldexp(gout, n - 1);   // Cbar of the full mask (the sink)
             double *aout = store + (size_t)s_loc[ell] * kLanes;   // O(ell), replaced by Obar(ell)
             const double *fsrc = aout;
             const double *a1 = store + (size_t)s_loc[ell + 1] * kLanes;
@@ -1037,7 +1032,7 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
                 const bool live = (ones != 0u) || (B == full);
                 double cbar = 0.0;
                 if (B == full) {
-                    cbar = CLOW ? gout : ldexp(gout, n - 1);
+                    cbar = cbar_full;
                 } else if (ones) {
                     const int k = __ffs(ones) - 1;
                     const uint32_t bk = 1u << k;
@@ -1049,13 +1044,8 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
                     const uint32_t ss = off1 + (uint32_t)(((hi1 * 2 + sk) * nA + __popc(A & (bk - 1u))) * 2 + sk);
                     const double seed = a1[(size_t)ss * kLanes + lane];
                     cbar = flavor_sum((CLOW && k == 0 && lam == 0) ? 0.0 : seed, nfl, ci);
-                    // vertex 0's shifted start on sublattice S & 1, once: by the owner of that unit
-                    if (sgrad && ell == 1 && ((own2 >> (S & 1u)) & 1u)) {
-                        if (S & 1u) gs1 = fma(sgn * 2.0, seed, gs1);
-                        else gs0 = fma(sgn * 2.0, seed, gs0);
-                    }
                 }
-                const double gamma = unit_weight ? neg(cbar) : cfac * cbar;
+                const double gamma = UW ? neg(cbar) : cfac * cbar;
                 for (uint32_t hh = H; hh; hh &= hh - 1u) {
                     const int h = __ffs(hh) - 1;
                     const int hidx = __popc(H & ((1u << h) - 1u));
@@ -1090,10 +1080,6 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
                     }
                 }
             }
-            if (sgrad) {
-                s_red[warp][0][lane] += gs0;
-                s_red[warp][1][lane] += gs1;
-            }
             __syncthreads();
         }
         if (active && a.gM) {
@@ -1116,11 +1102,12 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
             }
         } else if (a.gsig) {
             if (warp == 0 && active) {
-                double t0 = 0.0, t1 = 0.0;
-                for (int w = 0; w < nwarps; ++w) {
-                    t0 += s_red[w][0][lane];
-                    t1 += s_red[w][1][lane];
-                }
+                // vertex 0's shifted start on sublattice s: sgn 2 times the adjoint of the seed slot
+                // of its layer-1 mask's close, slot 3 s of the mask with vertex 0 full (code 3) in
+                // layer 2, still in place
+                const size_t sb = (size_t)s_loc[2] + __ldg(tab.rank4 + 3u);
+                double t0 = sgn * 2.0 * store[sb * kLanes + lane];
+                double t1 = sgn * 2.0 * store[(sb + 3u) * kLanes + lane];
                 // the shifted diagonal (v >= 1): sgn times the extension part of dc/dM[(v,s)][(v,s)]
                 for (int v = 1; v < n; ++v) {
                     t0 = fma(sgn, dM[((2 * v) * n2 + 2 * v) * kLanes + lane], t0);
@@ -1146,7 +1133,8 @@ static cos_status launch_bip_adjoint(Workspace *ws, const BipLaunch &L, const do
     const size_t extra = (dm_global ? mat_elems : 0) * sizeof(double);   // per CTA, beside the layers
     const int warps = std::min(16, std::max(4, 2 * L.n_max));
     const size_t smem = (dm_global ? 2 : 3) * mat_elems * sizeof(double);
-    auto kern = L.clow ? dp_bip_adjoint_kernel<true> : dp_bip_adjoint_kernel<false>;
+    auto kern = L.clow ? dp_bip_adjoint_kernel<true>
+                       : (L.loop_weight == 1 ? dp_bip_adjoint_kernel<false> : dp_bip_adjoint_kernel<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "bipartite adjoint smem attribute");
     int nsm = 1;
