@@ -920,6 +920,11 @@ def measure_det(torch, B, flush, peaks, steps):
     for p, f in fns.items():
         ts[p], _, cl[p] = timed_form(torch, f, steps, flush)
     B.cos_sync_status()
+    # c_det against c_CoS / 2^n on the same matrices, read at once and again after the gradient and
+    # all-subsets calls below (which must leave both outputs untouched)
+    rel_vs_cos = lambda: float(np.max(np.abs(outs["fp64"].cpu().numpy() - outs["cos"].cpu().numpy() / 2.0 ** n)
+                                      / np.abs(outs["fp64"].cpu().numpy())))
+    first_diff = rel_vs_cos()
     fl = n_cfg * 2 * 2.0 * det_fma(B, n)
     for p in ("fp64", "df64", "mixed"):
         r = {"configs": n_cfg, "configs_per_s": n_cfg / ts[p], "ms_median": ts[p] * 1e3,
@@ -955,8 +960,8 @@ def measure_det(torch, B, flush, peaks, steps):
                                            "frac_fp64_peak": 3 * fl / tg / peaks.fp64(cg), "steps": steps,
                                            "clocks": cg}
     got = outs["fp64"].cpu().numpy()
-    cos = outs["cos"].cpu().numpy()
-    res["su2_zeeman_n10_det_fp64"]["max_rel_diff_vs_cos_over_2n"] = float(np.max(np.abs(got - cos / 2.0 ** n) / np.abs(got)))
+    res["su2_zeeman_n10_det_fp64"]["max_rel_diff_vs_cos_over_2n"] = first_diff
+    res["su2_zeeman_n10_det_fp64"]["max_rel_diff_vs_cos_over_2n_after_grad_and_subsets"] = rel_vs_cos()
     tabs.close()
     # bipartite: the honeycomb workload's gathered matrices, det vs CoS bipartite sweep
     hw = I.WORKLOADS["hc_su2_af_n8"]
