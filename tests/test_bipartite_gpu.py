@@ -284,6 +284,7 @@ def close_to(a, b, rel=1e-9):
 
 @pytest.mark.parametrize("n,n_mat,wt,shifts,ncfg,det", [
     (1, 2, 1, True, 3, False), (2, 1, 2, False, 5, False), (3, 2, 1, True, 7, False), (4, 2, 1, False, 3, False),
+    (3, 1, 3, True, 4, False),   # loop weight 3 with shifts: the non-unit-weight sweep and dsigma
     (1, 2, 1, True, 3, True), (2, 2, 1, False, 5, True), (3, 2, 1, True, 4, True), (4, 2, 1, True, 3, True),
 ])
 def test_bipartite_grad_vs_exact_differences(n, n_mat, wt, shifts, ncfg, det):

@@ -111,3 +111,32 @@ def test_release_workspace_frees_and_recreates():
     B.cos_connected_sum_matrices(n, order, moff, n_mat, 1, None, M, "fp64", out2)
     B.cos_sync_status()
     assert np.array_equal(out1.cpu().numpy(), out2.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec,n,n_mat", [("mixed", 8, 4), ("mixed", 10, 3), ("df64", 8, 4), ("df64", 9, 2)])
+def test_prefetch_modes_leave_results_bitwise(prec, n, n_mat):
+    """Prefetch modes 0-4 of the pair kernels (none, next mask into L2 or L1, next row into L1,
+    both) and the launch shapes only move data: the connected sums are bit for bit the same,
+    with shifts and an uneven tail of orders."""
+    ncfg = 300
+    orders = np.array([n - (c % 3 == 2) for c in range(ncfg)], dtype=np.int32)
+    Ms = [I.random_matrices(77 + c, 1, n_mat, int(orders[c]), 0.9)[0] for c in range(ncfg)]
+    moff = np.concatenate([[0], np.cumsum([m.size for m in Ms])[:-1]]).astype(np.int64)
+    d_order = torch.tensor(orders, device="cuda")
+    d_moff = torch.tensor(moff, device="cuda")
+    M = torch.tensor(np.concatenate([m.ravel() for m in Ms]), device="cuda")
+    sigma = list(np.linspace(-0.1, 0.12, n_mat))
+    saved = B.cos_get_tuning(n, prec, n_mat)
+    outs = []
+    try:
+        for w, c, pf in [(16, 1, 0), (16, 1, 1), (16, 1, 2), (16, 1, 3), (16, 1, 4), (8, 1, 3)]:
+            B.cos_set_tuning(n, prec, n_mat, w, c, pf)
+            out = torch.empty(ncfg, dtype=torch.float64, device="cuda")
+            B.cos_connected_sum_matrices(n, d_order, d_moff, n_mat, 1, sigma, M, prec, out)
+            B.cos_sync_status()
+            outs.append(out.cpu().numpy())
+    finally:
+        B.cos_set_tuning(n, prec, n_mat, *saved)
+    assert np.all(np.isfinite(outs[0]))
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
