@@ -418,7 +418,8 @@ cos_status cos_plan_grid(const cos_plan *plan, int *grid);   /* persistent CTAs 
 cos_status cos_plan_destroy(cos_plan *plan);
 
 /* Launch shape of the DP kernel per (order n_max of the launch, precision, matrices per
- * configuration): warps per CTA (1..16), resident CTAs per SM (1..8) and whether a warp
+ * configuration): warps per CTA (1..16; 1..20 for mixed and double-float), resident CTAs per SM
+ * (1..8) and whether a warp
  * prefetches the states of its next mask while it computes the current one (prefetch:
  * 0 = off, 1 = into L2, 2 = into L1; 3 = the mixed and double-float kernels pull each next row's
  * states into L1 while a row computes, 4 = 3 plus the next mask into L2; the FP64 kernel treats

@@ -101,7 +101,7 @@ void load_tune_file_locked() {
         int n = 0, prec = 0, nf = 0, w = 0, c = 0, pf = 1;
         double ms = 0.0;
         const int got = sscanf(line, "%d %d %d %d %d %lf %d", &n, &prec, &nf, &w, &c, &ms, &pf);
-        if (got >= 5 && n >= 1 && n <= COS_NMAX && w >= 1 && w <= 16 && c >= 1 && c <= 8) {
+        if (got >= 5 && n >= 1 && n <= COS_NMAX && w >= 1 && w <= (prec == COS_FP64 ? 16 : 20) && c >= 1 && c <= 8) {
             Tuning t;
             t.warps = w;
             t.ctas_per_sm = c;

@@ -61,7 +61,10 @@ __device__ __forceinline__ void prefetch_rows_l1(const void *src, uint32_t off, 
 // [v][j] of lane l sits at ((v n + j) 32 + l) times its size (16 bytes, 32 for Md).  The row's
 // target slots are formed lane-parallel once (lane q: extension q) and read with one shuffle per
 // push.
-template <int NV>
+// CONT: the row's second part (rows longer than kRowStates run in two parts): the extension dot
+// products continue from the values the first part stored in the target slots (the same FMA
+// chain, so the same bits as one pass).
+template <int NV, bool CONT = false>
 __device__ __forceinline__ void do_row_pair(const FV<4> *__restrict__ src, FV<4> *__restrict__ dst1, uint32_t ms,
                                             uint32_t md, const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow,
                                             uint32_t A, uint32_t off, int h, int hidx, int nA, int n, bool needclose,
@@ -97,7 +100,15 @@ __device__ __forceinline__ void do_row_pair(const FV<4> *__restrict__ src, FV<4>
         jj &= jj - 1u;
         const uint32_t jb = (uint32_t)(__ffs(jj) - 1) * (kLanes * 16);
         jj &= jj - 1u;
+        const uint32_t sa = __shfl_sync(0xFFFFFFFFu, tslot, q), sb = __shfl_sync(0xFFFFFFFFu, tslot, q + 1);
         float2 a0 = make_float2(0.0f, 0.0f), a1 = a0, b0 = a0, b1 = a0;
+        if constexpr (CONT) {
+            const float4 pa = dl[(size_t)sa * kLanes], pb = dl[(size_t)sb * kLanes];
+            a0 = make_float2(pa.x, pa.y);
+            a1 = make_float2(pa.z, pa.w);
+            b0 = make_float2(pb.x, pb.y);
+            b1 = make_float2(pb.z, pb.w);
+        }
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
             const float4 ma_ = lds4(ma[t] + ja), mb_ = lds4(ma[t] + jb);
@@ -107,47 +118,68 @@ __device__ __forceinline__ void do_row_pair(const FV<4> *__restrict__ src, FV<4>
             b0 = fma2(o0, make_float2(mb_.x, mb_.y), b0);
             b1 = fma2(o1, make_float2(mb_.z, mb_.w), b1);
         }
-        const uint32_t sa = __shfl_sync(0xFFFFFFFFu, tslot, q), sb = __shfl_sync(0xFFFFFFFFu, tslot, q + 1);
         dl[(size_t)sa * kLanes] = make_float4(a0.x, a0.y, a1.x, a1.y);
         dl[(size_t)sb * kLanes] = make_float4(b0.x, b0.y, b1.x, b1.y);
     }
     if (q < nJ) {
         const uint32_t jo = (uint32_t)(__ffs(jj) - 1) * (kLanes * 16);
+        const uint32_t sq = __shfl_sync(0xFFFFFFFFu, tslot, q);
         float2 d0 = make_float2(0.0f, 0.0f), d1 = d0;
+        if constexpr (CONT) {
+            const float4 pd = dl[(size_t)sq * kLanes];
+            d0 = make_float2(pd.x, pd.y);
+            d1 = make_float2(pd.z, pd.w);
+        }
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
             const float4 m = lds4(ma[t] + jo);
             d0 = fma2(make_float2(o[t].x, o[t].y), make_float2(m.x, m.y), d0);
             d1 = fma2(make_float2(o[t].z, o[t].w), make_float2(m.z, m.w), d1);
         }
-        const uint32_t sq = __shfl_sync(0xFFFFFFFFu, tslot, q);
         dl[(size_t)sq * kLanes] = make_float4(d0.x, d0.y, d1.x, d1.y);
     }
 }
+
+// Longest row part run in one pass (the states of a part are held in registers; longer rows run
+// in two parts, the second continuing the first's dot products).
+constexpr int kRowStates = 6;
 
 __device__ __forceinline__ void row_dispatch_pair(int nv, const FV<4> *src, FV<4> *dst1, uint32_t ms, uint32_t md,
                                                   const TgtInfo &ti, int nJ, uint32_t J, uint32_t Vrow, uint32_t A,
                                                   uint32_t off, int h, int hidx, int nA, int n, bool needclose,
                                                   int lane, DotAcc2 (&csum)[2]) {
-#define COS_ROW_P(K)                                                                                           \
+#define COS_ROW_P(K, C, V)                                                                                     \
     case K:                                                                                                    \
-        do_row_pair<K>(src, dst1, ms, md, ti, nJ, J, Vrow, A, off, h, hidx, nA, n, needclose, lane, csum);     \
+        do_row_pair<K, C>(src, dst1, ms, md, ti, nJ, J, V, A, off, h, hidx, nA, n, needclose, lane, csum);     \
         break;
+    uint32_t V2 = 0u;
+    if (nv > kRowStates) {   // the first kRowStates endpoints, then the rest
+        const uint32_t cut = 1u << (__fns(Vrow, 0, kRowStates + 1));
+        V2 = Vrow & ~(cut - 1u);
+        Vrow &= cut - 1u;
+        nv = kRowStates;
+    }
     switch (nv) {
-        COS_ROW_P(1)
-        COS_ROW_P(2)
-        COS_ROW_P(3)
-        COS_ROW_P(4)
-        COS_ROW_P(5)
-        COS_ROW_P(6)
-        COS_ROW_P(7)
-        COS_ROW_P(8)
-        COS_ROW_P(9)
-        COS_ROW_P(10)
-        COS_ROW_P(11)
-        COS_ROW_P(12)
+        COS_ROW_P(1, false, Vrow)
+        COS_ROW_P(2, false, Vrow)
+        COS_ROW_P(3, false, Vrow)
+        COS_ROW_P(4, false, Vrow)
+        COS_ROW_P(5, false, Vrow)
+        COS_ROW_P(6, false, Vrow)
         default:
             break;
+    }
+    if (V2) {
+        switch (__popc(V2)) {
+            COS_ROW_P(1, true, V2)
+            COS_ROW_P(2, true, V2)
+            COS_ROW_P(3, true, V2)
+            COS_ROW_P(4, true, V2)
+            COS_ROW_P(5, true, V2)
+            COS_ROW_P(6, true, V2)
+            default:
+                break;
+        }
     }
 #undef COS_ROW_P
 }

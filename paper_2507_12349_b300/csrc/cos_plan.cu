@@ -218,7 +218,8 @@ extern "C" cos_status cos_plan_destroy(cos_plan *p) {
 
 extern "C" cos_status cos_set_tuning(int n, cos_precision precision, int n_mat, int warps, int ctas_per_sm,
                                      int prefetch) {
-    if (n < 1 || n > COS_NMAX || n_mat < 1 || n_mat > COS_MAX_FLAVORS || warps < 1 || warps > 16 ||
+    if (n < 1 || n > COS_NMAX || n_mat < 1 || n_mat > COS_MAX_FLAVORS || warps < 1 ||
+        warps > (precision == COS_FP64 ? 16 : 20) ||
         ctas_per_sm < 1 || ctas_per_sm > 8 || (precision != COS_FP64 && precision != COS_MIXED && precision != COS_DF64)) {
         set_error("cos_set_tuning: out of range");
         return COS_ERR_ARG;
