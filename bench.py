@@ -1020,7 +1020,8 @@ def measure_det(torch, B, flush, peaks, steps):
 def bipartite_arm(args):
     """Profiling runs of the bipartite path alone: the honeycomb workload's gather + DP from
     vertex coordinates, at its order or --order, --n-cfg configurations, CUDA-event timing;
-    with --subsets, gather + the all-subsets mode (c(S) and a(S) of every subset, FP64)."""
+    with --grad the gradient call instead (FP64); with --subsets, gather + the all-subsets
+    mode (c(S) and a(S) of every subset, FP64)."""
     import torch
     from paper_2507_12349_b300 import binding as B
     B.lib()
@@ -1034,6 +1035,11 @@ def bipartite_arm(args):
     out = torch.empty(n_cfg, dtype=torch.float64, device="cuda")
     flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     fn = lambda: B.cos_connected_sum_bipartite_batch(tabs, n, *d, args.precision, out)
+    if args.grad:   # the gradient from vertex coordinates: gather, reverse sweep, chain rule to mu, alpha
+        gout = torch.ones(n_cfg, dtype=torch.float64, device="cuda")
+        gmu = torch.empty(n_cfg, tabs.info().n_flavors, dtype=torch.float64, device="cuda")
+        gal = torch.empty_like(gmu)
+        fn = lambda: B.cos_connected_sum_bipartite_grad(tabs, n, *d, gout, out, gmu=gmu, galpha=gal)
     if args.subsets:
         moff = torch.as_tensor(B.bipartite_matrix_offsets(cfgs.order, n_mat), device="cuda")
         M4 = torch.empty(n_cfg * n_mat * 4 * n * n, dtype=torch.float64, device="cuda")
@@ -1055,10 +1061,11 @@ def bipartite_arm(args):
     t = statistics.mean(ts)
     fl = n_cfg * n_mat * 2.0 * (s.fma_ext + s.fma_close)
     print(json.dumps({"metric": ("bipartite all-subsets configs/s (c(S), a(S) of every subset)" if args.subsets else
+                                 "bipartite gradient configs/s (honeycomb, dc/dmu and dc/dalpha)" if args.grad else
                                  "bipartite connected-sum configs/s (honeycomb, sublattices summed)"),
                       "value": n_cfg / t, "unit": "configs/s", "order": n, "configs": n_cfg,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
-                      "tflops": None if args.subsets else fl / t / 1e12,
+                      "tflops": None if (args.subsets or args.grad) else fl / t / 1e12,
                       "dtype": "f64" if args.subsets else {"fp64": "f64", "df64": "f32 pairs (df64)"}.get(
                           args.precision, args.precision)}), flush=True)
     tabs.close()
