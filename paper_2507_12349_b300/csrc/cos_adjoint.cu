@@ -10,8 +10,10 @@
 //   Row (mu, h), D_j = Obar(mu + e_j, h, j):
 //     Obar(mu, h, v) = Cbar Mc[v][h] + sum_j D_j Ms[v][j]
 //     dM[v][h] += sgn w Cbar O(mu,h,v);   dM[v][j] += D_j O(mu,h,v)   (dMs/dM = 1)
-//     dsigma   += sgn D_j O(mu,h,j) for every half-visited j >= 1 (the shifted diagonal), and
-//                 sgn 2 Obar(2e_0, 0, 0) for the shifted start.
+//     dsigma    = sgn sum over half-visited j >= 1 of D_j O(mu,h,j) (the shifted diagonal) +
+//                 sgn 2 Obar(2e_0, 0, 0) (the shifted start); the first sum is the extension
+//                 part of the diagonal of dM, read off once per batch (the closes' own diagonal
+//                 terms accumulate apart, in dMd), the second read from layer 2 at the end.
 // Every adjoint slot read was written earlier in the same sweep (targets of reachable edges
 // are reachable), so nothing needs clearing.
 //

@@ -765,8 +765,9 @@ cos_status bip_subsets_dp(Workspace *ws, int n_cfg, int n_max, const int32_t *d_
 //   dM[(v,s_v)][(j_q,s_q)] += D_q O,  dM[(v,s_v)][(h,s_h)] += sgn w Cbar O,
 // D_q = Obar of extension target q (the forward's target table), Cbar = the flavor sum of the
 // seed slot's Obar (or gout 2^(n-1) at the full mask).  Shift weights: the shifted diagonal
-// (v,s) -> (v,s) for half-visited v >= 1 gives dsigma_{l,s} -= D O, the shifted start
-// sgn 2 Obar(seed) at layer 1.  Determinant weights (CLOW): the Alg. 1 sweep, the k = 0 close
+// (v,s) -> (v,s) for half-visited v >= 1 gives dsigma_{l,s} = sgn sum_v (the extension part of
+// dM[(v,s)][(v,s)], the closes' diagonal terms kept apart), read once per batch, plus the
+// shifted start sgn 2 Obar(seed) read from layer 2 at the end of the batch.  Determinant weights (CLOW): the Alg. 1 sweep, the k = 0 close
 // seeded block 1 only, Cbar(full) = gout, and dalpha_{b,s} = -sum_j dM_b[(j,s)][(j,s)].
 // Warps own endpoint units (v, s_v), unit v * 2 + s_v modulo the warp count (2n warps, at most
 // 16): one writer per dM row, no atomics.  Shared memory holds Ms, Md and dM, 3 x 4 n^2 doubles
