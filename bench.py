@@ -366,6 +366,8 @@ def rooflines(r, counts, t, prec, peaks, clocks):
         terms = counts["flops"] / 2.0
         r["tflops_equiv"] = counts["flops"] / t / 1e12
         r["frac_fp32_floor"] = terms * DF64_FP32_PER_TERM / t / peaks.fp32_lane_ops(clocks)
+        r["binding_roof"] = "hbm" if r["frac_hbm"] >= r["frac_fp32_floor"] else "fp32"
+        r["frac_binding_roof"] = max(r["frac_hbm"], r["frac_fp32_floor"])
     return r
 
 
