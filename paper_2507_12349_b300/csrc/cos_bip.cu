@@ -236,26 +236,26 @@ struct BipArgs {
 // the q-th target in (j ascending, s_j ascending) order.
 //   off1 : block offset of the target mask;  meta: ai1 (bits 0-3), nA1 (4-7), s_j (8),
 //   j (12-15), heads of the target mask (16-27).
+// The targets are the set bits of E: bit 2j for j in J (s_j = 0, or the walk's sublattice of a
+// touched j), bit 2j + 1 for an untouched j (s_j = 1), so lane q takes the (q+1)-th set bit.
+__device__ __forceinline__ uint32_t spread_even(uint32_t x) {   // bit i -> bit 2i, 16 bits
+    x &= 0xFFFFu;
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    return (x | (x << 1)) & 0x55555555u;
+}
 __device__ __forceinline__ TgtInfo bip_targets(uint32_t A, uint32_t B, uint32_t S, uint32_t J, uint32_t code,
                                                const uint32_t *__restrict__ rank4, int lane) {
     TgtInfo ti = {0u, 0u};
-    const int T = __popc(J) + __popc(J & ~A);
-    if (lane < T) {
-        int cnt = 0, j = 0, sj = 0;
-        bool untouched = false;
-        for (uint32_t jj = J; jj; jj &= jj - 1u) {
-            const int jc = __ffs(jj) - 1;
-            const bool u = !(A & (1u << jc));
-            const int c = u ? 2 : 1;
-            if (lane < cnt + c) {
-                j = jc;
-                untouched = u;
-                sj = u ? lane - cnt : (int)((S >> jc) & 1u);
-                break;
-            }
-            cnt += c;
-        }
+    const uint32_t U = J & ~A;
+    if (lane < __popc(J) + __popc(U)) {
+        const uint32_t E = spread_even(J) | (spread_even(U) << 1);
+        const int p = (int)__fns(E, 0u, lane + 1);
+        const int j = p >> 1;
         const uint32_t bj = 1u << j;
+        const bool untouched = (U & bj) != 0u;
+        const int sj = untouched ? (p & 1) : (int)((S >> j) & 1u);
         const uint32_t A1 = A | bj;
         const uint32_t B1 = untouched ? B : (B | bj);
         const uint32_t code1 = untouched ? code + (uint32_t)(1 + sj) * c_p4[j] : code + (uint32_t)(2 - sj) * c_p4[j];
