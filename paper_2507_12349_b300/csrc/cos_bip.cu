@@ -339,25 +339,28 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
                                         uint32_t Vrow, uint32_t A, uint32_t B, uint32_t S, uint32_t rowbase, int h,
                                         int sh, int n2, bool needclose, int lane, typename BipArith<T>::CAcc &csum) {
     using Ar = BipArith<T>;
+    // The row's endpoint states (v, s_v) in ascending order are the set bits 2 v + s_v of R: a
+    // half-visited v on its own sublattice, v = h on s_h, any other (full) v on both.  Lane t
+    // decodes state t once per row (its slot and its matrix row), the loop below shuffles them.
+    const uint32_t ones = A & ~B;
+    const uint32_t bh = 1u << h;
+    const uint32_t vhalf = Vrow & ones;
+    uint32_t R = spread_even(Vrow & ~ones & ~bh) * 3u | spread_even(vhalf & ~S) | (spread_even(vhalf & S) << 1);
+    if (Vrow & ~ones & bh) R |= 1u << (2 * h + sh);
+    uint32_t lslot = 0u;
+    int lrs = 0;
+    if (lane < NV) {
+        const int p = (int)__fns(R, 0u, lane + 1);   // 2 v + s_v of state `lane`
+        lslot = rowbase + (uint32_t)(__popc(A & ((1u << (p >> 1)) - 1u)) * 2 + (p & 1));
+        lrs = p * n2 * kLanes;
+    }
     T o[NV];
     int rs[NV];
-    const uint32_t ones = A & ~B;
-    uint32_t vv = Vrow;
-    int phase = 0;
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
-        const int v = __ffs(vv) - 1;
-        const uint32_t bv = 1u << v;
-        const bool half = (ones & bv) != 0;
-        const int sv = half ? (int)((S >> v) & 1u) : (v == h ? sh : phase);
-        o[t] = src[(size_t)(rowbase + (uint32_t)(__popc(A & (bv - 1u)) * 2 + sv)) * kLanes + lane];
-        rs[t] = (v * 2 + sv) * n2 * kLanes + lane;
-        if (!half && v != h && phase == 0) {
-            phase = 1;
-        } else {
-            vv &= vv - 1u;
-            phase = 0;
-        }
+        const uint32_t sl = __shfl_sync(0xFFFFFFFFu, lslot, t);
+        rs[t] = __shfl_sync(0xFFFFFFFFu, lrs, t) + lane;
+        o[t] = src[(size_t)sl * kLanes + lane];
     }
     if (needclose) {
         const int hc = (h * 2 + sh) * kLanes;
