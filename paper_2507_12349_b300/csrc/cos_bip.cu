@@ -340,27 +340,41 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
                                         int sh, int n2, bool needclose, int lane, typename BipArith<T>::CAcc &csum) {
     using Ar = BipArith<T>;
     // The row's endpoint states (v, s_v) in ascending order are the set bits 2 v + s_v of R: a
-    // half-visited v on its own sublattice, v = h on s_h, any other (full) v on both.  Lane t
-    // decodes state t once per row (its slot and its matrix row), the loop below shuffles them.
+    // half-visited v on its own sublattice, v = h on s_h, any other (full) v on both.
     const uint32_t ones = A & ~B;
     const uint32_t bh = 1u << h;
     const uint32_t vhalf = Vrow & ones;
     uint32_t R = spread_even(Vrow & ~ones & ~bh) * 3u | spread_even(vhalf & ~S) | (spread_even(vhalf & S) << 1);
     if (Vrow & ~ones & bh) R |= 1u << (2 * h + sh);
-    uint32_t lslot = 0u;
-    int lrs = 0;
-    if (lane < NV) {
-        const int p = (int)__fns(R, 0u, lane + 1);   // 2 v + s_v of state `lane`
-        lslot = rowbase + (uint32_t)(__popc(A & ((1u << (p >> 1)) - 1u)) * 2 + (p & 1));
-        lrs = p * n2 * kLanes;
-    }
     T o[NV];
     int rs[NV];
+    if constexpr (sizeof(T) == 4) {
+        // mixed: lane t decodes state t once per row, the loop shuffles it (FP32 rows are short
+        // in issue time, so the per-state chain below would lead them)
+        uint32_t lslot = 0u;
+        int lrs = 0;
+        if (lane < NV) {
+            const int p = (int)__fns(R, 0u, lane + 1);   // 2 v + s_v of state `lane`
+            lslot = rowbase + (uint32_t)(__popc(A & ((1u << (p >> 1)) - 1u)) * 2 + (p & 1));
+            lrs = p * n2 * kLanes;
+        }
 #pragma unroll
-    for (int t = 0; t < NV; ++t) {
-        const uint32_t sl = __shfl_sync(0xFFFFFFFFu, lslot, t);
-        rs[t] = __shfl_sync(0xFFFFFFFFu, lrs, t) + lane;
-        o[t] = src[(size_t)sl * kLanes + lane];
+        for (int t = 0; t < NV; ++t) {
+            const uint32_t sl = __shfl_sync(0xFFFFFFFFu, lslot, t);
+            rs[t] = __shfl_sync(0xFFFFFFFFu, lrs, t) + lane;
+            o[t] = src[(size_t)sl * kLanes + lane];
+        }
+    } else {
+        // FP64 and double-float: the set bits of R in turn (a short branch-free chain per state)
+        uint32_t rr = R;
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            const int p = __ffs(rr) - 1;
+            rr &= rr - 1u;
+            const uint32_t sl = rowbase + (uint32_t)(__popc(A & ((1u << (p >> 1)) - 1u)) * 2 + (p & 1));
+            rs[t] = p * n2 * kLanes + lane;
+            o[t] = src[(size_t)sl * kLanes + lane];
+        }
     }
     if (needclose) {
         const int hc = (h * 2 + sh) * kLanes;
