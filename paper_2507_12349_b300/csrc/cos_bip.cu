@@ -33,6 +33,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "cos_dp_device.cuh"
@@ -332,6 +333,35 @@ struct BipArith<df64> {
     static __device__ __forceinline__ double to_double(CV a) { return df64_to_double(a); }
 };
 
+// Loads of a matrix entry at a shared-memory byte address (the rows keep one 32-bit address
+// per state, so an entry costs one add).
+template <typename T>
+__device__ __forceinline__ T lds_as(uint32_t a);
+template <>
+__device__ __forceinline__ float lds_as<float>(uint32_t a) {
+    float r;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(r) : "r"(a));
+    return r;
+}
+template <>
+__device__ __forceinline__ double lds_as<double>(uint32_t a) {
+    double r;
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(r) : "r"(a));
+    return r;
+}
+template <>
+__device__ __forceinline__ df64 lds_as<df64>(uint32_t a) {
+    df64 r;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.hi), "=f"(r.lo) : "r"(a));
+    return r;
+}
+
+template <typename T, bool BYTE>
+__device__ __forceinline__ T ms_at(const T *Ms, uint32_t a) {
+    if constexpr (BYTE) return lds_as<T>(a);
+    else return Ms[a];
+}
+
 // One row (mu, h, s_h): NV reachable endpoint states, the close, every extension.
 template <typename T, int NV>
 __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict__ dst1, const T *__restrict__ Ms,
@@ -346,8 +376,15 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
     const uint32_t vhalf = Vrow & ones;
     uint32_t R = spread_even(Vrow & ~ones & ~bh) * 3u | spread_even(vhalf & ~S) | (spread_even(vhalf & S) << 1);
     if (Vrow & ~ones & bh) R |= 1u << (2 * h + sh);
+    using CT = typename Ar::CT;
+    // Matrix entries by shared-memory byte address (mixed, double-float: one add per entry) or,
+    // in FP64 where that measured no better, by element index: ra[t] locates Ms[(v_t, s_t)][0]
+    // of this lane in units of kU bytes from kBase.
+    constexpr bool kByte = !std::is_same<T, double>::value;
+    constexpr uint32_t kU = kByte ? (uint32_t)sizeof(T) : 1u;
+    const uint32_t msb = kByte ? (uint32_t)__cvta_generic_to_shared(Ms) : 0u;
     T o[NV];
-    int rs[NV];
+    uint32_t ra[NV];
     if constexpr (sizeof(T) == 4) {
         // mixed: lane t decodes state t once per row, the loop shuffles it (FP32 rows are short
         // in issue time, so the per-state chain below would lead them)
@@ -358,10 +395,11 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
             lslot = rowbase + (uint32_t)(__popc(A & ((1u << (p >> 1)) - 1u)) * 2 + (p & 1));
             lrs = p * n2 * kLanes;
         }
+        const uint32_t mlane = msb + (uint32_t)lane * kU;
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
             const uint32_t sl = __shfl_sync(0xFFFFFFFFu, lslot, t);
-            rs[t] = __shfl_sync(0xFFFFFFFFu, lrs, t) + lane;
+            ra[t] = mlane + (uint32_t)__shfl_sync(0xFFFFFFFFu, lrs, t) * kU;
             o[t] = src[(size_t)sl * kLanes + lane];
         }
     } else {
@@ -372,14 +410,22 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
             const int p = __ffs(rr) - 1;
             rr &= rr - 1u;
             const uint32_t sl = rowbase + (uint32_t)(__popc(A & ((1u << (p >> 1)) - 1u)) * 2 + (p & 1));
-            rs[t] = p * n2 * kLanes + lane;
+            ra[t] = msb + (uint32_t)(p * n2 * kLanes + lane) * kU;
             o[t] = src[(size_t)sl * kLanes + lane];
         }
     }
     if (needclose) {
-        const int hc = (h * 2 + sh) * kLanes;
+        // Md[(v,s)][(h,s_h)] at md + (ra - msb) kr + (h 2 + s_h) 32 sizeof(CT), kr = sizeof(CT) / sizeof(T)
+        const uint32_t hc = (uint32_t)((h * 2 + sh) * kLanes);
+        if constexpr (kByte) {
+            constexpr uint32_t kr = sizeof(CT) / sizeof(T);
+            const uint32_t dmd = (uint32_t)__cvta_generic_to_shared(Md) - kr * msb + hc * (uint32_t)sizeof(CT);
 #pragma unroll
-        for (int t = 0; t < NV; ++t) Ar::cmad(csum, o[t], Md[rs[t] + hc]);
+            for (int t = 0; t < NV; ++t) Ar::cmad(csum, o[t], lds_as<CT>(kr * ra[t] + dmd));
+        } else {
+#pragma unroll
+            for (int t = 0; t < NV; ++t) Ar::cmad(csum, o[t], Md[ra[t] + hc]);
+        }
     }
     // this row's target slots, lane-parallel: off1 + ((hidx1 * 2 + s_h) * nA1 + ai1) * 2 + s_j
     const uint32_t hlow = (1u << h) - 1u;
@@ -390,14 +436,14 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
     for (; q + 1 < nT; q += 2) {
         const uint32_t ma = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
         const uint32_t mb = __shfl_sync(0xFFFFFFFFu, ti.meta, q + 1);
-        const int ca = (int)(((ma >> 12) & 15u) * 2u + ((ma >> 8) & 1u)) * kLanes;
-        const int cb = (int)(((mb >> 12) & 15u) * 2u + ((mb >> 8) & 1u)) * kLanes;
-        typename Ar::Acc da = Ar::first(o[0], Ms[rs[0] + ca]);
-        typename Ar::Acc db = Ar::first(o[0], Ms[rs[0] + cb]);
+        const uint32_t ca = (((ma >> 12) & 15u) * 2u + ((ma >> 8) & 1u)) * (kLanes * kU);
+        const uint32_t cb = (((mb >> 12) & 15u) * 2u + ((mb >> 8) & 1u)) * (kLanes * kU);
+        typename Ar::Acc da = Ar::first(o[0], ms_at<T, kByte>(Ms, ra[0] + ca));
+        typename Ar::Acc db = Ar::first(o[0], ms_at<T, kByte>(Ms, ra[0] + cb));
 #pragma unroll
         for (int t = 1; t < NV; ++t) {
-            Ar::mad(da, o[t], Ms[rs[t] + ca]);
-            Ar::mad(db, o[t], Ms[rs[t] + cb]);
+            Ar::mad(da, o[t], ms_at<T, kByte>(Ms, ra[t] + ca));
+            Ar::mad(db, o[t], ms_at<T, kByte>(Ms, ra[t] + cb));
         }
         const uint32_t sa = __shfl_sync(0xFFFFFFFFu, tslot, q);
         const uint32_t sb = __shfl_sync(0xFFFFFFFFu, tslot, q + 1);
@@ -406,10 +452,10 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
     }
     if (q < nT) {
         const uint32_t ma = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
-        const int ca = (int)(((ma >> 12) & 15u) * 2u + ((ma >> 8) & 1u)) * kLanes;
-        typename Ar::Acc da = Ar::first(o[0], Ms[rs[0] + ca]);
+        const uint32_t ca = (((ma >> 12) & 15u) * 2u + ((ma >> 8) & 1u)) * (kLanes * kU);
+        typename Ar::Acc da = Ar::first(o[0], ms_at<T, kByte>(Ms, ra[0] + ca));
 #pragma unroll
-        for (int t = 1; t < NV; ++t) Ar::mad(da, o[t], Ms[rs[t] + ca]);
+        for (int t = 1; t < NV; ++t) Ar::mad(da, o[t], ms_at<T, kByte>(Ms, ra[t] + ca));
         const uint32_t sa = __shfl_sync(0xFFFFFFFFu, tslot, q);
         dst1[(size_t)sa * kLanes + lane] = Ar::store(da);
     }
