@@ -432,12 +432,19 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
     const uint32_t ai1 = ti.meta & 15u, nA1 = (ti.meta >> 4) & 15u, sj1 = (ti.meta >> 8) & 1u;
     const uint32_t hi1 = (uint32_t)__popc((ti.meta >> 16) & hlow);
     const uint32_t tslot = ti.off1 + ((hi1 * 2u + (uint32_t)sh) * nA1 + ai1) * 2u + sj1;
+    // and their matrix columns (j, s_j) in the units of ra: formed lane-parallel here for the
+    // byte-addressed rows, decoded per target from the shuffled meta in FP64 (measured better
+    // there)
+    const uint32_t tcol = (((ti.meta >> 12) & 15u) * 2u + sj1) * (kLanes * kU);
+    auto column = [&](int qq) -> uint32_t {
+        if constexpr (kByte) return __shfl_sync(0xFFFFFFFFu, tcol, qq);
+        const uint32_t m = __shfl_sync(0xFFFFFFFFu, ti.meta, qq);
+        return (((m >> 12) & 15u) * 2u + ((m >> 8) & 1u)) * (kLanes * kU);
+    };
     int q = 0;
     for (; q + 1 < nT; q += 2) {
-        const uint32_t ma = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
-        const uint32_t mb = __shfl_sync(0xFFFFFFFFu, ti.meta, q + 1);
-        const uint32_t ca = (((ma >> 12) & 15u) * 2u + ((ma >> 8) & 1u)) * (kLanes * kU);
-        const uint32_t cb = (((mb >> 12) & 15u) * 2u + ((mb >> 8) & 1u)) * (kLanes * kU);
+        const uint32_t ca = column(q);
+        const uint32_t cb = column(q + 1);
         typename Ar::Acc da = Ar::first(o[0], ms_at<T, kByte>(Ms, ra[0] + ca));
         typename Ar::Acc db = Ar::first(o[0], ms_at<T, kByte>(Ms, ra[0] + cb));
 #pragma unroll
@@ -451,8 +458,7 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
         dst1[(size_t)sb * kLanes + lane] = Ar::store(db);
     }
     if (q < nT) {
-        const uint32_t ma = __shfl_sync(0xFFFFFFFFu, ti.meta, q);
-        const uint32_t ca = (((ma >> 12) & 15u) * 2u + ((ma >> 8) & 1u)) * (kLanes * kU);
+        const uint32_t ca = column(q);
         typename Ar::Acc da = Ar::first(o[0], ms_at<T, kByte>(Ms, ra[0] + ca));
 #pragma unroll
         for (int t = 1; t < NV; ++t) Ar::mad(da, o[t], ms_at<T, kByte>(Ms, ra[t] + ca));
