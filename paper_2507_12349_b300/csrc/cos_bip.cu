@@ -1133,21 +1133,20 @@ __global__ void __launch_bounds__(512, 1) dp_bip_adjoint_kernel(const __grid_con
                         const uint32_t rowbase = off + (uint32_t)((hidx * 2 + sh) * nA * 2);
                         const uint32_t tslot = ti.off1 + ((hi1 * 2u + (uint32_t)sh) * nA1 + ai1) * 2u + sj1;
                         const int hc = (h * 2 + sh) * kLanes;
-                        for (uint32_t vv = Vrow; vv; vv &= vv - 1u) {
-                            const int v = __ffs(vv) - 1;
-                            const uint32_t bv = 1u << v;
-                            const bool half = (ones & bv) != 0;
-                            const int sv0 = half ? (int)((S >> v) & 1u) : (v == h ? sh : 0);
-                            const int sv1 = (half || v == h) ? sv0 : 1;
-                            const uint32_t below = bv - 1u;
-                            for (int sv = sv0; sv <= sv1; ++sv) {
-                                if (!((own2 >> (v * 2 + sv)) & 1u)) continue;
-                                const uint32_t slot = rowbase + (uint32_t)(__popc(A & below) * 2 + sv);
-                                const int vrow = (v * 2 + sv) * n2 * kLanes + lane;
-                                double *cdp = (v == h && sv == sh) ? &s_dmd[h * 2 + sh][lane] : dM + vrow + hc;
-                                bip_adj_dispatch(nT, fsrc, aout, a1, Ms, Md, dM, cdp, ti, tslot, slot, vrow, hc, live,
-                                                 cbar, gamma, lane);
-                            }
+                        // the row's endpoint units 2v + s_v (the forward row's mask) that this warp
+                        // owns, in ascending order
+                        const uint32_t bh = 1u << h, vhalf = Vrow & ones;
+                        uint32_t R = spread_even(Vrow & ~ones & ~bh) * 3u | spread_even(vhalf & ~S) |
+                                     (spread_even(vhalf & S) << 1);
+                        if (Vrow & ~ones & bh) R |= 1u << (2 * h + sh);
+                        for (uint32_t rr = R & own2; rr; rr &= rr - 1u) {
+                            const int u = __ffs(rr) - 1;
+                            const uint32_t slot =
+                                rowbase + (uint32_t)(__popc(A & ((1u << (u >> 1)) - 1u)) * 2 + (u & 1));
+                            const int vrow = u * n2 * kLanes + lane;
+                            double *cdp = (u == h * 2 + sh) ? &s_dmd[h * 2 + sh][lane] : dM + vrow + hc;
+                            bip_adj_dispatch(nT, fsrc, aout, a1, Ms, Md, dM, cdp, ti, tslot, slot, vrow, hc, live,
+                                             cbar, gamma, lane);
                         }
                     }
                 }
