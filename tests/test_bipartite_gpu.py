@@ -6,6 +6,7 @@ brute force and the sublattice-resolved DP of Alg. 1-2 in test_oracle_bip_pins.
 Tolerance: |err| <= 64 n 2^-53 mass, the FP64 bound of the square-lattice tests; the mass
 (the same DP on |M4|, |sigma| with all signs +) sums the assignments' masses.
 """
+import functools
 import math
 
 import numpy as np
@@ -100,29 +101,39 @@ def test_bipartite_mixed_matches_oracle(n, n_mat, wt, shifts, ncfg):
         assert mass[c] == pytest.approx(rmass, rel=1e-5)
 
 
-def test_bipartite_uneven_orders_and_order9():
-    """Orders 1..9 in one launch.  At n = 9 (512 assignments) the equal-block identity gives
-    the reference: every assignment sees the same matrices, so c_bip = 2^9 c."""
-    orders = [9, 3, 8, 1, 6, 2, 7, 5, 4, 9]
-    M4s = []
-    for c, n in enumerate(orders):
+UNEVEN_ORDERS = [9, 3, 8, 1, 6, 2, 7, 5, 4, 9]
+UNEVEN_SIG = [0.06, -0.09]
+
+
+@functools.lru_cache(maxsize=1)
+def uneven_case():
+    """Orders 1..9 for one launch, with the oracle's value and mass of each configuration.  At
+    n = 9 (512 assignments) the equal-block identity gives the reference: every assignment sees
+    the same matrices, so c_bip = 2^9 c."""
+    M4s, refs = [], []
+    s2 = [[UNEVEN_SIG[0], UNEVEN_SIG[0]], [UNEVEN_SIG[1], UNEVEN_SIG[1]]]
+    for c, n in enumerate(UNEVEN_ORDERS):
         if n == 9:
             M = I.random_matrices(900 + c, 1, 2, n, 0.9)[0]
             M4s.append(np.ascontiguousarray(np.broadcast_to(M[:, :, None, :, None], (2, n, 2, n, 2))))
+            refs.append((2 ** 9 * O.dp(M, UNEVEN_SIG, prec="ld"), 2 ** 9 * O.dp(M, UNEVEN_SIG, absmode=True)))
         else:
             M4s.append(rand_m4(700 + c, 1, 2, n)[0])
-    sig = [0.06, -0.09]
-    s2 = [[sig[0], sig[0]], [sig[1], sig[1]]]
-    got, mass = run(M4s, 2, 1, s2, abs_mass=True)
-    for c, n in enumerate(orders):
-        if n == 9:
-            M = M4s[c][:, :, 0, :, 0]
-            ref = 2 ** 9 * O.dp(M, sig, prec="ld")
-            rmass = 2 ** 9 * O.dp(M, sig, absmode=True)
-        else:
-            ref = O.bip(M4s[c], np.array(s2), method="sum_dp", prec="ld")
-            rmass = O.bip(M4s[c], np.array(s2), method="sum_dp", absmode=True)
-        assert abs(got[c] - ref) <= bound(n, rmass), (c, n, got[c], ref)
+            refs.append((O.bip(M4s[-1], np.array(s2), method="sum_dp", prec="ld"),
+                         O.bip(M4s[-1], np.array(s2), method="sum_dp", absmode=True)))
+    return M4s, s2, refs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "df64"])
+def test_bipartite_uneven_orders_and_order9(precision):
+    """Orders 1..9 in one launch, in every precision (the rows' state masks reach bit 2n + 1)."""
+    M4s, s2, refs = uneven_case()
+    got, mass = run(M4s, 2, 1, s2, abs_mass=True, precision=precision)
+    tol = {"fp64": bound, "mixed": mixed_bound, "df64": df64_bound}[precision]
+    for c, n in enumerate(UNEVEN_ORDERS):
+        ref, rmass = refs[c]
+        assert abs(got[c] - ref) <= tol(n, rmass), (c, n, got[c], ref)
+        assert mass[c] == pytest.approx(rmass, rel=1e-5 if precision == "mixed" else 1e-12)
 
 
 def test_bipartite_deterministic():
