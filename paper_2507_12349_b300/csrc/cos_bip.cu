@@ -332,6 +332,33 @@ struct BipArith<df64> {
     static __device__ __forceinline__ df64 add(df64 a, df64 b) { return df64_add(a, b); }
     static __device__ __forceinline__ double to_double(CV a) { return df64_to_double(a); }
 };
+// Mixed mode with two configurations per lane (components x, y): the extensions as packed FP32
+// pairs (each component bit for bit the one-per-lane mode's operation), the closes in FP64 per
+// component.  No to_double: the sweep writes each component's output itself.
+template <>
+struct BipArith<float2> {
+    using Acc = float2;
+    using CT = double2;
+    using CAcc = double2;
+    using CV = double2;
+    static __device__ __forceinline__ Acc zero() { return make_float2(0.0f, 0.0f); }
+    static __device__ __forceinline__ CAcc czero() { return make_double2(0.0, 0.0); }
+    static __device__ __forceinline__ Acc first(float2 x, float2 y) { return mul2(x, y); }
+    static __device__ __forceinline__ void mad(Acc &a, float2 x, float2 y) { a = fma2(x, y, a); }
+    static __device__ __forceinline__ void cmad(CAcc &a, float2 x, double2 y) {
+        a.x = fma(widen(x.x), y.x, a.x);
+        a.y = fma(widen(x.y), y.y, a.y);
+    }
+    static __device__ __forceinline__ float2 store(Acc a) { return a; }
+    static __device__ __forceinline__ CV close_sum(CAcc a, int nfl, int ci) {
+        return make_double2(flavor_sum(a.x, nfl, ci), flavor_sum(a.y, nfl, ci));
+    }
+    static __device__ __forceinline__ CV cadd(CV a, CV b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ float2 seed(CV a) {
+        return make_float2(narrow_to(0.0f, a.x), narrow_to(0.0f, a.y));
+    }
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return add2(a, b); }
+};
 
 // Loads of a matrix entry at a shared-memory byte address (the rows keep one 32-bit address
 // per state, so an entry costs one add).
@@ -353,6 +380,19 @@ template <>
 __device__ __forceinline__ df64 lds_as<df64>(uint32_t a) {
     df64 r;
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.hi), "=f"(r.lo) : "r"(a));
+    return r;
+}
+
+template <>
+__device__ __forceinline__ float2 lds_as<float2>(uint32_t a) {
+    float2 r;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(a));
+    return r;
+}
+template <>
+__device__ __forceinline__ double2 lds_as<double2>(uint32_t a) {
+    double2 r;
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "r"(a));
     return r;
 }
 
@@ -385,7 +425,7 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
     const uint32_t msb = kByte ? (uint32_t)__cvta_generic_to_shared(Ms) : 0u;
     T o[NV];
     uint32_t ra[NV];
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (std::is_same<T, float>::value || std::is_same<T, float2>::value) {
         // mixed: lane t decodes state t once per row, the loop shuffles it (FP32 rows are short
         // in issue time, so the per-state chain below would lead them)
         uint32_t lslot = 0u;
@@ -512,7 +552,7 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
                                          const typename BipArith<T>::CT *Md, int lane, int ci, int nfl,
                                          const typename BipArith<T>::CV seedsh[2], bool shifts, bool active, int lam,
                                          int cfg, double *out, int *status, int prefetch, double *csub = nullptr,
-                                         int cshift = 0) {
+                                         int cshift = 0, int cfg1 = -1) {
     using Ar = BipArith<T>;
     const uint32_t full = (1u << n) - 1u;
     const uint4 mk = __ldg(tab.masks + mask_index);
@@ -549,12 +589,14 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
     }
     if (!needclose) return;   // no half-visited vertex and not full: disconnected, dropped
     const typename Ar::CV C = Ar::close_sum(csum, nfl, ci);
-    if (SUB && ones == 0u) {
-        if (active && lam == 0) {
-            const double c = Ar::to_double(C);
-            csub[(int64_t)B << cshift] = CLOW ? c : ldexp(c, __popc(B) - 1);
+    if constexpr (SUB) {
+        if (ones == 0u) {
+            if (active && lam == 0) {
+                const double c = Ar::to_double(C);
+                csub[(int64_t)B << cshift] = CLOW ? c : ldexp(c, __popc(B) - 1);
+            }
+            if (dead) return;
         }
-        if (dead) return;
     }
     if (ones) {
         const int k = __ffs(ones) - 1;
@@ -573,11 +615,34 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
         else if (k == 0) *tp = Ar::add(*tp, tv);                                 // the extension into 0' wrote it
         else *tp = tv;
     } else if (active && (lam == 0) && out) {
-        const double c = CLOW ? Ar::to_double(C) : ldexp(Ar::to_double(C), n - 1);
-        out[cfg] = c;
-        if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
+        if constexpr (std::is_same<T, float2>::value) {   // cfg1: the lane's second configuration, or -1
+            const double c0 = CLOW ? C.x : ldexp(C.x, n - 1);
+            out[cfg] = c0;
+            bool fin = isfinite(c0);
+            if (cfg1 >= 0) {
+                const double c1 = CLOW ? C.y : ldexp(C.y, n - 1);
+                out[cfg1] = c1;
+                fin = fin && isfinite(c1);
+            }
+            if (!fin) atomicOr(status, kStatusNonFinite);
+        } else {
+            const double c = CLOW ? Ar::to_double(C) : ldexp(Ar::to_double(C), n - 1);
+            out[cfg] = c;
+            if (!isfinite(c)) atomicOr(status, kStatusNonFinite);
+        }
     }
 }
+
+// An element of the matrices or states from the values of the lane's configurations: the
+// packed mixed types take both (x, y), the one-per-lane types the first.
+template <typename T>
+__device__ __forceinline__ void to_elem2(double x0, double, T &r) {
+    to_elem(x0, r);
+}
+__device__ __forceinline__ void to_elem2(double x0, double x1, float2 &r) {
+    r = make_float2((float)x0, (float)x1);
+}
+__device__ __forceinline__ void to_elem2(double x0, double x1, double2 &r) { r = make_double2(x0, x1); }
 
 template <typename T, bool CLOW, bool SUB = false>
 __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ BipArgs a) {
@@ -599,10 +664,13 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
     typename BipArith<T>::CV seedsh[2];
     for (int s = 0; s < 2; ++s) {
         sig[s] = a.absmode ? fabs(a.sigma2[lam][s]) : a.sigma2[lam][s];
-        to_elem(sgn * 2.0 * sig[s], seedsh[s]);
+        to_elem2(sgn * 2.0 * sig[s], sgn * 2.0 * sig[s], seedsh[s]);
     }
     const bool shifts = a.shifts != 0;
     const int nbatch = *a.n_batches;
+    // mixed with two configurations per lane: the second sits cpl places after the first
+    constexpr bool kPair = std::is_same<T, float2>::value;
+    const int cpl = kLanes / nfl;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_batch = atomicAdd(a.queue, 1);
@@ -614,9 +682,12 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
         const BipOrderTab &tab = a.tabs[n];
         const bool active = (ci < bd.z) && (ci * nfl + nfl <= kLanes);
         const int cfg = active ? a.batch_list[bd.y + ci] : -1;
+        const bool active1 = kPair && active && (ci + cpl < bd.z);
+        const int cfg1 = active1 ? a.batch_list[bd.y + cpl + ci] : -1;
         const int n2 = 2 * n;
-        const double *Mc = nullptr;
+        const double *Mc = nullptr, *Mc1 = nullptr;
         if (active) Mc = a.M + a.moff[cfg] + (size_t)lam * n2 * n2;
+        if (active1) Mc1 = a.M + a.moff[cfg1] + (size_t)lam * n2 * n2;
         double *cs = nullptr;
         int csh = 0;
         if (SUB && active) {
@@ -627,16 +698,22 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
         const double cfac = sgn * a.loop_weight;
         for (int e = warp; e < n2 * n2; e += nwarps) {
             double val = active ? Mc[e] : 0.0;
-            if (a.absmode) val = fabs(val);
+            double val1 = active1 ? Mc1[e] : 0.0;
+            if (a.absmode) {
+                val = fabs(val);
+                val1 = fabs(val1);
+            }
             const int r = e / n2, c = e % n2;
             if (CLOW) {
-                const double m = (r == c) ? val + sgn * sig[r & 1] : val;   // a(j s, j s) - alpha_{b,s}
-                to_elem(m, Ms[e * kLanes + lane]);
-                to_elem(cfac * m, Md[e * kLanes + lane]);
+                const double d = (r == c) ? sgn * sig[r & 1] : 0.0;   // a(j s, j s) - alpha_{b,s}
+                const double m = (r == c) ? val + d : val, m1 = (r == c) ? val1 + d : val1;
+                to_elem2(m, m1, Ms[e * kLanes + lane]);
+                to_elem2(cfac * m, cfac * m1, Md[e * kLanes + lane]);
             } else {
                 const bool shifted = (r == c) && (r >= 2) && shifts;   // (j, s) -> (j, s), j >= 1
-                to_elem(shifted ? val + sgn * sig[r & 1] : val, Ms[e * kLanes + lane]);
-                to_elem(cfac * val, Md[e * kLanes + lane]);
+                const double d = sgn * sig[r & 1];
+                to_elem2(shifted ? val + d : val, shifted ? val1 + d : val1, Ms[e * kLanes + lane]);
+                to_elem2(cfac * val, cfac * val1, Md[e * kLanes + lane]);
             }
         }
         // Start: the loop through the normal point of vertex 0 on sublattice s_0 (layer 1,
@@ -644,8 +721,8 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
         if (warp == 0) {
             for (int s0 = 0; s0 < 2; ++s0) {
                 const uint32_t off = __ldg(tab.rank4 + 1 + s0);
-                to_elem((CLOW && lam != 0) ? 0.0 : 1.0,
-                        ring[(size_t)(1 & 1) * a.slot_elems + (size_t)(off + 3u * (uint32_t)s0) * kLanes + lane]);
+                const double one = (CLOW && lam != 0) ? 0.0 : 1.0;
+                to_elem2(one, one, ring[(size_t)(1 & 1) * a.slot_elems + (size_t)(off + 3u * (uint32_t)s0) * kLanes + lane]);
             }
         }
         __syncthreads();
@@ -657,7 +734,7 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
                 bip_mask<T, CLOW, SUB>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src,
                                        dst1, Ms, Md, lane, ci, nfl, seedsh, shifts, active, lam, cfg, a.out, a.status,
-                                       a.prefetch, cs, csh);
+                                       a.prefetch, cs, csh, cfg1);
             __syncthreads();
         }
     }
@@ -684,6 +761,15 @@ struct BipLaunch {
     bool allow_empty = false;            // order 0 = empty derived problem (skipped by the planner)
 };
 
+// Largest n_max of the two-configurations-per-lane mixed sweep: its matrices (4 n^2 entries per
+// lane, FP32 pairs and FP64 pairs for the closes) fill 192 KB of shared memory at n = 8.
+constexpr int kBipPairMaxN = 8;
+
+// Configurations per lane of a launch: two for the mixed sweep up to kBipPairMaxN, else one.
+static int bip_lane_width(const BipLaunch &L) {
+    return (L.precision == COS_MIXED && !L.csub && L.n_max <= kBipPairMaxN) ? 2 : 1;
+}
+
 static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t stream) {
     std::string err;
     const BipOrderTab *tabs = bip_device_orders(ws->device, &err);
@@ -694,8 +780,9 @@ static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t str
     int nsm = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
     const size_t slot_elems = (size_t)bip_host_order(L.n_max).max_slots * kLanes;
-    const size_t per_cta = 2 * slot_elems * sizeof(double);
-    const int cpb = kLanes / L.n_mat;
+    const size_t per_cta = 2 * slot_elems * sizeof(double);   // 8-byte states at most (float2 at width 2)
+    const int width = bip_lane_width(L);
+    const int cpb = width * (kLanes / L.n_mat);
     const int max_batches = (L.n_cfg + cpb - 1) / cpb + COS_NMAX;
     int grid = std::max(1, std::min(nsm, max_batches));
     size_t free_b = 0, total_b = 0;
@@ -706,11 +793,13 @@ static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t str
     ws->last_grid = grid;
     cos_status st = ensure(&ws->scratch, &ws->scratch_bytes, (size_t)grid * per_cta, 1, "bipartite layer scratch");
     if (st != COS_OK) return st;
-    // extension matrices in the state type, close matrices in FP64 (double-float for df64)
+    // extension matrices in the state type, close matrices in FP64 (double-float for df64), per
+    // configuration of the lane
     const size_t mel = (size_t)4 * L.n_max * L.n_max * kLanes;
-    const size_t es = L.precision == COS_MIXED ? sizeof(float) : sizeof(double);
-    const size_t smem = ((mel * es + 15) & ~size_t(15)) + mel * sizeof(double);
+    const size_t es = width * (L.precision == COS_MIXED ? sizeof(float) : sizeof(double));
+    const size_t smem = ((mel * es + 15) & ~size_t(15)) + mel * width * sizeof(double);
     auto kern = L.csub                     ? (L.clow ? dp_bip_kernel<double, true, true> : dp_bip_kernel<double, false, true>)
+                : width == 2               ? (L.clow ? dp_bip_kernel<float2, true> : dp_bip_kernel<float2, false>)
                 : L.precision == COS_DF64  ? (L.clow ? dp_bip_kernel<df64, true> : dp_bip_kernel<df64, false>)
                 : L.precision == COS_MIXED ? (L.clow ? dp_bip_kernel<float, true> : dp_bip_kernel<float, false>)
                                            : (L.clow ? dp_bip_kernel<double, true> : dp_bip_kernel<double, false>);
@@ -749,7 +838,8 @@ static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t str
 }
 
 static cos_status run_bip(Workspace *ws, BipLaunch L, double *d_abs_mass, cudaStream_t stream) {
-    cos_status st = launch_plan_batches(ws, L.n_cfg, L.n_max, L.order, kLanes / L.n_mat, stream, L.allow_empty);
+    cos_status st = launch_plan_batches(ws, L.n_cfg, L.n_max, L.order, bip_lane_width(L) * (kLanes / L.n_mat), stream,
+                                        L.allow_empty);
     if (st != COS_OK) return st;
     st = launch_bip(ws, L, stream);
     if (st != COS_OK || !d_abs_mass) return st;
