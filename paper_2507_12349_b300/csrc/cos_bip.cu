@@ -425,9 +425,10 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
     const uint32_t msb = kByte ? (uint32_t)__cvta_generic_to_shared(Ms) : 0u;
     T o[NV];
     uint32_t ra[NV];
-    if constexpr (std::is_same<T, float>::value || std::is_same<T, float2>::value) {
-        // mixed: lane t decodes state t once per row, the loop shuffles it (FP32 rows are short
-        // in issue time, so the per-state chain below would lead them)
+    if constexpr (std::is_same<T, float>::value) {
+        // mixed, one configuration per lane: lane t decodes state t once per row, the loop
+        // shuffles it (such rows are short in issue time, so the per-state chain below would
+        // lead them)
         uint32_t lslot = 0u;
         int lrs = 0;
         if (lane < NV) {
@@ -443,7 +444,8 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
             o[t] = src[(size_t)sl * kLanes + lane];
         }
     } else {
-        // FP64 and double-float: the set bits of R in turn (a short branch-free chain per state)
+        // FP64, double-float and mixed with two configurations per lane: the set bits of R in
+        // turn (a short branch-free chain per state)
         uint32_t rr = R;
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
@@ -822,9 +824,10 @@ static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t str
     a.scratch = ws->scratch;
     a.slot_elems = slot_elems;
     a.smem_n = L.n_max;
-    // an L2 prefetch of the next mask's rows pays only with 4-byte states (mixed: +1.6 %); with
-    // 8-byte states it costs (double-float -3.7 %, FP64 -0.4 %, order 8)
-    a.prefetch = L.precision == COS_MIXED ? 1 : 0;
+    // an L2 prefetch of the next mask's rows pays only with 4-byte states (mixed, one per lane:
+    // +1.6 %); with 8-byte states it costs (double-float -3.7 %, FP64 -0.4 %, mixed two per lane
+    // -1 %, order 8)
+    a.prefetch = (L.precision == COS_MIXED && width == 1) ? 1 : 0;
     a.out = L.out;
     a.status = ws->status;
     a.csub = L.csub;
