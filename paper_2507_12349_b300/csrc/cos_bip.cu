@@ -332,6 +332,50 @@ struct BipArith<df64> {
     static __device__ __forceinline__ df64 add(df64 a, df64 b) { return df64_add(a, b); }
     static __device__ __forceinline__ double to_double(CV a) { return df64_to_double(a); }
 };
+// Double-float with two configurations per lane (components x, y of df64x2): the compensated
+// accumulation of cos_df64.cuh in packed pairs, each component bit for bit the one-per-lane
+// mode's operation.  The close runs on the extension matrices' entries (and the unshifted
+// diagonal), its sign (sgn w = +-1) applied to the flavor-summed value: every step of the
+// compensated sums is symmetric under negation, so the values are those of the one-per-lane
+// sweep.
+template <>
+struct BipArith<df64x2> {
+    using Acc = DotAcc2;
+    using CT = df64x2;
+    using CAcc = DotAcc2;
+    using CV = df64x2;
+    static __device__ __forceinline__ Acc zero() {
+        DotAcc2 a;
+        a.s = a.c = make_float2(0.0f, 0.0f);
+        return a;
+    }
+    static __device__ __forceinline__ CAcc czero() { return zero(); }
+    static __device__ __forceinline__ Acc first(const df64x2 &x, const df64x2 &y) {
+        return dot_first2(x.hi, x.lo, y.hi, y.lo);
+    }
+    static __device__ __forceinline__ void mad(Acc &a, const df64x2 &x, const df64x2 &y) {
+        dot_add2(a, x.hi, x.lo, y.hi, y.lo);
+    }
+    static __device__ __forceinline__ void cmad(CAcc &a, const df64x2 &x, const df64x2 &y) {
+        dot_add2(a, x.hi, x.lo, y.hi, y.lo);
+    }
+    static __device__ __forceinline__ df64x2 store(const Acc &a) {
+        df64x2 r;
+        r.hi = a.s;
+        r.lo = a.c;
+        return r;
+    }
+    static __device__ __forceinline__ CV close_sum(const CAcc &a, int nfl, int ci) {
+        return dfpair(df64_flavor_sum(dot_value(DotAcc{a.s.x, a.c.x}), nfl, ci),
+                      df64_flavor_sum(dot_value(DotAcc{a.s.y, a.c.y}), nfl, ci));
+    }
+    static __device__ __forceinline__ CV cadd(const CV &a, const CV &b) {
+        return dfpair(df64_add(dfx(a), dfx(b)), df64_add(dfy(a), dfy(b)));
+    }
+    static __device__ __forceinline__ df64x2 seed(const CV &a) { return a; }
+    static __device__ __forceinline__ df64x2 add(const df64x2 &a, const df64x2 &b) { return cadd(a, b); }
+};
+
 // Mixed mode with two configurations per lane (components x, y): the extensions as packed FP32
 // pairs (each component bit for bit the one-per-lane mode's operation), the closes in FP64 per
 // component.  No to_double: the sweep writes each component's output itself.
@@ -393,6 +437,15 @@ template <>
 __device__ __forceinline__ double2 lds_as<double2>(uint32_t a) {
     double2 r;
     asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "r"(a));
+    return r;
+}
+
+template <>
+__device__ __forceinline__ df64x2 lds_as<df64x2>(uint32_t a) {
+    df64x2 r;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r.hi.x), "=f"(r.hi.y), "=f"(r.lo.x), "=f"(r.lo.y)
+                 : "r"(a));
     return r;
 }
 
@@ -459,7 +512,16 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
     if (needclose) {
         // Md[(v,s)][(h,s_h)] at md + (ra - msb) kr + (h 2 + s_h) 32 sizeof(CT), kr = sizeof(CT) / sizeof(T)
         const uint32_t hc = (uint32_t)((h * 2 + sh) * kLanes);
-        if constexpr (kByte) {
+        if constexpr (std::is_same<T, df64x2>::value) {
+            // the close on the extension matrices' column (h, s_h), except the head's own state,
+            // whose entry is the unshifted diagonal kept apart in Md[(h, s_h)][lane]; the sign
+            // sgn w comes after the flavor sum
+            const uint32_t own = msb + (uint32_t)((h * 2 + sh) * n2 * kLanes + lane) * kU;
+            const uint32_t dga = (uint32_t)__cvta_generic_to_shared(Md) + (hc + (uint32_t)lane) * kU;
+#pragma unroll
+            for (int t = 0; t < NV; ++t)
+                Ar::cmad(csum, o[t], lds_as<CT>(ra[t] == own ? dga : ra[t] + hc * kU));
+        } else if constexpr (kByte) {
             constexpr uint32_t kr = sizeof(CT) / sizeof(T);
             const uint32_t dmd = (uint32_t)__cvta_generic_to_shared(Md) - kr * msb + hc * (uint32_t)sizeof(CT);
 #pragma unroll
@@ -554,7 +616,7 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
                                          const typename BipArith<T>::CT *Md, int lane, int ci, int nfl,
                                          const typename BipArith<T>::CV seedsh[2], bool shifts, bool active, int lam,
                                          int cfg, double *out, int *status, int prefetch, double *csub = nullptr,
-                                         int cshift = 0, int cfg1 = -1) {
+                                         int cshift = 0, int cfg1 = -1, float csgn = 1.0f) {
     using Ar = BipArith<T>;
     const uint32_t full = (1u << n) - 1u;
     const uint4 mk = __ldg(tab.masks + mask_index);
@@ -590,7 +652,13 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
         }
     }
     if (!needclose) return;   // no half-visited vertex and not full: disconnected, dropped
-    const typename Ar::CV C = Ar::close_sum(csum, nfl, ci);
+    typename Ar::CV C = Ar::close_sum(csum, nfl, ci);
+    if constexpr (std::is_same<T, df64x2>::value) {   // the close's sign sgn w = csgn (see BipArith<df64x2>)
+        if (csgn < 0.0f) {
+            C.hi = neg2(C.hi);
+            C.lo = neg2(C.lo);
+        }
+    }
     if constexpr (SUB) {
         if (ones == 0u) {
             if (active && lam == 0) {
@@ -617,12 +685,21 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
         else if (k == 0) *tp = Ar::add(*tp, tv);                                 // the extension into 0' wrote it
         else *tp = tv;
     } else if (active && (lam == 0) && out) {
-        if constexpr (std::is_same<T, float2>::value) {   // cfg1: the lane's second configuration, or -1
-            const double c0 = CLOW ? C.x : ldexp(C.x, n - 1);
+        if constexpr (std::is_same<T, float2>::value || std::is_same<T, df64x2>::value) {
+            // cfg1: the lane's second configuration, or -1
+            double v0, v1;
+            if constexpr (std::is_same<T, float2>::value) {
+                v0 = C.x;
+                v1 = C.y;
+            } else {
+                v0 = df64_to_double(dfx(C));
+                v1 = df64_to_double(dfy(C));
+            }
+            const double c0 = CLOW ? v0 : ldexp(v0, n - 1);
             out[cfg] = c0;
             bool fin = isfinite(c0);
             if (cfg1 >= 0) {
-                const double c1 = CLOW ? C.y : ldexp(C.y, n - 1);
+                const double c1 = CLOW ? v1 : ldexp(v1, n - 1);
                 out[cfg1] = c1;
                 fin = fin && isfinite(c1);
             }
@@ -645,6 +722,7 @@ __device__ __forceinline__ void to_elem2(double x0, double x1, float2 &r) {
     r = make_float2((float)x0, (float)x1);
 }
 __device__ __forceinline__ void to_elem2(double x0, double x1, double2 &r) { r = make_double2(x0, x1); }
+__device__ __forceinline__ void to_elem2(double x0, double x1, df64x2 &r) { r = dfpair(df64_from(x0), df64_from(x1)); }
 
 template <typename T, bool CLOW, bool SUB = false>
 __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ BipArgs a) {
@@ -670,9 +748,13 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
     }
     const bool shifts = a.shifts != 0;
     const int nbatch = *a.n_batches;
-    // mixed with two configurations per lane: the second sits cpl places after the first
-    constexpr bool kPair = std::is_same<T, float2>::value;
+    // two configurations per lane (mixed float2, double-float df64x2): the second sits cpl
+    // places after the first.  Double-float keeps only the close's diagonal in Md and applies
+    // the close's sign sgn w = +-1 (loop weight 1) per mask.
+    constexpr bool kPair = std::is_same<T, float2>::value || std::is_same<T, df64x2>::value;
+    constexpr bool kDiagClose = std::is_same<T, df64x2>::value;
     const int cpl = kLanes / nfl;
+    const float csgn = (sgn * a.loop_weight < 0.0) ? -1.0f : 1.0f;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_batch = atomicAdd(a.queue, 1);
@@ -710,12 +792,20 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
                 const double d = (r == c) ? sgn * sig[r & 1] : 0.0;   // a(j s, j s) - alpha_{b,s}
                 const double m = (r == c) ? val + d : val, m1 = (r == c) ? val1 + d : val1;
                 to_elem2(m, m1, Ms[e * kLanes + lane]);
-                to_elem2(cfac * m, cfac * m1, Md[e * kLanes + lane]);
+                if constexpr (kDiagClose) {
+                    if (r == c) to_elem2(m, m1, Md[r * kLanes + lane]);
+                } else {
+                    to_elem2(cfac * m, cfac * m1, Md[e * kLanes + lane]);
+                }
             } else {
                 const bool shifted = (r == c) && (r >= 2) && shifts;   // (j, s) -> (j, s), j >= 1
                 const double d = sgn * sig[r & 1];
                 to_elem2(shifted ? val + d : val, shifted ? val1 + d : val1, Ms[e * kLanes + lane]);
-                to_elem2(cfac * val, cfac * val1, Md[e * kLanes + lane]);
+                if constexpr (kDiagClose) {
+                    if (r == c) to_elem2(val, val1, Md[r * kLanes + lane]);   // unshifted
+                } else {
+                    to_elem2(cfac * val, cfac * val1, Md[e * kLanes + lane]);
+                }
             }
         }
         // Start: the loop through the normal point of vertex 0 on sublattice s_0 (layer 1,
@@ -736,7 +826,7 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
                 bip_mask<T, CLOW, SUB>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src,
                                        dst1, Ms, Md, lane, ci, nfl, seedsh, shifts, active, lam, cfg, a.out, a.status,
-                                       a.prefetch, cs, csh, cfg1);
+                                       a.prefetch, cs, csh, cfg1, csgn);
             __syncthreads();
         }
     }
@@ -763,13 +853,17 @@ struct BipLaunch {
     bool allow_empty = false;            // order 0 = empty derived problem (skipped by the planner)
 };
 
-// Largest n_max of the two-configurations-per-lane mixed sweep: its matrices (4 n^2 entries per
-// lane, FP32 pairs and FP64 pairs for the closes) fill 192 KB of shared memory at n = 8.
+// Largest n_max of the two-configurations-per-lane sweeps: their matrices (4 n^2 entries per
+// lane) fill 192 KB of shared memory at n = 8 (mixed: FP32 pairs, FP64 pairs for the closes)
+// or 136 KB (double-float: df64 pairs, the closes on them and a diagonal of 2n pairs).
 constexpr int kBipPairMaxN = 8;
 
-// Configurations per lane of a launch: two for the mixed sweep up to kBipPairMaxN, else one.
+// Configurations per lane of a launch: two for the mixed sweep and, at loop weight 1 (the close
+// sign +-1 applied exactly), the double-float sweep up to kBipPairMaxN; else one.
 static int bip_lane_width(const BipLaunch &L) {
-    return (L.precision == COS_MIXED && !L.csub && L.n_max <= kBipPairMaxN) ? 2 : 1;
+    if (L.csub || L.n_max > kBipPairMaxN) return 1;
+    if (L.precision == COS_MIXED) return 2;
+    return (L.precision == COS_DF64 && L.loop_weight == 1) ? 2 : 1;
 }
 
 static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t stream) {
@@ -782,8 +876,9 @@ static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t str
     int nsm = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
     const size_t slot_elems = (size_t)bip_host_order(L.n_max).max_slots * kLanes;
-    const size_t per_cta = 2 * slot_elems * sizeof(double);   // 8-byte states at most (float2 at width 2)
     const int width = bip_lane_width(L);
+    const bool dfpair_sweep = width == 2 && L.precision == COS_DF64;
+    const size_t per_cta = 2 * slot_elems * (dfpair_sweep ? 16 : sizeof(double));   // state bytes per lane
     const int cpb = width * (kLanes / L.n_mat);
     const int max_batches = (L.n_cfg + cpb - 1) / cpb + COS_NMAX;
     int grid = std::max(1, std::min(nsm, max_batches));
@@ -799,8 +894,11 @@ static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t str
     // configuration of the lane
     const size_t mel = (size_t)4 * L.n_max * L.n_max * kLanes;
     const size_t es = width * (L.precision == COS_MIXED ? sizeof(float) : sizeof(double));
-    const size_t smem = ((mel * es + 15) & ~size_t(15)) + mel * width * sizeof(double);
+    const size_t close_bytes =
+        dfpair_sweep ? (size_t)2 * L.n_max * kLanes * sizeof(df64x2) : mel * width * sizeof(double);
+    const size_t smem = ((mel * es + 15) & ~size_t(15)) + close_bytes;
     auto kern = L.csub                     ? (L.clow ? dp_bip_kernel<double, true, true> : dp_bip_kernel<double, false, true>)
+                : dfpair_sweep             ? (L.clow ? dp_bip_kernel<df64x2, true> : dp_bip_kernel<df64x2, false>)
                 : width == 2               ? (L.clow ? dp_bip_kernel<float2, true> : dp_bip_kernel<float2, false>)
                 : L.precision == COS_DF64  ? (L.clow ? dp_bip_kernel<df64, true> : dp_bip_kernel<df64, false>)
                 : L.precision == COS_MIXED ? (L.clow ? dp_bip_kernel<float, true> : dp_bip_kernel<float, false>)

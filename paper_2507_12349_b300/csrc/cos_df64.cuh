@@ -116,6 +116,20 @@ __device__ __forceinline__ float2 two_sum2(float2 a, float2 b, float2 &e) {
     return s;
 }
 
+// Two df64 values (configurations x and y) of one lane, stored as (hi pair, lo pair) so that each
+// pair is one packed-FP32 operand.
+struct __align__(16) df64x2 {
+    float2 hi, lo;
+};
+__device__ __forceinline__ df64 dfx(const df64x2 &v) { return df64{v.hi.x, v.lo.x}; }
+__device__ __forceinline__ df64 dfy(const df64x2 &v) { return df64{v.hi.y, v.lo.y}; }
+__device__ __forceinline__ df64x2 dfpair(df64 x, df64 y) {
+    df64x2 r;
+    r.hi = make_float2(x.hi, y.hi);
+    r.lo = make_float2(x.lo, y.lo);
+    return r;
+}
+
 // Compensated dot-product accumulators of two configurations: value = s + c per component.
 struct DotAcc2 {
     float2 s, c;

@@ -273,19 +273,7 @@ __device__ __forceinline__ void fwd_mask_pair(const OrderTab &tab, uint32_t mask
 
 // ---------------------------------------------------------------- double-float, two per lane
 
-// Two df64 values (configurations x and y) of one lane, stored as (hi pair, lo pair) so that each
-// pair is one packed-FP32 operand.
-struct __align__(16) df64x2 {
-    float2 hi, lo;
-};
-__device__ __forceinline__ df64 dfx(const df64x2 &v) { return df64{v.hi.x, v.lo.x}; }
-__device__ __forceinline__ df64 dfy(const df64x2 &v) { return df64{v.hi.y, v.lo.y}; }
-__device__ __forceinline__ df64x2 dfpair(df64 x, df64 y) {
-    df64x2 r;
-    r.hi = make_float2(x.hi, y.hi);
-    r.lo = make_float2(x.lo, y.lo);
-    return r;
-}
+// df64x2 (two configurations' df64 values of a lane) and its accessors: cos_df64.cuh.
 
 // The accumulators are stored as they stand (sum, error) for both configurations.
 __device__ __forceinline__ void push_target_dfp(df64x2 *__restrict__ dst1, uint32_t tslot, int q, const DotAcc2 &d,
