@@ -377,25 +377,29 @@ struct BipArith<df64x2> {
 };
 
 // Mixed mode with two configurations per lane (components x, y): the extensions as packed FP32
-// pairs (each component bit for bit the one-per-lane mode's operation), the closes in FP64 per
-// component.  No to_double: the sweep writes each component's output itself.
+// pairs (each component bit for bit the one-per-lane mode's operation); the closes as the
+// square-lattice mixed sweep takes them, compensated FP32 sums (close_add2: Dot2 on close
+// matrices split into FP32 pairs hi + lo) widened and added in FP64 once per mask, so the FP64
+// pipe carries no per-state work.  No to_double: the sweep writes each component's output.
 template <>
 struct BipArith<float2> {
     using Acc = float2;
-    using CT = double2;
-    using CAcc = double2;
+    using CT = df64x2;     // close matrices sgn w M split into FP32 pairs, per configuration
+    using CAcc = DotAcc2;
     using CV = double2;
     static __device__ __forceinline__ Acc zero() { return make_float2(0.0f, 0.0f); }
-    static __device__ __forceinline__ CAcc czero() { return make_double2(0.0, 0.0); }
+    static __device__ __forceinline__ CAcc czero() {
+        DotAcc2 a;
+        a.s = a.c = make_float2(0.0f, 0.0f);
+        return a;
+    }
     static __device__ __forceinline__ Acc first(float2 x, float2 y) { return mul2(x, y); }
     static __device__ __forceinline__ void mad(Acc &a, float2 x, float2 y) { a = fma2(x, y, a); }
-    static __device__ __forceinline__ void cmad(CAcc &a, float2 x, double2 y) {
-        a.x = fma(widen(x.x), y.x, a.x);
-        a.y = fma(widen(x.y), y.y, a.y);
-    }
+    static __device__ __forceinline__ void cmad(CAcc &a, float2 x, const df64x2 &y) { close_add2(a, x, y.hi, y.lo); }
     static __device__ __forceinline__ float2 store(Acc a) { return a; }
-    static __device__ __forceinline__ CV close_sum(CAcc a, int nfl, int ci) {
-        return make_double2(flavor_sum(a.x, nfl, ci), flavor_sum(a.y, nfl, ci));
+    static __device__ __forceinline__ CV close_sum(const CAcc &a, int nfl, int ci) {
+        return make_double2(flavor_sum(close_value(DotAcc{a.s.x, a.c.x}), nfl, ci),
+                            flavor_sum(close_value(DotAcc{a.s.y, a.c.y}), nfl, ci));
     }
     static __device__ __forceinline__ CV cadd(CV a, CV b) { return make_double2(a.x + b.x, a.y + b.y); }
     static __device__ __forceinline__ float2 seed(CV a) {

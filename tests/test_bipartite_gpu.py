@@ -140,18 +140,25 @@ def test_bipartite_uneven_orders_and_order9(precision):
 @pytest.mark.parametrize("n_mat,wt", [(1, 1), (2, 1), (3, 2)])
 def test_bipartite_two_per_lane_bitwise(precision, n_mat, wt):
     """Mixed mode, and double-float at loop weight 1, run two configurations per lane up to
-    n_max = 8 and one per lane at n_max = 9.  Each packed operation is the one-per-lane
-    operation (double-float: the close's sign applied after the flavor sum, exact since every
-    compensated step is symmetric under negation), so on the same configurations (uneven
-    orders; batches whose lanes hold one or two configurations) both give the same values, for
-    the sum and the absolute mass."""
+    n_max = 8 and one per lane at n_max = 9, on the same configurations (uneven orders; batches
+    whose lanes hold one or two configurations).  Double-float: each packed operation is the
+    one-per-lane operation and the close's sign is applied after the flavor sum (exact, every
+    compensated step being symmetric under negation), so both give the same values.  Mixed:
+    the extensions are the same operations, but two per lane close with compensated FP32 sums
+    (about 47 bits) where one per lane closes in FP64, and a seed rounded to FP32 may then
+    differ by an ulp; the two agree within the mixed mode's error bound."""
     orders = [8, 3, 7, 1, 6, 5, 8, 2, 4] + [5] * 41 + [7] * 3
     M4s = [rand_m4(9900 + c, 1, n_mat, n)[0] for c, n in enumerate(orders)]
     s2 = [[0.05 - 0.02 * l, -0.03 + 0.01 * l] for l in range(n_mat)]
     a, ma = run(M4s, n_mat, wt, s2, abs_mass=True, precision=precision)
     b, mb = run(M4s, n_mat, wt, s2, abs_mass=True, precision=precision, n_max=9)
     assert np.all(np.isfinite(a))
-    assert np.array_equal(a, b) and np.array_equal(ma, mb)
+    if precision == "df64":
+        assert np.array_equal(a, b) and np.array_equal(ma, mb)
+    else:
+        for c, n in enumerate(orders):
+            assert abs(a[c] - b[c]) <= mixed_bound(n, mb[c]), (c, n, a[c], b[c])
+            assert ma[c] == pytest.approx(mb[c], rel=1e-5)
 
 
 def test_bipartite_deterministic():
