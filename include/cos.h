@@ -61,7 +61,10 @@ typedef enum {
 typedef enum {
     COS_FP64 = 0,   /* every step in FP64 */
     COS_MIXED = 1,  /* clow extension in FP32 with FP32 accumulation; loop-closing
-                       sums, seeds of new loops and the sink in FP64 */
+                       sums as compensated FP32 sums (Dot2 on close matrices split into
+                       FP32 pairs, about 47 bits) widened and added in FP64 once per mask
+                       (the bipartite sweep at n_max = 9: FP64 sums on exactly widened
+                       states); seeds of new loops and the sink formed in FP64 */
     COS_DF64 = 2    /* double-float: states, matrices, extension and loop-closing sums as
                        unevaluated pairs hi + lo of FP32 numbers (about 48 bits), each dot
                        product a compensated (TwoSum / FMA TwoProduct) accumulation on the
