@@ -437,12 +437,6 @@ __device__ __forceinline__ float2 lds_as<float2>(uint32_t a) {
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(a));
     return r;
 }
-template <>
-__device__ __forceinline__ double2 lds_as<double2>(uint32_t a) {
-    double2 r;
-    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "r"(a));
-    return r;
-}
 
 template <>
 __device__ __forceinline__ df64x2 lds_as<df64x2>(uint32_t a) {
@@ -514,7 +508,6 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
         }
     }
     if (needclose) {
-        // Md[(v,s)][(h,s_h)] at md + (ra - msb) kr + (h 2 + s_h) 32 sizeof(CT), kr = sizeof(CT) / sizeof(T)
         const uint32_t hc = (uint32_t)((h * 2 + sh) * kLanes);
         if constexpr (std::is_same<T, df64x2>::value) {
             // the close on the extension matrices' column (h, s_h), except the head's own state,
@@ -526,6 +519,7 @@ __device__ __forceinline__ void bip_row(const T *__restrict__ src, T *__restrict
             for (int t = 0; t < NV; ++t)
                 Ar::cmad(csum, o[t], lds_as<CT>(ra[t] == own ? dga : ra[t] + hc * kU));
         } else if constexpr (kByte) {
+            // Md[(v,s)][(h,s_h)] at md + (ra - msb) kr + (h 2 + s_h) 32 sizeof(CT), kr = sizeof(CT) / sizeof(T)
             constexpr uint32_t kr = sizeof(CT) / sizeof(T);
             const uint32_t dmd = (uint32_t)__cvta_generic_to_shared(Md) - kr * msb + hc * (uint32_t)sizeof(CT);
 #pragma unroll
