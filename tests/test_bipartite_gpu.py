@@ -161,6 +161,23 @@ def test_bipartite_two_per_lane_bitwise(precision, n_mat, wt):
             assert ma[c] == pytest.approx(mb[c], rel=1e-5)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "df64"])
+def test_bipartite_empty_batch_and_order_above_nmax(precision):
+    """No configurations: nothing to do, nothing written.  An order above n_max: the planner
+    flags it (COS_ERR_ORDER at the next status read), in every precision's sweep (two
+    configurations per lane in mixed and double-float at n_max <= 8)."""
+    empty_i = torch.zeros(0, dtype=torch.int32, device="cuda")
+    out = torch.zeros(0, dtype=torch.float64, device="cuda")
+    B.cos_connected_sum_bipartite_matrices(4, empty_i, torch.zeros(0, dtype=torch.int64, device="cuda"), 2, 1, None,
+                                           torch.zeros(1, dtype=torch.float64, device="cuda"), precision, out)
+    B.cos_sync_status()
+    assert out.shape == (0,)
+    M4s = [rand_m4(9950 + c, 1, 2, n)[0] for c, n in enumerate([5, 5, 6, 5])]
+    with pytest.raises(B.CosError) as ei:
+        run(M4s, 2, 1, None, n_max=5, precision=precision)
+    assert ei.value.status == -2
+
+
 def test_bipartite_deterministic():
     M4s = rand_m4(33, 40, 2, 5)
     a, _ = run(M4s, 2, 1, [[0.1, -0.1], [0.05, 0.02]])
