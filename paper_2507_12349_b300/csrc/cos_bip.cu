@@ -335,9 +335,9 @@ struct BipArith<df64> {
 // Double-float with two configurations per lane (components x, y of df64x2): the compensated
 // accumulation of cos_df64.cuh in packed pairs, each component bit for bit the one-per-lane
 // mode's operation.  The close runs on the extension matrices' entries (and the unshifted
-// diagonal), its sign (sgn w = +-1) applied to the flavor-summed value: every step of the
-// compensated sums is symmetric under negation, so the values are those of the one-per-lane
-// sweep.
+// diagonal), its factor sgn w = +-2^k applied to the flavor-summed value: every step of the
+// compensated sums is symmetric under negation and exact under scaling by a power of two, so
+// the values are those of the one-per-lane sweep.
 template <>
 struct BipArith<df64x2> {
     using Acc = DotAcc2;
@@ -614,7 +614,7 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
                                          const typename BipArith<T>::CT *Md, int lane, int ci, int nfl,
                                          const typename BipArith<T>::CV seedsh[2], bool shifts, bool active, int lam,
                                          int cfg, double *out, int *status, int prefetch, double *csub = nullptr,
-                                         int cshift = 0, int cfg1 = -1, float csgn = 1.0f) {
+                                         int cshift = 0, int cfg1 = -1, float cfac2 = 1.0f) {
     using Ar = BipArith<T>;
     const uint32_t full = (1u << n) - 1u;
     const uint4 mk = __ldg(tab.masks + mask_index);
@@ -651,10 +651,11 @@ __device__ __forceinline__ void bip_mask(const BipOrderTab &tab, uint32_t mask_i
     }
     if (!needclose) return;   // no half-visited vertex and not full: disconnected, dropped
     typename Ar::CV C = Ar::close_sum(csum, nfl, ci);
-    if constexpr (std::is_same<T, df64x2>::value) {   // the close's sign sgn w = csgn (see BipArith<df64x2>)
-        if (csgn < 0.0f) {
-            C.hi = neg2(C.hi);
-            C.lo = neg2(C.lo);
+    if constexpr (std::is_same<T, df64x2>::value) {   // the close's factor sgn w = cfac2 (see BipArith<df64x2>)
+        if (cfac2 != 1.0f) {
+            const float2 f = make_float2(cfac2, cfac2);
+            C.hi = mul2(C.hi, f);
+            C.lo = mul2(C.lo, f);
         }
     }
     if constexpr (SUB) {
@@ -748,11 +749,11 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
     const int nbatch = *a.n_batches;
     // two configurations per lane (mixed float2, double-float df64x2): the second sits cpl
     // places after the first.  Double-float keeps only the close's diagonal in Md and applies
-    // the close's sign sgn w = +-1 (loop weight 1) per mask.
+    // the close's factor sgn w = +-2^k (loop weight a power of two) per mask.
     constexpr bool kPair = std::is_same<T, float2>::value || std::is_same<T, df64x2>::value;
     constexpr bool kDiagClose = std::is_same<T, df64x2>::value;
     const int cpl = kLanes / nfl;
-    const float csgn = (sgn * a.loop_weight < 0.0) ? -1.0f : 1.0f;
+    const float cfac2 = (float)(sgn * a.loop_weight);   // +-2^k: applied exactly (double-float, two per lane)
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_batch = atomicAdd(a.queue, 1);
@@ -824,7 +825,7 @@ __global__ void __launch_bounds__(512, 1) dp_bip_kernel(const __grid_constant__ 
             for (uint32_t mi = warp; mi < cnt; mi += nwarps)
                 bip_mask<T, CLOW, SUB>(tab, first + mi, mi + nwarps < cnt ? first + mi + nwarps : 0xFFFFFFFFu, ell, n, src,
                                        dst1, Ms, Md, lane, ci, nfl, seedsh, shifts, active, lam, cfg, a.out, a.status,
-                                       a.prefetch, cs, csh, cfg1, csgn);
+                                       a.prefetch, cs, csh, cfg1, cfac2);
             __syncthreads();
         }
     }
@@ -852,16 +853,19 @@ struct BipLaunch {
 };
 
 // Largest n_max of the two-configurations-per-lane sweeps: their matrices (4 n^2 entries per
-// lane) fill 192 KB of shared memory at n = 8 (mixed: FP32 pairs, FP64 pairs for the closes)
-// or 136 KB (double-float: df64 pairs, the closes on them and a diagonal of 2n pairs).
+// lane) fill 192 KB of shared memory at n = 8 (mixed: FP32 pairs, close matrices split into
+// FP32 hi + lo pairs) or 136 KB (double-float: df64 pairs, the closes on them and a diagonal
+// of 2n pairs).
 constexpr int kBipPairMaxN = 8;
 
-// Configurations per lane of a launch: two for the mixed sweep and, at loop weight 1 (the close
-// sign +-1 applied exactly), the double-float sweep up to kBipPairMaxN; else one.
+// Configurations per lane of a launch: two for the mixed sweep and, at a loop weight that is a
+// power of two (the close's factor sgn w applied exactly), the double-float sweep up to
+// kBipPairMaxN; else one.
 static int bip_lane_width(const BipLaunch &L) {
     if (L.csub || L.n_max > kBipPairMaxN) return 1;
     if (L.precision == COS_MIXED) return 2;
-    return (L.precision == COS_DF64 && L.loop_weight == 1) ? 2 : 1;
+    const bool pow2 = L.loop_weight >= 1 && (L.loop_weight & (L.loop_weight - 1)) == 0;
+    return (L.precision == COS_DF64 && pow2) ? 2 : 1;
 }
 
 static cos_status launch_bip(Workspace *ws, const BipLaunch &L, cudaStream_t stream) {
